@@ -1,0 +1,691 @@
+/*
+ * em_oracle.c -- plain FP64 CPU oracle for fusing point clouds into a
+ * robot-centric 2.5D elevation grid, following Miki et al., "Elevation Mapping
+ * for Locomotion and Navigation using GPU" (arXiv 2204.12876).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or call
+ * this file.  Only the tests, the smoke check and the CPU-baseline leg of the
+ * benchmark use it.  It shares no code, header, table or constant with the CUDA
+ * path; it is written as plain loops over points and cells in the order the
+ * paper describes, in double precision, so that it can be checked against the
+ * paper by eye.
+ *
+ * Steps of one update (Section II-A, Fig. 2 caption; Section II-C..II-E):
+ *   1. snapshot the cell state (h, sigma_m^2, last-update time, normals)
+ *   2. per point: finiteness / range check, transform by the sensor pose,
+ *      distance d from the sensor, point variance from the noise model
+ *      (Section II-C), cell indices
+ *   3. per cell, its points in input order: wall rule (Section II-C, last
+ *      paragraph), Mahalanobis outlier gate against the snapshot (Section
+ *      II-C), then Eq. 1 and Eq. 2 applied point after point
+ *   4. ray casting against the snapshot (Section II-E, Eq. 3, Eq. 4)
+ *   5. removal of penetrated cells that were not updated recently
+ *   6. optional per-cell filters on the updated map: normals (Section II-A),
+ *      smoothing and in-painting (Section II-I)
+ * The map shift (robot-centric map, Section I) is a physical array copy.
+ *
+ * Readings of passages the paper leaves open (all listed in the design notes):
+ *   - an empty cell has sigma_m^2 = infinity, so its first point sets (h,
+ *     sigma_m^2) = (p_z, sigma_p^2): the limit of Eq. 1/2 as sigma_m^2 -> inf;
+ *   - noise model sigma_p = a0 + a1 d + a2 d^2, sigma_p^2 floored at var_min
+ *     (the paper's alpha_d d^2 is a0 = a2 = 0, a1 = sqrt(alpha_d));
+ *   - the gate and the wall rule look at the snapshot (pre-update) estimate,
+ *     so the result does not depend on the order of the points; the gate's
+ *     distance is |p_z - h| / sqrt(sigma_m^2 + sigma_p^2), reject iff > k;
+ *   - each rejected point adds outlier_variance to sigma_m^2 before the
+ *     accepted points are fused;
+ *   - time variance: sigma_t^2 per update, applied lazily from the cell's
+ *     last-update index (a Kalman prediction step);
+ *   - Eq. 3 is read with the standard deviation sqrt(sigma_m^2);
+ *   - ray samples o + k*step*rhat for k = 1, 2, ... while k*step < d, the
+ *     endpoint's own cell skipped; removal only for cells whose last update is
+ *     at least max(1, cleanup_min_age) updates old, the normal taken from the
+ *     previous normal layer ((0,0,1) where it is NaN).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_NORMALS 1u
+#define ORC_SMOOTH 2u
+#define ORC_INPAINT 4u
+
+/* per-point status codes of the trace */
+enum { ST_NONFINITE = 0, ST_RANGE = 1, ST_OUTSIDE = 2, ST_ACCEPT = 3, ST_REJECT = 4, ST_WALL = 5 };
+/* per-point marginal flags */
+enum { PF_BIN = 1, PF_GATE = 2, PF_WALL = 4, PF_RANGE = 8 };
+/* per-cell marginal flags */
+enum { CF_VALUE = 1, CF_MARK = 2 };
+
+typedef struct orc_params {
+  int32_t width, height;
+  double resolution;
+  double noise_a0, noise_a1, noise_a2;
+  double var_min;
+  double min_range, max_range;
+  double mahalanobis_k;
+  double outlier_variance;
+  int32_t wall_num_thresh;
+  double time_variance;
+  double ray_step;
+  int32_t cleanup_min_age;
+  double cleanup_normal_thresh;
+  uint32_t flags;
+} orc_params;
+
+typedef struct orc_cloud {
+  const float* pts;
+  int64_t n;
+  int32_t stride;
+  float pose[12]; /* sensor -> map, row-major 3x4 [R | t] */
+} orc_cloud;
+
+/* Optional per-update trace.  Every pointer may be NULL.  Per-point arrays are
+ * indexed over the clouds' points concatenated in order; per-cell arrays are
+ * logical row-major [iy][ix].  unit > 0 turns on the marginal bands: a
+ * decision is flagged when the exact value lies within
+ * abs_band + c * unit * (magnitude of the operands) of its threshold, c a small
+ * constant, i.e. where arithmetic with unit roundoff `unit` could decide it
+ * the other way. */
+typedef struct orc_trace {
+  int32_t* ix;
+  int32_t* iy;
+  uint8_t* status;
+  uint8_t* pflags;
+  uint8_t* mark;
+  uint8_t* cleared;
+  uint8_t* cflags;
+  int64_t counts[8]; /* in, valid, in-map, accepted, rejected, wall, cells updated, cells cleared */
+  double unit;
+  double abs_band;
+} orc_trace;
+
+typedef struct orc_map {
+  orc_params p;
+  int64_t shift_x, shift_y;
+  int32_t t_now;
+  double* h;
+  double* var;
+  int32_t* t_last;
+  double* nx;
+  double* ny;
+  double* nz;
+  double* smooth;
+  double* inpaint;
+} orc_map;
+
+static double* alloc_fill(int64_t n, double v) {
+  double* a = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  for (int64_t i = 0; i < n; ++i) a[i] = v;
+  return a;
+}
+
+static void clear_cell(orc_map* m, int64_t c) {
+  m->h[c] = NAN;
+  m->var[c] = INFINITY;
+  m->t_last[c] = 0;
+  m->nx[c] = m->ny[c] = m->nz[c] = NAN;
+  m->smooth[c] = NAN;
+  m->inpaint[c] = NAN;
+}
+
+orc_map* orc_create(const orc_params* p) {
+  if (!p || p->width <= 0 || p->height <= 0 || !(p->resolution > 0)) return NULL;
+  orc_map* m = (orc_map*)calloc(1, sizeof(orc_map));
+  m->p = *p;
+  int64_t nc = (int64_t)p->width * p->height;
+  m->h = alloc_fill(nc, NAN);
+  m->var = alloc_fill(nc, INFINITY);
+  m->t_last = (int32_t*)calloc((size_t)nc, sizeof(int32_t));
+  m->nx = alloc_fill(nc, NAN);
+  m->ny = alloc_fill(nc, NAN);
+  m->nz = alloc_fill(nc, NAN);
+  m->smooth = alloc_fill(nc, NAN);
+  m->inpaint = alloc_fill(nc, NAN);
+  return m;
+}
+
+void orc_destroy(orc_map* m) {
+  if (!m) return;
+  free(m->h); free(m->var); free(m->t_last);
+  free(m->nx); free(m->ny); free(m->nz); free(m->smooth); free(m->inpaint);
+  free(m);
+}
+
+/* lower-left corner of the map in the map frame: the map is centred on
+ * (shift_x * r, shift_y * r) and spans width*r by height*r. */
+void orc_origin(const orc_map* m, double* x0, double* y0) {
+  *x0 = m->p.resolution * ((double)m->shift_x - 0.5 * m->p.width);
+  *y0 = m->p.resolution * ((double)m->shift_y - 0.5 * m->p.height);
+}
+
+int32_t orc_t_now(const orc_map* m) { return m->t_now; }
+
+void orc_get_shift(const orc_map* m, int64_t* sx, int64_t* sy) {
+  *sx = m->shift_x;
+  *sy = m->shift_y;
+}
+
+static void copy_out(double* dst, const double* src, int64_t n) {
+  if (dst) memcpy(dst, src, sizeof(double) * (size_t)n);
+}
+
+void orc_get(const orc_map* m, double* h, double* var, int32_t* t_last, double* nx, double* ny,
+             double* nz, double* smooth, double* inpaint) {
+  int64_t nc = (int64_t)m->p.width * m->p.height;
+  copy_out(h, m->h, nc);
+  copy_out(var, m->var, nc);
+  if (t_last) memcpy(t_last, m->t_last, sizeof(int32_t) * (size_t)nc);
+  copy_out(nx, m->nx, nc);
+  copy_out(ny, m->ny, nc);
+  copy_out(nz, m->nz, nc);
+  copy_out(smooth, m->smooth, nc);
+  copy_out(inpaint, m->inpaint, nc);
+}
+
+/* Overwrite the state.  A cell is empty iff its variance is not finite; such a
+ * cell gets h = NaN.  Any pointer may be NULL (that layer is kept). */
+void orc_set(orc_map* m, const double* h, const double* var, const int32_t* t_last, const double* nx,
+             const double* ny, const double* nz, int32_t t_now, int64_t shift_x, int64_t shift_y) {
+  int64_t nc = (int64_t)m->p.width * m->p.height;
+  for (int64_t c = 0; c < nc; ++c) {
+    if (h) m->h[c] = h[c];
+    if (var) m->var[c] = var[c];
+    if (t_last) m->t_last[c] = t_last[c];
+    if (nx) m->nx[c] = nx[c];
+    if (ny) m->ny[c] = ny[c];
+    if (nz) m->nz[c] = nz[c];
+    if (!isfinite(m->var[c])) { m->var[c] = INFINITY; m->h[c] = NAN; }
+  }
+  m->t_now = t_now;
+  m->shift_x = shift_x;
+  m->shift_y = shift_y;
+}
+
+/* ---------------------------------------------------------------- helpers */
+
+static int in_map(const orc_map* m, int64_t ix, int64_t iy) {
+  return ix >= 0 && iy >= 0 && ix < m->p.width && iy < m->p.height;
+}
+
+/* distance of a coordinate (in cells) to the nearest cell edge, in metres */
+static double edge_dist(double q, double r) {
+  double f = q - floor(q);
+  return (f < 0.5 ? f : 1.0 - f) * r;
+}
+
+static int64_t clamp_index(double q) {
+  double f = floor(q);
+  if (f < -1e9) return -1000000000LL;
+  if (f > 1e9) return 1000000000LL;
+  return (int64_t)f;
+}
+
+static void flag_block(const orc_map* m, uint8_t* cflags, int64_t ix, int64_t iy, int rad, uint8_t bit) {
+  if (!cflags) return;
+  for (int64_t j = iy - rad; j <= iy + rad; ++j)
+    for (int64_t i = ix - rad; i <= ix + rad; ++i)
+      if (in_map(m, i, j)) cflags[j * m->p.width + i] |= bit;
+}
+
+/* effective variance at update t_now of a cell last written at t_last:
+ * sigma_m^2 grows by sigma_t^2 per update (Section II-C, time variance) */
+static double var_eff(const orc_params* p, double var, int32_t t_last, int32_t t_now) {
+  if (!isfinite(var)) return INFINITY;
+  return var + p->time_variance * (double)(t_now - t_last);
+}
+
+typedef struct pt_info {
+  double z, var_p, d;
+  double vx, vy, vz;    /* R * p_s: sensor-to-point vector in the map frame */
+  double sx, sy, sz;    /* magnitudes |R_r0 px| + |R_r1 py| + |R_r2 pz| per row */
+  int64_t ix, iy;
+  int cloud;
+  int status;
+  int flags;
+} pt_info;
+
+/* ------------------------------------------------------------ stencils */
+
+/* Per-cell surface normal from a least-squares plane z = a*x + b*y + c fitted
+ * to the valid cells of the 3x3 neighbourhood (normal calculation, Section
+ * II-A).  Needs at least 3 non-collinear valid cells, else NaN.  The normal is
+ * (-a, -b, 1) normalised. */
+static void compute_normals(orc_map* m) {
+  const int W = m->p.width, H = m->p.height;
+  const double r = m->p.resolution;
+  for (int iy = 0; iy < H; ++iy)
+    for (int ix = 0; ix < W; ++ix) {
+      int64_t c = (int64_t)iy * W + ix;
+      m->nx[c] = m->ny[c] = m->nz[c] = NAN;
+      if (!isfinite(m->var[c])) continue;
+      /* normal equations A^T A x = A^T b with rows [dx*r, dy*r, 1] */
+      double M[3][3] = {{0}}, rhs[3] = {0};
+      int n = 0;
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          int jx = ix + dx, jy = iy + dy;
+          if (!in_map(m, jx, jy)) continue;
+          int64_t k = (int64_t)jy * W + jx;
+          if (!isfinite(m->var[k])) continue;
+          double row[3] = {dx * r, dy * r, 1.0};
+          for (int a = 0; a < 3; ++a) {
+            for (int b = 0; b < 3; ++b) M[a][b] += row[a] * row[b];
+            rhs[a] += row[a] * m->h[k];
+          }
+          ++n;
+        }
+      if (n < 3) continue;
+      /* collinearity test on the integer offsets (exact) */
+      double det_int;
+      {
+        double sxx = M[0][0] / (r * r), sxy = M[0][1] / (r * r), syy = M[1][1] / (r * r);
+        double sx = M[0][2] / r, sy = M[1][2] / r, s1 = M[2][2];
+        det_int = sxx * (syy * s1 - sy * sy) - sxy * (sxy * s1 - sy * sx) + sx * (sxy * sy - syy * sx);
+      }
+      if (fabs(det_int) < 0.5) continue; /* integer-valued: 0 iff collinear */
+      /* Cramer's rule */
+      double det = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) -
+                   M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+                   M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+      double sol[3];
+      for (int col = 0; col < 3; ++col) {
+        double A[3][3];
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b) A[a][b] = (b == col) ? rhs[a] : M[a][b];
+        double dc = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) -
+                    A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+                    A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+        sol[col] = dc / det;
+      }
+      double nxv = -sol[0], nyv = -sol[1], nzv = 1.0;
+      double nn = sqrt(nxv * nxv + nyv * nyv + nzv * nzv);
+      m->nx[c] = nxv / nn;
+      m->ny[c] = nyv / nn;
+      m->nz[c] = nzv / nn;
+    }
+}
+
+/* 5x5 box mean over the valid cells of the window, for valid cells only
+ * (smoothing filter, Section II-I). */
+static void compute_smooth(orc_map* m) {
+  const int W = m->p.width, H = m->p.height;
+  for (int iy = 0; iy < H; ++iy)
+    for (int ix = 0; ix < W; ++ix) {
+      int64_t c = (int64_t)iy * W + ix;
+      m->smooth[c] = NAN;
+      if (!isfinite(m->var[c])) continue;
+      double s = 0.0;
+      int n = 0;
+      for (int dy = -2; dy <= 2; ++dy)
+        for (int dx = -2; dx <= 2; ++dx) {
+          int jx = ix + dx, jy = iy + dy;
+          if (!in_map(m, jx, jy)) continue;
+          int64_t k = (int64_t)jy * W + jx;
+          if (!isfinite(m->var[k])) continue;
+          s += m->h[k];
+          ++n;
+        }
+      m->smooth[c] = s / n;
+    }
+}
+
+/* Minimum in-painting (Section II-I): every 4-connected component of empty
+ * cells that does not touch the map border and has at most 8 cells is filled
+ * with the minimum height of the valid cells 8-adjacent to it.  Valid cells
+ * keep their height; other empty cells stay NaN.  Plain flood fill labelling. */
+static void compute_inpaint(orc_map* m) {
+  const int W = m->p.width, H = m->p.height;
+  const int64_t nc = (int64_t)W * H;
+  int32_t* label = (int32_t*)malloc(sizeof(int32_t) * (size_t)nc);
+  int64_t* queue = (int64_t*)malloc(sizeof(int64_t) * (size_t)nc);
+  for (int64_t c = 0; c < nc; ++c) {
+    label[c] = -1;
+    m->inpaint[c] = isfinite(m->var[c]) ? m->h[c] : NAN;
+  }
+  int32_t next_label = 0;
+  for (int64_t seed = 0; seed < nc; ++seed) {
+    if (isfinite(m->var[seed]) || label[seed] >= 0) continue;
+    int64_t qh = 0, qt = 0;
+    queue[qt++] = seed;
+    label[seed] = next_label;
+    int touches_edge = 0;
+    while (qh < qt) {
+      int64_t c = queue[qh++];
+      int cx = (int)(c % W), cy = (int)(c / W);
+      if (cx == 0 || cy == 0 || cx == W - 1 || cy == H - 1) touches_edge = 1;
+      const int ddx[4] = {1, -1, 0, 0}, ddy[4] = {0, 0, 1, -1};
+      for (int q = 0; q < 4; ++q) {
+        int jx = cx + ddx[q], jy = cy + ddy[q];
+        if (!in_map(m, jx, jy)) continue;
+        int64_t k = (int64_t)jy * W + jx;
+        if (isfinite(m->var[k]) || label[k] >= 0) continue;
+        label[k] = next_label;
+        queue[qt++] = k;
+      }
+    }
+    if (!touches_edge && qt <= 8) {
+      double mn = INFINITY;
+      for (int64_t q = 0; q < qt; ++q) {
+        int cx = (int)(queue[q] % W), cy = (int)(queue[q] / W);
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dx = -1; dx <= 1; ++dx) {
+            int jx = cx + dx, jy = cy + dy;
+            if (!in_map(m, jx, jy)) continue;
+            int64_t k = (int64_t)jy * W + jx;
+            if (isfinite(m->var[k]) && m->h[k] < mn) mn = m->h[k];
+          }
+      }
+      for (int64_t q = 0; q < qt; ++q) m->inpaint[queue[q]] = mn;
+    }
+    ++next_label;
+  }
+  free(label);
+  free(queue);
+}
+
+/* -------------------------------------------------------------- update */
+
+/* Walk one ray against the snapshot.  mode 0: mark penetrated cells (Eq. 3
+ * with the Eq. 4 guard); mode 1: only flag every cell the ray may touch as
+ * mark-marginal (used when the ray itself is marginal). */
+static void walk_ray(const orc_map* m, const pt_info* pi, const float* pose, const double* h0,
+                     const double* ve0, const double* nx0, const double* ny0, const double* nz0,
+                     uint8_t* mark, orc_trace* tr, int mode, double x0, double y0) {
+  const orc_params* p = &m->p;
+  const int W = p->width;
+  const double r = p->resolution, step = p->ray_step, d = pi->d;
+  const double ox = pose[3], oy = pose[7], oz = pose[11];
+  const double u = tr ? tr->unit : 0.0, ab = tr ? tr->abs_band : 0.0;
+  uint8_t* cflags = tr ? tr->cflags : NULL;
+  if (!(step > 0) || !(d > 0)) return;
+  const double rx = pi->vx / d, ry = pi->vy / d, rz = pi->vz / d;
+  /* samples k = 1, 2, ... while k*step < d; in marginal mode also the next one */
+  for (int64_t k = 1;; ++k) {
+    double len = (double)k * step;
+    int boundary_marginal = (u > 0) && fabs(len - d) < ab + 8.0 * u * d;
+    if (!(len < d) && !boundary_marginal) break;
+    int exists = len < d;
+    double f = len / d;
+    double sx = ox + f * pi->vx, sy = oy + f * pi->vy, sz = oz + f * pi->vz;
+    double qx = (sx - x0) / r, qy = (sy - y0) / r;
+    int64_t cx = clamp_index(qx), cy = clamp_index(qy);
+    int marginal = boundary_marginal || mode == 1;
+    if (u > 0) {
+      double esx = ab + 8.0 * u * (fabs(ox) + f * pi->sx + fabs(x0) + fabs(sx - x0));
+      double esy = ab + 8.0 * u * (fabs(oy) + f * pi->sy + fabs(y0) + fabs(sy - y0));
+      if (edge_dist(qx, r) < esx || edge_dist(qy, r) < esy) marginal = 1;
+    }
+    if (!in_map(m, cx, cy)) {
+      if (marginal && cflags) flag_block(m, cflags, cx, cy, 1, CF_MARK);
+      if (!exists) break;
+      continue;
+    }
+    if (cx == pi->ix && cy == pi->iy) { /* the endpoint's own cell is skipped */
+      if (marginal && cflags) flag_block(m, cflags, cx, cy, 1, CF_MARK);
+      if (!exists) break;
+      continue;
+    }
+    int64_t c = cy * W + cx;
+    if (isfinite(ve0[c])) {
+      double sd = sqrt(ve0[c]);
+      double thr = h0[c] - sd; /* Eq. 3 */
+      int below = sz < thr;
+      if (u > 0 && fabs(sz - thr) < ab + 8.0 * u * (fabs(oz) + f * pi->sz + fabs(h0[c]) + sd)) marginal = 1;
+      int guard_ok = 1;
+      if (p->cleanup_normal_thresh > 0) { /* Eq. 4 */
+        double n0 = nx0[c], n1 = ny0[c], n2 = nz0[c];
+        if (!(isfinite(n0) && isfinite(n1) && isfinite(n2))) { n0 = 0; n1 = 0; n2 = 1; }
+        double dot = fabs(rx * n0 + ry * n1 + rz * n2);
+        guard_ok = dot > p->cleanup_normal_thresh;
+        if (below && u > 0 && fabs(dot - p->cleanup_normal_thresh) < ab + 8.0 * u) marginal = 1;
+      }
+      if (mode == 0 && exists && below && guard_ok) mark[c] = 1;
+    }
+    if (marginal && cflags) flag_block(m, cflags, cx, cy, 1, CF_MARK);
+    if (!exists) break;
+  }
+}
+
+int orc_update(orc_map* m, const orc_cloud* clouds, int32_t ncloud, orc_trace* tr) {
+  if (!m || ncloud < 0 || (ncloud > 0 && !clouds)) return -1;
+  const orc_params* p = &m->p;
+  const int W = p->width, H = p->height;
+  const int64_t nc = (int64_t)W * H;
+  const double r = p->resolution;
+  const int32_t t_now = m->t_now + 1;
+  const double u = tr ? tr->unit : 0.0, ab = tr ? tr->abs_band : 0.0;
+  double x0, y0;
+  orc_origin(m, &x0, &y0);
+
+  int64_t npts = 0;
+  for (int ci = 0; ci < ncloud; ++ci) npts += clouds[ci].n > 0 ? clouds[ci].n : 0;
+  if (tr) {
+    memset(tr->counts, 0, sizeof(tr->counts));
+    if (tr->mark) memset(tr->mark, 0, (size_t)nc);
+    if (tr->cleared) memset(tr->cleared, 0, (size_t)nc);
+    if (tr->cflags) memset(tr->cflags, 0, (size_t)nc);
+  }
+
+  /* 1. snapshot */
+  double* h0 = (double*)malloc(sizeof(double) * (size_t)nc);
+  double* ve0 = (double*)malloc(sizeof(double) * (size_t)nc);
+  double* nx0 = (double*)malloc(sizeof(double) * (size_t)nc);
+  double* ny0 = (double*)malloc(sizeof(double) * (size_t)nc);
+  double* nz0 = (double*)malloc(sizeof(double) * (size_t)nc);
+  for (int64_t c = 0; c < nc; ++c) {
+    h0[c] = m->h[c];
+    ve0[c] = var_eff(p, m->var[c], m->t_last[c], t_now);
+    nx0[c] = m->nx[c];
+    ny0[c] = m->ny[c];
+    nz0[c] = m->nz[c];
+  }
+
+  /* 2. per point: validity, transform, noise variance, cell */
+  pt_info* pts = (pt_info*)calloc((size_t)(npts > 0 ? npts : 1), sizeof(pt_info));
+  int64_t gi = 0;
+  for (int ci = 0; ci < ncloud; ++ci) {
+    const orc_cloud* cl = &clouds[ci];
+    const float* R = cl->pose;
+    for (int64_t i = 0; i < cl->n; ++i, ++gi) {
+      pt_info* pi = &pts[gi];
+      const float* q = cl->pts + i * cl->stride;
+      double px = q[0], py = q[1], pz = q[2];
+      pi->cloud = ci;
+      pi->ix = pi->iy = INT32_MIN;
+      if (!(isfinite(px) && isfinite(py) && isfinite(pz))) { pi->status = ST_NONFINITE; continue; }
+      double d = sqrt(px * px + py * py + pz * pz);
+      pi->d = d;
+      int in_range = d >= p->min_range && d <= p->max_range;
+      if (u > 0) {
+        double bd = ab + 8.0 * u * d;
+        if (fabs(d - p->min_range) < bd || fabs(d - p->max_range) < bd) pi->flags |= PF_RANGE;
+      }
+      /* transform to the map frame */
+      pi->vx = R[0] * px + R[1] * py + R[2] * pz;
+      pi->vy = R[4] * px + R[5] * py + R[6] * pz;
+      pi->vz = R[8] * px + R[9] * py + R[10] * pz;
+      pi->sx = fabs(R[0] * px) + fabs(R[1] * py) + fabs(R[2] * pz);
+      pi->sy = fabs(R[4] * px) + fabs(R[5] * py) + fabs(R[6] * pz);
+      pi->sz = fabs(R[8] * px) + fabs(R[9] * py) + fabs(R[10] * pz);
+      double x = pi->vx + R[3], y = pi->vy + R[7], z = pi->vz + R[11];
+      pi->z = z;
+      /* noise model (Section II-C) */
+      double sig = p->noise_a0 + p->noise_a1 * d + p->noise_a2 * d * d;
+      double vp = sig * sig;
+      pi->var_p = vp > p->var_min ? vp : p->var_min;
+      /* cell indices */
+      double qx = (x - x0) / r, qy = (y - y0) / r;
+      pi->ix = clamp_index(qx);
+      pi->iy = clamp_index(qy);
+      if (u > 0) {
+        double bx = ab + 8.0 * u * (pi->sx + fabs(R[3]) + fabs(x0) + fabs(x - x0));
+        double by = ab + 8.0 * u * (pi->sy + fabs(R[7]) + fabs(y0) + fabs(y - y0));
+        if (edge_dist(qx, r) < bx || edge_dist(qy, r) < by) pi->flags |= PF_BIN;
+      }
+      if (!in_range) { pi->status = ST_RANGE; continue; }
+      pi->status = in_map(m, pi->ix, pi->iy) ? ST_ACCEPT : ST_OUTSIDE; /* decided per cell below */
+    }
+  }
+
+  /* 3. per cell: points in input order (linked lists built back to front) */
+  int64_t* head = (int64_t*)malloc(sizeof(int64_t) * (size_t)nc);
+  int64_t* next = (int64_t*)malloc(sizeof(int64_t) * (size_t)(npts > 0 ? npts : 1));
+  int64_t* cnt = (int64_t*)calloc((size_t)nc, sizeof(int64_t));
+  for (int64_t c = 0; c < nc; ++c) head[c] = -1;
+  for (int64_t i = npts - 1; i >= 0; --i) {
+    if (pts[i].status != ST_ACCEPT) continue;
+    int64_t c = pts[i].iy * W + pts[i].ix;
+    next[i] = head[c];
+    head[c] = i;
+    cnt[c]++;
+  }
+  int64_t n_acc = 0, n_rej = 0, n_wall = 0, n_upd = 0;
+  for (int64_t c = 0; c < nc; ++c) {
+    if (head[c] < 0) continue;
+    const int valid = isfinite(ve0[c]);
+    int64_t rej = 0, acc = 0;
+    /* decisions against the snapshot */
+    for (int64_t i = head[c]; i >= 0; i = next[i]) {
+      pt_info* pi = &pts[i];
+      if (p->wall_num_thresh > 0 && valid && cnt[c] > p->wall_num_thresh) {
+        if (u > 0 && fabs(pi->z - h0[c]) < ab + 8.0 * u * (pi->sz + fabs(clouds[pi->cloud].pose[11]) + fabs(h0[c])))
+          pi->flags |= PF_WALL;
+        if (pi->z < h0[c]) { pi->status = ST_WALL; continue; }
+      }
+      if (valid && p->mahalanobis_k > 0) {
+        double s = sqrt(ve0[c] + pi->var_p);
+        double md = fabs(pi->z - h0[c]) / s;
+        if (u > 0) {
+          double band = ab + 16.0 * u * md +
+                        8.0 * u * (pi->sz + fabs(clouds[pi->cloud].pose[11]) + fabs(h0[c])) / s;
+          if (fabs(md - p->mahalanobis_k) < band) pi->flags |= PF_GATE;
+        }
+        if (md > p->mahalanobis_k) { pi->status = ST_REJECT; ++rej; continue; }
+      }
+      pi->status = ST_ACCEPT;
+      ++acc;
+    }
+    if (acc + rej == 0) continue;
+    /* the variance grows with every rejected point, then Eq. 1 / Eq. 2 */
+    double hm = h0[c];
+    double vm = valid ? ve0[c] + (double)rej * p->outlier_variance : INFINITY;
+    for (int64_t i = head[c]; i >= 0; i = next[i]) {
+      const pt_info* pi = &pts[i];
+      if (pi->status != ST_ACCEPT) continue;
+      if (!isfinite(vm)) { /* first measurement of an empty cell */
+        hm = pi->z;
+        vm = pi->var_p;
+      } else {
+        double vp = pi->var_p;
+        hm = (vp * hm + vm * pi->z) / (vm + vp); /* Eq. 1 */
+        vm = (vm * vp) / (vm + vp);               /* Eq. 2 */
+      }
+    }
+    m->h[c] = hm;
+    m->var[c] = vm;
+    m->t_last[c] = t_now;
+    n_acc += acc;
+    n_rej += rej;
+    ++n_upd;
+  }
+  for (int64_t i = 0; i < npts; ++i) n_wall += pts[i].status == ST_WALL;
+
+  /* 4. ray casting against the snapshot (Section II-E) */
+  uint8_t* mark = (uint8_t*)calloc((size_t)nc, 1);
+  if (p->ray_step > 0) {
+    for (int64_t i = 0; i < npts; ++i) {
+      const pt_info* pi = &pts[i];
+      if (pi->status == ST_NONFINITE) continue;
+      const float* pose = clouds[pi->cloud].pose;
+      int valid_ray = pi->status != ST_RANGE;
+      int ray_marginal = (pi->flags & (PF_BIN | PF_RANGE)) != 0;
+      if (valid_ray) walk_ray(m, pi, pose, h0, ve0, nx0, ny0, nz0, mark, tr, 0, x0, y0);
+      if (ray_marginal && tr && tr->cflags) walk_ray(m, pi, pose, h0, ve0, nx0, ny0, nz0, mark, tr, 1, x0, y0);
+    }
+  }
+
+  /* 5. removal: penetrated and not updated for max(1, cleanup_min_age) updates */
+  int64_t n_clr = 0;
+  const int32_t min_age = p->cleanup_min_age > 1 ? p->cleanup_min_age : 1;
+  for (int64_t c = 0; c < nc; ++c) {
+    if (!mark[c] || !isfinite(m->var[c])) continue;
+    if (t_now - m->t_last[c] < min_age) continue;
+    m->h[c] = NAN;
+    m->var[c] = INFINITY;
+    if (tr && tr->cleared) tr->cleared[c] = 1;
+    ++n_clr;
+  }
+
+  /* 6. per-cell filters on the updated map */
+  if (p->flags & ORC_NORMALS) compute_normals(m);
+  if (p->flags & ORC_SMOOTH) compute_smooth(m);
+  if (p->flags & ORC_INPAINT) compute_inpaint(m);
+  m->t_now = t_now;
+
+  if (tr) {
+    int64_t n_valid = 0, n_inmap = 0;
+    for (int64_t i = 0; i < npts; ++i) {
+      const pt_info* pi = &pts[i];
+      n_valid += pi->status != ST_NONFINITE && pi->status != ST_RANGE;
+      n_inmap += pi->status >= ST_ACCEPT;
+      if (tr->ix) tr->ix[i] = (int32_t)(pi->ix < INT32_MIN ? INT32_MIN : pi->ix > INT32_MAX ? INT32_MAX : pi->ix);
+      if (tr->iy) tr->iy[i] = (int32_t)(pi->iy < INT32_MIN ? INT32_MIN : pi->iy > INT32_MAX ? INT32_MAX : pi->iy);
+      if (tr->status) tr->status[i] = (uint8_t)pi->status;
+      if (tr->pflags) tr->pflags[i] = (uint8_t)pi->flags;
+      if (tr->cflags && pi->flags && pi->status != ST_NONFINITE) {
+        int rad = (pi->flags & (PF_BIN | PF_RANGE)) ? 1 : 0;
+        flag_block(m, tr->cflags, pi->ix, pi->iy, rad, CF_VALUE);
+      }
+    }
+    if (tr->mark) memcpy(tr->mark, mark, (size_t)nc);
+    tr->counts[0] = npts;
+    tr->counts[1] = n_valid;
+    tr->counts[2] = n_inmap;
+    tr->counts[3] = n_acc;
+    tr->counts[4] = n_rej;
+    tr->counts[5] = n_wall;
+    tr->counts[6] = n_upd;
+    tr->counts[7] = n_clr;
+  }
+  free(mark); free(head); free(next); free(cnt); free(pts);
+  free(h0); free(ve0); free(nx0); free(ny0); free(nz0);
+  return 0;
+}
+
+/* Move the map by (dx, dy) cells: new cell (ix, iy) holds old cell
+ * (ix + dx, iy + dy); cells that come into view are empty. */
+void orc_shift(orc_map* m, int32_t dx, int32_t dy) {
+  const int W = m->p.width, H = m->p.height;
+  const int64_t nc = (int64_t)W * H;
+  orc_map* old = orc_create(&m->p);
+  orc_get(m, old->h, old->var, old->t_last, old->nx, old->ny, old->nz, old->smooth, old->inpaint);
+  for (int iy = 0; iy < H; ++iy)
+    for (int ix = 0; ix < W; ++ix) {
+      int64_t c = (int64_t)iy * W + ix;
+      int64_t sx = (int64_t)ix + dx, sy = (int64_t)iy + dy;
+      if (!in_map(m, sx, sy)) { clear_cell(m, c); continue; }
+      int64_t s = sy * W + sx;
+      m->h[c] = old->h[s];
+      m->var[c] = old->var[s];
+      m->t_last[c] = old->t_last[s];
+      m->nx[c] = old->nx[s];
+      m->ny[c] = old->ny[s];
+      m->nz[c] = old->nz[s];
+      m->smooth[c] = old->smooth[s];
+      m->inpaint[c] = old->inpaint[s];
+    }
+  (void)nc;
+  m->shift_x += dx;
+  m->shift_y += dy;
+  orc_destroy(old);
+}
+
+/* Run the filters of Section II-A / II-I on the current state (used by the
+ * tests to pin them on hand-made maps). */
+void orc_filters(orc_map* m, uint32_t which) {
+  if (which & ORC_NORMALS) compute_normals(m);
+  if (which & ORC_SMOOTH) compute_smooth(m);
+  if (which & ORC_INPAINT) compute_inpaint(m);
+}
