@@ -1,0 +1,225 @@
+/*
+ * em.h -- C ABI of libem.so: GPU fusion of point clouds into a robot-centric
+ * 2.5D elevation map, after Miki et al., "Elevation Mapping for Locomotion and
+ * Navigation using GPU" (arXiv 2204.12876), Section II.
+ *
+ * Conventions shared by every entry point:
+ *   - Return value: EM_OK (0) or a negative EM_ERR_* code.  No C++ exception
+ *     crosses this boundary.  em_status_str() names a code.
+ *   - Calls that take a stream enqueue their GPU work on it and return without
+ *     waiting for it, unless stated.  A NULL stream is the legacy default
+ *     stream.  The caller keeps every device buffer it passes alive until the
+ *     stream has reached the call.
+ *   - The library owns all device memory of a map.  Caller buffers are never
+ *     freed or retained by the library.
+ *   - Maps are not thread-safe; distinct maps may be used from distinct host
+ *     threads.
+ *   - Map layers are float32.  Layer arrays exchanged with the caller are in
+ *     logical row-major order [iy][ix], cell (ix, iy) covering
+ *     [x0 + ix r, x0 + (ix+1) r) x [y0 + iy r, y0 + (iy+1) r) of the map frame.
+ *   - Errors found by a kernel (a capacity overflow, a bounded wait that ran
+ *     out) are recorded on the device and reported by the next em_sync() or
+ *     em_get_stats() of that map.
+ */
+#ifndef EM_H
+#define EM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct em_map em_map;
+typedef struct CUstream_st* em_stream_t; /* the same handle as cudaStream_t */
+
+/* status codes */
+enum {
+  EM_OK = 0,
+  EM_ERR_INVALID_ARG = -1, /* NULL pointer, bad size / stride, non-finite pose, bad parameter */
+  EM_ERR_OOM = -2,         /* a device or pinned-host allocation failed */
+  EM_ERR_CUDA = -3,        /* a CUDA call failed; the CUDA error is logged by em_last_cuda_error() */
+  EM_ERR_TIMEOUT = -4,     /* a bounded wait ran out (host or device side) */
+  EM_ERR_REJECTED = -5,    /* admission refused (memory budget or slot limit) */
+  EM_ERR_BUSY = -6,        /* the object is in use by work that has not finished */
+  EM_ERR_CAPACITY = -7     /* a request exceeds a fixed capacity chosen at creation */
+};
+
+/* em_params.flags */
+enum {
+  EM_F_NORMALS = 1u << 0, /* keep the per-cell normal layer (Section II-A, "normal calculation") */
+  EM_F_SMOOTH = 1u << 1,  /* keep a 5x5 box-smoothed elevation layer (Section II-I) */
+  EM_F_INPAINT = 1u << 2, /* keep a minimum-in-painted elevation layer (Section II-I) */
+  EM_F_TRACE = 1u << 8    /* record per-point cells and decisions of the last update (testing) */
+};
+
+/* layer bits for em_get_layers / em_set_layers (ascending bit order in the buffers) */
+enum {
+  EM_LAYER_ELEVATION = 1u << 0, /* h, NaN where the cell is empty */
+  EM_LAYER_VARIANCE = 1u << 1,  /* sigma_m^2 as stored at the cell's last write (TIME); +inf if empty */
+  EM_LAYER_TIME = 1u << 2,      /* index of the update that last wrote the cell (exact below 2^24) */
+  EM_LAYER_NORMAL_X = 1u << 3,
+  EM_LAYER_NORMAL_Y = 1u << 4,
+  EM_LAYER_NORMAL_Z = 1u << 5,
+  EM_LAYER_SMOOTH = 1u << 6,
+  EM_LAYER_INPAINT = 1u << 7,
+  EM_LAYER_VALID = 1u << 8,       /* 1.0 where the cell holds an estimate, else 0.0 (get only) */
+  EM_LAYER_VARIANCE_NOW = 1u << 9 /* sigma_m^2 plus time variance up to the current update (get only) */
+};
+
+/* Map and method parameters.  The paper leaves most of them user-defined
+ * (Section II-C noise model alpha_d, time variance sigma_t^2, Mahalanobis
+ * distance, wall count; Section II-E ray step, update age, alpha_n). */
+typedef struct em_params {
+  int32_t width, height;        /* cells, >= 1, width*height <= 2^26 */
+  float resolution;             /* metres per cell, > 0 */
+  float noise_a0, noise_a1, noise_a2; /* sigma_p = a0 + a1 d + a2 d^2; the paper's alpha_d d^2 is a1 = sqrt(alpha_d) */
+  float var_min;                /* floor on sigma_p^2, > 0 */
+  float min_range, max_range;   /* points with d outside [min_range, max_range] are dropped */
+  float mahalanobis_k;          /* reject iff |p_z - h| / sqrt(sigma_m^2 + sigma_p^2) > k; <= 0 disables */
+  float outlier_variance;       /* added to sigma_m^2 per rejected point; 0 disables */
+  int32_t wall_num_thresh;      /* > 0: with more points than this in a valid cell, drop those below h */
+  float time_variance;          /* sigma_t^2 added per update since the cell was last written; 0 disables */
+  float ray_step;               /* visibility ray-march step in metres; 0 disables visibility cleanup */
+  int32_t cleanup_min_age;      /* remove only cells last written >= max(1, this) updates ago */
+  float cleanup_normal_thresh;  /* alpha_n of Eq. 4; <= 0 disables the normal guard */
+  uint32_t flags;               /* EM_F_* */
+} em_params;
+
+/* One point cloud: n points of `stride` floats (3 = xyz, 4 = xyz + pad) in the
+ * sensor frame, and the sensor-to-map pose as a row-major 3x4 [R | t]. */
+typedef struct em_cloud {
+  const float* points;
+  int64_t n;
+  int32_t stride;
+  float pose[12];
+} em_cloud;
+
+typedef struct em_info {
+  int32_t width, height;
+  float resolution;
+  int32_t t_now;           /* number of updates fused so far */
+  int64_t shift_x, shift_y;/* cumulative em_shift in cells; the map centre is (shift_x r, shift_y r) */
+  double x0, y0;           /* lower-left corner of the map in the map frame */
+  int64_t point_capacity;  /* points per update the workspace holds without growing */
+  int64_t device_bytes;    /* device memory held by the map */
+} em_info;
+
+typedef struct em_stats {
+  /* cumulative since em_create */
+  int64_t updates;
+  int64_t points_in;        /* all points offered */
+  int64_t points_valid;     /* finite and within [min_range, max_range] */
+  int64_t points_in_map;    /* valid and inside the map */
+  int64_t points_accepted;  /* fused */
+  int64_t points_rejected;  /* Mahalanobis outliers */
+  int64_t points_wall;      /* dropped by the wall rule */
+  int64_t cells_updated;    /* (cell, update) pairs written by fusion */
+  int64_t cells_cleared;    /* (cell, update) pairs removed by visibility cleanup */
+  int64_t ray_samples;      /* ray-march samples taken inside the map */
+} em_stats;
+
+/* Create a map of params->width x params->height empty cells centred on the
+ * map-frame origin on CUDA device `device`.  Validates every parameter
+ * (EM_ERR_INVALID_ARG), allocates the map's layers and a workspace for
+ * `params`-independent default capacity (grown on demand).  *out receives the
+ * handle.  Cites: 2.5D grid of Section I/II; initial sigma_m^2 "large"
+ * (Section II-C) is represented as +inf (an empty cell). */
+int em_create(const em_params* params, int device, em_map** out);
+
+/* Release the map and all its device memory.  NULL-safe; waits for the map's
+ * outstanding work first. */
+int em_destroy(em_map* map);
+
+/* Grow the workspace so that updates of up to max_points points (all clouds
+ * of one update together) need no allocation.  Synchronous. */
+int em_reserve(em_map* map, int64_t max_points);
+
+/* Fuse one point cloud (device pointer, n points, stride 3 or 4 floats) seen
+ * from a sensor with pose pose[12] (host memory, row-major 3x4, sensor -> map)
+ * into the map: transform, noise variance, binning, wall rule, Mahalanobis
+ * gate, Eq. 1/Eq. 2 fusion, visibility ray casting and removal (Eq. 3, Eq. 4),
+ * then the filters selected by params->flags (Section II-A to II-I).  n = 0 is
+ * a valid empty update (time advances).  Non-finite points are dropped and
+ * counted.  Asynchronous on `stream`; grows the workspace (synchronously) if n
+ * exceeds the current capacity. */
+int em_update(em_map* map, const float* points, int64_t n, int32_t stride, const float pose[12],
+              em_stream_t stream);
+
+/* One update made of several clouds (e.g. several cameras of one robot): all
+ * points are gated against the same pre-update map and fused together; each
+ * cloud's rays start at its own sensor origin.  clouds[] is host memory,
+ * clouds[i].points device memory. */
+int em_update_multi(em_map* map, const em_cloud* clouds, int32_t n_clouds, em_stream_t stream);
+
+/* Same as em_update_multi with clouds[i].points in HOST memory: the library
+ * copies the points to the device on `stream` (through a pinned staging
+ * buffer it owns) before fusing.  Returns once the points are staged. */
+int em_update_host(em_map* map, const em_cloud* clouds, int32_t n_clouds, em_stream_t stream);
+
+/* Move the map with the robot by (dx, dy) cells (robot-centric map, Section
+ * I): afterwards cell (ix, iy) holds what cell (ix + dx, iy + dy) held; cells
+ * that come into view are empty.  O(exposed cells) on the GPU. */
+int em_shift(em_map* map, int32_t dx, int32_t dy, em_stream_t stream);
+
+/* Copy the layers selected by layer_mask (EM_LAYER_*) in ascending bit order,
+ * each width*height floats in logical row-major order, to dst (device memory,
+ * or host memory if dst_is_host; then the call waits for the copy). */
+int em_get_layers(em_map* map, uint32_t layer_mask, float* dst, int dst_is_host, em_stream_t stream);
+
+/* Overwrite the selected layers from src (same layout).  Accepts ELEVATION,
+ * VARIANCE, TIME and NORMAL_X/Y/Z; a non-finite variance makes a cell empty.
+ * With em_set_time it restores a checkpoint taken with em_get_layers. */
+int em_set_layers(em_map* map, uint32_t layer_mask, const float* src, int src_is_host, em_stream_t stream);
+
+/* Set the update counter (the index the next update will use is t_now + 1). */
+int em_set_time(em_map* map, int32_t t_now);
+
+/* Geometry and bookkeeping; host only, does not synchronise. */
+int em_get_info(const em_map* map, em_info* out);
+
+/* Cumulative counters; waits for the map's outstanding work.  Returns a
+ * recorded device error (e.g. EM_ERR_TIMEOUT) if one occurred. */
+int em_get_stats(em_map* map, em_stats* out);
+
+/* Wait for the map's outstanding work and report any recorded error. */
+int em_sync(em_map* map);
+
+/* With EM_F_TRACE: per point of the last update (clouds concatenated) its
+ * logical cell (ix, iy) and its status (0 non-finite, 1 out of range, 2 outside
+ * the map, 3 fused, 4 rejected, 5 wall rule).  Host buffers of n entries (n must
+ * equal the last update's point count); waits for the map's work. */
+int em_get_trace(em_map* map, int32_t* ix, int32_t* iy, uint8_t* status, int64_t n);
+
+/* Per-kernel timing with CUDA events recorded on the update's stream around
+ * each kernel the library launches.  While enabled, every update first waits
+ * for the previous update's events (so timing adds a host wait per update).
+ * Slots of em_profile_read, in this order: */
+enum {
+  EM_PROF_COUNT = 0,   /* k_count: transform + bin + per-cell counts */
+  EM_PROF_RAY,         /* k_ray: visibility ray march */
+  EM_PROF_ALLOC,       /* k_alloc: segment allocation */
+  EM_PROF_SCATTER,     /* k_scatter: records into segments */
+  EM_PROF_FUSE,        /* k_fuse: per-cell gate + fusion */
+  EM_PROF_CLEAR,       /* k_clear: removal of penetrated cells */
+  EM_PROF_NORMALS,
+  EM_PROF_SMOOTH,
+  EM_PROF_INPAINT,
+  EM_PROF_SLOTS
+};
+int em_profile(em_map* map, int enable);
+/* Accumulated milliseconds and launch counts per slot since profiling was
+ * enabled (both arrays EM_PROF_SLOTS long, host memory); waits for the map. */
+int em_profile_read(em_map* map, double* ms, int64_t* launches);
+
+/* Text for a status code (static storage). */
+const char* em_status_str(int status);
+
+/* Text of the last CUDA error seen by this thread in the library (static
+ * thread-local storage). */
+const char* em_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EM_H */

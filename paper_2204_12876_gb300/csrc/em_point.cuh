@@ -1,0 +1,59 @@
+// em_point.cuh -- per-point arithmetic shared by the binning and ray kernels.
+//
+// Both kernels must find the same cell for a point (the ray march skips the
+// point's own cell), so the arithmetic is written with explicit rounding
+// intrinsics: no contraction choice of the compiler can make the two differ.
+#pragma once
+
+#include "em_internal.cuh"
+
+namespace em {
+
+struct PointGeom {
+  float vx, vy, vz;  // R * p_s: sensor-to-point vector in the map frame
+  float x, y, z;     // p_m = R * p_s + t
+  float d;           // |p_s|, distance from the sensor (Section II-C noise model)
+  int32_t ix, iy;    // logical cell indices (unbounded, clamped to +-1e9)
+  bool finite;
+  bool in_range;
+};
+
+// Transform by the sensor pose (Section II-A), distance, cell indices
+// ix = floor((x - x0) / r) of the robot-centric grid.
+__device__ __forceinline__ PointGeom point_geom(const MapDev& m, const CloudDev& c, float px, float py,
+                                                float pz) {
+  PointGeom g;
+  g.finite = isfinite(px) && isfinite(py) && isfinite(pz);
+  float d2 = __fmaf_rn(px, px, __fmaf_rn(py, py, __fmul_rn(pz, pz)));
+  g.d = __fsqrt_rn(d2);
+  g.in_range = g.finite && g.d >= m.min_range && g.d <= m.max_range;
+  g.vx = __fmaf_rn(c.R[0], px, __fmaf_rn(c.R[1], py, __fmul_rn(c.R[2], pz)));
+  g.vy = __fmaf_rn(c.R[3], px, __fmaf_rn(c.R[4], py, __fmul_rn(c.R[5], pz)));
+  g.vz = __fmaf_rn(c.R[6], px, __fmaf_rn(c.R[7], py, __fmul_rn(c.R[8], pz)));
+  g.x = __fadd_rn(g.vx, c.t[0]);
+  g.y = __fadd_rn(g.vy, c.t[1]);
+  g.z = __fadd_rn(g.vz, c.t[2]);
+  g.ix = clamp_floor(__fdiv_rn(__fsub_rn(g.x, m.x0), m.res));
+  g.iy = clamp_floor(__fdiv_rn(__fsub_rn(g.y, m.y0), m.res));
+  return g;
+}
+
+// sigma_p^2 = max((a0 + a1 d + a2 d^2)^2, var_min)  (Section II-C noise model)
+__device__ __forceinline__ float point_variance(const MapDev& m, float d) {
+  float s = __fmaf_rn(__fmaf_rn(m.a2, d, m.a1), d, m.a0);
+  return fmaxf(__fmul_rn(s, s), m.var_min);
+}
+
+__device__ __forceinline__ bool in_map(const MapDev& m, int32_t ix, int32_t iy) {
+  return ix >= 0 && iy >= 0 && ix < m.W && iy < m.H;
+}
+
+// Load point g of cloud c (stride 3 or 4) with scalar loads.
+__device__ __forceinline__ void load_point(const CloudDev& c, int64_t i, float& px, float& py, float& pz) {
+  const float* p = c.pts + i * c.stride;
+  px = __ldg(p);
+  py = __ldg(p + 1);
+  pz = __ldg(p + 2);
+}
+
+}  // namespace em

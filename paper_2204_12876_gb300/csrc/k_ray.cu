@@ -1,0 +1,174 @@
+// k_ray.cu -- visibility cleanup by ray casting (Section II-E of the paper).
+//
+// k_ray: one thread per valid point.  The ray from the sensor origin o (the
+// pose translation) to the point is sampled at s_k = o + (k step / d) (R p_s)
+// for k = 1, 2, ... while k step < d.  A sample inside the map, outside the
+// point's own cell, in a cell holding an estimate, below that cell's
+// h - sqrt(sigma_m^2) (Eq. 3), and -- when alpha_n > 0 -- with
+// |rhat . n| > alpha_n for the cell's previous normal (Eq. 4; a NaN normal
+// counts as (0, 0, 1)) marks the cell in a bitmask (atomicOr: idempotent, so
+// the marks do not depend on thread order).  The march only visits the k
+// whose samples can lie inside the map's box.  It runs before the fusion, so
+// it sees the pre-update map.
+//
+// k_clear: after the fusion, every marked cell that holds an estimate and was
+// last written at least max(1, cleanup_min_age) updates ago is removed; the
+// bitmask and the per-update counters are reset for the next update.
+#include "em_point.cuh"
+
+namespace em {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kRayThreads = 128;
+
+__device__ __forceinline__ void block_range_r(int64_t n, int64_t& beg, int64_t& end) {
+  int64_t per = (n + gridDim.x - 1) / gridDim.x;
+  per = (per + 31) & ~int64_t(31);
+  beg = (int64_t)blockIdx.x * per;
+  end = beg + per < n ? beg + per : n;
+}
+
+// parameter interval [lo, hi] (metres along the ray) where the xy track of
+// o + (s/d) v stays inside [a0, a1): returns false when it never does
+__device__ __forceinline__ bool slab(float o, float v, float d, float a0, float a1, float& lo, float& hi) {
+  if (v == 0.f) return o >= a0 && o < a1;
+  const float sa = (a0 - o) * d / v;
+  const float sb = (a1 - o) * d / v;
+  lo = fmaxf(lo, fminf(sa, sb));
+  hi = fminf(hi, fmaxf(sa, sb));
+  return true;
+}
+
+__global__ void __launch_bounds__(kRayThreads) k_ray(const BatchDev* __restrict__ bp) {
+  const BatchDev& b = *bp;
+  int64_t beg, end;
+  block_range_r(b.n_points, beg, end);
+  unsigned long long samples = 0;
+  int cur_map = -1;
+  for (int64_t g = beg + threadIdx.x; g < end; g += kRayThreads) {
+    const int ci = find_cloud(b.clouds, b.n_clouds, g);
+    const CloudDev& c = b.clouds[ci];
+    const MapDev& m = b.maps[c.map];
+    if (m.ray_step <= 0.f) continue;
+    float px, py, pz;
+    load_point(c, g - c.begin, px, py, pz);
+    const PointGeom pg = point_geom(m, c, px, py, pz);
+    if (!pg.in_range || !(pg.d > 0.f)) continue;
+    if (c.map != cur_map) {
+      if (cur_map >= 0 && samples) atomicAdd(&b.maps[cur_map].ctl->stats[kStRaySamples], samples);
+      samples = 0;
+      cur_map = c.map;
+    }
+    // clip the sample range to the map box (conservative by 1 mm + 1 step)
+    float lo = 0.f, hi = pg.d;
+    const float ext_x = __fmul_rn((float)m.W, m.res), ext_y = __fmul_rn((float)m.H, m.res);
+    if (!slab(c.t[0], pg.vx, pg.d, m.x0, m.x0 + ext_x, lo, hi)) continue;
+    if (!slab(c.t[1], pg.vy, pg.d, m.y0, m.y0 + ext_y, lo, hi)) continue;
+    if (lo > hi + 1e-3f) continue;
+    const float step = m.ray_step;
+    float kl = floorf((lo - 1e-3f) / step) - 1.f;
+    float kh = ceilf((hi + 1e-3f) / step) + 1.f;
+    const int32_t k_lo = kl < 1.f ? 1 : (int32_t)kl;
+    const int32_t k_hi = kh > 1.0e9f ? 1000000000 : (int32_t)kh;
+    const float cstep = __fdiv_rn(step, pg.d);  // f_k = k * step / d
+    const float inv_res = __frcp_rn(m.res);
+    const float rx = __fdiv_rn(pg.vx, pg.d), ry = __fdiv_rn(pg.vy, pg.d), rz = __fdiv_rn(pg.vz, pg.d);
+    const bool guard = m.alpha_n > 0.f;
+    int32_t prev = -1;
+    float prev_thr = 0.f;
+    bool prev_ok = false, prev_marked = false;
+    for (int32_t k = k_lo; k <= k_hi; ++k) {
+      const float len = __fmul_rn((float)k, step);
+      if (!(len < pg.d)) break;
+      const float f = __fmul_rn((float)k, cstep);
+      const float sx = __fmaf_rn(f, pg.vx, c.t[0]);
+      const float sy = __fmaf_rn(f, pg.vy, c.t[1]);
+      const float sz = __fmaf_rn(f, pg.vz, c.t[2]);
+      const int32_t cx = clamp_floor(__fmul_rn(__fsub_rn(sx, m.x0), inv_res));
+      const int32_t cy = clamp_floor(__fmul_rn(__fsub_rn(sy, m.y0), inv_res));
+      if (!in_map(m, cx, cy)) continue;
+      ++samples;
+      if (cx == pg.ix && cy == pg.iy) continue;
+      const int32_t p = phys_index(m, cx, cy);
+      if (p != prev) {
+        prev = p;
+        prev_marked = false;
+        const float var = m.var[p];
+        prev_ok = isfinite(var);
+        if (prev_ok) {
+          const float ve = m.sigma_t2 != 0.f ? var_eff(m, var, m.t_last[p]) : var;
+          prev_thr = __fsub_rn(m.h[p], __fsqrt_rn(ve));
+          if (guard) {
+            float n0 = m.nx[p], n1 = m.ny[p], n2 = m.nz[p];
+            if (!(isfinite(n0) && isfinite(n1) && isfinite(n2))) { n0 = 0.f; n1 = 0.f; n2 = 1.f; }
+            const float dot = fabsf(__fmaf_rn(rx, n0, __fmaf_rn(ry, n1, __fmul_rn(rz, n2))));
+            prev_ok = dot > m.alpha_n;
+          }
+        }
+      }
+      if (prev_ok && !prev_marked && sz < prev_thr) {
+        atomicOr(&m.mark[p >> 5], 1u << (p & 31));
+        prev_marked = true;
+      }
+    }
+  }
+  if (cur_map >= 0 && samples) atomicAdd(&b.maps[cur_map].ctl->stats[kStRaySamples], samples);
+}
+
+constexpr int kClearThreads = 256;
+
+__global__ void __launch_bounds__(kClearThreads) k_clear(const BatchDev* __restrict__ bp) {
+  const BatchDev& b = *bp;
+  if ((int)blockIdx.y >= b.n_maps) return;
+  const MapDev& m = b.maps[blockIdx.y];
+  const int32_t ncell = m.W * m.H;
+  const int32_t nword = (ncell + 31) >> 5;
+  const int32_t min_age = m.min_age > 1 ? m.min_age : 1;
+  unsigned long long cleared = 0;
+  for (int32_t w = blockIdx.x * kClearThreads + threadIdx.x; w < nword; w += gridDim.x * kClearThreads) {
+    uint32_t bits = m.mark[w];
+    if (!bits) continue;
+    m.mark[w] = 0u;
+    while (bits) {
+      const int bit = __ffs(bits) - 1;
+      bits &= bits - 1;
+      const int32_t p = w * 32 + bit;
+      if (p >= ncell) break;
+      if (!isfinite(m.var[p])) continue;
+      if (m.t_now - m.t_last[p] < min_age) continue;
+      m.h[p] = __int_as_float(0x7fc00000);
+      m.var[p] = __int_as_float(0x7f800000);
+      ++cleared;
+    }
+  }
+  for (int o = 16; o; o >>= 1) cleared += __shfl_xor_sync(kFull, cleared, o);
+  if ((threadIdx.x & 31) == 0 && cleared) atomicAdd(&m.ctl->stats[kStCleared], cleared);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    m.ctl->n_touched = 0;
+    m.ctl->seg_cursor = 0;
+    atomicAdd(&m.ctl->stats[kStUpdates], 1ull);
+  }
+}
+
+cudaError_t launch_ray(const BatchDev* b, int64_t n_points, cudaStream_t s) {
+  if (n_points <= 0) return cudaSuccess;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int64_t want = (n_points + kRayThreads - 1) / kRayThreads;
+  int64_t cap = (int64_t)sms * 16;
+  int grid = (int)(want < cap ? want : cap);
+  k_ray<<<grid < 1 ? 1 : grid, kRayThreads, 0, s>>>(b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_clear(const BatchDev* b, int32_t n_maps, int32_t max_cells, cudaStream_t s) {
+  int words = (max_cells + 31) / 32;
+  int gx = (words + kClearThreads - 1) / kClearThreads;
+  if (gx > 256) gx = 256;
+  dim3 grid(gx < 1 ? 1 : gx, n_maps);
+  k_clear<<<grid, kClearThreads, 0, s>>>(b);
+  return cudaGetLastError();
+}
+
+}  // namespace em

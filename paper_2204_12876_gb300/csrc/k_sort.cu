@@ -1,0 +1,283 @@
+// k_sort.cu -- grouping of points by cell: a counting sort keyed by the
+// physical cell index (one radix digit spanning the whole key).
+//
+//   k_count    per point: transform + bin, warp-aggregated per-cell counts
+//   k_alloc    per map, tiles of cells: block scans of the counts give every
+//              touched cell a segment [base, base + count) of the record array
+//   k_scatter  per point: transform + bin again, claim a slot in the cell's
+//              segment, write the record (z, sigma_p^2)
+//
+// The order of records inside a segment depends on atomic arrival order.  The
+// fusion kernel sums them exactly in integer fixed point, so that order never
+// changes a result.
+#include "em_point.cuh"
+
+namespace em {
+
+constexpr int kPointThreads = 256;
+constexpr unsigned kFull = 0xffffffffu;
+
+// Per-thread counters of one map, flushed with one atomic per block when the
+// whole block saw a single map, else per thread.
+struct MapCounters {
+  int map = -1;
+  unsigned long long v[3] = {0, 0, 0};
+};
+
+__device__ void flush_counters(const BatchDev& b, MapCounters& mc, const int* idx, int n) {
+  __shared__ int s_map;
+  __shared__ unsigned long long s_sum[3];
+  if (threadIdx.x == 0) s_map = mc.map;
+  if (threadIdx.x < 3) s_sum[threadIdx.x] = 0;
+  __syncthreads();
+  bool uniform = __syncthreads_and(mc.map == s_map || mc.map < 0);
+  if (uniform) {
+    for (int k = 0; k < n; ++k) {
+      unsigned long long v = mc.v[k];
+      for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+      if ((threadIdx.x & 31) == 0 && v) atomicAdd(&s_sum[k], v);
+    }
+    __syncthreads();
+    if (threadIdx.x < n && s_map >= 0 && s_sum[threadIdx.x])
+      atomicAdd(&b.maps[s_map].ctl->stats[idx[threadIdx.x]], s_sum[threadIdx.x]);
+  } else if (mc.map >= 0) {
+    for (int k = 0; k < n; ++k)
+      if (mc.v[k]) atomicAdd(&b.maps[mc.map].ctl->stats[idx[k]], mc.v[k]);
+  }
+}
+
+__device__ __forceinline__ void add_counter(const BatchDev& b, MapCounters& mc, int map, const int* idx, int n,
+                                            const unsigned long long* inc) {
+  if (map != mc.map) {
+    if (mc.map >= 0)
+      for (int k = 0; k < n; ++k)
+        if (mc.v[k]) atomicAdd(&b.maps[mc.map].ctl->stats[idx[k]], mc.v[k]);
+    mc.map = map;
+    for (int k = 0; k < n; ++k) mc.v[k] = 0;
+  }
+  for (int k = 0; k < n; ++k) mc.v[k] += inc[k];
+}
+
+// Block-contiguous partition of the point space into chunks of whole warps.
+__device__ __forceinline__ void block_range(int64_t n, int64_t& beg, int64_t& end) {
+  int64_t per = (n + gridDim.x - 1) / gridDim.x;
+  per = (per + 31) & ~int64_t(31);
+  beg = (int64_t)blockIdx.x * per;
+  end = beg + per < n ? beg + per : n;
+}
+
+// Load the warp's 32 points [wbase, wbase + 32).  When the whole chunk sits in
+// one cloud with 16-byte aligned rows the warp reads it with float4 loads:
+// stride 4 -> one float4 per lane; stride 3 -> 24 float4 staged in shared memory.
+__device__ __forceinline__ int load_warp_points(const BatchDev& b, int64_t wbase, int64_t end, float4* stage,
+                                                float& px, float& py, float& pz) {
+  const int lane = threadIdx.x & 31;
+  const int64_t g = wbase + lane;
+  const int c0 = find_cloud(b.clouds, b.n_clouds, wbase);
+  const CloudDev& cl0 = b.clouds[c0];
+  const bool whole = (wbase + 32 <= end) && (wbase + 32 <= cl0.begin + cl0.n);
+  int ci = c0;
+  if (whole) {
+    const int64_t i0 = wbase - cl0.begin;
+    const float* base = cl0.pts + i0 * cl0.stride;
+    if (cl0.stride == 4 && ((reinterpret_cast<uintptr_t>(base) & 15) == 0)) {
+      float4 q = __ldg(reinterpret_cast<const float4*>(base) + lane);
+      px = q.x; py = q.y; pz = q.z;
+      return ci;
+    }
+    if (cl0.stride == 3 && ((reinterpret_cast<uintptr_t>(base) & 15) == 0)) {
+      if (lane < 24) stage[lane] = __ldg(reinterpret_cast<const float4*>(base) + lane);
+      __syncwarp();
+      const float* sf = reinterpret_cast<const float*>(stage);
+      px = sf[lane * 3];
+      py = sf[lane * 3 + 1];
+      pz = sf[lane * 3 + 2];
+      __syncwarp();
+      return ci;
+    }
+  } else if (g < end) {
+    ci = find_cloud(b.clouds, b.n_clouds, g);
+  }
+  if (g < end) {
+    load_point(b.clouds[ci], g - b.clouds[ci].begin, px, py, pz);
+  } else {
+    px = py = pz = __int_as_float(0x7fc00000);
+  }
+  return ci;
+}
+
+__global__ void __launch_bounds__(kPointThreads) k_count(const BatchDev* __restrict__ bp) {
+  __shared__ float4 stage[kPointThreads / 32][24];
+  const BatchDev& b = *bp;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int64_t beg, end;
+  block_range(b.n_points, beg, end);
+  MapCounters mc;
+  const int idx[2] = {kStValid, kStInMap};
+  for (int64_t wbase = beg + warp * 32; wbase < end; wbase += kPointThreads) {
+    float px, py, pz;
+    const int ci = load_warp_points(b, wbase, end, stage[warp], px, py, pz);
+    const int64_t g = wbase + lane;
+    const bool live = g < end;
+    const CloudDev& c = b.clouds[ci];
+    const MapDev& m = b.maps[c.map];
+    const PointGeom pg = point_geom(m, c, px, py, pz);
+    const bool inm = live && pg.in_range && in_map(m, pg.ix, pg.iy);
+    const int32_t key = inm ? phys_index(m, pg.ix, pg.iy) : -1;
+    if (live) {
+      unsigned long long inc[2] = {pg.in_range ? 1ull : 0ull, inm ? 1ull : 0ull};
+      add_counter(b, mc, c.map, idx, 2, inc);
+      if (b.tr_status) {
+        b.tr_ix[g] = pg.finite ? pg.ix : INT32_MIN;
+        b.tr_iy[g] = pg.finite ? pg.iy : INT32_MIN;
+        b.tr_status[g] = !pg.finite ? kPtNonFinite : !pg.in_range ? kPtRange : !inm ? kPtOutside : kPtFused;
+      }
+    }
+    const unsigned long long tag = inm ? ((unsigned long long)(uint32_t)c.map << 32) | (uint32_t)key : ~0ull;
+    const unsigned peers = __match_any_sync(kFull, tag);
+    if (inm && lane == __ffs(peers) - 1) atomicAdd(&m.cnt[key], __popc(peers));
+  }
+  flush_counters(b, mc, idx, 2);
+}
+
+// One block per tile of 1024 physical cells of one map (blockIdx.y = map).
+constexpr int kAllocThreads = 256;
+constexpr int kAllocPer = 4;
+
+__device__ __forceinline__ int block_exclusive_scan(int v, int* warp_tot, int& total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int incl = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    int t = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) warp_tot[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    int w = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0;
+    int wi = w;
+    for (int o = 1; o < 32; o <<= 1) {
+      int t = __shfl_up_sync(kFull, wi, o);
+      if (lane >= o) wi += t;
+    }
+    if (lane < (int)(blockDim.x >> 5)) warp_tot[lane] = wi - w;
+    if (lane == 31) warp_tot[32] = wi;
+  }
+  __syncthreads();
+  int res = warp_tot[warp] + incl - v;
+  total = warp_tot[32];
+  __syncthreads();
+  return res;
+}
+
+__global__ void __launch_bounds__(kAllocThreads) k_alloc(const BatchDev* __restrict__ bp) {
+  __shared__ int warp_tot[33];
+  __shared__ int s_base[2];
+  const BatchDev& b = *bp;
+  if ((int)blockIdx.y >= b.n_maps) return;
+  const MapDev& m = b.maps[blockIdx.y];
+  const int32_t ncell = m.W * m.H;
+  const int tile = kAllocThreads * kAllocPer;
+  for (int32_t t0 = blockIdx.x * tile; t0 < ncell; t0 += gridDim.x * tile) {
+    int c[kAllocPer];
+    int sum = 0, nt = 0;
+    const int32_t first = t0 + threadIdx.x * kAllocPer;
+#pragma unroll
+    for (int k = 0; k < kAllocPer; ++k) {
+      c[k] = (first + k < ncell) ? m.cnt[first + k] : 0;
+      sum += c[k];
+      nt += c[k] > 0;
+    }
+    int tot_c, tot_t;
+    int off_c = block_exclusive_scan(sum, warp_tot, tot_c);
+    int off_t = block_exclusive_scan(nt, warp_tot, tot_t);
+    if (threadIdx.x == 0) {
+      s_base[0] = tot_c ? atomicAdd(&m.ctl->seg_cursor, tot_c) : 0;
+      s_base[1] = tot_t ? atomicAdd(&m.ctl->n_touched, tot_t) : 0;
+    }
+    __syncthreads();
+    int64_t rec = m.pt_begin + s_base[0] + off_c;
+    int32_t slot = s_base[1] + off_t;
+#pragma unroll
+    for (int k = 0; k < kAllocPer; ++k) {
+      if (c[k] > 0) {
+        m.touched[slot] = first + k;
+        m.seg_base[slot] = (int32_t)rec;
+        m.seg_len[slot] = c[k];
+        m.cell_base[first + k] = (int32_t)rec;
+        rec += c[k];
+        ++slot;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kPointThreads) k_scatter(const BatchDev* __restrict__ bp) {
+  __shared__ float4 stage[kPointThreads / 32][24];
+  const BatchDev& b = *bp;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int64_t beg, end;
+  block_range(b.n_points, beg, end);
+  for (int64_t wbase = beg + warp * 32; wbase < end; wbase += kPointThreads) {
+    float px, py, pz;
+    const int ci = load_warp_points(b, wbase, end, stage[warp], px, py, pz);
+    const int64_t g = wbase + lane;
+    const bool live = g < end;
+    const CloudDev& c = b.clouds[ci];
+    const MapDev& m = b.maps[c.map];
+    const PointGeom pg = point_geom(m, c, px, py, pz);
+    const bool inm = live && pg.in_range && in_map(m, pg.ix, pg.iy);
+    const int32_t key = inm ? phys_index(m, pg.ix, pg.iy) : -1;
+    const unsigned long long tag = inm ? ((unsigned long long)(uint32_t)c.map << 32) | (uint32_t)key : ~0ull;
+    const unsigned peers = __match_any_sync(kFull, tag);
+    int old = 0;
+    const int leader = __ffs(peers) - 1;
+    if (inm && lane == leader) old = atomicSub(&m.cnt[key], __popc(peers));
+    old = __shfl_sync(kFull, old, leader);
+    if (inm) {
+      const int rank = __popc(peers & ((1u << lane) - 1));
+      const int64_t pos = (int64_t)m.cell_base[key] + old - 1 - rank;
+      // the count pass found the same cell for this point, so pos lies in the
+      // cell's segment; anything else is recorded instead of written
+      if (pos < m.pt_begin || pos >= m.pt_begin + m.pt_count || old - rank <= 0) {
+        atomicCAS(&m.ctl->err, 0, -3);
+      } else {
+        b.zw_sorted[pos] = make_float2(pg.z, point_variance(m, pg.d));
+        if (b.idx_sorted) b.idx_sorted[pos] = (int32_t)g;
+      }
+    }
+  }
+}
+
+static int point_grid(int64_t n) {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int64_t want = (n + kPointThreads * 4 - 1) / (kPointThreads * 4);
+  int64_t cap = (int64_t)sms * 8;
+  if (want < 1) want = 1;
+  return (int)(want < cap ? want : cap);
+}
+
+cudaError_t launch_bin(const BatchDev* b, int64_t n_points, cudaStream_t s) {
+  if (n_points <= 0) return cudaSuccess;
+  k_count<<<point_grid(n_points), kPointThreads, 0, s>>>(b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_alloc(const BatchDev* b, int32_t n_maps, int32_t max_cells, cudaStream_t s) {
+  int tiles = (max_cells + kAllocThreads * kAllocPer - 1) / (kAllocThreads * kAllocPer);
+  if (tiles > 1024) tiles = 1024;
+  dim3 grid(tiles < 1 ? 1 : tiles, n_maps);
+  k_alloc<<<grid, kAllocThreads, 0, s>>>(b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(const BatchDev* b, int64_t n_points, cudaStream_t s) {
+  if (n_points <= 0) return cudaSuccess;
+  k_scatter<<<point_grid(n_points), kPointThreads, 0, s>>>(b);
+  return cudaGetLastError();
+}
+
+}  // namespace em

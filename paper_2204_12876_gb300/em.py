@@ -1,0 +1,292 @@
+"""ctypes binding of libem.so (include/em.h).  Argument marshalling only: every
+step of the fusion runs in the library's CUDA kernels.  PyTorch provides device
+memory and streams.
+
+The library must have been built (``paper_2204_12876_gb300.build.build()``);
+importing this module without it raises ImportError -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, fields
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libem.so")
+
+EM_OK = 0
+EM_ERR_INVALID_ARG, EM_ERR_OOM, EM_ERR_CUDA, EM_ERR_TIMEOUT, EM_ERR_REJECTED, EM_ERR_BUSY, EM_ERR_CAPACITY = \
+    -1, -2, -3, -4, -5, -6, -7
+F_NORMALS, F_SMOOTH, F_INPAINT, F_TRACE = 1, 2, 4, 256
+LAYER_ELEVATION, LAYER_VARIANCE, LAYER_TIME = 1, 2, 4
+LAYER_NORMAL_X, LAYER_NORMAL_Y, LAYER_NORMAL_Z = 8, 16, 32
+LAYER_SMOOTH, LAYER_INPAINT, LAYER_VALID, LAYER_VARIANCE_NOW = 64, 128, 256, 512
+PROF_SLOTS = ("count", "ray", "alloc", "scatter", "fuse", "clear", "normals", "smooth", "inpaint")
+KERNEL_NAMES = {"count": "k_count", "ray": "k_ray", "alloc": "k_alloc", "scatter": "k_scatter", "fuse": "k_fuse",
+                "clear": "k_clear", "normals": "k_normals", "smooth": "k_smooth", "inpaint": "k_inpaint"}
+LAYER_NAMES = {LAYER_ELEVATION: "h", LAYER_VARIANCE: "var", LAYER_TIME: "t_last", LAYER_NORMAL_X: "nx",
+               LAYER_NORMAL_Y: "ny", LAYER_NORMAL_Z: "nz", LAYER_SMOOTH: "smooth", LAYER_INPAINT: "inpaint",
+               LAYER_VALID: "valid", LAYER_VARIANCE_NOW: "var_now"}
+
+
+class EMError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {status_str(code)} ({code}) {last_cuda_error()}")
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("resolution", ctypes.c_float),
+                ("noise_a0", ctypes.c_float), ("noise_a1", ctypes.c_float), ("noise_a2", ctypes.c_float),
+                ("var_min", ctypes.c_float), ("min_range", ctypes.c_float), ("max_range", ctypes.c_float),
+                ("mahalanobis_k", ctypes.c_float), ("outlier_variance", ctypes.c_float),
+                ("wall_num_thresh", ctypes.c_int32), ("time_variance", ctypes.c_float),
+                ("ray_step", ctypes.c_float), ("cleanup_min_age", ctypes.c_int32),
+                ("cleanup_normal_thresh", ctypes.c_float), ("flags", ctypes.c_uint32)]
+
+
+class _Cloud(ctypes.Structure):
+    _fields_ = [("points", ctypes.c_void_p), ("n", ctypes.c_int64), ("stride", ctypes.c_int32),
+                ("pose", ctypes.c_float * 12)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("resolution", ctypes.c_float),
+                ("t_now", ctypes.c_int32), ("shift_x", ctypes.c_int64), ("shift_y", ctypes.c_int64),
+                ("x0", ctypes.c_double), ("y0", ctypes.c_double), ("point_capacity", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("updates", "points_in", "points_valid", "points_in_map",
+                                             "points_accepted", "points_rejected", "points_wall",
+                                             "cells_updated", "cells_cleared", "ray_samples")]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_2204_12876_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    sig = {
+        "em_create": ([ctypes.POINTER(_Params), ctypes.c_int, ctypes.POINTER(vp)], ctypes.c_int),
+        "em_destroy": ([vp], ctypes.c_int),
+        "em_reserve": ([vp, i64], ctypes.c_int),
+        "em_update": ([vp, vp, i64, i32, ctypes.POINTER(ctypes.c_float), vp], ctypes.c_int),
+        "em_update_multi": ([vp, ctypes.POINTER(_Cloud), i32, vp], ctypes.c_int),
+        "em_update_host": ([vp, ctypes.POINTER(_Cloud), i32, vp], ctypes.c_int),
+        "em_shift": ([vp, i32, i32, vp], ctypes.c_int),
+        "em_get_layers": ([vp, ctypes.c_uint32, vp, ctypes.c_int, vp], ctypes.c_int),
+        "em_set_layers": ([vp, ctypes.c_uint32, vp, ctypes.c_int, vp], ctypes.c_int),
+        "em_set_time": ([vp, i32], ctypes.c_int),
+        "em_get_info": ([vp, ctypes.POINTER(_Info)], ctypes.c_int),
+        "em_get_stats": ([vp, ctypes.POINTER(_Stats)], ctypes.c_int),
+        "em_sync": ([vp], ctypes.c_int),
+        "em_get_trace": ([vp, vp, vp, vp, i64], ctypes.c_int),
+        "em_profile": ([vp, ctypes.c_int], ctypes.c_int),
+        "em_profile_read": ([vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+        "em_status_str": ([ctypes.c_int], ctypes.c_char_p),
+        "em_last_cuda_error": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+lib = _load()
+
+
+def status_str(code: int) -> str:
+    return lib.em_status_str(int(code)).decode()
+
+
+def last_cuda_error() -> str:
+    return lib.em_last_cuda_error().decode()
+
+
+def _check(rc: int, what: str):
+    if rc != EM_OK:
+        raise EMError(rc, what)
+
+
+@dataclass
+class Params:
+    """em_params (include/em.h); float fields are float32 in the library."""
+    width: int = 100
+    height: int = 100
+    resolution: float = 0.04
+    noise_a0: float = 0.0
+    noise_a1: float = 0.0
+    noise_a2: float = 0.0
+    var_min: float = 1e-8
+    min_range: float = 0.0
+    max_range: float = 1e9
+    mahalanobis_k: float = 0.0
+    outlier_variance: float = 0.0
+    wall_num_thresh: int = 0
+    time_variance: float = 0.0
+    ray_step: float = 0.0
+    cleanup_min_age: int = 0
+    cleanup_normal_thresh: float = 0.0
+    flags: int = 0
+
+    def _c(self) -> _Params:
+        return _Params(**{f.name: getattr(self, f.name) for f in fields(self)})
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _pose(pose) -> ctypes.Array:
+    p = np.ascontiguousarray(pose, dtype=np.float32).reshape(12)
+    return (ctypes.c_float * 12)(*[float(v) for v in p])
+
+
+def _cloud_struct(pts, pose, host: bool) -> _Cloud:
+    if host:
+        n, stride = pts.shape
+        ptr = pts.ctypes.data
+    else:
+        if pts.dtype.__str__() != "torch.float32" or not pts.is_cuda or not pts.is_contiguous():
+            raise ValueError("points must be a contiguous float32 CUDA tensor of shape (n, 3) or (n, 4)")
+        n, stride = pts.shape
+        ptr = pts.data_ptr()
+    c = _Cloud()
+    c.points = ptr
+    c.n = n
+    c.stride = stride
+    c.pose = _pose(pose)
+    return c
+
+
+class Map:
+    """One elevation map resident on a CUDA device."""
+
+    def __init__(self, params: Params, device: int = 0):
+        self.params = params
+        self._cp = params._c()
+        h = ctypes.c_void_p()
+        _check(lib.em_create(ctypes.byref(self._cp), int(device), ctypes.byref(h)), "em_create")
+        self._h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.em_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        return self._h
+
+    @property
+    def shape(self):
+        return (self.params.height, self.params.width)
+
+    def reserve(self, max_points: int):
+        _check(lib.em_reserve(self._h, int(max_points)), "em_reserve")
+
+    def update(self, points, pose, stream=None):
+        """Fuse one device cloud: points is a float32 CUDA tensor (n, 3|4)."""
+        if points.dtype.__str__() != "torch.float32" or not points.is_cuda or not points.is_contiguous():
+            raise ValueError("points must be a contiguous float32 CUDA tensor of shape (n, 3) or (n, 4)")
+        n, stride = points.shape
+        _check(lib.em_update(self._h, points.data_ptr(), n, stride, _pose(pose), _stream_handle(stream)),
+               "em_update")
+
+    def update_multi(self, clouds, stream=None):
+        """One update from several device clouds [(tensor, pose), ...]."""
+        arr = (_Cloud * len(clouds))(*[_cloud_struct(p, q, False) for p, q in clouds])
+        _check(lib.em_update_multi(self._h, arr, len(clouds), _stream_handle(stream)), "em_update_multi")
+
+    def update_host(self, clouds, stream=None):
+        """One update from host clouds [(np.ndarray float32 (n,3|4), pose), ...]."""
+        keep = [np.ascontiguousarray(p, dtype=np.float32) for p, _ in clouds]
+        arr = (_Cloud * len(clouds))(*[_cloud_struct(k, q, True) for k, (_, q) in zip(keep, clouds)])
+        _check(lib.em_update_host(self._h, arr, len(clouds), _stream_handle(stream)), "em_update_host")
+
+    def shift(self, dx: int, dy: int, stream=None):
+        _check(lib.em_shift(self._h, int(dx), int(dy), _stream_handle(stream)), "em_shift")
+
+    def get_layers(self, mask: int, out=None, stream=None):
+        """Layers in ascending bit order.  out=None: host numpy (k, H, W); else a CUDA tensor."""
+        k = bin(mask).count("1")
+        H, W = self.shape
+        if out is None:
+            host = np.empty((k, H, W), np.float32)
+            _check(lib.em_get_layers(self._h, mask, host.ctypes.data, 1, _stream_handle(stream)), "em_get_layers")
+            return host
+        if out.numel() != k * H * W:
+            raise ValueError("output tensor has the wrong size")
+        _check(lib.em_get_layers(self._h, mask, out.data_ptr(), 0, _stream_handle(stream)), "em_get_layers")
+        return out
+
+    def state(self) -> dict:
+        """All layers as host float32 arrays keyed by name (t_last as int32)."""
+        mask = sum(LAYER_NAMES) & ~LAYER_VALID
+        arr = self.get_layers(mask)
+        out = {}
+        for i, bit in enumerate(b for b in sorted(LAYER_NAMES) if mask & b):
+            out[LAYER_NAMES[bit]] = arr[i]
+        out["t_last"] = out["t_last"].astype(np.int32)
+        return out
+
+    def set_layers(self, mask: int, src, stream=None):
+        if isinstance(src, np.ndarray):
+            src = np.ascontiguousarray(src, dtype=np.float32)
+            _check(lib.em_set_layers(self._h, mask, src.ctypes.data, 1, _stream_handle(stream)), "em_set_layers")
+        else:
+            _check(lib.em_set_layers(self._h, mask, src.data_ptr(), 0, _stream_handle(stream)), "em_set_layers")
+
+    def set_state(self, h=None, var=None, t_last=None, nx=None, ny=None, nz=None, t_now=None):
+        layers, mask = [], 0
+        for bit, a in ((LAYER_ELEVATION, h), (LAYER_VARIANCE, var), (LAYER_TIME, t_last), (LAYER_NORMAL_X, nx),
+                       (LAYER_NORMAL_Y, ny), (LAYER_NORMAL_Z, nz)):
+            if a is not None:
+                mask |= bit
+                layers.append(np.asarray(a, np.float32))
+        if mask:
+            self.set_layers(mask, np.stack(layers))
+        if t_now is not None:
+            _check(lib.em_set_time(self._h, int(t_now)), "em_set_time")
+
+    def info(self) -> dict:
+        i = _Info()
+        _check(lib.em_get_info(self._h, ctypes.byref(i)), "em_get_info")
+        return {f: getattr(i, f) for f, _ in _Info._fields_}
+
+    def stats(self) -> dict:
+        s = _Stats()
+        _check(lib.em_get_stats(self._h, ctypes.byref(s)), "em_get_stats")
+        return {f: getattr(s, f) for f, _ in _Stats._fields_}
+
+    def sync(self):
+        _check(lib.em_sync(self._h), "em_sync")
+
+    def profile(self, enable: bool = True):
+        _check(lib.em_profile(self._h, 1 if enable else 0), "em_profile")
+
+    def profile_read(self) -> dict:
+        ms = (ctypes.c_double * len(PROF_SLOTS))()
+        n = (ctypes.c_int64 * len(PROF_SLOTS))()
+        _check(lib.em_profile_read(self._h, ms, n), "em_profile_read")
+        return {k: (ms[i], n[i]) for i, k in enumerate(PROF_SLOTS)}
+
+    def trace(self, n: int):
+        ix = np.empty(n, np.int32)
+        iy = np.empty(n, np.int32)
+        st = np.empty(n, np.uint8)
+        _check(lib.em_get_trace(self._h, ix.ctypes.data, iy.ctypes.data, st.ctypes.data, int(n)), "em_get_trace")
+        return ix, iy, st

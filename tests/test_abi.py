@@ -1,0 +1,79 @@
+"""The C ABI: libem.so builds, loads and exports every entry point declared in
+include/em.h, and the binding's ctypes structures match the header's layout
+(checked against a C program compiled with gcc).  No GPU needed."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "em.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(em_\w+)\s*\(", text, re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    from paper_2204_12876_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("em_create", "em_update", "em_shift", "em_get_layers", "em_destroy", "em_update_multi",
+                     "em_set_layers", "em_get_stats", "em_sync", "em_status_str"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (em_\w+)$", out, re.M))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    lib = ctypes.CDLL(lib_path)
+    for n in declared_functions():
+        assert getattr(lib, n)
+
+
+def test_status_strings_without_gpu(lib_path):
+    lib = ctypes.CDLL(lib_path)
+    lib.em_status_str.restype = ctypes.c_char_p
+    assert lib.em_status_str(0) == b"ok"
+    assert lib.em_status_str(-1) == b"invalid argument"
+    assert lib.em_status_str(-4) == b"timeout"
+
+
+def test_struct_layout_matches_header(tmp_path, lib_path):
+    from paper_2204_12876_gb300 import em
+    src = tmp_path / "layout.c"
+    structs = {"em_params": em._Params, "em_cloud": em._Cloud, "em_info": em._Info, "em_stats": em._Stats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "em.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname}.{f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("return 0; }")
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = dict(line.rsplit(" ", 1) for line in out if line)
+    for cname, py in structs.items():
+        assert int(got[f"{cname} size"]) == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert int(got[f"{cname}.{f}"]) == getattr(py, f).offset, (cname, f)
+
+
+def test_product_path_has_no_oracle_dependency():
+    """The package never imports the oracle and never falls back to the CPU."""
+    pkg = os.path.join(ROOT, "paper_2204_12876_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "oracle" not in text.replace("the oracle", ""), f

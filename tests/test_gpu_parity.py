@@ -1,0 +1,291 @@
+"""CUDA path vs the FP64 oracle, element by element on the same seeded inputs.
+
+Every case runs one update (several clouds for a camera rig) on both sides from
+the same float32 map state, then compares per-point cells and decisions, the
+cell state, the removed cells and the filter layers (tolerances in parity.py).
+Multi-frame streams are checked frame by frame: before each frame both sides
+start from the oracle's own state of the previous frame, rounded to float32.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests import parity
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEPTH_P = dict(width=200, height=200, resolution=0.04, noise_a0=0.005, noise_a2=0.002, var_min=1e-8,
+               min_range=0.05, max_range=10.0, mahalanobis_k=2.5, outlier_variance=1e-4, ray_step=0.04,
+               cleanup_min_age=0, cleanup_normal_thresh=0.0)
+LIDAR_P = dict(width=500, height=500, resolution=0.04, noise_a0=0.01, noise_a2=0.001, var_min=1e-8,
+               min_range=0.3, max_range=40.0, mahalanobis_k=2.5, outlier_variance=1e-4, ray_step=0.04,
+               cleanup_min_age=0, cleanup_normal_thresh=0.1, flags=1 | 2 | 4)
+
+
+@pytest.fixture(scope="module")
+def em():
+    from paper_2204_12876_gb300 import build
+    build.build()
+    from paper_2204_12876_gb300 import em as mod
+    return mod
+
+
+def gpu_map(em, P, trace=True):
+    p = dict(P)
+    p["flags"] = p.get("flags", 0) | (em.F_TRACE if trace else 0)
+    return em.Map(em.Params(**p))
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def run_case(em, P, clouds, prior=None, shift=(0, 0), wall_on=False, stencils=()):
+    om = oracle.OracleMap(parity.oracle_params(P))
+    gm = gpu_map(em, P)
+    if shift != (0, 0):
+        om.shift(*shift)
+        gm.shift(*shift)
+    if prior is not None:
+        parity.prior_to_oracle(om, prior)
+        parity.prior_to_gpu(gm, prior)
+    prior_valid = np.isfinite(om.state()["var"])
+    tr = om.update(clouds, trace=True, unit=oracle.FP32_UNIT, abs_band=parity.ABS_BAND)
+    gm.update_multi([(dev(p), q) for p, q in clouds])
+    n = sum(len(p) for p, _ in clouds)
+    cmp = parity.compare_update(tr, om.state(), gm.state(), gm.trace(n), wall_on=wall_on,
+                                check_stencils=stencils, prior_valid=prior_valid)
+    return cmp, tr, gm, om
+
+
+def check_counts(gm, tr, slack):
+    st = gm.stats()
+    assert st["points_in"] == tr.counts["in"]
+    assert abs(st["points_valid"] - tr.counts["valid"]) <= slack
+    assert abs(st["points_in_map"] - tr.counts["in_map"]) <= slack
+    assert abs(st["points_accepted"] - tr.counts["accepted"]) <= slack
+    assert abs(st["points_rejected"] - tr.counts["rejected"]) <= slack
+    assert abs(st["points_wall"] - tr.counts["wall"]) <= slack
+    return st
+
+
+def test_single_update_empty_map(em):
+    """20,000 points, 100x100 grid at 0.04 m, empty prior, identity pose."""
+    P = dict(width=100, height=100, resolution=0.04, noise_a0=0.005, noise_a2=0.002, mahalanobis_k=2.5,
+             outlier_variance=1e-4)
+    pts, pose = synth.single_update(seed=1)
+    cmp, tr, gm, _ = run_case(em, P, [(pts, pose)])
+    assert cmp.notes["cells_compared"] > 5000
+    assert cmp.notes["value_marginal_cells"] < 0.01 * cmp.notes["cells_valid"]
+    check_counts(gm, tr, cmp.notes["marginal_points"])
+
+
+def test_single_update_prior_gate_wall_time(em):
+    """Seeded prior: Mahalanobis gate, outlier variance, wall rule, time variance."""
+    P = dict(width=100, height=100, resolution=0.04, noise_a0=0.005, noise_a2=0.002, mahalanobis_k=2.5,
+             outlier_variance=1e-4, wall_num_thresh=6, time_variance=2e-6)
+    prior = synth.random_prior(seed=21, width=100, height=100, t_now=10)
+    pts, pose = synth.single_update(seed=22, n=30000)
+    cmp, tr, gm, _ = run_case(em, P, [(pts, pose)], prior=prior, wall_on=True)
+    assert tr.counts["rejected"] > 100 and tr.counts["wall"] > 100 and tr.counts["accepted"] > 1000
+    check_counts(gm, tr, cmp.notes["marginal_points"])
+
+
+def test_stride4_and_misaligned_and_ragged(em):
+    """Stride-4 rows, a base pointer off 16-byte alignment and a ragged count
+    give the same state as the aligned stride-3 cloud, bit for bit."""
+    P = dict(width=100, height=100, resolution=0.04, noise_a0=0.005, noise_a2=0.002, mahalanobis_k=2.5)
+    prior = synth.random_prior(seed=3, width=100, height=100, t_now=4)
+    pts, pose = synth.single_update(seed=4, n=20001)
+    ref = gpu_map(em, P, trace=False)
+    parity.prior_to_gpu(ref, prior)
+    ref.update(dev(pts), pose)
+    s_ref = ref.state()
+    p4 = np.concatenate([pts, np.full((len(pts), 1), 7.0, np.float32)], axis=1)
+    big = dev(np.concatenate([np.zeros((1, 3), np.float32), pts]))
+    for variant in ("stride4", "offset"):
+        g = gpu_map(em, P, trace=False)
+        parity.prior_to_gpu(g, prior)
+        if variant == "stride4":
+            g.update(dev(p4), pose)
+        else:
+            g.update(big[1:], pose)  # 12-byte offset: not 16-byte aligned
+        s = g.state()
+        for k in ("h", "var", "t_last"):
+            assert np.array_equal(s[k], s_ref[k], equal_nan=True), (variant, k)
+
+
+def test_permutation_bit_identical(em):
+    """The fused map does not depend on the order of the points, bit for bit."""
+    P = dict(width=100, height=100, resolution=0.04, noise_a0=0.005, noise_a2=0.002, mahalanobis_k=2.5,
+             outlier_variance=1e-4)
+    prior = synth.random_prior(seed=5, width=100, height=100, t_now=3)
+    pts, pose = synth.single_update(seed=6, n=50000)
+    states = []
+    for seed in (None, 1, 2):
+        p = pts if seed is None else pts[np.random.default_rng(seed).permutation(len(pts))]
+        g = gpu_map(em, P, trace=False)
+        parity.prior_to_gpu(g, prior)
+        g.update(dev(p), pose)
+        states.append(g.state())
+    for s in states[1:]:
+        for k in ("h", "var", "t_last"):
+            assert np.array_equal(s[k], states[0][k], equal_nan=True), k
+
+
+def test_empty_and_degenerate_updates(em):
+    P = dict(width=64, height=48, resolution=0.05, noise_a0=0.01, ray_step=0.05)
+    g = gpu_map(em, P)
+    pts, pose = synth.single_update(seed=7, n=5000, half=1.0)
+    g.update(dev(pts), pose)
+    s0 = g.state()
+    g.update(dev(np.zeros((0, 3), np.float32)), pose)                 # n = 0: time advances only
+    s1 = g.state()
+    assert g.info()["t_now"] == 2
+    assert np.array_equal(s1["h"], s0["h"], equal_nan=True)
+    nan = np.full((1000, 3), np.nan, np.float32)
+    g.update(dev(nan), pose)                                          # all non-finite
+    far = np.full((1000, 3), 50.0, np.float32)
+    g.update(dev(far), pose)                                          # all outside
+    s2 = g.state()
+    assert np.array_equal(s2["h"], s0["h"], equal_nan=True)
+    st = g.stats()
+    assert st["updates"] == 4 and st["points_in"] == 7000 and st["points_valid"] == 5000 + 1000
+
+
+def test_two_clouds_equal_one_merged(em):
+    P = dict(width=100, height=100, resolution=0.04, noise_a0=0.005, noise_a2=0.002, mahalanobis_k=2.5)
+    pts, pose = synth.single_update(seed=8, n=20000)
+    a = gpu_map(em, P, trace=False)
+    a.update(dev(pts), pose)
+    b = gpu_map(em, P, trace=False)
+    b.update_multi([(dev(pts[:7000]), pose), (dev(pts[7000:]), pose)])
+    sa, sb = a.state(), b.state()
+    for k in ("h", "var"):
+        assert np.array_equal(sa[k], sb[k], equal_nan=True)
+
+
+def test_shift_parity(em):
+    P = dict(width=120, height=90, resolution=0.04, noise_a0=0.005, noise_a2=0.002, mahalanobis_k=2.5)
+    prior = synth.random_prior(seed=9, width=120, height=90, t_now=2)
+    pts, pose = synth.single_update(seed=10, n=20000)
+    run_case(em, P, [(pts, pose)], prior=prior, shift=(7, -11))
+    run_case(em, P, [(pts, pose)], prior=prior, shift=(-119, 89))
+    # a shift by more than the map empties it
+    g = gpu_map(em, P, trace=False)
+    parity.prior_to_gpu(g, prior)
+    g.shift(500, 0)
+    assert not np.isfinite(g.state()["var"]).any()
+
+
+def test_layers_roundtrip_with_ring(em):
+    P = dict(width=73, height=51, resolution=0.05, noise_a0=0.01, flags=1)
+    prior = synth.random_prior(seed=11, width=73, height=51, t_now=6)
+    g = gpu_map(em, P, trace=False)
+    g.shift(13, -29)
+    parity.prior_to_gpu(g, prior)
+    s = g.state()
+    fin = np.isfinite(prior["var"])
+    assert np.array_equal(s["h"][fin], prior["h"][fin])
+    assert np.array_equal(s["var"], np.where(fin, prior["var"], np.inf).astype(np.float32))
+    assert np.array_equal(s["t_last"], prior["t_last"])
+    for k in ("nx", "ny", "nz"):
+        assert np.array_equal(s[k], prior[k], equal_nan=True)
+    g.shift(-13, 29)
+    s2 = g.state()
+    assert np.isfinite(s2["var"]).sum() < fin.sum()
+
+
+def test_invalid_arguments(em):
+    with pytest.raises(em.EMError) as e:
+        em.Map(em.Params(width=0))
+    assert e.value.code == em.EM_ERR_INVALID_ARG
+    with pytest.raises(em.EMError):
+        em.Map(em.Params(var_min=0.0))
+    g = gpu_map(em, dict(width=10, height=10), trace=False)
+    pts = dev(np.zeros((10, 3), np.float32))
+    with pytest.raises(em.EMError) as e:
+        g.update(dev(np.zeros((10, 5), np.float32)), np.eye(3, 4).reshape(12))
+    assert e.value.code == em.EM_ERR_INVALID_ARG
+    bad = np.eye(3, 4).reshape(12).astype(np.float32)
+    bad[3] = np.nan
+    with pytest.raises(em.EMError):
+        g.update(pts, bad)
+    with pytest.raises(em.EMError):
+        g.get_layers(1 << 12)
+
+
+def test_visibility_depth_frame(em):
+    """One 4-camera depth frame over a prior with stale obstacles: ray casting,
+    removal, Mahalanobis gate (full frame: 4 x 76,800 points, 200 x 200)."""
+    fr = next(synth.depth_stream(seed=2, frames=1))
+    prior = synth.random_prior(seed=2, width=200, height=200, t_now=5, obstacle_frac=0.05)
+    cmp, tr, gm, _ = run_case(em, DEPTH_P, fr["clouds"], prior=prior)
+    assert cmp.notes["cleared"] > 50
+    assert tr.counts["rejected"] > 100
+    check_counts(gm, tr, cmp.notes["marginal_points"])
+    st = gm.stats()
+    assert st["cells_cleared"] >= cmp.notes["cleared"] - cmp.notes["mark_marginal_cells"]
+
+
+def test_depth_stream_frame_by_frame(em):
+    """Frames of the depth-camera stream with recentring shifts; each frame
+    starts both sides from the oracle's previous state (float32)."""
+    om = oracle.OracleMap(parity.oracle_params(DEPTH_P))
+    r = DEPTH_P["resolution"]
+    for t, fr in enumerate(synth.depth_stream(seed=2, frames=4)):
+        dx = int(round(fr["xy"][0] / r)) - om.shift_xy[0]
+        dy = int(round(fr["xy"][1] / r)) - om.shift_xy[1]
+        om.shift(dx, dy)
+        prior = parity.oracle_state_as_prior(om)
+        g = gpu_map(em, DEPTH_P)
+        sx, sy = om.shift_xy
+        g.shift(sx, sy)
+        parity.prior_to_gpu(g, prior)
+        parity.prior_to_oracle(om, prior)
+        prior_valid = np.isfinite(prior["var"])
+        tr = om.update(fr["clouds"], trace=True, unit=oracle.FP32_UNIT, abs_band=parity.ABS_BAND)
+        g.update_multi([(dev(p), q) for p, q in fr["clouds"]])
+        n = sum(len(p) for p, _ in fr["clouds"])
+        cmp = parity.compare_update(tr, om.state(), g.state(), g.trace(n), prior_valid=prior_valid)
+        assert cmp.notes["cells_compared"] > 3000, t
+
+
+def test_lidar_frame_with_filters(em):
+    """A LiDAR scan (128 x 2048) on a 500 x 500 map over stairs and a ramp, with
+    normals (and the Eq. 4 guard), 5x5 smoothing and in-painting."""
+    frames = synth.lidar_stream(seed=3, frames=2)
+    f0 = next(frames)
+    f1 = next(frames)
+    om = oracle.OracleMap(parity.oracle_params(LIDAR_P))
+    om.update(f0["clouds"])
+    prior = parity.oracle_state_as_prior(om)
+    cmp, tr, gm, _ = run_case(em, LIDAR_P, f1["clouds"], prior=prior,
+                              stencils=("nx", "ny", "nz", "smooth", "inpaint"))
+    assert cmp.notes["cells_compared"] > 20000
+    s = gm.state()
+    assert np.isfinite(s["nz"]).sum() > 10000 and np.isfinite(s["inpaint"]).sum() >= np.isfinite(s["h"]).sum()
+
+
+def test_maximum_map_size(em):
+    """The largest map (2^26 cells) takes an update; its centre agrees with a
+    small map on the same points (cells offset by an integer)."""
+    P = dict(width=8192, height=8192, resolution=0.04, noise_a0=0.005, noise_a2=0.002)
+    pts, pose = synth.single_update(seed=12, n=100000, half=1.9)
+    big = gpu_map(em, P, trace=False)
+    big.update(dev(pts), pose)
+    hb = big.get_layers(em.LAYER_ELEVATION)[0]
+    small = gpu_map(em, dict(P, width=100, height=100), trace=False)
+    small.update(dev(pts), pose)
+    hs = small.get_layers(em.LAYER_ELEVATION)[0]
+    o = (8192 - 100) // 2
+    sub = hb[o:o + 100, o:o + 100]
+    both = np.isfinite(sub) & np.isfinite(hs)
+    assert both.sum() > 0.99 * np.isfinite(hs).sum()
+    # the two grids bin a point near a cell edge the same way up to float32 rounding of x0
+    assert np.mean(np.abs(sub[both] - hs[both]) <= 1e-5) > 0.99
+    assert np.isfinite(hb).sum() == pytest.approx(np.isfinite(hs).sum(), rel=0.01)
