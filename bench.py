@@ -201,7 +201,7 @@ def run_ours(args, rank: int, world: int):
 
     # ---- per-kernel profile pass (same steps, events around every kernel)
     m.profile(True)
-    for i in range(K):
+    for i in range(K if not args.no_profile else 1):
         flush.zero_()
         step(args.warmup + i)
     prof = m.profile_read()
@@ -219,7 +219,7 @@ def run_ours(args, rank: int, world: int):
     torch.cuda.synchronize()
     e2e_pts = 0
     t0 = time.perf_counter()
-    for i in range(K):
+    for i in range(K if not args.no_e2e else 1):
         k = (args.warmup + i) % len(pool)
         me.update_host(host_pool[k])
         me.get_layers(out_mask)  # waits for the update: the published map
@@ -358,6 +358,8 @@ def main():
     ap.add_argument("--frames", type=int, default=6, help="distinct frames generated and cycled")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="one e2e step only (for profiler runs)")
+    ap.add_argument("--no-profile", action="store_true", help="one event-profiled step only (for profiler runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
