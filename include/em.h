@@ -212,6 +212,40 @@ int em_profile(em_map* map, int enable);
  * enabled (both arrays EM_PROF_SLOTS long, host memory); waits for the map. */
 int em_profile_read(em_map* map, double* ms, int64_t* launches);
 
+/* ---- Update without allocation.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory when they update a map -- a real-time loop
+ * that forbids allocation after start-up, a framework whose own allocator
+ * already holds the device memory, or code running while a stream is being
+ * captured.  It runs the update of em_update (binning, counting sort by cell,
+ * wall rule, Mahalanobis gate, Eq. 1/2 fusion, ray march and removal; not the
+ * per-cell filters) on layers the caller owns, in logical row-major order
+ * without a ring offset:
+ *   h, var      float32 [height][width], device memory, read and written;
+ *               an empty cell has var = +inf (h is then NaN)
+ *   t_last      int32 [height][width], device memory, read and written
+ *   nx, ny, nz  float32 [height][width], device memory, read only; required
+ *               when cleanup_normal_thresh > 0, else may be NULL
+ *   shift_x/y   the map centre is (shift_x r, shift_y r) (see em_info)
+ *   t_now       index of this update (>= 1): cells it writes get t_last = t_now
+ *   clouds[]    host array; clouds[i].points device memory
+ * All scratch lives in one static device array of the library (about 4 MiB,
+ * held by every GPU that loads the library until the process exits).  The
+ * first call on a device looks up that array's address with the device
+ * current; make that first call before any stream capture.  Every call uses
+ * the same array and it keeps the previous call's contents (the call clears
+ * what must start at zero); calls whose GPU work overlaps race on it.  Calls
+ * no cudaMalloc / cudaFree.  Returns EM_ERR_CAPACITY when width*height >
+ * EM_NOALLOC_MAX_CELLS, the points of all clouds > EM_NOALLOC_MAX_POINTS or
+ * n_clouds > EM_NOALLOC_MAX_CLOUDS; EM_ERR_INVALID_ARG for bad arguments.
+ * Asynchronous on `stream`; device-side errors are not reported. */
+#define EM_NOALLOC_MAX_CELLS 65536
+#define EM_NOALLOC_MAX_POINTS 327680
+#define EM_NOALLOC_MAX_CLOUDS 8
+int em_update_noalloc(const em_params* params, int64_t shift_x, int64_t shift_y, int32_t t_now, float* h,
+                      float* var, int32_t* t_last, const float* nx, const float* ny, const float* nz,
+                      const em_cloud* clouds, int32_t n_clouds, em_stream_t stream);
+
 /* Text for a status code (static storage). */
 const char* em_status_str(int status);
 

@@ -1,0 +1,196 @@
+// em_noalloc.cu -- em_update_noalloc: one map update that allocates no memory.
+//
+// Some callers cannot call cudaMalloc at update time: a real-time control loop
+// that forbids allocation after start-up (an allocation can block on the
+// driver for milliseconds), a host framework whose own caching allocator has
+// already claimed the device memory, or code that prepares work while a CUDA
+// stream is being captured.  For them this entry point runs the same kernels
+// as em_update (binning, counting sort by cell, gate + fusion, ray march,
+// removal) on map layers the caller owns, and keeps every piece of scratch
+// memory in one file-scope __device__ array of fixed size.
+//
+// Limits: at most kMaxCells cells per map and kMaxPoints points per update
+// (about 4 MiB of scratch, held by every GPU that loads the library until the
+// process exits).  Every call shares the array and it keeps the last call's
+// contents; the call clears what must start at zero.  Calls whose GPU work
+// overlaps (e.g. on two streams) race on the array.
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <cmath>
+#include <mutex>
+
+#include "em.h"
+#include "em_internal.cuh"
+
+using namespace em;
+
+namespace {
+
+constexpr int32_t kMaxCells = EM_NOALLOC_MAX_CELLS;
+constexpr int64_t kMaxPoints = EM_NOALLOC_MAX_POINTS;
+constexpr int kMaxCloudsNA = EM_NOALLOC_MAX_CLOUDS;
+
+constexpr size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// scratch layout; the part that must start at zero (ctl, marks, counts) is contiguous
+constexpr size_t kOffDesc = 0;
+constexpr size_t kOffCtl = kOffDesc + up256(sizeof(BatchDev) + sizeof(MapDev) + kMaxCloudsNA * sizeof(CloudDev));
+constexpr size_t kOffMark = kOffCtl + up256(sizeof(MapCtl));
+constexpr size_t kOffCnt = kOffMark + up256(((size_t)kMaxCells + 31) / 32 * sizeof(uint32_t));
+constexpr size_t kOffCellBase = kOffCnt + up256((size_t)kMaxCells * sizeof(int32_t));
+constexpr size_t kOffTouched = kOffCellBase + up256((size_t)kMaxCells * sizeof(int32_t));
+constexpr size_t kOffSegBase = kOffTouched + up256((size_t)kMaxCells * sizeof(int32_t));
+constexpr size_t kOffSegLen = kOffSegBase + up256((size_t)kMaxCells * sizeof(int32_t));
+constexpr size_t kOffRec = kOffSegLen + up256((size_t)kMaxCells * sizeof(int32_t));
+constexpr size_t kScratchBytes = kOffRec + up256((size_t)kMaxPoints * sizeof(float2));
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+unsigned char* g_addr[kMaxDevices] = {};
+
+thread_local char g_msg[192] = "";
+
+}  // namespace
+
+// The scratch itself.  In host code this name is only a stand-in for the
+// device array: its device address comes from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+namespace {
+
+int na_status(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return EM_OK;
+  snprintf(g_msg, sizeof(g_msg), "%s: %s", what, cudaGetErrorString(e));
+  return EM_ERR_CUDA;
+}
+
+// Device address of the scratch on the current device, looked up once per
+// device with that device current.
+int scratch_address(int dev, unsigned char** out) {
+  if (dev < 0 || dev >= kMaxDevices) return EM_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return na_status(e == cudaSuccess ? cudaErrorInvalidSymbol : e, "cudaGetSymbolAddress");
+    g_addr[dev] = static_cast<unsigned char*>(p);
+  }
+  *out = g_addr[dev];
+  return EM_OK;
+}
+
+bool na_params_ok(const em_params* p) {
+  if (!p || p->width < 1 || p->height < 1) return false;
+  if (!(std::isfinite(p->resolution) && p->resolution > 0.f)) return false;
+  const float f[] = {p->noise_a0, p->noise_a1, p->noise_a2, p->var_min, p->min_range, p->mahalanobis_k,
+                     p->outlier_variance, p->time_variance, p->ray_step, p->cleanup_normal_thresh};
+  for (float v : f)
+    if (!std::isfinite(v)) return false;
+  return p->var_min > 0.f && !std::isnan(p->max_range) && p->max_range >= p->min_range &&
+         p->outlier_variance >= 0.f && p->time_variance >= 0.f && p->ray_step >= 0.f &&
+         p->wall_num_thresh >= 0 && p->cleanup_min_age >= 0;
+}
+
+}  // namespace
+
+extern "C" int em_update_noalloc(const em_params* params, int64_t shift_x, int64_t shift_y, int32_t t_now,
+                                 float* h, float* var, int32_t* t_last, const float* nx, const float* ny,
+                                 const float* nz, const em_cloud* clouds, int32_t n_clouds, em_stream_t stream) {
+  if (!na_params_ok(params) || !h || !var || !t_last || !clouds || n_clouds < 1 || t_now < 1)
+    return EM_ERR_INVALID_ARG;
+  if (params->cleanup_normal_thresh > 0.f && (!nx || !ny || !nz)) return EM_ERR_INVALID_ARG;
+  if ((int64_t)params->width * params->height > kMaxCells || n_clouds > kMaxCloudsNA) return EM_ERR_CAPACITY;
+  int64_t total = 0;
+  for (int i = 0; i < n_clouds; ++i) {
+    const em_cloud& c = clouds[i];
+    if (c.n < 0 || (c.stride != 3 && c.stride != 4) || (c.n > 0 && !c.points)) return EM_ERR_INVALID_ARG;
+    for (int k = 0; k < 12; ++k)
+      if (!std::isfinite(c.pose[k])) return EM_ERR_INVALID_ARG;
+    total += c.n;
+  }
+  if (total > kMaxPoints) return EM_ERR_CAPACITY;
+
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return EM_ERR_CUDA;
+  unsigned char* base = nullptr;
+  int rc = scratch_address(dev, &base);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int32_t W = params->width, H = params->height, ncell = W * H;
+
+  // descriptor, built on the host stack and copied into the scratch
+  unsigned char desc[sizeof(BatchDev) + sizeof(MapDev) + kMaxCloudsNA * sizeof(CloudDev)];
+  BatchDev* b = reinterpret_cast<BatchDev*>(desc);
+  MapDev* m = reinterpret_cast<MapDev*>(desc + sizeof(BatchDev));
+  CloudDev* cd = reinterpret_cast<CloudDev*>(desc + sizeof(BatchDev) + sizeof(MapDev));
+  memset(desc, 0, sizeof(desc));
+  m->h = h;
+  m->var = var;
+  m->t_last = t_last;
+  m->nx = const_cast<float*>(nx);
+  m->ny = const_cast<float*>(ny);
+  m->nz = const_cast<float*>(nz);
+  m->mark = reinterpret_cast<uint32_t*>(base + kOffMark);
+  m->cnt = reinterpret_cast<int32_t*>(base + kOffCnt);
+  m->cell_base = reinterpret_cast<int32_t*>(base + kOffCellBase);
+  m->touched = reinterpret_cast<int32_t*>(base + kOffTouched);
+  m->seg_base = reinterpret_cast<int32_t*>(base + kOffSegBase);
+  m->seg_len = reinterpret_cast<int32_t*>(base + kOffSegLen);
+  m->ctl = reinterpret_cast<MapCtl*>(base + kOffCtl);
+  m->pt_begin = 0;
+  m->pt_count = total;
+  m->W = W;
+  m->H = H;
+  const double r = (double)params->resolution;
+  m->x0 = (float)(r * ((double)shift_x - 0.5 * W));
+  m->y0 = (float)(r * ((double)shift_y - 0.5 * H));
+  m->res = params->resolution;
+  m->t_now = t_now;
+  m->a0 = params->noise_a0; m->a1 = params->noise_a1; m->a2 = params->noise_a2; m->var_min = params->var_min;
+  m->min_range = params->min_range; m->max_range = params->max_range; m->k = params->mahalanobis_k;
+  m->v_out = params->outlier_variance; m->sigma_t2 = params->time_variance; m->ray_step = params->ray_step;
+  m->alpha_n = params->cleanup_normal_thresh; m->wall = params->wall_num_thresh;
+  m->min_age = params->cleanup_min_age;
+  int64_t begin = 0;
+  for (int i = 0; i < n_clouds; ++i) {
+    cd[i].pts = clouds[i].points;
+    cd[i].n = clouds[i].n;
+    cd[i].begin = begin;
+    cd[i].stride = clouds[i].stride;
+    cd[i].map = 0;
+    for (int row = 0; row < 3; ++row) {
+      for (int k = 0; k < 3; ++k) cd[i].R[row * 3 + k] = clouds[i].pose[row * 4 + k];
+      cd[i].t[row] = clouds[i].pose[row * 4 + 3];
+    }
+    begin += clouds[i].n;
+  }
+  b->n_maps = 1;
+  b->n_clouds = n_clouds;
+  b->n_points = total;
+  b->maps = reinterpret_cast<const MapDev*>(base + kOffDesc + sizeof(BatchDev));
+  b->clouds = reinterpret_cast<const CloudDev*>(base + kOffDesc + sizeof(BatchDev) + sizeof(MapDev));
+  b->zw_sorted = reinterpret_cast<float2*>(base + kOffRec);
+
+  const BatchDev* bd = reinterpret_cast<const BatchDev*>(base + kOffDesc);
+  const size_t desc_bytes = sizeof(BatchDev) + sizeof(MapDev) + (size_t)n_clouds * sizeof(CloudDev);
+  // pageable source: returns once the bytes are staged, so the stack buffer may go
+  rc = na_status(cudaMemcpyAsync(base + kOffDesc, desc, desc_bytes, cudaMemcpyHostToDevice, s), "descriptor");
+  if (rc) return rc;
+  // counters, marks and per-cell counts start at zero
+  rc = na_status(cudaMemsetAsync(base + kOffCtl, 0, kOffCnt - kOffCtl + (size_t)ncell * sizeof(int32_t), s),
+                 "cudaMemsetAsync");
+  if (rc) return rc;
+  cudaError_t e = cudaSuccess;
+  if (total > 0) {
+    const int32_t max_touched = ncell < total ? ncell : (int32_t)total;
+    if (e == cudaSuccess) e = launch_bin(bd, total, s);
+    if (e == cudaSuccess && params->ray_step > 0.f) e = launch_ray(bd, total, s);
+    if (e == cudaSuccess) e = launch_alloc(bd, 1, ncell, s);
+    if (e == cudaSuccess) e = launch_scatter(bd, total, s);
+    if (e == cudaSuccess) e = launch_fuse(bd, 1, max_touched, 8, s);
+  }
+  if (e == cudaSuccess) e = launch_clear(bd, 1, ncell, s);
+  return na_status(e, "em_update_noalloc launch");
+}

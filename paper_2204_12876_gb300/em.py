@@ -87,6 +87,8 @@ def _load():
         "em_get_trace": ([vp, vp, vp, vp, i64], ctypes.c_int),
         "em_profile": ([vp, ctypes.c_int], ctypes.c_int),
         "em_profile_read": ([vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+        "em_update_noalloc": ([ctypes.POINTER(_Params), i64, i64, i32, vp, vp, vp, vp, vp, vp,
+                               ctypes.POINTER(_Cloud), i32, vp], ctypes.c_int),
         "em_status_str": ([ctypes.c_int], ctypes.c_char_p),
         "em_last_cuda_error": ([], ctypes.c_char_p),
     }
@@ -290,3 +292,17 @@ class Map:
         st = np.empty(n, np.uint8)
         _check(lib.em_get_trace(self._h, ix.ctypes.data, iy.ctypes.data, st.ctypes.data, int(n)), "em_get_trace")
         return ix, iy, st
+
+
+NOALLOC_MAX_CELLS, NOALLOC_MAX_POINTS, NOALLOC_MAX_CLOUDS = 65536, 327680, 8
+
+
+def update_noalloc(params: Params, h, var, t_last, clouds, t_now: int, shift=(0, 0), normals=None, stream=None):
+    """em_update_noalloc: one update of caller-owned layers (CUDA tensors: h, var
+    float32 (H, W), t_last int32 (H, W)) that allocates no device memory."""
+    cp = params._c()
+    arr = (_Cloud * len(clouds))(*[_cloud_struct(p, q, False) for p, q in clouds])
+    nx, ny, nz = (None, None, None) if normals is None else (n.data_ptr() for n in normals)
+    _check(lib.em_update_noalloc(ctypes.byref(cp), int(shift[0]), int(shift[1]), int(t_now), h.data_ptr(),
+                                 var.data_ptr(), t_last.data_ptr(), nx, ny, nz, arr, len(clouds),
+                                 _stream_handle(stream)), "em_update_noalloc")
