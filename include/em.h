@@ -212,6 +212,48 @@ int em_profile(em_map* map, int enable);
  * enabled (both arrays EM_PROF_SLOTS long, host memory); waits for the map. */
 int em_profile_read(em_map* map, double* ms, int64_t* launches);
 
+/* ---- Batched form: many maps (each with one or more clouds) updated by one
+ * sequence of kernels over all of them -- the per-point and per-cell work of
+ * every map shares each launch, so small updates no longer pay a launch
+ * sequence each.  The arithmetic per map is exactly em_update's.
+ * A batch object owns the record workspace (max_points records), a ring of
+ * device descriptors, and -- with EM_BATCH_GRAPH -- one captured CUDA graph
+ * per descriptor slot, replayed with a single cudaGraphLaunch per batch (grids
+ * are sized from the capacities; actual sizes are read from the descriptor). */
+typedef struct em_batch em_batch;
+
+enum { EM_BATCH_GRAPH = 1u << 0 };
+
+/* Launch shapes picked by the autotuner (or set by hand). */
+typedef struct em_tuning {
+  int32_t ray_group;   /* lanes per ray in the ray march: 1, 2, 4, 8, 16 or 32 */
+  int32_t fuse_group;  /* lanes per small cell in the fusion: 4, 8, 16 or 32 */
+  int32_t big_thresh;  /* cells with more records are fused by a whole block, >= 1 */
+} em_tuning;
+
+/* Capacities: at most max_maps distinct maps, max_clouds clouds and
+ * max_points points per batch, maps of at most max_cells cells. */
+int em_batch_create(int device, int32_t max_maps, int32_t max_clouds, int64_t max_points, int32_t max_cells,
+                    uint32_t flags, em_batch** out);
+int em_batch_destroy(em_batch* batch); /* NULL-safe; waits for the batch's work */
+
+/* Fuse clouds[i] into maps[i] for i < count (host arrays; points on the device).
+ * A map may appear several times: its clouds form one multi-cloud update
+ * (em_update_multi).  Every listed map advances by one update.  Returns
+ * EM_ERR_CAPACITY beyond the batch's capacities.  Asynchronous on `stream`. */
+int em_update_batch(em_batch* batch, em_map* const* maps, const em_cloud* clouds, int32_t count,
+                    em_stream_t stream);
+
+int em_batch_set_tuning(em_batch* batch, const em_tuning* tuning);
+int em_batch_get_tuning(const em_batch* batch, em_tuning* tuning);
+
+/* Autotuner: times candidate launch shapes on this workload (median of `reps`
+ * runs each, coordinate by coordinate) on scratch copies of the maps -- the
+ * maps themselves are not changed -- and keeps the fastest.  Synchronous.
+ * *out (may be NULL) receives the choice. */
+int em_batch_autotune(em_batch* batch, em_map* const* maps, const em_cloud* clouds, int32_t count,
+                      em_stream_t stream, int32_t reps, em_tuning* out);
+
 /* ---- Update without allocation.
  * The paper has no counterpart: this entry point exists for callers that
  * cannot allocate device memory when they update a map -- a real-time loop
@@ -229,7 +271,7 @@ int em_profile_read(em_map* map, double* ms, int64_t* launches);
  *   shift_x/y   the map centre is (shift_x r, shift_y r) (see em_info)
  *   t_now       index of this update (>= 1): cells it writes get t_last = t_now
  *   clouds[]    host array; clouds[i].points device memory
- * All scratch lives in one static device array of the library (about 4 MiB,
+ * All scratch lives in one static device array of the library (about 4.5 MiB,
  * held by every GPU that loads the library until the process exits).  The
  * first call on a device looks up that array's address with the device
  * current; make that first call before any stream capture.  Every call uses

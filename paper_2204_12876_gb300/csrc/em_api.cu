@@ -67,6 +67,7 @@ struct em_map {
   float* inpaint = nullptr;
   // per-cell scratch
   uint32_t* mark = nullptr;
+  float* thr = nullptr;
   int32_t* cnt = nullptr;
   int32_t* cell_base = nullptr;
   int32_t* touched = nullptr;
@@ -102,6 +103,8 @@ struct em_map {
   int64_t layer_bytes = 0;
   int64_t work_bytes = 0;
   int fuse_group = 8;
+  int ray_group = 2;
+  int big_thresh = 64;
   int64_t points_in = 0;
   // per-kernel profiling
   bool prof = false;
@@ -125,7 +128,7 @@ MapDev make_mapdev(const em_map* m) {
   memset(&d, 0, sizeof(d));
   d.h = m->h; d.var = m->var; d.t_last = m->t_last;
   d.nx = m->nx; d.ny = m->ny; d.nz = m->nz; d.smooth = m->smooth; d.inpaint = m->inpaint;
-  d.mark = m->mark; d.cnt = m->cnt; d.cell_base = m->cell_base; d.touched = m->touched;
+  d.mark = m->mark; d.thr = m->thr; d.cnt = m->cnt; d.cell_base = m->cell_base; d.touched = m->touched;
   d.seg_base = m->seg_base; d.seg_len = m->seg_len; d.ctl = m->ctl;
   d.W = m->p.width; d.H = m->p.height; d.ox = m->ox; d.oy = m->oy;
   double x0, y0;
@@ -137,6 +140,7 @@ MapDev make_mapdev(const em_map* m) {
   d.v_out = m->p.outlier_variance; d.sigma_t2 = m->p.time_variance; d.ray_step = m->p.ray_step;
   d.alpha_n = m->p.cleanup_normal_thresh; d.wall = m->p.wall_num_thresh; d.min_age = m->p.cleanup_min_age;
   d.flags = m->p.flags;
+  d.big_thresh = m->big_thresh;
   return d;
 }
 
@@ -192,7 +196,7 @@ void release(em_map* m) {
     if (m->prof_ev[i]) cudaEventDestroy(m->prof_ev[i]);
   cudaFree(m->h); cudaFree(m->var); cudaFree(m->t_last);
   cudaFree(m->nx); cudaFree(m->ny); cudaFree(m->nz); cudaFree(m->smooth); cudaFree(m->inpaint);
-  cudaFree(m->mark); cudaFree(m->cnt); cudaFree(m->cell_base); cudaFree(m->touched);
+  cudaFree(m->mark); cudaFree(m->thr); cudaFree(m->cnt); cudaFree(m->cell_base); cudaFree(m->touched);
   cudaFree(m->seg_base); cudaFree(m->seg_len); cudaFree(m->ctl);
   free_workspace(m);
   cudaFree(m->desc_dev);
@@ -290,6 +294,55 @@ cudaError_t timed(em_map* m, int slot, cudaStream_t s, F fn) {
 
 }  // namespace
 
+// ---- internal accessors for the batched and served forms (em_host.h)
+namespace em {
+
+int map_device(const em_map* m) { return m->device; }
+uint32_t map_flags(const em_map* m) { return m->p.flags; }
+int32_t map_cells(const em_map* m) { return m->p.width * m->p.height; }
+const em_params& map_params(const em_map* m) { return m->p; }
+
+MapDev map_begin_update(em_map* m, int64_t points, int big_thresh) {
+  m->t_now += 1;
+  m->points_in += points;
+  MapDev d = make_mapdev(m);
+  d.big_thresh = big_thresh;
+  return d;
+}
+
+void map_end_update(em_map* m, cudaStream_t s, int64_t points) {
+  m->last_stream = s;
+  m->last_n = points;
+}
+
+void map_undo_update(em_map* m, int64_t points) {
+  m->t_now -= 1;
+  m->points_in -= points;
+}
+
+int map_copy_state(em_map* dst, const em_map* src, cudaStream_t s) {
+  if (dst->p.width != src->p.width || dst->p.height != src->p.height) return EM_ERR_INVALID_ARG;
+  const size_t nc = (size_t)src->p.width * src->p.height;
+  EM_TRY(cudaMemcpyAsync(dst->h, src->h, nc * 4, cudaMemcpyDeviceToDevice, s), "copy state");
+  EM_TRY(cudaMemcpyAsync(dst->var, src->var, nc * 4, cudaMemcpyDeviceToDevice, s), "copy state");
+  EM_TRY(cudaMemcpyAsync(dst->t_last, src->t_last, nc * 4, cudaMemcpyDeviceToDevice, s), "copy state");
+  if (dst->nx && src->nx) {
+    EM_TRY(cudaMemcpyAsync(dst->nx, src->nx, nc * 4, cudaMemcpyDeviceToDevice, s), "copy state");
+    EM_TRY(cudaMemcpyAsync(dst->ny, src->ny, nc * 4, cudaMemcpyDeviceToDevice, s), "copy state");
+    EM_TRY(cudaMemcpyAsync(dst->nz, src->nz, nc * 4, cudaMemcpyDeviceToDevice, s), "copy state");
+  }
+  dst->ox = src->ox;
+  dst->oy = src->oy;
+  dst->shift_x = src->shift_x;
+  dst->shift_y = src->shift_y;
+  dst->t_now = src->t_now;
+  return EM_OK;
+}
+
+int map_record_error(const char* what, cudaError_t e) { return cuda_status(e, what); }
+
+}  // namespace em
+
 extern "C" {
 
 const char* em_status_str(int status) {
@@ -330,7 +383,7 @@ int em_create(const em_params* params, int device, em_map** out) {
   if (normals) { EM_ALLOC(m->nx, nc) EM_ALLOC(m->ny, nc) EM_ALLOC(m->nz, nc) }
   if (params->flags & EM_F_SMOOTH) { EM_ALLOC(m->smooth, nc) }
   if (params->flags & EM_F_INPAINT) { EM_ALLOC(m->inpaint, nc) }
-  EM_ALLOC(m->mark, (nc + 31) / 32) EM_ALLOC(m->cnt, nc) EM_ALLOC(m->cell_base, nc)
+  EM_ALLOC(m->mark, (nc + 31) / 32) EM_ALLOC(m->thr, nc) EM_ALLOC(m->cnt, nc) EM_ALLOC(m->cell_base, nc)
   EM_ALLOC(m->touched, nc) EM_ALLOC(m->seg_base, nc) EM_ALLOC(m->seg_len, nc) EM_ALLOC(m->ctl, 1)
   EM_ALLOC(m->desc_dev, kDescBytes * kSlots)
 #undef EM_ALLOC
@@ -346,10 +399,18 @@ int em_create(const em_params* params, int device, em_map** out) {
     return code;
   }
   m->layer_bytes = tot;
-  const char* g = getenv("EM_FUSE_GROUP");
-  if (g) {
+  // tuning knobs (defaults chosen by measurement; the environment overrides them)
+  if (const char* g = getenv("EM_FUSE_GROUP")) {
     int v = atoi(g);
     if (v == 4 || v == 8 || v == 16 || v == 32) m->fuse_group = v;
+  }
+  if (const char* g = getenv("EM_RAY_GROUP")) {
+    int v = atoi(g);
+    if (v == 1 || v == 2 || v == 4 || v == 8 || v == 16 || v == 32) m->ray_group = v;
+  }
+  if (const char* g = getenv("EM_BIG_THRESH")) {
+    int v = atoi(g);
+    if (v >= 1) m->big_thresh = v;
   }
   *out = m;
   return EM_OK;
@@ -390,7 +451,7 @@ static int update_impl(em_map* m, const em_cloud* clouds, int32_t n_clouds, cuda
   if (total > 0) {
     const int32_t max_touched = ncell < total ? ncell : (int32_t)total;
     EM_TRY(timed(m, EM_PROF_COUNT, s, [&] { return launch_bin(bd, total, s); }), "k_count");
-    if (m->p.ray_step > 0.f) EM_TRY(timed(m, EM_PROF_RAY, s, [&] { return launch_ray(bd, total, s); }), "k_ray");
+    if (m->p.ray_step > 0.f) EM_TRY(timed(m, EM_PROF_RAY, s, [&] { return launch_ray(bd, total, m->ray_group, s); }), "k_ray");
     EM_TRY(timed(m, EM_PROF_ALLOC, s, [&] { return launch_alloc(bd, 1, ncell, s); }), "k_alloc");
     EM_TRY(timed(m, EM_PROF_SCATTER, s, [&] { return launch_scatter(bd, total, s); }), "k_scatter");
     EM_TRY(timed(m, EM_PROF_FUSE, s, [&] { return launch_fuse(bd, 1, max_touched, m->fuse_group, s); }), "k_fuse");

@@ -1,0 +1,411 @@
+// em_batch.cu -- the batched form: many maps updated by one kernel sequence.
+//
+// Every kernel of the update already works on a list of maps and clouds (the
+// device descriptor), so a batch is the same launch sequence as one em_update
+// with more maps in the descriptor: per-point kernels span all clouds of all
+// maps, per-cell kernels use a 2D grid (y = map).  With EM_BATCH_GRAPH the
+// sequence is captured once per descriptor slot (grids sized from the batch
+// capacities) and replayed by one cudaGraphLaunch.
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include "em.h"
+#include "em_host.h"
+#include "em_internal.cuh"
+
+using namespace em;
+
+namespace {
+
+constexpr int kSlots = 3;
+
+#define EB_TRY(expr, what)                                  \
+  do {                                                      \
+    cudaError_t _e = (expr);                                \
+    if (_e != cudaSuccess) return map_record_error((what), _e); \
+  } while (0)
+
+bool tuning_ok(const em_tuning& t) {
+  const int r = t.ray_group, f = t.fuse_group;
+  return (r == 1 || r == 2 || r == 4 || r == 8 || r == 16 || r == 32) && (f == 4 || f == 8 || f == 16 || f == 32) &&
+         t.big_thresh >= 1;
+}
+
+// what a captured graph depends on besides the slot
+struct GraphKey {
+  em_tuning t;
+  bool ray;
+  uint32_t stencils;
+  bool operator==(const GraphKey& o) const {
+    return t.ray_group == o.t.ray_group && t.fuse_group == o.t.fuse_group && t.big_thresh == o.t.big_thresh &&
+           ray == o.ray && stencils == o.stencils;
+  }
+};
+
+}  // namespace
+
+struct em_batch {
+  int device = 0;
+  int32_t max_maps = 0, max_clouds = 0, max_cells = 0;
+  int64_t max_points = 0;
+  uint32_t flags = 0;
+  float2* zw_sorted = nullptr;
+  size_t desc_bytes = 0;
+  unsigned char* desc_host = nullptr;
+  unsigned char* desc_dev = nullptr;
+  cudaEvent_t ev[kSlots] = {};
+  int slot = 0;
+  em_tuning tune{2, 8, 64};
+  cudaStream_t capture_stream = nullptr;
+  cudaGraphExec_t graph[kSlots] = {};
+  GraphKey graph_key[kSlots] = {};
+  // host scratch for grouping
+  std::vector<int> first_of, order, map_of;
+  std::vector<em_map*> uniq;
+};
+
+namespace {
+
+// The kernel sequence of one update over the descriptor at `bd`.
+cudaError_t launch_sequence(const BatchDev* bd, int64_t grid_points, int32_t grid_maps, int32_t grid_cells,
+                            const GraphKey& k, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  const int32_t touched = grid_cells < grid_points ? grid_cells : (int32_t)grid_points;
+  if (grid_points > 0) {
+    if (e == cudaSuccess) e = launch_bin(bd, grid_points, s);
+    if (e == cudaSuccess && k.ray) e = launch_ray(bd, grid_points, k.t.ray_group, s);
+    if (e == cudaSuccess) e = launch_alloc(bd, grid_maps, grid_cells, s);
+    if (e == cudaSuccess) e = launch_scatter(bd, grid_points, s);
+    if (e == cudaSuccess) e = launch_fuse(bd, grid_maps, touched, k.t.fuse_group, s);
+  }
+  if (e == cudaSuccess) e = launch_clear(bd, grid_maps, grid_cells, s);
+  if (e == cudaSuccess && (k.stencils & EM_F_NORMALS)) e = launch_normals(bd, grid_maps, grid_cells, s);
+  if (e == cudaSuccess && (k.stencils & EM_F_SMOOTH)) e = launch_smooth(bd, grid_maps, grid_cells, s);
+  if (e == cudaSuccess && (k.stencils & EM_F_INPAINT)) e = launch_inpaint(bd, grid_maps, grid_cells, s);
+  return e;
+}
+
+struct Prepared {
+  const BatchDev* bd = nullptr;
+  int slot = -1;
+  int64_t points = 0;
+  int32_t n_maps = 0, cells = 0;
+  GraphKey key{};
+};
+
+// Group the pairs by map, build the descriptor in slot `slot` and upload it.
+int prepare(em_batch* b, em_map* const* maps, const em_cloud* clouds, int32_t count, const em_tuning& tune,
+            cudaStream_t s, Prepared* out) {
+  if (!maps || !clouds || count < 1) return EM_ERR_INVALID_ARG;
+  if (count > b->max_clouds) return EM_ERR_CAPACITY;
+  b->uniq.clear();
+  b->map_of.assign(count, -1);
+  for (int i = 0; i < count; ++i) {
+    const em_cloud& c = clouds[i];
+    if (!maps[i] || c.n < 0 || (c.stride != 3 && c.stride != 4) || (c.n > 0 && !c.points)) return EM_ERR_INVALID_ARG;
+    for (int k = 0; k < 12; ++k)
+      if (!std::isfinite(c.pose[k])) return EM_ERR_INVALID_ARG;
+    if (map_device(maps[i]) != b->device) return EM_ERR_INVALID_ARG;
+    int u = -1;
+    for (size_t j = 0; j < b->uniq.size(); ++j)
+      if (b->uniq[j] == maps[i]) { u = (int)j; break; }
+    if (u < 0) {
+      if ((int)b->uniq.size() >= b->max_maps) return EM_ERR_CAPACITY;
+      if (map_cells(maps[i]) > b->max_cells) return EM_ERR_CAPACITY;
+      u = (int)b->uniq.size();
+      b->uniq.push_back(maps[i]);
+    }
+    b->map_of[i] = u;
+  }
+  const int nm = (int)b->uniq.size();
+  std::vector<int64_t> map_pts(nm, 0);
+  int64_t total = 0;
+  for (int i = 0; i < count; ++i) {
+    map_pts[b->map_of[i]] += clouds[i].n;
+    total += clouds[i].n;
+  }
+  if (total > b->max_points) return EM_ERR_CAPACITY;
+
+  const int slot = b->slot;
+  b->slot = (b->slot + 1) % kSlots;
+  EB_TRY(cudaEventSynchronize(b->ev[slot]), "cudaEventSynchronize");
+  unsigned char* hb = b->desc_host + (size_t)slot * b->desc_bytes;
+  unsigned char* db = b->desc_dev + (size_t)slot * b->desc_bytes;
+  BatchDev* bd = reinterpret_cast<BatchDev*>(hb);
+  MapDev* md = reinterpret_cast<MapDev*>(hb + sizeof(BatchDev));
+  CloudDev* cd = reinterpret_cast<CloudDev*>(hb + sizeof(BatchDev) + (size_t)b->max_maps * sizeof(MapDev));
+  memset(bd, 0, sizeof(BatchDev));
+  GraphKey key{tune, false, 0u};
+  int32_t cells = 0;
+  int64_t rec = 0;
+  for (int u = 0; u < nm; ++u) {
+    md[u] = map_begin_update(b->uniq[u], map_pts[u], tune.big_thresh);
+    md[u].pt_begin = rec;
+    md[u].pt_count = map_pts[u];
+    rec += map_pts[u];
+    key.ray |= md[u].ray_step > 0.f;
+    key.stencils |= map_flags(b->uniq[u]) & (EM_F_NORMALS | EM_F_SMOOTH | EM_F_INPAINT);
+    cells = std::max(cells, map_cells(b->uniq[u]));
+  }
+  // clouds ordered by map (stable), so each map's points are contiguous
+  int ci = 0;
+  int64_t begin = 0;
+  for (int u = 0; u < nm; ++u)
+    for (int i = 0; i < count; ++i) {
+      if (b->map_of[i] != u) continue;
+      CloudDev& c = cd[ci++];
+      memset(&c, 0, sizeof(c));
+      c.pts = clouds[i].points;
+      c.n = clouds[i].n;
+      c.begin = begin;
+      c.stride = clouds[i].stride;
+      c.map = u;
+      for (int r = 0; r < 3; ++r) {
+        for (int k = 0; k < 3; ++k) c.R[r * 3 + k] = clouds[i].pose[r * 4 + k];
+        c.t[r] = clouds[i].pose[r * 4 + 3];
+      }
+      begin += clouds[i].n;
+    }
+  bd->n_maps = nm;
+  bd->n_clouds = count;
+  bd->n_points = total;
+  bd->maps = reinterpret_cast<const MapDev*>(db + sizeof(BatchDev));
+  bd->clouds = reinterpret_cast<const CloudDev*>(db + sizeof(BatchDev) + (size_t)b->max_maps * sizeof(MapDev));
+  bd->zw_sorted = b->zw_sorted;
+  // upload header + maps, and the clouds at their fixed offset
+  cudaError_t e = cudaMemcpyAsync(db, hb, sizeof(BatchDev) + (size_t)nm * sizeof(MapDev), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(db + sizeof(BatchDev) + (size_t)b->max_maps * sizeof(MapDev), cd,
+                        (size_t)count * sizeof(CloudDev), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) {
+    for (int u = 0; u < nm; ++u) map_undo_update(b->uniq[u], map_pts[u]);
+    return map_record_error("upload batch descriptor", e);
+  }
+  out->bd = reinterpret_cast<const BatchDev*>(db);
+  out->slot = slot;
+  out->points = total;
+  out->n_maps = nm;
+  out->cells = cells;
+  out->key = key;
+  return EM_OK;
+}
+
+void finish(em_batch* b, const Prepared& p, cudaStream_t s) {
+  for (size_t u = 0; u < b->uniq.size(); ++u) map_end_update(b->uniq[u], s, 0);
+  cudaEventRecord(b->ev[p.slot], s);
+}
+
+int run_graph(em_batch* b, const Prepared& p, cudaStream_t s) {
+  if (!b->graph[p.slot] || !(b->graph_key[p.slot] == p.key)) {
+    if (b->graph[p.slot]) {
+      cudaGraphExecDestroy(b->graph[p.slot]);
+      b->graph[p.slot] = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    EB_TRY(cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    cudaError_t le = launch_sequence(p.bd, b->max_points, b->max_maps, b->max_cells, p.key, b->capture_stream);
+    cudaError_t ce = cudaStreamEndCapture(b->capture_stream, &g);
+    if (le != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return map_record_error("capture launches", le);
+    }
+    EB_TRY(ce, "end capture");
+    cudaGraphExec_t ex = nullptr;
+    cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    EB_TRY(ie, "cudaGraphInstantiate");
+    b->graph[p.slot] = ex;
+    b->graph_key[p.slot] = p.key;
+  }
+  EB_TRY(cudaGraphLaunch(b->graph[p.slot], s), "cudaGraphLaunch");
+  return EM_OK;
+}
+
+int set_dev(int dev) {
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess || cur != dev) EB_TRY(cudaSetDevice(dev), "cudaSetDevice");
+  return EM_OK;
+}
+
+void release(em_batch* b) {
+  for (int i = 0; i < kSlots; ++i) {
+    if (b->graph[i]) cudaGraphExecDestroy(b->graph[i]);
+    if (b->ev[i]) cudaEventDestroy(b->ev[i]);
+  }
+  if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+  cudaFree(b->zw_sorted);
+  cudaFree(b->desc_dev);
+  cudaFreeHost(b->desc_host);
+  delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+int em_batch_create(int device, int32_t max_maps, int32_t max_clouds, int64_t max_points, int32_t max_cells,
+                    uint32_t flags, em_batch** out) {
+  if (!out) return EM_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (max_maps < 1 || max_maps > 65535 || max_clouds < 1 || max_points < 0 || max_points > (int64_t(1) << 31) - 1 ||
+      max_cells < 1 || max_cells > (1 << 26) || (flags & ~EM_BATCH_GRAPH))
+    return EM_ERR_INVALID_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return EM_ERR_INVALID_ARG;
+  int rc = set_dev(device);
+  if (rc) return rc;
+  em_batch* b = new (std::nothrow) em_batch();
+  if (!b) return EM_ERR_OOM;
+  b->device = device;
+  b->max_maps = max_maps;
+  b->max_clouds = max_clouds;
+  b->max_points = max_points;
+  b->max_cells = max_cells;
+  b->flags = flags;
+  b->desc_bytes = (sizeof(BatchDev) + (size_t)max_maps * sizeof(MapDev) + (size_t)max_clouds * sizeof(CloudDev) + 255) &
+                  ~size_t(255);
+  cudaError_t e = cudaMalloc((void**)&b->zw_sorted, (size_t)(max_points > 0 ? max_points : 1) * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->desc_dev, b->desc_bytes * kSlots);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&b->desc_host, b->desc_bytes * kSlots);
+  for (int i = 0; i < kSlots && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&b->ev[i], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    release(b);
+    return map_record_error("em_batch_create", e);
+  }
+  *out = b;
+  return EM_OK;
+}
+
+int em_batch_destroy(em_batch* b) {
+  if (!b) return EM_OK;
+  set_dev(b->device);
+  cudaDeviceSynchronize();
+  release(b);
+  return EM_OK;
+}
+
+int em_update_batch(em_batch* b, em_map* const* maps, const em_cloud* clouds, int32_t count, em_stream_t stream) {
+  if (!b) return EM_ERR_INVALID_ARG;
+  int rc = set_dev(b->device);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  Prepared p;
+  rc = prepare(b, maps, clouds, count, b->tune, s, &p);
+  if (rc) return rc;
+  if (b->flags & EM_BATCH_GRAPH) {
+    rc = run_graph(b, p, s);
+  } else {
+    cudaError_t e = launch_sequence(p.bd, p.points, p.n_maps, p.cells, p.key, s);
+    rc = e == cudaSuccess ? EM_OK : map_record_error("batch launches", e);
+  }
+  finish(b, p, s);
+  return rc;
+}
+
+int em_batch_set_tuning(em_batch* b, const em_tuning* t) {
+  if (!b || !t || !tuning_ok(*t)) return EM_ERR_INVALID_ARG;
+  b->tune = *t;
+  return EM_OK;
+}
+
+int em_batch_get_tuning(const em_batch* b, em_tuning* t) {
+  if (!b || !t) return EM_ERR_INVALID_ARG;
+  *t = b->tune;
+  return EM_OK;
+}
+
+int em_batch_autotune(em_batch* b, em_map* const* maps, const em_cloud* clouds, int32_t count, em_stream_t stream,
+                      int32_t reps, em_tuning* out) {
+  if (!b || !maps || !clouds || count < 1) return EM_ERR_INVALID_ARG;
+  int rc = set_dev(b->device);
+  if (rc) return rc;
+  if (reps < 1) reps = 3;
+  cudaStream_t s = (cudaStream_t)stream;
+  // scratch copies of the distinct maps
+  std::vector<em_map*> uniq, clones;
+  std::vector<em_map*> cmaps(count);
+  for (int i = 0; i < count; ++i) {
+    if (!maps[i]) return EM_ERR_INVALID_ARG;
+    size_t j = 0;
+    while (j < uniq.size() && uniq[j] != maps[i]) ++j;
+    if (j == uniq.size()) {
+      em_params p = map_params(maps[i]);
+      p.flags &= ~(uint32_t)EM_F_TRACE;
+      em_map* c = nullptr;
+      rc = em_create(&p, b->device, &c);
+      if (rc) {
+        for (em_map* x : clones) em_destroy(x);
+        return rc;
+      }
+      uniq.push_back(maps[i]);
+      clones.push_back(c);
+    }
+    cmaps[i] = clones[j];
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  auto time_one = [&](const em_tuning& t, float* ms_out) -> int {
+    std::vector<float> ms;
+    for (int r = 0; r < reps + 1; ++r) {
+      for (size_t j = 0; j < uniq.size(); ++j) {
+        int c = map_copy_state(clones[j], uniq[j], s);
+        if (c) return c;
+      }
+      Prepared p;
+      int c = prepare(b, cmaps.data(), clouds, count, t, s, &p);
+      if (c) return c;
+      cudaEventRecord(e0, s);
+      cudaError_t le = launch_sequence(p.bd, p.points, p.n_maps, p.cells, p.key, s);
+      cudaEventRecord(e1, s);
+      finish(b, p, s);
+      if (le != cudaSuccess) return map_record_error("autotune launches", le);
+      if (cudaEventSynchronize(e1) != cudaSuccess) return EM_ERR_CUDA;
+      float x = 0.f;
+      cudaEventElapsedTime(&x, e0, e1);
+      if (r > 0) ms.push_back(x);  // the first run warms up
+    }
+    std::sort(ms.begin(), ms.end());
+    *ms_out = ms[ms.size() / 2];
+    return EM_OK;
+  };
+  em_tuning best = b->tune;
+  float best_ms = 0.f;
+  rc = time_one(best, &best_ms);
+  const int ray_c[] = {1, 2, 4, 8, 16};
+  const int fuse_c[] = {4, 8, 16, 32};
+  const int big_c[] = {32, 64, 128, 256};
+  for (int pass = 0; pass < 3 && rc == EM_OK; ++pass) {
+    const int* cand = pass == 0 ? ray_c : pass == 1 ? fuse_c : big_c;
+    const int nc = pass == 0 ? 5 : 4;
+    for (int i = 0; i < nc && rc == EM_OK; ++i) {
+      em_tuning t = best;
+      if (pass == 0) t.ray_group = cand[i];
+      if (pass == 1) t.fuse_group = cand[i];
+      if (pass == 2) t.big_thresh = cand[i];
+      if (t.ray_group == best.ray_group && t.fuse_group == best.fuse_group && t.big_thresh == best.big_thresh) continue;
+      float ms = 0.f;
+      rc = time_one(t, &ms);
+      if (rc == EM_OK && ms < best_ms) {
+        best_ms = ms;
+        best = t;
+      }
+    }
+  }
+  cudaStreamSynchronize(s);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (em_map* x : clones) em_destroy(x);
+  if (rc) return rc;
+  b->tune = best;
+  if (out) *out = best;
+  return EM_OK;
+}
+
+}  // extern "C"

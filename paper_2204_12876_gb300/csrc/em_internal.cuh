@@ -8,8 +8,8 @@
 //
 // Pipeline of one update (Section II-A of the paper: transform, height update
 // and ray casting in the same iteration, then per-cell passes):
-//   k_bin      transform + noise variance + cell binning, per-cell counts,
-//              list of touched cells                          (Section II-C)
+//   k_count    transform + noise variance + cell binning, per-cell counts;
+//              per-cell ray thresholds of the pre-update map   (Section II-C)
 //   k_ray      visibility ray march against the pre-update map (Section II-E)
 //   k_alloc    one segment of the sorted record array per touched cell
 //   k_scatter  records into their cell's segment (counting sort by cell)
@@ -24,8 +24,6 @@
 
 namespace em {
 
-constexpr uint32_t kNoKey = 0xFFFFFFFFu;
-
 // per-map counters (device), in em_stats order
 enum StatIdx {
   kStUpdates = 0, kStIn, kStValid, kStInMap, kStAccepted, kStRejected, kStWall, kStCellsUpdated,
@@ -35,10 +33,12 @@ enum StatIdx {
 // per-map device control block: counters that live across kernels of an update
 struct MapCtl {
   unsigned long long stats[kStCount];
-  int32_t n_touched;   // touched cells this update (reset by k_clear)
+  int32_t n_touched;   // small touched cells this update, front of the touched list (reset by k_clear)
   int32_t seg_cursor;  // records allocated to segments this update (reset by k_clear)
   int32_t err;         // first device-side error code of this map (sticky until read)
-  int32_t pad;
+  int32_t n_big;       // large touched cells, back of the touched list (reset by k_clear)
+  int32_t big_next;    // work-stealing cursor over the large cells (reset by k_clear)
+  int32_t pad[3];
 };
 
 // point status codes (trace)
@@ -55,9 +55,11 @@ struct MapDev {
   float* smooth;    // may be null
   float* inpaint;   // may be null
   uint32_t* mark;   // visibility marks, one bit per physical cell, zero between updates
+  float* thr;       // per physical cell: h - sqrt(var_eff) of the pre-update map, -inf if empty
   int32_t* cnt;     // per physical cell point count, zero between updates
   int32_t* cell_base;  // per physical cell: start of its segment (valid for touched cells)
-  int32_t* touched;    // touched physical cells this update (capacity W*H)
+  int32_t* touched;    // touched physical cells this update (capacity W*H): cells with at most
+                       // big_thresh records from the front, larger ones from the back
   int32_t* seg_base;   // per touched entry: segment start (absolute record index)
   int32_t* seg_len;    // per touched entry: segment length
   MapCtl* ctl;
@@ -70,7 +72,7 @@ struct MapDev {
   float a0, a1, a2, var_min, min_range, max_range, k, v_out, sigma_t2, ray_step, alpha_n;
   int32_t wall, min_age;
   uint32_t flags;
-  int32_t pad;
+  int32_t big_thresh;  // segments longer than this are fused by a whole block
 };
 
 struct CloudDev {
@@ -88,18 +90,19 @@ struct BatchDev {
   int64_t n_points;
   const MapDev* maps;
   const CloudDev* clouds;
-  uint32_t* key;       // per point: physical cell or kNoKey
-  float2* zw;          // per point: (z, sigma_p^2)
-  float2* zw_sorted;   // records grouped by cell
+  float2* zw_sorted;   // records (z, sigma_p^2) grouped by cell
   int32_t* idx_sorted; // original point index per sorted record (trace only, else null)
   int32_t* tr_ix;      // trace (null unless EM_F_TRACE)
   int32_t* tr_iy;
   uint8_t* tr_status;
 };
 
+// number of SMs of the current device (cached)
+int sm_count();
+
 // ---- launchers (each returns cudaGetLastError() of its launches)
 cudaError_t launch_bin(const BatchDev* b, int64_t n_points, cudaStream_t s);
-cudaError_t launch_ray(const BatchDev* b, int64_t n_points, cudaStream_t s);
+cudaError_t launch_ray(const BatchDev* b, int64_t n_points, int group, cudaStream_t s);
 cudaError_t launch_alloc(const BatchDev* b, int32_t n_maps, int32_t max_cells, cudaStream_t s);
 cudaError_t launch_scatter(const BatchDev* b, int64_t n_points, cudaStream_t s);
 cudaError_t launch_fuse(const BatchDev* b, int32_t n_maps, int32_t max_cells, int group, cudaStream_t s);
@@ -131,7 +134,7 @@ __device__ __forceinline__ int32_t phys_index(const MapDev& m, int32_t ix, int32
 
 // effective variance of a cell at update t_now (lazy time variance)
 __device__ __forceinline__ float var_eff(const MapDev& m, float var, int32_t t_last) {
-  return var + m.sigma_t2 * (float)(m.t_now - t_last);
+  return __fmaf_rn(m.sigma_t2, (float)(m.t_now - t_last), var);
 }
 
 // index of the cloud that holds batch point g (clouds sorted by begin)

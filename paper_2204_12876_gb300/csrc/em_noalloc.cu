@@ -10,7 +10,7 @@
 // memory in one file-scope __device__ array of fixed size.
 //
 // Limits: at most kMaxCells cells per map and kMaxPoints points per update
-// (about 4 MiB of scratch, held by every GPU that loads the library until the
+// (about 4.5 MiB of scratch, held by every GPU that loads the library until the
 // process exits).  Every call shares the array and it keeps the last call's
 // contents; the call clears what must start at zero.  Calls whose GPU work
 // overlaps (e.g. on two streams) race on the array.
@@ -39,7 +39,8 @@ constexpr size_t kOffDesc = 0;
 constexpr size_t kOffCtl = kOffDesc + up256(sizeof(BatchDev) + sizeof(MapDev) + kMaxCloudsNA * sizeof(CloudDev));
 constexpr size_t kOffMark = kOffCtl + up256(sizeof(MapCtl));
 constexpr size_t kOffCnt = kOffMark + up256(((size_t)kMaxCells + 31) / 32 * sizeof(uint32_t));
-constexpr size_t kOffCellBase = kOffCnt + up256((size_t)kMaxCells * sizeof(int32_t));
+constexpr size_t kOffThr = kOffCnt + up256((size_t)kMaxCells * sizeof(int32_t));
+constexpr size_t kOffCellBase = kOffThr + up256((size_t)kMaxCells * sizeof(float));
 constexpr size_t kOffTouched = kOffCellBase + up256((size_t)kMaxCells * sizeof(int32_t));
 constexpr size_t kOffSegBase = kOffTouched + up256((size_t)kMaxCells * sizeof(int32_t));
 constexpr size_t kOffSegLen = kOffSegBase + up256((size_t)kMaxCells * sizeof(int32_t));
@@ -133,6 +134,7 @@ extern "C" int em_update_noalloc(const em_params* params, int64_t shift_x, int64
   m->ny = const_cast<float*>(ny);
   m->nz = const_cast<float*>(nz);
   m->mark = reinterpret_cast<uint32_t*>(base + kOffMark);
+  m->thr = reinterpret_cast<float*>(base + kOffThr);
   m->cnt = reinterpret_cast<int32_t*>(base + kOffCnt);
   m->cell_base = reinterpret_cast<int32_t*>(base + kOffCellBase);
   m->touched = reinterpret_cast<int32_t*>(base + kOffTouched);
@@ -153,6 +155,7 @@ extern "C" int em_update_noalloc(const em_params* params, int64_t shift_x, int64
   m->v_out = params->outlier_variance; m->sigma_t2 = params->time_variance; m->ray_step = params->ray_step;
   m->alpha_n = params->cleanup_normal_thresh; m->wall = params->wall_num_thresh;
   m->min_age = params->cleanup_min_age;
+  m->big_thresh = 64;
   int64_t begin = 0;
   for (int i = 0; i < n_clouds; ++i) {
     cd[i].pts = clouds[i].points;
@@ -186,7 +189,7 @@ extern "C" int em_update_noalloc(const em_params* params, int64_t shift_x, int64
   if (total > 0) {
     const int32_t max_touched = ncell < total ? ncell : (int32_t)total;
     if (e == cudaSuccess) e = launch_bin(bd, total, s);
-    if (e == cudaSuccess && params->ray_step > 0.f) e = launch_ray(bd, total, s);
+    if (e == cudaSuccess && params->ray_step > 0.f) e = launch_ray(bd, total, 2, s);
     if (e == cudaSuccess) e = launch_alloc(bd, 1, ncell, s);
     if (e == cudaSuccess) e = launch_scatter(bd, total, s);
     if (e == cudaSuccess) e = launch_fuse(bd, 1, max_touched, 8, s);

@@ -48,6 +48,49 @@ __device__ __forceinline__ bool in_map(const MapDev& m, int32_t ix, int32_t iy) 
   return ix >= 0 && iy >= 0 && ix < m.W && iy < m.H;
 }
 
+// Per-thread statistics counters of one map.  They are flushed with one atomic
+// per block and counter when the whole block saw a single map (the usual
+// case), else per thread: many threads adding to one address serialise on a
+// single L2 slice.
+struct MapCounters {
+  int map = -1;
+  unsigned long long v[3] = {0, 0, 0};
+};
+
+__device__ __forceinline__ void flush_counters(const BatchDev& b, MapCounters& mc, const int* idx, int n) {
+  __shared__ int s_map;
+  __shared__ unsigned long long s_sum[3];
+  if (threadIdx.x == 0) s_map = mc.map;
+  if (threadIdx.x < 3) s_sum[threadIdx.x] = 0;
+  __syncthreads();
+  const bool uniform = __syncthreads_and(mc.map == s_map || mc.map < 0);
+  if (uniform) {
+    for (int k = 0; k < n; ++k) {
+      unsigned long long v = mc.v[k];
+      for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if ((threadIdx.x & 31) == 0 && v) atomicAdd(&s_sum[k], v);
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < n && s_map >= 0 && s_sum[threadIdx.x])
+      atomicAdd(&b.maps[s_map].ctl->stats[idx[threadIdx.x]], s_sum[threadIdx.x]);
+  } else if (mc.map >= 0) {
+    for (int k = 0; k < n; ++k)
+      if (mc.v[k]) atomicAdd(&b.maps[mc.map].ctl->stats[idx[k]], mc.v[k]);
+  }
+}
+
+__device__ __forceinline__ void add_counter(const BatchDev& b, MapCounters& mc, int map, const int* idx, int n,
+                                            const unsigned long long* inc) {
+  if (map != mc.map) {
+    if (mc.map >= 0)
+      for (int k = 0; k < n; ++k)
+        if (mc.v[k]) atomicAdd(&b.maps[mc.map].ctl->stats[idx[k]], mc.v[k]);
+    mc.map = map;
+    for (int k = 0; k < n; ++k) mc.v[k] = 0;
+  }
+  for (int k = 0; k < n; ++k) mc.v[k] += inc[k];
+}
+
 // Load point g of cloud c (stride 3 or 4) with scalar loads.
 __device__ __forceinline__ void load_point(const CloudDev& c, int64_t i, float& px, float& py, float& pz) {
   const float* p = c.pts + i * c.stride;

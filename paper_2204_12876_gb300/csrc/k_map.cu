@@ -11,6 +11,7 @@
 // [0, H) does not exist (the ring never wraps a stencil).
 #include <math.h>
 
+#include "em.h"
 #include "em_internal.cuh"
 
 namespace em {
@@ -26,7 +27,7 @@ __global__ void __launch_bounds__(kMapThreads) k_normals(const BatchDev* __restr
   const BatchDev& b = *bp;
   if ((int)blockIdx.y >= b.n_maps) return;
   const MapDev& m = b.maps[blockIdx.y];
-  if (!m.nx) return;
+  if (!m.nx || !(m.flags & EM_F_NORMALS)) return;  // a batch may mix maps with and without normals
   const int32_t ncell = m.W * m.H;
   for (int32_t c = blockIdx.x * kMapThreads + threadIdx.x; c < ncell; c += gridDim.x * kMapThreads) {
     const int32_t lx = c % m.W, ly = c / m.W;

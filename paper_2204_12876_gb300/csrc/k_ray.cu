@@ -1,15 +1,17 @@
 // k_ray.cu -- visibility cleanup by ray casting (Section II-E of the paper).
 //
-// k_ray: one thread per valid point.  The ray from the sensor origin o (the
-// pose translation) to the point is sampled at s_k = o + (k step / d) (R p_s)
-// for k = 1, 2, ... while k step < d.  A sample inside the map, outside the
-// point's own cell, in a cell holding an estimate, below that cell's
-// h - sqrt(sigma_m^2) (Eq. 3), and -- when alpha_n > 0 -- with
-// |rhat . n| > alpha_n for the cell's previous normal (Eq. 4; a NaN normal
-// counts as (0, 0, 1)) marks the cell in a bitmask (atomicOr: idempotent, so
-// the marks do not depend on thread order).  The march only visits the k
-// whose samples can lie inside the map's box.  It runs before the fusion, so
-// it sees the pre-update map.
+// k_ray: a group of G lanes per valid point.  The ray from the sensor origin o
+// (the pose translation) to the point is sampled at
+// s_k = o + (k step / d) (R p_s) for k = 1, 2, ... while k step < d; lane j of
+// the group takes k = k_lo + j, k_lo + j + G, ..., so the group keeps G
+// independent gathers in flight.  A sample inside the map, outside the point's
+// own cell, below the cell's threshold h - sqrt(sigma_m^2) of the pre-update
+// map (Eq. 3; the threshold layer is -inf for empty cells) and -- when
+// alpha_n > 0 -- with |rhat . n| > alpha_n for the cell's previous normal
+// (Eq. 4; a NaN normal counts as (0, 0, 1)) marks the cell in a bitmask
+// (atomicOr: idempotent, so the marks do not depend on thread order).  Only
+// the k whose samples can lie inside the map's box are visited.  The kernel
+// runs before the fusion, so it sees the pre-update map.
 //
 // k_clear: after the fusion, every marked cell that holds an estimate and was
 // last written at least max(1, cleanup_min_age) updates ago is removed; the
@@ -19,17 +21,10 @@
 namespace em {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kRayThreads = 128;
+constexpr int kRayThreads = 256;
 
-__device__ __forceinline__ void block_range_r(int64_t n, int64_t& beg, int64_t& end) {
-  int64_t per = (n + gridDim.x - 1) / gridDim.x;
-  per = (per + 31) & ~int64_t(31);
-  beg = (int64_t)blockIdx.x * per;
-  end = beg + per < n ? beg + per : n;
-}
-
-// parameter interval [lo, hi] (metres along the ray) where the xy track of
-// o + (s/d) v stays inside [a0, a1): returns false when it never does
+// Narrow [lo, hi] (metres along the ray) to where the track o + (s/d) v stays
+// inside [a0, a1); false when it never does.
 __device__ __forceinline__ bool slab(float o, float v, float d, float a0, float a1, float& lo, float& hi) {
   if (v == 0.f) return o >= a0 && o < a1;
   const float sa = (a0 - o) * d / v;
@@ -39,13 +34,16 @@ __device__ __forceinline__ bool slab(float o, float v, float d, float a0, float 
   return true;
 }
 
+template <int G>
 __global__ void __launch_bounds__(kRayThreads) k_ray(const BatchDev* __restrict__ bp) {
   const BatchDev& b = *bp;
-  int64_t beg, end;
-  block_range_r(b.n_points, beg, end);
+  const int gl = (threadIdx.x & 31) % G;
+  const int64_t group = ((int64_t)blockIdx.x * kRayThreads + threadIdx.x) / G;
+  const int64_t n_groups = (int64_t)gridDim.x * kRayThreads / G;
+  MapCounters mc;
+  const int stat_idx[1] = {kStRaySamples};
   unsigned long long samples = 0;
-  int cur_map = -1;
-  for (int64_t g = beg + threadIdx.x; g < end; g += kRayThreads) {
+  for (int64_t g = group; g < b.n_points; g += n_groups) {
     const int ci = find_cloud(b.clouds, b.n_clouds, g);
     const CloudDev& c = b.clouds[ci];
     const MapDev& m = b.maps[c.map];
@@ -54,10 +52,10 @@ __global__ void __launch_bounds__(kRayThreads) k_ray(const BatchDev* __restrict_
     load_point(c, g - c.begin, px, py, pz);
     const PointGeom pg = point_geom(m, c, px, py, pz);
     if (!pg.in_range || !(pg.d > 0.f)) continue;
-    if (c.map != cur_map) {
-      if (cur_map >= 0 && samples) atomicAdd(&b.maps[cur_map].ctl->stats[kStRaySamples], samples);
+    if (c.map != mc.map) {  // fold this map's samples in, then switch maps
+      if (mc.map >= 0) add_counter(b, mc, mc.map, stat_idx, 1, &samples);
       samples = 0;
-      cur_map = c.map;
+      add_counter(b, mc, c.map, stat_idx, 1, &samples);
     }
     // clip the sample range to the map box (conservative by 1 mm + 1 step)
     float lo = 0.f, hi = pg.d;
@@ -66,53 +64,42 @@ __global__ void __launch_bounds__(kRayThreads) k_ray(const BatchDev* __restrict_
     if (!slab(c.t[1], pg.vy, pg.d, m.y0, m.y0 + ext_y, lo, hi)) continue;
     if (lo > hi + 1e-3f) continue;
     const float step = m.ray_step;
-    float kl = floorf((lo - 1e-3f) / step) - 1.f;
-    float kh = ceilf((hi + 1e-3f) / step) + 1.f;
+    const float kl = floorf((lo - 1e-3f) / step) - 1.f;
+    const float kh = ceilf((hi + 1e-3f) / step) + 1.f;
     const int32_t k_lo = kl < 1.f ? 1 : (int32_t)kl;
     const int32_t k_hi = kh > 1.0e9f ? 1000000000 : (int32_t)kh;
     const float cstep = __fdiv_rn(step, pg.d);  // f_k = k * step / d
     const float inv_res = __frcp_rn(m.res);
-    const float rx = __fdiv_rn(pg.vx, pg.d), ry = __fdiv_rn(pg.vy, pg.d), rz = __fdiv_rn(pg.vz, pg.d);
     const bool guard = m.alpha_n > 0.f;
-    int32_t prev = -1;
-    float prev_thr = 0.f;
-    bool prev_ok = false, prev_marked = false;
-    for (int32_t k = k_lo; k <= k_hi; ++k) {
+    for (int32_t k = k_lo + gl; k <= k_hi; k += G) {
       const float len = __fmul_rn((float)k, step);
       if (!(len < pg.d)) break;
       const float f = __fmul_rn((float)k, cstep);
       const float sx = __fmaf_rn(f, pg.vx, c.t[0]);
       const float sy = __fmaf_rn(f, pg.vy, c.t[1]);
-      const float sz = __fmaf_rn(f, pg.vz, c.t[2]);
       const int32_t cx = clamp_floor(__fmul_rn(__fsub_rn(sx, m.x0), inv_res));
       const int32_t cy = clamp_floor(__fmul_rn(__fsub_rn(sy, m.y0), inv_res));
       if (!in_map(m, cx, cy)) continue;
       ++samples;
       if (cx == pg.ix && cy == pg.iy) continue;
       const int32_t p = phys_index(m, cx, cy);
-      if (p != prev) {
-        prev = p;
-        prev_marked = false;
-        const float var = m.var[p];
-        prev_ok = isfinite(var);
-        if (prev_ok) {
-          const float ve = m.sigma_t2 != 0.f ? var_eff(m, var, m.t_last[p]) : var;
-          prev_thr = __fsub_rn(m.h[p], __fsqrt_rn(ve));
-          if (guard) {
-            float n0 = m.nx[p], n1 = m.ny[p], n2 = m.nz[p];
-            if (!(isfinite(n0) && isfinite(n1) && isfinite(n2))) { n0 = 0.f; n1 = 0.f; n2 = 1.f; }
-            const float dot = fabsf(__fmaf_rn(rx, n0, __fmaf_rn(ry, n1, __fmul_rn(rz, n2))));
-            prev_ok = dot > m.alpha_n;
-          }
-        }
+      const float sz = __fmaf_rn(f, pg.vz, c.t[2]);
+      if (!(sz < __ldg(m.thr + p))) continue;
+      if (guard) {
+        float n0 = m.nx[p], n1 = m.ny[p], n2 = m.nz[p];
+        if (!(isfinite(n0) && isfinite(n1) && isfinite(n2))) { n0 = 0.f; n1 = 0.f; n2 = 1.f; }
+        const float rx = __fdiv_rn(pg.vx, pg.d), ry = __fdiv_rn(pg.vy, pg.d), rz = __fdiv_rn(pg.vz, pg.d);
+        const float dot = fabsf(__fmaf_rn(rx, n0, __fmaf_rn(ry, n1, __fmul_rn(rz, n2))));
+        if (!(dot > m.alpha_n)) continue;
       }
-      if (prev_ok && !prev_marked && sz < prev_thr) {
-        atomicOr(&m.mark[p >> 5], 1u << (p & 31));
-        prev_marked = true;
-      }
+      // many rays graze the same surface cells: skip the atomic when the bit is
+      // already set (marks are only ever set during this kernel)
+      const uint32_t bit = 1u << (p & 31);
+      if (!(*(volatile uint32_t*)(m.mark + (p >> 5)) & bit)) atomicOr(&m.mark[p >> 5], bit);
     }
   }
-  if (cur_map >= 0 && samples) atomicAdd(&b.maps[cur_map].ctl->stats[kStRaySamples], samples);
+  if (mc.map >= 0) add_counter(b, mc, mc.map, stat_idx, 1, &samples);
+  flush_counters(b, mc, stat_idx, 1);
 }
 
 constexpr int kClearThreads = 256;
@@ -145,20 +132,28 @@ __global__ void __launch_bounds__(kClearThreads) k_clear(const BatchDev* __restr
   if ((threadIdx.x & 31) == 0 && cleared) atomicAdd(&m.ctl->stats[kStCleared], cleared);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     m.ctl->n_touched = 0;
+    m.ctl->n_big = 0;
+    m.ctl->big_next = 0;
     m.ctl->seg_cursor = 0;
     atomicAdd(&m.ctl->stats[kStUpdates], 1ull);
   }
 }
 
-cudaError_t launch_ray(const BatchDev* b, int64_t n_points, cudaStream_t s) {
+cudaError_t launch_ray(const BatchDev* b, int64_t n_points, int group, cudaStream_t s) {
   if (n_points <= 0) return cudaSuccess;
-  int dev = 0, sms = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int64_t want = (n_points + kRayThreads - 1) / kRayThreads;
-  int64_t cap = (int64_t)sms * 16;
-  int grid = (int)(want < cap ? want : cap);
-  k_ray<<<grid < 1 ? 1 : grid, kRayThreads, 0, s>>>(b);
+  const int g = (group == 1 || group == 2 || group == 4 || group == 8 || group == 16 || group == 32) ? group : 4;
+  const int64_t want = (n_points * g + kRayThreads - 1) / kRayThreads;
+  const int64_t cap = (int64_t)sm_count() * 16;
+  const int grid = (int)(want < cap ? want : cap);
+  switch (g) {
+    case 1: k_ray<1><<<grid, kRayThreads, 0, s>>>(b); break;
+    case 2: k_ray<2><<<grid, kRayThreads, 0, s>>>(b); break;
+    case 4: k_ray<4><<<grid, kRayThreads, 0, s>>>(b); break;
+    case 8: k_ray<8><<<grid, kRayThreads, 0, s>>>(b); break;
+    case 32: k_ray<32><<<grid, kRayThreads, 0, s>>>(b); break;
+    case 16: k_ray<16><<<grid, kRayThreads, 0, s>>>(b); break;
+    default: k_ray<4><<<grid, kRayThreads, 0, s>>>(b); break;
+  }
   return cudaGetLastError();
 }
 

@@ -1,9 +1,13 @@
 // k_sort.cu -- grouping of points by cell: a counting sort keyed by the
 // physical cell index (one radix digit spanning the whole key).
 //
-//   k_count    per point: transform + bin, warp-aggregated per-cell counts
+//   k_count    per point: transform + bin, warp-aggregated per-cell counts;
+//              then per cell: the ray-march threshold h - sqrt(var_eff) of the
+//              pre-update map (one 4-byte gather per ray sample later)
 //   k_alloc    per map, tiles of cells: block scans of the counts give every
 //              touched cell a segment [base, base + count) of the record array
+//              and a slot in the touched list (cells with more than big_thresh
+//              records from the back, for whole-block fusion)
 //   k_scatter  per point: transform + bin again, claim a slot in the cell's
 //              segment, write the record (z, sigma_p^2)
 //
@@ -16,47 +20,6 @@ namespace em {
 
 constexpr int kPointThreads = 256;
 constexpr unsigned kFull = 0xffffffffu;
-
-// Per-thread counters of one map, flushed with one atomic per block when the
-// whole block saw a single map, else per thread.
-struct MapCounters {
-  int map = -1;
-  unsigned long long v[3] = {0, 0, 0};
-};
-
-__device__ void flush_counters(const BatchDev& b, MapCounters& mc, const int* idx, int n) {
-  __shared__ int s_map;
-  __shared__ unsigned long long s_sum[3];
-  if (threadIdx.x == 0) s_map = mc.map;
-  if (threadIdx.x < 3) s_sum[threadIdx.x] = 0;
-  __syncthreads();
-  bool uniform = __syncthreads_and(mc.map == s_map || mc.map < 0);
-  if (uniform) {
-    for (int k = 0; k < n; ++k) {
-      unsigned long long v = mc.v[k];
-      for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-      if ((threadIdx.x & 31) == 0 && v) atomicAdd(&s_sum[k], v);
-    }
-    __syncthreads();
-    if (threadIdx.x < n && s_map >= 0 && s_sum[threadIdx.x])
-      atomicAdd(&b.maps[s_map].ctl->stats[idx[threadIdx.x]], s_sum[threadIdx.x]);
-  } else if (mc.map >= 0) {
-    for (int k = 0; k < n; ++k)
-      if (mc.v[k]) atomicAdd(&b.maps[mc.map].ctl->stats[idx[k]], mc.v[k]);
-  }
-}
-
-__device__ __forceinline__ void add_counter(const BatchDev& b, MapCounters& mc, int map, const int* idx, int n,
-                                            const unsigned long long* inc) {
-  if (map != mc.map) {
-    if (mc.map >= 0)
-      for (int k = 0; k < n; ++k)
-        if (mc.v[k]) atomicAdd(&b.maps[mc.map].ctl->stats[idx[k]], mc.v[k]);
-    mc.map = map;
-    for (int k = 0; k < n; ++k) mc.v[k] = 0;
-  }
-  for (int k = 0; k < n; ++k) mc.v[k] += inc[k];
-}
 
 // Block-contiguous partition of the point space into chunks of whole warps.
 __device__ __forceinline__ void block_range(int64_t n, int64_t& beg, int64_t& end) {
@@ -138,6 +101,20 @@ __global__ void __launch_bounds__(kPointThreads) k_count(const BatchDev* __restr
     if (inm && lane == __ffs(peers) - 1) atomicAdd(&m.cnt[key], __popc(peers));
   }
   flush_counters(b, mc, idx, 2);
+  // ray thresholds of the pre-update map, every cell of every map (Eq. 3)
+  const int64_t tid = (int64_t)blockIdx.x * kPointThreads + threadIdx.x;
+  const int64_t nthreads = (int64_t)gridDim.x * kPointThreads;
+  for (int mi = 0; mi < b.n_maps; ++mi) {
+    const MapDev& m = b.maps[mi];
+    if (m.ray_step <= 0.f) continue;
+    const int32_t ncell = m.W * m.H;
+    for (int64_t p = tid; p < ncell; p += nthreads) {
+      const float var = m.var[p];
+      float t = __int_as_float(0xff800000);  // -inf: an empty cell is never penetrated
+      if (isfinite(var)) t = __fsub_rn(m.h[p], __fsqrt_rn(var_eff(m, var, m.t_last[p])));
+      m.thr[p] = t;
+    }
+  }
 }
 
 // One block per tile of 1024 physical cells of one map (blockIdx.y = map).
@@ -172,7 +149,7 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* warp_tot, int& t
 
 __global__ void __launch_bounds__(kAllocThreads) k_alloc(const BatchDev* __restrict__ bp) {
   __shared__ int warp_tot[33];
-  __shared__ int s_base[2];
+  __shared__ int s_base[3];
   const BatchDev& b = *bp;
   if ((int)blockIdx.y >= b.n_maps) return;
   const MapDev& m = b.maps[blockIdx.y];
@@ -180,33 +157,37 @@ __global__ void __launch_bounds__(kAllocThreads) k_alloc(const BatchDev* __restr
   const int tile = kAllocThreads * kAllocPer;
   for (int32_t t0 = blockIdx.x * tile; t0 < ncell; t0 += gridDim.x * tile) {
     int c[kAllocPer];
-    int sum = 0, nt = 0;
+    int sum = 0, ns = 0, nb = 0;
     const int32_t first = t0 + threadIdx.x * kAllocPer;
 #pragma unroll
     for (int k = 0; k < kAllocPer; ++k) {
       c[k] = (first + k < ncell) ? m.cnt[first + k] : 0;
       sum += c[k];
-      nt += c[k] > 0;
+      ns += c[k] > 0 && c[k] <= m.big_thresh;
+      nb += c[k] > m.big_thresh;
     }
-    int tot_c, tot_t;
-    int off_c = block_exclusive_scan(sum, warp_tot, tot_c);
-    int off_t = block_exclusive_scan(nt, warp_tot, tot_t);
+    int tot_c, tot_s, tot_b;
+    const int off_c = block_exclusive_scan(sum, warp_tot, tot_c);
+    const int off_s = block_exclusive_scan(ns, warp_tot, tot_s);
+    const int off_b = block_exclusive_scan(nb, warp_tot, tot_b);
     if (threadIdx.x == 0) {
       s_base[0] = tot_c ? atomicAdd(&m.ctl->seg_cursor, tot_c) : 0;
-      s_base[1] = tot_t ? atomicAdd(&m.ctl->n_touched, tot_t) : 0;
+      s_base[1] = tot_s ? atomicAdd(&m.ctl->n_touched, tot_s) : 0;
+      s_base[2] = tot_b ? atomicAdd(&m.ctl->n_big, tot_b) : 0;
     }
     __syncthreads();
     int64_t rec = m.pt_begin + s_base[0] + off_c;
-    int32_t slot = s_base[1] + off_t;
+    int32_t small_slot = s_base[1] + off_s;
+    int32_t big_slot = ncell - 1 - (s_base[2] + off_b);  // large cells fill the list from the back
 #pragma unroll
     for (int k = 0; k < kAllocPer; ++k) {
       if (c[k] > 0) {
+        const int32_t slot = c[k] > m.big_thresh ? big_slot-- : small_slot++;
         m.touched[slot] = first + k;
         m.seg_base[slot] = (int32_t)rec;
         m.seg_len[slot] = c[k];
         m.cell_base[first + k] = (int32_t)rec;
         rec += c[k];
-        ++slot;
       }
     }
     __syncthreads();
@@ -250,12 +231,23 @@ __global__ void __launch_bounds__(kPointThreads) k_scatter(const BatchDev* __res
   }
 }
 
-static int point_grid(int64_t n) {
-  int dev = 0, sms = 148;
+int sm_count() {
+  static int cached[64] = {};
+  int dev = 0;
   cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int64_t want = (n + kPointThreads * 4 - 1) / (kPointThreads * 4);
-  int64_t cap = (int64_t)sms * 8;
+  if (dev < 0 || dev >= 64) return 148;
+  if (!cached[dev]) {
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cached[dev] = sms;
+  }
+  return cached[dev];
+}
+
+static int point_grid(int64_t n) {
+  const int sms = sm_count();
+  int64_t want = (n + kPointThreads - 1) / kPointThreads;  // one 32-point chunk per warp
+  int64_t cap = (int64_t)sms * 16;
   if (want < 1) want = 1;
   return (int)(want < cap ? want : cap);
 }

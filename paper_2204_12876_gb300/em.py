@@ -306,3 +306,76 @@ def update_noalloc(params: Params, h, var, t_last, clouds, t_now: int, shift=(0,
     _check(lib.em_update_noalloc(ctypes.byref(cp), int(shift[0]), int(shift[1]), int(t_now), h.data_ptr(),
                                  var.data_ptr(), t_last.data_ptr(), nx, ny, nz, arr, len(clouds),
                                  _stream_handle(stream)), "em_update_noalloc")
+
+
+BATCH_GRAPH = 1
+
+
+class _Tuning(ctypes.Structure):
+    _fields_ = [("ray_group", ctypes.c_int32), ("fuse_group", ctypes.c_int32), ("big_thresh", ctypes.c_int32)]
+
+
+def _bind_batch():
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    sig = {
+        "em_batch_create": ([ctypes.c_int, i32, i32, i64, i32, ctypes.c_uint32, ctypes.POINTER(vp)], ctypes.c_int),
+        "em_batch_destroy": ([vp], ctypes.c_int),
+        "em_update_batch": ([vp, ctypes.POINTER(vp), ctypes.POINTER(_Cloud), i32, vp], ctypes.c_int),
+        "em_batch_set_tuning": ([vp, ctypes.POINTER(_Tuning)], ctypes.c_int),
+        "em_batch_get_tuning": ([vp, ctypes.POINTER(_Tuning)], ctypes.c_int),
+        "em_batch_autotune": ([vp, ctypes.POINTER(vp), ctypes.POINTER(_Cloud), i32, vp, i32,
+                               ctypes.POINTER(_Tuning)], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+
+
+_bind_batch()
+
+
+class Batch:
+    """em_batch: many maps updated by one kernel sequence (optionally one CUDA graph launch)."""
+
+    def __init__(self, max_maps: int, max_clouds: int, max_points: int, max_cells: int, graph: bool = True,
+                 device: int = 0):
+        h = ctypes.c_void_p()
+        _check(lib.em_batch_create(int(device), int(max_maps), int(max_clouds), int(max_points), int(max_cells),
+                                   BATCH_GRAPH if graph else 0, ctypes.byref(h)), "em_batch_create")
+        self._h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.em_batch_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    @staticmethod
+    def _pairs(pairs):
+        maps = (ctypes.c_void_p * len(pairs))(*[m.handle.value for m, _, _ in pairs])
+        clouds = (_Cloud * len(pairs))(*[_cloud_struct(p, q, False) for _, p, q in pairs])
+        return maps, clouds
+
+    def update(self, pairs, stream=None):
+        """pairs: [(Map, points CUDA tensor (n,3|4), pose), ...]; a map may repeat."""
+        maps, clouds = self._pairs(pairs)
+        _check(lib.em_update_batch(self._h, maps, clouds, len(pairs), _stream_handle(stream)), "em_update_batch")
+
+    def autotune(self, pairs, reps: int = 3, stream=None) -> dict:
+        maps, clouds = self._pairs(pairs)
+        t = _Tuning()
+        _check(lib.em_batch_autotune(self._h, maps, clouds, len(pairs), _stream_handle(stream), int(reps),
+                                     ctypes.byref(t)), "em_batch_autotune")
+        return {f: getattr(t, f) for f, _ in _Tuning._fields_}
+
+    def tuning(self) -> dict:
+        t = _Tuning()
+        _check(lib.em_batch_get_tuning(self._h, ctypes.byref(t)), "em_batch_get_tuning")
+        return {f: getattr(t, f) for f, _ in _Tuning._fields_}
+
+    def set_tuning(self, ray_group: int, fuse_group: int, big_thresh: int):
+        t = _Tuning(ray_group, fuse_group, big_thresh)
+        _check(lib.em_batch_set_tuning(self._h, ctypes.byref(t)), "em_batch_set_tuning")

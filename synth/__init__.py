@@ -11,7 +11,7 @@ in for them with the same shapes: depth images with invalid pixels, spinning
 LiDAR scans, terrain with steps, boxes, stairs and ramps.
 """
 from .terrain import (Terrain, StairsTerrain, raycast, pose_matrix, single_update, DepthRig, depth_stream,
-                      LidarRig, lidar_stream, batch_clouds, random_prior)
+                      LidarRig, lidar_stream, scattered_cloud, batch_clouds, random_prior)
 
 __all__ = ["Terrain", "StairsTerrain", "raycast", "pose_matrix", "single_update", "DepthRig", "depth_stream",
-           "LidarRig", "lidar_stream", "batch_clouds", "random_prior"]
+           "LidarRig", "lidar_stream", "scattered_cloud", "batch_clouds", "random_prior"]
