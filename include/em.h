@@ -254,6 +254,70 @@ int em_batch_get_tuning(const em_batch* batch, em_tuning* tuning);
 int em_batch_autotune(em_batch* batch, em_map* const* maps, const em_cloud* clouds, int32_t count,
                       em_stream_t stream, int32_t reps, em_tuning* out);
 
+/* ---- Served form: a request loop for many robots / sensors.
+ * The server keeps every map resident on its device and runs a worker thread.
+ * Requests (one update of one map) are admitted while the admitted ones fit in
+ * max_slots and their bytes fit in the memory budget (resident maps included);
+ * the rest wait in arrival order.  In EM_SERVE_BATCHED mode the worker starts a
+ * batch (em_update_batch) on any free stream whenever admitted requests wait,
+ * so requests that arrive while earlier batches run join the next batch and
+ * batches on different streams overlap on the device (continuous batching).  A
+ * map takes at most one update per batch and a map with an update in flight
+ * waits, so every request sees exactly the map it would see served alone.  In
+ * EM_SERVE_PLAIN mode the worker issues one em_update_multi per request in
+ * arrival order on one stream (the plain per-request path). */
+typedef struct em_server em_server;
+
+enum { EM_SERVE_BATCHED = 0, EM_SERVE_PLAIN = 1 };
+
+typedef struct em_server_cfg {
+  int32_t device;
+  int64_t budget_bytes;     /* device bytes for resident maps + batch workspaces + admitted requests */
+  int32_t max_slots;        /* requests admitted at a time */
+  int32_t n_streams;        /* batches in flight at a time (batched mode) */
+  int32_t max_batch_maps;   /* maps per batch */
+  int64_t max_batch_points; /* points per batch (also the largest request) */
+  int32_t max_map_cells;    /* largest map the server accepts */
+  uint32_t mode;            /* EM_SERVE_BATCHED or EM_SERVE_PLAIN */
+  uint32_t batch_flags;     /* EM_BATCH_GRAPH */
+  int32_t fail_alloc_at;    /* fault injection: the n-th em_server_add_map (1-based) fails with EM_ERR_OOM; 0 = off */
+} em_server_cfg;
+
+typedef struct em_result {
+  int32_t status;           /* EM_OK, EM_ERR_REJECTED, EM_ERR_TIMEOUT (cancelled), or the launch's error */
+  int32_t map_id;
+  int64_t points;
+  int32_t batch_size;       /* requests in the batch that carried this one */
+  int64_t t_submit_ns;      /* steady-clock timestamps */
+  int64_t t_start_ns;       /* launched */
+  int64_t t_done_ns;        /* the worker saw the GPU finish */
+} em_result;
+
+typedef struct em_server_stats {
+  int64_t submitted, completed, rejected, cancelled, batches, batched_requests;
+  int64_t max_batch_size, bytes_in_use, peak_bytes, slots_in_use;
+} em_server_stats;
+
+int em_server_create(const em_server_cfg* cfg, em_server** out);
+/* Create a resident map; EM_ERR_REJECTED when it does not fit the budget. */
+int em_server_add_map(em_server* srv, const em_params* params, int32_t* map_id);
+/* The resident map (to read layers after em_server_drain; do not update it directly). */
+int em_server_map(em_server* srv, int32_t map_id, em_map** out);
+/* Queue one update of map_id from n_clouds device clouds (host array of
+ * descriptors; the points stay valid until the request completes).  Returns at
+ * once with a ticket; EM_ERR_REJECTED when the request can never fit. */
+int em_server_submit(em_server* srv, int32_t map_id, const em_cloud* clouds, int32_t n_clouds, uint64_t* ticket);
+/* Wait for a ticket (timeout_us < 0: forever); EM_ERR_TIMEOUT when it has not
+ * finished in time (the request stays queued).  Fills *out and forgets the
+ * ticket once finished. */
+int em_server_wait(em_server* srv, uint64_t ticket, int64_t timeout_us, em_result* out);
+/* Withdraw a request that has not been launched; EM_ERR_BUSY if it already runs. */
+int em_server_cancel(em_server* srv, uint64_t ticket);
+/* Wait until every submitted request has finished. */
+int em_server_drain(em_server* srv, int64_t timeout_us);
+int em_server_get_stats(em_server* srv, em_server_stats* out);
+int em_server_destroy(em_server* srv); /* NULL-safe: drains, stops the worker, frees the maps */
+
 /* ---- Update without allocation.
  * The paper has no counterpart: this entry point exists for callers that
  * cannot allocate device memory when they update a map -- a real-time loop

@@ -1,0 +1,442 @@
+// em_server.cu -- the served form: a continuous-batching request loop.
+//
+// Host side only (no kernels of its own): the worker thread admits requests by
+// slots and memory budget, forms batches of distinct idle maps, launches each
+// batch with em_update_batch on a free stream, and polls the streams' events
+// to complete tickets.  A map is never in two batches in flight at once, and a
+// map takes one update per batch, so each request is fused against exactly
+// the map state it would see if it were served alone.
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "em.h"
+#include "em_host.h"
+
+using namespace em;
+
+namespace {
+
+int64_t now_ns() {
+  return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+enum ReqState { kPending, kAdmitted, kRunning, kDone };
+
+struct Request {
+  int32_t map_id = 0;
+  std::vector<em_cloud> clouds;
+  int64_t points = 0;
+  int64_t bytes = 0;
+  ReqState state = kPending;
+  em_result res{};
+};
+
+struct Flight {
+  bool busy = false;
+  cudaEvent_t ev = nullptr;
+  std::vector<uint64_t> tickets;
+  std::vector<int32_t> maps;
+  int64_t bytes = 0;
+};
+
+constexpr int64_t kRecordBytes = 8;  // one (z, sigma_p^2) record per point
+
+}  // namespace
+
+struct em_server {
+  em_server_cfg cfg{};
+  std::vector<em_map*> maps;
+  std::vector<int64_t> map_bytes;
+  std::vector<char> map_busy;
+  std::vector<cudaStream_t> streams;
+  std::vector<em_batch*> batches;
+  std::vector<Flight> flights;            // batched: one per stream; plain: grows as needed
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<uint64_t> pending, admitted;
+  std::unordered_map<uint64_t, Request> reqs;
+  uint64_t next_ticket = 1;
+  int64_t bytes_in_use = 0, fixed_bytes = 0;
+  int32_t slots_in_use = 0;
+  int32_t maps_added = 0;
+  em_server_stats st{};
+  bool stop = false;
+  std::thread worker;
+};
+
+namespace {
+
+// Move pending requests into the admitted set while slots and memory allow
+// (strict arrival order).  Caller holds the lock.
+void admit(em_server* s) {
+  while (!s->pending.empty()) {
+    Request& r = s->reqs[s->pending.front()];
+    if (s->slots_in_use >= s->cfg.max_slots) break;
+    if (s->bytes_in_use + r.bytes > s->cfg.budget_bytes) break;
+    s->bytes_in_use += r.bytes;
+    if (s->bytes_in_use > s->st.peak_bytes) s->st.peak_bytes = s->bytes_in_use;
+    s->slots_in_use += 1;
+    r.state = kAdmitted;
+    s->admitted.push_back(s->pending.front());
+    s->pending.pop_front();
+  }
+}
+
+void complete(em_server* s, Flight& f, int status) {
+  const int64_t t = now_ns();
+  for (uint64_t tk : f.tickets) {
+    Request& r = s->reqs[tk];
+    r.state = kDone;
+    r.res.status = status;
+    r.res.t_done_ns = t;
+    s->bytes_in_use -= r.bytes;
+    s->slots_in_use -= 1;
+    s->st.completed += 1;
+  }
+  for (int32_t m : f.maps) s->map_busy[m] = 0;
+  f.tickets.clear();
+  f.maps.clear();
+  f.busy = false;
+}
+
+// One worker pass: complete finished flights, admit, launch.  Returns true when
+// anything is in flight or waiting (the worker keeps polling).
+bool worker_pass(em_server* s, std::unique_lock<std::mutex>& lk) {
+  // completions (cudaEventQuery does not block)
+  for (Flight& f : s->flights) {
+    if (!f.busy) continue;
+    cudaError_t q = cudaEventQuery(f.ev);
+    if (q == cudaErrorNotReady) continue;
+    complete(s, f, q == cudaSuccess ? EM_OK : map_record_error("request", q));
+    s->cv_done.notify_all();
+  }
+  admit(s);
+  if (s->cfg.mode == EM_SERVE_PLAIN) {
+    // one update per request, arrival order, one stream
+    while (!s->admitted.empty()) {
+      const uint64_t tk = s->admitted.front();
+      Request& r = s->reqs[tk];
+      size_t fi = 0;
+      while (fi < s->flights.size() && s->flights[fi].busy) ++fi;
+      if (fi == s->flights.size()) {
+        Flight nf;
+        if (cudaEventCreateWithFlags(&nf.ev, cudaEventDisableTiming) != cudaSuccess) break;
+        s->flights.push_back(nf);
+      }
+      Flight& f = s->flights[fi];
+      s->admitted.pop_front();
+      r.state = kRunning;
+      r.res.t_start_ns = now_ns();
+      r.res.batch_size = 1;
+      f.busy = true;
+      f.tickets.assign(1, tk);
+      f.maps.clear();
+      em_map* m = s->maps[r.map_id];
+      std::vector<em_cloud> cl = r.clouds;
+      lk.unlock();
+      int rc = em_update_multi(m, cl.data(), (int32_t)cl.size(), (em_stream_t)s->streams[0]);
+      if (rc == EM_OK) cudaEventRecord(f.ev, s->streams[0]);
+      lk.lock();
+      s->st.batches += 1;
+      s->st.batched_requests += 1;
+      if (s->st.max_batch_size < 1) s->st.max_batch_size = 1;
+      if (rc != EM_OK) complete(s, f, rc);
+    }
+  } else {
+    for (size_t si = 0; si < s->streams.size(); ++si) {
+      Flight& f = s->flights[si];
+      if (f.busy || s->admitted.empty()) continue;
+      // distinct idle maps in arrival order, within the batch limits
+      std::vector<uint64_t> take;
+      std::vector<int32_t> bmaps;
+      int64_t pts = 0;
+      for (auto it = s->admitted.begin(); it != s->admitted.end();) {
+        Request& r = s->reqs[*it];
+        bool dup = s->map_busy[r.map_id] != 0;
+        for (int32_t m : bmaps) dup |= (m == r.map_id);
+        if (dup || (int32_t)bmaps.size() >= s->cfg.max_batch_maps || pts + r.points > s->cfg.max_batch_points) {
+          ++it;
+          continue;
+        }
+        take.push_back(*it);
+        bmaps.push_back(r.map_id);
+        pts += r.points;
+        it = s->admitted.erase(it);
+      }
+      if (take.empty()) break;
+      std::vector<em_map*> pm;
+      std::vector<em_cloud> pc;
+      const int64_t t0 = now_ns();
+      for (uint64_t tk : take) {
+        Request& r = s->reqs[tk];
+        r.state = kRunning;
+        r.res.t_start_ns = t0;
+        r.res.batch_size = (int32_t)take.size();
+        for (const em_cloud& c : r.clouds) {
+          pm.push_back(s->maps[r.map_id]);
+          pc.push_back(c);
+        }
+        s->map_busy[r.map_id] = 1;
+      }
+      f.busy = true;
+      f.tickets = take;
+      f.maps = bmaps;
+      s->st.batches += 1;
+      s->st.batched_requests += (int64_t)take.size();
+      if ((int64_t)take.size() > s->st.max_batch_size) s->st.max_batch_size = (int64_t)take.size();
+      lk.unlock();
+      int rc = em_update_batch(s->batches[si], pm.data(), pc.data(), (int32_t)pc.size(), (em_stream_t)s->streams[si]);
+      if (rc == EM_OK) cudaEventRecord(f.ev, s->streams[si]);
+      lk.lock();
+      if (rc != EM_OK) {
+        complete(s, f, rc);
+        s->cv_done.notify_all();
+      }
+    }
+  }
+  bool busy = !s->pending.empty() || !s->admitted.empty();
+  for (const Flight& f : s->flights) busy |= f.busy;
+  return busy;
+}
+
+void worker_main(em_server* s) {
+  cudaSetDevice(s->cfg.device);
+  std::unique_lock<std::mutex> lk(s->mu);
+  while (true) {
+    const bool busy = worker_pass(s, lk);
+    if (s->stop && !busy) break;
+    if (busy) {
+      // poll the in-flight events; let submitters in between
+      lk.unlock();
+      std::this_thread::yield();
+      lk.lock();
+    } else {
+      s->cv_work.wait(lk, [&] { return s->stop || !s->pending.empty(); });
+    }
+  }
+}
+
+int64_t map_device_bytes(const em_map* m) {
+  em_info i;
+  em_get_info(m, &i);
+  return i.device_bytes;
+}
+
+}  // namespace
+
+extern "C" {
+
+int em_server_create(const em_server_cfg* cfg, em_server** out) {
+  if (!cfg || !out) return EM_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (cfg->budget_bytes <= 0 || cfg->max_slots < 1 || cfg->n_streams < 1 || cfg->max_batch_maps < 1 ||
+      cfg->max_batch_points < 1 || cfg->max_map_cells < 1 || (cfg->mode != EM_SERVE_BATCHED && cfg->mode != EM_SERVE_PLAIN))
+    return EM_ERR_INVALID_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) return EM_ERR_INVALID_ARG;
+  if (cudaSetDevice(cfg->device) != cudaSuccess) return EM_ERR_CUDA;
+  em_server* s = new (std::nothrow) em_server();
+  if (!s) return EM_ERR_OOM;
+  s->cfg = *cfg;
+  const int ns = cfg->mode == EM_SERVE_PLAIN ? 1 : cfg->n_streams;
+  int rc = EM_OK;
+  for (int i = 0; i < ns && rc == EM_OK; ++i) {
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) { rc = EM_ERR_CUDA; break; }
+    s->streams.push_back(st);
+    if (cfg->mode == EM_SERVE_BATCHED) {
+      em_batch* b = nullptr;
+      rc = em_batch_create(cfg->device, cfg->max_batch_maps, cfg->max_batch_maps * 8, cfg->max_batch_points,
+                           cfg->max_map_cells, cfg->batch_flags, &b);
+      if (rc == EM_OK) {
+        s->batches.push_back(b);
+        s->fixed_bytes += cfg->max_batch_points * kRecordBytes;
+      }
+      Flight f;
+      if (rc == EM_OK && cudaEventCreateWithFlags(&f.ev, cudaEventDisableTiming) != cudaSuccess) rc = EM_ERR_CUDA;
+      s->flights.push_back(f);
+    }
+  }
+  if (rc == EM_OK && s->fixed_bytes > cfg->budget_bytes) rc = EM_ERR_REJECTED;
+  if (rc != EM_OK) {
+    for (em_batch* b : s->batches) em_batch_destroy(b);
+    for (Flight& f : s->flights) if (f.ev) cudaEventDestroy(f.ev);
+    for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
+    delete s;
+    return rc;
+  }
+  s->bytes_in_use = s->fixed_bytes;
+  s->st.bytes_in_use = s->bytes_in_use;
+  s->worker = std::thread(worker_main, s);
+  *out = s;
+  return EM_OK;
+}
+
+int em_server_add_map(em_server* s, const em_params* params, int32_t* map_id) {
+  if (!s || !params || !map_id) return EM_ERR_INVALID_ARG;
+  if ((int64_t)params->width * params->height > s->cfg.max_map_cells) return EM_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->maps_added += 1;
+  if (s->cfg.fail_alloc_at > 0 && s->maps_added == s->cfg.fail_alloc_at) return EM_ERR_OOM;
+  em_params p = *params;
+  p.flags &= ~(uint32_t)EM_F_TRACE;
+  em_map* m = nullptr;
+  int rc = em_create(&p, s->cfg.device, &m);
+  if (rc) return rc;
+  const int64_t bytes = map_device_bytes(m);
+  if (s->bytes_in_use + bytes > s->cfg.budget_bytes) {
+    em_destroy(m);
+    return EM_ERR_REJECTED;
+  }
+  s->bytes_in_use += bytes;
+  s->maps.push_back(m);
+  s->map_bytes.push_back(bytes);
+  s->map_busy.push_back(0);
+  *map_id = (int32_t)s->maps.size() - 1;
+  return EM_OK;
+}
+
+int em_server_map(em_server* s, int32_t map_id, em_map** out) {
+  if (!s || !out) return EM_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (map_id < 0 || map_id >= (int32_t)s->maps.size()) return EM_ERR_INVALID_ARG;
+  *out = s->maps[map_id];
+  return EM_OK;
+}
+
+int em_server_submit(em_server* s, int32_t map_id, const em_cloud* clouds, int32_t n_clouds, uint64_t* ticket) {
+  if (!s || !clouds || n_clouds < 1 || n_clouds > 8 || !ticket) return EM_ERR_INVALID_ARG;
+  int64_t pts = 0;
+  for (int i = 0; i < n_clouds; ++i) {
+    const em_cloud& c = clouds[i];
+    if (c.n < 0 || (c.stride != 3 && c.stride != 4) || (c.n > 0 && !c.points)) return EM_ERR_INVALID_ARG;
+    pts += c.n;
+  }
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (map_id < 0 || map_id >= (int32_t)s->maps.size()) return EM_ERR_INVALID_ARG;
+  s->st.submitted += 1;
+  const int64_t bytes = pts * kRecordBytes;
+  const int64_t maps_bytes = [&] {
+    int64_t t = 0;
+    for (int64_t b : s->map_bytes) t += b;
+    return t;
+  }();
+  if (pts > s->cfg.max_batch_points || s->fixed_bytes + maps_bytes + bytes > s->cfg.budget_bytes) {
+    s->st.rejected += 1;
+    return EM_ERR_REJECTED;
+  }
+  const uint64_t tk = s->next_ticket++;
+  Request& r = s->reqs[tk];
+  r.map_id = map_id;
+  r.clouds.assign(clouds, clouds + n_clouds);
+  r.points = pts;
+  r.bytes = bytes;
+  r.res.map_id = map_id;
+  r.res.points = pts;
+  r.res.t_submit_ns = now_ns();
+  s->pending.push_back(tk);
+  *ticket = tk;
+  s->cv_work.notify_one();
+  return EM_OK;
+}
+
+int em_server_wait(em_server* s, uint64_t ticket, int64_t timeout_us, em_result* out) {
+  if (!s) return EM_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return EM_ERR_INVALID_ARG;
+  auto done = [&] { return s->reqs[ticket].state == kDone; };
+  if (timeout_us < 0) {
+    s->cv_done.wait(lk, done);
+  } else if (!s->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), done)) {
+    return EM_ERR_TIMEOUT;
+  }
+  if (out) *out = s->reqs[ticket].res;
+  s->reqs.erase(ticket);
+  return EM_OK;
+}
+
+int em_server_cancel(em_server* s, uint64_t ticket) {
+  if (!s) return EM_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return EM_ERR_INVALID_ARG;
+  Request& r = it->second;
+  if (r.state == kRunning || r.state == kDone) return EM_ERR_BUSY;
+  auto drop = [&](std::deque<uint64_t>& q) {
+    for (auto q_it = q.begin(); q_it != q.end(); ++q_it)
+      if (*q_it == ticket) { q.erase(q_it); return true; }
+    return false;
+  };
+  if (r.state == kAdmitted) {
+    drop(s->admitted);
+    s->bytes_in_use -= r.bytes;
+    s->slots_in_use -= 1;
+  } else {
+    drop(s->pending);
+  }
+  r.state = kDone;
+  r.res.status = EM_ERR_TIMEOUT;
+  r.res.t_done_ns = now_ns();
+  s->st.cancelled += 1;
+  s->cv_done.notify_all();
+  s->cv_work.notify_one();
+  return EM_OK;
+}
+
+int em_server_drain(em_server* s, int64_t timeout_us) {
+  if (!s) return EM_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto idle = [&] {
+    if (!s->pending.empty() || !s->admitted.empty()) return false;
+    for (const Flight& f : s->flights)
+      if (f.busy) return false;
+    return true;
+  };
+  if (timeout_us < 0) {
+    s->cv_done.wait(lk, idle);
+  } else if (!s->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), idle)) {
+    return EM_ERR_TIMEOUT;
+  }
+  return EM_OK;
+}
+
+int em_server_get_stats(em_server* s, em_server_stats* out) {
+  if (!s || !out) return EM_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  *out = s->st;
+  out->bytes_in_use = s->bytes_in_use;
+  out->slots_in_use = s->slots_in_use;
+  return EM_OK;
+}
+
+int em_server_destroy(em_server* s) {
+  if (!s) return EM_OK;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+    s->cv_work.notify_all();
+  }
+  if (s->worker.joinable()) s->worker.join();
+  cudaSetDevice(s->cfg.device);
+  for (cudaStream_t st : s->streams) cudaStreamSynchronize(st);
+  for (em_batch* b : s->batches) em_batch_destroy(b);
+  for (Flight& f : s->flights)
+    if (f.ev) cudaEventDestroy(f.ev);
+  for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
+  for (em_map* m : s->maps) em_destroy(m);
+  delete s;
+  return EM_OK;
+}
+
+}  // extern "C"

@@ -379,3 +379,122 @@ class Batch:
     def set_tuning(self, ray_group: int, fuse_group: int, big_thresh: int):
         t = _Tuning(ray_group, fuse_group, big_thresh)
         _check(lib.em_batch_set_tuning(self._h, ctypes.byref(t)), "em_batch_set_tuning")
+
+
+SERVE_BATCHED, SERVE_PLAIN = 0, 1
+
+
+class _ServerCfg(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("budget_bytes", ctypes.c_int64), ("max_slots", ctypes.c_int32),
+                ("n_streams", ctypes.c_int32), ("max_batch_maps", ctypes.c_int32),
+                ("max_batch_points", ctypes.c_int64), ("max_map_cells", ctypes.c_int32), ("mode", ctypes.c_uint32),
+                ("batch_flags", ctypes.c_uint32), ("fail_alloc_at", ctypes.c_int32)]
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("map_id", ctypes.c_int32), ("points", ctypes.c_int64),
+                ("batch_size", ctypes.c_int32), ("t_submit_ns", ctypes.c_int64), ("t_start_ns", ctypes.c_int64),
+                ("t_done_ns", ctypes.c_int64)]
+
+
+class _ServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "completed", "rejected", "cancelled", "batches",
+                                             "batched_requests", "max_batch_size", "bytes_in_use", "peak_bytes",
+                                             "slots_in_use")]
+
+
+def _bind_server():
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    sig = {
+        "em_server_create": ([ctypes.POINTER(_ServerCfg), ctypes.POINTER(vp)], ctypes.c_int),
+        "em_server_add_map": ([vp, ctypes.POINTER(_Params), ctypes.POINTER(i32)], ctypes.c_int),
+        "em_server_map": ([vp, i32, ctypes.POINTER(vp)], ctypes.c_int),
+        "em_server_submit": ([vp, i32, ctypes.POINTER(_Cloud), i32, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+        "em_server_wait": ([vp, ctypes.c_uint64, i64, ctypes.POINTER(_Result)], ctypes.c_int),
+        "em_server_cancel": ([vp, ctypes.c_uint64], ctypes.c_int),
+        "em_server_drain": ([vp, i64], ctypes.c_int),
+        "em_server_get_stats": ([vp, ctypes.POINTER(_ServerStats)], ctypes.c_int),
+        "em_server_destroy": ([vp], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+
+
+_bind_server()
+
+
+class _MapView(Map):
+    """A resident map owned by a server (not destroyed by Python)."""
+
+    def __init__(self, handle, params):
+        self.params = params
+        self._h = handle
+        self.device = 0
+
+    def close(self):
+        self._h = None
+
+    __del__ = close
+
+
+class Server:
+    """em_server: continuous-batching request loop over resident maps."""
+
+    def __init__(self, budget_bytes: int, max_slots: int = 256, n_streams: int = 2, max_batch_maps: int = 32,
+                 max_batch_points: int = 8_000_000, max_map_cells: int = 250_000, mode: int = SERVE_BATCHED,
+                 graph: bool = True, device: int = 0, fail_alloc_at: int = 0):
+        self._cfg = _ServerCfg(device, int(budget_bytes), max_slots, n_streams, max_batch_maps,
+                               int(max_batch_points), max_map_cells, mode, BATCH_GRAPH if graph else 0,
+                               fail_alloc_at)
+        h = ctypes.c_void_p()
+        _check(lib.em_server_create(ctypes.byref(self._cfg), ctypes.byref(h)), "em_server_create")
+        self._h = h
+        self._keep = {}
+        self._params = []
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.em_server_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def add_map(self, params: Params) -> int:
+        cp = params._c()
+        mid = ctypes.c_int32()
+        _check(lib.em_server_add_map(self._h, ctypes.byref(cp), ctypes.byref(mid)), "em_server_add_map")
+        self._params.append(params)
+        return mid.value
+
+    def map(self, map_id: int) -> Map:
+        h = ctypes.c_void_p()
+        _check(lib.em_server_map(self._h, int(map_id), ctypes.byref(h)), "em_server_map")
+        return _MapView(h, self._params[map_id])
+
+    def submit(self, map_id: int, clouds) -> int:
+        """clouds: [(points CUDA tensor, pose), ...]; tensors are kept alive until the ticket is waited."""
+        arr = (_Cloud * len(clouds))(*[_cloud_struct(p, q, False) for p, q in clouds])
+        tk = ctypes.c_uint64()
+        _check(lib.em_server_submit(self._h, int(map_id), arr, len(clouds), ctypes.byref(tk)), "em_server_submit")
+        self._keep[tk.value] = clouds
+        return tk.value
+
+    def wait(self, ticket: int, timeout_us: int = -1) -> dict:
+        r = _Result()
+        _check(lib.em_server_wait(self._h, ctypes.c_uint64(ticket), int(timeout_us), ctypes.byref(r)),
+               "em_server_wait")
+        self._keep.pop(ticket, None)
+        return {f: getattr(r, f) for f, _ in _Result._fields_}
+
+    def cancel(self, ticket: int):
+        _check(lib.em_server_cancel(self._h, ctypes.c_uint64(ticket)), "em_server_cancel")
+
+    def drain(self, timeout_us: int = -1):
+        _check(lib.em_server_drain(self._h, int(timeout_us)), "em_server_drain")
+
+    def stats(self) -> dict:
+        s = _ServerStats()
+        _check(lib.em_server_get_stats(self._h, ctypes.byref(s)), "em_server_get_stats")
+        return {f: getattr(s, f) for f, _ in _ServerStats._fields_}

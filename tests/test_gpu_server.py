@@ -1,0 +1,120 @@
+"""Served form: requests from many robots through the continuous-batching
+server give, for every map, exactly the state that the same requests give when
+applied alone with em_update (bit for bit); admission follows the memory
+budget; oversize requests are rejected; cancel / timeout / an injected
+allocation failure are handled on the host (no GPU fault involved)."""
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+BASE = dict(resolution=0.04, noise_a0=0.005, noise_a2=0.002, mahalanobis_k=2.5, outlier_variance=1e-4,
+            ray_step=0.04)
+SIDES = [60, 90, 120, 75, 100, 140]
+
+
+@pytest.fixture(scope="module")
+def em():
+    from paper_2204_12876_gb300 import build
+    build.build()
+    from paper_2204_12876_gb300 import em as mod
+    return mod
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def workload(n_req=40, seed=5):
+    """A seeded interleaving of requests over the maps: (map index, cloud)."""
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for k in range(n_req):
+        j = int(rng.integers(0, len(SIDES)))
+        half = 0.5 * SIDES[j] * 0.04
+        pts, pose = synth.scattered_cloud(seed * 1000 + k, int(rng.integers(2000, 20000)), half, nan_frac=0.02)
+        reqs.append((j, dev(pts), pose))
+    return reqs
+
+
+@pytest.mark.parametrize("mode,streams", [(0, 1), (0, 3), (1, 1)])
+def test_served_equals_alone(em, mode, streams):
+    reqs = workload()
+    # alone: each map's requests applied in order with em_update
+    alone = [em.Map(em.Params(width=s, height=s, **BASE)) for s in SIDES]
+    for j, p, q in reqs:
+        alone[j].update(p, q)
+    torch.cuda.synchronize()
+    srv = em.Server(budget_bytes=1 << 30, n_streams=streams, max_batch_maps=4, max_batch_points=100_000, mode=mode)
+    ids = [srv.add_map(em.Params(width=s, height=s, **BASE)) for s in SIDES]
+    tickets = [srv.submit(ids[j], [(p, q)]) for j, p, q in reqs]
+    results = [srv.wait(t) for t in tickets]
+    assert all(r["status"] == 0 for r in results)
+    assert all(r["t_submit_ns"] <= r["t_start_ns"] <= r["t_done_ns"] for r in results)
+    st = srv.stats()
+    assert st["completed"] == len(reqs) and st["slots_in_use"] == 0
+    if mode == 0:
+        assert st["max_batch_size"] > 1  # requests were batched
+    for j, m in enumerate(alone):
+        a = m.state()
+        b = srv.map(ids[j]).state()
+        for k in ("h", "var", "t_last"):
+            assert np.array_equal(a[k], b[k], equal_nan=True), (j, k)
+    srv.close()
+
+
+def test_admission_by_budget(em):
+    reqs = workload(n_req=30, seed=6)
+    probe = em.Server(budget_bytes=1 << 30, n_streams=2, max_batch_maps=4, max_batch_points=50_000)
+    for s in SIDES:
+        probe.add_map(em.Params(width=s, height=s, **BASE))
+    base = probe.stats()["bytes_in_use"]  # batch workspaces + resident maps
+    probe.close()
+    budget = base + 40_000 * 8  # room for ~40k records in flight
+    srv = em.Server(budget_bytes=budget, n_streams=2, max_batch_maps=4, max_batch_points=50_000)
+    ids = [srv.add_map(em.Params(width=s, height=s, **BASE)) for s in SIDES]
+    tickets = [srv.submit(ids[j], [(p, q)]) for j, p, q in reqs]
+    for t in tickets:
+        assert srv.wait(t)["status"] == 0
+    st = srv.stats()
+    assert st["peak_bytes"] <= budget
+    assert st["completed"] == len(reqs)
+    # a request larger than the whole budget can never run: rejected at once
+    big = dev(np.zeros((45_000, 3), np.float32))
+    with pytest.raises(em.EMError) as e:
+        srv.submit(ids[0], [(big, np.eye(3, 4).reshape(12))])
+    assert e.value.code == em.EM_ERR_REJECTED
+    # a map that does not fit the budget is refused
+    with pytest.raises(em.EMError) as e:
+        srv.add_map(em.Params(width=500, height=500, **BASE))
+    assert e.value.code in (em.EM_ERR_REJECTED, em.EM_ERR_INVALID_ARG)
+    srv.close()
+
+
+def test_cancel_timeout_and_injected_allocation_failure(em):
+    srv = em.Server(budget_bytes=1 << 30, n_streams=1, mode=1, fail_alloc_at=2)
+    a = srv.add_map(em.Params(width=100, height=100, **BASE))
+    with pytest.raises(em.EMError) as e:  # the injected failure hits the second map
+        srv.add_map(em.Params(width=100, height=100, **BASE))
+    assert e.value.code == em.EM_ERR_OOM
+    b = srv.add_map(em.Params(width=100, height=100, **BASE))
+    pts = dev(synth.scattered_cloud(1, 200_000, 2.0)[0])
+    pose = np.eye(3, 4).reshape(12)
+    tickets = [srv.submit(a if i % 2 else b, [(pts, pose)]) for i in range(60)]
+    last = tickets[-1]
+    with pytest.raises(em.EMError) as e:
+        srv.wait(last, timeout_us=0)
+    assert e.value.code == em.EM_ERR_TIMEOUT
+    try:
+        srv.cancel(last)
+        r = srv.wait(last)
+        assert r["status"] == em.EM_ERR_TIMEOUT and srv.stats()["cancelled"] == 1
+    except em.EMError as err:  # it had already been launched
+        assert err.code == em.EM_ERR_BUSY
+    srv.drain()
+    st = srv.stats()
+    assert st["completed"] + st["cancelled"] == 60
+    srv.close()
