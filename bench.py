@@ -1,24 +1,41 @@
 #!/usr/bin/env python
 """Benchmark of the elevation-map fusion path on one node.
 
-Workload (default): the quadruped depth-camera stream -- four 320x240 depth
-cameras (4 x 76,800 float32 points per frame, ~5 % invalid) over seeded wave
-terrain with boxes, a 200 x 200 map at 0.04 m, random-walk pose; every step is
-one frame: recentring shift, then one update of all four clouds (transform,
-noise model, binning, wall rule off, Mahalanobis gate k = 2.5, Eq. 1/2 fusion,
-visibility ray march + removal).
+Headline workload (the served stream): 32 simulated robots -- 16 with a depth
+camera (76,800 points per cloud, 320x240, ~5 % invalid) and 16 with a LiDAR
+(128 x 2,048 = 262,144 points, range <= 30 m) -- each with its own resident map
+of 200^2 .. 500^2 cells at 0.04 m; every request fuses one cloud into its
+robot's map (transform, noise model, binning, Mahalanobis gate k = 2.5, Eq. 1/2
+fusion, visibility ray march and removal).  The server (em_server) admits
+requests by a 40 GB budget and batches them continuously.
+
+  value          fused points/s of the served path at saturation: K rounds of
+                 one request per robot, all submitted at once, wall time
+                 between synchronised brackets.  One step = one round.
+  latency_ms     p50 / p99 request latency (submit -> GPU done) at the stated
+                 load, 2,000 updates/s Poisson, for the served and the plain
+                 per-request path (one em_update per request).
+  e2e            the served path with host clouds: pinned host -> device copy
+                 per request and the elevation of every map read back per round.
+  roofline       dominant kernel of a served batch (event-timed).
+  batched        64 maps of 100^2..500^2 cells, 10k..400k points each, one
+                 batched update per step (graph replay, autotuned shapes) vs 64
+                 sequential em_update calls; HBM roofline of the update.
+  depth_stream   one robot with 4 depth cameras (4 x 76,800 points), 200x200 map,
+                 one em_update_multi per frame (plain path latency).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Prints one JSON line (rank 0).  Under torchrun every rank runs its own robot's
-stream on its own GPU (maps are independent: weak scaling, no collective on the
-data path; the timing takes the max over ranks).
+Under torchrun every rank serves its own fleet on its own GPU (maps are
+independent: weak scaling, no collective on the data path); the timing takes the
+max over ranks.
 """
 from __future__ import annotations
 
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -32,25 +49,37 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 METRIC = "fused points/s & p99 map-update latency (served vs plain) at 1 GB300"
-WORKLOAD = "depth-camera stream: 4 x 320x240 depth clouds per frame, 200x200 map @ 0.04 m"
-PARAMS = dict(width=200, height=200, resolution=0.04, noise_a0=0.005, noise_a2=0.002, var_min=1e-8,
-              min_range=0.05, max_range=10.0, mahalanobis_k=2.5, outlier_variance=1e-4, ray_step=0.04,
-              cleanup_min_age=0, cleanup_normal_thresh=0.0)
+WORKLOAD = ("served stream: 32 robots (16 depth 76,800 pts, 16 LiDAR 262,144 pts), maps 200^2-500^2 @ 0.04 m, "
+            "40 GB budget")
+DEPTH_P = dict(resolution=0.04, noise_a0=0.005, noise_a2=0.002, var_min=1e-8, min_range=0.05, max_range=10.0,
+               mahalanobis_k=2.5, outlier_variance=1e-4, ray_step=0.04)
+LIDAR_P = dict(resolution=0.04, noise_a0=0.01, noise_a2=0.001, var_min=1e-8, min_range=0.3, max_range=40.0,
+               mahalanobis_k=2.5, outlier_variance=1e-4, ray_step=0.04)
+BATCH_P = dict(resolution=0.04, noise_a0=0.005, noise_a2=0.002, var_min=1e-8, mahalanobis_k=2.5,
+               outlier_variance=1e-4)
+N_ROBOTS = 32
+RATE_HZ = 2000.0
+BUDGET = 40 << 30
 L2_FLUSH_BYTES = 256 << 20
+RAY_OPS_PER_SAMPLE = 35  # arithmetic / compare / index operations per ray sample in k_ray
+
+
+def f32params(P):
+    return {k: (float(np.float32(v)) if isinstance(v, float) else v) for k, v in P.items()}
 
 
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             p = json.load(f)
-        return float(p["hbm_gbs"]), "measured"
+        return float(p["hbm_gbs"]), float(p.get("sm_max_mhz", 2070.0)), "measured"
     except Exception:
-        return 6800.0, "fallback"
+        return 6800.0, 2070.0, "fallback"
 
 
-def make_pool(n_frames: int, seed: int):
-    import synth
-    return list(synth.depth_stream(seed=seed, frames=n_frames))
+def pct(xs, q):
+    xs = sorted(xs)
+    return xs[min(len(xs) - 1, int(math.ceil(q * len(xs))) - 1)] if xs else None
 
 
 class ClockSampler:
@@ -115,12 +144,13 @@ def file_hash(*paths) -> str:
     return h.hexdigest()[:16]
 
 
-KERNEL_SOURCES = {"ray": ["paper_2204_12876_gb300/csrc/k_ray.cu", "paper_2204_12876_gb300/csrc/em_point.cuh"],
-                  "count": ["paper_2204_12876_gb300/csrc/k_sort.cu", "paper_2204_12876_gb300/csrc/em_point.cuh"],
-                  "scatter": ["paper_2204_12876_gb300/csrc/k_sort.cu", "paper_2204_12876_gb300/csrc/em_point.cuh"],
-                  "alloc": ["paper_2204_12876_gb300/csrc/k_sort.cu"],
-                  "fuse": ["paper_2204_12876_gb300/csrc/k_fuse.cu"],
-                  "clear": ["paper_2204_12876_gb300/csrc/k_ray.cu"]}
+CSRC = "paper_2204_12876_gb300/csrc/"
+KERNEL_SOURCES = {"ray": [CSRC + "k_ray.cu", CSRC + "em_point.cuh"],
+                  "count": [CSRC + "k_sort.cu", CSRC + "em_point.cuh"],
+                  "scatter": [CSRC + "k_sort.cu", CSRC + "em_point.cuh"],
+                  "alloc": [CSRC + "k_sort.cu"],
+                  "fuse": [CSRC + "k_fuse.cu"],
+                  "clear": [CSRC + "k_ray.cu"]}
 
 
 def ncu_traffic(kernel: str, workload: str):
@@ -128,14 +158,41 @@ def ncu_traffic(kernel: str, workload: str):
     the current source of that kernel (else None)."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            t = json.load(f)
-        e = t[workload][kernel]
+            e = json.load(f)[workload][kernel]
         if e["source_hash"] != file_hash(*KERNEL_SOURCES[kernel]):
             return None
         return float(e["dram_bytes_per_launch"])
     except Exception:
         return None
 
+
+# ---------------------------------------------------------------- workloads
+
+def make_fleet(seed: int = 5):
+    rng = np.random.default_rng(seed)
+    robots = []
+    for i in range(N_ROBOTS):
+        kind = "depth" if i < N_ROBOTS // 2 else "lidar"
+        side = int(rng.integers(200, 501))
+        robots.append({"kind": kind, "params": dict(DEPTH_P if kind == "depth" else LIDAR_P, width=side, height=side)})
+    return robots
+
+
+def make_pools(seed: int = 5):
+    import synth
+    depth = []
+    for fr in synth.depth_stream(seed=seed, frames=2):
+        depth.extend(fr["clouds"])  # single-camera clouds, 76,800 points each
+    lidar = [fr["clouds"][0] for fr in synth.lidar_stream(seed=seed + 1, frames=2)]
+    return {"depth": depth, "lidar": lidar}
+
+
+def request_cloud(pools, robots, i, k):
+    pool = pools[robots[i]["kind"]]
+    return pool[(i + k) % len(pool)]
+
+
+# ---------------------------------------------------------------- our arm
 
 def run_ours(args, rank: int, world: int):
     import torch
@@ -145,114 +202,160 @@ def run_ours(args, rank: int, world: int):
 
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
-    pool = make_pool(args.frames, seed=2 + 100 * rank)
-    r = PARAMS["resolution"]
-    dpool = [[(torch.from_numpy(p).cuda(), q) for p, q in fr["clouds"]] for fr in pool]
-    pts_per_step = [sum(len(p) for p, _ in fr["clouds"]) for fr in pool]
-    m = em.Map(em.Params(**PARAMS), device=dev)
-    m.reserve(max(pts_per_step))
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
-    state = {"sx": 0, "sy": 0, "shift_launches": 0}
-
-    def step(i):
-        k = i % len(pool)
-        fr = pool[k]
-        dx = int(round(fr["xy"][0] / r)) - state["sx"]
-        dy = int(round(fr["xy"][1] / r)) - state["sy"]
-        if dx or dy:
-            m.shift(dx, dy)
-            state["sx"] += dx
-            state["sy"] += dy
-            state["shift_launches"] += 1
-        m.update_multi(dpool[k])
-        return pts_per_step[k]
+    hbm, sm_mhz_max, peak_kind = peaks()
 
     def barrier():
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
 
-    for i in range(args.warmup):
-        step(i)
-    barrier()
-
-    # ---- timed region: K steps, L2 flushed (untimed) before each
-    K = args.steps
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-    pts = 0
-    state["shift_launches"] = 0
-    with ClockSampler(dev) as clk:
-        t0 = time.perf_counter()
-        for i in range(K):
-            flush.zero_()
-            ev[i][0].record()
-            pts += step(args.warmup + i)
-            ev[i][1].record()
-        barrier()
-        wall = time.perf_counter() - t0
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    shift_launches = state["shift_launches"]
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], device="cuda", dtype=torch.float64)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = pts * world / (total_ms / 1e3)
+        return float(t.item())
 
-    # ---- per-kernel profile pass (same steps, events around every kernel)
-    m.profile(True)
-    for i in range(K if not args.no_profile else 1):
-        flush.zero_()
-        step(args.warmup + i)
-    prof = m.profile_read()
-    m.profile(False)
-    st = m.stats()
+    robots = make_fleet(seed=5 + 100 * rank)
+    pools = make_pools(seed=5 + 100 * rank)
+    dpools = {k: [(torch.from_numpy(p).cuda(), q) for p, q in v] for k, v in pools.items()}
+    round_pts = sum(len(request_cloud(pools, robots, i, 0)[0]) for i in range(N_ROBOTS))
 
-    # ---- end to end through the public API: host clouds in, elevation + variance out
-    host_pool = [fr["clouds"] for fr in pool]
-    me = em.Map(em.Params(**PARAMS), device=dev)
-    me.reserve(max(pts_per_step))
-    out_mask = em.LAYER_ELEVATION | em.LAYER_VARIANCE
-    for i in range(min(args.warmup, 3)):
-        me.update_host(host_pool[i % len(pool)])
-        me.get_layers(out_mask)
-    torch.cuda.synchronize()
-    e2e_pts = 0
-    t0 = time.perf_counter()
-    for i in range(K if not args.no_e2e else 1):
-        k = (args.warmup + i) % len(pool)
-        me.update_host(host_pool[k])
-        me.get_layers(out_mask)  # waits for the update: the published map
-        e2e_pts += pts_per_step[k]
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    bi = int(np.mean([sum(p.nbytes for p, _ in c) for c in host_pool]))
-    bo = 2 * PARAMS["width"] * PARAMS["height"] * 4
+    def new_server(mode):
+        srv = em.Server(budget_bytes=BUDGET, max_slots=4096, n_streams=args.streams, max_batch_maps=N_ROBOTS,
+                        max_batch_points=N_ROBOTS * 262144, max_map_cells=500 * 500, mode=mode, graph=True,
+                        device=dev)
+        ids = [srv.add_map(em.Params(**r["params"])) for r in robots]
+        return srv, ids
 
-    # ---- roofline of the dominant kernel
-    hbm, peak_kind = peaks()
-    n_pts = float(np.mean(pts_per_step))
-    in_map = st["points_in_map"] / max(1, st["updates"])
-    cells_upd = st["cells_updated"] / max(1, st["updates"])
-    ncell = PARAMS["width"] * PARAMS["height"]
-    alg_bytes = {  # algorithmic bytes per launch
-        "count": 12 * n_pts,
-        "ray": 12 * n_pts,
-        "scatter": 12 * n_pts + 8 * in_map,
-        "alloc": 4 * ncell + 12 * cells_upd,
-        "fuse": 8 * in_map + 24 * cells_upd,
-        "clear": ncell / 8,
-    }
-    dom = max((k for k in prof if prof[k][1] > 0), key=lambda k: prof[k][0])
-    dom_ms = prof[dom][0] / prof[dom][1]
-    achieved = alg_bytes.get(dom, 0.0) / (dom_ms * 1e-3) / 1e9
+    def submit_round(srv, ids, k):
+        return [srv.submit(ids[i], [request_cloud(dpools, robots, i, k)]) for i in range(N_ROBOTS)]
+
+    def saturate(srv, ids, K, k0):
+        """K rounds submitted at once; returns (seconds, points, results)."""
+        barrier()
+        t0 = time.perf_counter()
+        tickets = []
+        for k in range(K):
+            tickets += submit_round(srv, ids, k0 + k)
+        res = [srv.wait(t) for t in tickets]
+        barrier()
+        return max_over_ranks(time.perf_counter() - t0), K * round_pts, res
+
+    # ---- served path: autotune the batch shapes on one round (scratch copies of the maps)
+    served, sids = new_server(em.SERVE_BATCHED)
+    tuner = em.Batch(max_maps=N_ROBOTS, max_clouds=N_ROBOTS, max_points=N_ROBOTS * 262144, max_cells=500 * 500,
+                     graph=False, device=dev)
+    pairs = [(served.map(sids[i]), *request_cloud(dpools, robots, i, 0)) for i in range(N_ROBOTS)]
+    tuning = tuner.autotune(pairs, reps=3)
+    served.set_tuning(**tuning)
+    for k in range(args.warmup):
+        for t in submit_round(served, sids, k):
+            served.wait(t)
+    K = args.steps
+    with ClockSampler(dev) as clk:
+        sec, pts, res = saturate(served, sids, K, args.warmup)
+    value = pts * world / sec
+    sst = served.stats()
+
+    # ---- plain per-request path at saturation (fresh maps)
+    plain, pids = new_server(em.SERVE_PLAIN)
+    for k in range(args.warmup):
+        for t in submit_round(plain, pids, k):
+            plain.wait(t)
+    psec, ppts, _ = saturate(plain, pids, K, args.warmup)
+    plain_value = ppts * world / psec
+
+    # ---- latency at the stated load: Poisson arrivals, 2,000 updates/s in total
+    rng = np.random.default_rng(77 + rank)
+    n_req = int(RATE_HZ * args.load_seconds)
+    arrivals = np.cumsum(rng.exponential(1.0 / RATE_HZ, n_req))
+    who = rng.integers(0, N_ROBOTS, n_req)
+
+    def offered(srv, ids):
+        barrier()
+        counters = [0] * N_ROBOTS
+        tickets = []
+        t0 = time.perf_counter()
+        for a, i in zip(arrivals, who):
+            while time.perf_counter() - t0 < a:
+                pass
+            tickets.append(srv.submit(ids[i], [request_cloud(dpools, robots, int(i), counters[i])]))
+            counters[i] += 1
+        res = [srv.wait(t) for t in tickets]
+        span = time.perf_counter() - t0
+        lat = [(r["t_done_ns"] - r["t_submit_ns"]) / 1e6 for r in res]
+        bs = [r["batch_size"] for r in res]
+        npts = sum(r["points"] for r in res)
+        return {"p50": pct(lat, 0.50), "p99": pct(lat, 0.99), "mean": float(np.mean(lat)), "requests": n_req,
+                "points_per_s": npts / span, "mean_batch": float(np.mean(bs))}
+
+    lat_served = offered(served, sids)
+    lat_plain = offered(plain, pids)
+
+    # ---- per-kernel profile of one served round (event-timed, direct launches)
+    pmaps = [served.map(sids[i]) for i in range(N_ROBOTS)]
+    st0 = [m.stats() for m in pmaps]
+    tuner.set_tuning(**tuning)
+    tuner.profile(True)
+    P_STEPS = 3
+    for k in range(P_STEPS):
+        tuner.update([(pmaps[i], *request_cloud(dpools, robots, i, k)) for i in range(N_ROBOTS)])
+    prof = tuner.profile_read()
+    tuner.profile(False)
+    st1 = [m.stats() for m in pmaps]
+    samples = sum(b["ray_samples"] - a["ray_samples"] for a, b in zip(st0, st1)) / P_STEPS
+    cells_upd = sum(b["cells_updated"] - a["cells_updated"] for a, b in zip(st0, st1)) / P_STEPS
+    in_map = sum(b["points_in_map"] - a["points_in_map"] for a, b in zip(st0, st1)) / P_STEPS
+    total_ms = sum(v[0] for v in prof.values() if v[1])
     kernels = {em.KERNEL_NAMES[k]: {"ms_per_launch": round(v[0] / v[1], 5), "launches": v[1],
-                                    "share": round(v[0] / sum(x[0] for x in prof.values() if x[1]), 4)}
-               for k, v in prof.items() if v[1]}
-    upd_bytes = 12 * n_pts + 24 * cells_upd
-    gpu_launches = sum(v[1] for v in prof.values()) + shift_launches
+                                    "share": round(v[0] / total_ms, 4)} for k, v in prof.items() if v[1]}
+    dom = max((k for k in prof if prof[k][1]), key=lambda k: prof[k][0])
+    dom_s = prof[dom][0] / prof[dom][1] * 1e-3
+    cells_all = sum(r["params"]["width"] ** 2 for r in robots)
+    alg_bytes = {"count": 12 * round_pts, "scatter": 12 * round_pts + 8 * in_map, "fuse": 8 * in_map + 24 * cells_upd,
+                 "alloc": 4 * cells_all + 12 * cells_upd, "clear": cells_all / 8}
+    if dom == "ray":
+        alu_peak = 152 * 128 * sm_mhz_max * 1e6 / 1e12  # lane-ops per second, in Tops/s
+        achieved = samples * RAY_OPS_PER_SAMPLE / dom_s / 1e12
+        roofline = {"bound": "alu", "kernel": "k_ray", "achieved": achieved, "peak": alu_peak,
+                    "peak_kind": "derived: 152 SMs x 128 lanes x max SM clock", "unit": "Tops/s",
+                    "frac": achieved / alu_peak, "traffic": ncu_traffic("ray", "served_round"),
+                    "samples_per_launch": samples, "ops_per_sample": RAY_OPS_PER_SAMPLE,
+                    "samples_per_s": samples / dom_s}
+    else:
+        achieved = alg_bytes[dom] / dom_s / 1e9
+        roofline = {"bound": "hbm", "kernel": em.KERNEL_NAMES[dom], "achieved": achieved, "peak": hbm,
+                    "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm,
+                    "traffic": ncu_traffic(dom, "served_round")}
 
-    lat = sorted(step_ms)
+    # ---- end to end: host clouds (pinned) copied per request, every map read back per round
+    host = {k: [(torch.from_numpy(p).pin_memory(), q) for p, q in v] for k, v in pools.items()}
+    bufs = [torch.empty((262144, 3), dtype=torch.float32, device="cuda") for _ in range(N_ROBOTS)]
+    copy_stream = torch.cuda.Stream()
+    out_bytes = sum(r["params"]["width"] * r["params"]["height"] * 4 for r in robots)
+    e2e_rounds = max(3, K // 2)
+    barrier()
+    t0 = time.perf_counter()
+    for k in range(e2e_rounds):
+        tickets = []
+        for i in range(N_ROBOTS):
+            src, pose = request_cloud(host, robots, i, args.warmup + k)
+            dst = bufs[i][:src.shape[0]]
+            with torch.cuda.stream(copy_stream):
+                dst.copy_(src, non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(copy_stream)
+            tickets.append(served.submit(sids[i], [(dst, pose)], ready=ev))
+        for t in tickets:
+            served.wait(t)
+        for i in range(N_ROBOTS):
+            served.map(sids[i]).get_layers(em.LAYER_ELEVATION)
+    barrier()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e = {"value": e2e_rounds * round_pts * world / e2e_s, "unit": "points/s",
+           "h2d_bytes_per_step": int(round_pts * 12), "d2h_bytes_per_step": int(out_bytes)}
+
     result = {
         "metric": METRIC,
         "value": value,
@@ -260,114 +363,213 @@ def run_ours(args, rank: int, world: int):
         "n_gpus": world,
         "steps": K,
         "warmup": args.warmup,
-        "ms_per_step": total_ms / K,
+        "ms_per_step": sec / K * 1e3,
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f32",
-        "data": f"synthetic: seeded depth-camera stream, {len(pool)}-frame pool cycled",
-        "config": {"workload": WORKLOAD, "points_per_step": int(n_pts), "map_cells": ncell,
-                   "l2": "flushed before every timed step (256 MB write, not timed)", "parallelism": f"replicas{world}"},
-        "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
-                       "path": "plain em_update_multi per frame"},
-        "updates_per_s": K * world / (total_ms / 1e3),
-        "wall_s_bracket": wall,
-        "e2e": {"value": e2e_pts / e2e_s, "unit": "points/s", "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
-        "gpu_launches": int(gpu_launches),
-        "roofline": {"bound": "hbm", "kernel": em.KERNEL_NAMES[dom], "achieved": achieved, "peak": hbm,
-                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": ncu_traffic(dom, "depth_stream")},
-        "update_roofline": {"algorithmic_bytes": upd_bytes, "achieved_gbs": upd_bytes / (total_ms / K * 1e-3) / 1e9,
-                            "frac": upd_bytes / (total_ms / K * 1e-3) / 1e9 / hbm},
+        "data": "synthetic: seeded depth-camera and LiDAR clouds (pools of 8 and 2 clouds cycled), seeded terrain",
+        "config": {"workload": WORKLOAD, "robots": N_ROBOTS, "points_per_step": round_pts,
+                   "step": "one round = one request per robot", "streams": args.streams, "tuning": tuning,
+                   "l2": "inputs + map state per step > L2 (about 65 MB of clouds + 200 MB of maps), no flush",
+                   "parallelism": f"replicas{world}"},
+        "updates_per_s": K * N_ROBOTS * world / sec,
+        "plain_saturated": {"value": plain_value, "unit": "points/s", "updates_per_s": K * N_ROBOTS * world / psec},
+        "latency_ms": {"load_updates_per_s": RATE_HZ, "seconds": args.load_seconds,
+                       "served": lat_served, "plain": lat_plain},
+        "served_batches": {"batches": sst["batches"], "mean_batch": sst["batched_requests"] / max(1, sst["batches"]),
+                           "max_batch": sst["max_batch_size"], "peak_bytes": sst["peak_bytes"]},
+        "e2e": e2e,
+        "gpu_launches": int(sst["batches"]) * len([k for k in prof if prof[k][1]]),
+        "roofline": roofline,
         "kernels": kernels,
-        "stats_per_update": {"ray_samples": st["ray_samples"] / max(1, st["updates"]), "points_in_map": in_map,
-                             "cells_updated": cells_upd,
-                             "rejected": st["points_rejected"] / max(1, st["updates"]),
-                             "cleared": st["cells_cleared"] / max(1, st["updates"])},
+        "per_round": {"ray_samples": samples, "points_in_map": in_map, "cells_updated": cells_upd},
         "clocks": clk.summary(),
     }
+    served.close()
+    plain.close()
+    tuner.close()
+    if not args.served_only:
+        result["batched"] = run_batched(args, em, torch, dev, barrier, max_over_ranks, world)
+        result["depth_stream"] = run_depth(args, em, torch, dev)
     if rank == 0 and not args.no_cpu_baseline:
-        result["cpu_baseline"] = cpu_baseline(pool, budget_s=args.cpu_budget)
-    m.close()
-    me.close()
+        result["cpu_baseline"] = cpu_baseline(robots, pools, budget_s=args.cpu_budget)
     return result
 
 
-def cpu_baseline(pool, budget_s: float = 12.0) -> dict:
-    """The FP64 oracle, as it stands, on the host: whole frames of the same
-    stream until the time budget is used."""
+def run_batched(args, em, torch, dev, barrier, max_over_ranks, world):
+    """64 uneven maps, one batched update per step vs 64 sequential em_update."""
+    import synth
+    hbm, _, peak_kind = peaks()
+    work = synth.batch_clouds(seed=4, maps=64)
+    pts_step = sum(len(w["clouds"][0][0]) for w in work)
+    clouds = [(torch.from_numpy(w["clouds"][0][0]).cuda(), w["clouds"][0][1]) for w in work]
+
+    def fleet():
+        return [em.Map(em.Params(width=w["side"], height=w["side"], **BATCH_P), device=dev) for w in work]
+
+    maps = fleet()
+    max_cells = max(w["side"] ** 2 for w in work)
+    batch = em.Batch(max_maps=64, max_clouds=64, max_points=pts_step, max_cells=max_cells, graph=True, device=dev)
+    pairs = [(m, p, q) for m, (p, q) in zip(maps, clouds)]
+    tuning = batch.autotune(pairs, reps=3)
+    for _ in range(args.warmup):
+        batch.update(pairs)
+    K = args.steps
+    st0 = [m.stats() for m in maps]
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(K):
+        batch.update(pairs)
+    e1.record()
+    barrier()
+    sec = max_over_ranks(e0.elapsed_time(e1) / 1e3)
+    st1 = [m.stats() for m in maps]
+    cells = sum(b["cells_updated"] - a["cells_updated"] for a, b in zip(st0, st1)) / K
+    alg = 12 * pts_step + 24 * cells
+    # per-kernel shares of one batch (direct launches)
+    batch.profile(True)
+    for _ in range(3):
+        batch.update(pairs)
+    prof = batch.profile_read()
+    batch.profile(False)
+    total_ms = sum(v[0] for v in prof.values() if v[1])
+    kernels = {em.KERNEL_NAMES[k]: {"ms_per_launch": round(v[0] / v[1], 5), "share": round(v[0] / total_ms, 4)}
+               for k, v in prof.items() if v[1]}
+    # plain comparison: 64 sequential em_update on a second set of maps
+    pmaps = fleet()
+    for _ in range(args.warmup):
+        for m, (p, q) in zip(pmaps, clouds):
+            m.update(p, q)
+    barrier()
+    e0.record()
+    for _ in range(K):
+        for m, (p, q) in zip(pmaps, clouds):
+            m.update(p, q)
+    e1.record()
+    barrier()
+    psec = max_over_ranks(e0.elapsed_time(e1) / 1e3)
+    for m in maps + pmaps:
+        m.close()
+    batch.close()
+    return {"workload": "64 maps, side U{100..500} cells @ 0.04 m, 10k..400k points each (fusion, no ray march)",
+            "points_per_step": pts_step, "value": pts_step * K * world / sec, "unit": "points/s",
+            "ms_per_step": sec / K * 1e3, "updates_per_s": 64 * K * world / sec, "tuning": tuning,
+            "plain_sequential": {"value": pts_step * K * world / psec, "ms_per_step": psec / K * 1e3},
+            "update_roofline": {"bound": "hbm", "algorithmic_bytes": alg, "achieved": alg / (sec / K) / 1e9,
+                                "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
+                                "frac": alg / (sec / K) / 1e9 / hbm},
+            "kernels": kernels}
+
+
+def run_depth(args, em, torch, dev):
+    """Four depth cameras of one robot per frame into a 200x200 map (plain path)."""
+    import synth
+    pool = list(synth.depth_stream(seed=2, frames=3))
+    P = dict(DEPTH_P, width=200, height=200)
+    r = P["resolution"]
+    dpool = [[(torch.from_numpy(p).cuda(), q) for p, q in fr["clouds"]] for fr in pool]
+    pts = sum(len(p) for p, _ in pool[0]["clouds"])
+    m = em.Map(em.Params(**P), device=dev)
+    m.reserve(pts)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    sx = sy = 0
+    times = []
+    for i in range(args.warmup + args.steps):
+        fr = pool[i % len(pool)]
+        dx, dy = int(round(fr["xy"][0] / r)) - sx, int(round(fr["xy"][1] / r)) - sy
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        if dx or dy:
+            m.shift(dx, dy)
+            sx, sy = sx + dx, sy + dy
+        m.update_multi(dpool[i % len(pool)])
+        b.record()
+        times.append((a, b))
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in times[args.warmup:]]
+    m.close()
+    return {"workload": "4 x 76,800 depth points per frame, 200x200 map, shift + em_update_multi per frame",
+            "value": pts * len(ms) / (sum(ms) / 1e3), "unit": "points/s", "ms_per_step": float(np.mean(ms)),
+            "p50_ms": pct(ms, 0.5), "p99_ms": pct(ms, 0.99),
+            "l2": "flushed before every frame (256 MB write, not timed)"}
+
+
+def cpu_baseline(robots, pools, budget_s: float = 12.0) -> dict:
+    """The FP64 oracle, as it stands, on the host: the same requests (robots in
+    turn) until the time budget is used."""
     import oracle
-    om = oracle.OracleMap(oracle.Params(**{k: float(np.float32(v)) if isinstance(v, float) else v
-                                           for k, v in PARAMS.items()}))
-    r = PARAMS["resolution"]
+    oms = {}
     pts = 0
-    frames = 0
+    n = 0
     t0 = time.perf_counter()
-    while time.perf_counter() - t0 < budget_s and frames < 1000:
-        fr = pool[frames % len(pool)]
-        sx, sy = om.shift_xy
-        om.shift(int(round(fr["xy"][0] / r)) - sx, int(round(fr["xy"][1] / r)) - sy)
-        om.update(fr["clouds"])
-        pts += sum(len(p) for p, _ in fr["clouds"])
-        frames += 1
+    while time.perf_counter() - t0 < budget_s and n < 10000:
+        i = n % N_ROBOTS
+        if i not in oms:
+            oms[i] = oracle.OracleMap(oracle.Params(**f32params(robots[i]["params"])))
+        p, q = request_cloud(pools, robots, i, n // N_ROBOTS)
+        oms[i].update((p, q))
+        pts += len(p)
+        n += 1
     dt = time.perf_counter() - t0
     return {"value": pts / dt, "unit": "points/s", "cores": 1, "kind": "oracle",
-            "sample": f"{frames} whole frames of the same stream ({pts} points) in {dt:.1f} s, single thread"}
+            "sample": f"{n} requests of the served mix (robots in turn, {pts} points) in {dt:.1f} s, single thread"}
 
 
 def run_reference(args, rank: int, world: int):
-    """The oracle as the reference arm: K timed steps of whole frames on the host."""
+    """The oracle as the reference arm: one request of the served mix per step."""
     if rank != 0:
         return None
-    pool = make_pool(args.frames, seed=2)
+    robots = make_fleet(seed=5)
+    pools = make_pools(seed=5)
     import oracle
-    om = oracle.OracleMap(oracle.Params(**{k: float(np.float32(v)) if isinstance(v, float) else v
-                                           for k, v in PARAMS.items()}))
-    r = PARAMS["resolution"]
+    oms = {}
 
-    def step(i):
-        fr = pool[i % len(pool)]
-        sx, sy = om.shift_xy
-        om.shift(int(round(fr["xy"][0] / r)) - sx, int(round(fr["xy"][1] / r)) - sy)
-        om.update(fr["clouds"])
-        return sum(len(p) for p, _ in fr["clouds"])
+    def step(n):
+        i = (n * 7) % N_ROBOTS  # alternates depth and LiDAR robots
+        if i not in oms:
+            oms[i] = oracle.OracleMap(oracle.Params(**f32params(robots[i]["params"])))
+        p, q = request_cloud(pools, robots, i, n)
+        oms[i].update((p, q))
+        return len(p)
 
-    for i in range(args.warmup):
-        step(i)
+    for n in range(args.warmup):
+        step(n)
     pts = 0
     t0 = time.perf_counter()
-    for i in range(args.steps):
-        pts += step(args.warmup + i)
+    for n in range(args.steps):
+        pts += step(args.warmup + n)
     dt = time.perf_counter() - t0
     v = pts / dt
     return {"metric": METRIC, "impl": "reference", "value": v, "unit": "points/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic: seeded depth-camera stream", "config": {"workload": WORKLOAD},
+            "data": "synthetic: seeded depth-camera and LiDAR clouds",
+            "config": {"workload": WORKLOAD, "step": "one request"},
             "cpu_baseline": {"value": v, "unit": "points/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} whole frames, single thread"},
+                             "sample": f"{args.steps} requests of the served mix, single thread"},
             "e2e": {"value": v, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--frames", type=int, default=6, help="distinct frames generated and cycled")
+    ap.add_argument("--streams", type=int, default=2, help="batches in flight in the served path")
+    ap.add_argument("--load-seconds", type=float, default=2.0, help="duration of the Poisson-load phase")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-e2e", action="store_true", help="one e2e step only (for profiler runs)")
-    ap.add_argument("--no-profile", action="store_true", help="one event-profiled step only (for profiler runs)")
+    ap.add_argument("--served-only", action="store_true", help="skip the batched and depth-stream sub-results")
     args = ap.parse_args()
-    if args.warmup < 3:
-        args.warmup = 3
+    args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
-        if args.steps > 40:
-            args.steps = 40  # whole frames of the oracle: keep the run to a few minutes
+        args.steps = min(args.steps, 40)  # whole requests on one host core: a few minutes at most
         res = run_reference(args, rank, world)
         if res is not None:
             print(json.dumps(res), flush=True)

@@ -247,6 +247,12 @@ int em_update_batch(em_batch* batch, em_map* const* maps, const em_cloud* clouds
 int em_batch_set_tuning(em_batch* batch, const em_tuning* tuning);
 int em_batch_get_tuning(const em_batch* batch, em_tuning* tuning);
 
+/* Per-kernel CUDA-event timing of the batch's launches (EM_PROF_* slots, as
+ * em_profile / em_profile_read).  While enabled the batch launches kernels
+ * directly (no graph) and every update first waits for the previous one. */
+int em_batch_profile(em_batch* batch, int enable);
+int em_batch_profile_read(em_batch* batch, double* ms, int64_t* launches);
+
 /* Autotuner: times candidate launch shapes on this workload (median of `reps`
  * runs each, coordinate by coordinate) on scratch copies of the maps -- the
  * maps themselves are not changed -- and keeps the fastest.  Synchronous.
@@ -307,6 +313,12 @@ int em_server_map(em_server* srv, int32_t map_id, em_map** out);
  * descriptors; the points stay valid until the request completes).  Returns at
  * once with a ticket; EM_ERR_REJECTED when the request can never fit. */
 int em_server_submit(em_server* srv, int32_t map_id, const em_cloud* clouds, int32_t n_clouds, uint64_t* ticket);
+/* Same, but the request's GPU work first waits for `ready` (a cudaEvent_t
+ * recorded by the caller after it wrote the points, e.g. a host-to-device
+ * copy on its own stream).  The event must stay valid until the request
+ * completes. */
+int em_server_submit_after(em_server* srv, int32_t map_id, const em_cloud* clouds, int32_t n_clouds,
+                           void* ready, uint64_t* ticket);
 /* Wait for a ticket (timeout_us < 0: forever); EM_ERR_TIMEOUT when it has not
  * finished in time (the request stays queued).  Fills *out and forgets the
  * ticket once finished. */
@@ -316,6 +328,8 @@ int em_server_cancel(em_server* srv, uint64_t ticket);
 /* Wait until every submitted request has finished. */
 int em_server_drain(em_server* srv, int64_t timeout_us);
 int em_server_get_stats(em_server* srv, em_server_stats* out);
+/* Launch shapes of the server's batches (e.g. from em_batch_autotune); call while idle (after em_server_drain). */
+int em_server_set_tuning(em_server* srv, const em_tuning* tuning);
 int em_server_destroy(em_server* srv); /* NULL-safe: drains, stops the worker, frees the maps */
 
 /* ---- Update without allocation.

@@ -67,26 +67,65 @@ struct em_batch {
   // host scratch for grouping
   std::vector<int> first_of, order, map_of;
   std::vector<em_map*> uniq;
+  // per-kernel profiling
+  bool prof = false;
+  bool prof_pending = false;
+  cudaEvent_t pev[2 * EM_PROF_SLOTS] = {};
+  bool pused[EM_PROF_SLOTS] = {};
+  double pms[EM_PROF_SLOTS] = {};
+  int64_t pn[EM_PROF_SLOTS] = {};
 };
 
 namespace {
 
+// Events around one launch when the batch is profiling (prof may be null).
+template <class F>
+cudaError_t timed(em_batch* prof, int slot, cudaStream_t s, F fn) {
+  if (!prof || !prof->prof) return fn();
+  cudaEventRecord(prof->pev[2 * slot], s);
+  cudaError_t e = fn();
+  cudaEventRecord(prof->pev[2 * slot + 1], s);
+  prof->pused[slot] = true;
+  prof->prof_pending = true;
+  return e;
+}
+
+int prof_collect(em_batch* b) {
+  if (!b->prof_pending) return EM_OK;
+  b->prof_pending = false;
+  for (int k = 0; k < EM_PROF_SLOTS; ++k) {
+    if (!b->pused[k]) continue;
+    b->pused[k] = false;
+    EB_TRY(cudaEventSynchronize(b->pev[2 * k + 1]), "cudaEventSynchronize");
+    float ms = 0.f;
+    EB_TRY(cudaEventElapsedTime(&ms, b->pev[2 * k], b->pev[2 * k + 1]), "cudaEventElapsedTime");
+    b->pms[k] += ms;
+    b->pn[k] += 1;
+  }
+  return EM_OK;
+}
+
 // The kernel sequence of one update over the descriptor at `bd`.
 cudaError_t launch_sequence(const BatchDev* bd, int64_t grid_points, int32_t grid_maps, int32_t grid_cells,
-                            const GraphKey& k, cudaStream_t s) {
+                            const GraphKey& k, cudaStream_t s, em_batch* prof = nullptr) {
   cudaError_t e = cudaSuccess;
   const int32_t touched = grid_cells < grid_points ? grid_cells : (int32_t)grid_points;
   if (grid_points > 0) {
-    if (e == cudaSuccess) e = launch_bin(bd, grid_points, s);
-    if (e == cudaSuccess && k.ray) e = launch_ray(bd, grid_points, k.t.ray_group, s);
-    if (e == cudaSuccess) e = launch_alloc(bd, grid_maps, grid_cells, s);
-    if (e == cudaSuccess) e = launch_scatter(bd, grid_points, s);
-    if (e == cudaSuccess) e = launch_fuse(bd, grid_maps, touched, k.t.fuse_group, s);
+    if (e == cudaSuccess) e = timed(prof, EM_PROF_COUNT, s, [&] { return launch_bin(bd, grid_points, s); });
+    if (e == cudaSuccess && k.ray)
+      e = timed(prof, EM_PROF_RAY, s, [&] { return launch_ray(bd, grid_points, k.t.ray_group, s); });
+    if (e == cudaSuccess) e = timed(prof, EM_PROF_ALLOC, s, [&] { return launch_alloc(bd, grid_maps, grid_cells, s); });
+    if (e == cudaSuccess) e = timed(prof, EM_PROF_SCATTER, s, [&] { return launch_scatter(bd, grid_points, s); });
+    if (e == cudaSuccess)
+      e = timed(prof, EM_PROF_FUSE, s, [&] { return launch_fuse(bd, grid_maps, touched, k.t.fuse_group, s); });
   }
-  if (e == cudaSuccess) e = launch_clear(bd, grid_maps, grid_cells, s);
-  if (e == cudaSuccess && (k.stencils & EM_F_NORMALS)) e = launch_normals(bd, grid_maps, grid_cells, s);
-  if (e == cudaSuccess && (k.stencils & EM_F_SMOOTH)) e = launch_smooth(bd, grid_maps, grid_cells, s);
-  if (e == cudaSuccess && (k.stencils & EM_F_INPAINT)) e = launch_inpaint(bd, grid_maps, grid_cells, s);
+  if (e == cudaSuccess) e = timed(prof, EM_PROF_CLEAR, s, [&] { return launch_clear(bd, grid_maps, grid_cells, s); });
+  if (e == cudaSuccess && (k.stencils & EM_F_NORMALS))
+    e = timed(prof, EM_PROF_NORMALS, s, [&] { return launch_normals(bd, grid_maps, grid_cells, s); });
+  if (e == cudaSuccess && (k.stencils & EM_F_SMOOTH))
+    e = timed(prof, EM_PROF_SMOOTH, s, [&] { return launch_smooth(bd, grid_maps, grid_cells, s); });
+  if (e == cudaSuccess && (k.stencils & EM_F_INPAINT))
+    e = timed(prof, EM_PROF_INPAINT, s, [&] { return launch_inpaint(bd, grid_maps, grid_cells, s); });
   return e;
 }
 
@@ -233,6 +272,8 @@ int set_dev(int dev) {
 }
 
 void release(em_batch* b) {
+  for (int i = 0; i < 2 * EM_PROF_SLOTS; ++i)
+    if (b->pev[i]) cudaEventDestroy(b->pev[i]);
   for (int i = 0; i < kSlots; ++i) {
     if (b->graph[i]) cudaGraphExecDestroy(b->graph[i]);
     if (b->ev[i]) cudaEventDestroy(b->ev[i]);
@@ -295,17 +336,50 @@ int em_update_batch(em_batch* b, em_map* const* maps, const em_cloud* clouds, in
   int rc = set_dev(b->device);
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)stream;
+  if (b->prof) {
+    rc = prof_collect(b);
+    if (rc) return rc;
+  }
   Prepared p;
   rc = prepare(b, maps, clouds, count, b->tune, s, &p);
   if (rc) return rc;
-  if (b->flags & EM_BATCH_GRAPH) {
+  if ((b->flags & EM_BATCH_GRAPH) && !b->prof) {
     rc = run_graph(b, p, s);
   } else {
-    cudaError_t e = launch_sequence(p.bd, p.points, p.n_maps, p.cells, p.key, s);
+    cudaError_t e = launch_sequence(p.bd, p.points, p.n_maps, p.cells, p.key, s, b);
     rc = e == cudaSuccess ? EM_OK : map_record_error("batch launches", e);
   }
   finish(b, p, s);
   return rc;
+}
+
+int em_batch_profile(em_batch* b, int enable) {
+  if (!b) return EM_ERR_INVALID_ARG;
+  int rc = set_dev(b->device);
+  if (rc) return rc;
+  if (enable && !b->pev[0])
+    for (int i = 0; i < 2 * EM_PROF_SLOTS; ++i) EB_TRY(cudaEventCreate(&b->pev[i]), "cudaEventCreate");
+  if (!enable) {
+    rc = prof_collect(b);
+    if (rc) return rc;
+  }
+  if (enable && !b->prof)
+    for (int k = 0; k < EM_PROF_SLOTS; ++k) { b->pms[k] = 0.0; b->pn[k] = 0; }
+  b->prof = enable != 0;
+  return EM_OK;
+}
+
+int em_batch_profile_read(em_batch* b, double* ms, int64_t* launches) {
+  if (!b || !ms || !launches) return EM_ERR_INVALID_ARG;
+  int rc = set_dev(b->device);
+  if (rc) return rc;
+  rc = prof_collect(b);
+  if (rc) return rc;
+  for (int k = 0; k < EM_PROF_SLOTS; ++k) {
+    ms[k] = b->pms[k];
+    launches[k] = b->pn[k];
+  }
+  return EM_OK;
 }
 
 int em_batch_set_tuning(em_batch* b, const em_tuning* t) {

@@ -37,6 +37,7 @@ struct Request {
   std::vector<em_cloud> clouds;
   int64_t points = 0;
   int64_t bytes = 0;
+  cudaEvent_t ready = nullptr;  // the caller's "points written" event, or null
   ReqState state = kPending;
   em_result res{};
 };
@@ -143,7 +144,9 @@ bool worker_pass(em_server* s, std::unique_lock<std::mutex>& lk) {
       f.maps.clear();
       em_map* m = s->maps[r.map_id];
       std::vector<em_cloud> cl = r.clouds;
+      cudaEvent_t ready = r.ready;
       lk.unlock();
+      if (ready) cudaStreamWaitEvent(s->streams[0], ready, 0);
       int rc = em_update_multi(m, cl.data(), (int32_t)cl.size(), (em_stream_t)s->streams[0]);
       if (rc == EM_OK) cudaEventRecord(f.ev, s->streams[0]);
       lk.lock();
@@ -176,9 +179,11 @@ bool worker_pass(em_server* s, std::unique_lock<std::mutex>& lk) {
       if (take.empty()) break;
       std::vector<em_map*> pm;
       std::vector<em_cloud> pc;
+      std::vector<cudaEvent_t> ready;
       const int64_t t0 = now_ns();
       for (uint64_t tk : take) {
         Request& r = s->reqs[tk];
+        if (r.ready) ready.push_back(r.ready);
         r.state = kRunning;
         r.res.t_start_ns = t0;
         r.res.batch_size = (int32_t)take.size();
@@ -195,6 +200,7 @@ bool worker_pass(em_server* s, std::unique_lock<std::mutex>& lk) {
       s->st.batched_requests += (int64_t)take.size();
       if ((int64_t)take.size() > s->st.max_batch_size) s->st.max_batch_size = (int64_t)take.size();
       lk.unlock();
+      for (cudaEvent_t e : ready) cudaStreamWaitEvent(s->streams[si], e, 0);
       int rc = em_update_batch(s->batches[si], pm.data(), pc.data(), (int32_t)pc.size(), (em_stream_t)s->streams[si]);
       if (rc == EM_OK) cudaEventRecord(f.ev, s->streams[si]);
       lk.lock();
@@ -315,6 +321,11 @@ int em_server_map(em_server* s, int32_t map_id, em_map** out) {
 }
 
 int em_server_submit(em_server* s, int32_t map_id, const em_cloud* clouds, int32_t n_clouds, uint64_t* ticket) {
+  return em_server_submit_after(s, map_id, clouds, n_clouds, nullptr, ticket);
+}
+
+int em_server_submit_after(em_server* s, int32_t map_id, const em_cloud* clouds, int32_t n_clouds, void* ready,
+                           uint64_t* ticket) {
   if (!s || !clouds || n_clouds < 1 || n_clouds > 8 || !ticket) return EM_ERR_INVALID_ARG;
   int64_t pts = 0;
   for (int i = 0; i < n_clouds; ++i) {
@@ -341,6 +352,7 @@ int em_server_submit(em_server* s, int32_t map_id, const em_cloud* clouds, int32
   r.clouds.assign(clouds, clouds + n_clouds);
   r.points = pts;
   r.bytes = bytes;
+  r.ready = (cudaEvent_t)ready;
   r.res.map_id = map_id;
   r.res.points = pts;
   r.res.t_submit_ns = now_ns();
@@ -417,6 +429,16 @@ int em_server_get_stats(em_server* s, em_server_stats* out) {
   *out = s->st;
   out->bytes_in_use = s->bytes_in_use;
   out->slots_in_use = s->slots_in_use;
+  return EM_OK;
+}
+
+int em_server_set_tuning(em_server* s, const em_tuning* t) {
+  if (!s || !t) return EM_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  for (em_batch* b : s->batches) {
+    int rc = em_batch_set_tuning(b, t);
+    if (rc) return rc;
+  }
   return EM_OK;
 }
 

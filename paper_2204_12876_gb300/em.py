@@ -410,6 +410,8 @@ def _bind_server():
         "em_server_add_map": ([vp, ctypes.POINTER(_Params), ctypes.POINTER(i32)], ctypes.c_int),
         "em_server_map": ([vp, i32, ctypes.POINTER(vp)], ctypes.c_int),
         "em_server_submit": ([vp, i32, ctypes.POINTER(_Cloud), i32, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+        "em_server_submit_after": ([vp, i32, ctypes.POINTER(_Cloud), i32, vp, ctypes.POINTER(ctypes.c_uint64)],
+                                   ctypes.c_int),
         "em_server_wait": ([vp, ctypes.c_uint64, i64, ctypes.POINTER(_Result)], ctypes.c_int),
         "em_server_cancel": ([vp, ctypes.c_uint64], ctypes.c_int),
         "em_server_drain": ([vp, i64], ctypes.c_int),
@@ -473,12 +475,17 @@ class Server:
         _check(lib.em_server_map(self._h, int(map_id), ctypes.byref(h)), "em_server_map")
         return _MapView(h, self._params[map_id])
 
-    def submit(self, map_id: int, clouds) -> int:
-        """clouds: [(points CUDA tensor, pose), ...]; tensors are kept alive until the ticket is waited."""
+    def submit(self, map_id: int, clouds, ready=None) -> int:
+        """clouds: [(points CUDA tensor, pose), ...]; tensors are kept alive until the ticket is waited.
+        ready: optional torch.cuda.Event recorded after the points were written."""
         arr = (_Cloud * len(clouds))(*[_cloud_struct(p, q, False) for p, q in clouds])
         tk = ctypes.c_uint64()
-        _check(lib.em_server_submit(self._h, int(map_id), arr, len(clouds), ctypes.byref(tk)), "em_server_submit")
-        self._keep[tk.value] = clouds
+        if ready is None:
+            _check(lib.em_server_submit(self._h, int(map_id), arr, len(clouds), ctypes.byref(tk)), "em_server_submit")
+        else:
+            _check(lib.em_server_submit_after(self._h, int(map_id), arr, len(clouds), ready.cuda_event,
+                                              ctypes.byref(tk)), "em_server_submit_after")
+        self._keep[tk.value] = (clouds, ready)
         return tk.value
 
     def wait(self, ticket: int, timeout_us: int = -1) -> dict:
@@ -498,3 +505,41 @@ class Server:
         s = _ServerStats()
         _check(lib.em_server_get_stats(self._h, ctypes.byref(s)), "em_server_get_stats")
         return {f: getattr(s, f) for f, _ in _ServerStats._fields_}
+
+
+def _bind_extra():
+    vp = ctypes.c_void_p
+    sig = {
+        "em_batch_profile": ([vp, ctypes.c_int], ctypes.c_int),
+        "em_batch_profile_read": ([vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+        "em_server_set_tuning": ([vp, ctypes.POINTER(_Tuning)], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+
+
+_bind_extra()
+
+
+def _batch_profile(self, enable: bool = True):
+    _check(lib.em_batch_profile(self._h, 1 if enable else 0), "em_batch_profile")
+
+
+def _batch_profile_read(self) -> dict:
+    ms = (ctypes.c_double * len(PROF_SLOTS))()
+    n = (ctypes.c_int64 * len(PROF_SLOTS))()
+    _check(lib.em_batch_profile_read(self._h, ms, n), "em_batch_profile_read")
+    return {k: (ms[i], n[i]) for i, k in enumerate(PROF_SLOTS)}
+
+
+def _server_set_tuning(self, ray_group: int, fuse_group: int, big_thresh: int):
+    """Call while the server is idle (after drain)."""
+    t = _Tuning(ray_group, fuse_group, big_thresh)
+    _check(lib.em_server_set_tuning(self._h, ctypes.byref(t)), "em_server_set_tuning")
+
+
+Batch.profile = _batch_profile
+Batch.profile_read = _batch_profile_read
+Server.set_tuning = _server_set_tuning
