@@ -560,10 +560,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--streams", type=int, default=2, help="batches in flight in the served path")
-    ap.add_argument("--load-seconds", type=float, default=2.0, help="duration of the Poisson-load phase")
+    ap.add_argument("--load-seconds", type=float, default=4.0, help="duration of the Poisson-load phase")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--served-only", action="store_true", help="skip the batched and depth-stream sub-results")
+    ap.add_argument("--workload", default="all", choices=["all", "batched", "depth"],
+                    help="batched / depth: run only that sub-result (for profiler runs)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -577,6 +579,23 @@ def main():
     if world > 1:
         import torch
         torch.distributed.init_process_group("nccl")
+    if args.workload != "all":  # one sub-result alone (profiler runs)
+        import torch
+        from paper_2204_12876_gb300 import build
+        build.build()
+        from paper_2204_12876_gb300 import em
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+
+        def barrier():
+            torch.cuda.synchronize()
+
+        if args.workload == "batched":
+            res = run_batched(args, em, torch, 0, barrier, lambda x: x, 1)
+        else:
+            res = run_depth(args, em, torch, 0)
+        if rank == 0:
+            print(json.dumps(res), flush=True)
+        return
     res = run_ours(args, rank, world)
     if rank == 0:
         print(json.dumps(res), flush=True)

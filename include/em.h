@@ -226,9 +226,10 @@ enum { EM_BATCH_GRAPH = 1u << 0 };
 
 /* Launch shapes picked by the autotuner (or set by hand). */
 typedef struct em_tuning {
-  int32_t ray_group;   /* lanes per ray in the ray march: 1, 2, 4, 8, 16 or 32 */
-  int32_t fuse_group;  /* lanes per small cell in the fusion: 4, 8, 16 or 32 */
-  int32_t big_thresh;  /* cells with more records are fused by a whole block, >= 1 */
+  int32_t ray_group;    /* lanes per ray in the ray march: 1, 2, 4, 8, 16 or 32 */
+  int32_t fuse_group;   /* lanes per medium cell in the fusion: 4, 8, 16 or 32 */
+  int32_t big_thresh;   /* cells with more records are fused by a whole block, >= 32 */
+  int32_t small_thresh; /* cells with at most this many records take one thread, >= 4, <= big_thresh */
 } em_tuning;
 
 /* Capacities: at most max_maps distinct maps, max_clouds clouds and

@@ -70,10 +70,9 @@ struct em_map {
   float* thr = nullptr;
   int32_t* cnt = nullptr;
   int32_t* cell_base = nullptr;
-  int32_t* touched = nullptr;
-  int32_t* seg_base = nullptr;
-  int32_t* seg_len = nullptr;
+  int32_t* cell_len = nullptr;
   MapCtl* ctl = nullptr;
+  BatchCtl* bctl = nullptr;
   // geometry
   int32_t ox = 0, oy = 0;
   int64_t shift_x = 0, shift_y = 0;
@@ -85,6 +84,8 @@ struct em_map {
   int32_t* tr_ix = nullptr;
   int32_t* tr_iy = nullptr;
   uint8_t* tr_status = nullptr;
+  int2* med_list = nullptr;
+  int2* big_list = nullptr;
   int64_t last_n = 0;
   // descriptors
   unsigned char* desc_host = nullptr;
@@ -105,6 +106,7 @@ struct em_map {
   int fuse_group = 8;
   int ray_group = 2;
   int big_thresh = 64;
+  int small_thresh = 8;
   int64_t points_in = 0;
   // per-kernel profiling
   bool prof = false;
@@ -128,8 +130,9 @@ MapDev make_mapdev(const em_map* m) {
   memset(&d, 0, sizeof(d));
   d.h = m->h; d.var = m->var; d.t_last = m->t_last;
   d.nx = m->nx; d.ny = m->ny; d.nz = m->nz; d.smooth = m->smooth; d.inpaint = m->inpaint;
-  d.mark = m->mark; d.thr = m->thr; d.cnt = m->cnt; d.cell_base = m->cell_base; d.touched = m->touched;
-  d.seg_base = m->seg_base; d.seg_len = m->seg_len; d.ctl = m->ctl;
+  d.mark = m->mark; d.thr = m->thr; d.cnt = m->cnt; d.cell_base = m->cell_base; d.cell_len = m->cell_len;
+  d.ctl = m->ctl;
+  d.cell_begin = 0;
   d.W = m->p.width; d.H = m->p.height; d.ox = m->ox; d.oy = m->oy;
   double x0, y0;
   host_origin(m, &x0, &y0);
@@ -140,7 +143,6 @@ MapDev make_mapdev(const em_map* m) {
   d.v_out = m->p.outlier_variance; d.sigma_t2 = m->p.time_variance; d.ray_step = m->p.ray_step;
   d.alpha_n = m->p.cleanup_normal_thresh; d.wall = m->p.wall_num_thresh; d.min_age = m->p.cleanup_min_age;
   d.flags = m->p.flags;
-  d.big_thresh = m->big_thresh;
   return d;
 }
 
@@ -163,7 +165,9 @@ bool params_ok(const em_params* p) {
 void free_workspace(em_map* m) {
   cudaFree(m->zw_sorted); cudaFree(m->idx_sorted);
   cudaFree(m->tr_ix); cudaFree(m->tr_iy); cudaFree(m->tr_status);
+  cudaFree(m->med_list); cudaFree(m->big_list);
   m->zw_sorted = nullptr; m->idx_sorted = nullptr; m->tr_ix = m->tr_iy = nullptr; m->tr_status = nullptr;
+  m->med_list = m->big_list = nullptr;
   m->cap = 0;
   m->work_bytes = 0;
 }
@@ -179,6 +183,8 @@ int grow_workspace(em_map* m, int64_t n) {
   const bool trace = (m->p.flags & EM_F_TRACE) != 0;
   int64_t tot = 0;
   EM_TRY(dev_alloc(&m->zw_sorted, (size_t)want, &tot), "alloc workspace");
+  EM_TRY(dev_alloc(&m->med_list, (size_t)med_list_cap(want), &tot), "alloc workspace");
+  EM_TRY(dev_alloc(&m->big_list, (size_t)big_list_cap(want), &tot), "alloc workspace");
   if (trace) {
     EM_TRY(dev_alloc(&m->idx_sorted, (size_t)want, &tot), "alloc trace");
     EM_TRY(dev_alloc(&m->tr_ix, (size_t)want, &tot), "alloc trace");
@@ -196,8 +202,8 @@ void release(em_map* m) {
     if (m->prof_ev[i]) cudaEventDestroy(m->prof_ev[i]);
   cudaFree(m->h); cudaFree(m->var); cudaFree(m->t_last);
   cudaFree(m->nx); cudaFree(m->ny); cudaFree(m->nz); cudaFree(m->smooth); cudaFree(m->inpaint);
-  cudaFree(m->mark); cudaFree(m->thr); cudaFree(m->cnt); cudaFree(m->cell_base); cudaFree(m->touched);
-  cudaFree(m->seg_base); cudaFree(m->seg_len); cudaFree(m->ctl);
+  cudaFree(m->mark); cudaFree(m->thr); cudaFree(m->cnt); cudaFree(m->cell_base); cudaFree(m->cell_len);
+  cudaFree(m->ctl); cudaFree(m->bctl);
   free_workspace(m);
   cudaFree(m->desc_dev);
   cudaFreeHost(m->desc_host);
@@ -258,6 +264,14 @@ int upload_desc(em_map* m, const em_cloud* clouds, int32_t n_clouds, int64_t tot
   b->tr_ix = m->tr_ix;
   b->tr_iy = m->tr_iy;
   b->tr_status = m->tr_status;
+  b->n_cells = pad_tile((int64_t)m->p.width * m->p.height);
+  b->ctl = m->bctl;
+  b->med_list = m->med_list;
+  b->big_list = m->big_list;
+  b->med_cap = (int32_t)med_list_cap(m->cap);
+  b->big_cap = (int32_t)big_list_cap(m->cap);
+  b->small_thresh = m->small_thresh;
+  b->big_thresh = m->big_thresh;
   const size_t bytes = sizeof(BatchDev) + sizeof(MapDev) + (size_t)n_clouds * sizeof(CloudDev);
   EM_TRY(cudaMemcpyAsync(db, hb, bytes, cudaMemcpyHostToDevice, s), "upload descriptor");
   *out = reinterpret_cast<const BatchDev*>(db);
@@ -302,12 +316,10 @@ uint32_t map_flags(const em_map* m) { return m->p.flags; }
 int32_t map_cells(const em_map* m) { return m->p.width * m->p.height; }
 const em_params& map_params(const em_map* m) { return m->p; }
 
-MapDev map_begin_update(em_map* m, int64_t points, int big_thresh) {
+MapDev map_begin_update(em_map* m, int64_t points) {
   m->t_now += 1;
   m->points_in += points;
-  MapDev d = make_mapdev(m);
-  d.big_thresh = big_thresh;
-  return d;
+  return make_mapdev(m);
 }
 
 void map_end_update(em_map* m, cudaStream_t s, int64_t points) {
@@ -384,13 +396,14 @@ int em_create(const em_params* params, int device, em_map** out) {
   if (params->flags & EM_F_SMOOTH) { EM_ALLOC(m->smooth, nc) }
   if (params->flags & EM_F_INPAINT) { EM_ALLOC(m->inpaint, nc) }
   EM_ALLOC(m->mark, (nc + 31) / 32) EM_ALLOC(m->thr, nc) EM_ALLOC(m->cnt, nc) EM_ALLOC(m->cell_base, nc)
-  EM_ALLOC(m->touched, nc) EM_ALLOC(m->seg_base, nc) EM_ALLOC(m->seg_len, nc) EM_ALLOC(m->ctl, 1)
+  EM_ALLOC(m->cell_len, nc) EM_ALLOC(m->ctl, 1) EM_ALLOC(m->bctl, 1)
   EM_ALLOC(m->desc_dev, kDescBytes * kSlots)
 #undef EM_ALLOC
   if (e == cudaSuccess) e = cudaMallocHost((void**)&m->desc_host, kDescBytes * kSlots);
   for (int i = 0; i < kSlots && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&m->desc_ev[i], cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->stage_ev, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMemset(m->ctl, 0, sizeof(MapCtl));
+  if (e == cudaSuccess) e = cudaMemset(m->bctl, 0, sizeof(BatchCtl));
   if (e == cudaSuccess) e = cuda_status(launch_fill_map(make_mapdev(m), nullptr), "fill") ? cudaErrorUnknown : cudaSuccess;
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
@@ -410,8 +423,13 @@ int em_create(const em_params* params, int device, em_map** out) {
   }
   if (const char* g = getenv("EM_BIG_THRESH")) {
     int v = atoi(g);
-    if (v >= 1) m->big_thresh = v;
+    if (v >= kMinBig) m->big_thresh = v;
   }
+  if (const char* g = getenv("EM_SMALL_THRESH")) {
+    int v = atoi(g);
+    if (v >= kMinSmall) m->small_thresh = v;
+  }
+  if (m->big_thresh < m->small_thresh) m->big_thresh = m->small_thresh;
   *out = m;
   return EM_OK;
 }
@@ -447,22 +465,21 @@ static int update_impl(em_map* m, const em_cloud* clouds, int32_t n_clouds, cuda
     m->t_now -= 1;
     return slot;
   }
-  const int32_t ncell = m->p.width * m->p.height;
+  const int64_t ncell = pad_tile((int64_t)m->p.width * m->p.height);
+  EM_TRY(timed(m, EM_PROF_COUNT, s, [&] { return launch_bin(bd, total, ncell, s); }), "k_count");
   if (total > 0) {
-    const int32_t max_touched = ncell < total ? ncell : (int32_t)total;
-    EM_TRY(timed(m, EM_PROF_COUNT, s, [&] { return launch_bin(bd, total, s); }), "k_count");
     if (m->p.ray_step > 0.f) EM_TRY(timed(m, EM_PROF_RAY, s, [&] { return launch_ray(bd, total, m->ray_group, s); }), "k_ray");
-    EM_TRY(timed(m, EM_PROF_ALLOC, s, [&] { return launch_alloc(bd, 1, ncell, s); }), "k_alloc");
+    EM_TRY(timed(m, EM_PROF_ALLOC, s, [&] { return launch_alloc(bd, ncell, s); }), "k_alloc");
     EM_TRY(timed(m, EM_PROF_SCATTER, s, [&] { return launch_scatter(bd, total, s); }), "k_scatter");
-    EM_TRY(timed(m, EM_PROF_FUSE, s, [&] { return launch_fuse(bd, 1, max_touched, m->fuse_group, s); }), "k_fuse");
+    EM_TRY(timed(m, EM_PROF_FUSE, s, [&] { return launch_fuse(bd, ncell, total, m->fuse_group, s); }), "k_fuse");
   }
-  EM_TRY(timed(m, EM_PROF_CLEAR, s, [&] { return launch_clear(bd, 1, ncell, s); }), "k_clear");
+  EM_TRY(timed(m, EM_PROF_CLEAR, s, [&] { return launch_clear(bd, ncell, s); }), "k_clear");
   if (m->p.flags & EM_F_NORMALS)
-    EM_TRY(timed(m, EM_PROF_NORMALS, s, [&] { return launch_normals(bd, 1, ncell, s); }), "k_normals");
+    EM_TRY(timed(m, EM_PROF_NORMALS, s, [&] { return launch_normals(bd, ncell, s); }), "k_normals");
   if (m->p.flags & EM_F_SMOOTH)
-    EM_TRY(timed(m, EM_PROF_SMOOTH, s, [&] { return launch_smooth(bd, 1, ncell, s); }), "k_smooth");
+    EM_TRY(timed(m, EM_PROF_SMOOTH, s, [&] { return launch_smooth(bd, ncell, s); }), "k_smooth");
   if (m->p.flags & EM_F_INPAINT)
-    EM_TRY(timed(m, EM_PROF_INPAINT, s, [&] { return launch_inpaint(bd, 1, ncell, s); }), "k_inpaint");
+    EM_TRY(timed(m, EM_PROF_INPAINT, s, [&] { return launch_inpaint(bd, ncell, s); }), "k_inpaint");
   EM_TRY(cudaEventRecord(m->desc_ev[slot], s), "cudaEventRecord");
   m->last_stream = s;
   m->last_n = total;

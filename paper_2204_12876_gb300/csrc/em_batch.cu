@@ -3,7 +3,7 @@
 // Every kernel of the update already works on a list of maps and clouds (the
 // device descriptor), so a batch is the same launch sequence as one em_update
 // with more maps in the descriptor: per-point kernels span all clouds of all
-// maps, per-cell kernels use a 2D grid (y = map).  With EM_BATCH_GRAPH the
+// maps, per-cell kernels walk the tiles of all maps' cells.  With EM_BATCH_GRAPH the
 // sequence is captured once per descriptor slot (grids sized from the batch
 // capacities) and replayed by one cudaGraphLaunch.
 #include <cuda_runtime.h>
@@ -33,7 +33,7 @@ constexpr int kSlots = 3;
 bool tuning_ok(const em_tuning& t) {
   const int r = t.ray_group, f = t.fuse_group;
   return (r == 1 || r == 2 || r == 4 || r == 8 || r == 16 || r == 32) && (f == 4 || f == 8 || f == 16 || f == 32) &&
-         t.big_thresh >= 1;
+         t.small_thresh >= kMinSmall && t.big_thresh >= kMinBig && t.big_thresh >= t.small_thresh;
 }
 
 // what a captured graph depends on besides the slot
@@ -43,7 +43,7 @@ struct GraphKey {
   uint32_t stencils;
   bool operator==(const GraphKey& o) const {
     return t.ray_group == o.t.ray_group && t.fuse_group == o.t.fuse_group && t.big_thresh == o.t.big_thresh &&
-           ray == o.ray && stencils == o.stencils;
+           t.small_thresh == o.t.small_thresh && ray == o.ray && stencils == o.stencils;
   }
 };
 
@@ -55,12 +55,15 @@ struct em_batch {
   int64_t max_points = 0;
   uint32_t flags = 0;
   float2* zw_sorted = nullptr;
+  BatchCtl* bctl = nullptr;
+  int2* med_list = nullptr;
+  int2* big_list = nullptr;
   size_t desc_bytes = 0;
   unsigned char* desc_host = nullptr;
   unsigned char* desc_dev = nullptr;
   cudaEvent_t ev[kSlots] = {};
   int slot = 0;
-  em_tuning tune{2, 8, 64};
+  em_tuning tune{2, 8, 64, 8};
   cudaStream_t capture_stream = nullptr;
   cudaGraphExec_t graph[kSlots] = {};
   GraphKey graph_key[kSlots] = {};
@@ -106,26 +109,25 @@ int prof_collect(em_batch* b) {
 }
 
 // The kernel sequence of one update over the descriptor at `bd`.
-cudaError_t launch_sequence(const BatchDev* bd, int64_t grid_points, int32_t grid_maps, int32_t grid_cells,
-                            const GraphKey& k, cudaStream_t s, em_batch* prof = nullptr) {
+cudaError_t launch_sequence(const BatchDev* bd, int64_t grid_points, int64_t grid_cells, const GraphKey& k,
+                            cudaStream_t s, em_batch* prof = nullptr) {
   cudaError_t e = cudaSuccess;
-  const int32_t touched = grid_cells < grid_points ? grid_cells : (int32_t)grid_points;
+  e = timed(prof, EM_PROF_COUNT, s, [&] { return launch_bin(bd, grid_points, grid_cells, s); });
   if (grid_points > 0) {
-    if (e == cudaSuccess) e = timed(prof, EM_PROF_COUNT, s, [&] { return launch_bin(bd, grid_points, s); });
     if (e == cudaSuccess && k.ray)
       e = timed(prof, EM_PROF_RAY, s, [&] { return launch_ray(bd, grid_points, k.t.ray_group, s); });
-    if (e == cudaSuccess) e = timed(prof, EM_PROF_ALLOC, s, [&] { return launch_alloc(bd, grid_maps, grid_cells, s); });
+    if (e == cudaSuccess) e = timed(prof, EM_PROF_ALLOC, s, [&] { return launch_alloc(bd, grid_cells, s); });
     if (e == cudaSuccess) e = timed(prof, EM_PROF_SCATTER, s, [&] { return launch_scatter(bd, grid_points, s); });
     if (e == cudaSuccess)
-      e = timed(prof, EM_PROF_FUSE, s, [&] { return launch_fuse(bd, grid_maps, touched, k.t.fuse_group, s); });
+      e = timed(prof, EM_PROF_FUSE, s, [&] { return launch_fuse(bd, grid_cells, grid_points, k.t.fuse_group, s); });
   }
-  if (e == cudaSuccess) e = timed(prof, EM_PROF_CLEAR, s, [&] { return launch_clear(bd, grid_maps, grid_cells, s); });
+  if (e == cudaSuccess) e = timed(prof, EM_PROF_CLEAR, s, [&] { return launch_clear(bd, grid_cells, s); });
   if (e == cudaSuccess && (k.stencils & EM_F_NORMALS))
-    e = timed(prof, EM_PROF_NORMALS, s, [&] { return launch_normals(bd, grid_maps, grid_cells, s); });
+    e = timed(prof, EM_PROF_NORMALS, s, [&] { return launch_normals(bd, grid_cells, s); });
   if (e == cudaSuccess && (k.stencils & EM_F_SMOOTH))
-    e = timed(prof, EM_PROF_SMOOTH, s, [&] { return launch_smooth(bd, grid_maps, grid_cells, s); });
+    e = timed(prof, EM_PROF_SMOOTH, s, [&] { return launch_smooth(bd, grid_cells, s); });
   if (e == cudaSuccess && (k.stencils & EM_F_INPAINT))
-    e = timed(prof, EM_PROF_INPAINT, s, [&] { return launch_inpaint(bd, grid_maps, grid_cells, s); });
+    e = timed(prof, EM_PROF_INPAINT, s, [&] { return launch_inpaint(bd, grid_cells, s); });
   return e;
 }
 
@@ -133,7 +135,8 @@ struct Prepared {
   const BatchDev* bd = nullptr;
   int slot = -1;
   int64_t points = 0;
-  int32_t n_maps = 0, cells = 0;
+  int32_t n_maps = 0;
+  int64_t cells = 0;  // padded size of the cell space
   GraphKey key{};
 };
 
@@ -180,16 +183,17 @@ int prepare(em_batch* b, em_map* const* maps, const em_cloud* clouds, int32_t co
   CloudDev* cd = reinterpret_cast<CloudDev*>(hb + sizeof(BatchDev) + (size_t)b->max_maps * sizeof(MapDev));
   memset(bd, 0, sizeof(BatchDev));
   GraphKey key{tune, false, 0u};
-  int32_t cells = 0;
+  int64_t cells = 0;
   int64_t rec = 0;
   for (int u = 0; u < nm; ++u) {
-    md[u] = map_begin_update(b->uniq[u], map_pts[u], tune.big_thresh);
+    md[u] = map_begin_update(b->uniq[u], map_pts[u]);
     md[u].pt_begin = rec;
     md[u].pt_count = map_pts[u];
+    md[u].cell_begin = cells;
     rec += map_pts[u];
+    cells += pad_tile(map_cells(b->uniq[u]));
     key.ray |= md[u].ray_step > 0.f;
     key.stencils |= map_flags(b->uniq[u]) & (EM_F_NORMALS | EM_F_SMOOTH | EM_F_INPAINT);
-    cells = std::max(cells, map_cells(b->uniq[u]));
   }
   // clouds ordered by map (stable), so each map's points are contiguous
   int ci = 0;
@@ -216,6 +220,14 @@ int prepare(em_batch* b, em_map* const* maps, const em_cloud* clouds, int32_t co
   bd->maps = reinterpret_cast<const MapDev*>(db + sizeof(BatchDev));
   bd->clouds = reinterpret_cast<const CloudDev*>(db + sizeof(BatchDev) + (size_t)b->max_maps * sizeof(MapDev));
   bd->zw_sorted = b->zw_sorted;
+  bd->n_cells = cells;
+  bd->ctl = b->bctl;
+  bd->med_list = b->med_list;
+  bd->big_list = b->big_list;
+  bd->med_cap = (int32_t)med_list_cap(b->max_points);
+  bd->big_cap = (int32_t)big_list_cap(b->max_points);
+  bd->small_thresh = tune.small_thresh;
+  bd->big_thresh = tune.big_thresh;
   // upload header + maps, and the clouds at their fixed offset
   cudaError_t e = cudaMemcpyAsync(db, hb, sizeof(BatchDev) + (size_t)nm * sizeof(MapDev), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
@@ -247,7 +259,8 @@ int run_graph(em_batch* b, const Prepared& p, cudaStream_t s) {
     }
     cudaGraph_t g = nullptr;
     EB_TRY(cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-    cudaError_t le = launch_sequence(p.bd, b->max_points, b->max_maps, b->max_cells, p.key, b->capture_stream);
+    cudaError_t le = launch_sequence(p.bd, b->max_points, (int64_t)b->max_maps * pad_tile(b->max_cells), p.key,
+                                     b->capture_stream);
     cudaError_t ce = cudaStreamEndCapture(b->capture_stream, &g);
     if (le != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
@@ -280,6 +293,9 @@ void release(em_batch* b) {
   }
   if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
   cudaFree(b->zw_sorted);
+  cudaFree(b->bctl);
+  cudaFree(b->med_list);
+  cudaFree(b->big_list);
   cudaFree(b->desc_dev);
   cudaFreeHost(b->desc_host);
   delete b;
@@ -311,6 +327,10 @@ int em_batch_create(int device, int32_t max_maps, int32_t max_clouds, int64_t ma
   b->desc_bytes = (sizeof(BatchDev) + (size_t)max_maps * sizeof(MapDev) + (size_t)max_clouds * sizeof(CloudDev) + 255) &
                   ~size_t(255);
   cudaError_t e = cudaMalloc((void**)&b->zw_sorted, (size_t)(max_points > 0 ? max_points : 1) * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->bctl, sizeof(BatchCtl));
+  if (e == cudaSuccess) e = cudaMemset(b->bctl, 0, sizeof(BatchCtl));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->med_list, (size_t)med_list_cap(max_points) * sizeof(int2));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->big_list, (size_t)big_list_cap(max_points) * sizeof(int2));
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->desc_dev, b->desc_bytes * kSlots);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&b->desc_host, b->desc_bytes * kSlots);
   for (int i = 0; i < kSlots && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&b->ev[i], cudaEventDisableTiming);
@@ -346,7 +366,7 @@ int em_update_batch(em_batch* b, em_map* const* maps, const em_cloud* clouds, in
   if ((b->flags & EM_BATCH_GRAPH) && !b->prof) {
     rc = run_graph(b, p, s);
   } else {
-    cudaError_t e = launch_sequence(p.bd, p.points, p.n_maps, p.cells, p.key, s, b);
+    cudaError_t e = launch_sequence(p.bd, p.points, p.cells, p.key, s, b);
     rc = e == cudaSuccess ? EM_OK : map_record_error("batch launches", e);
   }
   finish(b, p, s);
@@ -436,7 +456,7 @@ int em_batch_autotune(em_batch* b, em_map* const* maps, const em_cloud* clouds, 
       int c = prepare(b, cmaps.data(), clouds, count, t, s, &p);
       if (c) return c;
       cudaEventRecord(e0, s);
-      cudaError_t le = launch_sequence(p.bd, p.points, p.n_maps, p.cells, p.key, s);
+      cudaError_t le = launch_sequence(p.bd, p.points, p.cells, p.key, s);
       cudaEventRecord(e1, s);
       finish(b, p, s);
       if (le != cudaSuccess) return map_record_error("autotune launches", le);
@@ -455,15 +475,26 @@ int em_batch_autotune(em_batch* b, em_map* const* maps, const em_cloud* clouds, 
   const int ray_c[] = {1, 2, 4, 8, 16};
   const int fuse_c[] = {4, 8, 16, 32};
   const int big_c[] = {32, 64, 128, 256};
-  for (int pass = 0; pass < 3 && rc == EM_OK; ++pass) {
-    const int* cand = pass == 0 ? ray_c : pass == 1 ? fuse_c : big_c;
+  const int small_c[] = {4, 8, 16, 32};
+  const bool any_ray = [&] {
+    for (em_map* m : uniq)
+      if (map_params(m).ray_step > 0.f) return true;
+    return false;
+  }();
+  for (int pass = 0; pass < 4 && rc == EM_OK; ++pass) {
+    if (pass == 0 && !any_ray) continue;
+    const int* cand = pass == 0 ? ray_c : pass == 1 ? small_c : pass == 2 ? fuse_c : big_c;
     const int nc = pass == 0 ? 5 : 4;
     for (int i = 0; i < nc && rc == EM_OK; ++i) {
       em_tuning t = best;
       if (pass == 0) t.ray_group = cand[i];
-      if (pass == 1) t.fuse_group = cand[i];
-      if (pass == 2) t.big_thresh = cand[i];
-      if (t.ray_group == best.ray_group && t.fuse_group == best.fuse_group && t.big_thresh == best.big_thresh) continue;
+      if (pass == 1) t.small_thresh = cand[i];
+      if (pass == 2) t.fuse_group = cand[i];
+      if (pass == 3) t.big_thresh = cand[i];
+      if (t.big_thresh < t.small_thresh) continue;
+      if (t.ray_group == best.ray_group && t.fuse_group == best.fuse_group && t.big_thresh == best.big_thresh &&
+          t.small_thresh == best.small_thresh)
+        continue;
       float ms = 0.f;
       rc = time_one(t, &ms);
       if (rc == EM_OK && ms < best_ms) {

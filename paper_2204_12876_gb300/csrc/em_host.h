@@ -16,7 +16,7 @@ const em_params& map_params(const em_map* m);
 
 // Start one update of map m: advances its update index and returns its
 // device descriptor (pt_begin / pt_count are left to the caller).
-MapDev map_begin_update(em_map* m, int64_t points, int big_thresh);
+MapDev map_begin_update(em_map* m, int64_t points);
 void map_end_update(em_map* m, cudaStream_t s, int64_t points);
 void map_undo_update(em_map* m, int64_t points);
 

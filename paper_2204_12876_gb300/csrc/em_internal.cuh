@@ -6,12 +6,19 @@
 // CloudDev), so the same kernels serve the plain, multi-cloud and batched
 // forms, and launches can be captured in a CUDA graph.
 //
+// Work spaces of a batch:
+//   points  the clouds of all maps concatenated (per-point kernels, 1D grid);
+//   cells   the cells of all maps concatenated, each map's range padded to a
+//           multiple of kTile cells, so every tile of kTile cells lies in one
+//           map (per-cell kernels, 1D grid over tiles: uneven maps balance).
+//
 // Pipeline of one update (Section II-A of the paper: transform, height update
 // and ray casting in the same iteration, then per-cell passes):
 //   k_count    transform + noise variance + cell binning, per-cell counts;
 //              per-cell ray thresholds of the pre-update map   (Section II-C)
 //   k_ray      visibility ray march against the pre-update map (Section II-E)
-//   k_alloc    one segment of the sorted record array per touched cell
+//   k_alloc    one segment of the record array per touched cell; medium and
+//              large cells listed for group / block fusion
 //   k_scatter  records into their cell's segment (counting sort by cell)
 //   k_fuse     per cell: wall rule, Mahalanobis gate, Eq. 1/2 in information
 //              form with exact integer accumulation          (Section II-C)
@@ -24,21 +31,27 @@
 
 namespace em {
 
+constexpr int kTile = 1024;  // cells per tile of the cell space
+
 // per-map counters (device), in em_stats order
 enum StatIdx {
   kStUpdates = 0, kStIn, kStValid, kStInMap, kStAccepted, kStRejected, kStWall, kStCellsUpdated,
   kStCleared, kStRaySamples, kStCount
 };
 
-// per-map device control block: counters that live across kernels of an update
+// per-map device control block
 struct MapCtl {
   unsigned long long stats[kStCount];
-  int32_t n_touched;   // small touched cells this update, front of the touched list (reset by k_clear)
-  int32_t seg_cursor;  // records allocated to segments this update (reset by k_clear)
+  int32_t seg_cursor;  // records given to segments this update (reset by k_count)
   int32_t err;         // first device-side error code of this map (sticky until read)
-  int32_t n_big;       // large touched cells, back of the touched list (reset by k_clear)
-  int32_t big_next;    // work-stealing cursor over the large cells (reset by k_clear)
-  int32_t pad[3];
+  int32_t pad[2];
+};
+
+// per-batch device control block (reset by k_count)
+struct BatchCtl {
+  int32_t n_med, n_big;      // entries in the medium / large cell lists
+  int32_t big_next;          // work-stealing cursor over the large cells
+  int32_t overflow;          // a list was full (never with the sizes the host allocates)
 };
 
 // point status codes (trace)
@@ -57,14 +70,12 @@ struct MapDev {
   uint32_t* mark;   // visibility marks, one bit per physical cell, zero between updates
   float* thr;       // per physical cell: h - sqrt(var_eff) of the pre-update map, -inf if empty
   int32_t* cnt;     // per physical cell point count, zero between updates
-  int32_t* cell_base;  // per physical cell: start of its segment (valid for touched cells)
-  int32_t* touched;    // touched physical cells this update (capacity W*H): cells with at most
-                       // big_thresh records from the front, larger ones from the back
-  int32_t* seg_base;   // per touched entry: segment start (absolute record index)
-  int32_t* seg_len;    // per touched entry: segment length
+  int32_t* cell_base;  // per physical cell: start of its segment of records (this update)
+  int32_t* cell_len;   // per physical cell: number of records (this update)
   MapCtl* ctl;
   int64_t pt_begin;    // this map's records occupy [pt_begin, pt_begin + pt_count)
   int64_t pt_count;
+  int64_t cell_begin;  // this map's first cell in the batch cell space (multiple of kTile)
   int32_t W, H, ox, oy;
   float x0, y0, res;
   int32_t t_now;       // index of this update
@@ -72,7 +83,7 @@ struct MapDev {
   float a0, a1, a2, var_min, min_range, max_range, k, v_out, sigma_t2, ray_step, alpha_n;
   int32_t wall, min_age;
   uint32_t flags;
-  int32_t big_thresh;  // segments longer than this are fused by a whole block
+  int32_t pad;
 };
 
 struct CloudDev {
@@ -88,6 +99,7 @@ struct CloudDev {
 struct BatchDev {
   int32_t n_maps, n_clouds;
   int64_t n_points;
+  int64_t n_cells;     // padded size of the cell space
   const MapDev* maps;
   const CloudDev* clouds;
   float2* zw_sorted;   // records (z, sigma_p^2) grouped by cell
@@ -95,21 +107,33 @@ struct BatchDev {
   int32_t* tr_ix;      // trace (null unless EM_F_TRACE)
   int32_t* tr_iy;
   uint8_t* tr_status;
+  BatchCtl* ctl;
+  int2* med_list;      // (map, physical cell) of cells with small_thresh < records <= big_thresh
+  int2* big_list;      // (map, physical cell) of cells with more than big_thresh records
+  int32_t med_cap, big_cap;
+  int32_t small_thresh, big_thresh;
 };
+
+// List capacities for n points: small_thresh >= kMinSmall, big_thresh >= kMinBig.
+constexpr int kMinSmall = 4;
+constexpr int kMinBig = 32;
+inline int64_t med_list_cap(int64_t n) { return n / (kMinSmall + 1) + 1; }
+inline int64_t big_list_cap(int64_t n) { return n / (kMinBig + 1) + 1; }
+inline int64_t pad_tile(int64_t cells) { return (cells + kTile - 1) / kTile * kTile; }
 
 // number of SMs of the current device (cached)
 int sm_count();
 
 // ---- launchers (each returns cudaGetLastError() of its launches)
-cudaError_t launch_bin(const BatchDev* b, int64_t n_points, cudaStream_t s);
+cudaError_t launch_bin(const BatchDev* b, int64_t n_points, int64_t n_cells, cudaStream_t s);
 cudaError_t launch_ray(const BatchDev* b, int64_t n_points, int group, cudaStream_t s);
-cudaError_t launch_alloc(const BatchDev* b, int32_t n_maps, int32_t max_cells, cudaStream_t s);
+cudaError_t launch_alloc(const BatchDev* b, int64_t n_cells, cudaStream_t s);
 cudaError_t launch_scatter(const BatchDev* b, int64_t n_points, cudaStream_t s);
-cudaError_t launch_fuse(const BatchDev* b, int32_t n_maps, int32_t max_cells, int group, cudaStream_t s);
-cudaError_t launch_clear(const BatchDev* b, int32_t n_maps, int32_t max_cells, cudaStream_t s);
-cudaError_t launch_normals(const BatchDev* b, int32_t n_maps, int32_t max_cells, cudaStream_t s);
-cudaError_t launch_smooth(const BatchDev* b, int32_t n_maps, int32_t max_cells, cudaStream_t s);
-cudaError_t launch_inpaint(const BatchDev* b, int32_t n_maps, int32_t max_cells, cudaStream_t s);
+cudaError_t launch_fuse(const BatchDev* b, int64_t n_cells, int64_t n_points, int group, cudaStream_t s);
+cudaError_t launch_clear(const BatchDev* b, int64_t n_cells, cudaStream_t s);
+cudaError_t launch_normals(const BatchDev* b, int64_t n_cells, cudaStream_t s);
+cudaError_t launch_smooth(const BatchDev* b, int64_t n_cells, cudaStream_t s);
+cudaError_t launch_inpaint(const BatchDev* b, int64_t n_cells, cudaStream_t s);
 cudaError_t launch_shift_clear(const MapDev& m, int32_t dx, int32_t dy, cudaStream_t s);
 cudaError_t launch_layers_out(const MapDev& m, uint32_t mask, float* dst, cudaStream_t s);
 cudaError_t launch_layers_in(const MapDev& m, uint32_t mask, const float* src, cudaStream_t s);
@@ -132,6 +156,15 @@ __device__ __forceinline__ int32_t phys_index(const MapDev& m, int32_t ix, int32
   return py * m.W + px;
 }
 
+// logical coordinates of physical cell p
+__device__ __forceinline__ void logical_of(const MapDev& m, int32_t p, int32_t& lx, int32_t& ly) {
+  const int32_t py = p / m.W, px = p - py * m.W;
+  lx = px - m.ox;
+  lx += (lx < 0) ? m.W : 0;
+  ly = py - m.oy;
+  ly += (ly < 0) ? m.H : 0;
+}
+
 // effective variance of a cell at update t_now (lazy time variance)
 __device__ __forceinline__ float var_eff(const MapDev& m, float var, int32_t t_last) {
   return __fmaf_rn(m.sigma_t2, (float)(m.t_now - t_last), var);
@@ -145,6 +178,33 @@ __device__ __forceinline__ int find_cloud(const CloudDev* cl, int n_clouds, int6
     if (cl[mid].begin <= g) lo = mid; else hi = mid - 1;
   }
   return lo;
+}
+
+// index of the map whose cell range holds batch cell g (maps sorted by cell_begin)
+__device__ __forceinline__ int find_map_cell(const MapDev* maps, int n_maps, int64_t g) {
+  int lo = 0, hi = n_maps - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (maps[mid].cell_begin <= g) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Iterate over the tiles of the cell space: for each tile the map it lies in
+// (block-uniform) and the tile's first physical cell.  body(m, map, p0, count).
+template <class F>
+__device__ __forceinline__ void for_each_tile(const struct BatchDev& b, F body) {
+  const int64_t n_tiles = b.n_cells / kTile;
+  for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const int64_t g0 = t * kTile;
+    const int mi = find_map_cell(b.maps, b.n_maps, g0);
+    const MapDev& m = b.maps[mi];
+    const int64_t p0 = g0 - m.cell_begin;
+    const int32_t ncell = m.W * m.H;
+    if (p0 >= ncell) continue;  // padding at the end of a map
+    const int32_t cnt = (int32_t)(ncell - p0 < kTile ? ncell - p0 : kTile);
+    body(m, mi, (int32_t)p0, cnt);
+  }
 }
 
 }  // namespace em

@@ -37,14 +37,15 @@ constexpr size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
 // scratch layout; the part that must start at zero (ctl, marks, counts) is contiguous
 constexpr size_t kOffDesc = 0;
 constexpr size_t kOffCtl = kOffDesc + up256(sizeof(BatchDev) + sizeof(MapDev) + kMaxCloudsNA * sizeof(CloudDev));
-constexpr size_t kOffMark = kOffCtl + up256(sizeof(MapCtl));
+constexpr size_t kOffBCtl = kOffCtl + up256(sizeof(MapCtl));
+constexpr size_t kOffMark = kOffBCtl + up256(sizeof(BatchCtl));
 constexpr size_t kOffCnt = kOffMark + up256(((size_t)kMaxCells + 31) / 32 * sizeof(uint32_t));
 constexpr size_t kOffThr = kOffCnt + up256((size_t)kMaxCells * sizeof(int32_t));
 constexpr size_t kOffCellBase = kOffThr + up256((size_t)kMaxCells * sizeof(float));
-constexpr size_t kOffTouched = kOffCellBase + up256((size_t)kMaxCells * sizeof(int32_t));
-constexpr size_t kOffSegBase = kOffTouched + up256((size_t)kMaxCells * sizeof(int32_t));
-constexpr size_t kOffSegLen = kOffSegBase + up256((size_t)kMaxCells * sizeof(int32_t));
-constexpr size_t kOffRec = kOffSegLen + up256((size_t)kMaxCells * sizeof(int32_t));
+constexpr size_t kOffCellLen = kOffCellBase + up256((size_t)kMaxCells * sizeof(int32_t));
+constexpr size_t kOffMed = kOffCellLen + up256((size_t)kMaxCells * sizeof(int32_t));
+constexpr size_t kOffBig = kOffMed + up256((size_t)(kMaxPoints / (kMinSmall + 1) + 1) * sizeof(int2));
+constexpr size_t kOffRec = kOffBig + up256((size_t)(kMaxPoints / (kMinBig + 1) + 1) * sizeof(int2));
 constexpr size_t kScratchBytes = kOffRec + up256((size_t)kMaxPoints * sizeof(float2));
 
 constexpr int kMaxDevices = 64;
@@ -137,10 +138,9 @@ extern "C" int em_update_noalloc(const em_params* params, int64_t shift_x, int64
   m->thr = reinterpret_cast<float*>(base + kOffThr);
   m->cnt = reinterpret_cast<int32_t*>(base + kOffCnt);
   m->cell_base = reinterpret_cast<int32_t*>(base + kOffCellBase);
-  m->touched = reinterpret_cast<int32_t*>(base + kOffTouched);
-  m->seg_base = reinterpret_cast<int32_t*>(base + kOffSegBase);
-  m->seg_len = reinterpret_cast<int32_t*>(base + kOffSegLen);
+  m->cell_len = reinterpret_cast<int32_t*>(base + kOffCellLen);
   m->ctl = reinterpret_cast<MapCtl*>(base + kOffCtl);
+  m->cell_begin = 0;
   m->pt_begin = 0;
   m->pt_count = total;
   m->W = W;
@@ -155,7 +155,6 @@ extern "C" int em_update_noalloc(const em_params* params, int64_t shift_x, int64
   m->v_out = params->outlier_variance; m->sigma_t2 = params->time_variance; m->ray_step = params->ray_step;
   m->alpha_n = params->cleanup_normal_thresh; m->wall = params->wall_num_thresh;
   m->min_age = params->cleanup_min_age;
-  m->big_thresh = 64;
   int64_t begin = 0;
   for (int i = 0; i < n_clouds; ++i) {
     cd[i].pts = clouds[i].points;
@@ -175,6 +174,14 @@ extern "C" int em_update_noalloc(const em_params* params, int64_t shift_x, int64
   b->maps = reinterpret_cast<const MapDev*>(base + kOffDesc + sizeof(BatchDev));
   b->clouds = reinterpret_cast<const CloudDev*>(base + kOffDesc + sizeof(BatchDev) + sizeof(MapDev));
   b->zw_sorted = reinterpret_cast<float2*>(base + kOffRec);
+  b->n_cells = pad_tile(ncell);
+  b->ctl = reinterpret_cast<BatchCtl*>(base + kOffBCtl);
+  b->med_list = reinterpret_cast<int2*>(base + kOffMed);
+  b->big_list = reinterpret_cast<int2*>(base + kOffBig);
+  b->med_cap = (int32_t)(kMaxPoints / (kMinSmall + 1) + 1);
+  b->big_cap = (int32_t)(kMaxPoints / (kMinBig + 1) + 1);
+  b->small_thresh = 8;
+  b->big_thresh = 64;
 
   const BatchDev* bd = reinterpret_cast<const BatchDev*>(base + kOffDesc);
   const size_t desc_bytes = sizeof(BatchDev) + sizeof(MapDev) + (size_t)n_clouds * sizeof(CloudDev);
@@ -185,15 +192,14 @@ extern "C" int em_update_noalloc(const em_params* params, int64_t shift_x, int64
   rc = na_status(cudaMemsetAsync(base + kOffCtl, 0, kOffCnt - kOffCtl + (size_t)ncell * sizeof(int32_t), s),
                  "cudaMemsetAsync");
   if (rc) return rc;
-  cudaError_t e = cudaSuccess;
+  const int64_t cells = pad_tile(ncell);
+  cudaError_t e = launch_bin(bd, total, cells, s);
   if (total > 0) {
-    const int32_t max_touched = ncell < total ? ncell : (int32_t)total;
-    if (e == cudaSuccess) e = launch_bin(bd, total, s);
     if (e == cudaSuccess && params->ray_step > 0.f) e = launch_ray(bd, total, 2, s);
-    if (e == cudaSuccess) e = launch_alloc(bd, 1, ncell, s);
+    if (e == cudaSuccess) e = launch_alloc(bd, cells, s);
     if (e == cudaSuccess) e = launch_scatter(bd, total, s);
-    if (e == cudaSuccess) e = launch_fuse(bd, 1, max_touched, 8, s);
+    if (e == cudaSuccess) e = launch_fuse(bd, cells, total, 8, s);
   }
-  if (e == cudaSuccess) e = launch_clear(bd, 1, ncell, s);
+  if (e == cudaSuccess) e = launch_clear(bd, cells, s);
   return na_status(e, "em_update_noalloc launch");
 }

@@ -54,14 +54,14 @@ __device__ __forceinline__ bool in_map(const MapDev& m, int32_t ix, int32_t iy) 
 // single L2 slice.
 struct MapCounters {
   int map = -1;
-  unsigned long long v[3] = {0, 0, 0};
+  unsigned long long v[4] = {0, 0, 0, 0};
 };
 
 __device__ __forceinline__ void flush_counters(const BatchDev& b, MapCounters& mc, const int* idx, int n) {
   __shared__ int s_map;
-  __shared__ unsigned long long s_sum[3];
+  __shared__ unsigned long long s_sum[4];
   if (threadIdx.x == 0) s_map = mc.map;
-  if (threadIdx.x < 3) s_sum[threadIdx.x] = 0;
+  if (threadIdx.x < 4) s_sum[threadIdx.x] = 0;
   __syncthreads();
   const bool uniform = __syncthreads_and(mc.map == s_map || mc.map < 0);
   if (uniform) {

@@ -1,7 +1,7 @@
 // k_fuse.cu -- per-cell fusion (Section II-C of the paper).
 //
 // For every cell that received points in this update, its segment of records
-// (z, sigma_p^2) is walked by a group of lanes:
+// (z, sigma_p^2) is walked:
 //   1. wall rule: in a valid cell with more than wall_num_thresh points, points
 //      below the current height are dropped (before the outlier test);
 //   2. Mahalanobis gate against the pre-update estimate: reject iff
@@ -20,11 +20,13 @@
 // every order of the points, bit for bit (no float atomics, no dependence on
 // the order records reached their segment or on how lanes split a segment).
 //
-// Work split: cells with at most big_thresh records (front of the touched list)
-// go to groups of G lanes; larger cells (back of the list) go to whole blocks,
-// which take them one at a time from a counter (atomicAdd; no block ever waits
-// for another).
-#include "em_internal.cuh"
+// Three tiers by segment length, in one launch:
+//   large  (> big_thresh records)   one whole block per cell, cells taken from
+//                                   a counter (atomicAdd; no block waits);
+//   medium (> small_thresh)         a group of G lanes per cell, grid-stride;
+//   small  (1 .. small_thresh)      one thread per cell, walking the tiles of
+//                                   the cell space (coalesced per-cell loads).
+#include "em_point.cuh"
 
 namespace em {
 
@@ -104,16 +106,16 @@ struct CellCtx {
   bool valid, wall_on, gate_on;
 };
 
-__device__ __forceinline__ CellCtx load_cell(const MapDev& m, int slot) {
+__device__ __forceinline__ CellCtx load_cell(const MapDev& m, int32_t cell, int32_t base, int32_t len) {
   CellCtx c;
-  c.cell = m.touched[slot];
-  c.base = m.seg_base[slot];
-  c.len = m.seg_len[slot];
-  c.h = m.h[c.cell];
-  const float var = m.var[c.cell];
+  c.cell = cell;
+  c.base = base;
+  c.len = len;
+  c.h = m.h[cell];
+  const float var = m.var[cell];
   c.valid = isfinite(var);
-  c.ve = c.valid ? var_eff(m, var, m.t_last[c.cell]) : var;
-  c.wall_on = m.wall > 0 && c.valid && c.len > m.wall;
+  c.ve = c.valid ? var_eff(m, var, m.t_last[cell]) : var;
+  c.wall_on = m.wall > 0 && c.valid && len > m.wall;
   c.gate_on = c.valid && m.k > 0.f;
   return c;
 }
@@ -173,85 +175,94 @@ __device__ __forceinline__ bool write_cell(const MapDev& m, const CellCtx& c, fl
   return true;
 }
 
+__device__ __forceinline__ void count_cell(const BatchDev& b, MapCounters& mc, int map, const Acc& a, bool upd) {
+  const int idx[4] = {kStAccepted, kStRejected, kStWall, kStCellsUpdated};
+  unsigned long long inc[4] = {(unsigned long long)a.acc, (unsigned long long)a.rej, (unsigned long long)a.wal,
+                               upd ? 1ull : 0ull};
+  add_counter(b, mc, map, idx, 4, inc);
+}
+
 template <int G>
 __global__ void __launch_bounds__(kFuseThreads) k_fuse(const BatchDev* __restrict__ bp) {
   __shared__ int s_slot;
   __shared__ float s_min[kFuseWarps];
   __shared__ __int128 s_q[2][kFuseWarps];
   __shared__ int s_n[3][kFuseWarps];
-  __shared__ unsigned long long s_c[4];
   const BatchDev& b = *bp;
-  if ((int)blockIdx.y >= b.n_maps) return;
-  const MapDev& m = b.maps[blockIdx.y];
-  const int32_t ncell = m.W * m.H;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned long long n_acc = 0, n_rej = 0, n_wall = 0, n_upd = 0;
+  MapCounters mc;
 
   // ---- large cells: one block each, taken from a counter
-  const int n_big = m.ctl->n_big;
-  for (;;) {
-    if (threadIdx.x == 0) s_slot = atomicAdd(&m.ctl->big_next, 1);
-    __syncthreads();
-    const int jb = s_slot;
-    __syncthreads();
-    if (jb >= n_big) break;
-    const CellCtx c = load_cell(m, ncell - 1 - jb);
-    float href = c.h;
-    if (!c.valid) {
-      float zmin = __int_as_float(0x7f800000);
-      for (int i = threadIdx.x; i < c.len; i += kFuseThreads) zmin = fminf(zmin, b.zw_sorted[c.base + i].x);
-      zmin = group_min<32>(zmin);
-      if (lane == 0) s_min[warp] = zmin;
+  const int n_big = min(b.ctl->n_big, b.big_cap);
+  if (n_big > 0) {
+    for (;;) {
+      if (threadIdx.x == 0) s_slot = atomicAdd(&b.ctl->big_next, 1);
       __syncthreads();
-      zmin = s_min[0];
-      for (int w = 1; w < kFuseWarps; ++w) zmin = fminf(zmin, s_min[w]);
-      href = zmin;
-    }
-    Acc a{0, 0, 0, 0, 0};
-    fuse_records(b, m, c, href, threadIdx.x, kFuseThreads, a);
-    group_reduce<32>(a);
-    if (lane == 0) {
-      s_q[0][warp] = a.qw;
-      s_q[1][warp] = a.qt;
-      s_n[0][warp] = a.acc;
-      s_n[1][warp] = a.rej;
-      s_n[2][warp] = a.wal;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      Acc t{0, 0, 0, 0, 0};
-      for (int w = 0; w < kFuseWarps; ++w) {
-        t.qw += s_q[0][w];
-        t.qt += s_q[1][w];
-        t.acc += s_n[0][w];
-        t.rej += s_n[1][w];
-        t.wal += s_n[2][w];
+      const int jb = s_slot;
+      __syncthreads();
+      if (jb >= n_big) break;
+      const int2 e = b.big_list[jb];
+      const MapDev& m = b.maps[e.x];
+      const CellCtx c = load_cell(m, e.y, m.cell_base[e.y], m.cell_len[e.y]);
+      float href = c.h;
+      if (!c.valid) {
+        float zmin = __int_as_float(0x7f800000);
+        for (int i = threadIdx.x; i < c.len; i += kFuseThreads) zmin = fminf(zmin, b.zw_sorted[c.base + i].x);
+        zmin = group_min<32>(zmin);
+        if (lane == 0) s_min[warp] = zmin;
+        __syncthreads();
+        zmin = s_min[0];
+        for (int w = 1; w < kFuseWarps; ++w) zmin = fminf(zmin, s_min[w]);
+        href = zmin;
       }
-      n_acc += t.acc;
-      n_rej += t.rej;
-      n_wall += t.wal;
-      n_upd += write_cell(m, c, href, t);
+      Acc a{0, 0, 0, 0, 0};
+      fuse_records(b, m, c, href, threadIdx.x, kFuseThreads, a);
+      group_reduce<32>(a);
+      if (lane == 0) {
+        s_q[0][warp] = a.qw;
+        s_q[1][warp] = a.qt;
+        s_n[0][warp] = a.acc;
+        s_n[1][warp] = a.rej;
+        s_n[2][warp] = a.wal;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        Acc t{0, 0, 0, 0, 0};
+        for (int w = 0; w < kFuseWarps; ++w) {
+          t.qw += s_q[0][w];
+          t.qt += s_q[1][w];
+          t.acc += s_n[0][w];
+          t.rej += s_n[1][w];
+          t.wal += s_n[2][w];
+        }
+        const bool upd = write_cell(m, c, href, t);
+        count_cell(b, mc, e.x, t, upd);
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
 
-  // ---- small cells: groups of G lanes
+  // ---- medium cells: groups of G lanes, grid-stride over the list
   constexpr int kGroupsPerWarp = 32 / G;
-  const int n_small = m.ctl->n_touched;
+  const int n_med = min(b.ctl->n_med, b.med_cap);
   const int gl = lane % G, gw = lane / G;
   const int warp_global = blockIdx.x * kFuseWarps + warp;
   const int warp_stride = gridDim.x * kFuseWarps;
-  for (int jb = warp_global * kGroupsPerWarp; jb < n_small; jb += warp_stride * kGroupsPerWarp) {
+  for (int jb = warp_global * kGroupsPerWarp; jb < n_med; jb += warp_stride * kGroupsPerWarp) {
     const int j = jb + gw;
-    const bool has = j < n_small;
+    const bool has = j < n_med;
+    int2 e = make_int2(0, 0);
     CellCtx c;
     if (has) {
-      c = load_cell(m, j);
+      e = b.med_list[j];
+      const MapDev& m = b.maps[e.x];
+      c = load_cell(m, e.y, m.cell_base[e.y], m.cell_len[e.y]);
     } else {
       c.len = 0;
       c.valid = true;
       c.h = 0.f;
     }
+    const MapDev& m = b.maps[e.x];
     float zmin = __int_as_float(0x7f800000);
     if (!c.valid)
       for (int i = gl; i < c.len; i += G) zmin = fminf(zmin, b.zw_sorted[c.base + i].x);
@@ -261,39 +272,46 @@ __global__ void __launch_bounds__(kFuseThreads) k_fuse(const BatchDev* __restric
     if (has) fuse_records(b, m, c, href, gl, G, a);
     group_reduce<G>(a);
     if (has && gl == 0) {
-      n_acc += a.acc;
-      n_rej += a.rej;
-      n_wall += a.wal;
-      n_upd += write_cell(m, c, href, a);
+      const bool upd = write_cell(m, c, href, a);
+      count_cell(b, mc, e.x, a, upd);
     }
   }
 
-  // ---- block-level counters (the block is map-uniform): one atomic per counter
-  if (threadIdx.x < 4) s_c[threadIdx.x] = 0;
-  __syncthreads();
-  unsigned long long v[4] = {n_acc, n_rej, n_wall, n_upd};
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    unsigned long long x = v[k];
-    for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
-    if (lane == 0 && x) atomicAdd(&s_c[k], x);
+  // ---- small cells: one thread per cell over the tiles of the cell space
+  for_each_tile(b, [&](const MapDev& m, int mi, int32_t p0, int32_t count) {
+    for (int32_t i = threadIdx.x; i < count; i += kFuseThreads) {
+      const int32_t p = p0 + i;
+      const int32_t len = m.cell_len[p];
+      if (len < 1 || len > b.small_thresh) continue;
+      const CellCtx c = load_cell(m, p, m.cell_base[p], len);
+      float href = c.h;
+      if (!c.valid) {
+        href = __int_as_float(0x7f800000);
+        for (int k = 0; k < len; ++k) href = fminf(href, b.zw_sorted[c.base + k].x);
+      }
+      Acc a{0, 0, 0, 0, 0};
+      fuse_records(b, m, c, href, 0, 1, a);
+      const bool upd = write_cell(m, c, href, a);
+      count_cell(b, mc, mi, a, upd);
+    }
+  });
+
+  const int idx[4] = {kStAccepted, kStRejected, kStWall, kStCellsUpdated};
+  if (mc.map >= 0) {  // fold nothing new; flush per block
+    unsigned long long zero[4] = {0, 0, 0, 0};
+    add_counter(b, mc, mc.map, idx, 4, zero);
   }
-  __syncthreads();
-  if (threadIdx.x < 4 && s_c[threadIdx.x]) {
-    const int idx = threadIdx.x == 0 ? kStAccepted : threadIdx.x == 1 ? kStRejected
-                  : threadIdx.x == 2 ? kStWall : kStCellsUpdated;
-    atomicAdd(&m.ctl->stats[idx], s_c[threadIdx.x]);
-  }
+  flush_counters(b, mc, idx, 4);
 }
 
-cudaError_t launch_fuse(const BatchDev* b, int32_t n_maps, int32_t max_cells, int group, cudaStream_t s) {
+cudaError_t launch_fuse(const BatchDev* b, int64_t n_cells, int64_t n_points, int group, cudaStream_t s) {
   const int g = (group == 4 || group == 8 || group == 16 || group == 32) ? group : 8;
-  const int per_block = kFuseThreads / g;
-  const int want = (max_cells + per_block - 1) / per_block;
-  int cap = sm_count() * 8 / (n_maps > 0 ? n_maps : 1);
-  if (cap < 4) cap = 4;
-  const int gx = want < cap ? want : cap;
-  dim3 grid(gx < 1 ? 1 : gx, n_maps);
+  const int64_t tiles = n_cells / kTile;
+  int64_t want = tiles > 1 ? tiles : 1;
+  const int64_t med_blocks = (n_points / (kMinSmall + 1)) / (kFuseThreads / g) + 1;
+  if (med_blocks > want) want = med_blocks;
+  const int64_t cap = (int64_t)sm_count() * 8;
+  const int grid = (int)(want < cap ? want : cap);
   switch (g) {
     case 4: k_fuse<4><<<grid, kFuseThreads, 0, s>>>(b); break;
     case 16: k_fuse<16><<<grid, kFuseThreads, 0, s>>>(b); break;

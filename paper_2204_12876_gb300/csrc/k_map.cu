@@ -12,7 +12,7 @@
 #include <math.h>
 
 #include "em.h"
-#include "em_internal.cuh"
+#include "em_point.cuh"
 
 namespace em {
 
@@ -25,13 +25,12 @@ __device__ __forceinline__ bool valid_at(const MapDev& m, int32_t p) { return is
 
 __global__ void __launch_bounds__(kMapThreads) k_normals(const BatchDev* __restrict__ bp) {
   const BatchDev& b = *bp;
-  if ((int)blockIdx.y >= b.n_maps) return;
-  const MapDev& m = b.maps[blockIdx.y];
+  for_each_tile(b, [&](const MapDev& m, int, int32_t p0, int32_t count) {
   if (!m.nx || !(m.flags & EM_F_NORMALS)) return;  // a batch may mix maps with and without normals
-  const int32_t ncell = m.W * m.H;
-  for (int32_t c = blockIdx.x * kMapThreads + threadIdx.x; c < ncell; c += gridDim.x * kMapThreads) {
-    const int32_t lx = c % m.W, ly = c / m.W;
-    const int32_t p = phys_index(m, lx, ly);
+  for (int32_t i = threadIdx.x; i < count; i += kMapThreads) {
+    const int32_t p = p0 + i;
+    int32_t lx, ly;
+    logical_of(m, p, lx, ly);
     float rx = qnan(), ry = qnan(), rz = qnan();
     if (valid_at(m, p)) {
       const float hc = m.h[p];
@@ -67,17 +66,17 @@ __global__ void __launch_bounds__(kMapThreads) k_normals(const BatchDev* __restr
     m.ny[p] = ry;
     m.nz[p] = rz;
   }
+  });
 }
 
 __global__ void __launch_bounds__(kMapThreads) k_smooth(const BatchDev* __restrict__ bp) {
   const BatchDev& b = *bp;
-  if ((int)blockIdx.y >= b.n_maps) return;
-  const MapDev& m = b.maps[blockIdx.y];
+  for_each_tile(b, [&](const MapDev& m, int, int32_t p0, int32_t count) {
   if (!m.smooth) return;
-  const int32_t ncell = m.W * m.H;
-  for (int32_t c = blockIdx.x * kMapThreads + threadIdx.x; c < ncell; c += gridDim.x * kMapThreads) {
-    const int32_t lx = c % m.W, ly = c / m.W;
-    const int32_t p = phys_index(m, lx, ly);
+  for (int32_t i = threadIdx.x; i < count; i += kMapThreads) {
+    const int32_t p = p0 + i;
+    int32_t lx, ly;
+    logical_of(m, p, lx, ly);
     float out = qnan();
     if (valid_at(m, p)) {
       float s = 0.f;
@@ -98,6 +97,7 @@ __global__ void __launch_bounds__(kMapThreads) k_smooth(const BatchDev* __restri
     }
     m.smooth[p] = out;
   }
+  });
 }
 
 // Every empty cell explores its 4-connected component of empty cells until
@@ -107,13 +107,12 @@ __global__ void __launch_bounds__(kMapThreads) k_smooth(const BatchDev* __restri
 // value independently, so no labels are needed).
 __global__ void __launch_bounds__(kMapThreads) k_inpaint(const BatchDev* __restrict__ bp) {
   const BatchDev& b = *bp;
-  if ((int)blockIdx.y >= b.n_maps) return;
-  const MapDev& m = b.maps[blockIdx.y];
+  for_each_tile(b, [&](const MapDev& m, int, int32_t p0, int32_t count) {
   if (!m.inpaint) return;
-  const int32_t ncell = m.W * m.H;
-  for (int32_t c = blockIdx.x * kMapThreads + threadIdx.x; c < ncell; c += gridDim.x * kMapThreads) {
-    const int32_t lx = c % m.W, ly = c / m.W;
-    const int32_t p = phys_index(m, lx, ly);
+  for (int32_t i = threadIdx.x; i < count; i += kMapThreads) {
+    const int32_t p = p0 + i;
+    int32_t lx, ly;
+    logical_of(m, p, lx, ly);
     if (valid_at(m, p)) {
       m.inpaint[p] = m.h[p];
       continue;
@@ -153,6 +152,7 @@ __global__ void __launch_bounds__(kMapThreads) k_inpaint(const BatchDev* __restr
     }
     m.inpaint[p] = out;
   }
+  });
 }
 
 __device__ __forceinline__ void empty_cell(const MapDev& m, int32_t p) {
@@ -181,6 +181,7 @@ __global__ void __launch_bounds__(kMapThreads) k_fill(MapDev m) {
   for (int32_t p = blockIdx.x * kMapThreads + threadIdx.x; p < ncell; p += gridDim.x * kMapThreads) {
     empty_cell(m, p);
     m.cnt[p] = 0;
+    m.cell_len[p] = 0;
     if ((p & 31) == 0) m.mark[p >> 5] = 0u;
   }
 }
@@ -248,16 +249,22 @@ static int cell_grid(int64_t cells) {
   return g < 1 ? 1 : (int)g;
 }
 
-cudaError_t launch_normals(const BatchDev* b, int32_t n_maps, int32_t max_cells, cudaStream_t s) {
-  k_normals<<<dim3(cell_grid(max_cells), n_maps), kMapThreads, 0, s>>>(b);
+static int tile_grid(int64_t n_cells) {
+  const int64_t tiles = n_cells / kTile;
+  const int64_t cap = (int64_t)sm_count() * 8;
+  return (int)(tiles < 1 ? 1 : tiles < cap ? tiles : cap);
+}
+
+cudaError_t launch_normals(const BatchDev* b, int64_t n_cells, cudaStream_t s) {
+  k_normals<<<tile_grid(n_cells), kMapThreads, 0, s>>>(b);
   return cudaGetLastError();
 }
-cudaError_t launch_smooth(const BatchDev* b, int32_t n_maps, int32_t max_cells, cudaStream_t s) {
-  k_smooth<<<dim3(cell_grid(max_cells), n_maps), kMapThreads, 0, s>>>(b);
+cudaError_t launch_smooth(const BatchDev* b, int64_t n_cells, cudaStream_t s) {
+  k_smooth<<<tile_grid(n_cells), kMapThreads, 0, s>>>(b);
   return cudaGetLastError();
 }
-cudaError_t launch_inpaint(const BatchDev* b, int32_t n_maps, int32_t max_cells, cudaStream_t s) {
-  k_inpaint<<<dim3(cell_grid(max_cells), n_maps), kMapThreads, 0, s>>>(b);
+cudaError_t launch_inpaint(const BatchDev* b, int64_t n_cells, cudaStream_t s) {
+  k_inpaint<<<tile_grid(n_cells), kMapThreads, 0, s>>>(b);
   return cudaGetLastError();
 }
 

@@ -15,12 +15,12 @@
 //
 // k_clear: after the fusion, every marked cell that holds an estimate and was
 // last written at least max(1, cleanup_min_age) updates ago is removed; the
-// bitmask and the per-update counters are reset for the next update.
+// bitmask is reset for the next update.  Tiles start on multiples of kTile
+// cells, so a tile owns whole mark words.
 #include "em_point.cuh"
 
 namespace em {
 
-constexpr unsigned kFull = 0xffffffffu;
 constexpr int kRayThreads = 256;
 
 // Narrow [lo, hi] (metres along the ray) to where the track o + (s/d) v stays
@@ -106,37 +106,33 @@ constexpr int kClearThreads = 256;
 
 __global__ void __launch_bounds__(kClearThreads) k_clear(const BatchDev* __restrict__ bp) {
   const BatchDev& b = *bp;
-  if ((int)blockIdx.y >= b.n_maps) return;
-  const MapDev& m = b.maps[blockIdx.y];
-  const int32_t ncell = m.W * m.H;
-  const int32_t nword = (ncell + 31) >> 5;
-  const int32_t min_age = m.min_age > 1 ? m.min_age : 1;
-  unsigned long long cleared = 0;
-  for (int32_t w = blockIdx.x * kClearThreads + threadIdx.x; w < nword; w += gridDim.x * kClearThreads) {
-    uint32_t bits = m.mark[w];
-    if (!bits) continue;
-    m.mark[w] = 0u;
-    while (bits) {
-      const int bit = __ffs(bits) - 1;
-      bits &= bits - 1;
-      const int32_t p = w * 32 + bit;
-      if (p >= ncell) break;
-      if (!isfinite(m.var[p])) continue;
-      if (m.t_now - m.t_last[p] < min_age) continue;
-      m.h[p] = __int_as_float(0x7fc00000);
-      m.var[p] = __int_as_float(0x7f800000);
-      ++cleared;
+  MapCounters mc;
+  const int idx[1] = {kStCleared};
+  // a tile of kTile cells is kTile / 32 mark words; one word per thread
+  for_each_tile(b, [&](const MapDev& m, int mi, int32_t p0, int32_t count) {
+    const int32_t min_age = m.min_age > 1 ? m.min_age : 1;
+    const int32_t nword = (count + 31) >> 5;
+    unsigned long long cleared = 0;
+    for (int32_t wi = threadIdx.x; wi < nword; wi += kClearThreads) {
+      const int32_t w = (p0 >> 5) + wi;
+      uint32_t bits = m.mark[w];
+      if (!bits) continue;
+      m.mark[w] = 0u;
+      while (bits) {
+        const int bit = __ffs(bits) - 1;
+        bits &= bits - 1;
+        const int32_t p = w * 32 + bit;
+        if (p >= p0 + count) break;
+        if (!isfinite(m.var[p])) continue;
+        if (m.t_now - m.t_last[p] < min_age) continue;
+        m.h[p] = __int_as_float(0x7fc00000);
+        m.var[p] = __int_as_float(0x7f800000);
+        ++cleared;
+      }
     }
-  }
-  for (int o = 16; o; o >>= 1) cleared += __shfl_xor_sync(kFull, cleared, o);
-  if ((threadIdx.x & 31) == 0 && cleared) atomicAdd(&m.ctl->stats[kStCleared], cleared);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    m.ctl->n_touched = 0;
-    m.ctl->n_big = 0;
-    m.ctl->big_next = 0;
-    m.ctl->seg_cursor = 0;
-    atomicAdd(&m.ctl->stats[kStUpdates], 1ull);
-  }
+    add_counter(b, mc, mi, idx, 1, &cleared);
+  });
+  flush_counters(b, mc, idx, 1);
 }
 
 cudaError_t launch_ray(const BatchDev* b, int64_t n_points, int group, cudaStream_t s) {
@@ -157,11 +153,10 @@ cudaError_t launch_ray(const BatchDev* b, int64_t n_points, int group, cudaStrea
   return cudaGetLastError();
 }
 
-cudaError_t launch_clear(const BatchDev* b, int32_t n_maps, int32_t max_cells, cudaStream_t s) {
-  int words = (max_cells + 31) / 32;
-  int gx = (words + kClearThreads - 1) / kClearThreads;
-  if (gx > 256) gx = 256;
-  dim3 grid(gx < 1 ? 1 : gx, n_maps);
+cudaError_t launch_clear(const BatchDev* b, int64_t n_cells, cudaStream_t s) {
+  const int64_t tiles = n_cells / kTile;
+  const int64_t cap = (int64_t)sm_count() * 8;
+  const int grid = (int)(tiles < 1 ? 1 : tiles < cap ? tiles : cap);
   k_clear<<<grid, kClearThreads, 0, s>>>(b);
   return cudaGetLastError();
 }

@@ -4,10 +4,10 @@
 //   k_count    per point: transform + bin, warp-aggregated per-cell counts;
 //              then per cell: the ray-march threshold h - sqrt(var_eff) of the
 //              pre-update map (one 4-byte gather per ray sample later)
-//   k_alloc    per map, tiles of cells: block scans of the counts give every
-//              touched cell a segment [base, base + count) of the record array
-//              and a slot in the touched list (cells with more than big_thresh
-//              records from the back, for whole-block fusion)
+//   k_alloc    per tile of cells: block scans of the counts give every touched
+//              cell a segment [base, base + count) of the record array; cells
+//              with more than small_thresh records are listed for group fusion,
+//              more than big_thresh for whole-block fusion
 //   k_scatter  per point: transform + bin again, claim a slot in the cell's
 //              segment, write the record (z, sigma_p^2)
 //
@@ -19,6 +19,7 @@
 namespace em {
 
 constexpr int kPointThreads = 256;
+constexpr int kCellThreads = 256;
 constexpr unsigned kFull = 0xffffffffu;
 
 // Block-contiguous partition of the point space into chunks of whole warps.
@@ -73,6 +74,16 @@ __global__ void __launch_bounds__(kPointThreads) k_count(const BatchDev* __restr
   __shared__ float4 stage[kPointThreads / 32][24];
   const BatchDev& b = *bp;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // per-update counters start at zero (the previous update is complete)
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    b.ctl->n_med = 0;
+    b.ctl->n_big = 0;
+    b.ctl->big_next = 0;
+    for (int mi = 0; mi < b.n_maps; ++mi) {
+      b.maps[mi].ctl->seg_cursor = 0;
+      atomicAdd(&b.maps[mi].ctl->stats[kStUpdates], 1ull);
+    }
+  }
   int64_t beg, end;
   block_range(b.n_points, beg, end);
   MapCounters mc;
@@ -101,25 +112,18 @@ __global__ void __launch_bounds__(kPointThreads) k_count(const BatchDev* __restr
     if (inm && lane == __ffs(peers) - 1) atomicAdd(&m.cnt[key], __popc(peers));
   }
   flush_counters(b, mc, idx, 2);
-  // ray thresholds of the pre-update map, every cell of every map (Eq. 3)
-  const int64_t tid = (int64_t)blockIdx.x * kPointThreads + threadIdx.x;
-  const int64_t nthreads = (int64_t)gridDim.x * kPointThreads;
-  for (int mi = 0; mi < b.n_maps; ++mi) {
-    const MapDev& m = b.maps[mi];
-    if (m.ray_step <= 0.f) continue;
-    const int32_t ncell = m.W * m.H;
-    for (int64_t p = tid; p < ncell; p += nthreads) {
+  // ray thresholds of the pre-update map over the cell space (Eq. 3)
+  for_each_tile(b, [&](const MapDev& m, int, int32_t p0, int32_t count) {
+    if (m.ray_step <= 0.f) return;
+    for (int32_t i = threadIdx.x; i < count; i += kPointThreads) {
+      const int32_t p = p0 + i;
       const float var = m.var[p];
       float t = __int_as_float(0xff800000);  // -inf: an empty cell is never penetrated
       if (isfinite(var)) t = __fsub_rn(m.h[p], __fsqrt_rn(var_eff(m, var, m.t_last[p])));
       m.thr[p] = t;
     }
-  }
+  });
 }
-
-// One block per tile of 1024 physical cells of one map (blockIdx.y = map).
-constexpr int kAllocThreads = 256;
-constexpr int kAllocPer = 4;
 
 __device__ __forceinline__ int block_exclusive_scan(int v, int* warp_tot, int& total) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -147,47 +151,63 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* warp_tot, int& t
   return res;
 }
 
-__global__ void __launch_bounds__(kAllocThreads) k_alloc(const BatchDev* __restrict__ bp) {
+// One tile of kTile cells per block iteration, 4 consecutive cells per thread.
+constexpr int kAllocPer = kTile / kCellThreads;
+
+__global__ void __launch_bounds__(kCellThreads) k_alloc(const BatchDev* __restrict__ bp) {
   __shared__ int warp_tot[33];
   __shared__ int s_base[3];
   const BatchDev& b = *bp;
-  if ((int)blockIdx.y >= b.n_maps) return;
-  const MapDev& m = b.maps[blockIdx.y];
-  const int32_t ncell = m.W * m.H;
-  const int tile = kAllocThreads * kAllocPer;
-  for (int32_t t0 = blockIdx.x * tile; t0 < ncell; t0 += gridDim.x * tile) {
+  const int64_t n_tiles = b.n_cells / kTile;
+  for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const int64_t g0 = t * kTile;
+    const int mi = find_map_cell(b.maps, b.n_maps, g0);
+    const MapDev& m = b.maps[mi];
+    const int32_t ncell = m.W * m.H;
+    const int64_t p0 = g0 - m.cell_begin;
+    if (p0 >= ncell) continue;  // padding (block-uniform)
     int c[kAllocPer];
-    int sum = 0, ns = 0, nb = 0;
-    const int32_t first = t0 + threadIdx.x * kAllocPer;
+    int sum = 0, nm = 0, nb = 0;
+    const int32_t first = (int32_t)p0 + threadIdx.x * kAllocPer;
 #pragma unroll
     for (int k = 0; k < kAllocPer; ++k) {
       c[k] = (first + k < ncell) ? m.cnt[first + k] : 0;
       sum += c[k];
-      ns += c[k] > 0 && c[k] <= m.big_thresh;
-      nb += c[k] > m.big_thresh;
+      nm += c[k] > b.small_thresh && c[k] <= b.big_thresh;
+      nb += c[k] > b.big_thresh;
     }
-    int tot_c, tot_s, tot_b;
+    int tot_c, tot_m, tot_b;
     const int off_c = block_exclusive_scan(sum, warp_tot, tot_c);
-    const int off_s = block_exclusive_scan(ns, warp_tot, tot_s);
+    const int off_m = block_exclusive_scan(nm, warp_tot, tot_m);
     const int off_b = block_exclusive_scan(nb, warp_tot, tot_b);
     if (threadIdx.x == 0) {
       s_base[0] = tot_c ? atomicAdd(&m.ctl->seg_cursor, tot_c) : 0;
-      s_base[1] = tot_s ? atomicAdd(&m.ctl->n_touched, tot_s) : 0;
-      s_base[2] = tot_b ? atomicAdd(&m.ctl->n_big, tot_b) : 0;
+      s_base[1] = tot_m ? atomicAdd(&b.ctl->n_med, tot_m) : 0;
+      s_base[2] = tot_b ? atomicAdd(&b.ctl->n_big, tot_b) : 0;
     }
     __syncthreads();
     int64_t rec = m.pt_begin + s_base[0] + off_c;
-    int32_t small_slot = s_base[1] + off_s;
-    int32_t big_slot = ncell - 1 - (s_base[2] + off_b);  // large cells fill the list from the back
+    int32_t ms = s_base[1] + off_m, bs = s_base[2] + off_b;
+    int32_t base[kAllocPer];
 #pragma unroll
     for (int k = 0; k < kAllocPer; ++k) {
-      if (c[k] > 0) {
-        const int32_t slot = c[k] > m.big_thresh ? big_slot-- : small_slot++;
-        m.touched[slot] = first + k;
-        m.seg_base[slot] = (int32_t)rec;
-        m.seg_len[slot] = c[k];
-        m.cell_base[first + k] = (int32_t)rec;
-        rec += c[k];
+      base[k] = (int32_t)rec;
+      rec += c[k];
+      if (c[k] > b.big_thresh) {
+        if (bs < b.big_cap) b.big_list[bs] = make_int2(mi, first + k); else atomicExch(&b.ctl->overflow, 1);
+        ++bs;
+      } else if (c[k] > b.small_thresh) {
+        if (ms < b.med_cap) b.med_list[ms] = make_int2(mi, first + k); else atomicExch(&b.ctl->overflow, 1);
+        ++ms;
+      }
+    }
+    if (first + kAllocPer <= ncell) {  // 16-byte stores of the per-cell base / length
+      *reinterpret_cast<int4*>(m.cell_base + first) = make_int4(base[0], base[1], base[2], base[3]);
+      *reinterpret_cast<int4*>(m.cell_len + first) = make_int4(c[0], c[1], c[2], c[3]);
+    } else {
+      for (int k = 0; k < kAllocPer && first + k < ncell; ++k) {
+        m.cell_base[first + k] = base[k];
+        m.cell_len[first + k] = c[k];
       }
     }
     __syncthreads();
@@ -252,17 +272,23 @@ static int point_grid(int64_t n) {
   return (int)(want < cap ? want : cap);
 }
 
-cudaError_t launch_bin(const BatchDev* b, int64_t n_points, cudaStream_t s) {
-  if (n_points <= 0) return cudaSuccess;
-  k_count<<<point_grid(n_points), kPointThreads, 0, s>>>(b);
+static int tile_grid(int64_t n_cells) {
+  const int64_t tiles = n_cells / kTile;
+  const int64_t cap = (int64_t)sm_count() * 8;
+  const int64_t g = tiles < cap ? tiles : cap;
+  return g < 1 ? 1 : (int)g;
+}
+
+cudaError_t launch_bin(const BatchDev* b, int64_t n_points, int64_t n_cells, cudaStream_t s) {
+  const int64_t tiles = n_cells / kTile;
+  int grid = point_grid(n_points);
+  if (grid < tiles && tiles < (int64_t)sm_count() * 8) grid = (int)tiles;  // enough blocks for the cell pass
+  k_count<<<grid, kPointThreads, 0, s>>>(b);
   return cudaGetLastError();
 }
 
-cudaError_t launch_alloc(const BatchDev* b, int32_t n_maps, int32_t max_cells, cudaStream_t s) {
-  int tiles = (max_cells + kAllocThreads * kAllocPer - 1) / (kAllocThreads * kAllocPer);
-  if (tiles > 1024) tiles = 1024;
-  dim3 grid(tiles < 1 ? 1 : tiles, n_maps);
-  k_alloc<<<grid, kAllocThreads, 0, s>>>(b);
+cudaError_t launch_alloc(const BatchDev* b, int64_t n_cells, cudaStream_t s) {
+  k_alloc<<<tile_grid(n_cells), kCellThreads, 0, s>>>(b);
   return cudaGetLastError();
 }
 
