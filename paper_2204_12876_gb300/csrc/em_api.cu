@@ -137,6 +137,7 @@ MapDev make_mapdev(const em_map* m) {
   double x0, y0;
   host_origin(m, &x0, &y0);
   d.x0 = (float)x0; d.y0 = (float)y0; d.res = m->p.resolution;
+  d.inv_res = (float)(1.0 / (double)m->p.resolution);
   d.t_now = m->t_now;
   d.a0 = m->p.noise_a0; d.a1 = m->p.noise_a1; d.a2 = m->p.noise_a2; d.var_min = m->p.var_min;
   d.min_range = m->p.min_range; d.max_range = m->p.max_range; d.k = m->p.mahalanobis_k;

@@ -77,13 +77,12 @@ struct MapDev {
   int64_t pt_count;
   int64_t cell_begin;  // this map's first cell in the batch cell space (multiple of kTile)
   int32_t W, H, ox, oy;
-  float x0, y0, res;
+  float x0, y0, res, inv_res;  // inv_res = 1 / res rounded to float
   int32_t t_now;       // index of this update
   // method parameters
   float a0, a1, a2, var_min, min_range, max_range, k, v_out, sigma_t2, ray_step, alpha_n;
   int32_t wall, min_age;
   uint32_t flags;
-  int32_t pad;
 };
 
 struct CloudDev {

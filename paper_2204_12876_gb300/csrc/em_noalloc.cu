@@ -149,6 +149,7 @@ extern "C" int em_update_noalloc(const em_params* params, int64_t shift_x, int64
   m->x0 = (float)(r * ((double)shift_x - 0.5 * W));
   m->y0 = (float)(r * ((double)shift_y - 0.5 * H));
   m->res = params->resolution;
+  m->inv_res = (float)(1.0 / (double)params->resolution);
   m->t_now = t_now;
   m->a0 = params->noise_a0; m->a1 = params->noise_a1; m->a2 = params->noise_a2; m->var_min = params->var_min;
   m->min_range = params->min_range; m->max_range = params->max_range; m->k = params->mahalanobis_k;

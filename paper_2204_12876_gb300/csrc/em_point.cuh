@@ -19,7 +19,7 @@ struct PointGeom {
 };
 
 // Transform by the sensor pose (Section II-A), distance, cell indices
-// ix = floor((x - x0) / r) of the robot-centric grid.
+// ix = floor((x - x0) / r) of the robot-centric grid (as (x - x0) * (1/r)).
 __device__ __forceinline__ PointGeom point_geom(const MapDev& m, const CloudDev& c, float px, float py,
                                                 float pz) {
   PointGeom g;
@@ -33,8 +33,8 @@ __device__ __forceinline__ PointGeom point_geom(const MapDev& m, const CloudDev&
   g.x = __fadd_rn(g.vx, c.t[0]);
   g.y = __fadd_rn(g.vy, c.t[1]);
   g.z = __fadd_rn(g.vz, c.t[2]);
-  g.ix = clamp_floor(__fdiv_rn(__fsub_rn(g.x, m.x0), m.res));
-  g.iy = clamp_floor(__fdiv_rn(__fsub_rn(g.y, m.y0), m.res));
+  g.ix = clamp_floor(__fmul_rn(__fsub_rn(g.x, m.x0), m.inv_res));
+  g.iy = clamp_floor(__fmul_rn(__fsub_rn(g.y, m.y0), m.inv_res));
   return g;
 }
 
@@ -89,6 +89,19 @@ __device__ __forceinline__ void add_counter(const BatchDev& b, MapCounters& mc, 
     for (int k = 0; k < n; ++k) mc.v[k] = 0;
   }
   for (int k = 0; k < n; ++k) mc.v[k] += inc[k];
+}
+
+// Runs of equal keys in consecutive lanes (sensor order puts neighbouring
+// points in the same cell): head = first lane of this lane's run, len = run
+// length (meaningful on the head lane).  All 32 lanes must call it.
+__device__ __forceinline__ void key_runs(unsigned long long tag, int& head, int& len) {
+  const int lane = threadIdx.x & 31;
+  const unsigned long long prev = __shfl_up_sync(0xffffffffu, tag, 1);
+  const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || prev != tag);
+  const unsigned le = lane == 31 ? 0xffffffffu : ((1u << (lane + 1)) - 1u);
+  head = 31 - __clz(heads & le);
+  const unsigned above = heads & ~le;
+  len = (above ? __ffs(above) - 1 : 32) - lane;
 }
 
 // Load point g of cloud c (stride 3 or 4) with scalar loads.

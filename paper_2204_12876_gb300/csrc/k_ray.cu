@@ -1,10 +1,11 @@
 // k_ray.cu -- visibility cleanup by ray casting (Section II-E of the paper).
 //
-// k_ray: a group of G lanes per valid point.  The ray from the sensor origin o
-// (the pose translation) to the point is sampled at
-// s_k = o + (k step / d) (R p_s) for k = 1, 2, ... while k step < d; lane j of
-// the group takes k = k_lo + j, k_lo + j + G, ..., so the group keeps G
-// independent gathers in flight.  A sample inside the map, outside the point's
+// k_ray: one ray per valid point, marched by a group of G lanes.  The ray from
+// the sensor origin o (the pose translation) to the point is sampled at
+// s_k = o + (k step / d) (R p_s) for k = 1, 2, ... while k step < d (computed
+// as a + k b in cell units: one FMA per coordinate); lane j of the group takes
+// k = k_lo + j, k_lo + j + G, ..., so the group keeps G independent gathers in
+// flight.  A sample inside the map, outside the point's
 // own cell, below the cell's threshold h - sqrt(sigma_m^2) of the pre-update
 // map (Eq. 3; the threshold layer is -inf for empty cells) and -- when
 // alpha_n > 0 -- with |rhat . n| > alpha_n for the cell's previous normal
@@ -34,69 +35,123 @@ __device__ __forceinline__ bool slab(float o, float v, float d, float a0, float 
   return true;
 }
 
+// Per-ray set-up shared by the lanes that march it.  Sample k lies at
+// q = a + k b in cell units (x, y) and at z = az + k bz, i.e. the track
+// o + (k step / d) (R p_s) measured from the map corner in cells.
+struct RaySetup {
+  float ax, bx, ay, by, az, bz;
+  float vx, vy, vz, d;  // for the Eq. 4 guard
+  int32_t ix, iy, k_lo, n, map;
+};
+
+// Each warp takes 32 consecutive points: first every lane sets up one ray
+// (transform, distance, own cell, the k range inside the map box and before
+// the point), then the warp marches them G lanes per ray, 32 / G rays at a
+// time, so the set-up cost is paid once per ray.
 template <int G>
 __global__ void __launch_bounds__(kRayThreads) k_ray(const BatchDev* __restrict__ bp) {
+  __shared__ RaySetup s_ray[kRayThreads];
   const BatchDev& b = *bp;
-  const int gl = (threadIdx.x & 31) % G;
-  const int64_t group = ((int64_t)blockIdx.x * kRayThreads + threadIdx.x) / G;
-  const int64_t n_groups = (int64_t)gridDim.x * kRayThreads / G;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  RaySetup* wr = s_ray + warp * 32;
+  const int64_t n_warps = (int64_t)gridDim.x * (kRayThreads / 32);
   MapCounters mc;
   const int stat_idx[1] = {kStRaySamples};
   unsigned long long samples = 0;
-  for (int64_t g = group; g < b.n_points; g += n_groups) {
-    const int ci = find_cloud(b.clouds, b.n_clouds, g);
-    const CloudDev& c = b.clouds[ci];
-    const MapDev& m = b.maps[c.map];
-    if (m.ray_step <= 0.f) continue;
-    float px, py, pz;
-    load_point(c, g - c.begin, px, py, pz);
-    const PointGeom pg = point_geom(m, c, px, py, pz);
-    if (!pg.in_range || !(pg.d > 0.f)) continue;
-    if (c.map != mc.map) {  // fold this map's samples in, then switch maps
-      if (mc.map >= 0) add_counter(b, mc, mc.map, stat_idx, 1, &samples);
-      samples = 0;
-      add_counter(b, mc, c.map, stat_idx, 1, &samples);
-    }
-    // clip the sample range to the map box (conservative by 1 mm + 1 step)
-    float lo = 0.f, hi = pg.d;
-    const float ext_x = __fmul_rn((float)m.W, m.res), ext_y = __fmul_rn((float)m.H, m.res);
-    if (!slab(c.t[0], pg.vx, pg.d, m.x0, m.x0 + ext_x, lo, hi)) continue;
-    if (!slab(c.t[1], pg.vy, pg.d, m.y0, m.y0 + ext_y, lo, hi)) continue;
-    if (lo > hi + 1e-3f) continue;
-    const float step = m.ray_step;
-    const float kl = floorf((lo - 1e-3f) / step) - 1.f;
-    const float kh = ceilf((hi + 1e-3f) / step) + 1.f;
-    const int32_t k_lo = kl < 1.f ? 1 : (int32_t)kl;
-    const int32_t k_hi = kh > 1.0e9f ? 1000000000 : (int32_t)kh;
-    const float cstep = __fdiv_rn(step, pg.d);  // f_k = k * step / d
-    const float inv_res = __frcp_rn(m.res);
-    const bool guard = m.alpha_n > 0.f;
-    for (int32_t k = k_lo + gl; k <= k_hi; k += G) {
-      const float len = __fmul_rn((float)k, step);
-      if (!(len < pg.d)) break;
-      const float f = __fmul_rn((float)k, cstep);
-      const float sx = __fmaf_rn(f, pg.vx, c.t[0]);
-      const float sy = __fmaf_rn(f, pg.vy, c.t[1]);
-      const int32_t cx = clamp_floor(__fmul_rn(__fsub_rn(sx, m.x0), inv_res));
-      const int32_t cy = clamp_floor(__fmul_rn(__fsub_rn(sy, m.y0), inv_res));
-      if (!in_map(m, cx, cy)) continue;
-      ++samples;
-      if (cx == pg.ix && cy == pg.iy) continue;
-      const int32_t p = phys_index(m, cx, cy);
-      const float sz = __fmaf_rn(f, pg.vz, c.t[2]);
-      if (!(sz < __ldg(m.thr + p))) continue;
-      if (guard) {
-        float n0 = m.nx[p], n1 = m.ny[p], n2 = m.nz[p];
-        if (!(isfinite(n0) && isfinite(n1) && isfinite(n2))) { n0 = 0.f; n1 = 0.f; n2 = 1.f; }
-        const float rx = __fdiv_rn(pg.vx, pg.d), ry = __fdiv_rn(pg.vy, pg.d), rz = __fdiv_rn(pg.vz, pg.d);
-        const float dot = fabsf(__fmaf_rn(rx, n0, __fmaf_rn(ry, n1, __fmul_rn(rz, n2))));
-        if (!(dot > m.alpha_n)) continue;
+  for (int64_t wbase = ((int64_t)blockIdx.x * (kRayThreads / 32) + warp) * 32; wbase < b.n_points;
+       wbase += n_warps * 32) {
+    // ---- set-up: one ray per lane
+    RaySetup r;
+    r.n = 0;
+    r.map = 0;
+    const int64_t g = wbase + lane;
+    if (g < b.n_points) {
+      const int ci = find_cloud(b.clouds, b.n_clouds, g);
+      const CloudDev& c = b.clouds[ci];
+      const MapDev& m = b.maps[c.map];
+      r.map = c.map;
+      if (m.ray_step > 0.f) {
+        float px, py, pz;
+        load_point(c, g - c.begin, px, py, pz);
+        const PointGeom pg = point_geom(m, c, px, py, pz);
+        // clip the sample range to the map box (conservative by 1 mm + 1 step)
+        float lo = 0.f, hi = pg.d;
+        const float ext_x = __fmul_rn((float)m.W, m.res), ext_y = __fmul_rn((float)m.H, m.res);
+        if (pg.in_range && pg.d > 0.f && slab(c.t[0], pg.vx, pg.d, m.x0, m.x0 + ext_x, lo, hi) &&
+            slab(c.t[1], pg.vy, pg.d, m.y0, m.y0 + ext_y, lo, hi) && lo <= hi + 1e-3f) {
+          const float step = m.ray_step;
+          const float kl = floorf((lo - 1e-3f) / step) - 1.f;
+          const float kh = ceilf((hi + 1e-3f) / step) + 1.f;
+          const int32_t k_lo = kl < 1.f ? 1 : (int32_t)kl;
+          int32_t k_hi = kh > 1.0e9f ? 1000000000 : (int32_t)kh;
+          // last k with k * step < d, decided exactly as sample by sample
+          float kf = floorf(__fdiv_rn(pg.d, step));
+          int32_t k_last = kf > 1.0e9f ? 1000000000 : (int32_t)kf;
+          while (k_last > 0 && !(__fmul_rn((float)k_last, step) < pg.d)) --k_last;
+          while (k_last < 1000000000 && __fmul_rn((float)(k_last + 1), step) < pg.d) ++k_last;
+          if (k_last < k_hi) k_hi = k_last;
+          const float cstep = __fdiv_rn(step, pg.d);  // f_k = k * step / d
+          r.ax = __fmul_rn(__fsub_rn(c.t[0], m.x0), m.inv_res);
+          r.ay = __fmul_rn(__fsub_rn(c.t[1], m.y0), m.inv_res);
+          r.bx = __fmul_rn(__fmul_rn(cstep, pg.vx), m.inv_res);
+          r.by = __fmul_rn(__fmul_rn(cstep, pg.vy), m.inv_res);
+          r.az = c.t[2];
+          r.bz = __fmul_rn(cstep, pg.vz);
+          r.vx = pg.vx; r.vy = pg.vy; r.vz = pg.vz;
+          r.d = pg.d;
+          r.ix = pg.ix;
+          r.iy = pg.iy;
+          r.k_lo = k_lo;
+          r.n = k_hi >= k_lo ? k_hi - k_lo + 1 : 0;
+        }
       }
-      // many rays graze the same surface cells: skip the atomic when the bit is
-      // already set (marks are only ever set during this kernel)
-      const uint32_t bit = 1u << (p & 31);
-      if (!(*(volatile uint32_t*)(m.mark + (p >> 5)) & bit)) atomicOr(&m.mark[p >> 5], bit);
     }
+    wr[lane] = r;
+    __syncwarp();
+    // ---- march: G lanes per ray
+    const int gl = lane % G;
+    for (int r0 = 0; r0 < 32; r0 += 32 / G) {
+      const RaySetup& R = wr[r0 + lane / G];
+      if (R.n <= 0) continue;
+      if (R.map != mc.map) {  // fold this map's samples in, then switch maps
+        if (mc.map >= 0) add_counter(b, mc, mc.map, stat_idx, 1, &samples);
+        samples = 0;
+        add_counter(b, mc, R.map, stat_idx, 1, &samples);
+      }
+      const MapDev& m = b.maps[R.map];
+      const uint32_t W = (uint32_t)m.W, H = (uint32_t)m.H;
+      const int32_t ox = m.ox, oy = m.oy;
+      const float* __restrict__ thr = m.thr;
+      const bool guard = m.alpha_n > 0.f;
+      const int32_t k_end = R.k_lo + R.n;
+      const float ax = R.ax, bx = R.bx, ay = R.ay, by = R.by, az = R.az, bz = R.bz;
+      for (int32_t k = R.k_lo + gl; k < k_end; k += G) {
+        const float kf = (float)k;
+        const int32_t cx = __float2int_rd(__fmaf_rn(kf, bx, ax));  // floor; saturates far outside
+        const int32_t cy = __float2int_rd(__fmaf_rn(kf, by, ay));
+        if ((uint32_t)cx >= W || (uint32_t)cy >= H) continue;
+        ++samples;
+        if (cx == R.ix && cy == R.iy) continue;
+        int32_t px = cx + ox;
+        px -= (px >= (int32_t)W) ? (int32_t)W : 0;
+        int32_t py = cy + oy;
+        py -= (py >= (int32_t)H) ? (int32_t)H : 0;
+        const int32_t p = py * (int32_t)W + px;
+        if (!(__fmaf_rn(kf, bz, az) < __ldg(thr + p))) continue;
+        if (guard) {
+          float n0 = m.nx[p], n1 = m.ny[p], n2 = m.nz[p];
+          if (!(isfinite(n0) && isfinite(n1) && isfinite(n2))) { n0 = 0.f; n1 = 0.f; n2 = 1.f; }
+          const float rx = __fdiv_rn(R.vx, R.d), ry = __fdiv_rn(R.vy, R.d), rz = __fdiv_rn(R.vz, R.d);
+          const float dot = fabsf(__fmaf_rn(rx, n0, __fmaf_rn(ry, n1, __fmul_rn(rz, n2))));
+          if (!(dot > m.alpha_n)) continue;
+        }
+        // many rays graze the same surface cells: skip the atomic when the bit is
+        // already set (marks are only ever set during this kernel)
+        const uint32_t bit = 1u << (p & 31);
+        if (!(*(volatile uint32_t*)(m.mark + (p >> 5)) & bit)) atomicOr(&m.mark[p >> 5], bit);
+      }
+    }
+    __syncwarp();
   }
   if (mc.map >= 0) add_counter(b, mc, mc.map, stat_idx, 1, &samples);
   flush_counters(b, mc, stat_idx, 1);
@@ -138,7 +193,7 @@ __global__ void __launch_bounds__(kClearThreads) k_clear(const BatchDev* __restr
 cudaError_t launch_ray(const BatchDev* b, int64_t n_points, int group, cudaStream_t s) {
   if (n_points <= 0) return cudaSuccess;
   const int g = (group == 1 || group == 2 || group == 4 || group == 8 || group == 16 || group == 32) ? group : 4;
-  const int64_t want = (n_points * g + kRayThreads - 1) / kRayThreads;
+  const int64_t want = (n_points + kRayThreads - 1) / kRayThreads;  // one 32-ray chunk per warp
   const int64_t cap = (int64_t)sm_count() * 16;
   const int grid = (int)(want < cap ? want : cap);
   switch (g) {

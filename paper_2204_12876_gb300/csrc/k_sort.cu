@@ -108,8 +108,9 @@ __global__ void __launch_bounds__(kPointThreads) k_count(const BatchDev* __restr
       }
     }
     const unsigned long long tag = inm ? ((unsigned long long)(uint32_t)c.map << 32) | (uint32_t)key : ~0ull;
-    const unsigned peers = __match_any_sync(kFull, tag);
-    if (inm && lane == __ffs(peers) - 1) atomicAdd(&m.cnt[key], __popc(peers));
+    int head, run;
+    key_runs(tag, head, run);
+    if (inm && lane == head) atomicAdd(&m.cnt[key], run);
   }
   flush_counters(b, mc, idx, 2);
   // ray thresholds of the pre-update map over the cell space (Eq. 3)
@@ -231,13 +232,13 @@ __global__ void __launch_bounds__(kPointThreads) k_scatter(const BatchDev* __res
     const bool inm = live && pg.in_range && in_map(m, pg.ix, pg.iy);
     const int32_t key = inm ? phys_index(m, pg.ix, pg.iy) : -1;
     const unsigned long long tag = inm ? ((unsigned long long)(uint32_t)c.map << 32) | (uint32_t)key : ~0ull;
-    const unsigned peers = __match_any_sync(kFull, tag);
+    int head, run;
+    key_runs(tag, head, run);
     int old = 0;
-    const int leader = __ffs(peers) - 1;
-    if (inm && lane == leader) old = atomicSub(&m.cnt[key], __popc(peers));
-    old = __shfl_sync(kFull, old, leader);
+    if (inm && lane == head) old = atomicSub(&m.cnt[key], run);
+    old = __shfl_sync(kFull, old, head);
     if (inm) {
-      const int rank = __popc(peers & ((1u << lane) - 1));
+      const int rank = lane - head;
       const int64_t pos = (int64_t)m.cell_base[key] + old - 1 - rank;
       // the count pass found the same cell for this point, so pos lies in the
       // cell's segment; anything else is recorded instead of written
