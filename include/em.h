@@ -116,7 +116,7 @@ typedef struct em_stats {
   int64_t points_wall;      /* dropped by the wall rule */
   int64_t cells_updated;    /* (cell, update) pairs written by fusion */
   int64_t cells_cleared;    /* (cell, update) pairs removed by visibility cleanup */
-  int64_t ray_samples;      /* ray-march samples taken inside the map */
+  int64_t ray_samples;      /* ray-march sample positions in each ray's k range clipped to the map box */
 } em_stats;
 
 /* Create a map of params->width x params->height empty cells centred on the

@@ -104,7 +104,7 @@ struct em_map {
   int64_t layer_bytes = 0;
   int64_t work_bytes = 0;
   int fuse_group = 8;
-  int ray_group = 2;
+  int ray_group = 4;
   int big_thresh = 64;
   int small_thresh = 8;
   int64_t points_in = 0;

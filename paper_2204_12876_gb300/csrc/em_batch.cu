@@ -63,7 +63,7 @@ struct em_batch {
   unsigned char* desc_dev = nullptr;
   cudaEvent_t ev[kSlots] = {};
   int slot = 0;
-  em_tuning tune{2, 8, 64, 8};
+  em_tuning tune{4, 8, 64, 8};
   cudaStream_t capture_stream = nullptr;
   cudaGraphExec_t graph[kSlots] = {};
   GraphKey graph_key[kSlots] = {};

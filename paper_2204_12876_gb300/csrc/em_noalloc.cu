@@ -196,7 +196,7 @@ extern "C" int em_update_noalloc(const em_params* params, int64_t shift_x, int64
   const int64_t cells = pad_tile(ncell);
   cudaError_t e = launch_bin(bd, total, cells, s);
   if (total > 0) {
-    if (e == cudaSuccess && params->ray_step > 0.f) e = launch_ray(bd, total, 2, s);
+    if (e == cudaSuccess && params->ray_step > 0.f) e = launch_ray(bd, total, 4, s);
     if (e == cudaSuccess) e = launch_alloc(bd, cells, s);
     if (e == cudaSuccess) e = launch_scatter(bd, total, s);
     if (e == cudaSuccess) e = launch_fuse(bd, cells, total, 8, s);

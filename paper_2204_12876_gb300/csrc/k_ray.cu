@@ -5,7 +5,7 @@
 // s_k = o + (k step / d) (R p_s) for k = 1, 2, ... while k step < d (computed
 // as a + k b in cell units: one FMA per coordinate); lane j of the group takes
 // k = k_lo + j, k_lo + j + G, ..., so the group keeps G independent gathers in
-// flight.  A sample inside the map, outside the point's
+// flight, and each lane loads the thresholds of 4 samples before testing them.  A sample inside the map, outside the point's
 // own cell, below the cell's threshold h - sqrt(sigma_m^2) of the pre-update
 // map (Eq. 3; the threshold layer is -inf for empty cells) and -- when
 // alpha_n > 0 -- with |rhat . n| > alpha_n for the cell's previous normal
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(kRayThreads) k_ray(const BatchDev* __restrict_
     }
     wr[lane] = r;
     __syncwarp();
-    // ---- march: G lanes per ray
+    // ---- march: G lanes per ray, 4 samples per lane and step (4 gathers in flight)
     const int gl = lane % G;
     for (int r0 = 0; r0 < 32; r0 += 32 / G) {
       const RaySetup& R = wr[r0 + lane / G];
@@ -118,37 +118,48 @@ __global__ void __launch_bounds__(kRayThreads) k_ray(const BatchDev* __restrict_
         samples = 0;
         add_counter(b, mc, R.map, stat_idx, 1, &samples);
       }
+      if (gl == 0) samples += (unsigned long long)R.n;
       const MapDev& m = b.maps[R.map];
-      const uint32_t W = (uint32_t)m.W, H = (uint32_t)m.H;
-      const int32_t ox = m.ox, oy = m.oy;
+      const int32_t W = m.W, H = m.H, ox = m.ox, oy = m.oy;
       const float* __restrict__ thr = m.thr;
       const bool guard = m.alpha_n > 0.f;
       const int32_t k_end = R.k_lo + R.n;
       const float ax = R.ax, bx = R.bx, ay = R.ay, by = R.by, az = R.az, bz = R.bz;
-      for (int32_t k = R.k_lo + gl; k < k_end; k += G) {
-        const float kf = (float)k;
-        const int32_t cx = __float2int_rd(__fmaf_rn(kf, bx, ax));  // floor; saturates far outside
-        const int32_t cy = __float2int_rd(__fmaf_rn(kf, by, ay));
-        if ((uint32_t)cx >= W || (uint32_t)cy >= H) continue;
-        ++samples;
-        if (cx == R.ix && cy == R.iy) continue;
-        int32_t px = cx + ox;
-        px -= (px >= (int32_t)W) ? (int32_t)W : 0;
-        int32_t py = cy + oy;
-        py -= (py >= (int32_t)H) ? (int32_t)H : 0;
-        const int32_t p = py * (int32_t)W + px;
-        if (!(__fmaf_rn(kf, bz, az) < __ldg(thr + p))) continue;
-        if (guard) {
-          float n0 = m.nx[p], n1 = m.ny[p], n2 = m.nz[p];
-          if (!(isfinite(n0) && isfinite(n1) && isfinite(n2))) { n0 = 0.f; n1 = 0.f; n2 = 1.f; }
-          const float rx = __fdiv_rn(R.vx, R.d), ry = __fdiv_rn(R.vy, R.d), rz = __fdiv_rn(R.vz, R.d);
-          const float dot = fabsf(__fmaf_rn(rx, n0, __fmaf_rn(ry, n1, __fmul_rn(rz, n2))));
-          if (!(dot > m.alpha_n)) continue;
+      for (int32_t k = R.k_lo + gl; k < k_end; k += 4 * G) {
+        int32_t pp[4];
+        float zz[4], th[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int32_t kk = k + u * G;
+          const float kf = (float)kk;
+          const int32_t cx = __float2int_rd(__fmaf_rn(kf, bx, ax));  // floor; saturates far outside
+          const int32_t cy = __float2int_rd(__fmaf_rn(kf, by, ay));
+          const bool ok = kk < k_end && (uint32_t)cx < (uint32_t)W && (uint32_t)cy < (uint32_t)H &&
+                          !(cx == R.ix && cy == R.iy);
+          int32_t px = cx + ox;
+          px -= (px >= W) ? W : 0;
+          int32_t py = cy + oy;
+          py -= (py >= H) ? H : 0;
+          pp[u] = ok ? py * W + px : -1;
+          zz[u] = __fmaf_rn(kf, bz, az);
+          th[u] = ok ? __ldg(thr + pp[u]) : __int_as_float(0xff800000);
         }
-        // many rays graze the same surface cells: skip the atomic when the bit is
-        // already set (marks are only ever set during this kernel)
-        const uint32_t bit = 1u << (p & 31);
-        if (!(*(volatile uint32_t*)(m.mark + (p >> 5)) & bit)) atomicOr(&m.mark[p >> 5], bit);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (!(zz[u] < th[u])) continue;  // also skips the samples that are not taken (th = -inf)
+          const int32_t p = pp[u];
+          if (guard) {
+            float n0 = m.nx[p], n1 = m.ny[p], n2 = m.nz[p];
+            if (!(isfinite(n0) && isfinite(n1) && isfinite(n2))) { n0 = 0.f; n1 = 0.f; n2 = 1.f; }
+            const float rx = __fdiv_rn(R.vx, R.d), ry = __fdiv_rn(R.vy, R.d), rz = __fdiv_rn(R.vz, R.d);
+            const float dot = fabsf(__fmaf_rn(rx, n0, __fmaf_rn(ry, n1, __fmul_rn(rz, n2))));
+            if (!(dot > m.alpha_n)) continue;
+          }
+          // many rays graze the same surface cells: skip the atomic when the bit is
+          // already set (marks are only ever set during this kernel)
+          const uint32_t bit = 1u << (p & 31);
+          if (!(*(volatile uint32_t*)(m.mark + (p >> 5)) & bit)) atomicOr(&m.mark[p >> 5], bit);
+        }
       }
     }
     __syncwarp();
