@@ -10,8 +10,9 @@ fusion, visibility ray march and removal).  The server (em_server) admits
 requests by a 40 GB budget and batches them continuously.
 
   value          fused points/s of the served path at saturation: K rounds of
-                 one request per robot, all submitted at once, wall time
-                 between synchronised brackets.  One step = one round.
+                 one request per robot, all submitted at once, timed with
+                 CUDA events recorded with the device idle on both sides
+                 (barrier + synchronize).  One step = one round.
   latency_ms     p50 / p99 request latency (submit -> GPU done) at the stated
                  load, 2,000 updates/s Poisson, for the served and the plain
                  per-request path (one em_update per request).
@@ -166,6 +167,30 @@ def ncu_traffic(kernel: str, workload: str):
         return None
 
 
+# ---------------------------------------------------------------- ranks
+
+def fleet_seed(rank: int) -> int:
+    """Each rank serves its own fleet (maps are independent: no exchange)."""
+    return 5 + 100 * rank
+
+
+def rank_max(world: int, device: str):
+    """x -> max of x over all ranks (the slowest rank sets the job's time)."""
+    def f(x: float) -> float:
+        if world == 1:
+            return x
+        import torch
+        t = torch.tensor([x], device=device, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+    return f
+
+
+def job_rate(units_per_rank: float, world: int, seconds_max: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the max time."""
+    return units_per_rank * world / seconds_max
+
+
 # ---------------------------------------------------------------- workloads
 
 def make_fleet(seed: int = 5):
@@ -209,15 +234,9 @@ def run_ours(args, rank: int, world: int):
         if world > 1:
             torch.distributed.barrier()
 
-    def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
-
-    robots = make_fleet(seed=5 + 100 * rank)
-    pools = make_pools(seed=5 + 100 * rank)
+    max_over_ranks = rank_max(world, "cuda")
+    robots = make_fleet(seed=fleet_seed(rank))
+    pools = make_pools(seed=fleet_seed(rank))
     dpools = {k: [(torch.from_numpy(p).cuda(), q) for p, q in v] for k, v in pools.items()}
     round_pts = sum(len(request_cloud(pools, robots, i, 0)[0]) for i in range(N_ROBOTS))
 
@@ -232,30 +251,40 @@ def run_ours(args, rank: int, world: int):
         return [srv.submit(ids[i], [request_cloud(dpools, robots, i, k)]) for i in range(N_ROBOTS)]
 
     def saturate(srv, ids, K, k0):
-        """K rounds submitted at once; returns (seconds, points, results)."""
+        """K rounds submitted at once; returns (seconds, points, batches).  The
+        span is taken with CUDA events on this thread's stream, recorded with
+        the device idle on both sides (the server's streams have drained before
+        the closing record), so it covers every batch of the K rounds."""
+        b0 = srv.stats()["batches"]
         barrier()
-        t0 = time.perf_counter()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
         tickets = []
         for k in range(K):
             tickets += submit_round(srv, ids, k0 + k)
-        res = [srv.wait(t) for t in tickets]
+        for t in tickets:
+            srv.wait(t)
+        e1.record()
         barrier()
-        return max_over_ranks(time.perf_counter() - t0), K * round_pts, res
+        sec = e0.elapsed_time(e1) / 1e3
+        return max_over_ranks(sec), K * round_pts, srv.stats()["batches"] - b0
 
-    # ---- served path: autotune the batch shapes on one round (scratch copies of the maps)
+    # ---- served path: warm up (the maps fill), then autotune the batch shapes
+    # on one round (scratch copies of the maps: the served maps do not advance)
     served, sids = new_server(em.SERVE_BATCHED)
-    tuner = em.Batch(max_maps=N_ROBOTS, max_clouds=N_ROBOTS, max_points=N_ROBOTS * 262144, max_cells=500 * 500,
-                     graph=False, device=dev)
-    pairs = [(served.map(sids[i]), *request_cloud(dpools, robots, i, 0)) for i in range(N_ROBOTS)]
-    tuning = tuner.autotune(pairs, reps=3)
-    served.set_tuning(**tuning)
     for k in range(args.warmup):
         for t in submit_round(served, sids, k):
             served.wait(t)
+    served.drain()
+    tuner = em.Batch(max_maps=N_ROBOTS, max_clouds=N_ROBOTS, max_points=N_ROBOTS * 262144, max_cells=500 * 500,
+                     graph=False, device=dev)
+    pairs = [(served.map(sids[i]), *request_cloud(dpools, robots, i, args.warmup)) for i in range(N_ROBOTS)]
+    tuning = tuner.autotune(pairs, reps=3)
+    served.set_tuning(**tuning)
     K = args.steps
     with ClockSampler(dev) as clk:
-        sec, pts, res = saturate(served, sids, K, args.warmup)
-    value = pts * world / sec
+        sec, pts, timed_batches = saturate(served, sids, K, args.warmup)
+    value = job_rate(pts, world, sec)
     sst = served.stats()
 
     # ---- plain per-request path at saturation (fresh maps)
@@ -264,7 +293,7 @@ def run_ours(args, rank: int, world: int):
         for t in submit_round(plain, pids, k):
             plain.wait(t)
     psec, ppts, _ = saturate(plain, pids, K, args.warmup)
-    plain_value = ppts * world / psec
+    plain_value = job_rate(ppts, world, psec)
 
     # ---- latency at the stated load: Poisson arrivals, 2,000 updates/s in total
     rng = np.random.default_rng(77 + rank)
@@ -380,7 +409,7 @@ def run_ours(args, rank: int, world: int):
         "served_batches": {"batches": sst["batches"], "mean_batch": sst["batched_requests"] / max(1, sst["batches"]),
                            "max_batch": sst["max_batch_size"], "peak_bytes": sst["peak_bytes"]},
         "e2e": e2e,
-        "gpu_launches": int(sst["batches"]) * len([k for k in prof if prof[k][1]]),
+        "gpu_launches": int(timed_batches) * len([k for k in prof if prof[k][1]]),
         "roofline": roofline,
         "kernels": kernels,
         "per_round": {"ray_samples": samples, "points_in_map": in_map, "cells_updated": cells_upd},
@@ -412,9 +441,9 @@ def run_batched(args, em, torch, dev, barrier, max_over_ranks, world):
     max_cells = max(w["side"] ** 2 for w in work)
     batch = em.Batch(max_maps=64, max_clouds=64, max_points=pts_step, max_cells=max_cells, graph=True, device=dev)
     pairs = [(m, p, q) for m, (p, q) in zip(maps, clouds)]
-    tuning = batch.autotune(pairs, reps=3)
     for _ in range(args.warmup):
         batch.update(pairs)
+    tuning = batch.autotune(pairs, reps=3)  # on scratch copies of the warmed-up maps
     K = args.steps
     st0 = [m.stats() for m in maps]
     barrier()

@@ -68,7 +68,7 @@ struct MapDev {
   float* smooth;    // may be null
   float* inpaint;   // may be null
   uint32_t* mark;   // visibility marks, one bit per physical cell, zero between updates
-  float* thr;       // per physical cell: h - sqrt(var_eff) of the pre-update map, -inf if empty
+  float* thr;       // per LOGICAL cell [iy][ix]: h - sqrt(var_eff) of the pre-update map, -inf if empty
   int32_t* cnt;     // per physical cell point count, zero between updates
   int32_t* cell_base;  // per physical cell: start of its segment of records (this update)
   int32_t* cell_len;   // per physical cell: number of records (this update)

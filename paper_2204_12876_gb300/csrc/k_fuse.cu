@@ -5,8 +5,9 @@
 //   1. wall rule: in a valid cell with more than wall_num_thresh points, points
 //      below the current height are dropped (before the outlier test);
 //   2. Mahalanobis gate against the pre-update estimate: reject iff
-//      |z - h| / sqrt(sigma_m^2 + sigma_p^2) > k; every rejection adds
-//      outlier_variance to sigma_m^2;
+//      |z - h| / sqrt(sigma_m^2 + sigma_p^2) > k, tested as
+//      (z - h)^2 > k^2 (sigma_m^2 + sigma_p^2) (no division or square root);
+//      every rejection adds outlier_variance to sigma_m^2;
 //   3. Eq. 1 and Eq. 2 for all accepted points at once, in information form:
 //        Lambda = 1 / (sigma_m^2 + n_rej v_out) + sum_i 1/sigma_p,i^2
 //        h'     = h + sum_i (z_i - h) / sigma_p,i^2 / Lambda,   sigma_m^2' = 1 / Lambda
@@ -35,35 +36,57 @@ constexpr int kFuseThreads = 256;
 constexpr int kFuseWarps = kFuseThreads / 32;
 
 // trunc(a * 2^44) as a signed 128-bit integer, exact for |a| >= 2^-44 (bits
-// below 2^-44 are dropped, the same way for every order of summation).
+// below 2^-44 are dropped, the same way for every order of summation).  The
+// 24-bit significand is placed with 64-bit shifts into the two halves.
 __device__ __forceinline__ __int128 to_fixed(float a) {
   const uint32_t u = __float_as_uint(a);
   const int e = (int)((u >> 23) & 0xffu);
-  if (e == 0) return 0;
-  const uint32_t mant = (u & 0x7fffffu) | 0x800000u;
-  int sh = e - 106;  // a = mant * 2^(e - 150); a * 2^44 = mant * 2^(e - 106)
-  unsigned __int128 v;
-  if (sh >= 0) {
-    if (sh > 100) sh = 100;  // |a| >= 2^78: saturate (never reached by bounded inputs)
-    v = (unsigned __int128)mant << sh;
-  } else if (sh > -32) {
-    v = (unsigned __int128)(mant >> (-sh));
+  const unsigned long long mant = (u & 0x7fffffu) | 0x800000u;
+  int sh = e - 106;          // a = mant * 2^(e - 150); a * 2^44 = mant * 2^(e - 106)
+  sh = sh > 100 ? 100 : sh;  // |a| >= 2^78: saturate (never reached by bounded inputs)
+  unsigned long long lo, hi;
+  if (e == 0 || sh <= -32) {
+    lo = 0; hi = 0;
+  } else if (sh < 0) {
+    lo = mant >> (-sh); hi = 0;
+  } else if (sh <= 40) {
+    lo = mant << sh; hi = 0;
+  } else if (sh < 64) {
+    lo = mant << sh; hi = mant >> (64 - sh);
   } else {
-    v = 0;
+    lo = 0; hi = mant << (sh - 64);
   }
-  const __int128 r = (__int128)v;
+  const __int128 r = (__int128)(((unsigned __int128)hi << 64) | lo);
   return (u >> 31) ? -r : r;
 }
 
-// s * 2^-44 rounded to float (through a double of the magnitude).
+// s * 2^-44 rounded to the nearest float (ties to even), in integer arithmetic
+// (this part's FP64 rate is a small fraction of its integer rate).  Every
+// nonzero |s| < 2^127 gives a normal float: 2^-44 <= |s| 2^-44 < 2^83.
 __device__ __forceinline__ float from_fixed(__int128 s) {
-  const bool neg = s < 0;
-  const unsigned __int128 a = neg ? (unsigned __int128)(-s) : (unsigned __int128)s;
-  const double hi = (double)(unsigned long long)(a >> 64);
-  const double lo = (double)(unsigned long long)a;
-  const double v = (hi * 18446744073709551616.0 + lo) * 5.684341886080801486968994140625e-14;  // 2^-44
-  const float f = (float)v;
-  return neg ? -f : f;
+  if (s == 0) return 0.f;
+  const uint32_t sign = s < 0 ? 0x80000000u : 0u;
+  const unsigned __int128 a = s < 0 ? (unsigned __int128)(-s) : (unsigned __int128)s;
+  const unsigned long long hi = (unsigned long long)(a >> 64), lo = (unsigned long long)a;
+  const int msb = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);  // leading one
+  uint32_t mant;
+  int e = msb;
+  if (msb <= 23) {
+    mant = (uint32_t)(lo << (23 - msb));  // exact
+  } else {
+    const int sh = msb - 23;
+    mant = (uint32_t)(a >> sh);  // 24 bits, leading one at bit 23
+    const unsigned __int128 rem = a & ((((unsigned __int128)1) << sh) - 1);
+    const unsigned __int128 half = ((unsigned __int128)1) << (sh - 1);
+    if (rem > half || (rem == half && (mant & 1u))) {
+      if (++mant == (1u << 24)) {
+        mant >>= 1;
+        ++e;
+      }
+    }
+  }
+  // value = mant 2^(e - 23) 2^-44: biased exponent e - 44 + 127
+  return __uint_as_float(sign | ((uint32_t)(e + 83) << 23) | (mant & 0x7fffffu));
 }
 
 __device__ __forceinline__ __int128 shfl_xor_i128(__int128 v, int o) {
@@ -102,7 +125,7 @@ __device__ __forceinline__ float group_min(float v) {
 // The cell's snapshot and the decisions that do not depend on single points.
 struct CellCtx {
   int32_t cell, base, len;
-  float h, ve;
+  float h, ve, k2;
   bool valid, wall_on, gate_on;
 };
 
@@ -117,6 +140,7 @@ __device__ __forceinline__ CellCtx load_cell(const MapDev& m, int32_t cell, int3
   c.ve = c.valid ? var_eff(m, var, m.t_last[cell]) : var;
   c.wall_on = m.wall > 0 && c.valid && len > m.wall;
   c.gate_on = c.valid && m.k > 0.f;
+  c.k2 = __fmul_rn(m.k, m.k);
   return c;
 }
 
@@ -131,9 +155,9 @@ __device__ __forceinline__ void fuse_records(const BatchDev& b, const MapDev& m,
     if (c.wall_on && z < c.h) {
       st = kPtWall;
     } else if (c.gate_on) {
-      const float sd = __fsqrt_rn(__fadd_rn(c.ve, vp));
-      const float md = __fdiv_rn(fabsf(__fsub_rn(z, c.h)), sd);
-      if (md > m.k) st = kPtRejected;
+      // |z - h| / sqrt(sigma_m^2 + sigma_p^2) > k  <=>  (z - h)^2 > k^2 (sigma_m^2 + sigma_p^2)  (k > 0)
+      const float dz = __fsub_rn(z, c.h);
+      if (__fmul_rn(dz, dz) > __fmul_rn(c.k2, __fadd_rn(c.ve, vp))) st = kPtRejected;
     }
     if (st == kPtFused) {
       const float w = __frcp_rn(vp);
@@ -183,7 +207,7 @@ __device__ __forceinline__ void count_cell(const BatchDev& b, MapCounters& mc, i
 }
 
 template <int G>
-__global__ void __launch_bounds__(kFuseThreads) k_fuse(const BatchDev* __restrict__ bp) {
+__global__ void __launch_bounds__(kFuseThreads, 4) k_fuse(const BatchDev* __restrict__ bp) {
   __shared__ int s_slot;
   __shared__ float s_min[kFuseWarps];
   __shared__ __int128 s_q[2][kFuseWarps];

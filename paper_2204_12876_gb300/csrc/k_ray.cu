@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(kRayThreads) k_ray(const BatchDev* __restrict_
       const int32_t k_end = R.k_lo + R.n;
       const float ax = R.ax, bx = R.bx, ay = R.ay, by = R.by, az = R.az, bz = R.bz;
       for (int32_t k = R.k_lo + gl; k < k_end; k += 4 * G) {
-        int32_t pp[4];
+        int32_t pl[4];
         float zz[4], th[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -136,18 +136,20 @@ __global__ void __launch_bounds__(kRayThreads) k_ray(const BatchDev* __restrict_
           const int32_t cy = __float2int_rd(__fmaf_rn(kf, by, ay));
           const bool ok = kk < k_end && (uint32_t)cx < (uint32_t)W && (uint32_t)cy < (uint32_t)H &&
                           !(cx == R.ix && cy == R.iy);
-          int32_t px = cx + ox;
-          px -= (px >= W) ? W : 0;
-          int32_t py = cy + oy;
-          py -= (py >= H) ? H : 0;
-          pp[u] = ok ? py * W + px : -1;
+          pl[u] = cy * W + cx;  // logical index
           zz[u] = __fmaf_rn(kf, bz, az);
-          th[u] = ok ? __ldg(thr + pp[u]) : __int_as_float(0xff800000);
+          th[u] = ok ? __ldg(thr + pl[u]) : __int_as_float(0xff800000);
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           if (!(zz[u] < th[u])) continue;  // also skips the samples that are not taken (th = -inf)
-          const int32_t p = pp[u];
+          // physical cell of the sample (ring-buffer layout of the map layers)
+          const int32_t cy = pl[u] / W, cx = pl[u] - cy * W;
+          int32_t px = cx + ox;
+          px -= (px >= W) ? W : 0;
+          int32_t py = cy + oy;
+          py -= (py >= H) ? H : 0;
+          const int32_t p = py * W + px;
           if (guard) {
             float n0 = m.nx[p], n1 = m.ny[p], n2 = m.nz[p];
             if (!(isfinite(n0) && isfinite(n1) && isfinite(n2))) { n0 = 0.f; n1 = 0.f; n2 = 1.f; }

@@ -3,7 +3,8 @@
 //
 //   k_count    per point: transform + bin, warp-aggregated per-cell counts;
 //              then per cell: the ray-march threshold h - sqrt(var_eff) of the
-//              pre-update map (one 4-byte gather per ray sample later)
+//              pre-update map, stored in logical order (one 4-byte gather per
+//              ray sample later, with no ring-buffer wrap)
 //   k_alloc    per tile of cells: block scans of the counts give every touched
 //              cell a segment [base, base + count) of the record array; cells
 //              with more than small_thresh records are listed for group fusion,
@@ -121,7 +122,9 @@ __global__ void __launch_bounds__(kPointThreads) k_count(const BatchDev* __restr
       const float var = m.var[p];
       float t = __int_as_float(0xff800000);  // -inf: an empty cell is never penetrated
       if (isfinite(var)) t = __fsub_rn(m.h[p], __fsqrt_rn(var_eff(m, var, m.t_last[p])));
-      m.thr[p] = t;
+      int32_t lx, ly;
+      logical_of(m, p, lx, ly);
+      m.thr[ly * m.W + lx] = t;  // logical layout: the ray march indexes it without the ring wrap
     }
   });
 }
@@ -234,12 +237,14 @@ __global__ void __launch_bounds__(kPointThreads) k_scatter(const BatchDev* __res
     const unsigned long long tag = inm ? ((unsigned long long)(uint32_t)c.map << 32) | (uint32_t)key : ~0ull;
     int head, run;
     key_runs(tag, head, run);
+    // the segment base is read before the slot claim so both loads are in flight together
+    const int32_t seg = inm ? __ldg(m.cell_base + key) : 0;
     int old = 0;
     if (inm && lane == head) old = atomicSub(&m.cnt[key], run);
     old = __shfl_sync(kFull, old, head);
     if (inm) {
       const int rank = lane - head;
-      const int64_t pos = (int64_t)m.cell_base[key] + old - 1 - rank;
+      const int64_t pos = (int64_t)seg + old - 1 - rank;
       // the count pass found the same cell for this point, so pos lies in the
       // cell's segment; anything else is recorded instead of written
       if (pos < m.pt_begin || pos >= m.pt_begin + m.pt_count || old - rank <= 0) {
