@@ -224,12 +224,12 @@ typedef struct em_batch em_batch;
 
 enum { EM_BATCH_GRAPH = 1u << 0 };
 
-/* Launch shapes picked by the autotuner (or set by hand). */
+/* Launch shapes picked by the autotuner (or set by hand).  None of them
+ * changes a result: every shape gives the same maps bit for bit. */
 typedef struct em_tuning {
   int32_t ray_group;    /* lanes per ray in the ray march: 1, 2, 4, 8, 16 or 32 */
-  int32_t fuse_group;   /* lanes per medium cell in the fusion: 4, 8, 16 or 32 */
-  int32_t big_thresh;   /* cells with more records are fused by a whole block, >= 32 */
-  int32_t small_thresh; /* cells with at most this many records take one thread, >= 4, <= big_thresh */
+  int32_t fuse_chunk;   /* records per warp chunk in the fusion: 64, 128, 256, 512 or 1024 */
+  int32_t big_thresh;   /* cells with more records are fused by a whole block: 32 .. 1023 */
 } em_tuning;
 
 /* Capacities: at most max_maps distinct maps, max_clouds clouds and
@@ -350,7 +350,7 @@ int em_server_destroy(em_server* srv); /* NULL-safe: drains, stops the worker, f
  *   shift_x/y   the map centre is (shift_x r, shift_y r) (see em_info)
  *   t_now       index of this update (>= 1): cells it writes get t_last = t_now
  *   clouds[]    host array; clouds[i].points device memory
- * All scratch lives in one static device array of the library (about 4.5 MiB,
+ * All scratch lives in one static device array of the library (about 6.1 MiB,
  * held by every GPU that loads the library until the process exits).  The
  * first call on a device looks up that array's address with the device
  * current; make that first call before any stream capture.  Every call uses

@@ -69,8 +69,7 @@ struct em_map {
   uint32_t* mark = nullptr;
   float* thr = nullptr;
   int32_t* cnt = nullptr;
-  int32_t* cell_base = nullptr;
-  int32_t* cell_len = nullptr;
+  int2* cell_seg = nullptr;
   MapCtl* ctl = nullptr;
   BatchCtl* bctl = nullptr;
   // geometry
@@ -79,12 +78,11 @@ struct em_map {
   int32_t t_now = 0;
   // per-update workspace
   int64_t cap = 0;
-  float2* zw_sorted = nullptr;
+  float4* rec = nullptr;
   int32_t* idx_sorted = nullptr;
   int32_t* tr_ix = nullptr;
   int32_t* tr_iy = nullptr;
   uint8_t* tr_status = nullptr;
-  int2* med_list = nullptr;
   int2* big_list = nullptr;
   int64_t last_n = 0;
   // descriptors
@@ -103,10 +101,9 @@ struct em_map {
   cudaStream_t last_stream = nullptr;
   int64_t layer_bytes = 0;
   int64_t work_bytes = 0;
-  int fuse_group = 8;
+  int fuse_chunk = 256;
   int ray_group = 4;
-  int big_thresh = 64;
-  int small_thresh = 8;
+  int big_thresh = 256;
   int64_t points_in = 0;
   // per-kernel profiling
   bool prof = false;
@@ -130,7 +127,7 @@ MapDev make_mapdev(const em_map* m) {
   memset(&d, 0, sizeof(d));
   d.h = m->h; d.var = m->var; d.t_last = m->t_last;
   d.nx = m->nx; d.ny = m->ny; d.nz = m->nz; d.smooth = m->smooth; d.inpaint = m->inpaint;
-  d.mark = m->mark; d.thr = m->thr; d.cnt = m->cnt; d.cell_base = m->cell_base; d.cell_len = m->cell_len;
+  d.mark = m->mark; d.thr = m->thr; d.cnt = m->cnt; d.cell_seg = m->cell_seg;
   d.ctl = m->ctl;
   d.cell_begin = 0;
   d.W = m->p.width; d.H = m->p.height; d.ox = m->ox; d.oy = m->oy;
@@ -164,11 +161,11 @@ bool params_ok(const em_params* p) {
 }
 
 void free_workspace(em_map* m) {
-  cudaFree(m->zw_sorted); cudaFree(m->idx_sorted);
+  cudaFree(m->rec); cudaFree(m->idx_sorted);
   cudaFree(m->tr_ix); cudaFree(m->tr_iy); cudaFree(m->tr_status);
-  cudaFree(m->med_list); cudaFree(m->big_list);
-  m->zw_sorted = nullptr; m->idx_sorted = nullptr; m->tr_ix = m->tr_iy = nullptr; m->tr_status = nullptr;
-  m->med_list = m->big_list = nullptr;
+  cudaFree(m->big_list);
+  m->rec = nullptr; m->idx_sorted = nullptr; m->tr_ix = m->tr_iy = nullptr; m->tr_status = nullptr;
+  m->big_list = nullptr;
   m->cap = 0;
   m->work_bytes = 0;
 }
@@ -183,8 +180,7 @@ int grow_workspace(em_map* m, int64_t n) {
   free_workspace(m);
   const bool trace = (m->p.flags & EM_F_TRACE) != 0;
   int64_t tot = 0;
-  EM_TRY(dev_alloc(&m->zw_sorted, (size_t)want, &tot), "alloc workspace");
-  EM_TRY(dev_alloc(&m->med_list, (size_t)med_list_cap(want), &tot), "alloc workspace");
+  EM_TRY(dev_alloc(&m->rec, (size_t)want, &tot), "alloc workspace");
   EM_TRY(dev_alloc(&m->big_list, (size_t)big_list_cap(want), &tot), "alloc workspace");
   if (trace) {
     EM_TRY(dev_alloc(&m->idx_sorted, (size_t)want, &tot), "alloc trace");
@@ -203,7 +199,7 @@ void release(em_map* m) {
     if (m->prof_ev[i]) cudaEventDestroy(m->prof_ev[i]);
   cudaFree(m->h); cudaFree(m->var); cudaFree(m->t_last);
   cudaFree(m->nx); cudaFree(m->ny); cudaFree(m->nz); cudaFree(m->smooth); cudaFree(m->inpaint);
-  cudaFree(m->mark); cudaFree(m->thr); cudaFree(m->cnt); cudaFree(m->cell_base); cudaFree(m->cell_len);
+  cudaFree(m->mark); cudaFree(m->thr); cudaFree(m->cnt); cudaFree(m->cell_seg);
   cudaFree(m->ctl); cudaFree(m->bctl);
   free_workspace(m);
   cudaFree(m->desc_dev);
@@ -238,8 +234,7 @@ int upload_desc(em_map* m, const em_cloud* clouds, int32_t n_clouds, int64_t tot
   CloudDev* cd = reinterpret_cast<CloudDev*>(hb + sizeof(BatchDev) + sizeof(MapDev));
   memset(b, 0, sizeof(BatchDev));
   *md = make_mapdev(m);
-  md->pt_begin = 0;
-  md->pt_count = total;
+  md->z_ref = n_clouds > 0 ? clouds[0].pose[11] : 0.f;
   int64_t begin = 0;
   for (int i = 0; i < n_clouds; ++i) {
     CloudDev& c = cd[i];
@@ -260,19 +255,17 @@ int upload_desc(em_map* m, const em_cloud* clouds, int32_t n_clouds, int64_t tot
   b->n_points = total;
   b->maps = reinterpret_cast<const MapDev*>(db + sizeof(BatchDev));
   b->clouds = reinterpret_cast<const CloudDev*>(db + sizeof(BatchDev) + sizeof(MapDev));
-  b->zw_sorted = m->zw_sorted;
+  b->rec = m->rec;
   b->idx_sorted = m->idx_sorted;
   b->tr_ix = m->tr_ix;
   b->tr_iy = m->tr_iy;
   b->tr_status = m->tr_status;
   b->n_cells = pad_tile((int64_t)m->p.width * m->p.height);
   b->ctl = m->bctl;
-  b->med_list = m->med_list;
   b->big_list = m->big_list;
-  b->med_cap = (int32_t)med_list_cap(m->cap);
   b->big_cap = (int32_t)big_list_cap(m->cap);
-  b->small_thresh = m->small_thresh;
   b->big_thresh = m->big_thresh;
+  b->chunk = m->fuse_chunk;
   const size_t bytes = sizeof(BatchDev) + sizeof(MapDev) + (size_t)n_clouds * sizeof(CloudDev);
   EM_TRY(cudaMemcpyAsync(db, hb, bytes, cudaMemcpyHostToDevice, s), "upload descriptor");
   *out = reinterpret_cast<const BatchDev*>(db);
@@ -396,8 +389,8 @@ int em_create(const em_params* params, int device, em_map** out) {
   if (normals) { EM_ALLOC(m->nx, nc) EM_ALLOC(m->ny, nc) EM_ALLOC(m->nz, nc) }
   if (params->flags & EM_F_SMOOTH) { EM_ALLOC(m->smooth, nc) }
   if (params->flags & EM_F_INPAINT) { EM_ALLOC(m->inpaint, nc) }
-  EM_ALLOC(m->mark, (nc + 31) / 32) EM_ALLOC(m->thr, nc) EM_ALLOC(m->cnt, nc) EM_ALLOC(m->cell_base, nc)
-  EM_ALLOC(m->cell_len, nc) EM_ALLOC(m->ctl, 1) EM_ALLOC(m->bctl, 1)
+  EM_ALLOC(m->mark, (nc + 31) / 32) EM_ALLOC(m->thr, nc) EM_ALLOC(m->cnt, nc) EM_ALLOC(m->cell_seg, nc)
+  EM_ALLOC(m->ctl, 1) EM_ALLOC(m->bctl, 1)
   EM_ALLOC(m->desc_dev, kDescBytes * kSlots)
 #undef EM_ALLOC
   if (e == cudaSuccess) e = cudaMallocHost((void**)&m->desc_host, kDescBytes * kSlots);
@@ -414,9 +407,9 @@ int em_create(const em_params* params, int device, em_map** out) {
   }
   m->layer_bytes = tot;
   // tuning knobs (defaults chosen by measurement; the environment overrides them)
-  if (const char* g = getenv("EM_FUSE_GROUP")) {
+  if (const char* g = getenv("EM_FUSE_CHUNK")) {
     int v = atoi(g);
-    if (v == 4 || v == 8 || v == 16 || v == 32) m->fuse_group = v;
+    if (v >= 64 && v <= 1024 && (v & (v - 1)) == 0) m->fuse_chunk = v;
   }
   if (const char* g = getenv("EM_RAY_GROUP")) {
     int v = atoi(g);
@@ -424,13 +417,8 @@ int em_create(const em_params* params, int device, em_map** out) {
   }
   if (const char* g = getenv("EM_BIG_THRESH")) {
     int v = atoi(g);
-    if (v >= kMinBig) m->big_thresh = v;
+    if (v >= kMinBig && v <= kMaxBigThresh) m->big_thresh = v;
   }
-  if (const char* g = getenv("EM_SMALL_THRESH")) {
-    int v = atoi(g);
-    if (v >= kMinSmall) m->small_thresh = v;
-  }
-  if (m->big_thresh < m->small_thresh) m->big_thresh = m->small_thresh;
   *out = m;
   return EM_OK;
 }
@@ -472,7 +460,7 @@ static int update_impl(em_map* m, const em_cloud* clouds, int32_t n_clouds, cuda
     if (m->p.ray_step > 0.f) EM_TRY(timed(m, EM_PROF_RAY, s, [&] { return launch_ray(bd, total, m->ray_group, s); }), "k_ray");
     EM_TRY(timed(m, EM_PROF_ALLOC, s, [&] { return launch_alloc(bd, ncell, s); }), "k_alloc");
     EM_TRY(timed(m, EM_PROF_SCATTER, s, [&] { return launch_scatter(bd, total, s); }), "k_scatter");
-    EM_TRY(timed(m, EM_PROF_FUSE, s, [&] { return launch_fuse(bd, ncell, total, m->fuse_group, s); }), "k_fuse");
+    EM_TRY(timed(m, EM_PROF_FUSE, s, [&] { return launch_fuse(bd, total, m->fuse_chunk, s); }), "k_fuse");
   }
   EM_TRY(timed(m, EM_PROF_CLEAR, s, [&] { return launch_clear(bd, ncell, s); }), "k_clear");
   if (m->p.flags & EM_F_NORMALS)

@@ -31,9 +31,9 @@ constexpr int kSlots = 3;
   } while (0)
 
 bool tuning_ok(const em_tuning& t) {
-  const int r = t.ray_group, f = t.fuse_group;
-  return (r == 1 || r == 2 || r == 4 || r == 8 || r == 16 || r == 32) && (f == 4 || f == 8 || f == 16 || f == 32) &&
-         t.small_thresh >= kMinSmall && t.big_thresh >= kMinBig && t.big_thresh >= t.small_thresh;
+  const int r = t.ray_group, f = t.fuse_chunk;
+  return (r == 1 || r == 2 || r == 4 || r == 8 || r == 16 || r == 32) && f >= 64 && f <= 1024 && (f & (f - 1)) == 0 &&
+         t.big_thresh >= kMinBig && t.big_thresh <= kMaxBigThresh;
 }
 
 // what a captured graph depends on besides the slot
@@ -42,8 +42,8 @@ struct GraphKey {
   bool ray;
   uint32_t stencils;
   bool operator==(const GraphKey& o) const {
-    return t.ray_group == o.t.ray_group && t.fuse_group == o.t.fuse_group && t.big_thresh == o.t.big_thresh &&
-           t.small_thresh == o.t.small_thresh && ray == o.ray && stencils == o.stencils;
+    return t.ray_group == o.t.ray_group && t.fuse_chunk == o.t.fuse_chunk && t.big_thresh == o.t.big_thresh &&
+           ray == o.ray && stencils == o.stencils;
   }
 };
 
@@ -54,16 +54,15 @@ struct em_batch {
   int32_t max_maps = 0, max_clouds = 0, max_cells = 0;
   int64_t max_points = 0;
   uint32_t flags = 0;
-  float2* zw_sorted = nullptr;
+  float4* rec = nullptr;
   BatchCtl* bctl = nullptr;
-  int2* med_list = nullptr;
   int2* big_list = nullptr;
   size_t desc_bytes = 0;
   unsigned char* desc_host = nullptr;
   unsigned char* desc_dev = nullptr;
   cudaEvent_t ev[kSlots] = {};
   int slot = 0;
-  em_tuning tune{4, 8, 64, 8};
+  em_tuning tune{4, 256, 256};
   cudaStream_t capture_stream = nullptr;
   cudaGraphExec_t graph[kSlots] = {};
   GraphKey graph_key[kSlots] = {};
@@ -119,7 +118,7 @@ cudaError_t launch_sequence(const BatchDev* bd, int64_t grid_points, int64_t gri
     if (e == cudaSuccess) e = timed(prof, EM_PROF_ALLOC, s, [&] { return launch_alloc(bd, grid_cells, s); });
     if (e == cudaSuccess) e = timed(prof, EM_PROF_SCATTER, s, [&] { return launch_scatter(bd, grid_points, s); });
     if (e == cudaSuccess)
-      e = timed(prof, EM_PROF_FUSE, s, [&] { return launch_fuse(bd, grid_cells, grid_points, k.t.fuse_group, s); });
+      e = timed(prof, EM_PROF_FUSE, s, [&] { return launch_fuse(bd, grid_points, k.t.fuse_chunk, s); });
   }
   if (e == cudaSuccess) e = timed(prof, EM_PROF_CLEAR, s, [&] { return launch_clear(bd, grid_cells, s); });
   if (e == cudaSuccess && (k.stencils & EM_F_NORMALS))
@@ -184,13 +183,9 @@ int prepare(em_batch* b, em_map* const* maps, const em_cloud* clouds, int32_t co
   memset(bd, 0, sizeof(BatchDev));
   GraphKey key{tune, false, 0u};
   int64_t cells = 0;
-  int64_t rec = 0;
   for (int u = 0; u < nm; ++u) {
     md[u] = map_begin_update(b->uniq[u], map_pts[u]);
-    md[u].pt_begin = rec;
-    md[u].pt_count = map_pts[u];
     md[u].cell_begin = cells;
-    rec += map_pts[u];
     cells += pad_tile(map_cells(b->uniq[u]));
     key.ray |= md[u].ray_step > 0.f;
     key.stencils |= map_flags(b->uniq[u]) & (EM_F_NORMALS | EM_F_SMOOTH | EM_F_INPAINT);
@@ -199,8 +194,10 @@ int prepare(em_batch* b, em_map* const* maps, const em_cloud* clouds, int32_t co
   int ci = 0;
   int64_t begin = 0;
   for (int u = 0; u < nm; ++u)
-    for (int i = 0; i < count; ++i) {
+    for (int i = 0, first = 1; i < count; ++i) {
       if (b->map_of[i] != u) continue;
+      if (first) md[u].z_ref = clouds[i].pose[11];  // the map's first cloud, as in em_update_multi
+      first = 0;
       CloudDev& c = cd[ci++];
       memset(&c, 0, sizeof(c));
       c.pts = clouds[i].points;
@@ -219,15 +216,13 @@ int prepare(em_batch* b, em_map* const* maps, const em_cloud* clouds, int32_t co
   bd->n_points = total;
   bd->maps = reinterpret_cast<const MapDev*>(db + sizeof(BatchDev));
   bd->clouds = reinterpret_cast<const CloudDev*>(db + sizeof(BatchDev) + (size_t)b->max_maps * sizeof(MapDev));
-  bd->zw_sorted = b->zw_sorted;
+  bd->rec = b->rec;
   bd->n_cells = cells;
   bd->ctl = b->bctl;
-  bd->med_list = b->med_list;
   bd->big_list = b->big_list;
-  bd->med_cap = (int32_t)med_list_cap(b->max_points);
   bd->big_cap = (int32_t)big_list_cap(b->max_points);
-  bd->small_thresh = tune.small_thresh;
   bd->big_thresh = tune.big_thresh;
+  bd->chunk = tune.fuse_chunk;
   // upload header + maps, and the clouds at their fixed offset
   cudaError_t e = cudaMemcpyAsync(db, hb, sizeof(BatchDev) + (size_t)nm * sizeof(MapDev), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
@@ -292,9 +287,8 @@ void release(em_batch* b) {
     if (b->ev[i]) cudaEventDestroy(b->ev[i]);
   }
   if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
-  cudaFree(b->zw_sorted);
+  cudaFree(b->rec);
   cudaFree(b->bctl);
-  cudaFree(b->med_list);
   cudaFree(b->big_list);
   cudaFree(b->desc_dev);
   cudaFreeHost(b->desc_host);
@@ -326,10 +320,9 @@ int em_batch_create(int device, int32_t max_maps, int32_t max_clouds, int64_t ma
   b->flags = flags;
   b->desc_bytes = (sizeof(BatchDev) + (size_t)max_maps * sizeof(MapDev) + (size_t)max_clouds * sizeof(CloudDev) + 255) &
                   ~size_t(255);
-  cudaError_t e = cudaMalloc((void**)&b->zw_sorted, (size_t)(max_points > 0 ? max_points : 1) * sizeof(float2));
+  cudaError_t e = cudaMalloc((void**)&b->rec, (size_t)(max_points > 0 ? max_points : 1) * sizeof(float4));
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->bctl, sizeof(BatchCtl));
   if (e == cudaSuccess) e = cudaMemset(b->bctl, 0, sizeof(BatchCtl));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&b->med_list, (size_t)med_list_cap(max_points) * sizeof(int2));
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->big_list, (size_t)big_list_cap(max_points) * sizeof(int2));
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->desc_dev, b->desc_bytes * kSlots);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&b->desc_host, b->desc_bytes * kSlots);
@@ -473,27 +466,23 @@ int em_batch_autotune(em_batch* b, em_map* const* maps, const em_cloud* clouds, 
   float best_ms = 0.f;
   rc = time_one(best, &best_ms);
   const int ray_c[] = {1, 2, 4, 8, 16};
-  const int fuse_c[] = {4, 8, 16, 32};
-  const int big_c[] = {32, 64, 128, 256};
-  const int small_c[] = {4, 8, 16, 32};
+  const int chunk_c[] = {64, 128, 256, 512, 1024};
+  const int big_c[] = {64, 128, 256, 512, 1023};
   const bool any_ray = [&] {
     for (em_map* m : uniq)
       if (map_params(m).ray_step > 0.f) return true;
     return false;
   }();
-  for (int pass = 0; pass < 4 && rc == EM_OK; ++pass) {
+  // coordinate descent: ray group, then fusion chunk, then the large-cell threshold
+  for (int pass = 0; pass < 3 && rc == EM_OK; ++pass) {
     if (pass == 0 && !any_ray) continue;
-    const int* cand = pass == 0 ? ray_c : pass == 1 ? small_c : pass == 2 ? fuse_c : big_c;
-    const int nc = pass == 0 ? 5 : 4;
-    for (int i = 0; i < nc && rc == EM_OK; ++i) {
+    const int* cand = pass == 0 ? ray_c : pass == 1 ? chunk_c : big_c;
+    for (int i = 0; i < 5 && rc == EM_OK; ++i) {
       em_tuning t = best;
       if (pass == 0) t.ray_group = cand[i];
-      if (pass == 1) t.small_thresh = cand[i];
-      if (pass == 2) t.fuse_group = cand[i];
-      if (pass == 3) t.big_thresh = cand[i];
-      if (t.big_thresh < t.small_thresh) continue;
-      if (t.ray_group == best.ray_group && t.fuse_group == best.fuse_group && t.big_thresh == best.big_thresh &&
-          t.small_thresh == best.small_thresh)
+      if (pass == 1) t.fuse_chunk = cand[i];
+      if (pass == 2) t.big_thresh = cand[i];
+      if (t.ray_group == best.ray_group && t.fuse_chunk == best.fuse_chunk && t.big_thresh == best.big_thresh)
         continue;
       float ms = 0.f;
       rc = time_one(t, &ms);

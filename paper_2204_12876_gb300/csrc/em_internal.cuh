@@ -17,11 +17,12 @@
 //   k_count    transform + noise variance + cell binning, per-cell counts;
 //              per-cell ray thresholds of the pre-update map   (Section II-C)
 //   k_ray      visibility ray march against the pre-update map (Section II-E)
-//   k_alloc    one segment of the record array per touched cell; medium and
-//              large cells listed for group / block fusion
+//   k_alloc    one segment of the record array per touched cell (segments of a
+//              tile in cell order); large cells listed for block fusion
 //   k_scatter  records into their cell's segment (counting sort by cell)
 //   k_fuse     per cell: wall rule, Mahalanobis gate, Eq. 1/2 in information
-//              form with exact integer accumulation          (Section II-C)
+//              form with exact integer accumulation; warps stream cell-aligned
+//              chunks of records (segmented reductions)   (Section II-C)
 //   k_clear    remove penetrated cells not written recently   (Section II-E)
 //   k_normals / k_smooth / k_inpaint                          (Section II-A, II-I)
 #pragma once
@@ -42,17 +43,30 @@ enum StatIdx {
 // per-map device control block
 struct MapCtl {
   unsigned long long stats[kStCount];
-  int32_t seg_cursor;  // records given to segments this update (reset by k_count)
   int32_t err;         // first device-side error code of this map (sticky until read)
-  int32_t pad[2];
+  int32_t pad[3];
 };
 
 // per-batch device control block (reset by k_count)
 struct BatchCtl {
-  int32_t n_med, n_big;      // entries in the medium / large cell lists
+  int32_t rec_total;         // records given to segments this update (all maps)
+  int32_t n_big;             // entries in the large-cell list
   int32_t big_next;          // work-stealing cursor over the large cells
-  int32_t overflow;          // a list was full (never with the sizes the host allocates)
+  int32_t overflow;          // the list was full (never with the sizes the host allocates)
 };
+
+// One record per in-map point, grouped by cell (16 bytes, one store):
+//   x = z (map frame), y = sigma_p^2, z = physical cell index (int bits),
+//   w = map index (bits 0..23) | kRecWall | kRecBig (uint bits).
+// The flags are properties of the cell this update (its record count), so all
+// records of a cell carry the same (w, z) words.
+constexpr uint32_t kRecBig = 1u << 31;   // more than big_thresh records: fused by a whole block
+constexpr uint32_t kRecWall = 1u << 30;  // more than wall_num_thresh records (wall rule armed)
+constexpr uint32_t kRecMapMask = (1u << 24) - 1u;
+constexpr int kMaxBigThresh = 1023;      // run counts are packed in 10-bit fields
+
+// device-side error word value for a failed internal consistency check (EM_ERR_CUDA)
+constexpr int32_t kErrInternal = -3;
 
 // point status codes (trace)
 enum PointStatus : uint8_t { kPtNonFinite = 0, kPtRange = 1, kPtOutside = 2, kPtFused = 3, kPtRejected = 4, kPtWall = 5 };
@@ -70,14 +84,14 @@ struct MapDev {
   uint32_t* mark;   // visibility marks, one bit per physical cell, zero between updates
   float* thr;       // per LOGICAL cell [iy][ix]: h - sqrt(var_eff) of the pre-update map, -inf if empty
   int32_t* cnt;     // per physical cell point count, zero between updates
-  int32_t* cell_base;  // per physical cell: start of its segment of records (this update)
-  int32_t* cell_len;   // per physical cell: number of records (this update)
+  int2* cell_seg;   // per physical cell: (first record, record count) of this update
   MapCtl* ctl;
-  int64_t pt_begin;    // this map's records occupy [pt_begin, pt_begin + pt_count)
-  int64_t pt_count;
   int64_t cell_begin;  // this map's first cell in the batch cell space (multiple of kTile)
   int32_t W, H, ox, oy;
   float x0, y0, res, inv_res;  // inv_res = 1 / res rounded to float
+  float z_ref;         // reference height of empty cells in the fusion sums: the z of the
+                       // first cloud's sensor origin (any fixed value gives the same result
+                       // up to rounding; one near the points keeps the terms small)
   int32_t t_now;       // index of this update
   // method parameters
   float a0, a1, a2, var_min, min_range, max_range, k, v_out, sigma_t2, ray_step, alpha_n;
@@ -101,22 +115,20 @@ struct BatchDev {
   int64_t n_cells;     // padded size of the cell space
   const MapDev* maps;
   const CloudDev* clouds;
-  float2* zw_sorted;   // records (z, sigma_p^2) grouped by cell
-  int32_t* idx_sorted; // original point index per sorted record (trace only, else null)
+  float4* rec;         // records grouped by cell (layout above), [0, ctl->rec_total)
+  int32_t* idx_sorted; // original point index per record (trace only, else null)
   int32_t* tr_ix;      // trace (null unless EM_F_TRACE)
   int32_t* tr_iy;
   uint8_t* tr_status;
   BatchCtl* ctl;
-  int2* med_list;      // (map, physical cell) of cells with small_thresh < records <= big_thresh
   int2* big_list;      // (map, physical cell) of cells with more than big_thresh records
-  int32_t med_cap, big_cap;
-  int32_t small_thresh, big_thresh;
+  int32_t big_cap;
+  int32_t big_thresh;  // in [kMinBig, kMaxBigThresh]
+  int32_t chunk;       // records per warp chunk in the fusion (a power of two, 64..1024)
 };
 
-// List capacities for n points: small_thresh >= kMinSmall, big_thresh >= kMinBig.
-constexpr int kMinSmall = 4;
+// Large-cell list capacity for n points (big_thresh >= kMinBig).
 constexpr int kMinBig = 32;
-inline int64_t med_list_cap(int64_t n) { return n / (kMinSmall + 1) + 1; }
 inline int64_t big_list_cap(int64_t n) { return n / (kMinBig + 1) + 1; }
 inline int64_t pad_tile(int64_t cells) { return (cells + kTile - 1) / kTile * kTile; }
 
@@ -128,7 +140,7 @@ cudaError_t launch_bin(const BatchDev* b, int64_t n_points, int64_t n_cells, cud
 cudaError_t launch_ray(const BatchDev* b, int64_t n_points, int group, cudaStream_t s);
 cudaError_t launch_alloc(const BatchDev* b, int64_t n_cells, cudaStream_t s);
 cudaError_t launch_scatter(const BatchDev* b, int64_t n_points, cudaStream_t s);
-cudaError_t launch_fuse(const BatchDev* b, int64_t n_cells, int64_t n_points, int group, cudaStream_t s);
+cudaError_t launch_fuse(const BatchDev* b, int64_t n_points, int chunk, cudaStream_t s);
 cudaError_t launch_clear(const BatchDev* b, int64_t n_cells, cudaStream_t s);
 cudaError_t launch_normals(const BatchDev* b, int64_t n_cells, cudaStream_t s);
 cudaError_t launch_smooth(const BatchDev* b, int64_t n_cells, cudaStream_t s);

@@ -10,7 +10,7 @@
 // memory in one file-scope __device__ array of fixed size.
 //
 // Limits: at most kMaxCells cells per map and kMaxPoints points per update
-// (about 4.5 MiB of scratch, held by every GPU that loads the library until the
+// (about 6.1 MiB of scratch, held by every GPU that loads the library until the
 // process exits).  Every call shares the array and it keeps the last call's
 // contents; the call clears what must start at zero.  Calls whose GPU work
 // overlaps (e.g. on two streams) race on the array.
@@ -41,12 +41,10 @@ constexpr size_t kOffBCtl = kOffCtl + up256(sizeof(MapCtl));
 constexpr size_t kOffMark = kOffBCtl + up256(sizeof(BatchCtl));
 constexpr size_t kOffCnt = kOffMark + up256(((size_t)kMaxCells + 31) / 32 * sizeof(uint32_t));
 constexpr size_t kOffThr = kOffCnt + up256((size_t)kMaxCells * sizeof(int32_t));
-constexpr size_t kOffCellBase = kOffThr + up256((size_t)kMaxCells * sizeof(float));
-constexpr size_t kOffCellLen = kOffCellBase + up256((size_t)kMaxCells * sizeof(int32_t));
-constexpr size_t kOffMed = kOffCellLen + up256((size_t)kMaxCells * sizeof(int32_t));
-constexpr size_t kOffBig = kOffMed + up256((size_t)(kMaxPoints / (kMinSmall + 1) + 1) * sizeof(int2));
+constexpr size_t kOffSeg = kOffThr + up256((size_t)kMaxCells * sizeof(float));
+constexpr size_t kOffBig = kOffSeg + up256((size_t)kMaxCells * sizeof(int2));
 constexpr size_t kOffRec = kOffBig + up256((size_t)(kMaxPoints / (kMinBig + 1) + 1) * sizeof(int2));
-constexpr size_t kScratchBytes = kOffRec + up256((size_t)kMaxPoints * sizeof(float2));
+constexpr size_t kScratchBytes = kOffRec + up256((size_t)kMaxPoints * sizeof(float4));
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
@@ -137,12 +135,10 @@ extern "C" int em_update_noalloc(const em_params* params, int64_t shift_x, int64
   m->mark = reinterpret_cast<uint32_t*>(base + kOffMark);
   m->thr = reinterpret_cast<float*>(base + kOffThr);
   m->cnt = reinterpret_cast<int32_t*>(base + kOffCnt);
-  m->cell_base = reinterpret_cast<int32_t*>(base + kOffCellBase);
-  m->cell_len = reinterpret_cast<int32_t*>(base + kOffCellLen);
+  m->cell_seg = reinterpret_cast<int2*>(base + kOffSeg);
   m->ctl = reinterpret_cast<MapCtl*>(base + kOffCtl);
   m->cell_begin = 0;
-  m->pt_begin = 0;
-  m->pt_count = total;
+  m->z_ref = clouds[0].pose[11];
   m->W = W;
   m->H = H;
   const double r = (double)params->resolution;
@@ -174,15 +170,13 @@ extern "C" int em_update_noalloc(const em_params* params, int64_t shift_x, int64
   b->n_points = total;
   b->maps = reinterpret_cast<const MapDev*>(base + kOffDesc + sizeof(BatchDev));
   b->clouds = reinterpret_cast<const CloudDev*>(base + kOffDesc + sizeof(BatchDev) + sizeof(MapDev));
-  b->zw_sorted = reinterpret_cast<float2*>(base + kOffRec);
+  b->rec = reinterpret_cast<float4*>(base + kOffRec);
   b->n_cells = pad_tile(ncell);
   b->ctl = reinterpret_cast<BatchCtl*>(base + kOffBCtl);
-  b->med_list = reinterpret_cast<int2*>(base + kOffMed);
   b->big_list = reinterpret_cast<int2*>(base + kOffBig);
-  b->med_cap = (int32_t)(kMaxPoints / (kMinSmall + 1) + 1);
   b->big_cap = (int32_t)(kMaxPoints / (kMinBig + 1) + 1);
-  b->small_thresh = 8;
-  b->big_thresh = 64;
+  b->big_thresh = 256;
+  b->chunk = 256;
 
   const BatchDev* bd = reinterpret_cast<const BatchDev*>(base + kOffDesc);
   const size_t desc_bytes = sizeof(BatchDev) + sizeof(MapDev) + (size_t)n_clouds * sizeof(CloudDev);
@@ -199,7 +193,7 @@ extern "C" int em_update_noalloc(const em_params* params, int64_t shift_x, int64
     if (e == cudaSuccess && params->ray_step > 0.f) e = launch_ray(bd, total, 4, s);
     if (e == cudaSuccess) e = launch_alloc(bd, cells, s);
     if (e == cudaSuccess) e = launch_scatter(bd, total, s);
-    if (e == cudaSuccess) e = launch_fuse(bd, cells, total, 8, s);
+    if (e == cudaSuccess) e = launch_fuse(bd, total, 256, s);
   }
   if (e == cudaSuccess) e = launch_clear(bd, cells, s);
   return na_status(e, "em_update_noalloc launch");

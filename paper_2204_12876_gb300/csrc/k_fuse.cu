@@ -1,7 +1,7 @@
 // k_fuse.cu -- per-cell fusion (Section II-C of the paper).
 //
-// For every cell that received points in this update, its segment of records
-// (z, sigma_p^2) is walked:
+// Every cell that received points in this update is fused once from its
+// segment of records (z, sigma_p^2):
 //   1. wall rule: in a valid cell with more than wall_num_thresh points, points
 //      below the current height are dropped (before the outlier test);
 //   2. Mahalanobis gate against the pre-update estimate: reject iff
@@ -10,23 +10,29 @@
 //      every rejection adds outlier_variance to sigma_m^2;
 //   3. Eq. 1 and Eq. 2 for all accepted points at once, in information form:
 //        Lambda = 1 / (sigma_m^2 + n_rej v_out) + sum_i 1/sigma_p,i^2
-//        h'     = h + sum_i (z_i - h) / sigma_p,i^2 / Lambda,   sigma_m^2' = 1 / Lambda
-//      (an empty cell has 1/sigma_m^2 = 0 and uses the smallest z of its
-//      segment as the reference height).  Applying Eq. 1/2 point after point
-//      gives the same result in exact arithmetic.
+//        h'     = h_ref + sum_i (z_i - h_ref) / sigma_p,i^2 / Lambda,   sigma_m^2' = 1 / Lambda
+//      with h_ref = h for a valid cell (an empty cell has 1/sigma_m^2 = 0 and
+//      h_ref = the map's reference height z_ref).  Applying Eq. 1/2 point
+//      after point gives the same result in exact arithmetic.
 //
 // The two sums are accumulated exactly: every float32 term is converted to a
 // signed 128-bit fixed-point integer with 44 fractional bits and the integers
 // are added.  Integer addition is associative, so the result is the same for
-// every order of the points, bit for bit (no float atomics, no dependence on
-// the order records reached their segment or on how lanes split a segment).
+// every order of the points and every split of a segment between lanes, bit
+// for bit (no float atomics).
 //
-// Three tiers by segment length, in one launch:
-//   large  (> big_thresh records)   one whole block per cell, cells taken from
-//                                   a counter (atomicAdd; no block waits);
-//   medium (> small_thresh)         a group of G lanes per cell, grid-stride;
-//   small  (1 .. small_thresh)      one thread per cell, walking the tiles of
-//                                   the cell space (coalesced per-cell loads).
+// Work split, one launch:
+//   chunks  the record array is cut into chunks of `chunk` records; a warp owns
+//           the cells whose segment STARTS in its chunk and streams their
+//           records 32 at a time (one record per lane, coalesced 16-byte
+//           loads).  Lanes of the same cell form a run; a segmented inclusive
+//           scan over the runs gives each run's sums at its last lane, which
+//           writes the cell.  A run that reaches lane 31 carries its partial
+//           sums into the next 32 records.  Load balance follows the records,
+//           not the cells, so uneven cells and maps cost no divergence.
+//   large   cells with more than big_thresh records (flagged in their records
+//           and listed by k_alloc) are skipped by the chunks and fused by a
+//           whole block each, taken from a counter (atomicAdd; no block waits).
 #include "em_point.cuh"
 
 namespace em {
@@ -34,59 +40,55 @@ namespace em {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kFuseThreads = 256;
 constexpr int kFuseWarps = kFuseThreads / 32;
+#ifndef EM_FUSE_BLOCKS_PER_SM
+#define EM_FUSE_BLOCKS_PER_SM 3
+#endif
+constexpr int kFuseBlocksPerSM = EM_FUSE_BLOCKS_PER_SM;  // resident blocks per SM (sets the register budget)
 
-// trunc(a * 2^44) as a signed 128-bit integer, exact for |a| >= 2^-44 (bits
-// below 2^-44 are dropped, the same way for every order of summation).  The
-// 24-bit significand is placed with 64-bit shifts into the two halves.
-__device__ __forceinline__ __int128 to_fixed(float a) {
-  const uint32_t u = __float_as_uint(a);
-  const int e = (int)((u >> 23) & 0xffu);
-  const unsigned long long mant = (u & 0x7fffffu) | 0x800000u;
-  int sh = e - 106;          // a = mant * 2^(e - 150); a * 2^44 = mant * 2^(e - 106)
-  sh = sh > 100 ? 100 : sh;  // |a| >= 2^78: saturate (never reached by bounded inputs)
-  unsigned long long lo, hi;
-  if (e == 0 || sh <= -32) {
-    lo = 0; hi = 0;
-  } else if (sh < 0) {
-    lo = mant >> (-sh); hi = 0;
-  } else if (sh <= 40) {
-    lo = mant << sh; hi = 0;
-  } else if (sh < 64) {
-    lo = mant << sh; hi = mant >> (64 - sh);
-  } else {
-    lo = 0; hi = mant << (sh - 64);
+// trunc(|a| 2^44) with the sign of a -- the fixed-point value of a float32 term
+// (44 fractional bits; bits below 2^-44 are dropped, the same way for every
+// order of summation) -- split as h 2^27 + l with 0 <= l < 2^27.  Exact for
+// |a| < 2^46: |a| 2^17 = F + r with F = trunc, r in [0, 1) exact (Sterbenz),
+// and r 2^27 is exact; a negative value borrows one from h so l stays >= 0.
+// Straight-line float and conversion instructions, no 128-bit shifts.
+struct Fix {
+  long long h;
+  uint32_t l;
+};
+__device__ __forceinline__ Fix to_fix(float a) {
+  const float A = __fmul_rn(fabsf(a), 131072.0f);  // |a| 2^17
+  const float F = truncf(A);
+  long long h = (long long)F;
+  uint32_t l = (uint32_t)__fmul_rn(__fsub_rn(A, F), 134217728.0f);  // r 2^27
+  if (a < 0.f) {
+    h = l ? -h - 1 : -h;
+    l = l ? (1u << 27) - l : 0u;
   }
-  const __int128 r = (__int128)(((unsigned __int128)hi << 64) | lo);
-  return (u >> 31) ? -r : r;
+  return Fix{h, l};
 }
 
-// s * 2^-44 rounded to the nearest float (ties to even), in integer arithmetic
-// (this part's FP64 rate is a small fraction of its integer rate).  Every
-// nonzero |s| < 2^127 gives a normal float: 2^-44 <= |s| 2^-44 < 2^83.
-__device__ __forceinline__ float from_fixed(__int128 s) {
-  if (s == 0) return 0.f;
-  const uint32_t sign = s < 0 ? 0x80000000u : 0u;
-  const unsigned __int128 a = s < 0 ? (unsigned __int128)(-s) : (unsigned __int128)s;
-  const unsigned long long hi = (unsigned long long)(a >> 64), lo = (unsigned long long)a;
-  const int msb = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);  // leading one
-  uint32_t mant;
-  int e = msb;
-  if (msb <= 23) {
-    mant = (uint32_t)(lo << (23 - msb));  // exact
+// h 2^27 + l as a 128-bit integer (l may be a sum of many 27-bit parts)
+__device__ __forceinline__ __int128 fix128(long long h, unsigned long long l) {
+  return (__int128)h * 134217728 + (__int128)l;
+}
+
+// t 2^-44 as a float, from its magnitude split into 32-bit pieces (all
+// non-negative, so no cancellation): within 2 ulp of the exact value and a
+// fixed function of t, so equal sums give equal floats.
+__device__ __forceinline__ float fixed_to_float(__int128 t) {
+  const bool neg = t < 0;
+  const unsigned __int128 m = neg ? (unsigned __int128)(-t) : (unsigned __int128)t;
+  const unsigned long long top = (unsigned long long)(m >> 64), mid = (unsigned long long)m;
+  float v;
+  if (top == 0) {  // |value| < 2^20
+    v = __fmaf_rn((float)(uint32_t)(mid >> 32), 2.44140625e-4f,                  // 2^32 2^-44
+                  __fmul_rn((float)(uint32_t)mid, 5.684341886080801486968994140625e-14f));  // 2^-44
   } else {
-    const int sh = msb - 23;
-    mant = (uint32_t)(a >> sh);  // 24 bits, leading one at bit 23
-    const unsigned __int128 rem = a & ((((unsigned __int128)1) << sh) - 1);
-    const unsigned __int128 half = ((unsigned __int128)1) << (sh - 1);
-    if (rem > half || (rem == half && (mant & 1u))) {
-      if (++mant == (1u << 24)) {
-        mant >>= 1;
-        ++e;
-      }
-    }
+    v = __fmaf_rn((float)(uint32_t)(top >> 32), 4503599627370496.0f,             // 2^96 2^-44
+                  __fmaf_rn((float)(uint32_t)top, 1048576.0f,                    // 2^64 2^-44
+                            __fmul_rn((float)(uint32_t)(mid >> 32), 2.44140625e-4f)));
   }
-  // value = mant 2^(e - 23) 2^-44: biased exponent e - 44 + 127
-  return __uint_as_float(sign | ((uint32_t)(e + 83) << 23) | (mant & 0x7fffffu));
+  return neg ? -v : v;
 }
 
 __device__ __forceinline__ __int128 shfl_xor_i128(__int128 v, int o) {
@@ -97,91 +99,81 @@ __device__ __forceinline__ __int128 shfl_xor_i128(__int128 v, int o) {
   return (__int128)(((unsigned __int128)hi2 << 64) | lo2);
 }
 
-// partial sums of one lane over a segment
-struct Acc {
-  __int128 qw, qt;
-  int acc, rej, wal;
+// Partial sums of a run of records: the two fixed-point sums as (h, l) pairs
+// (value h 2^27 + l) and the counts packed as accepted | rejected << 10 |
+// dropped-by-wall << 20 (a run holds at most kMaxBigThresh records).  Within
+// 32 records the l parts stay below 2^32; across passes they are carried in
+// 64 bits.
+struct Part {
+  long long wh, th;
+  unsigned long long wl, tl;
+  uint32_t n;
 };
-
-template <int G>
-__device__ __forceinline__ void group_reduce(Acc& a) {
-#pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) {
-    a.qw += shfl_xor_i128(a.qw, o);
-    a.qt += shfl_xor_i128(a.qt, o);
-    a.acc += __shfl_xor_sync(kFull, a.acc, o);
-    a.rej += __shfl_xor_sync(kFull, a.rej, o);
-    a.wal += __shfl_xor_sync(kFull, a.wal, o);
-  }
-}
-
-template <int G>
-__device__ __forceinline__ float group_min(float v) {
-#pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(kFull, v, o));
-  return v;
-}
+constexpr uint32_t kCntAcc = 1u, kCntRej = 1u << 10, kCntWall = 1u << 20;
+__device__ __forceinline__ int cnt_acc(uint32_t n) { return (int)(n & 1023u); }
+__device__ __forceinline__ int cnt_rej(uint32_t n) { return (int)((n >> 10) & 1023u); }
+__device__ __forceinline__ int cnt_wall(uint32_t n) { return (int)(n >> 20); }
 
 // The cell's snapshot and the decisions that do not depend on single points.
 struct CellCtx {
-  int32_t cell, base, len;
-  float h, ve, k2;
+  float h, ve, href, k2;
   bool valid, wall_on, gate_on;
 };
 
-__device__ __forceinline__ CellCtx load_cell(const MapDev& m, int32_t cell, int32_t base, int32_t len) {
+// The pre-update state of a cell, loaded ahead of its use.
+struct Snap {
+  float h, var;
+  int32_t t_last;
+};
+
+__device__ __forceinline__ Snap load_snap(const MapDev& m, int32_t cell) {
+  return Snap{m.h[cell], m.var[cell], m.t_last[cell]};
+}
+
+__device__ __forceinline__ CellCtx make_cell(const MapDev& m, const Snap& sn, bool wall_armed) {
   CellCtx c;
-  c.cell = cell;
-  c.base = base;
-  c.len = len;
-  c.h = m.h[cell];
-  const float var = m.var[cell];
-  c.valid = isfinite(var);
-  c.ve = c.valid ? var_eff(m, var, m.t_last[cell]) : var;
-  c.wall_on = m.wall > 0 && c.valid && len > m.wall;
+  c.h = sn.h;
+  c.valid = isfinite(sn.var);
+  c.ve = c.valid ? var_eff(m, sn.var, sn.t_last) : sn.var;
+  c.href = c.valid ? c.h : m.z_ref;
+  c.wall_on = wall_armed && c.valid;
   c.gate_on = c.valid && m.k > 0.f;
   c.k2 = __fmul_rn(m.k, m.k);
   return c;
 }
 
-// Records i0, i0 + stride, ... of the cell's segment into this lane's partials.
-__device__ __forceinline__ void fuse_records(const BatchDev& b, const MapDev& m, const CellCtx& c, float href,
-                                             int i0, int stride, Acc& a) {
-  const float2* __restrict__ rec = b.zw_sorted + c.base;
-  for (int i = i0; i < c.len; i += stride) {
-    const float2 r = rec[i];
-    const float z = r.x, vp = r.y;
-    uint8_t st = kPtFused;
-    if (c.wall_on && z < c.h) {
-      st = kPtWall;
-    } else if (c.gate_on) {
-      // |z - h| / sqrt(sigma_m^2 + sigma_p^2) > k  <=>  (z - h)^2 > k^2 (sigma_m^2 + sigma_p^2)  (k > 0)
-      const float dz = __fsub_rn(z, c.h);
-      if (__fmul_rn(dz, dz) > __fmul_rn(c.k2, __fadd_rn(c.ve, vp))) st = kPtRejected;
-    }
-    if (st == kPtFused) {
-      const float w = __frcp_rn(vp);
-      a.qw += to_fixed(w);
-      a.qt += to_fixed(__fmul_rn(w, __fsub_rn(z, href)));
-      ++a.acc;
-    } else if (st == kPtRejected) {
-      ++a.rej;
-    } else {
-      ++a.wal;
-    }
-    if (b.tr_status) b.tr_status[b.idx_sorted[c.base + i]] = st;
-  }
+__device__ __forceinline__ CellCtx load_cell(const MapDev& m, int32_t cell, bool wall_armed) {
+  return make_cell(m, load_snap(m, cell), wall_armed);
 }
 
-// New state of the cell from the reduced sums (one thread).
-__device__ __forceinline__ bool write_cell(const MapDev& m, const CellCtx& c, float href, const Acc& a) {
-  if (a.acc + a.rej == 0) return false;
+// One record: wall rule, gate, and its two fixed-point terms when accepted
+// (zero terms otherwise).
+__device__ __forceinline__ uint8_t fuse_one(const CellCtx& c, float z, float vp, Fix& fw, Fix& ft) {
+  fw = Fix{0, 0u};
+  ft = Fix{0, 0u};
+  if (c.wall_on && z < c.h) return kPtWall;
+  if (c.gate_on) {
+    // |z - h| / sqrt(sigma_m^2 + sigma_p^2) > k  <=>  (z - h)^2 > k^2 (sigma_m^2 + sigma_p^2)  (k > 0)
+    const float dz = __fsub_rn(z, c.h);
+    if (__fmul_rn(dz, dz) > __fmul_rn(c.k2, __fadd_rn(c.ve, vp))) return kPtRejected;
+  }
+  const float w = __frcp_rn(vp);
+  fw = to_fix(w);
+  ft = to_fix(__fmul_rn(w, __fsub_rn(z, c.href)));
+  return kPtFused;
+}
+
+// New state of the cell from its complete sums (one thread); true when the
+// cell took a point (accepted or rejected).
+__device__ __forceinline__ bool write_cell(const MapDev& m, int32_t cell, const CellCtx& c, __int128 qw,
+                                           __int128 qt, int acc, int rej) {
+  if (acc + rej == 0) return false;
   float h_new, var_new;
-  const float sw = from_fixed(a.qw);
-  const float st = from_fixed(a.qt);
+  const float sw = fixed_to_float(qw);
+  const float st = fixed_to_float(qt);
   if (c.valid) {
-    const float vprior = __fadd_rn(c.ve, __fmul_rn((float)a.rej, m.v_out));
-    if (a.acc == 0) {
+    const float vprior = __fadd_rn(c.ve, __fmul_rn((float)rej, m.v_out));
+    if (acc == 0) {
       h_new = c.h;
       var_new = vprior;
     } else {
@@ -190,33 +182,283 @@ __device__ __forceinline__ bool write_cell(const MapDev& m, const CellCtx& c, fl
       var_new = __frcp_rn(lam);
     }
   } else {
-    h_new = __fadd_rn(href, __fdiv_rn(st, sw));
+    h_new = __fadd_rn(c.href, __fdiv_rn(st, sw));
     var_new = __frcp_rn(sw);
   }
-  m.h[c.cell] = h_new;
-  m.var[c.cell] = var_new;
-  m.t_last[c.cell] = m.t_now;
+  m.h[cell] = h_new;
+  m.var[cell] = var_new;
+  m.t_last[cell] = m.t_now;
   return true;
 }
 
-__device__ __forceinline__ void count_cell(const BatchDev& b, MapCounters& mc, int map, const Acc& a, bool upd) {
-  const int idx[4] = {kStAccepted, kStRejected, kStWall, kStCellsUpdated};
-  unsigned long long inc[4] = {(unsigned long long)a.acc, (unsigned long long)a.rej, (unsigned long long)a.wal,
-                               upd ? 1ull : 0ull};
-  add_counter(b, mc, map, idx, 4, inc);
+// Statistics of one warp for its current map, in lane registers: each lane
+// counts its own records and the cells it wrote; a flush (warp sums, four
+// atomics by lane 0) happens when the warp moves to another map and at the end.
+struct WarpCount {
+  int map = -1;
+  uint32_t acc = 0, rej = 0, wal = 0, cells = 0;
+};
+
+__device__ __forceinline__ void add_stats(const BatchDev& b, int mi, uint32_t acc, uint32_t rej, uint32_t wal,
+                                          uint32_t cells) {
+  unsigned long long* st = b.maps[mi].ctl->stats;
+  if (acc) atomicAdd(st + kStAccepted, (unsigned long long)acc);
+  if (rej) atomicAdd(st + kStRejected, (unsigned long long)rej);
+  if (wal) atomicAdd(st + kStWall, (unsigned long long)wal);
+  if (cells) atomicAdd(st + kStCellsUpdated, (unsigned long long)cells);
 }
 
-template <int G>
-__global__ void __launch_bounds__(kFuseThreads, 4) k_fuse(const BatchDev* __restrict__ bp) {
-  __shared__ int s_slot;
-  __shared__ float s_min[kFuseWarps];
-  __shared__ __int128 s_q[2][kFuseWarps];
-  __shared__ int s_n[3][kFuseWarps];
-  const BatchDev& b = *bp;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  MapCounters mc;
+// all 32 lanes
+__device__ __forceinline__ void warp_flush(const BatchDev& b, WarpCount& wc) {
+  const uint32_t a = __reduce_add_sync(kFull, wc.acc), r = __reduce_add_sync(kFull, wc.rej);
+  const uint32_t w = __reduce_add_sync(kFull, wc.wal), c = __reduce_add_sync(kFull, wc.cells);
+  if ((threadIdx.x & 31) == 0 && wc.map >= 0) add_stats(b, wc.map, a, r, w, c);
+  wc.acc = wc.rej = wc.wal = wc.cells = 0;
+}
 
-  // ---- large cells: one block each, taken from a counter
+__device__ __forceinline__ unsigned long long rec_tag(const float4& q) {
+  return ((unsigned long long)__float_as_uint(q.w) << 32) | (unsigned long long)__float_as_uint(q.z);
+}
+
+// Write a carried run that ended at the previous pass (one lane).  Its records
+// were counted in their passes; the cell is counted here.
+__device__ __forceinline__ void finish_tag(const BatchDev& b, WarpCount& wc, unsigned long long tag, const Part& a) {
+  const uint32_t w = (uint32_t)(tag >> 32);
+  const int mi = (int)(w & kRecMapMask);
+  const int32_t cell = (int32_t)(uint32_t)tag;
+  const MapDev& m = b.maps[mi];
+  const CellCtx c = load_cell(m, cell, (w & kRecWall) != 0);
+  if (write_cell(m, cell, c, fix128(a.wh, a.wl), fix128(a.th, a.tl), cnt_acc(a.n), cnt_rej(a.n))) {
+    if (mi == wc.map) ++wc.cells; else add_stats(b, mi, 0, 0, 0, 1);
+  }
+}
+
+// Record r of the batch (zeros beyond n_rec).
+__device__ __forceinline__ float4 load_rec(const BatchDev& b, int64_t r, int32_t n_rec) {
+  return r < n_rec ? __ldg(b.rec + r) : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// A record's map and cell words are in range (every record in [0, rec_total)
+// was written by k_scatter this update; anything else is recorded and skipped).
+__device__ __forceinline__ bool rec_sane(const BatchDev& b, const float4& q) {
+  const int mi = (int)(__float_as_uint(q.w) & kRecMapMask);
+  return mi < b.n_maps && (uint32_t)__float_as_int(q.z) < (uint32_t)(b.maps[mi].W * b.maps[mi].H);
+}
+
+// Cell state for a record, loaded one pass ahead (a cell is written only by the
+// warp that owns it, when its run ends, so the prefetched value is current).
+__device__ __forceinline__ Snap prefetch_snap(const BatchDev& b, const float4& q, bool inr) {
+  if (!inr || !rec_sane(b, q)) return Snap{0.f, 0.f, 0};
+  return load_snap(b.maps[__float_as_uint(q.w) & kRecMapMask], __float_as_int(q.z));
+}
+
+// The cells whose segment starts in [ch * chunk, (ch + 1) * chunk), one warp.
+// Software pipeline: the records of pass i + 2 and the cell state of pass i + 1
+// are in flight while pass i is fused.
+__device__ __forceinline__ void fuse_chunk(const BatchDev& b, WarpCount& wc, int64_t ch, int32_t n_rec) {
+  const int lane = threadIdx.x & 31;
+  const unsigned upto = lane == 31 ? kFull : ((1u << (lane + 1)) - 1u);  // lanes <= this lane
+  const int64_t win_end = (ch + 1) * (int64_t)b.chunk;
+  int64_t pos = ch * (int64_t)b.chunk;
+  // carried run: 0 none, 1 ours (partial sums in cp), 2 not ours (started before the chunk)
+  int cmode = 0;
+  unsigned long long ctag = 0;
+  Part cp{0, 0, 0ull, 0ull, 0u};
+  if (pos > 0) {
+    ctag = rec_tag(__ldg(b.rec + pos - 1));
+    cmode = 2;
+  }
+  float4 q = load_rec(b, pos + lane, n_rec);
+  float4 qn = load_rec(b, pos + 32 + lane, n_rec);
+  Snap sn = prefetch_snap(b, q, pos + lane < n_rec);
+  for (;;) {
+    const int64_t r = pos + lane;
+    const bool inr = r < n_rec;
+    const float4 qnn = load_rec(b, pos + 64 + lane, n_rec);
+    const Snap snn = prefetch_snap(b, qn, pos + 32 + lane < n_rec);
+    const unsigned long long tag = inr ? rec_tag(q) : ~0ull;
+    unsigned long long prev = __shfl_up_sync(kFull, tag, 1);
+    if (lane == 0) prev = cmode ? ctag : ~tag;  // nothing carried: lane 0 starts a run
+    const bool head = inr && tag != prev;
+    // the carried run of ours ends where this pass starts another run (or nothing)
+    if (cmode == 1 && __shfl_sync(kFull, !inr || head, 0)) {
+      if (lane == 0) finish_tag(b, wc, ctag, cp);
+      cmode = 0;
+    }
+    const unsigned stops = __ballot_sync(kFull, !inr || (head && r >= win_end));
+    const int first_stop = stops ? __ffs(stops) - 1 : 32;
+    if (first_stop == 0) break;
+    const bool live = lane < first_stop;
+    const unsigned heads = __ballot_sync(kFull, head && live);
+    const unsigned hm = heads & upto;
+    const bool cont = live && hm == 0;  // continues the carried run
+    const int hd = hm ? 31 - __clz(hm) : 0;
+    const uint32_t w = __float_as_uint(q.w);
+    const bool big = (w & kRecBig) != 0;
+    const int mi = (int)(w & kRecMapMask);
+    const int32_t cell = __float_as_int(q.z);
+    const bool sane = live && rec_sane(b, q);
+    if (live && !sane) atomicCAS(&b.maps[0].ctl->err, 0, kErrInternal);
+    const bool ours = sane && !big && !(cont && cmode == 2);
+    // statistics: one map per pass (the usual case) goes to the lane registers
+    const int pm = ours ? mi : -1;
+    bool mixed = false;
+    if (!__all_sync(kFull, pm < 0 || pm == wc.map)) {
+      const unsigned om = __ballot_sync(kFull, pm >= 0);
+      const int first = __shfl_sync(kFull, pm, __ffs(om) - 1);
+      if (__all_sync(kFull, pm < 0 || pm == first)) {
+        warp_flush(b, wc);
+        wc.map = first;
+      } else {
+        mixed = true;  // a pass across a map boundary: count with atomics
+      }
+    }
+    Fix fw{0, 0u}, ft{0, 0u};
+    uint32_t n = 0u;
+    CellCtx c;
+    if (ours) {
+      c = make_cell(b.maps[mi], sn, (w & kRecWall) != 0);
+      const uint8_t st = fuse_one(c, q.x, q.y, fw, ft);
+      n = st == kPtFused ? kCntAcc : st == kPtRejected ? kCntRej : kCntWall;
+      if (!mixed) {
+        wc.acc += st == kPtFused;
+        wc.rej += st == kPtRejected;
+        wc.wal += st == kPtWall;
+      } else {
+        add_stats(b, mi, st == kPtFused, st == kPtRejected, st == kPtWall, 0);
+      }
+      if (b.tr_status) b.tr_status[b.idx_sorted[r]] = st;
+    }
+    // segmented inclusive scan: lane l sums lanes hd(l) .. l of its run; only as
+    // many steps as the longest run of this pass needs
+    const int runlen = live ? lane - hd + 1 : 0;
+    const int maxrun = (int)__reduce_max_sync(kFull, (unsigned)runlen);
+    long long wh = fw.h, th = ft.h;
+    uint32_t wl = fw.l, tl = ft.l;
+    for (int o = 1; o < maxrun; o <<= 1) {
+      const long long awh = __shfl_up_sync(kFull, wh, o), ath = __shfl_up_sync(kFull, th, o);
+      const uint32_t awl = __shfl_up_sync(kFull, wl, o), atl = __shfl_up_sync(kFull, tl, o);
+      const uint32_t an = __shfl_up_sync(kFull, n, o);
+      if (lane - o >= hd) {
+        wh += awh;
+        th += ath;
+        wl += awl;
+        tl += atl;
+        n += an;
+      }
+    }
+    Part v{wh, th, (unsigned long long)wl, (unsigned long long)tl, n};
+    if (cont && cmode == 1) {  // the carried partial sums belong to this run
+      v.wh += cp.wh;
+      v.th += cp.th;
+      v.wl += cp.wl;
+      v.tl += cp.tl;
+      v.n += cp.n;
+    }
+    const bool next_head = lane < 31 && ((heads >> (lane + 1)) & 1u);
+    const bool end = live && (next_head || (lane == first_stop - 1 && first_stop < 32));
+    if (end && ours &&
+        write_cell(b.maps[mi], cell, c, fix128(v.wh, v.wl), fix128(v.th, v.tl), cnt_acc(v.n), cnt_rej(v.n))) {
+      if (!mixed) ++wc.cells; else add_stats(b, mi, 0, 0, 0, 1);
+    }
+    if (first_stop < 32) break;
+    // lane 31's run goes on in the next 32 records
+    const unsigned long long t31 = __shfl_sync(kFull, tag, 31);
+    if (__shfl_sync(kFull, ours, 31)) {
+      cp.wh = __shfl_sync(kFull, v.wh, 31);
+      cp.th = __shfl_sync(kFull, v.th, 31);
+      cp.wl = __shfl_sync(kFull, v.wl, 31);
+      cp.tl = __shfl_sync(kFull, v.tl, 31);
+      cp.n = __shfl_sync(kFull, v.n, 31);
+      cmode = 1;
+      ctag = t31;
+    } else if (__shfl_sync(kFull, big && sane, 31)) {
+      // skip the rest of a large cell: its segment end from the cell's (base, count)
+      const uint32_t w31 = (uint32_t)(t31 >> 32);
+      const int2 sg = b.maps[w31 & kRecMapMask].cell_seg[(int32_t)(uint32_t)t31];
+      const int64_t next = (int64_t)sg.x + sg.y;
+      if (next > pos + 32) {  // restart the pipeline there
+        pos = next;
+        cmode = 0;
+        q = load_rec(b, pos + lane, n_rec);
+        qn = load_rec(b, pos + 32 + lane, n_rec);
+        sn = prefetch_snap(b, q, pos + lane < n_rec);
+        continue;
+      }
+      cmode = 0;
+    } else {
+      cmode = 2;  // a run that started before the chunk
+      ctag = t31;
+    }
+    pos += 32;
+    q = qn;
+    qn = qnn;
+    sn = snn;
+  }
+}
+
+// A large cell with a whole block: lane partial sums, warp and block reductions.
+__device__ __forceinline__ void fuse_big(const BatchDev& b, int2 e, __int128* s_q, uint32_t* s_n) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const MapDev& m = b.maps[e.x];
+  const int2 sg = m.cell_seg[e.y];
+  const CellCtx c = load_cell(m, e.y, m.wall > 0 && sg.y > m.wall);
+  long long wh = 0, th = 0;
+  unsigned long long wl = 0, tl = 0;
+  uint32_t acc = 0, rej = 0, wal = 0;
+  for (int i = threadIdx.x; i < sg.y; i += kFuseThreads) {
+    const float4 q = __ldg(b.rec + sg.x + i);
+    Fix fw, ft;
+    const uint8_t st = fuse_one(c, q.x, q.y, fw, ft);
+    wh += fw.h;
+    wl += fw.l;
+    th += ft.h;
+    tl += ft.l;
+    acc += st == kPtFused;
+    rej += st == kPtRejected;
+    wal += st == kPtWall;
+    if (b.tr_status) b.tr_status[b.idx_sorted[sg.x + i]] = st;
+  }
+  __int128 qw = fix128(wh, wl), qt = fix128(th, tl);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    qw += shfl_xor_i128(qw, o);
+    qt += shfl_xor_i128(qt, o);
+  }
+  acc = __reduce_add_sync(kFull, acc);
+  rej = __reduce_add_sync(kFull, rej);
+  wal = __reduce_add_sync(kFull, wal);
+  if (lane == 0) {
+    s_q[warp] = qw;
+    s_q[kFuseWarps + warp] = qt;
+    s_n[warp] = acc;
+    s_n[kFuseWarps + warp] = rej;
+    s_n[2 * kFuseWarps + warp] = wal;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __int128 tw = 0, tt = 0;
+    uint32_t ta = 0, tr = 0, tl2 = 0;
+    for (int k = 0; k < kFuseWarps; ++k) {
+      tw += s_q[k];
+      tt += s_q[kFuseWarps + k];
+      ta += s_n[k];
+      tr += s_n[kFuseWarps + k];
+      tl2 += s_n[2 * kFuseWarps + k];
+    }
+    const bool upd = write_cell(m, e.y, c, tw, tt, (int)ta, (int)tr);
+    add_stats(b, e.x, ta, tr, tl2, upd ? 1u : 0u);
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kFuseThreads, kFuseBlocksPerSM) k_fuse(const BatchDev* __restrict__ bp) {
+  __shared__ int s_slot;
+  __shared__ __int128 s_q[2 * kFuseWarps];
+  __shared__ uint32_t s_n[3 * kFuseWarps];
+  const BatchDev& b = *bp;
+
+  // ---- large cells first (the longest jobs): one block each, taken from a counter
   const int n_big = min(b.ctl->n_big, b.big_cap);
   if (n_big > 0) {
     for (;;) {
@@ -225,123 +467,27 @@ __global__ void __launch_bounds__(kFuseThreads, 4) k_fuse(const BatchDev* __rest
       const int jb = s_slot;
       __syncthreads();
       if (jb >= n_big) break;
-      const int2 e = b.big_list[jb];
-      const MapDev& m = b.maps[e.x];
-      const CellCtx c = load_cell(m, e.y, m.cell_base[e.y], m.cell_len[e.y]);
-      float href = c.h;
-      if (!c.valid) {
-        float zmin = __int_as_float(0x7f800000);
-        for (int i = threadIdx.x; i < c.len; i += kFuseThreads) zmin = fminf(zmin, b.zw_sorted[c.base + i].x);
-        zmin = group_min<32>(zmin);
-        if (lane == 0) s_min[warp] = zmin;
-        __syncthreads();
-        zmin = s_min[0];
-        for (int w = 1; w < kFuseWarps; ++w) zmin = fminf(zmin, s_min[w]);
-        href = zmin;
-      }
-      Acc a{0, 0, 0, 0, 0};
-      fuse_records(b, m, c, href, threadIdx.x, kFuseThreads, a);
-      group_reduce<32>(a);
-      if (lane == 0) {
-        s_q[0][warp] = a.qw;
-        s_q[1][warp] = a.qt;
-        s_n[0][warp] = a.acc;
-        s_n[1][warp] = a.rej;
-        s_n[2][warp] = a.wal;
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        Acc t{0, 0, 0, 0, 0};
-        for (int w = 0; w < kFuseWarps; ++w) {
-          t.qw += s_q[0][w];
-          t.qt += s_q[1][w];
-          t.acc += s_n[0][w];
-          t.rej += s_n[1][w];
-          t.wal += s_n[2][w];
-        }
-        const bool upd = write_cell(m, c, href, t);
-        count_cell(b, mc, e.x, t, upd);
-      }
-      __syncthreads();
+      fuse_big(b, b.big_list[jb], s_q, s_n);
     }
   }
 
-  // ---- medium cells: groups of G lanes, grid-stride over the list
-  constexpr int kGroupsPerWarp = 32 / G;
-  const int n_med = min(b.ctl->n_med, b.med_cap);
-  const int gl = lane % G, gw = lane / G;
-  const int warp_global = blockIdx.x * kFuseWarps + warp;
-  const int warp_stride = gridDim.x * kFuseWarps;
-  for (int jb = warp_global * kGroupsPerWarp; jb < n_med; jb += warp_stride * kGroupsPerWarp) {
-    const int j = jb + gw;
-    const bool has = j < n_med;
-    int2 e = make_int2(0, 0);
-    CellCtx c;
-    if (has) {
-      e = b.med_list[j];
-      const MapDev& m = b.maps[e.x];
-      c = load_cell(m, e.y, m.cell_base[e.y], m.cell_len[e.y]);
-    } else {
-      c.len = 0;
-      c.valid = true;
-      c.h = 0.f;
-    }
-    const MapDev& m = b.maps[e.x];
-    float zmin = __int_as_float(0x7f800000);
-    if (!c.valid)
-      for (int i = gl; i < c.len; i += G) zmin = fminf(zmin, b.zw_sorted[c.base + i].x);
-    zmin = group_min<G>(zmin);
-    const float href = c.valid ? c.h : zmin;
-    Acc a{0, 0, 0, 0, 0};
-    if (has) fuse_records(b, m, c, href, gl, G, a);
-    group_reduce<G>(a);
-    if (has && gl == 0) {
-      const bool upd = write_cell(m, c, href, a);
-      count_cell(b, mc, e.x, a, upd);
-    }
-  }
-
-  // ---- small cells: one thread per cell over the tiles of the cell space
-  for_each_tile(b, [&](const MapDev& m, int mi, int32_t p0, int32_t count) {
-    for (int32_t i = threadIdx.x; i < count; i += kFuseThreads) {
-      const int32_t p = p0 + i;
-      const int32_t len = m.cell_len[p];
-      if (len < 1 || len > b.small_thresh) continue;
-      const CellCtx c = load_cell(m, p, m.cell_base[p], len);
-      float href = c.h;
-      if (!c.valid) {
-        href = __int_as_float(0x7f800000);
-        for (int k = 0; k < len; ++k) href = fminf(href, b.zw_sorted[c.base + k].x);
-      }
-      Acc a{0, 0, 0, 0, 0};
-      fuse_records(b, m, c, href, 0, 1, a);
-      const bool upd = write_cell(m, c, href, a);
-      count_cell(b, mc, mi, a, upd);
-    }
-  });
-
-  const int idx[4] = {kStAccepted, kStRejected, kStWall, kStCellsUpdated};
-  if (mc.map >= 0) {  // fold nothing new; flush per block
-    unsigned long long zero[4] = {0, 0, 0, 0};
-    add_counter(b, mc, mc.map, idx, 4, zero);
-  }
-  flush_counters(b, mc, idx, 4);
+  // ---- record chunks, one warp each (grid-stride)
+  const int32_t n_rec = (int32_t)min((int64_t)b.ctl->rec_total, b.n_points);
+  const int64_t n_chunks = ((int64_t)n_rec + b.chunk - 1) / b.chunk;
+  const int64_t wstride = (int64_t)gridDim.x * kFuseWarps;
+  WarpCount wc;
+  for (int64_t ch = (int64_t)blockIdx.x * kFuseWarps + (threadIdx.x >> 5); ch < n_chunks; ch += wstride)
+    fuse_chunk(b, wc, ch, n_rec);
+  warp_flush(b, wc);
 }
 
-cudaError_t launch_fuse(const BatchDev* b, int64_t n_cells, int64_t n_points, int group, cudaStream_t s) {
-  const int g = (group == 4 || group == 8 || group == 16 || group == 32) ? group : 8;
-  const int64_t tiles = n_cells / kTile;
-  int64_t want = tiles > 1 ? tiles : 1;
-  const int64_t med_blocks = (n_points / (kMinSmall + 1)) / (kFuseThreads / g) + 1;
-  if (med_blocks > want) want = med_blocks;
-  const int64_t cap = (int64_t)sm_count() * 8;
-  const int grid = (int)(want < cap ? want : cap);
-  switch (g) {
-    case 4: k_fuse<4><<<grid, kFuseThreads, 0, s>>>(b); break;
-    case 16: k_fuse<16><<<grid, kFuseThreads, 0, s>>>(b); break;
-    case 32: k_fuse<32><<<grid, kFuseThreads, 0, s>>>(b); break;
-    default: k_fuse<8><<<grid, kFuseThreads, 0, s>>>(b); break;
-  }
+cudaError_t launch_fuse(const BatchDev* b, int64_t n_points, int chunk, cudaStream_t s) {
+  const int c = (chunk >= 64 && chunk <= 1024 && (chunk & (chunk - 1)) == 0) ? chunk : 256;
+  const int64_t warps = n_points / c + 1;
+  const int64_t want = (warps + kFuseWarps - 1) / kFuseWarps;
+  const int64_t cap = (int64_t)sm_count() * kFuseBlocksPerSM;  // one resident wave
+  const int grid = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
+  k_fuse<<<grid, kFuseThreads, 0, s>>>(b);
   return cudaGetLastError();
 }
 

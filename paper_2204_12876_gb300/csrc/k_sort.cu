@@ -5,16 +5,19 @@
 //              then per cell: the ray-march threshold h - sqrt(var_eff) of the
 //              pre-update map, stored in logical order (one 4-byte gather per
 //              ray sample later, with no ring-buffer wrap)
-//   k_alloc    per tile of cells: block scans of the counts give every touched
-//              cell a segment [base, base + count) of the record array; cells
-//              with more than small_thresh records are listed for group fusion,
-//              more than big_thresh for whole-block fusion
+//   k_alloc    per tile of cells: a block scan of the counts gives every cell
+//              a segment [base, base + count) of the record array (the tile's
+//              segments are consecutive, in cell order; a tile takes its range
+//              from one cursor shared by all maps of the batch, so the records
+//              of the batch fill [0, rec_total) without holes); cells with more
+//              than big_thresh records are listed for whole-block fusion
 //   k_scatter  per point: transform + bin again, claim a slot in the cell's
-//              segment, write the record (z, sigma_p^2)
+//              segment, write the 16-byte record (z, sigma_p^2, cell, map|flags)
 //
-// The order of records inside a segment depends on atomic arrival order.  The
-// fusion kernel sums them exactly in integer fixed point, so that order never
-// changes a result.
+// The order of records inside a segment depends on atomic arrival order, and
+// the order of the tiles' ranges on the cursor.  The fusion kernel sums the
+// records of a cell exactly in integer fixed point, so neither order changes
+// a result.
 #include "em_point.cuh"
 
 namespace em {
@@ -77,13 +80,10 @@ __global__ void __launch_bounds__(kPointThreads) k_count(const BatchDev* __restr
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // per-update counters start at zero (the previous update is complete)
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    b.ctl->n_med = 0;
+    b.ctl->rec_total = 0;
     b.ctl->n_big = 0;
     b.ctl->big_next = 0;
-    for (int mi = 0; mi < b.n_maps; ++mi) {
-      b.maps[mi].ctl->seg_cursor = 0;
-      atomicAdd(&b.maps[mi].ctl->stats[kStUpdates], 1ull);
-    }
+    for (int mi = 0; mi < b.n_maps; ++mi) atomicAdd(&b.maps[mi].ctl->stats[kStUpdates], 1ull);
   }
   int64_t beg, end;
   block_range(b.n_points, beg, end);
@@ -160,7 +160,7 @@ constexpr int kAllocPer = kTile / kCellThreads;
 
 __global__ void __launch_bounds__(kCellThreads) k_alloc(const BatchDev* __restrict__ bp) {
   __shared__ int warp_tot[33];
-  __shared__ int s_base[3];
+  __shared__ int s_base[2];
   const BatchDev& b = *bp;
   const int64_t n_tiles = b.n_cells / kTile;
   for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
@@ -171,48 +171,46 @@ __global__ void __launch_bounds__(kCellThreads) k_alloc(const BatchDev* __restri
     const int64_t p0 = g0 - m.cell_begin;
     if (p0 >= ncell) continue;  // padding (block-uniform)
     int c[kAllocPer];
-    int sum = 0, nm = 0, nb = 0;
+    int sum = 0, nb = 0;
     const int32_t first = (int32_t)p0 + threadIdx.x * kAllocPer;
+    if (first + kAllocPer <= ncell) {
+      const int4 v = *reinterpret_cast<const int4*>(m.cnt + first);
+      c[0] = v.x; c[1] = v.y; c[2] = v.z; c[3] = v.w;
+    } else {
+#pragma unroll
+      for (int k = 0; k < kAllocPer; ++k) c[k] = (first + k < ncell) ? m.cnt[first + k] : 0;
+    }
 #pragma unroll
     for (int k = 0; k < kAllocPer; ++k) {
-      c[k] = (first + k < ncell) ? m.cnt[first + k] : 0;
       sum += c[k];
-      nm += c[k] > b.small_thresh && c[k] <= b.big_thresh;
       nb += c[k] > b.big_thresh;
     }
-    int tot_c, tot_m, tot_b;
+    int tot_c, tot_b;
     const int off_c = block_exclusive_scan(sum, warp_tot, tot_c);
-    const int off_m = block_exclusive_scan(nm, warp_tot, tot_m);
     const int off_b = block_exclusive_scan(nb, warp_tot, tot_b);
     if (threadIdx.x == 0) {
-      s_base[0] = tot_c ? atomicAdd(&m.ctl->seg_cursor, tot_c) : 0;
-      s_base[1] = tot_m ? atomicAdd(&b.ctl->n_med, tot_m) : 0;
-      s_base[2] = tot_b ? atomicAdd(&b.ctl->n_big, tot_b) : 0;
+      s_base[0] = tot_c ? atomicAdd(&b.ctl->rec_total, tot_c) : 0;
+      s_base[1] = tot_b ? atomicAdd(&b.ctl->n_big, tot_b) : 0;
     }
     __syncthreads();
-    int64_t rec = m.pt_begin + s_base[0] + off_c;
-    int32_t ms = s_base[1] + off_m, bs = s_base[2] + off_b;
-    int32_t base[kAllocPer];
+    int32_t rec = s_base[0] + off_c;
+    int32_t bs = s_base[1] + off_b;
+    int2 seg[kAllocPer];
 #pragma unroll
     for (int k = 0; k < kAllocPer; ++k) {
-      base[k] = (int32_t)rec;
+      seg[k] = make_int2(rec, c[k]);
       rec += c[k];
       if (c[k] > b.big_thresh) {
         if (bs < b.big_cap) b.big_list[bs] = make_int2(mi, first + k); else atomicExch(&b.ctl->overflow, 1);
         ++bs;
-      } else if (c[k] > b.small_thresh) {
-        if (ms < b.med_cap) b.med_list[ms] = make_int2(mi, first + k); else atomicExch(&b.ctl->overflow, 1);
-        ++ms;
       }
     }
-    if (first + kAllocPer <= ncell) {  // 16-byte stores of the per-cell base / length
-      *reinterpret_cast<int4*>(m.cell_base + first) = make_int4(base[0], base[1], base[2], base[3]);
-      *reinterpret_cast<int4*>(m.cell_len + first) = make_int4(c[0], c[1], c[2], c[3]);
+    if (first + kAllocPer <= ncell) {  // two 16-byte stores of the (base, count) pairs
+      int4* dst = reinterpret_cast<int4*>(m.cell_seg + first);
+      dst[0] = make_int4(seg[0].x, seg[0].y, seg[1].x, seg[1].y);
+      dst[1] = make_int4(seg[2].x, seg[2].y, seg[3].x, seg[3].y);
     } else {
-      for (int k = 0; k < kAllocPer && first + k < ncell; ++k) {
-        m.cell_base[first + k] = base[k];
-        m.cell_len[first + k] = c[k];
-      }
+      for (int k = 0; k < kAllocPer && first + k < ncell; ++k) m.cell_seg[first + k] = seg[k];
     }
     __syncthreads();
   }
@@ -237,20 +235,22 @@ __global__ void __launch_bounds__(kPointThreads) k_scatter(const BatchDev* __res
     const unsigned long long tag = inm ? ((unsigned long long)(uint32_t)c.map << 32) | (uint32_t)key : ~0ull;
     int head, run;
     key_runs(tag, head, run);
-    // the segment base is read before the slot claim so both loads are in flight together
-    const int32_t seg = inm ? __ldg(m.cell_base + key) : 0;
+    // the segment is read before the slot claim so both loads are in flight together
+    const int2 seg = inm ? __ldg(m.cell_seg + key) : make_int2(0, 0);
     int old = 0;
     if (inm && lane == head) old = atomicSub(&m.cnt[key], run);
     old = __shfl_sync(kFull, old, head);
     if (inm) {
       const int rank = lane - head;
-      const int64_t pos = (int64_t)seg + old - 1 - rank;
+      const int64_t pos = (int64_t)seg.x + old - 1 - rank;
       // the count pass found the same cell for this point, so pos lies in the
       // cell's segment; anything else is recorded instead of written
-      if (pos < m.pt_begin || pos >= m.pt_begin + m.pt_count || old - rank <= 0) {
-        atomicCAS(&m.ctl->err, 0, -3);
+      if (pos < seg.x || pos >= (int64_t)seg.x + seg.y || pos >= b.n_points || old - rank <= 0) {
+        atomicCAS(&m.ctl->err, 0, kErrInternal);
       } else {
-        b.zw_sorted[pos] = make_float2(pg.z, point_variance(m, pg.d));
+        const uint32_t w = (uint32_t)c.map | (seg.y > b.big_thresh ? kRecBig : 0u) |
+                           (m.wall > 0 && seg.y > m.wall ? kRecWall : 0u);
+        b.rec[pos] = make_float4(pg.z, point_variance(m, pg.d), __int_as_float(key), __uint_as_float(w));
         if (b.idx_sorted) b.idx_sorted[pos] = (int32_t)g;
       }
     }

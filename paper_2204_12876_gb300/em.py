@@ -312,8 +312,7 @@ BATCH_GRAPH = 1
 
 
 class _Tuning(ctypes.Structure):
-    _fields_ = [("ray_group", ctypes.c_int32), ("fuse_group", ctypes.c_int32), ("big_thresh", ctypes.c_int32),
-                ("small_thresh", ctypes.c_int32)]
+    _fields_ = [("ray_group", ctypes.c_int32), ("fuse_chunk", ctypes.c_int32), ("big_thresh", ctypes.c_int32)]
 
 
 def _bind_batch():
@@ -377,8 +376,8 @@ class Batch:
         _check(lib.em_batch_get_tuning(self._h, ctypes.byref(t)), "em_batch_get_tuning")
         return {f: getattr(t, f) for f, _ in _Tuning._fields_}
 
-    def set_tuning(self, ray_group: int, fuse_group: int, big_thresh: int, small_thresh: int = 8):
-        t = _Tuning(ray_group, fuse_group, big_thresh, small_thresh)
+    def set_tuning(self, ray_group: int, fuse_chunk: int, big_thresh: int):
+        t = _Tuning(ray_group, fuse_chunk, big_thresh)
         _check(lib.em_batch_set_tuning(self._h, ctypes.byref(t)), "em_batch_set_tuning")
 
 
@@ -535,9 +534,9 @@ def _batch_profile_read(self) -> dict:
     return {k: (ms[i], n[i]) for i, k in enumerate(PROF_SLOTS)}
 
 
-def _server_set_tuning(self, ray_group: int, fuse_group: int, big_thresh: int, small_thresh: int = 8):
+def _server_set_tuning(self, ray_group: int, fuse_chunk: int, big_thresh: int):
     """Call while the server is idle (after drain)."""
-    t = _Tuning(ray_group, fuse_group, big_thresh, small_thresh)
+    t = _Tuning(ray_group, fuse_chunk, big_thresh)
     _check(lib.em_server_set_tuning(self._h, ctypes.byref(t)), "em_server_set_tuning")
 
 

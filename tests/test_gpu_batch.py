@@ -79,7 +79,8 @@ def test_autotune_keeps_maps_and_picks_valid_shapes(em):
     info = [m.info()["t_now"] for m in maps]
     batch = em.Batch(max_maps=8, max_clouds=16, max_points=200000, max_cells=200 * 200, graph=True)
     t = batch.autotune(pairs, reps=2)
-    assert t["ray_group"] in (1, 2, 4, 8, 16, 32) and t["fuse_group"] in (4, 8, 16, 32) and t["big_thresh"] >= 1
+    assert t["ray_group"] in (1, 2, 4, 8, 16, 32) and t["fuse_chunk"] in (64, 128, 256, 512, 1024)
+    assert 32 <= t["big_thresh"] <= 1023
     assert batch.tuning() == t
     torch.cuda.synchronize()
     assert_same(before, states(maps))
@@ -105,3 +106,46 @@ def test_batch_capacities(em):
     assert e.value.code == em.EM_ERR_CAPACITY
     # a refused batch leaves the maps untouched
     assert [m.info()["t_now"] for m in maps] == [5] * len(maps)
+
+
+def dense_cloud(seed, centres, per_cell, half):
+    """Clusters of per_cell points inside single cells (more than the large-cell
+    threshold) plus a uniform sprinkle; sensor 0.5 m above the map origin."""
+    rng = np.random.default_rng(seed)
+    pts = []
+    for cx, cy in centres:
+        xy = np.array([cx, cy]) + rng.uniform(0.005, 0.035, (per_cell, 2))
+        z = 0.1 + rng.normal(0.0, 0.01, per_cell)
+        pts.append(np.column_stack([xy, z]))
+    n = 4000
+    pts.append(np.column_stack([rng.uniform(-half, half, (n, 2)), rng.normal(0.0, 0.02, n)]))
+    pw = np.concatenate(pts).astype(np.float32)
+    rng.shuffle(pw)
+    t = np.array([0.0, 0.0, 0.5], np.float32)
+    return (pw - t).astype(np.float32), synth.pose_matrix(np.eye(3), t)
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_launch_shapes_give_identical_maps(em, graph):
+    """Every tuning (records per warp chunk, large-cell threshold, lanes per ray)
+    gives the same maps bit for bit, including cells with thousands of records."""
+    results = []
+    shapes = [dict(ray_group=4, fuse_chunk=256, big_thresh=256), dict(ray_group=1, fuse_chunk=64, big_thresh=32),
+              dict(ray_group=32, fuse_chunk=1024, big_thresh=1023)]
+    for tune in shapes:
+        maps, pairs = make_maps(em, seed=300)
+        half = 0.5 * 100 * 0.04
+        pts, pose = dense_cloud(7, [(-0.52, 0.36), (0.8, -1.2), (0.0, 0.0), (1.6, 1.6)], 3000, half)
+        pairs.append((maps[1], dev(pts), pose))
+        batch = em.Batch(max_maps=8, max_clouds=16, max_points=400000, max_cells=200 * 200, graph=graph)
+        batch.set_tuning(**tune)
+        for _ in range(2):
+            batch.update(pairs)
+        torch.cuda.synchronize()
+        results.append((states(maps), [m.stats() for m in maps]))
+        batch.close()
+    for st, stats in results[1:]:
+        assert_same(results[0][0], st)
+        for a, b in zip(results[0][1], stats):
+            for k in ("points_accepted", "points_rejected", "cells_updated", "cells_cleared", "ray_samples"):
+                assert a[k] == b[k], k

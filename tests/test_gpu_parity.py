@@ -95,6 +95,28 @@ def test_single_update_prior_gate_wall_time(em):
     check_counts(gm, tr, cmp.notes["marginal_points"])
 
 
+def test_dense_cells_block_fusion_and_wall(em):
+    """Cells holding hundreds to thousands of points (fused by a whole block)
+    next to sparse ones, with the wall rule and the gate armed."""
+    P = dict(width=100, height=100, resolution=0.04, noise_a0=0.005, noise_a2=0.002, mahalanobis_k=2.5,
+             outlier_variance=1e-4, wall_num_thresh=6)
+    prior = synth.random_prior(seed=23, width=100, height=100, t_now=6)
+    rng = np.random.default_rng(24)
+    parts = []
+    for (cx, cy), n in zip([(-0.52, 0.36), (0.8, -1.2), (0.04, 0.0), (1.6, 1.6), (-1.0, -1.0)],
+                           [3000, 700, 300, 1500, 40]):
+        xy = np.array([cx, cy]) + rng.uniform(0.003, 0.037, (n, 2))
+        parts.append(np.column_stack([xy, rng.normal(0.0, 0.05, n)]))
+    parts.append(np.column_stack([rng.uniform(-2.0, 2.0, (20000, 2)), rng.normal(0.0, 0.05, 20000)]))
+    pw = np.concatenate(parts)
+    pw = pw[rng.permutation(len(pw))].astype(np.float32)
+    t = np.array([0.0, 0.0, 0.5], np.float32)
+    pts, pose = (pw - t).astype(np.float32), synth.pose_matrix(np.eye(3), t)
+    cmp, tr, gm, _ = run_case(em, P, [(pts, pose)], prior=prior, wall_on=True)
+    assert tr.counts["wall"] > 500 and tr.counts["rejected"] > 500
+    check_counts(gm, tr, cmp.notes["marginal_points"])
+
+
 def test_stride4_and_misaligned_and_ragged(em):
     """Stride-4 rows, a base pointer off 16-byte alignment and a ragged count
     give the same state as the aligned stride-3 cloud, bit for bit."""
