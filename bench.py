@@ -62,7 +62,7 @@ N_ROBOTS = 32
 RATE_HZ = 2000.0
 BUDGET = 40 << 30
 L2_FLUSH_BYTES = 256 << 20
-RAY_OPS_PER_SAMPLE = 26  # integer / float / compare / load operations per ray sample in the k_ray march
+RAY_OPS_PER_SAMPLE = 22  # float / integer / compare / load operations per ray sample in the k_ray march
 
 
 def f32params(P):

@@ -71,7 +71,7 @@ enum {
  * (Section II-C noise model alpha_d, time variance sigma_t^2, Mahalanobis
  * distance, wall count; Section II-E ray step, update age, alpha_n). */
 typedef struct em_params {
-  int32_t width, height;        /* cells, >= 1, width*height <= 2^26 */
+  int32_t width, height;        /* cells, 1 .. 2^22 each, width*height <= 2^26 */
   float resolution;             /* metres per cell, > 0 */
   float noise_a0, noise_a1, noise_a2; /* sigma_p = a0 + a1 d + a2 d^2; the paper's alpha_d d^2 is a1 = sqrt(alpha_d) */
   float var_min;                /* floor on sigma_p^2, > 0 */

@@ -146,7 +146,7 @@ MapDev make_mapdev(const em_map* m) {
 
 bool params_ok(const em_params* p) {
   if (!p) return false;
-  if (p->width < 1 || p->height < 1) return false;
+  if (p->width < 1 || p->height < 1 || p->width > (1 << 22) || p->height > (1 << 22)) return false;
   if ((int64_t)p->width * p->height > (int64_t(1) << 26)) return false;
   if (!(std::isfinite(p->resolution) && p->resolution > 0.f)) return false;
   const float f[] = {p->noise_a0, p->noise_a1, p->noise_a2, p->var_min, p->min_range, p->mahalanobis_k,

@@ -82,7 +82,7 @@ int scratch_address(int dev, unsigned char** out) {
 }
 
 bool na_params_ok(const em_params* p) {
-  if (!p || p->width < 1 || p->height < 1) return false;
+  if (!p || p->width < 1 || p->height < 1 || p->width > (1 << 22) || p->height > (1 << 22)) return false;
   if (!(std::isfinite(p->resolution) && p->resolution > 0.f)) return false;
   const float f[] = {p->noise_a0, p->noise_a1, p->noise_a2, p->var_min, p->min_range, p->mahalanobis_k,
                      p->outlier_variance, p->time_variance, p->ray_step, p->cleanup_normal_thresh};

@@ -38,6 +38,9 @@ __device__ __forceinline__ bool slab(float o, float v, float d, float a0, float 
 // Per-ray set-up shared by the lanes that march it.  Sample k lies at
 // q = a + k b in cell units (x, y) and at z = az + k bz, i.e. the track
 // o + (k step / d) (R p_s) measured from the map corner in cells.
+// Samples per ray are capped at 2^24 - 1, so the float sample index is exact.
+constexpr int32_t kMaxRayK = (1 << 24) - 1;
+
 struct RaySetup {
   float ax, bx, ay, by, az, bz;
   float vx, vy, vz, d;  // for the Eq. 4 guard
@@ -55,8 +58,7 @@ __global__ void __launch_bounds__(kRayThreads) k_ray(const BatchDev* __restrict_
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   RaySetup* wr = s_ray + warp * 32;
   const int64_t n_warps = (int64_t)gridDim.x * (kRayThreads / 32);
-  MapCounters mc;
-  const int stat_idx[1] = {kStRaySamples};
+  int smap = -1;  // map of this lane's sample count
   unsigned long long samples = 0;
   for (int64_t wbase = ((int64_t)blockIdx.x * (kRayThreads / 32) + warp) * 32; wbase < b.n_points;
        wbase += n_warps * 32) {
@@ -82,8 +84,8 @@ __global__ void __launch_bounds__(kRayThreads) k_ray(const BatchDev* __restrict_
           const float step = m.ray_step;
           const float kl = floorf((lo - 1e-3f) / step) - 1.f;
           const float kh = ceilf((hi + 1e-3f) / step) + 1.f;
-          const int32_t k_lo = kl < 1.f ? 1 : (int32_t)kl;
-          int32_t k_hi = kh > 1.0e9f ? 1000000000 : (int32_t)kh;
+          const int32_t k_lo = kl < 1.f ? 1 : kl > (float)kMaxRayK ? kMaxRayK : (int32_t)kl;
+          int32_t k_hi = kh > (float)kMaxRayK ? kMaxRayK : (int32_t)kh;
           // last k with k * step < d, decided exactly as sample by sample
           float kf = floorf(__fdiv_rn(pg.d, step));
           int32_t k_last = kf > 1.0e9f ? 1000000000 : (int32_t)kf;
@@ -113,33 +115,40 @@ __global__ void __launch_bounds__(kRayThreads) k_ray(const BatchDev* __restrict_
     for (int r0 = 0; r0 < 32; r0 += 32 / G) {
       const RaySetup& R = wr[r0 + lane / G];
       if (R.n <= 0) continue;
-      if (R.map != mc.map) {  // fold this map's samples in, then switch maps
-        if (mc.map >= 0) add_counter(b, mc, mc.map, stat_idx, 1, &samples);
+      if (R.map != smap) {  // count this lane's samples per map
+        if (smap >= 0 && samples) atomicAdd(&b.maps[smap].ctl->stats[kStRaySamples], samples);
         samples = 0;
-        add_counter(b, mc, R.map, stat_idx, 1, &samples);
+        smap = R.map;
       }
       if (gl == 0) samples += (unsigned long long)R.n;
       const MapDev& m = b.maps[R.map];
       const int32_t W = m.W, H = m.H, ox = m.ox, oy = m.oy;
       const float* __restrict__ thr = m.thr;
       const bool guard = m.alpha_n > 0.f;
-      const int32_t k_end = R.k_lo + R.n;
+      const int32_t k_end = R.k_lo + R.n, rix = R.ix, riy = R.iy;
       const float ax = R.ax, bx = R.bx, ay = R.ay, by = R.by, az = R.az, bz = R.bz;
+      float kf = (float)(R.k_lo + gl);  // sample index as a float, stepped exactly (k < 2^24)
       for (int32_t k = R.k_lo + gl; k < k_end; k += 4 * G) {
         int32_t pl[4];
         float zz[4], th[4];
+        bool any = false;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const int32_t kk = k + u * G;
-          const float kf = (float)kk;
-          const int32_t cx = __float2int_rd(__fmaf_rn(kf, bx, ax));  // floor; saturates far outside
-          const int32_t cy = __float2int_rd(__fmaf_rn(kf, by, ay));
-          const bool ok = kk < k_end && (uint32_t)cx < (uint32_t)W && (uint32_t)cy < (uint32_t)H &&
-                          !(cx == R.ix && cy == R.iy);
+          // floor(t) of t = fma(k, b, a) by one add rounded down: t + 1.5 2^23 lands where the
+          // float spacing is 1, so its bits hold floor(t) + 0x4B400000 (|t| < 2^22; anything
+          // farther out gives an index outside [0, 2^22) and fails the box test below)
+          const int32_t cx = __float_as_int(__fadd_rd(__fmaf_rn(kf, bx, ax), 12582912.0f)) - 0x4B400000;
+          const int32_t cy = __float_as_int(__fadd_rd(__fmaf_rn(kf, by, ay), 12582912.0f)) - 0x4B400000;
+          const bool ok = k + u * G < k_end && (uint32_t)cx < (uint32_t)W && (uint32_t)cy < (uint32_t)H &&
+                          !(cx == rix && cy == riy);
           pl[u] = cy * W + cx;  // logical index
           zz[u] = __fmaf_rn(kf, bz, az);
           th[u] = ok ? __ldg(thr + pl[u]) : __int_as_float(0xff800000);
+          kf = __fadd_rn(kf, (float)G);
         }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) any |= zz[u] < th[u];
+        if (!any) continue;  // the common case: no sample of these four is below its cell
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           if (!(zz[u] < th[u])) continue;  // also skips the samples that are not taken (th = -inf)
@@ -166,8 +175,16 @@ __global__ void __launch_bounds__(kRayThreads) k_ray(const BatchDev* __restrict_
     }
     __syncwarp();
   }
-  if (mc.map >= 0) add_counter(b, mc, mc.map, stat_idx, 1, &samples);
-  flush_counters(b, mc, stat_idx, 1);
+  // samples per map: a warp sum when the warp's lanes end on one map, else per
+  // lane (no block barrier: warps of a block finish at different times)
+  const int m0 = __shfl_sync(0xffffffffu, smap, 0);
+  if (__all_sync(0xffffffffu, smap == m0 || samples == 0)) {
+    unsigned long long t = samples;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0 && m0 >= 0 && t) atomicAdd(&b.maps[m0].ctl->stats[kStRaySamples], t);
+  } else if (smap >= 0 && samples) {
+    atomicAdd(&b.maps[smap].ctl->stats[kStRaySamples], samples);
+  }
 }
 
 constexpr int kClearThreads = 256;

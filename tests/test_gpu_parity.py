@@ -228,6 +228,9 @@ def test_invalid_arguments(em):
     assert e.value.code == em.EM_ERR_INVALID_ARG
     with pytest.raises(em.EMError):
         em.Map(em.Params(var_min=0.0))
+    with pytest.raises(em.EMError) as e:  # a side longer than 2^22 cells
+        em.Map(em.Params(width=(1 << 22) + 1, height=1))
+    assert e.value.code == em.EM_ERR_INVALID_ARG
     g = gpu_map(em, dict(width=10, height=10), trace=False)
     pts = dev(np.zeros((10, 3), np.float32))
     with pytest.raises(em.EMError) as e:
