@@ -62,7 +62,11 @@ N_ROBOTS = 32
 RATE_HZ = 2000.0
 BUDGET = 40 << 30
 L2_FLUSH_BYTES = 256 << 20
-RAY_OPS_PER_SAMPLE = 22  # float / integer / compare / load operations per ray sample in the k_ray march
+# Lane operations per ray sample in the k_ray march as written: 1 float step of the
+# sample index; 2 x (FMA + round-down add + integer subtract) for the cell x, y; 2 for
+# the k-range test; 4 compares (box, own cell) and 3 logical combines; 1 IMAD (index);
+# 1 FMA (sample height); 1 predicated gather and 1 select; 1 compare and 1 OR (flag).
+RAY_OPS_PER_SAMPLE = 22
 
 
 def f32params(P):
@@ -146,12 +150,12 @@ def file_hash(*paths) -> str:
 
 
 CSRC = "paper_2204_12876_gb300/csrc/"
-KERNEL_SOURCES = {"ray": [CSRC + "k_ray.cu", CSRC + "em_point.cuh"],
-                  "count": [CSRC + "k_sort.cu", CSRC + "em_point.cuh"],
-                  "scatter": [CSRC + "k_sort.cu", CSRC + "em_point.cuh"],
-                  "alloc": [CSRC + "k_sort.cu"],
-                  "fuse": [CSRC + "k_fuse.cu"],
-                  "clear": [CSRC + "k_ray.cu"]}
+KERNEL_SOURCES = {"ray": [CSRC + "k_ray.cu", CSRC + "em_point.cuh", CSRC + "em_internal.cuh"],
+                  "count": [CSRC + "k_sort.cu", CSRC + "em_point.cuh", CSRC + "em_internal.cuh"],
+                  "scatter": [CSRC + "k_sort.cu", CSRC + "em_point.cuh", CSRC + "em_internal.cuh"],
+                  "alloc": [CSRC + "k_sort.cu", CSRC + "em_internal.cuh"],
+                  "fuse": [CSRC + "k_fuse.cu", CSRC + "em_point.cuh", CSRC + "em_internal.cuh"],
+                  "clear": [CSRC + "k_ray.cu", CSRC + "em_internal.cuh"]}
 
 
 def ncu_traffic(kernel: str, workload: str):

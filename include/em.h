@@ -277,6 +277,11 @@ typedef struct em_server em_server;
 
 enum { EM_SERVE_BATCHED = 0, EM_SERVE_PLAIN = 1 };
 
+/* Admission accounting: each admitted request holds this many bytes per point
+ * (one grouped record per point), and each batch stream a workspace of
+ * max_batch_points records. */
+enum { EM_SERVE_RECORD_BYTES = 16 };
+
 typedef struct em_server_cfg {
   int32_t device;
   int64_t budget_bytes;     /* device bytes for resident maps + batch workspaces + admitted requests */

@@ -50,7 +50,8 @@ struct Flight {
   int64_t bytes = 0;
 };
 
-constexpr int64_t kRecordBytes = 8;  // one (z, sigma_p^2) record per point
+constexpr int64_t kRecordBytes = EM_SERVE_RECORD_BYTES;  // one grouped record per point
+static_assert(kRecordBytes == sizeof(float4), "record size");
 
 }  // namespace
 

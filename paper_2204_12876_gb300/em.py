@@ -382,6 +382,7 @@ class Batch:
 
 
 SERVE_BATCHED, SERVE_PLAIN = 0, 1
+SERVE_RECORD_BYTES = 16  # admission accounting per point (EM_SERVE_RECORD_BYTES)
 
 
 class _ServerCfg(ctypes.Structure):

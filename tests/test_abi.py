@@ -51,8 +51,19 @@ def test_status_strings_without_gpu(lib_path):
 def test_struct_layout_matches_header(tmp_path, lib_path):
     from paper_2204_12876_gb300 import em
     src = tmp_path / "layout.c"
-    structs = {"em_params": em._Params, "em_cloud": em._Cloud, "em_info": em._Info, "em_stats": em._Stats}
+    structs = {"em_params": em._Params, "em_cloud": em._Cloud, "em_info": em._Info, "em_stats": em._Stats,
+               "em_tuning": em._Tuning, "em_server_cfg": em._ServerCfg, "em_result": em._Result,
+               "em_server_stats": em._ServerStats}
+    consts = {"EM_OK": em.EM_OK, "EM_ERR_INVALID_ARG": em.EM_ERR_INVALID_ARG, "EM_ERR_OOM": em.EM_ERR_OOM,
+              "EM_ERR_CUDA": em.EM_ERR_CUDA, "EM_ERR_TIMEOUT": em.EM_ERR_TIMEOUT,
+              "EM_ERR_REJECTED": em.EM_ERR_REJECTED, "EM_ERR_BUSY": em.EM_ERR_BUSY,
+              "EM_ERR_CAPACITY": em.EM_ERR_CAPACITY, "EM_SERVE_BATCHED": em.SERVE_BATCHED,
+              "EM_SERVE_PLAIN": em.SERVE_PLAIN, "EM_SERVE_RECORD_BYTES": em.SERVE_RECORD_BYTES,
+              "EM_BATCH_GRAPH": em.BATCH_GRAPH, "EM_NOALLOC_MAX_CELLS": em.NOALLOC_MAX_CELLS,
+              "EM_NOALLOC_MAX_POINTS": em.NOALLOC_MAX_POINTS, "EM_NOALLOC_MAX_CLOUDS": em.NOALLOC_MAX_CLOUDS}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "em.h"', "int main(void) {"]
+    for cname in consts:
+        lines.append(f'printf("{cname} %lld\\n", (long long){cname});')
     for cname, py in structs.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
         for f, _ in py._fields_:
@@ -63,6 +74,8 @@ def test_struct_layout_matches_header(tmp_path, lib_path):
     subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
     got = dict(line.rsplit(" ", 1) for line in out if line)
+    for cname, v in consts.items():
+        assert int(got[cname]) == v, cname
     for cname, py in structs.items():
         assert int(got[f"{cname} size"]) == ctypes.sizeof(py), cname
         for f, _ in py._fields_:

@@ -73,7 +73,7 @@ def test_admission_by_budget(em):
         probe.add_map(em.Params(width=s, height=s, **BASE))
     base = probe.stats()["bytes_in_use"]  # batch workspaces + resident maps
     probe.close()
-    budget = base + 40_000 * 8  # room for ~40k records in flight
+    budget = base + 40_000 * em.SERVE_RECORD_BYTES  # room for ~40k records in flight
     srv = em.Server(budget_bytes=budget, n_streams=2, max_batch_maps=4, max_batch_points=50_000)
     ids = [srv.add_map(em.Params(width=s, height=s, **BASE)) for s in SIDES]
     tickets = [srv.submit(ids[j], [(p, q)]) for j, p, q in reqs]
