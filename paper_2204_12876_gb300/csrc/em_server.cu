@@ -60,6 +60,7 @@ struct em_server {
   std::vector<em_map*> maps;
   std::vector<int64_t> map_bytes;
   std::vector<char> map_busy;
+  std::vector<char> blocked;  // batch-builder scratch, one flag per map
   std::vector<cudaStream_t> streams;
   std::vector<em_batch*> batches;
   std::vector<Flight> flights;            // batched: one per stream; plain: grows as needed
@@ -160,15 +161,19 @@ bool worker_pass(em_server* s, std::unique_lock<std::mutex>& lk) {
     for (size_t si = 0; si < s->streams.size(); ++si) {
       Flight& f = s->flights[si];
       if (f.busy || s->admitted.empty()) continue;
-      // distinct idle maps in arrival order, within the batch limits
+      // distinct idle maps in arrival order, within the batch limits; a map whose
+      // earlier request is not taken (the batch is full) takes no later one, so
+      // each map's updates stay in arrival order
       std::vector<uint64_t> take;
       std::vector<int32_t> bmaps;
       int64_t pts = 0;
+      s->blocked.assign(s->maps.size(), 0);
       for (auto it = s->admitted.begin(); it != s->admitted.end();) {
         Request& r = s->reqs[*it];
-        bool dup = s->map_busy[r.map_id] != 0;
-        for (int32_t m : bmaps) dup |= (m == r.map_id);
-        if (dup || (int32_t)bmaps.size() >= s->cfg.max_batch_maps || pts + r.points > s->cfg.max_batch_points) {
+        const bool skip = s->map_busy[r.map_id] != 0 || s->blocked[r.map_id] != 0 ||
+                          (int32_t)bmaps.size() >= s->cfg.max_batch_maps || pts + r.points > s->cfg.max_batch_points;
+        s->blocked[r.map_id] = 1;  // at most one request per map, the earliest
+        if (skip) {
           ++it;
           continue;
         }

@@ -66,6 +66,36 @@ def test_served_equals_alone(em, mode, streams):
     srv.close()
 
 
+def test_map_order_kept_when_a_batch_is_full(em):
+    """A map's earlier request that does not fit the batch holds back its later
+    ones: the map still receives its updates in arrival order."""
+    half = 0.5 * 120 * 0.04
+    clouds = [synth.scattered_cloud(900 + k, n, half) for k, n in enumerate((1_000, 50_000, 60_000, 1_000))]
+    alone_a = em.Map(em.Params(width=120, height=120, **BASE))
+    for pts, pose in clouds[2:]:
+        alone_a.update(dev(pts), pose)
+    torch.cuda.synchronize()
+    srv = em.Server(budget_bytes=1 << 30, n_streams=1, max_batch_maps=4, max_batch_points=100_000)
+    ia, ib, ic = (srv.add_map(em.Params(width=120, height=120, **BASE)) for _ in range(3))
+    # a first request on map C holds the only stream (its points wait on a timed
+    # kernel) while B (50k), A (60k) and A (1k) queue up behind it; the next batch
+    # takes B, cannot fit A's 60k next to it, and must not take A's 1k either
+    gate = torch.cuda.Event()
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        torch.cuda._sleep(20_000_000)
+        gate.record(side)
+    tickets = [srv.submit(ic, [(dev(clouds[0][0]), clouds[0][1])], ready=gate)]
+    tickets += [srv.submit(ib, [(dev(clouds[1][0]), clouds[1][1])])]
+    tickets += [srv.submit(ia, [(dev(p), q)]) for p, q in clouds[2:]]
+    for t in tickets:
+        assert srv.wait(t)["status"] == 0
+    a, b = alone_a.state(), srv.map(ia).state()
+    for k in ("h", "var", "t_last"):
+        assert np.array_equal(a[k], b[k], equal_nan=True), k
+    srv.close()
+
+
 def test_admission_by_budget(em):
     reqs = workload(n_req=30, seed=6)
     probe = em.Server(budget_bytes=1 << 30, n_streams=2, max_batch_maps=4, max_batch_points=50_000)
