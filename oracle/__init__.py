@@ -21,7 +21,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "em_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "liboracle_em.so")
 
-NORMALS, SMOOTH, INPAINT = 1, 2, 4
+NORMALS, SMOOTH, INPAINT, MEDIAN, GAUSS = 1, 2, 4, 8, 16
 ST_NONFINITE, ST_RANGE, ST_OUTSIDE, ST_ACCEPT, ST_REJECT, ST_WALL = range(6)
 PF_BIN, PF_GATE, PF_WALL, PF_RANGE = 1, 2, 4, 8
 CF_VALUE, CF_MARK = 1, 2

@@ -21,7 +21,7 @@
  *   4. ray casting against the snapshot (Section II-E, Eq. 3, Eq. 4)
  *   5. removal of penetrated cells that were not updated recently
  *   6. optional per-cell filters on the updated map: normals (Section II-A),
- *      smoothing and in-painting (Section II-I)
+ *      smoothing (box, median or Gaussian) and in-painting (Section II-I)
  * The map shift (robot-centric map, Section I) is a physical array copy.
  *
  * Readings of passages the paper leaves open (all listed in the design notes):
@@ -50,6 +50,8 @@
 #define ORC_NORMALS 1u
 #define ORC_SMOOTH 2u
 #define ORC_INPAINT 4u
+#define ORC_MEDIAN 8u
+#define ORC_GAUSS 16u
 
 /* per-point status codes of the trace */
 enum { ST_NONFINITE = 0, ST_RANGE = 1, ST_OUTSIDE = 2, ST_ACCEPT = 3, ST_REJECT = 4, ST_WALL = 5 };
@@ -328,6 +330,64 @@ static void compute_smooth(orc_map* m) {
           ++n;
         }
       m->smooth[c] = s / n;
+    }
+}
+
+/* 5x5 median over the valid cells of the window, for valid cells only
+ * (median smoothing, Section II-I): the lower median, i.e. the element of rank
+ * floor((n - 1) / 2) of the n valid heights sorted ascending. */
+static void compute_median(orc_map* m) {
+  const int W = m->p.width, H = m->p.height;
+  for (int iy = 0; iy < H; ++iy)
+    for (int ix = 0; ix < W; ++ix) {
+      int64_t c = (int64_t)iy * W + ix;
+      m->smooth[c] = NAN;
+      if (!isfinite(m->var[c])) continue;
+      double v[25];
+      int n = 0;
+      for (int dy = -2; dy <= 2; ++dy)
+        for (int dx = -2; dx <= 2; ++dx) {
+          int jx = ix + dx, jy = iy + dy;
+          if (!in_map(m, jx, jy)) continue;
+          int64_t k = (int64_t)jy * W + jx;
+          if (!isfinite(m->var[k])) continue;
+          v[n++] = m->h[k];
+        }
+      for (int a = 1; a < n; ++a) { /* insertion sort */
+        double x = v[a];
+        int b = a - 1;
+        while (b >= 0 && v[b] > x) {
+          v[b + 1] = v[b];
+          --b;
+        }
+        v[b + 1] = x;
+      }
+      m->smooth[c] = v[(n - 1) / 2];
+    }
+}
+
+/* 5x5 Gaussian over the valid cells of the window, for valid cells only
+ * (Gaussian smoothing, Section II-I): weights exp(-(dx^2 + dy^2) / (2 s^2))
+ * with s = 1 cell, normalised over the valid cells of the window. */
+static void compute_gauss(orc_map* m) {
+  const int W = m->p.width, H = m->p.height;
+  for (int iy = 0; iy < H; ++iy)
+    for (int ix = 0; ix < W; ++ix) {
+      int64_t c = (int64_t)iy * W + ix;
+      m->smooth[c] = NAN;
+      if (!isfinite(m->var[c])) continue;
+      double s = 0.0, ws = 0.0;
+      for (int dy = -2; dy <= 2; ++dy)
+        for (int dx = -2; dx <= 2; ++dx) {
+          int jx = ix + dx, jy = iy + dy;
+          if (!in_map(m, jx, jy)) continue;
+          int64_t k = (int64_t)jy * W + jx;
+          if (!isfinite(m->var[k])) continue;
+          double w = exp(-0.5 * (double)(dx * dx + dy * dy));
+          s += w * m->h[k];
+          ws += w;
+        }
+      m->smooth[c] = s / ws;
     }
 }
 
@@ -621,6 +681,8 @@ int orc_update(orc_map* m, const orc_cloud* clouds, int32_t ncloud, orc_trace* t
   /* 6. per-cell filters on the updated map */
   if (p->flags & ORC_NORMALS) compute_normals(m);
   if (p->flags & ORC_SMOOTH) compute_smooth(m);
+  if (p->flags & ORC_MEDIAN) compute_median(m);
+  if (p->flags & ORC_GAUSS) compute_gauss(m);
   if (p->flags & ORC_INPAINT) compute_inpaint(m);
   m->t_now = t_now;
 
@@ -687,5 +749,7 @@ void orc_shift(orc_map* m, int32_t dx, int32_t dy) {
 void orc_filters(orc_map* m, uint32_t which) {
   if (which & ORC_NORMALS) compute_normals(m);
   if (which & ORC_SMOOTH) compute_smooth(m);
+  if (which & ORC_MEDIAN) compute_median(m);
+  if (which & ORC_GAUSS) compute_gauss(m);
   if (which & ORC_INPAINT) compute_inpaint(m);
 }

@@ -363,6 +363,61 @@ def test_smoothing(oracle_mod):
     assert s["smooth"][0, 0] == pytest.approx(np.mean([0, 1, 2, 5, 7, 10, 11, 12]))
 
 
+def test_median_smoothing(oracle_mod):
+    """5x5 lower median over the valid cells (Section II-I, median filter)."""
+    s = _field(oracle_mod, np.full((7, 9), -0.21), oracle_mod.MEDIAN)
+    assert np.all(s["smooth"] == -0.21)
+    h = np.arange(25, dtype=float).reshape(5, 5)
+    s = _field(oracle_mod, h, oracle_mod.MEDIAN)
+    assert s["smooth"][2, 2] == 12.0                       # 25 values 0..24
+    assert s["smooth"][0, 0] == 6.0                        # {0,1,2,5,6,7,10,11,12}
+    h[1, 1] = np.nan
+    s = _field(oracle_mod, h, oracle_mod.MEDIAN)
+    assert np.isnan(s["smooth"][1, 1])
+    assert s["smooth"][0, 0] == 5.0                        # 8 values: the lower of 5 and 7
+    spike = np.full((9, 9), 0.1)
+    spike[4, 4] = 3.0                                      # a lone spike is rejected
+    assert _field(oracle_mod, spike, oracle_mod.MEDIAN)["smooth"][4, 4] == 0.1
+    # every cell against numpy's lower median of the same window
+    rng = np.random.default_rng(11)
+    f = rng.normal(0.0, 0.3, (12, 13))
+    f[rng.random(f.shape) < 0.2] = np.nan
+    out = _field(oracle_mod, f, oracle_mod.MEDIAN)["smooth"]
+    for iy in range(f.shape[0]):
+        for ix in range(f.shape[1]):
+            if np.isnan(f[iy, ix]):
+                assert np.isnan(out[iy, ix])
+                continue
+            win = f[max(0, iy - 2):iy + 3, max(0, ix - 2):ix + 3]
+            assert out[iy, ix] == np.quantile(win[~np.isnan(win)], 0.5, method="lower")
+
+
+def test_gaussian_smoothing(oracle_mod):
+    """5x5 Gaussian, sigma = 1 cell, weights renormalised over the valid cells
+    (Section II-I, Gaussian filter)."""
+    s = _field(oracle_mod, np.full((7, 9), 0.37), oracle_mod.GAUSS)
+    assert np.allclose(s["smooth"], 0.37, atol=1e-15)
+    # a symmetric kernel keeps a plane exactly where the whole window is valid
+    a, b, c = 0.3, -0.2, 0.1
+    X, Y = np.meshgrid(np.arange(9) * 0.04, np.arange(9) * 0.04)
+    plane = a * X + b * Y + c
+    s = _field(oracle_mod, plane, oracle_mod.GAUSS)
+    assert np.allclose(s["smooth"][2:7, 2:7], plane[2:7, 2:7], atol=1e-12, rtol=0)
+    # two valid cells: weights 1 and exp(-1/2)
+    h = np.full((5, 5), np.nan)
+    h[2, 2], h[2, 3] = 0.0, 1.0
+    s = _field(oracle_mod, h, oracle_mod.GAUSS)
+    w = math.exp(-0.5)
+    assert s["smooth"][2, 2] == pytest.approx(w / (1.0 + w), abs=1e-15)
+    # interior cells against scipy's separable Gaussian (same 5-tap kernel)
+    nd = pytest.importorskip("scipy.ndimage")
+    rng = np.random.default_rng(12)
+    f = rng.normal(0.0, 0.3, (14, 15))
+    ref = nd.gaussian_filter(f, sigma=1.0, truncate=2.0, mode="nearest")
+    out = _field(oracle_mod, f, oracle_mod.GAUSS)["smooth"]
+    assert np.allclose(out[2:-2, 2:-2], ref[2:-2, 2:-2], atol=1e-12, rtol=0)
+
+
 def test_inpainting(oracle_mod):
     rng = np.random.default_rng(2)
     h = rng.uniform(0.0, 1.0, (16, 16))
