@@ -50,6 +50,11 @@ enum {
   EM_F_NORMALS = 1u << 0, /* keep the per-cell normal layer (Section II-A, "normal calculation") */
   EM_F_SMOOTH = 1u << 1,  /* keep a 5x5 box-smoothed elevation layer (Section II-I) */
   EM_F_INPAINT = 1u << 2, /* keep a minimum-in-painted elevation layer (Section II-I) */
+  EM_F_MEDIAN = 1u << 3,  /* the smoothed layer holds the 5x5 median instead (lower median of the
+                             window's valid heights; Section II-I) */
+  EM_F_GAUSS = 1u << 4,   /* the smoothed layer holds a 5x5 Gaussian instead (sigma = 1 cell, weights
+                             renormalised over the window's valid cells; Section II-I).  At most one
+                             of EM_F_SMOOTH, EM_F_MEDIAN, EM_F_GAUSS may be set. */
   EM_F_TRACE = 1u << 8    /* record per-point cells and decisions of the last update (testing) */
 };
 

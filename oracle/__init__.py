@@ -21,7 +21,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "em_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "liboracle_em.so")
 
-NORMALS, SMOOTH, INPAINT, MEDIAN, GAUSS = 1, 2, 4, 8, 16
+NORMALS, SMOOTH, INPAINT, MEDIAN, GAUSS, UPPER = 1, 2, 4, 8, 16, 32
 ST_NONFINITE, ST_RANGE, ST_OUTSIDE, ST_ACCEPT, ST_REJECT, ST_WALL = range(6)
 PF_BIN, PF_GATE, PF_WALL, PF_RANGE = 1, 2, 4, 8
 CF_VALUE, CF_MARK = 1, 2
@@ -86,6 +86,8 @@ def _load():
         lib.orc_update.argtypes = [vp, ctypes.POINTER(_Cloud), ctypes.c_int32, ctypes.POINTER(_Trace)]
         lib.orc_shift.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
         lib.orc_filters.argtypes = [vp, ctypes.c_uint32]
+        lib.orc_get_upper.argtypes = [vp, vp]
+        lib.orc_set_upper.argtypes = [vp, vp]
         _lib = lib
     return _lib
 
@@ -167,7 +169,15 @@ class OracleMap:
         out["t_last"] = np.empty((H, W), np.int32)
         self._lib.orc_get(self._h, _ptr(out["h"]), _ptr(out["var"]), _ptr(out["t_last"]), _ptr(out["nx"]),
                           _ptr(out["ny"]), _ptr(out["nz"]), _ptr(out["smooth"]), _ptr(out["inpaint"]))
+        out["upper"] = np.empty((H, W), np.float64)
+        self._lib.orc_get_upper(self._h, _ptr(out["upper"]))
         return out
+
+    def set_upper(self, upper):
+        a = np.ascontiguousarray(upper, dtype=np.float64).reshape(-1)
+        if a.size != self.params.width * self.params.height:
+            raise ValueError("layer size mismatch")
+        self._lib.orc_set_upper(self._h, _ptr(a))
 
     def set_state(self, h=None, var=None, t_last=None, nx=None, ny=None, nz=None, t_now=None, shift=None):
         """Overwrite layers (None keeps a layer).  Empty cells are those with non-finite variance."""

@@ -18,8 +18,11 @@
  *   3. per cell, its points in input order: wall rule (Section II-C, last
  *      paragraph), Mahalanobis outlier gate against the snapshot (Section
  *      II-C), then Eq. 1 and Eq. 2 applied point after point
- *   4. ray casting against the snapshot (Section II-E, Eq. 3, Eq. 4)
- *   5. removal of penetrated cells that were not updated recently
+ *   4. ray casting against the snapshot (Section II-E, Eq. 3, Eq. 4); with the
+ *      upper-bound layer (Section II-F), samples in cells that are empty in the
+ *      snapshot lower the cell's bound to the sample height
+ *   5. removal of penetrated cells that were not updated recently; cells that
+ *      hold an estimate after the update have no upper bound
  *   6. optional per-cell filters on the updated map: normals (Section II-A),
  *      smoothing (box, median or Gaussian) and in-painting (Section II-I)
  * The map shift (robot-centric map, Section I) is a physical array copy.
@@ -52,6 +55,7 @@
 #define ORC_INPAINT 4u
 #define ORC_MEDIAN 8u
 #define ORC_GAUSS 16u
+#define ORC_UPPER 32u
 
 /* per-point status codes of the trace */
 enum { ST_NONFINITE = 0, ST_RANGE = 1, ST_OUTSIDE = 2, ST_ACCEPT = 3, ST_REJECT = 4, ST_WALL = 5 };
@@ -115,6 +119,7 @@ typedef struct orc_map {
   double* nz;
   double* smooth;
   double* inpaint;
+  double* upper; /* upper bound of the ground height (Section II-F), +inf where none */
 } orc_map;
 
 static double* alloc_fill(int64_t n, double v) {
@@ -130,6 +135,7 @@ static void clear_cell(orc_map* m, int64_t c) {
   m->nx[c] = m->ny[c] = m->nz[c] = NAN;
   m->smooth[c] = NAN;
   m->inpaint[c] = NAN;
+  m->upper[c] = INFINITY;
 }
 
 orc_map* orc_create(const orc_params* p) {
@@ -145,13 +151,14 @@ orc_map* orc_create(const orc_params* p) {
   m->nz = alloc_fill(nc, NAN);
   m->smooth = alloc_fill(nc, NAN);
   m->inpaint = alloc_fill(nc, NAN);
+  m->upper = alloc_fill(nc, INFINITY);
   return m;
 }
 
 void orc_destroy(orc_map* m) {
   if (!m) return;
   free(m->h); free(m->var); free(m->t_last);
-  free(m->nx); free(m->ny); free(m->nz); free(m->smooth); free(m->inpaint);
+  free(m->nx); free(m->ny); free(m->nz); free(m->smooth); free(m->inpaint); free(m->upper);
   free(m);
 }
 
@@ -184,6 +191,16 @@ void orc_get(const orc_map* m, double* h, double* var, int32_t* t_last, double* 
   copy_out(nz, m->nz, nc);
   copy_out(smooth, m->smooth, nc);
   copy_out(inpaint, m->inpaint, nc);
+}
+
+/* The upper-bound layer (logical row-major), read and written on its own. */
+void orc_get_upper(const orc_map* m, double* upper) {
+  copy_out(upper, m->upper, (int64_t)m->p.width * m->p.height);
+}
+
+void orc_set_upper(orc_map* m, const double* upper) {
+  int64_t nc = (int64_t)m->p.width * m->p.height;
+  for (int64_t c = 0; c < nc; ++c) m->upper[c] = upper[c];
 }
 
 /* Overwrite the state.  A cell is empty iff its variance is not finite; such a
@@ -450,7 +467,7 @@ static void compute_inpaint(orc_map* m) {
 /* Walk one ray against the snapshot.  mode 0: mark penetrated cells (Eq. 3
  * with the Eq. 4 guard); mode 1: only flag every cell the ray may touch as
  * mark-marginal (used when the ray itself is marginal). */
-static void walk_ray(const orc_map* m, const pt_info* pi, const float* pose, const double* h0,
+static void walk_ray(orc_map* m, const pt_info* pi, const float* pose, const double* h0,
                      const double* ve0, const double* nx0, const double* ny0, const double* nz0,
                      uint8_t* mark, orc_trace* tr, int mode, double x0, double y0) {
   const orc_params* p = &m->p;
@@ -502,6 +519,9 @@ static void walk_ray(const orc_map* m, const pt_info* pi, const float* pose, con
         if (below && u > 0 && fabs(dot - p->cleanup_normal_thresh) < ab + 8.0 * u) marginal = 1;
       }
       if (mode == 0 && exists && below && guard_ok) mark[c] = 1;
+    } else if (mode == 0 && exists && (p->flags & ORC_UPPER)) {
+      /* a ray through an empty cell: its ground is not above the ray (Section II-F) */
+      if (sz < m->upper[c]) m->upper[c] = sz;
     }
     if (marginal && cflags) flag_block(m, cflags, cx, cy, 1, CF_MARK);
     if (!exists) break;
@@ -677,6 +697,9 @@ int orc_update(orc_map* m, const orc_cloud* clouds, int32_t ncloud, orc_trace* t
     if (tr && tr->cleared) tr->cleared[c] = 1;
     ++n_clr;
   }
+  if (p->flags & ORC_UPPER)
+    for (int64_t c = 0; c < nc; ++c)
+      if (isfinite(m->var[c])) m->upper[c] = INFINITY; /* observed: no bound needed */
 
   /* 6. per-cell filters on the updated map */
   if (p->flags & ORC_NORMALS) compute_normals(m);
@@ -723,6 +746,7 @@ void orc_shift(orc_map* m, int32_t dx, int32_t dy) {
   const int64_t nc = (int64_t)W * H;
   orc_map* old = orc_create(&m->p);
   orc_get(m, old->h, old->var, old->t_last, old->nx, old->ny, old->nz, old->smooth, old->inpaint);
+  orc_get_upper(m, old->upper);
   for (int iy = 0; iy < H; ++iy)
     for (int ix = 0; ix < W; ++ix) {
       int64_t c = (int64_t)iy * W + ix;
@@ -737,6 +761,7 @@ void orc_shift(orc_map* m, int32_t dx, int32_t dy) {
       m->nz[c] = old->nz[s];
       m->smooth[c] = old->smooth[s];
       m->inpaint[c] = old->inpaint[s];
+      m->upper[c] = old->upper[s];
     }
   (void)nc;
   m->shift_x += dx;

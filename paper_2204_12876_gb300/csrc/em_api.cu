@@ -157,6 +157,8 @@ bool params_ok(const em_params* p) {
   if (!(p->max_range >= p->min_range) || std::isnan(p->max_range)) return false;
   if (p->outlier_variance < 0.f || p->time_variance < 0.f || p->ray_step < 0.f) return false;
   if (p->wall_num_thresh < 0 || p->cleanup_min_age < 0) return false;
+  const uint32_t sm = p->flags & (EM_F_SMOOTH | EM_F_MEDIAN | EM_F_GAUSS);
+  if (sm & (sm - 1)) return false;  // one smoothing filter at most
   return true;
 }
 
@@ -387,7 +389,7 @@ int em_create(const em_params* params, int device, em_map** out) {
   if (e == cudaSuccess) e = dev_alloc(&(ptr), (n), &tot);
   EM_ALLOC(m->h, nc) EM_ALLOC(m->var, nc) EM_ALLOC(m->t_last, nc)
   if (normals) { EM_ALLOC(m->nx, nc) EM_ALLOC(m->ny, nc) EM_ALLOC(m->nz, nc) }
-  if (params->flags & EM_F_SMOOTH) { EM_ALLOC(m->smooth, nc) }
+  if (params->flags & (EM_F_SMOOTH | EM_F_MEDIAN | EM_F_GAUSS)) { EM_ALLOC(m->smooth, nc) }
   if (params->flags & EM_F_INPAINT) { EM_ALLOC(m->inpaint, nc) }
   EM_ALLOC(m->mark, (nc + 31) / 32) EM_ALLOC(m->thr, nc) EM_ALLOC(m->cnt, nc) EM_ALLOC(m->cell_seg, nc)
   EM_ALLOC(m->ctl, 1) EM_ALLOC(m->bctl, 1)
@@ -465,7 +467,7 @@ static int update_impl(em_map* m, const em_cloud* clouds, int32_t n_clouds, cuda
   EM_TRY(timed(m, EM_PROF_CLEAR, s, [&] { return launch_clear(bd, ncell, s); }), "k_clear");
   if (m->p.flags & EM_F_NORMALS)
     EM_TRY(timed(m, EM_PROF_NORMALS, s, [&] { return launch_normals(bd, ncell, s); }), "k_normals");
-  if (m->p.flags & EM_F_SMOOTH)
+  if (m->p.flags & (EM_F_SMOOTH | EM_F_MEDIAN | EM_F_GAUSS))
     EM_TRY(timed(m, EM_PROF_SMOOTH, s, [&] { return launch_smooth(bd, ncell, s); }), "k_smooth");
   if (m->p.flags & EM_F_INPAINT)
     EM_TRY(timed(m, EM_PROF_INPAINT, s, [&] { return launch_inpaint(bd, ncell, s); }), "k_inpaint");

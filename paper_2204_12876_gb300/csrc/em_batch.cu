@@ -123,7 +123,7 @@ cudaError_t launch_sequence(const BatchDev* bd, int64_t grid_points, int64_t gri
   if (e == cudaSuccess) e = timed(prof, EM_PROF_CLEAR, s, [&] { return launch_clear(bd, grid_cells, s); });
   if (e == cudaSuccess && (k.stencils & EM_F_NORMALS))
     e = timed(prof, EM_PROF_NORMALS, s, [&] { return launch_normals(bd, grid_cells, s); });
-  if (e == cudaSuccess && (k.stencils & EM_F_SMOOTH))
+  if (e == cudaSuccess && (k.stencils & (EM_F_SMOOTH | EM_F_MEDIAN | EM_F_GAUSS)))
     e = timed(prof, EM_PROF_SMOOTH, s, [&] { return launch_smooth(bd, grid_cells, s); });
   if (e == cudaSuccess && (k.stencils & EM_F_INPAINT))
     e = timed(prof, EM_PROF_INPAINT, s, [&] { return launch_inpaint(bd, grid_cells, s); });
@@ -188,7 +188,7 @@ int prepare(em_batch* b, em_map* const* maps, const em_cloud* clouds, int32_t co
     md[u].cell_begin = cells;
     cells += pad_tile(map_cells(b->uniq[u]));
     key.ray |= md[u].ray_step > 0.f;
-    key.stencils |= map_flags(b->uniq[u]) & (EM_F_NORMALS | EM_F_SMOOTH | EM_F_INPAINT);
+    key.stencils |= map_flags(b->uniq[u]) & (EM_F_NORMALS | EM_F_SMOOTH | EM_F_MEDIAN | EM_F_GAUSS | EM_F_INPAINT);
   }
   // clouds ordered by map (stable), so each map's points are contiguous
   int ci = 0;

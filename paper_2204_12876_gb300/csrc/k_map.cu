@@ -69,31 +69,72 @@ __global__ void __launch_bounds__(kMapThreads) k_normals(const BatchDev* __restr
   });
 }
 
+// 5x5 smoothing of valid cells over the valid cells of the window (Section
+// II-I): the box mean (EM_F_SMOOTH), the lower median (EM_F_MEDIAN: the value of
+// rank floor((n - 1) / 2) of the n valid heights, found by counting ranks in
+// registers) or a Gaussian with sigma = 1 cell renormalised over the valid
+// cells (EM_F_GAUSS).  Sums run in a fixed window order.
 __global__ void __launch_bounds__(kMapThreads) k_smooth(const BatchDev* __restrict__ bp) {
   const BatchDev& b = *bp;
   for_each_tile(b, [&](const MapDev& m, int, int32_t p0, int32_t count) {
   if (!m.smooth) return;
+  const int mode = (m.flags & EM_F_MEDIAN) ? 1 : (m.flags & EM_F_GAUSS) ? 2 : 0;
   for (int32_t i = threadIdx.x; i < count; i += kMapThreads) {
     const int32_t p = p0 + i;
     int32_t lx, ly;
     logical_of(m, p, lx, ly);
     float out = qnan();
     if (valid_at(m, p)) {
-      float s = 0.f;
+      float v[25];  // the window's heights, +inf where not valid
       int n = 0;
+#pragma unroll
       for (int dy = -2; dy <= 2; ++dy) {
-        const int32_t jy = ly + dy;
-        if (jy < 0 || jy >= m.H) continue;
+#pragma unroll
         for (int dx = -2; dx <= 2; ++dx) {
-          const int32_t jx = lx + dx;
-          if (jx < 0 || jx >= m.W) continue;
-          const int32_t q = phys_index(m, jx, jy);
-          if (!valid_at(m, q)) continue;
-          s += m.h[q];
-          ++n;
+          const int32_t jx = lx + dx, jy = ly + dy;
+          float h = pinf();
+          if (jx >= 0 && jx < m.W && jy >= 0 && jy < m.H) {
+            const int32_t q = phys_index(m, jx, jy);
+            if (valid_at(m, q)) {
+              h = m.h[q];
+              ++n;
+            }
+          }
+          v[(dy + 2) * 5 + dx + 2] = h;
         }
       }
-      out = s / (float)n;
+      if (mode == 0) {
+        float s = 0.f;
+#pragma unroll
+        for (int k = 0; k < 25; ++k)
+          if (v[k] != pinf()) s += v[k];
+        out = s / (float)n;
+      } else if (mode == 1) {
+        // rank of v[k] = #{j : v[j] < v[k]} + #{j < k : v[j] == v[k]}; the invalid
+        // (+inf) entries rank last, so rank (n - 1) / 2 is the lower median
+        const int want = (n - 1) / 2;
+#pragma unroll
+        for (int k = 0; k < 25; ++k) {
+          int rank = 0;
+#pragma unroll
+          for (int j = 0; j < 25; ++j) rank += (v[j] < v[k]) || (j < k && v[j] == v[k]);
+          if (rank == want) out = v[k];
+        }
+      } else {
+        float s = 0.f, ws = 0.f;
+#pragma unroll
+        for (int dy = -2; dy <= 2; ++dy) {
+#pragma unroll
+          for (int dx = -2; dx <= 2; ++dx) {
+            const float h = v[(dy + 2) * 5 + dx + 2];
+            if (h == pinf()) continue;
+            const float w = expf(-0.5f * (float)(dx * dx + dy * dy));
+            s = __fmaf_rn(w, h, s);
+            ws += w;
+          }
+        }
+        out = __fdiv_rn(s, ws);
+      }
     }
     m.smooth[p] = out;
   }

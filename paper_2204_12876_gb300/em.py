@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libem.so")
 EM_OK = 0
 EM_ERR_INVALID_ARG, EM_ERR_OOM, EM_ERR_CUDA, EM_ERR_TIMEOUT, EM_ERR_REJECTED, EM_ERR_BUSY, EM_ERR_CAPACITY = \
     -1, -2, -3, -4, -5, -6, -7
-F_NORMALS, F_SMOOTH, F_INPAINT, F_TRACE = 1, 2, 4, 256
+F_NORMALS, F_SMOOTH, F_INPAINT, F_MEDIAN, F_GAUSS, F_TRACE = 1, 2, 4, 8, 16, 256
 LAYER_ELEVATION, LAYER_VARIANCE, LAYER_TIME = 1, 2, 4
 LAYER_NORMAL_X, LAYER_NORMAL_Y, LAYER_NORMAL_Z = 8, 16, 32
 LAYER_SMOOTH, LAYER_INPAINT, LAYER_VALID, LAYER_VARIANCE_NOW = 64, 128, 256, 512

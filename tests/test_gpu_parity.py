@@ -228,6 +228,9 @@ def test_invalid_arguments(em):
     assert e.value.code == em.EM_ERR_INVALID_ARG
     with pytest.raises(em.EMError):
         em.Map(em.Params(var_min=0.0))
+    with pytest.raises(em.EMError) as e:  # two smoothing filters at once
+        em.Map(em.Params(width=10, height=10, flags=em.F_SMOOTH | em.F_MEDIAN))
+    assert e.value.code == em.EM_ERR_INVALID_ARG
     with pytest.raises(em.EMError) as e:  # a side longer than 2^22 cells
         em.Map(em.Params(width=(1 << 22) + 1, height=1))
     assert e.value.code == em.EM_ERR_INVALID_ARG
@@ -280,16 +283,20 @@ def test_depth_stream_frame_by_frame(em):
         assert cmp.notes["cells_compared"] > 3000, t
 
 
-def test_lidar_frame_with_filters(em):
+@pytest.mark.parametrize("smoothing", ["box", "median", "gauss"])
+def test_lidar_frame_with_filters(em, smoothing):
     """A LiDAR scan (128 x 2048) on a 500 x 500 map over stairs and a ramp, with
-    normals (and the Eq. 4 guard), 5x5 smoothing and in-painting."""
+    normals (and the Eq. 4 guard), 5x5 smoothing (box mean, median or Gaussian)
+    and in-painting."""
+    kind = {"box": em.F_SMOOTH, "median": em.F_MEDIAN, "gauss": em.F_GAUSS}[smoothing]
+    P = dict(LIDAR_P, flags=em.F_NORMALS | kind | em.F_INPAINT)
     frames = synth.lidar_stream(seed=3, frames=2)
     f0 = next(frames)
     f1 = next(frames)
-    om = oracle.OracleMap(parity.oracle_params(LIDAR_P))
+    om = oracle.OracleMap(parity.oracle_params(P))
     om.update(f0["clouds"])
     prior = parity.oracle_state_as_prior(om)
-    cmp, tr, gm, _ = run_case(em, LIDAR_P, f1["clouds"], prior=prior,
+    cmp, tr, gm, _ = run_case(em, P, f1["clouds"], prior=prior,
                               stencils=("nx", "ny", "nz", "smooth", "inpaint"))
     assert cmp.notes["cells_compared"] > 20000
     s = gm.state()

@@ -418,6 +418,68 @@ def test_gaussian_smoothing(oracle_mod):
     assert np.allclose(out[2:-2, 2:-2], ref[2:-2, 2:-2], atol=1e-12, rtol=0)
 
 
+def _upper_map(oracle_mod, **kw):
+    P = dict(width=8, height=8, resolution=1.0, noise_a0=0.01, ray_step=1.0, flags=oracle_mod.UPPER)
+    P.update(kw)
+    return oracle_mod.OracleMap(oracle_mod.Params(**P))
+
+
+def _pose(t):
+    return np.array([1, 0, 0, t[0], 0, 1, 0, t[1], 0, 0, 1, t[2]], np.float32)
+
+
+def test_upper_bound_layer_hand_worked(oracle_mod):
+    """Section II-F: a ray through empty cells bounds their ground by the ray
+    height.  Sensor at (-3.5, 0.5, 2), point at (1.5, 0.5, 1) on an 8 x 8 map of
+    1 m cells centred on the origin, step 1 m: samples k = 1..5 at x = -3.5 + 5k/d,
+    z = 2 - k/d, d = sqrt(26); sample 5 lies in the point's own cell."""
+    m = _upper_map(oracle_mod)
+    m.update((np.array([[5.0, 0.0, -1.0]], np.float32), _pose((-3.5, 0.5, 2.0))))
+    up = m.state()["upper"]
+    d = math.sqrt(26.0)
+    want = np.full((8, 8), np.inf)
+    for k in range(1, 5):
+        want[4, k] = 2.0 - k / d
+    assert np.allclose(up[np.isfinite(want)], want[np.isfinite(want)], atol=1e-6, rtol=0)
+    assert np.array_equal(np.isfinite(up), np.isfinite(want))
+    # a lower ray over the same cells lowers the bound (running minimum) ...
+    m.update((np.array([[5.0, 0.0, -1.5]], np.float32), _pose((-3.5, 0.5, 1.8))))
+    up2 = m.state()["upper"]
+    assert np.all(up2[4, 1:5] <= up[4, 1:5]) and np.any(up2[4, 1:5] < up[4, 1:5])
+    # ... and a cell that receives a point has no bound any more
+    m.update((np.array([[0.0, 0.0, -1.5]], np.float32), _pose((-1.5, 0.5, 1.8))))
+    assert np.isinf(m.state()["upper"][4, 2])
+    assert np.isfinite(m.state()["var"][4, 2])
+
+
+def test_upper_bound_skips_observed_cells_and_moves_with_the_map(oracle_mod):
+    m = _upper_map(oracle_mod)
+    h = np.full((8, 8), np.nan)
+    var = np.full((8, 8), np.inf)
+    h[4, 2], var[4, 2] = -5.0, 1e-4  # observed far below the ray: bounded by nothing
+    m.set_state(h=h, var=var, t_last=np.zeros((8, 8), np.int32), t_now=1)
+    m.update((np.array([[5.0, 0.0, -1.0]], np.float32), _pose((-3.5, 0.5, 2.0))))
+    up = m.state()["upper"]
+    assert np.isinf(up[4, 2]) and np.isfinite(up[4, 1]) and np.isfinite(up[4, 3])
+    before = up.copy()
+    m.shift(1, 0)
+    after = m.state()["upper"]
+    assert np.array_equal(after[:, :7], before[:, 1:]) and np.all(np.isinf(after[:, 7]))
+
+
+def test_upper_bound_does_not_depend_on_point_order(oracle_mod):
+    rng = np.random.default_rng(4)
+    pts = np.column_stack([rng.uniform(-3.5, 3.5, 12), rng.uniform(-3.5, 3.5, 12),
+                           rng.uniform(-2.5, -1.0, 12)]).astype(np.float32)  # few points: most cells stay empty
+    outs = []
+    for perm in (np.arange(12), rng.permutation(12)):
+        m = _upper_map(oracle_mod, ray_step=0.3)
+        m.update((pts[perm], _pose((0.2, -0.1, 1.5))))
+        outs.append(m.state()["upper"])
+    assert np.array_equal(outs[0], outs[1])
+    assert np.isfinite(outs[0]).sum() > 5
+
+
 def test_inpainting(oracle_mod):
     rng = np.random.default_rng(2)
     h = rng.uniform(0.0, 1.0, (16, 16))
