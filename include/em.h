@@ -55,6 +55,10 @@ enum {
   EM_F_GAUSS = 1u << 4,   /* the smoothed layer holds a 5x5 Gaussian instead (sigma = 1 cell, weights
                              renormalised over the window's valid cells; Section II-I).  At most one
                              of EM_F_SMOOTH, EM_F_MEDIAN, EM_F_GAUSS may be set. */
+  EM_F_UPPER = 1u << 5,   /* keep an upper-bound layer (Section II-F): every ray sample in a cell
+                             that holds no estimate lowers the cell's bound to the sample height
+                             (a running minimum over updates); a cell that takes an estimate, or
+                             comes into view by a shift, has no bound (+inf).  Needs ray_step > 0. */
   EM_F_TRACE = 1u << 8    /* record per-point cells and decisions of the last update (testing) */
 };
 
@@ -69,7 +73,8 @@ enum {
   EM_LAYER_SMOOTH = 1u << 6,
   EM_LAYER_INPAINT = 1u << 7,
   EM_LAYER_VALID = 1u << 8,       /* 1.0 where the cell holds an estimate, else 0.0 (get only) */
-  EM_LAYER_VARIANCE_NOW = 1u << 9 /* sigma_m^2 plus time variance up to the current update (get only) */
+  EM_LAYER_VARIANCE_NOW = 1u << 9, /* sigma_m^2 plus time variance up to the current update (get only) */
+  EM_LAYER_UPPER = 1u << 10        /* upper bound of the ground height (EM_F_UPPER); +inf where none */
 };
 
 /* Map and method parameters.  The paper leaves most of them user-defined

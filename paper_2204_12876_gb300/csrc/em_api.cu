@@ -65,6 +65,7 @@ struct em_map {
   float* nz = nullptr;
   float* smooth = nullptr;
   float* inpaint = nullptr;
+  float* upper = nullptr;
   // per-cell scratch
   uint32_t* mark = nullptr;
   float* thr = nullptr;
@@ -126,7 +127,7 @@ MapDev make_mapdev(const em_map* m) {
   MapDev d;
   memset(&d, 0, sizeof(d));
   d.h = m->h; d.var = m->var; d.t_last = m->t_last;
-  d.nx = m->nx; d.ny = m->ny; d.nz = m->nz; d.smooth = m->smooth; d.inpaint = m->inpaint;
+  d.nx = m->nx; d.ny = m->ny; d.nz = m->nz; d.smooth = m->smooth; d.inpaint = m->inpaint; d.upper = m->upper;
   d.mark = m->mark; d.thr = m->thr; d.cnt = m->cnt; d.cell_seg = m->cell_seg;
   d.ctl = m->ctl;
   d.cell_begin = 0;
@@ -200,7 +201,7 @@ void release(em_map* m) {
   for (int i = 0; i < 2 * EM_PROF_SLOTS; ++i)
     if (m->prof_ev[i]) cudaEventDestroy(m->prof_ev[i]);
   cudaFree(m->h); cudaFree(m->var); cudaFree(m->t_last);
-  cudaFree(m->nx); cudaFree(m->ny); cudaFree(m->nz); cudaFree(m->smooth); cudaFree(m->inpaint);
+  cudaFree(m->nx); cudaFree(m->ny); cudaFree(m->nz); cudaFree(m->smooth); cudaFree(m->inpaint); cudaFree(m->upper);
   cudaFree(m->mark); cudaFree(m->thr); cudaFree(m->cnt); cudaFree(m->cell_seg);
   cudaFree(m->ctl); cudaFree(m->bctl);
   free_workspace(m);
@@ -391,6 +392,7 @@ int em_create(const em_params* params, int device, em_map** out) {
   if (normals) { EM_ALLOC(m->nx, nc) EM_ALLOC(m->ny, nc) EM_ALLOC(m->nz, nc) }
   if (params->flags & (EM_F_SMOOTH | EM_F_MEDIAN | EM_F_GAUSS)) { EM_ALLOC(m->smooth, nc) }
   if (params->flags & EM_F_INPAINT) { EM_ALLOC(m->inpaint, nc) }
+  if (params->flags & EM_F_UPPER) { EM_ALLOC(m->upper, nc) }
   EM_ALLOC(m->mark, (nc + 31) / 32) EM_ALLOC(m->thr, nc) EM_ALLOC(m->cnt, nc) EM_ALLOC(m->cell_seg, nc)
   EM_ALLOC(m->ctl, 1) EM_ALLOC(m->bctl, 1)
   EM_ALLOC(m->desc_dev, kDescBytes * kSlots)
@@ -579,7 +581,7 @@ static int ensure_layer_stage(em_map* m, size_t floats) {
 }
 
 int em_get_layers(em_map* m, uint32_t mask, float* dst, int dst_is_host, em_stream_t stream) {
-  if (!m || !dst || !mask || (mask >> 10)) return EM_ERR_INVALID_ARG;
+  if (!m || !dst || !mask || (mask >> 11)) return EM_ERR_INVALID_ARG;
   int rc = set_device(m->device);
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)stream;
@@ -599,7 +601,7 @@ int em_get_layers(em_map* m, uint32_t mask, float* dst, int dst_is_host, em_stre
 
 int em_set_layers(em_map* m, uint32_t mask, const float* src, int src_is_host, em_stream_t stream) {
   const uint32_t allowed = EM_LAYER_ELEVATION | EM_LAYER_VARIANCE | EM_LAYER_TIME | EM_LAYER_NORMAL_X |
-                           EM_LAYER_NORMAL_Y | EM_LAYER_NORMAL_Z;
+                           EM_LAYER_NORMAL_Y | EM_LAYER_NORMAL_Z | EM_LAYER_UPPER;
   if (!m || !src || !mask || (mask & ~allowed)) return EM_ERR_INVALID_ARG;
   int rc = set_device(m->device);
   if (rc) return rc;

@@ -203,6 +203,7 @@ __device__ __forceinline__ void empty_cell(const MapDev& m, int32_t p) {
   if (m.nx) { m.nx[p] = qnan(); m.ny[p] = qnan(); m.nz[p] = qnan(); }
   if (m.smooth) m.smooth[p] = qnan();
   if (m.inpaint) m.inpaint[p] = qnan();
+  if (m.upper) m.upper[p] = pinf();
 }
 
 // exposed logical columns [cx0, cx1) over all rows, and rows [ry0, ry1) over all columns
@@ -230,7 +231,7 @@ __global__ void __launch_bounds__(kMapThreads) k_fill(MapDev m) {
 // layer bits (see em.h)
 enum : uint32_t {
   L_ELEV = 1u << 0, L_VAR = 1u << 1, L_TIME = 1u << 2, L_NX = 1u << 3, L_NY = 1u << 4, L_NZ = 1u << 5,
-  L_SMOOTH = 1u << 6, L_INPAINT = 1u << 7, L_VALID = 1u << 8, L_VAR_NOW = 1u << 9
+  L_SMOOTH = 1u << 6, L_INPAINT = 1u << 7, L_VALID = 1u << 8, L_VAR_NOW = 1u << 9, L_UPPER = 1u << 10
 };
 
 __global__ void __launch_bounds__(kMapThreads) k_layers_out(MapDev m, uint32_t mask, float* __restrict__ dst) {
@@ -240,7 +241,7 @@ __global__ void __launch_bounds__(kMapThreads) k_layers_out(MapDev m, uint32_t m
     const int32_t p = phys_index(m, lx, ly);
     const bool v = isfinite(m.var[p]);
     int k = 0;
-    for (uint32_t bit = 1; bit <= L_VAR_NOW; bit <<= 1) {
+    for (uint32_t bit = 1; bit <= L_UPPER; bit <<= 1) {
       if (!(mask & bit)) continue;
       float x;
       switch (bit) {
@@ -253,7 +254,8 @@ __global__ void __launch_bounds__(kMapThreads) k_layers_out(MapDev m, uint32_t m
         case L_SMOOTH: x = m.smooth ? m.smooth[p] : qnan(); break;
         case L_INPAINT: x = m.inpaint ? m.inpaint[p] : qnan(); break;
         case L_VALID: x = v ? 1.f : 0.f; break;
-        default: x = v ? var_eff(m, m.var[p], m.t_last[p]) : pinf(); break;
+        case L_VAR_NOW: x = v ? var_eff(m, m.var[p], m.t_last[p]) : pinf(); break;
+        default: x = m.upper ? m.upper[p] : pinf(); break;
       }
       dst[(size_t)k * ncell + c] = x;
       ++k;
@@ -267,7 +269,7 @@ __global__ void __launch_bounds__(kMapThreads) k_layers_in(MapDev m, uint32_t ma
     const int32_t lx = c % m.W, ly = c / m.W;
     const int32_t p = phys_index(m, lx, ly);
     int k = 0;
-    for (uint32_t bit = 1; bit <= L_NZ; bit <<= 1) {
+    for (uint32_t bit = 1; bit <= L_UPPER; bit <<= 1) {
       if (!(mask & bit)) continue;
       const float x = src[(size_t)k * ncell + c];
       switch (bit) {
@@ -276,7 +278,8 @@ __global__ void __launch_bounds__(kMapThreads) k_layers_in(MapDev m, uint32_t ma
         case L_TIME: m.t_last[p] = (int32_t)x; break;
         case L_NX: if (m.nx) m.nx[p] = x; break;
         case L_NY: if (m.ny) m.ny[p] = x; break;
-        default: if (m.nz) m.nz[p] = x; break;
+        case L_NZ: if (m.nz) m.nz[p] = x; break;
+        default: if (m.upper) m.upper[p] = x; break;  // L_UPPER (the only other bit allowed in)
       }
       ++k;
     }

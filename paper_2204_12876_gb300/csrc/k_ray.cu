@@ -159,6 +159,14 @@ __global__ void __launch_bounds__(kRayThreads) k_ray(const BatchDev* __restrict_
           int32_t py = cy + oy;
           py -= (py >= H) ? H : 0;
           const int32_t p = py * W + px;
+          if (!isfinite(m.var[p])) {
+            // an empty cell (its threshold is the upper bound): the sample lowers
+            // the bound (Section II-F); float minimum through the ordered bits
+            const float z = zz[u];
+            if (__float_as_int(z) >= 0) atomicMin(reinterpret_cast<int*>(m.upper + p), __float_as_int(z));
+            else atomicMax(reinterpret_cast<unsigned int*>(m.upper + p), __float_as_uint(z));
+            continue;
+          }
           if (guard) {
             float n0 = m.nx[p], n1 = m.ny[p], n2 = m.nz[p];
             if (!(isfinite(n0) && isfinite(n1) && isfinite(n2))) { n0 = 0.f; n1 = 0.f; n2 = 1.f; }

@@ -120,7 +120,10 @@ __global__ void __launch_bounds__(kPointThreads) k_count(const BatchDev* __restr
     for (int32_t i = threadIdx.x; i < count; i += kPointThreads) {
       const int32_t p = p0 + i;
       const float var = m.var[p];
-      float t = __int_as_float(0xff800000);  // -inf: an empty cell is never penetrated
+      // an empty cell is never penetrated (-inf); with the upper-bound layer it holds
+      // the cell's bound instead, so a ray sample below the bound takes the march's
+      // candidate path and lowers it (Section II-F)
+      float t = m.upper ? m.upper[p] : __int_as_float(0xff800000);
       if (isfinite(var)) t = __fsub_rn(m.h[p], __fsqrt_rn(var_eff(m, var, m.t_last[p])));
       int32_t lx, ly;
       logical_of(m, p, lx, ly);

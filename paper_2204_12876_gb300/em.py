@@ -19,16 +19,16 @@ LIB_PATH = os.path.join(_HERE, "libem.so")
 EM_OK = 0
 EM_ERR_INVALID_ARG, EM_ERR_OOM, EM_ERR_CUDA, EM_ERR_TIMEOUT, EM_ERR_REJECTED, EM_ERR_BUSY, EM_ERR_CAPACITY = \
     -1, -2, -3, -4, -5, -6, -7
-F_NORMALS, F_SMOOTH, F_INPAINT, F_MEDIAN, F_GAUSS, F_TRACE = 1, 2, 4, 8, 16, 256
+F_NORMALS, F_SMOOTH, F_INPAINT, F_MEDIAN, F_GAUSS, F_UPPER, F_TRACE = 1, 2, 4, 8, 16, 32, 256
 LAYER_ELEVATION, LAYER_VARIANCE, LAYER_TIME = 1, 2, 4
 LAYER_NORMAL_X, LAYER_NORMAL_Y, LAYER_NORMAL_Z = 8, 16, 32
-LAYER_SMOOTH, LAYER_INPAINT, LAYER_VALID, LAYER_VARIANCE_NOW = 64, 128, 256, 512
+LAYER_SMOOTH, LAYER_INPAINT, LAYER_VALID, LAYER_VARIANCE_NOW, LAYER_UPPER = 64, 128, 256, 512, 1024
 PROF_SLOTS = ("count", "ray", "alloc", "scatter", "fuse", "clear", "normals", "smooth", "inpaint")
 KERNEL_NAMES = {"count": "k_count", "ray": "k_ray", "alloc": "k_alloc", "scatter": "k_scatter", "fuse": "k_fuse",
                 "clear": "k_clear", "normals": "k_normals", "smooth": "k_smooth", "inpaint": "k_inpaint"}
 LAYER_NAMES = {LAYER_ELEVATION: "h", LAYER_VARIANCE: "var", LAYER_TIME: "t_last", LAYER_NORMAL_X: "nx",
                LAYER_NORMAL_Y: "ny", LAYER_NORMAL_Z: "nz", LAYER_SMOOTH: "smooth", LAYER_INPAINT: "inpaint",
-               LAYER_VALID: "valid", LAYER_VARIANCE_NOW: "var_now"}
+               LAYER_VALID: "valid", LAYER_VARIANCE_NOW: "var_now", LAYER_UPPER: "upper"}
 
 
 class EMError(RuntimeError):
@@ -252,10 +252,10 @@ class Map:
         else:
             _check(lib.em_set_layers(self._h, mask, src.data_ptr(), 0, _stream_handle(stream)), "em_set_layers")
 
-    def set_state(self, h=None, var=None, t_last=None, nx=None, ny=None, nz=None, t_now=None):
+    def set_state(self, h=None, var=None, t_last=None, nx=None, ny=None, nz=None, t_now=None, upper=None):
         layers, mask = [], 0
         for bit, a in ((LAYER_ELEVATION, h), (LAYER_VARIANCE, var), (LAYER_TIME, t_last), (LAYER_NORMAL_X, nx),
-                       (LAYER_NORMAL_Y, ny), (LAYER_NORMAL_Z, nz)):
+                       (LAYER_NORMAL_Y, ny), (LAYER_NORMAL_Z, nz), (LAYER_UPPER, upper)):
             if a is not None:
                 mask |= bit
                 layers.append(np.asarray(a, np.float32))

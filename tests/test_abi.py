@@ -62,7 +62,9 @@ def test_struct_layout_matches_header(tmp_path, lib_path):
               "EM_BATCH_GRAPH": em.BATCH_GRAPH, "EM_NOALLOC_MAX_CELLS": em.NOALLOC_MAX_CELLS,
               "EM_NOALLOC_MAX_POINTS": em.NOALLOC_MAX_POINTS, "EM_NOALLOC_MAX_CLOUDS": em.NOALLOC_MAX_CLOUDS,
               "EM_F_NORMALS": em.F_NORMALS, "EM_F_SMOOTH": em.F_SMOOTH, "EM_F_INPAINT": em.F_INPAINT,
-              "EM_F_MEDIAN": em.F_MEDIAN, "EM_F_GAUSS": em.F_GAUSS, "EM_F_TRACE": em.F_TRACE}
+              "EM_F_MEDIAN": em.F_MEDIAN, "EM_F_GAUSS": em.F_GAUSS, "EM_F_UPPER": em.F_UPPER,
+              "EM_F_TRACE": em.F_TRACE, "EM_LAYER_UPPER": em.LAYER_UPPER,
+              "EM_LAYER_VARIANCE_NOW": em.LAYER_VARIANCE_NOW}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "em.h"', "int main(void) {"]
     for cname in consts:
         lines.append(f'printf("{cname} %lld\\n", (long long){cname});')

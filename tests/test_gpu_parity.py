@@ -260,6 +260,39 @@ def test_visibility_depth_frame(em):
     assert st["cells_cleared"] >= cmp.notes["cleared"] - cmp.notes["mark_marginal_cells"]
 
 
+def test_upper_bound_layer_depth_frames(em):
+    """Section II-F: two depth frames over a prior with empty cells; rays through
+    empty cells lower their upper bound, cells that take an estimate lose it.
+    Frame by frame from the oracle's state (upper layer included)."""
+    P = dict(DEPTH_P, flags=em.F_UPPER)
+    frames = synth.depth_stream(seed=7, frames=2)
+    prior = synth.random_prior(seed=32, width=200, height=200, t_now=5, invalid_frac=0.4)
+    om = oracle.OracleMap(parity.oracle_params(P))
+    parity.prior_to_oracle(om, prior)
+    bounded = 0
+    for fr in frames:
+        gm = gpu_map(em, P)
+        state = parity.oracle_state_as_prior(om)
+        upper0 = om.state()["upper"].astype(np.float32)
+        parity.prior_to_gpu(gm, state)
+        gm.set_state(upper=upper0)
+        om.set_upper(upper0.astype(np.float64))
+        prior_valid = np.isfinite(om.state()["var"])
+        tr = om.update(fr["clouds"], trace=True, unit=oracle.FP32_UNIT, abs_band=parity.ABS_BAND)
+        gm.update_multi([(dev(p), q) for p, q in fr["clouds"]])
+        n = sum(len(p) for p, _ in fr["clouds"])
+        parity.compare_update(tr, om.state(), gm.state(), gm.trace(n), prior_valid=prior_valid, check_stencils=())
+        o_up, g_up = om.state()["upper"], gm.state()["upper"].astype(np.float64)
+        excl = parity.dilate((tr.cflags & oracle.CF_MARK) != 0, 1) | parity.dilate((tr.cflags & oracle.CF_VALUE) != 0, 1)
+        oi, gi = np.isinf(o_up), np.isinf(g_up)
+        assert not ((oi != gi) & ~excl).any(), "upper-bound pattern differs"
+        ok = ~oi & ~gi & ~excl
+        assert np.all(np.abs(g_up - o_up)[ok] <= parity.H_TOL)
+        assert np.all(np.isinf(g_up[np.isfinite(gm.state()["var"])]))  # observed cells carry no bound
+        bounded = max(bounded, int(ok.sum()))
+    assert bounded > 1000
+
+
 def test_depth_stream_frame_by_frame(em):
     """Frames of the depth-camera stream with recentring shifts; each frame
     starts both sides from the oracle's previous state (float32)."""
