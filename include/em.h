@@ -55,7 +55,7 @@ enum {
   EM_F_GAUSS = 1u << 4,   /* the smoothed layer holds a 5x5 Gaussian instead (sigma = 1 cell, weights
                              renormalised over the window's valid cells; Section II-I).  At most one
                              of EM_F_SMOOTH, EM_F_MEDIAN, EM_F_GAUSS may be set. */
-  EM_F_UPPER = 1u << 5,   /* keep an upper-bound layer (Section II-F): every ray sample in a cell
+  EM_F_UPPER = 1u << 5,   /* keep an upper-bound layer (Section II-H): every ray sample in a cell
                              that holds no estimate lowers the cell's bound to the sample height
                              (a running minimum over updates); a cell that takes an estimate, or
                              comes into view by a shift, has no bound (+inf).  Needs ray_step > 0. */

@@ -50,7 +50,7 @@ class _Params(ctypes.Structure):
                 ("ray_step", ctypes.c_double),
                 ("cleanup_min_age", ctypes.c_int32),
                 ("cleanup_normal_thresh", ctypes.c_double),
-                ("flags", ctypes.c_uint32)]
+                ("flags", ctypes.c_uint32), ("drift_flatness", ctypes.c_double)]
 
 
 class _Cloud(ctypes.Structure):
@@ -87,6 +87,7 @@ def _load():
         lib.orc_shift.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
         lib.orc_filters.argtypes = [vp, ctypes.c_uint32]
         lib.orc_get_upper.argtypes = [vp, vp]
+        lib.orc_last_drift.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
         lib.orc_set_upper.argtypes = [vp, vp]
         _lib = lib
     return _lib
@@ -112,6 +113,7 @@ class Params:
     cleanup_min_age: int = 0
     cleanup_normal_thresh: float = 0.0
     flags: int = 0
+    drift_flatness: float = 0.0
 
     def _c(self) -> _Params:
         return _Params(**{f.name: getattr(self, f.name) for f in fields(self)})
@@ -172,6 +174,12 @@ class OracleMap:
         out["upper"] = np.empty((H, W), np.float64)
         self._lib.orc_get_upper(self._h, _ptr(out["upper"]))
         return out
+
+    def last_drift(self):
+        """(mean height error added by the last update, points that entered it)."""
+        d, n = ctypes.c_double(), ctypes.c_int64()
+        self._lib.orc_last_drift(self._h, ctypes.byref(d), ctypes.byref(n))
+        return d.value, n.value
 
     def set_upper(self, upper):
         a = np.ascontiguousarray(upper, dtype=np.float64).reshape(-1)

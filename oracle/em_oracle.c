@@ -14,12 +14,14 @@
  *   1. snapshot the cell state (h, sigma_m^2, last-update time, normals)
  *   2. per point: finiteness / range check, transform by the sensor pose,
  *      distance d from the sensor, point variance from the noise model
- *      (Section II-C), cell indices
+ *      (Section II-C), cell indices; then, with drift compensation (Section
+ *      II-D), the mean height error of the points that fall into flat cells
+ *      holding an estimate is added to every estimate
  *   3. per cell, its points in input order: wall rule (Section II-C, last
  *      paragraph), Mahalanobis outlier gate against the snapshot (Section
  *      II-C), then Eq. 1 and Eq. 2 applied point after point
  *   4. ray casting against the snapshot (Section II-E, Eq. 3, Eq. 4); with the
- *      upper-bound layer (Section II-F), samples in cells that are empty in the
+ *      upper-bound layer (Section II-H), samples in cells that are empty in the
  *      snapshot lower the cell's bound to the sample height
  *   5. removal of penetrated cells that were not updated recently; cells that
  *      hold an estimate after the update have no upper bound
@@ -78,6 +80,7 @@ typedef struct orc_params {
   int32_t cleanup_min_age;
   double cleanup_normal_thresh;
   uint32_t flags;
+  double drift_flatness; /* drift compensation: cells with normal n_z >= this count as flat; 0 = off */
 } orc_params;
 
 typedef struct orc_cloud {
@@ -119,7 +122,9 @@ typedef struct orc_map {
   double* nz;
   double* smooth;
   double* inpaint;
-  double* upper; /* upper bound of the ground height (Section II-F), +inf where none */
+  double* upper; /* upper bound of the ground height (Section II-H), +inf where none */
+  double last_drift;    /* mean height error added by the last update's drift compensation */
+  int64_t drift_points; /* points that entered that mean */
 } orc_map;
 
 static double* alloc_fill(int64_t n, double v) {
@@ -170,6 +175,11 @@ void orc_origin(const orc_map* m, double* x0, double* y0) {
 }
 
 int32_t orc_t_now(const orc_map* m) { return m->t_now; }
+
+void orc_last_drift(const orc_map* m, double* drift, int64_t* points) {
+  *drift = m->last_drift;
+  *points = m->drift_points;
+}
 
 void orc_get_shift(const orc_map* m, int64_t* sx, int64_t* sy) {
   *sx = m->shift_x;
@@ -520,7 +530,7 @@ static void walk_ray(orc_map* m, const pt_info* pi, const float* pose, const dou
       }
       if (mode == 0 && exists && below && guard_ok) mark[c] = 1;
     } else if (mode == 0 && exists && (p->flags & ORC_UPPER)) {
-      /* a ray through an empty cell: its ground is not above the ray (Section II-F) */
+      /* a ray through an empty cell: its ground is not above the ray (Section II-H) */
       if (sz < m->upper[c]) m->upper[c] = sz;
     }
     if (marginal && cflags) flag_block(m, cflags, cx, cy, 1, CF_MARK);
@@ -607,6 +617,33 @@ int orc_update(orc_map* m, const orc_cloud* clouds, int32_t ncloud, orc_trace* t
       if (!in_range) { pi->status = ST_RANGE; continue; }
       pi->status = in_map(m, pi->ix, pi->iy) ? ST_ACCEPT : ST_OUTSIDE; /* decided per cell below */
     }
+  }
+
+  /* height drift compensation (Section II-D): the error of each point against
+   * the estimate of its cell, over cells that hold an estimate and are flat
+   * (the previous normal has n_z >= drift_flatness; a NaN normal is not flat);
+   * the mean error is added to every estimate before the update uses them */
+  if (p->drift_flatness > 0) {
+    double eps = 0.0;
+    int64_t n_eps = 0;
+    for (int64_t i = 0; i < npts; ++i) {
+      const pt_info* pi = &pts[i];
+      if (pi->status != ST_ACCEPT) continue;
+      int64_t c = pi->iy * W + pi->ix;
+      if (!isfinite(ve0[c]) || !(nz0[c] >= p->drift_flatness)) continue;
+      eps += pi->z - h0[c];
+      ++n_eps;
+    }
+    if (n_eps > 0) {
+      const double mean = eps / (double)n_eps;
+      for (int64_t c = 0; c < nc; ++c) {
+        if (!isfinite(ve0[c])) continue;
+        h0[c] += mean;
+        m->h[c] += mean;
+      }
+    }
+    m->last_drift = n_eps > 0 ? eps / (double)n_eps : 0.0;
+    m->drift_points = n_eps;
   }
 
   /* 3. per cell: points in input order (linked lists built back to front) */

@@ -81,7 +81,7 @@ struct MapDev {
   float* nz;
   float* smooth;    // may be null
   float* inpaint;   // may be null
-  float* upper;     // upper bound of the ground height (Section II-F), +inf where none; may be null
+  float* upper;     // upper bound of the ground height (Section II-H), +inf where none; may be null
   uint32_t* mark;   // visibility marks, one bit per physical cell, zero between updates
   float* thr;       // per LOGICAL cell [iy][ix]: h - sqrt(var_eff) of the pre-update map, -inf if empty
   int32_t* cnt;     // per physical cell point count, zero between updates

@@ -188,7 +188,7 @@ __device__ __forceinline__ bool write_cell(const MapDev& m, int32_t cell, const 
   m.h[cell] = h_new;
   m.var[cell] = var_new;
   m.t_last[cell] = m.t_now;
-  if (m.upper) m.upper[cell] = __int_as_float(0x7f800000);  // observed: no bound (Section II-F)
+  if (m.upper) m.upper[cell] = __int_as_float(0x7f800000);  // observed: no bound (Section II-H)
   return true;
 }
 

@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(kRayThreads) k_ray(const BatchDev* __restrict_
           const int32_t p = py * W + px;
           if (!isfinite(m.var[p])) {
             // an empty cell (its threshold is the upper bound): the sample lowers
-            // the bound (Section II-F); float minimum through the ordered bits
+            // the bound (Section II-H); float minimum through the ordered bits
             const float z = zz[u];
             if (__float_as_int(z) >= 0) atomicMin(reinterpret_cast<int*>(m.upper + p), __float_as_int(z));
             else atomicMax(reinterpret_cast<unsigned int*>(m.upper + p), __float_as_uint(z));

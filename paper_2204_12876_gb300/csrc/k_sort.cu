@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(kPointThreads) k_count(const BatchDev* __restr
       const float var = m.var[p];
       // an empty cell is never penetrated (-inf); with the upper-bound layer it holds
       // the cell's bound instead, so a ray sample below the bound takes the march's
-      // candidate path and lowers it (Section II-F)
+      // candidate path and lowers it (Section II-H)
       float t = m.upper ? m.upper[p] : __int_as_float(0xff800000);
       if (isfinite(var)) t = __fsub_rn(m.h[p], __fsqrt_rn(var_eff(m, var, m.t_last[p])));
       int32_t lx, ly;

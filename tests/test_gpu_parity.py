@@ -261,7 +261,7 @@ def test_visibility_depth_frame(em):
 
 
 def test_upper_bound_layer_depth_frames(em):
-    """Section II-F: two depth frames over a prior with empty cells; rays through
+    """Section II-H: two depth frames over a prior with empty cells; rays through
     empty cells lower their upper bound, cells that take an estimate lose it.
     Frame by frame from the oracle's state (upper layer included)."""
     P = dict(DEPTH_P, flags=em.F_UPPER)

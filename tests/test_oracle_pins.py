@@ -429,7 +429,7 @@ def _pose(t):
 
 
 def test_upper_bound_layer_hand_worked(oracle_mod):
-    """Section II-F: a ray through empty cells bounds their ground by the ray
+    """Section II-H: a ray through empty cells bounds their ground by the ray
     height.  Sensor at (-3.5, 0.5, 2), point at (1.5, 0.5, 1) on an 8 x 8 map of
     1 m cells centred on the origin, step 1 m: samples k = 1..5 at x = -3.5 + 5k/d,
     z = 2 - k/d, d = sqrt(26); sample 5 lies in the point's own cell."""
@@ -478,6 +478,64 @@ def test_upper_bound_does_not_depend_on_point_order(oracle_mod):
         outs.append(m.state()["upper"])
     assert np.array_equal(outs[0], outs[1])
     assert np.isfinite(outs[0]).sum() > 5
+
+
+def _drift_map(oracle_mod, h, nz, flat=0.9, var=1e-4):
+    H, W = h.shape
+    m = oracle_mod.OracleMap(oracle_mod.Params(width=W, height=H, resolution=1.0, noise_a0=0.01,
+                                               drift_flatness=flat))
+    v = np.where(np.isnan(h), np.inf, var)
+    m.set_state(h=h, var=v, t_last=np.ones((H, W), np.int32), nx=np.zeros((H, W)), ny=np.zeros((H, W)),
+                nz=nz, t_now=1)
+    return m
+
+
+def _cell_points(cells, z):
+    """One point at the centre of each (ix, iy) cell of a 1 m grid centred on the
+    origin (W = H = 6: centre at (ix - 2.5, iy - 2.5)), height z, identity pose."""
+    pts = np.array([[ix - 2.5, iy - 2.5, zz] for (ix, iy), zz in zip(cells, z)], np.float32)
+    return pts, np.array([1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0], np.float32)
+
+
+def test_drift_compensation_closed_form(oracle_mod):
+    """Section II-D: the mean error of points in flat cells holding an estimate
+    is added to every estimate before the update."""
+    h = np.zeros((6, 6))
+    h[0, 5] = np.nan                                   # an empty cell
+    nz = np.ones((6, 6))
+    nz[3:, :] = 0.5                                    # steep rows: not flat at 0.9
+    m = _drift_map(oracle_mod, h, nz)
+    cells = [(1, 1), (2, 1), (4, 2), (0, 0)]           # flat cells: errors 0.05, 0.07, 0.09, 0.03
+    steep = [(1, 4), (2, 5)]                           # ignored whatever their error
+    pts, pose = _cell_points(cells + steep + [(5, 0)], [0.05, 0.07, 0.09, 0.03, -3.0, 4.0, 9.0])
+    m.update((pts, pose))
+    z = pts[:, 2].astype(np.float64)                   # the heights as the float32 points carry them
+    mean = z[:4].mean()
+    drift, n = m.last_drift()
+    assert n == 4 and drift == pytest.approx(mean, abs=1e-15)
+    s = m.state()
+    assert s["h"][4, 4] == pytest.approx(mean, abs=1e-15)   # untouched cells move by the mean
+    assert s["h"][3, 3] == pytest.approx(mean, abs=1e-15)
+    assert s["h"][0, 5] == pytest.approx(z[6], abs=1e-15)   # the empty cell took its point as is
+    # one point of the same variance as the drifted estimate: the two-point mean (Eq. 1)
+    var_p = 0.01 ** 2
+    assert s["h"][1, 1] == pytest.approx((var_p * mean + 1e-4 * z[0]) / (1e-4 + var_p), abs=1e-12)
+
+
+def test_drift_compensation_off_and_empty(oracle_mod):
+    h = np.zeros((6, 6))
+    nz = np.ones((6, 6))
+    for flat in (0.0, 0.9):
+        m = _drift_map(oracle_mod, h, nz, flat=flat)
+        pts, pose = _cell_points([(1, 1), (2, 2)], [0.2, 0.2])
+        m.update((pts, pose))
+        s = m.state()
+        assert s["h"][4, 4] == (0.0 if flat == 0.0 else pytest.approx(float(np.float32(0.2)), abs=1e-15))
+    # no flat cell with an estimate: nothing moves
+    m = _drift_map(oracle_mod, h, np.full((6, 6), np.nan))
+    pts, pose = _cell_points([(1, 1)], [0.3])
+    m.update((pts, pose))
+    assert m.last_drift() == (0.0, 0) and m.state()["h"][4, 4] == 0.0
 
 
 def test_inpainting(oracle_mod):
