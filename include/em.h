@@ -94,6 +94,12 @@ typedef struct em_params {
   int32_t cleanup_min_age;      /* remove only cells last written >= max(1, this) updates ago */
   float cleanup_normal_thresh;  /* alpha_n of Eq. 4; <= 0 disables the normal guard */
   uint32_t flags;               /* EM_F_* */
+  float drift_flatness;         /* height drift compensation (Section II-D), 0 disables: the mean error
+                                   z - h of the points that fall into cells holding an estimate whose
+                                   previous normal has n_z >= drift_flatness (flat cells; the paper's
+                                   traversability threshold) is added to every estimate before the
+                                   update; in (0, 1], needs the normal layer (EM_F_NORMALS or
+                                   cleanup_normal_thresh > 0) */
 } em_params;
 
 /* One point cloud: n points of `stride` floats (3 = xyz, 4 = xyz + pad) in the
@@ -127,6 +133,8 @@ typedef struct em_stats {
   int64_t cells_updated;    /* (cell, update) pairs written by fusion */
   int64_t cells_cleared;    /* (cell, update) pairs removed by visibility cleanup */
   int64_t ray_samples;      /* ray-march sample positions in each ray's k range clipped to the map box */
+  int64_t drift_points;     /* points that entered a drift-compensation mean */
+  double drift_last;        /* height error added by the last update's drift compensation (metres) */
 } em_stats;
 
 /* Create a map of params->width x params->height empty cells centred on the
@@ -215,6 +223,7 @@ enum {
   EM_PROF_NORMALS,
   EM_PROF_SMOOTH,
   EM_PROF_INPAINT,
+  EM_PROF_DRIFT,       /* k_drift: drift compensation of the estimates (and the ray thresholds) */
   EM_PROF_SLOTS
 };
 int em_profile(em_map* map, int enable);
@@ -361,7 +370,8 @@ int em_server_destroy(em_server* srv); /* NULL-safe: drains, stops the worker, f
  *               an empty cell has var = +inf (h is then NaN)
  *   t_last      int32 [height][width], device memory, read and written
  *   nx, ny, nz  float32 [height][width], device memory, read only; required
- *               when cleanup_normal_thresh > 0, else may be NULL
+ *               when cleanup_normal_thresh > 0 or drift_flatness > 0, else may be
+ *               NULL (EM_F_UPPER is not available here: EM_ERR_INVALID_ARG)
  *   shift_x/y   the map centre is (shift_x r, shift_y r) (see em_info)
  *   t_now       index of this update (>= 1): cells it writes get t_last = t_now
  *   clouds[]    host array; clouds[i].points device memory

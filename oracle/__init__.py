@@ -87,7 +87,8 @@ def _load():
         lib.orc_shift.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
         lib.orc_filters.argtypes = [vp, ctypes.c_uint32]
         lib.orc_get_upper.argtypes = [vp, vp]
-        lib.orc_last_drift.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
+        lib.orc_last_drift.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
+                                       ctypes.POINTER(ctypes.c_double)]
         lib.orc_set_upper.argtypes = [vp, vp]
         _lib = lib
     return _lib
@@ -177,9 +178,13 @@ class OracleMap:
 
     def last_drift(self):
         """(mean height error added by the last update, points that entered it)."""
-        d, n = ctypes.c_double(), ctypes.c_int64()
-        self._lib.orc_last_drift(self._h, ctypes.byref(d), ctypes.byref(n))
-        return d.value, n.value
+        return self.last_drift_band()[:2]
+
+    def last_drift_band(self):
+        """(mean, points, marginal band of the mean in metres; 0 without marginal bands)."""
+        d, n, b = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
+        self._lib.orc_last_drift(self._h, ctypes.byref(d), ctypes.byref(n), ctypes.byref(b))
+        return d.value, n.value, b.value
 
     def set_upper(self, upper):
         a = np.ascontiguousarray(upper, dtype=np.float64).reshape(-1)

@@ -125,6 +125,7 @@ typedef struct orc_map {
   double* upper; /* upper bound of the ground height (Section II-H), +inf where none */
   double last_drift;    /* mean height error added by the last update's drift compensation */
   int64_t drift_points; /* points that entered that mean */
+  double drift_unc;     /* marginal band of that mean (metres), with the trace's marginal bands */
 } orc_map;
 
 static double* alloc_fill(int64_t n, double v) {
@@ -176,9 +177,10 @@ void orc_origin(const orc_map* m, double* x0, double* y0) {
 
 int32_t orc_t_now(const orc_map* m) { return m->t_now; }
 
-void orc_last_drift(const orc_map* m, double* drift, int64_t* points) {
+void orc_last_drift(const orc_map* m, double* drift, int64_t* points, double* band) {
   *drift = m->last_drift;
   *points = m->drift_points;
+  *band = m->drift_unc;
 }
 
 void orc_get_shift(const orc_map* m, int64_t* sx, int64_t* sy) {
@@ -519,7 +521,8 @@ static void walk_ray(orc_map* m, const pt_info* pi, const float* pose, const dou
       double sd = sqrt(ve0[c]);
       double thr = h0[c] - sd; /* Eq. 3 */
       int below = sz < thr;
-      if (u > 0 && fabs(sz - thr) < ab + 8.0 * u * (fabs(oz) + f * pi->sz + fabs(h0[c]) + sd)) marginal = 1;
+      if (u > 0 && fabs(sz - thr) < ab + m->drift_unc + 8.0 * u * (fabs(oz) + f * pi->sz + fabs(h0[c]) + sd))
+        marginal = 1;
       int guard_ok = 1;
       if (p->cleanup_normal_thresh > 0) { /* Eq. 4 */
         double n0 = nx0[c], n1 = ny0[c], n2 = nz0[c];
@@ -634,8 +637,35 @@ int orc_update(orc_map* m, const orc_cloud* clouds, int32_t ncloud, orc_trace* t
       eps += pi->z - h0[c];
       ++n_eps;
     }
+    m->drift_unc = 0.0;
     if (n_eps > 0) {
       const double mean = eps / (double)n_eps;
+      if (u > 0) {
+        /* Marginal band of the mean: a point whose cell is marginal (PF_BIN) may
+         * fall into any cell of its 3x3 block in float32, entering the mean with
+         * another error or not at all; bound each by the largest |z - h| over
+         * the flat cells with an estimate of the block plus |mean|, and add the
+         * float32 rounding of the errors and of the mean. */
+        double sum_b = 0.0, sum_abs = 0.0;
+        for (int64_t i = 0; i < npts; ++i) {
+          const pt_info* pi = &pts[i];
+          if (pi->status != ST_ACCEPT) continue;
+          int64_t c = pi->iy * W + pi->ix;
+          if (isfinite(ve0[c]) && nz0[c] >= p->drift_flatness) sum_abs += fabs(pi->z - h0[c]);
+          if (!(pi->flags & PF_BIN)) continue;
+          double bmax = 0.0;
+          for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+              int64_t jx = pi->ix + dx, jy = pi->iy + dy;
+              if (!in_map(m, jx, jy)) continue;
+              int64_t k = jy * W + jx;
+              if (isfinite(ve0[k]) && nz0[k] >= p->drift_flatness && fabs(pi->z - h0[k]) > bmax)
+                bmax = fabs(pi->z - h0[k]);
+            }
+          sum_b += bmax + fabs(mean);
+        }
+        m->drift_unc = (sum_b + 4.0 * u * sum_abs) / (double)n_eps + 2.0 * u * fabs(mean);
+      }
       for (int64_t c = 0; c < nc; ++c) {
         if (!isfinite(ve0[c])) continue;
         h0[c] += mean;
@@ -644,7 +674,10 @@ int orc_update(orc_map* m, const orc_cloud* clouds, int32_t ncloud, orc_trace* t
     }
     m->last_drift = n_eps > 0 ? eps / (double)n_eps : 0.0;
     m->drift_points = n_eps;
+  } else {
+    m->drift_unc = 0.0;
   }
+  const double du = m->drift_unc; /* widens every decision taken against the moved estimates */
 
   /* 3. per cell: points in input order (linked lists built back to front) */
   int64_t* head = (int64_t*)malloc(sizeof(int64_t) * (size_t)nc);
@@ -667,7 +700,7 @@ int orc_update(orc_map* m, const orc_cloud* clouds, int32_t ncloud, orc_trace* t
     for (int64_t i = head[c]; i >= 0; i = next[i]) {
       pt_info* pi = &pts[i];
       if (p->wall_num_thresh > 0 && valid && cnt[c] > p->wall_num_thresh) {
-        if (u > 0 && fabs(pi->z - h0[c]) < ab + 8.0 * u * (pi->sz + fabs(clouds[pi->cloud].pose[11]) + fabs(h0[c])))
+        if (u > 0 && fabs(pi->z - h0[c]) < ab + du + 8.0 * u * (pi->sz + fabs(clouds[pi->cloud].pose[11]) + fabs(h0[c])))
           pi->flags |= PF_WALL;
         if (pi->z < h0[c]) { pi->status = ST_WALL; continue; }
       }
@@ -676,7 +709,7 @@ int orc_update(orc_map* m, const orc_cloud* clouds, int32_t ncloud, orc_trace* t
         double md = fabs(pi->z - h0[c]) / s;
         if (u > 0) {
           double band = ab + 16.0 * u * md +
-                        8.0 * u * (pi->sz + fabs(clouds[pi->cloud].pose[11]) + fabs(h0[c])) / s;
+                        (8.0 * u * (pi->sz + fabs(clouds[pi->cloud].pose[11]) + fabs(h0[c])) + du) / s;
           if (fabs(md - p->mahalanobis_k) < band) pi->flags |= PF_GATE;
         }
         if (md > p->mahalanobis_k) { pi->status = ST_REJECT; ++rej; continue; }

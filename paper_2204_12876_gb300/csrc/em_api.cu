@@ -141,6 +141,7 @@ MapDev make_mapdev(const em_map* m) {
   d.min_range = m->p.min_range; d.max_range = m->p.max_range; d.k = m->p.mahalanobis_k;
   d.v_out = m->p.outlier_variance; d.sigma_t2 = m->p.time_variance; d.ray_step = m->p.ray_step;
   d.alpha_n = m->p.cleanup_normal_thresh; d.wall = m->p.wall_num_thresh; d.min_age = m->p.cleanup_min_age;
+  d.drift_flat = m->p.drift_flatness;
   d.flags = m->p.flags;
   return d;
 }
@@ -160,6 +161,9 @@ bool params_ok(const em_params* p) {
   if (p->wall_num_thresh < 0 || p->cleanup_min_age < 0) return false;
   const uint32_t sm = p->flags & (EM_F_SMOOTH | EM_F_MEDIAN | EM_F_GAUSS);
   if (sm & (sm - 1)) return false;  // one smoothing filter at most
+  // drift compensation reads the normal layer of the previous update
+  if (!(std::isfinite(p->drift_flatness) && p->drift_flatness >= 0.f && p->drift_flatness <= 1.f)) return false;
+  if (p->drift_flatness > 0.f && !((p->flags & EM_F_NORMALS) || p->cleanup_normal_thresh > 0.f)) return false;
   return true;
 }
 
@@ -460,6 +464,8 @@ static int update_impl(em_map* m, const em_cloud* clouds, int32_t n_clouds, cuda
   }
   const int64_t ncell = pad_tile((int64_t)m->p.width * m->p.height);
   EM_TRY(timed(m, EM_PROF_COUNT, s, [&] { return launch_bin(bd, total, ncell, s); }), "k_count");
+  if (m->p.drift_flatness > 0.f)
+    EM_TRY(timed(m, EM_PROF_DRIFT, s, [&] { return launch_drift(bd, ncell, s); }), "k_drift");
   if (total > 0) {
     if (m->p.ray_step > 0.f) EM_TRY(timed(m, EM_PROF_RAY, s, [&] { return launch_ray(bd, total, m->ray_group, s); }), "k_ray");
     EM_TRY(timed(m, EM_PROF_ALLOC, s, [&] { return launch_alloc(bd, ncell, s); }), "k_alloc");
@@ -671,6 +677,8 @@ int em_get_stats(em_map* m, em_stats* out) {
   out->cells_updated = (int64_t)ctl.stats[kStCellsUpdated];
   out->cells_cleared = (int64_t)ctl.stats[kStCleared];
   out->ray_samples = (int64_t)ctl.stats[kStRaySamples];
+  out->drift_points = (int64_t)ctl.stats[kStDriftPoints];
+  out->drift_last = (double)ctl.drift_last;
   return rc;
 }
 

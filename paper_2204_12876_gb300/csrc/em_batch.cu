@@ -40,10 +40,11 @@ bool tuning_ok(const em_tuning& t) {
 struct GraphKey {
   em_tuning t;
   bool ray;
+  bool drift;
   uint32_t stencils;
   bool operator==(const GraphKey& o) const {
     return t.ray_group == o.t.ray_group && t.fuse_chunk == o.t.fuse_chunk && t.big_thresh == o.t.big_thresh &&
-           ray == o.ray && stencils == o.stencils;
+           ray == o.ray && drift == o.drift && stencils == o.stencils;
   }
 };
 
@@ -112,6 +113,7 @@ cudaError_t launch_sequence(const BatchDev* bd, int64_t grid_points, int64_t gri
                             cudaStream_t s, em_batch* prof = nullptr) {
   cudaError_t e = cudaSuccess;
   e = timed(prof, EM_PROF_COUNT, s, [&] { return launch_bin(bd, grid_points, grid_cells, s); });
+  if (e == cudaSuccess && k.drift) e = timed(prof, EM_PROF_DRIFT, s, [&] { return launch_drift(bd, grid_cells, s); });
   if (grid_points > 0) {
     if (e == cudaSuccess && k.ray)
       e = timed(prof, EM_PROF_RAY, s, [&] { return launch_ray(bd, grid_points, k.t.ray_group, s); });
@@ -181,13 +183,14 @@ int prepare(em_batch* b, em_map* const* maps, const em_cloud* clouds, int32_t co
   MapDev* md = reinterpret_cast<MapDev*>(hb + sizeof(BatchDev));
   CloudDev* cd = reinterpret_cast<CloudDev*>(hb + sizeof(BatchDev) + (size_t)b->max_maps * sizeof(MapDev));
   memset(bd, 0, sizeof(BatchDev));
-  GraphKey key{tune, false, 0u};
+  GraphKey key{tune, false, false, 0u};
   int64_t cells = 0;
   for (int u = 0; u < nm; ++u) {
     md[u] = map_begin_update(b->uniq[u], map_pts[u]);
     md[u].cell_begin = cells;
     cells += pad_tile(map_cells(b->uniq[u]));
     key.ray |= md[u].ray_step > 0.f;
+    key.drift |= md[u].drift_flat > 0.f;
     key.stencils |= map_flags(b->uniq[u]) & (EM_F_NORMALS | EM_F_SMOOTH | EM_F_MEDIAN | EM_F_GAUSS | EM_F_INPAINT);
   }
   // clouds ordered by map (stable), so each map's points are contiguous

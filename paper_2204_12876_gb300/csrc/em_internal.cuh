@@ -37,14 +37,21 @@ constexpr int kTile = 1024;  // cells per tile of the cell space
 // per-map counters (device), in em_stats order
 enum StatIdx {
   kStUpdates = 0, kStIn, kStValid, kStInMap, kStAccepted, kStRejected, kStWall, kStCellsUpdated,
-  kStCleared, kStRaySamples, kStCount
+  kStCleared, kStRaySamples, kStDriftPoints, kStCount
 };
 
 // per-map device control block
 struct MapCtl {
   unsigned long long stats[kStCount];
   int32_t err;         // first device-side error code of this map (sticky until read)
-  int32_t pad[3];
+  float drift_last;    // height error added by the last drift compensation
+  int32_t pad[2];
+  // drift-compensation sums, one slot per update parity: update t accumulates
+  // into slot t & 1 (k_count) and reads it (k_drift); k_count of update t clears
+  // slot (t + 1) & 1, last read by update t - 1, which has completed
+  long long drift_h[2];           // sum of the errors' fixed-point high parts
+  unsigned long long drift_l[2];  // ... and low parts (value h 2^27 + l, 2^-44 m units)
+  unsigned long long drift_n[2];  // points in the sum
 };
 
 // per-batch device control block (reset by k_count)
@@ -90,6 +97,7 @@ struct MapDev {
   int64_t cell_begin;  // this map's first cell in the batch cell space (multiple of kTile)
   int32_t W, H, ox, oy;
   float x0, y0, res, inv_res;  // inv_res = 1 / res rounded to float
+  float drift_flat;    // drift compensation: flat iff previous normal n_z >= this; 0 = off
   float z_ref;         // reference height of empty cells in the fusion sums: the z of the
                        // first cloud's sensor origin (any fixed value gives the same result
                        // up to rounding; one near the points keeps the terms small)
@@ -138,6 +146,7 @@ int sm_count();
 
 // ---- launchers (each returns cudaGetLastError() of its launches)
 cudaError_t launch_bin(const BatchDev* b, int64_t n_points, int64_t n_cells, cudaStream_t s);
+cudaError_t launch_drift(const BatchDev* b, int64_t n_cells, cudaStream_t s);
 cudaError_t launch_ray(const BatchDev* b, int64_t n_points, int group, cudaStream_t s);
 cudaError_t launch_alloc(const BatchDev* b, int64_t n_cells, cudaStream_t s);
 cudaError_t launch_scatter(const BatchDev* b, int64_t n_points, cudaStream_t s);

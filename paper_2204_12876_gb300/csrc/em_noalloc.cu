@@ -90,7 +90,9 @@ bool na_params_ok(const em_params* p) {
     if (!std::isfinite(v)) return false;
   return p->var_min > 0.f && !std::isnan(p->max_range) && p->max_range >= p->min_range &&
          p->outlier_variance >= 0.f && p->time_variance >= 0.f && p->ray_step >= 0.f &&
-         p->wall_num_thresh >= 0 && p->cleanup_min_age >= 0;
+         p->wall_num_thresh >= 0 && p->cleanup_min_age >= 0 && std::isfinite(p->drift_flatness) &&
+         p->drift_flatness >= 0.f && p->drift_flatness <= 1.f &&
+         !(p->flags & EM_F_UPPER);  // the upper-bound layer is not one of the caller's layers here
 }
 
 }  // namespace
@@ -100,7 +102,8 @@ extern "C" int em_update_noalloc(const em_params* params, int64_t shift_x, int64
                                  const float* nz, const em_cloud* clouds, int32_t n_clouds, em_stream_t stream) {
   if (!na_params_ok(params) || !h || !var || !t_last || !clouds || n_clouds < 1 || t_now < 1)
     return EM_ERR_INVALID_ARG;
-  if (params->cleanup_normal_thresh > 0.f && (!nx || !ny || !nz)) return EM_ERR_INVALID_ARG;
+  if ((params->cleanup_normal_thresh > 0.f || params->drift_flatness > 0.f) && (!nx || !ny || !nz))
+    return EM_ERR_INVALID_ARG;
   if ((int64_t)params->width * params->height > kMaxCells || n_clouds > kMaxCloudsNA) return EM_ERR_CAPACITY;
   int64_t total = 0;
   for (int i = 0; i < n_clouds; ++i) {
@@ -152,6 +155,7 @@ extern "C" int em_update_noalloc(const em_params* params, int64_t shift_x, int64
   m->v_out = params->outlier_variance; m->sigma_t2 = params->time_variance; m->ray_step = params->ray_step;
   m->alpha_n = params->cleanup_normal_thresh; m->wall = params->wall_num_thresh;
   m->min_age = params->cleanup_min_age;
+  m->drift_flat = params->drift_flatness;
   int64_t begin = 0;
   for (int i = 0; i < n_clouds; ++i) {
     cd[i].pts = clouds[i].points;
@@ -189,6 +193,7 @@ extern "C" int em_update_noalloc(const em_params* params, int64_t shift_x, int64
   if (rc) return rc;
   const int64_t cells = pad_tile(ncell);
   cudaError_t e = launch_bin(bd, total, cells, s);
+  if (e == cudaSuccess && params->drift_flatness > 0.f) e = launch_drift(bd, cells, s);
   if (total > 0) {
     if (e == cudaSuccess && params->ray_step > 0.f) e = launch_ray(bd, total, 4, s);
     if (e == cudaSuccess) e = launch_alloc(bd, cells, s);

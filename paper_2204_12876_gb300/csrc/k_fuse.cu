@@ -45,52 +45,6 @@ constexpr int kFuseWarps = kFuseThreads / 32;
 #endif
 constexpr int kFuseBlocksPerSM = EM_FUSE_BLOCKS_PER_SM;  // resident blocks per SM (sets the register budget)
 
-// trunc(|a| 2^44) with the sign of a -- the fixed-point value of a float32 term
-// (44 fractional bits; bits below 2^-44 are dropped, the same way for every
-// order of summation) -- split as h 2^27 + l with 0 <= l < 2^27.  Exact for
-// |a| < 2^46: |a| 2^17 = F + r with F = trunc, r in [0, 1) exact (Sterbenz),
-// and r 2^27 is exact; a negative value borrows one from h so l stays >= 0.
-// Straight-line float and conversion instructions, no 128-bit shifts.
-struct Fix {
-  long long h;
-  uint32_t l;
-};
-__device__ __forceinline__ Fix to_fix(float a) {
-  const float A = __fmul_rn(fabsf(a), 131072.0f);  // |a| 2^17
-  const float F = truncf(A);
-  long long h = (long long)F;
-  uint32_t l = (uint32_t)__fmul_rn(__fsub_rn(A, F), 134217728.0f);  // r 2^27
-  if (a < 0.f) {
-    h = l ? -h - 1 : -h;
-    l = l ? (1u << 27) - l : 0u;
-  }
-  return Fix{h, l};
-}
-
-// h 2^27 + l as a 128-bit integer (l may be a sum of many 27-bit parts)
-__device__ __forceinline__ __int128 fix128(long long h, unsigned long long l) {
-  return (__int128)h * 134217728 + (__int128)l;
-}
-
-// t 2^-44 as a float, from its magnitude split into 32-bit pieces (all
-// non-negative, so no cancellation): within 2 ulp of the exact value and a
-// fixed function of t, so equal sums give equal floats.
-__device__ __forceinline__ float fixed_to_float(__int128 t) {
-  const bool neg = t < 0;
-  const unsigned __int128 m = neg ? (unsigned __int128)(-t) : (unsigned __int128)t;
-  const unsigned long long top = (unsigned long long)(m >> 64), mid = (unsigned long long)m;
-  float v;
-  if (top == 0) {  // |value| < 2^20
-    v = __fmaf_rn((float)(uint32_t)(mid >> 32), 2.44140625e-4f,                  // 2^32 2^-44
-                  __fmul_rn((float)(uint32_t)mid, 5.684341886080801486968994140625e-14f));  // 2^-44
-  } else {
-    v = __fmaf_rn((float)(uint32_t)(top >> 32), 4503599627370496.0f,             // 2^96 2^-44
-                  __fmaf_rn((float)(uint32_t)top, 1048576.0f,                    // 2^64 2^-44
-                            __fmul_rn((float)(uint32_t)(mid >> 32), 2.44140625e-4f)));
-  }
-  return neg ? -v : v;
-}
-
 __device__ __forceinline__ __int128 shfl_xor_i128(__int128 v, int o) {
   const unsigned long long lo = (unsigned long long)v;
   const unsigned long long hi = (unsigned long long)((unsigned __int128)v >> 64);

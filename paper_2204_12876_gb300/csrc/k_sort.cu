@@ -74,6 +74,22 @@ __device__ __forceinline__ int load_warp_points(const BatchDev& b, int64_t wbase
   return ci;
 }
 
+// Add a lane's or warp's drift-compensation sums to the map's slot of this update.
+__device__ __forceinline__ void drift_add(const MapDev& m, long long h, unsigned long long l,
+                                          unsigned long long n) {
+  const int slot = m.t_now & 1;
+  atomicAdd(reinterpret_cast<unsigned long long*>(&m.ctl->drift_h[slot]), (unsigned long long)h);
+  atomicAdd(&m.ctl->drift_l[slot], l);
+  atomicAdd(&m.ctl->drift_n[slot], n);
+}
+
+// Ray threshold of physical cell p for the march (Eq. 3): h - sqrt(var_eff); for
+// an empty cell -inf (never penetrated), or its upper bound with that layer.
+__device__ __forceinline__ float ray_threshold(const MapDev& m, int32_t p, float h, float var) {
+  if (!isfinite(var)) return m.upper ? m.upper[p] : __int_as_float(0xff800000);
+  return __fsub_rn(h, __fsqrt_rn(var_eff(m, var, m.t_last[p])));
+}
+
 __global__ void __launch_bounds__(kPointThreads) k_count(const BatchDev* __restrict__ bp) {
   __shared__ float4 stage[kPointThreads / 32][24];
   const BatchDev& b = *bp;
@@ -83,12 +99,25 @@ __global__ void __launch_bounds__(kPointThreads) k_count(const BatchDev* __restr
     b.ctl->rec_total = 0;
     b.ctl->n_big = 0;
     b.ctl->big_next = 0;
-    for (int mi = 0; mi < b.n_maps; ++mi) atomicAdd(&b.maps[mi].ctl->stats[kStUpdates], 1ull);
+    for (int mi = 0; mi < b.n_maps; ++mi) {
+      const MapDev& m = b.maps[mi];
+      atomicAdd(&m.ctl->stats[kStUpdates], 1ull);
+      if (m.drift_flat > 0.f) {  // clear the next update's drift slot (this one's was cleared before)
+        const int nxt = (m.t_now + 1) & 1;
+        m.ctl->drift_h[nxt] = 0;
+        m.ctl->drift_l[nxt] = 0;
+        m.ctl->drift_n[nxt] = 0;
+      }
+    }
   }
   int64_t beg, end;
   block_range(b.n_points, beg, end);
   MapCounters mc;
   const int idx[2] = {kStValid, kStInMap};
+  // drift compensation sums of this lane (Section II-D), for map dmap
+  int dmap = -1;
+  long long dh = 0;
+  unsigned long long dl = 0, dn = 0;
   for (int64_t wbase = beg + warp * 32; wbase < end; wbase += kPointThreads) {
     float px, py, pz;
     const int ci = load_warp_points(b, wbase, end, stage[warp], px, py, pz);
@@ -112,22 +141,79 @@ __global__ void __launch_bounds__(kPointThreads) k_count(const BatchDev* __restr
     int head, run;
     key_runs(tag, head, run);
     if (inm && lane == head) atomicAdd(&m.cnt[key], run);
+    // the point's error against a flat cell holding an estimate (previous normal
+    // n_z >= drift_flatness; a NaN normal is not flat), summed exactly
+    if (inm && m.drift_flat > 0.f && isfinite(m.var[key]) && m.nz[key] >= m.drift_flat) {
+      if (c.map != dmap) {
+        if (dmap >= 0) drift_add(b.maps[dmap], dh, dl, dn);
+        dmap = c.map;
+        dh = 0;
+        dl = dn = 0;
+      }
+      const Fix e = to_fix(__fsub_rn(pg.z, m.h[key]));
+      dh += e.h;
+      dl += e.l;
+      ++dn;
+    }
   }
   flush_counters(b, mc, idx, 2);
+  // drift sums: a warp sum when the warp's lanes hold one map (the usual case)
+  const int d0 = __shfl_sync(kFull, dmap, 0);
+  if (__all_sync(kFull, dmap == d0 || dn == 0)) {
+    for (int o = 16; o > 0; o >>= 1) {
+      dh += __shfl_xor_sync(kFull, dh, o);
+      dl += __shfl_xor_sync(kFull, dl, o);
+      dn += __shfl_xor_sync(kFull, dn, o);
+    }
+    if (lane == 0 && d0 >= 0 && dn) drift_add(b.maps[d0], dh, dl, dn);
+  } else if (dmap >= 0 && dn) {
+    drift_add(b.maps[dmap], dh, dl, dn);
+  }
   // ray thresholds of the pre-update map over the cell space (Eq. 3)
   for_each_tile(b, [&](const MapDev& m, int, int32_t p0, int32_t count) {
-    if (m.ray_step <= 0.f) return;
+    if (m.ray_step <= 0.f || m.drift_flat > 0.f) return;  // with drift: k_drift, after the shift
     for (int32_t i = threadIdx.x; i < count; i += kPointThreads) {
       const int32_t p = p0 + i;
-      const float var = m.var[p];
       // an empty cell is never penetrated (-inf); with the upper-bound layer it holds
       // the cell's bound instead, so a ray sample below the bound takes the march's
       // candidate path and lowers it (Section II-H)
-      float t = m.upper ? m.upper[p] : __int_as_float(0xff800000);
-      if (isfinite(var)) t = __fsub_rn(m.h[p], __fsqrt_rn(var_eff(m, var, m.t_last[p])));
+      const float var = m.var[p];
+      const float t = ray_threshold(m, p, isfinite(var) ? m.h[p] : 0.f, var);
       int32_t lx, ly;
       logical_of(m, p, lx, ly);
       m.thr[ly * m.W + lx] = t;  // logical layout: the ray march indexes it without the ring wrap
+    }
+  });
+}
+
+// Height drift compensation (Section II-D): every estimate moves by the mean
+// error of this update's points in flat cells (k_count summed them exactly, so
+// every thread derives the same mean); then the ray thresholds of the moved map.
+__global__ void __launch_bounds__(kPointThreads) k_drift(const BatchDev* __restrict__ bp) {
+  const BatchDev& b = *bp;
+  for_each_tile(b, [&](const MapDev& m, int, int32_t p0, int32_t count) {
+    if (m.drift_flat <= 0.f) return;
+    const int slot = m.t_now & 1;
+    const unsigned long long n = m.ctl->drift_n[slot];
+    const float mean =
+        n ? __fdiv_rn(fixed_to_float(fix128(m.ctl->drift_h[slot], m.ctl->drift_l[slot])), (float)n) : 0.f;
+    if (p0 == 0 && threadIdx.x == 0) {  // once per map: its first tile
+      atomicAdd(&m.ctl->stats[kStDriftPoints], n);
+      m.ctl->drift_last = mean;
+    }
+    for (int32_t i = threadIdx.x; i < count; i += kPointThreads) {
+      const int32_t p = p0 + i;
+      const float var = m.var[p];
+      float h = m.h[p];
+      if (isfinite(var) && n) {
+        h = __fadd_rn(h, mean);
+        m.h[p] = h;
+      }
+      if (m.ray_step > 0.f) {
+        int32_t lx, ly;
+        logical_of(m, p, lx, ly);
+        m.thr[ly * m.W + lx] = ray_threshold(m, p, h, var);
+      }
     }
   });
 }
@@ -293,6 +379,11 @@ cudaError_t launch_bin(const BatchDev* b, int64_t n_points, int64_t n_cells, cud
   int grid = point_grid(n_points);
   if (grid < tiles && tiles < (int64_t)sm_count() * 8) grid = (int)tiles;  // enough blocks for the cell pass
   k_count<<<grid, kPointThreads, 0, s>>>(b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_drift(const BatchDev* b, int64_t n_cells, cudaStream_t s) {
+  k_drift<<<tile_grid(n_cells), kPointThreads, 0, s>>>(b);
   return cudaGetLastError();
 }
 

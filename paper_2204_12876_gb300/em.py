@@ -23,9 +23,10 @@ F_NORMALS, F_SMOOTH, F_INPAINT, F_MEDIAN, F_GAUSS, F_UPPER, F_TRACE = 1, 2, 4, 8
 LAYER_ELEVATION, LAYER_VARIANCE, LAYER_TIME = 1, 2, 4
 LAYER_NORMAL_X, LAYER_NORMAL_Y, LAYER_NORMAL_Z = 8, 16, 32
 LAYER_SMOOTH, LAYER_INPAINT, LAYER_VALID, LAYER_VARIANCE_NOW, LAYER_UPPER = 64, 128, 256, 512, 1024
-PROF_SLOTS = ("count", "ray", "alloc", "scatter", "fuse", "clear", "normals", "smooth", "inpaint")
+PROF_SLOTS = ("count", "ray", "alloc", "scatter", "fuse", "clear", "normals", "smooth", "inpaint", "drift")
 KERNEL_NAMES = {"count": "k_count", "ray": "k_ray", "alloc": "k_alloc", "scatter": "k_scatter", "fuse": "k_fuse",
-                "clear": "k_clear", "normals": "k_normals", "smooth": "k_smooth", "inpaint": "k_inpaint"}
+                "clear": "k_clear", "normals": "k_normals", "smooth": "k_smooth", "inpaint": "k_inpaint",
+                "drift": "k_drift"}
 LAYER_NAMES = {LAYER_ELEVATION: "h", LAYER_VARIANCE: "var", LAYER_TIME: "t_last", LAYER_NORMAL_X: "nx",
                LAYER_NORMAL_Y: "ny", LAYER_NORMAL_Z: "nz", LAYER_SMOOTH: "smooth", LAYER_INPAINT: "inpaint",
                LAYER_VALID: "valid", LAYER_VARIANCE_NOW: "var_now", LAYER_UPPER: "upper"}
@@ -44,7 +45,8 @@ class _Params(ctypes.Structure):
                 ("mahalanobis_k", ctypes.c_float), ("outlier_variance", ctypes.c_float),
                 ("wall_num_thresh", ctypes.c_int32), ("time_variance", ctypes.c_float),
                 ("ray_step", ctypes.c_float), ("cleanup_min_age", ctypes.c_int32),
-                ("cleanup_normal_thresh", ctypes.c_float), ("flags", ctypes.c_uint32)]
+                ("cleanup_normal_thresh", ctypes.c_float), ("flags", ctypes.c_uint32),
+                ("drift_flatness", ctypes.c_float)]
 
 
 class _Cloud(ctypes.Structure):
@@ -62,7 +64,8 @@ class _Info(ctypes.Structure):
 class _Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("updates", "points_in", "points_valid", "points_in_map",
                                              "points_accepted", "points_rejected", "points_wall",
-                                             "cells_updated", "cells_cleared", "ray_samples")]
+                                             "cells_updated", "cells_cleared", "ray_samples",
+                                             "drift_points")] + [("drift_last", ctypes.c_double)]
 
 
 def _load():
@@ -135,6 +138,7 @@ class Params:
     cleanup_min_age: int = 0
     cleanup_normal_thresh: float = 0.0
     flags: int = 0
+    drift_flatness: float = 0.0
 
     def _c(self) -> _Params:
         return _Params(**{f.name: getattr(self, f.name) for f in fields(self)})

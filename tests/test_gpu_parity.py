@@ -293,6 +293,26 @@ def test_upper_bound_layer_depth_frames(em):
     assert bounded > 1000
 
 
+def test_drift_compensation_depth_frame(em):
+    """Section II-D: a depth frame over a prior that sits 4 cm too high; the
+    mean error of the points in flat cells moves every estimate before fusion."""
+    P = dict(DEPTH_P, flags=em.F_NORMALS, drift_flatness=0.95)
+    fr = next(synth.depth_stream(seed=2, frames=1))
+    prior = synth.random_prior(seed=2, width=200, height=200, t_now=5, obstacle_frac=0.0)  # the stream's terrain
+    prior["h"] = (prior["h"] + 0.04).astype(np.float32)
+    # normals (needed for the flatness test) are not compared here: the drift mean
+    # may differ within its marginal band, which enters fused cells in different
+    # proportions and tilts 4 cm planes beyond the 1e-5 stencil tolerance; the
+    # LiDAR filter tests cover the normals
+    cmp, tr, gm, om = run_case(em, P, fr["clouds"], prior=prior, stencils=())
+    drift, n, band = om.last_drift_band()
+    st = gm.stats()
+    assert n > 50000 and drift < -0.01                  # the frame pulls the map down
+    assert abs(st["drift_points"] - n) <= cmp.notes["marginal_points"]
+    assert abs(st["drift_last"] - drift) <= band
+    check_counts(gm, tr, cmp.notes["marginal_points"])
+
+
 def test_depth_stream_frame_by_frame(em):
     """Frames of the depth-camera stream with recentring shifts; each frame
     starts both sides from the oracle's previous state (float32)."""
