@@ -24,6 +24,9 @@ requests by a 40 GB budget and batches them continuously.
                  sequential em_update calls; HBM roofline of the update.
   depth_stream   one robot with 4 depth cameras (4 x 76,800 points), 200x200 map,
                  one em_update_multi per frame (plain path latency).
+  lidar_filters  one LiDAR robot, 500x500 map, every per-cell feature (normals,
+                 box / median / Gaussian smoothing, in-painting, upper bound,
+                 drift compensation): update time and kernel times.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -425,6 +428,7 @@ def run_ours(args, rank: int, world: int):
     if not args.served_only:
         result["batched"] = run_batched(args, em, torch, dev, barrier, max_over_ranks, world)
         result["depth_stream"] = run_depth(args, em, torch, dev)
+        result["lidar_filters"] = run_lidar_filters(args, em, torch, dev)
     if rank == 0 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(robots, pools, budget_s=args.cpu_budget)
     return result
@@ -494,6 +498,47 @@ def run_batched(args, em, torch, dev, barrier, max_over_ranks, world):
                                 "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
                                 "frac": alg / (sec / K) / 1e9 / hbm},
             "kernels": kernels}
+
+
+def run_lidar_filters(args, em, torch, dev):
+    """One LiDAR robot (128 x 2,048 points) on a 500 x 500 map with every per-cell
+    feature: normals, smoothing (box, median or Gaussian), in-painting, the
+    upper-bound layer and drift compensation; per-update time and kernel times."""
+    import synth
+    frames = list(synth.lidar_stream(seed=3, frames=3))
+    clouds = [[(torch.from_numpy(p).cuda(), q) for p, q in fr["clouds"]] for fr in frames]
+    pts = sum(len(p) for p, _ in frames[0]["clouds"])
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    out = {"workload": "128 x 2,048 LiDAR points per update, 500x500 map, normals + smoothing + in-painting + "
+                       "upper bound + drift compensation", "points_per_update": pts, "smoothing": {}}
+    for name, flag in (("box", em.F_SMOOTH), ("median", em.F_MEDIAN), ("gauss", em.F_GAUSS)):
+        P = dict(LIDAR_P, width=500, height=500, cleanup_normal_thresh=0.1, drift_flatness=0.95,
+                 flags=em.F_NORMALS | flag | em.F_INPAINT | em.F_UPPER)
+        m = em.Map(em.Params(**P), device=dev)
+        m.reserve(pts)
+        for i in range(args.warmup):
+            m.update_multi(clouds[i % len(clouds)])
+        m.profile(True)
+        times = []
+        for i in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            m.update_multi(clouds[i % len(clouds)])
+            b.record()
+            times.append((a, b))
+        torch.cuda.synchronize()
+        prof = m.profile_read()
+        m.profile(False)
+        ms = [x.elapsed_time(y) for x, y in times]
+        st = m.stats()
+        m.close()
+        out["smoothing"][name] = {
+            "ms_per_update": float(np.mean(ms)), "p99_ms": pct(ms, 0.99), "points_per_s": pts / (np.mean(ms) / 1e3),
+            "kernels_ms": {em.KERNEL_NAMES[k]: round(v[0] / v[1], 5) for k, v in prof.items() if v[1]},
+            "drift_points": st["drift_points"], "drift_last_m": st["drift_last"]}
+    out["l2"] = "flushed before every update (256 MB write, not timed); kernels_ms from per-kernel events"
+    return out
 
 
 def run_depth(args, em, torch, dev):
@@ -597,7 +642,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--served-only", action="store_true", help="skip the batched and depth-stream sub-results")
-    ap.add_argument("--workload", default="all", choices=["all", "batched", "depth"],
+    ap.add_argument("--workload", default="all", choices=["all", "batched", "depth", "lidar"],
                     help="batched / depth: run only that sub-result (for profiler runs)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -624,6 +669,8 @@ def main():
 
         if args.workload == "batched":
             res = run_batched(args, em, torch, 0, barrier, lambda x: x, 1)
+        elif args.workload == "lidar":
+            res = run_lidar_filters(args, em, torch, 0)
         else:
             res = run_depth(args, em, torch, 0)
         if rank == 0:

@@ -50,7 +50,9 @@ class _Params(ctypes.Structure):
                 ("ray_step", ctypes.c_double),
                 ("cleanup_min_age", ctypes.c_int32),
                 ("cleanup_normal_thresh", ctypes.c_double),
-                ("flags", ctypes.c_uint32), ("drift_flatness", ctypes.c_double)]
+                ("flags", ctypes.c_uint32), ("drift_flatness", ctypes.c_double),
+                ("excl_b", ctypes.c_double), ("excl_c", ctypes.c_double), ("excl_theta", ctypes.c_double),
+                ("excl_d", ctypes.c_double), ("overlap_radius", ctypes.c_double), ("overlap_dz", ctypes.c_double)]
 
 
 class _Cloud(ctypes.Structure):
@@ -115,6 +117,12 @@ class Params:
     cleanup_normal_thresh: float = 0.0
     flags: int = 0
     drift_flatness: float = 0.0
+    excl_b: float = 0.0
+    excl_c: float = 0.0
+    excl_theta: float = 0.0
+    excl_d: float = 0.0
+    overlap_radius: float = 0.0
+    overlap_dz: float = 0.0
 
     def _c(self) -> _Params:
         return _Params(**{f.name: getattr(self, f.name) for f in fields(self)})

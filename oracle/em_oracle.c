@@ -81,6 +81,15 @@ typedef struct orc_params {
   double cleanup_normal_thresh;
   uint32_t flags;
   double drift_flatness; /* drift compensation: cells with normal n_z >= this count as flat; 0 = off */
+  /* exclusion area (Section II-C, Fig. 3 not available; reading): a point whose
+   * height above the sensor exceeds b for a horizontal distance r <= c, else
+   * b + (r - c) tan(theta), at most d, is ignored; d <= 0 = off */
+  double excl_b, excl_c, excl_theta, excl_d;
+  /* overlap clearance (Section II-F; reading): after the update, estimates whose
+   * cell centre lies within overlap_radius of the sensor origin (horizontally)
+   * and whose height differs from the origin's by more than overlap_dz are
+   * cleared; overlap_dz <= 0 = off */
+  double overlap_radius, overlap_dz;
 } orc_params;
 
 typedef struct orc_cloud {
@@ -617,6 +626,19 @@ int orc_update(orc_map* m, const orc_cloud* clouds, int32_t ncloud, orc_trace* t
         double by = ab + 8.0 * u * (pi->sy + fabs(R[7]) + fabs(y0) + fabs(y - y0));
         if (edge_dist(qx, r) < bx || edge_dist(qy, r) < by) pi->flags |= PF_BIN;
       }
+      /* exclusion area (Section II-C): the point is ignored above the ramp */
+      if (in_range && p->excl_d > 0) {
+        const double dxs = x - R[3], dys = y - R[7], zr = z - R[11];
+        const double rxy = sqrt(dxs * dxs + dys * dys);
+        double lim = rxy <= p->excl_c ? p->excl_b : p->excl_b + (rxy - p->excl_c) * tan(p->excl_theta);
+        if (lim > p->excl_d) lim = p->excl_d;
+        if (zr > lim) in_range = 0;
+        if (u > 0) {
+          const double band = ab + 8.0 * u * (pi->sx + pi->sy + pi->sz + fabs(R[3]) + fabs(R[7]) + fabs(R[11]) +
+                                              fabs(lim) + fabs(p->excl_b) + fabs(p->excl_d) + rxy * 4.0);
+          if (fabs(zr - lim) < band || fabs(rxy - p->excl_c) < band) pi->flags |= PF_RANGE;
+        }
+      }
       if (!in_range) { pi->status = ST_RANGE; continue; }
       pi->status = in_map(m, pi->ix, pi->iy) ? ST_ACCEPT : ST_OUTSIDE; /* decided per cell below */
     }
@@ -770,6 +792,28 @@ int orc_update(orc_map* m, const orc_cloud* clouds, int32_t ncloud, orc_trace* t
   if (p->flags & ORC_UPPER)
     for (int64_t c = 0; c < nc; ++c)
       if (isfinite(m->var[c])) m->upper[c] = INFINITY; /* observed: no bound needed */
+
+  /* overlap clearance (Section II-F): estimates near the robot (the first
+   * cloud's sensor origin) that are far from its height belong to another floor */
+  if (p->overlap_dz > 0 && ncloud > 0) {
+    const double ox = clouds[0].pose[3], oy = clouds[0].pose[7], oz = clouds[0].pose[11];
+    for (int iy = 0; iy < H; ++iy)
+      for (int ix = 0; ix < W; ++ix) {
+        const int64_t c = (int64_t)iy * W + ix;
+        if (!isfinite(m->var[c])) continue;
+        const double cx = x0 + (ix + 0.5) * r - ox, cy = y0 + (iy + 0.5) * r - oy;
+        const double dist = sqrt(cx * cx + cy * cy), dz = fabs(m->h[c] - oz);
+        if (u > 0 && tr && tr->cflags) {
+          const double bd = ab + 8.0 * u * (fabs(x0) + fabs(ox) + fabs(y0) + fabs(oy) + dist + W * r + H * r);
+          const double bz = ab + 8.0 * u * (fabs(m->h[c]) + fabs(oz)) + 1e-5; /* the estimate's parity tolerance */
+          if (fabs(dist - p->overlap_radius) < bd || fabs(dz - p->overlap_dz) < bz) tr->cflags[c] |= CF_VALUE;
+        }
+        if (dist <= p->overlap_radius && dz > p->overlap_dz) {
+          m->h[c] = NAN;
+          m->var[c] = INFINITY;
+        }
+      }
+  }
 
   /* 6. per-cell filters on the updated map */
   if (p->flags & ORC_NORMALS) compute_normals(m);

@@ -538,6 +538,41 @@ def test_drift_compensation_off_and_empty(oracle_mod):
     assert m.last_drift() == (0.0, 0) and m.state()["h"][4, 4] == 0.0
 
 
+def test_exclusion_area_ramp(oracle_mod):
+    """Exclusion area (Section II-C, read as a ramp): above the sensor by more than
+    b = 0.5 m within c = 1 m, then b + (r - c) tan(45 deg), at most d = 1.5 m."""
+    m = oracle_mod.OracleMap(oracle_mod.Params(width=8, height=8, resolution=1.0, noise_a0=0.01, excl_b=0.5,
+                                               excl_c=1.0, excl_theta=math.pi / 4, excl_d=1.5))
+    # (horizontal distance along x, height above the sensor) -> kept?
+    cases = [(0.5, 0.4, True), (0.5, 0.6, False), (2.0, 1.4, True), (2.0, 1.6, False),
+             (3.0, 1.45, True), (3.0, 1.55, False), (1.0, 0.45, True), (1.0, 0.55, False)]
+    pts = np.array([[r, 0.1, zr] for r, zr, _ in cases], np.float32)   # sensor frame = map frame - (0, 0, 1)
+    pose = np.array([1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 1.0], np.float32)
+    tr = m.update((pts, pose), trace=True)
+    kept = tr.status != oracle_mod.ST_RANGE
+    assert list(kept) == [k for _, _, k in cases]
+
+
+def test_overlap_clearance(oracle_mod):
+    """Overlap clearance (Section II-F): estimates within 1.6 m of the sensor origin
+    (0.2, 0.3) whose height is more than 0.8 m from its height 1.0 are cleared."""
+    W = H = 8
+    m = oracle_mod.OracleMap(oracle_mod.Params(width=W, height=H, resolution=1.0, overlap_radius=1.6,
+                                               overlap_dz=0.8))
+    h = np.full((H, W), 0.5)
+    h[4, 4] = 2.5     # centre (0.5, 0.5): 0.36 m away, 1.5 m off -> cleared
+    h[3, 5] = 1.75    # centre (1.5, -0.5): 1.53 m away, 0.75 m off -> kept
+    h[3, 2] = 1.85    # centre (-1.5, -0.5): 1.86 m away -> kept (too far)
+    h[5, 3] = 0.15    # centre (-0.5, 1.5): 1.38 m away, 0.85 m off -> cleared
+    m.set_state(h=h, var=np.full((H, W), 1e-4), t_last=np.ones((H, W), np.int32), t_now=1)
+    pose = np.array([1, 0, 0, 0.2, 0, 1, 0, 0.3, 0, 0, 1, 1.0], np.float32)
+    m.update((np.zeros((0, 3), np.float32), pose))
+    cleared = ~np.isfinite(m.state()["var"])
+    want = np.zeros((H, W), bool)
+    want[4, 4] = want[5, 3] = True
+    assert np.array_equal(cleared, want)
+
+
 def test_inpainting(oracle_mod):
     rng = np.random.default_rng(2)
     h = rng.uniform(0.0, 1.0, (16, 16))
