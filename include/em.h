@@ -100,6 +100,16 @@ typedef struct em_params {
                                    traversability threshold) is added to every estimate before the
                                    update; in (0, 1], needs the normal layer (EM_F_NORMALS or
                                    cleanup_normal_thresh > 0) */
+  /* Exclusion area (Section II-C; its figure is not available, so this is a
+   * reading): a point whose height above the sensor exceeds excl_b within a
+   * horizontal distance excl_c of it, else excl_b + (r - excl_c) tan(excl_theta),
+   * at most excl_d, is ignored (no fusion, no ray).  excl_d <= 0 disables. */
+  float excl_b, excl_c, excl_theta, excl_d;
+  /* Overlap clearance (Section II-F): after the update, estimates whose cell
+   * centre lies within overlap_radius (horizontally) of the first cloud's sensor
+   * origin and whose height differs from the origin's by more than overlap_dz
+   * are cleared.  overlap_dz <= 0 disables. */
+  float overlap_radius, overlap_dz;
 } em_params;
 
 /* One point cloud: n points of `stride` floats (3 = xyz, 4 = xyz + pad) in the
@@ -224,6 +234,7 @@ enum {
   EM_PROF_SMOOTH,
   EM_PROF_INPAINT,
   EM_PROF_DRIFT,       /* k_drift: drift compensation of the estimates (and the ray thresholds) */
+  EM_PROF_OVERLAP,     /* k_overlap: overlap clearance near the robot */
   EM_PROF_SLOTS
 };
 int em_profile(em_map* map, int enable);

@@ -811,6 +811,7 @@ int orc_update(orc_map* m, const orc_cloud* clouds, int32_t ncloud, orc_trace* t
         if (dist <= p->overlap_radius && dz > p->overlap_dz) {
           m->h[c] = NAN;
           m->var[c] = INFINITY;
+          if (tr && tr->cleared) tr->cleared[c] = 1; /* a removal (not counted as visibility) */
         }
       }
   }

@@ -142,6 +142,9 @@ MapDev make_mapdev(const em_map* m) {
   d.v_out = m->p.outlier_variance; d.sigma_t2 = m->p.time_variance; d.ray_step = m->p.ray_step;
   d.alpha_n = m->p.cleanup_normal_thresh; d.wall = m->p.wall_num_thresh; d.min_age = m->p.cleanup_min_age;
   d.drift_flat = m->p.drift_flatness;
+  d.excl_b = m->p.excl_b; d.excl_c = m->p.excl_c; d.excl_d = m->p.excl_d;
+  d.excl_tan = (float)std::tan((double)m->p.excl_theta);
+  d.ovl_r2 = m->p.overlap_radius * m->p.overlap_radius; d.ovl_dz = m->p.overlap_dz;
   d.flags = m->p.flags;
   return d;
 }
@@ -164,6 +167,10 @@ bool params_ok(const em_params* p) {
   // drift compensation reads the normal layer of the previous update
   if (!(std::isfinite(p->drift_flatness) && p->drift_flatness >= 0.f && p->drift_flatness <= 1.f)) return false;
   if (p->drift_flatness > 0.f && !((p->flags & EM_F_NORMALS) || p->cleanup_normal_thresh > 0.f)) return false;
+  const float g[] = {p->excl_b, p->excl_c, p->excl_theta, p->excl_d, p->overlap_radius, p->overlap_dz};
+  for (float v : g)
+    if (!std::isfinite(v)) return false;
+  if (p->excl_d > 0.f && !(p->excl_theta > -1.5707963f && p->excl_theta < 1.5707963f)) return false;
   return true;
 }
 
@@ -241,7 +248,9 @@ int upload_desc(em_map* m, const em_cloud* clouds, int32_t n_clouds, int64_t tot
   CloudDev* cd = reinterpret_cast<CloudDev*>(hb + sizeof(BatchDev) + sizeof(MapDev));
   memset(b, 0, sizeof(BatchDev));
   *md = make_mapdev(m);
-  md->z_ref = n_clouds > 0 ? clouds[0].pose[11] : 0.f;
+  md->z_ref = n_clouds > 0 ? clouds[0].pose[11] : 0.f;  // the first cloud's sensor origin
+  md->ref_x = n_clouds > 0 ? clouds[0].pose[3] : 0.f;
+  md->ref_y = n_clouds > 0 ? clouds[0].pose[7] : 0.f;
   int64_t begin = 0;
   for (int i = 0; i < n_clouds; ++i) {
     CloudDev& c = cd[i];
@@ -473,6 +482,8 @@ static int update_impl(em_map* m, const em_cloud* clouds, int32_t n_clouds, cuda
     EM_TRY(timed(m, EM_PROF_FUSE, s, [&] { return launch_fuse(bd, total, m->fuse_chunk, s); }), "k_fuse");
   }
   EM_TRY(timed(m, EM_PROF_CLEAR, s, [&] { return launch_clear(bd, ncell, s); }), "k_clear");
+  if (m->p.overlap_dz > 0.f && n_clouds > 0)
+    EM_TRY(timed(m, EM_PROF_OVERLAP, s, [&] { return launch_overlap(bd, ncell, s); }), "k_overlap");
   if (m->p.flags & EM_F_NORMALS)
     EM_TRY(timed(m, EM_PROF_NORMALS, s, [&] { return launch_normals(bd, ncell, s); }), "k_normals");
   if (m->p.flags & (EM_F_SMOOTH | EM_F_MEDIAN | EM_F_GAUSS))

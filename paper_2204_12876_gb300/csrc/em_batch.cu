@@ -41,10 +41,11 @@ struct GraphKey {
   em_tuning t;
   bool ray;
   bool drift;
+  bool overlap;
   uint32_t stencils;
   bool operator==(const GraphKey& o) const {
     return t.ray_group == o.t.ray_group && t.fuse_chunk == o.t.fuse_chunk && t.big_thresh == o.t.big_thresh &&
-           ray == o.ray && drift == o.drift && stencils == o.stencils;
+           ray == o.ray && drift == o.drift && overlap == o.overlap && stencils == o.stencils;
   }
 };
 
@@ -123,6 +124,8 @@ cudaError_t launch_sequence(const BatchDev* bd, int64_t grid_points, int64_t gri
       e = timed(prof, EM_PROF_FUSE, s, [&] { return launch_fuse(bd, grid_points, k.t.fuse_chunk, s); });
   }
   if (e == cudaSuccess) e = timed(prof, EM_PROF_CLEAR, s, [&] { return launch_clear(bd, grid_cells, s); });
+  if (e == cudaSuccess && k.overlap)
+    e = timed(prof, EM_PROF_OVERLAP, s, [&] { return launch_overlap(bd, grid_cells, s); });
   if (e == cudaSuccess && (k.stencils & EM_F_NORMALS))
     e = timed(prof, EM_PROF_NORMALS, s, [&] { return launch_normals(bd, grid_cells, s); });
   if (e == cudaSuccess && (k.stencils & (EM_F_SMOOTH | EM_F_MEDIAN | EM_F_GAUSS)))
@@ -183,7 +186,7 @@ int prepare(em_batch* b, em_map* const* maps, const em_cloud* clouds, int32_t co
   MapDev* md = reinterpret_cast<MapDev*>(hb + sizeof(BatchDev));
   CloudDev* cd = reinterpret_cast<CloudDev*>(hb + sizeof(BatchDev) + (size_t)b->max_maps * sizeof(MapDev));
   memset(bd, 0, sizeof(BatchDev));
-  GraphKey key{tune, false, false, 0u};
+  GraphKey key{tune, false, false, false, 0u};
   int64_t cells = 0;
   for (int u = 0; u < nm; ++u) {
     md[u] = map_begin_update(b->uniq[u], map_pts[u]);
@@ -191,6 +194,7 @@ int prepare(em_batch* b, em_map* const* maps, const em_cloud* clouds, int32_t co
     cells += pad_tile(map_cells(b->uniq[u]));
     key.ray |= md[u].ray_step > 0.f;
     key.drift |= md[u].drift_flat > 0.f;
+    key.overlap |= md[u].ovl_dz > 0.f;
     key.stencils |= map_flags(b->uniq[u]) & (EM_F_NORMALS | EM_F_SMOOTH | EM_F_MEDIAN | EM_F_GAUSS | EM_F_INPAINT);
   }
   // clouds ordered by map (stable), so each map's points are contiguous
@@ -199,7 +203,11 @@ int prepare(em_batch* b, em_map* const* maps, const em_cloud* clouds, int32_t co
   for (int u = 0; u < nm; ++u)
     for (int i = 0, first = 1; i < count; ++i) {
       if (b->map_of[i] != u) continue;
-      if (first) md[u].z_ref = clouds[i].pose[11];  // the map's first cloud, as in em_update_multi
+      if (first) {  // the map's first cloud's sensor origin, as in em_update_multi
+        md[u].z_ref = clouds[i].pose[11];
+        md[u].ref_x = clouds[i].pose[3];
+        md[u].ref_y = clouds[i].pose[7];
+      }
       first = 0;
       CloudDev& c = cd[ci++];
       memset(&c, 0, sizeof(c));

@@ -98,6 +98,8 @@ struct MapDev {
   int32_t W, H, ox, oy;
   float x0, y0, res, inv_res;  // inv_res = 1 / res rounded to float
   float drift_flat;    // drift compensation: flat iff previous normal n_z >= this; 0 = off
+  float excl_b, excl_c, excl_tan, excl_d;  // exclusion ramp (tan of its angle); excl_d <= 0 = off
+  float ovl_r2, ovl_dz, ref_x, ref_y;      // overlap clearance: radius^2, height gap, robot position
   float z_ref;         // reference height of empty cells in the fusion sums: the z of the
                        // first cloud's sensor origin (any fixed value gives the same result
                        // up to rounding; one near the points keeps the terms small)
@@ -152,6 +154,7 @@ cudaError_t launch_alloc(const BatchDev* b, int64_t n_cells, cudaStream_t s);
 cudaError_t launch_scatter(const BatchDev* b, int64_t n_points, cudaStream_t s);
 cudaError_t launch_fuse(const BatchDev* b, int64_t n_points, int chunk, cudaStream_t s);
 cudaError_t launch_clear(const BatchDev* b, int64_t n_cells, cudaStream_t s);
+cudaError_t launch_overlap(const BatchDev* b, int64_t n_cells, cudaStream_t s);
 cudaError_t launch_normals(const BatchDev* b, int64_t n_cells, cudaStream_t s);
 cudaError_t launch_smooth(const BatchDev* b, int64_t n_cells, cudaStream_t s);
 cudaError_t launch_inpaint(const BatchDev* b, int64_t n_cells, cudaStream_t s);

@@ -156,6 +156,11 @@ extern "C" int em_update_noalloc(const em_params* params, int64_t shift_x, int64
   m->alpha_n = params->cleanup_normal_thresh; m->wall = params->wall_num_thresh;
   m->min_age = params->cleanup_min_age;
   m->drift_flat = params->drift_flatness;
+  m->excl_b = params->excl_b; m->excl_c = params->excl_c; m->excl_d = params->excl_d;
+  m->excl_tan = (float)std::tan((double)params->excl_theta);
+  m->ovl_r2 = params->overlap_radius * params->overlap_radius; m->ovl_dz = params->overlap_dz;
+  m->ref_x = clouds[0].pose[3];
+  m->ref_y = clouds[0].pose[7];
   int64_t begin = 0;
   for (int i = 0; i < n_clouds; ++i) {
     cd[i].pts = clouds[i].points;
@@ -201,5 +206,6 @@ extern "C" int em_update_noalloc(const em_params* params, int64_t shift_x, int64
     if (e == cudaSuccess) e = launch_fuse(bd, total, 256, s);
   }
   if (e == cudaSuccess) e = launch_clear(bd, cells, s);
+  if (e == cudaSuccess && params->overlap_dz > 0.f) e = launch_overlap(bd, cells, s);
   return na_status(e, "em_update_noalloc launch");
 }

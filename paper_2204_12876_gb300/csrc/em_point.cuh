@@ -35,6 +35,14 @@ __device__ __forceinline__ PointGeom point_geom(const MapDev& m, const CloudDev&
   g.z = __fadd_rn(g.vz, c.t[2]);
   g.ix = clamp_floor(__fmul_rn(__fsub_rn(g.x, m.x0), m.inv_res));
   g.iy = clamp_floor(__fmul_rn(__fsub_rn(g.y, m.y0), m.inv_res));
+  // exclusion area (Section II-C): a point above the ramp over its horizontal
+  // distance r from the sensor is ignored (counted as out of range)
+  if (g.in_range && m.excl_d > 0.f) {
+    const float r = __fsqrt_rn(__fmaf_rn(g.vx, g.vx, __fmul_rn(g.vy, g.vy)));
+    float lim = r <= m.excl_c ? m.excl_b : __fmaf_rn(__fsub_rn(r, m.excl_c), m.excl_tan, m.excl_b);
+    lim = fminf(lim, m.excl_d);
+    if (g.vz > lim) g.in_range = false;
+  }
   return g;
 }
 

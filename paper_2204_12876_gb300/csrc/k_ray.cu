@@ -246,6 +246,36 @@ cudaError_t launch_ray(const BatchDev* b, int64_t n_points, int group, cudaStrea
   return cudaGetLastError();
 }
 
+// Overlap clearance (Section II-F): after the update, an estimate whose cell
+// centre lies within overlap_radius of the robot (the first cloud's sensor
+// origin) and whose height is more than overlap_dz from the robot's belongs to
+// another floor and is removed.
+__global__ void __launch_bounds__(kClearThreads) k_overlap(const BatchDev* __restrict__ bp) {
+  const BatchDev& b = *bp;
+  for_each_tile(b, [&](const MapDev& m, int, int32_t p0, int32_t count) {
+    if (m.ovl_dz <= 0.f) return;
+    for (int32_t i = threadIdx.x; i < count; i += kClearThreads) {
+      const int32_t p = p0 + i;
+      if (!isfinite(m.var[p])) continue;
+      int32_t lx, ly;
+      logical_of(m, p, lx, ly);
+      const float cx = __fsub_rn(__fmaf_rn(__fadd_rn((float)lx, 0.5f), m.res, m.x0), m.ref_x);
+      const float cy = __fsub_rn(__fmaf_rn(__fadd_rn((float)ly, 0.5f), m.res, m.y0), m.ref_y);
+      if (__fmaf_rn(cx, cx, __fmul_rn(cy, cy)) <= m.ovl_r2 && fabsf(__fsub_rn(m.h[p], m.z_ref)) > m.ovl_dz) {
+        m.h[p] = __int_as_float(0x7fc00000);
+        m.var[p] = __int_as_float(0x7f800000);
+      }
+    }
+  });
+}
+
+cudaError_t launch_overlap(const BatchDev* b, int64_t n_cells, cudaStream_t s) {
+  const int64_t tiles = n_cells / kTile;
+  const int64_t cap = (int64_t)sm_count() * 8;
+  k_overlap<<<(int)(tiles < 1 ? 1 : tiles < cap ? tiles : cap), kClearThreads, 0, s>>>(b);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_clear(const BatchDev* b, int64_t n_cells, cudaStream_t s) {
   const int64_t tiles = n_cells / kTile;
   const int64_t cap = (int64_t)sm_count() * 8;

@@ -23,10 +23,11 @@ F_NORMALS, F_SMOOTH, F_INPAINT, F_MEDIAN, F_GAUSS, F_UPPER, F_TRACE = 1, 2, 4, 8
 LAYER_ELEVATION, LAYER_VARIANCE, LAYER_TIME = 1, 2, 4
 LAYER_NORMAL_X, LAYER_NORMAL_Y, LAYER_NORMAL_Z = 8, 16, 32
 LAYER_SMOOTH, LAYER_INPAINT, LAYER_VALID, LAYER_VARIANCE_NOW, LAYER_UPPER = 64, 128, 256, 512, 1024
-PROF_SLOTS = ("count", "ray", "alloc", "scatter", "fuse", "clear", "normals", "smooth", "inpaint", "drift")
+PROF_SLOTS = ("count", "ray", "alloc", "scatter", "fuse", "clear", "normals", "smooth", "inpaint", "drift",
+              "overlap")
 KERNEL_NAMES = {"count": "k_count", "ray": "k_ray", "alloc": "k_alloc", "scatter": "k_scatter", "fuse": "k_fuse",
                 "clear": "k_clear", "normals": "k_normals", "smooth": "k_smooth", "inpaint": "k_inpaint",
-                "drift": "k_drift"}
+                "drift": "k_drift", "overlap": "k_overlap"}
 LAYER_NAMES = {LAYER_ELEVATION: "h", LAYER_VARIANCE: "var", LAYER_TIME: "t_last", LAYER_NORMAL_X: "nx",
                LAYER_NORMAL_Y: "ny", LAYER_NORMAL_Z: "nz", LAYER_SMOOTH: "smooth", LAYER_INPAINT: "inpaint",
                LAYER_VALID: "valid", LAYER_VARIANCE_NOW: "var_now", LAYER_UPPER: "upper"}
@@ -46,7 +47,9 @@ class _Params(ctypes.Structure):
                 ("wall_num_thresh", ctypes.c_int32), ("time_variance", ctypes.c_float),
                 ("ray_step", ctypes.c_float), ("cleanup_min_age", ctypes.c_int32),
                 ("cleanup_normal_thresh", ctypes.c_float), ("flags", ctypes.c_uint32),
-                ("drift_flatness", ctypes.c_float)]
+                ("drift_flatness", ctypes.c_float), ("excl_b", ctypes.c_float), ("excl_c", ctypes.c_float),
+                ("excl_theta", ctypes.c_float), ("excl_d", ctypes.c_float), ("overlap_radius", ctypes.c_float),
+                ("overlap_dz", ctypes.c_float)]
 
 
 class _Cloud(ctypes.Structure):
@@ -139,6 +142,12 @@ class Params:
     cleanup_normal_thresh: float = 0.0
     flags: int = 0
     drift_flatness: float = 0.0
+    excl_b: float = 0.0
+    excl_c: float = 0.0
+    excl_theta: float = 0.0
+    excl_d: float = 0.0
+    overlap_radius: float = 0.0
+    overlap_dz: float = 0.0
 
     def _c(self) -> _Params:
         return _Params(**{f.name: getattr(self, f.name) for f in fields(self)})

@@ -313,6 +313,31 @@ def test_drift_compensation_depth_frame(em):
     check_counts(gm, tr, cmp.notes["marginal_points"])
 
 
+def test_exclusion_area_and_overlap_clearance(em):
+    """A LiDAR frame with the exclusion ramp (points high above the sensor are
+    ignored) and overlap clearance (estimates near the robot far from its height
+    are removed), both on the readings stated in em.h."""
+    P = dict(LIDAR_P, flags=0, cleanup_normal_thresh=0.0, excl_b=0.2, excl_c=2.0, excl_theta=0.15,
+             excl_d=0.8, overlap_radius=2.0, overlap_dz=1.0)
+    frames = synth.lidar_stream(seed=5, frames=2)
+    f0 = next(frames)
+    f1 = next(frames)
+    om = oracle.OracleMap(parity.oracle_params(P))
+    om.update(f0["clouds"])
+    prior = parity.oracle_state_as_prior(om)
+    # another floor under the robot: a few cells near it, far below its height
+    x0, y0 = om.origin()
+    ox, oy = float(f1["clouds"][0][1][3]), float(f1["clouds"][0][1][7])
+    ix, iy = int((ox - x0) / 0.04), int((oy - y0) / 0.04)
+    prior["h"][iy - 10:iy + 10:3, ix - 10:ix + 10:3] = -2.5
+    prior["var"][iy - 10:iy + 10:3, ix - 10:ix + 10:3] = 1e-4
+    cmp, tr, gm, _ = run_case(em, P, f1["clouds"], prior=prior, stencils=())
+    n_valid_raw = int(np.isfinite(f1["clouds"][0][0]).all(axis=1).sum())
+    assert tr.counts["valid"] < n_valid_raw - 1000           # the ramp excluded points
+    assert cmp.notes["cleared"] >= 40                        # the other floor was cleared
+    check_counts(gm, tr, cmp.notes["marginal_points"])
+
+
 def test_depth_stream_frame_by_frame(em):
     """Frames of the depth-camera stream with recentring shifts; each frame
     starts both sides from the oracle's previous state (float32)."""
