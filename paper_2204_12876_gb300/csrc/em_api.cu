@@ -472,13 +472,14 @@ static int update_impl(em_map* m, const em_cloud* clouds, int32_t n_clouds, cuda
     return slot;
   }
   const int64_t ncell = pad_tile((int64_t)m->p.width * m->p.height);
-  EM_TRY(timed(m, EM_PROF_COUNT, s, [&] { return launch_bin(bd, total, ncell, s); }), "k_count");
+  const bool ext = m->p.excl_d > 0.f || (m->p.flags & EM_F_UPPER);  // kernels with the extended features
+  EM_TRY(timed(m, EM_PROF_COUNT, s, [&] { return launch_bin(bd, total, ncell, ext, s); }), "k_count");
   if (m->p.drift_flatness > 0.f)
-    EM_TRY(timed(m, EM_PROF_DRIFT, s, [&] { return launch_drift(bd, ncell, s); }), "k_drift");
+    EM_TRY(timed(m, EM_PROF_DRIFT, s, [&] { return launch_drift(bd, total, ncell, ext, s); }), "k_drift");
   if (total > 0) {
-    if (m->p.ray_step > 0.f) EM_TRY(timed(m, EM_PROF_RAY, s, [&] { return launch_ray(bd, total, m->ray_group, s); }), "k_ray");
+    if (m->p.ray_step > 0.f) EM_TRY(timed(m, EM_PROF_RAY, s, [&] { return launch_ray(bd, total, m->ray_group, ext, s); }), "k_ray");
     EM_TRY(timed(m, EM_PROF_ALLOC, s, [&] { return launch_alloc(bd, ncell, s); }), "k_alloc");
-    EM_TRY(timed(m, EM_PROF_SCATTER, s, [&] { return launch_scatter(bd, total, s); }), "k_scatter");
+    EM_TRY(timed(m, EM_PROF_SCATTER, s, [&] { return launch_scatter(bd, total, ext, s); }), "k_scatter");
     EM_TRY(timed(m, EM_PROF_FUSE, s, [&] { return launch_fuse(bd, total, m->fuse_chunk, s); }), "k_fuse");
   }
   EM_TRY(timed(m, EM_PROF_CLEAR, s, [&] { return launch_clear(bd, ncell, s); }), "k_clear");

@@ -42,10 +42,11 @@ struct GraphKey {
   bool ray;
   bool drift;
   bool overlap;
+  bool ext;  // some map uses the exclusion area or the upper-bound layer
   uint32_t stencils;
   bool operator==(const GraphKey& o) const {
     return t.ray_group == o.t.ray_group && t.fuse_chunk == o.t.fuse_chunk && t.big_thresh == o.t.big_thresh &&
-           ray == o.ray && drift == o.drift && overlap == o.overlap && stencils == o.stencils;
+           ray == o.ray && drift == o.drift && overlap == o.overlap && ext == o.ext && stencils == o.stencils;
   }
 };
 
@@ -113,13 +114,13 @@ int prof_collect(em_batch* b) {
 cudaError_t launch_sequence(const BatchDev* bd, int64_t grid_points, int64_t grid_cells, const GraphKey& k,
                             cudaStream_t s, em_batch* prof = nullptr) {
   cudaError_t e = cudaSuccess;
-  e = timed(prof, EM_PROF_COUNT, s, [&] { return launch_bin(bd, grid_points, grid_cells, s); });
-  if (e == cudaSuccess && k.drift) e = timed(prof, EM_PROF_DRIFT, s, [&] { return launch_drift(bd, grid_cells, s); });
+  e = timed(prof, EM_PROF_COUNT, s, [&] { return launch_bin(bd, grid_points, grid_cells, k.ext, s); });
+  if (e == cudaSuccess && k.drift) e = timed(prof, EM_PROF_DRIFT, s, [&] { return launch_drift(bd, grid_points, grid_cells, k.ext, s); });
   if (grid_points > 0) {
     if (e == cudaSuccess && k.ray)
-      e = timed(prof, EM_PROF_RAY, s, [&] { return launch_ray(bd, grid_points, k.t.ray_group, s); });
+      e = timed(prof, EM_PROF_RAY, s, [&] { return launch_ray(bd, grid_points, k.t.ray_group, k.ext, s); });
     if (e == cudaSuccess) e = timed(prof, EM_PROF_ALLOC, s, [&] { return launch_alloc(bd, grid_cells, s); });
-    if (e == cudaSuccess) e = timed(prof, EM_PROF_SCATTER, s, [&] { return launch_scatter(bd, grid_points, s); });
+    if (e == cudaSuccess) e = timed(prof, EM_PROF_SCATTER, s, [&] { return launch_scatter(bd, grid_points, k.ext, s); });
     if (e == cudaSuccess)
       e = timed(prof, EM_PROF_FUSE, s, [&] { return launch_fuse(bd, grid_points, k.t.fuse_chunk, s); });
   }
@@ -186,7 +187,7 @@ int prepare(em_batch* b, em_map* const* maps, const em_cloud* clouds, int32_t co
   MapDev* md = reinterpret_cast<MapDev*>(hb + sizeof(BatchDev));
   CloudDev* cd = reinterpret_cast<CloudDev*>(hb + sizeof(BatchDev) + (size_t)b->max_maps * sizeof(MapDev));
   memset(bd, 0, sizeof(BatchDev));
-  GraphKey key{tune, false, false, false, 0u};
+  GraphKey key{tune, false, false, false, false, 0u};
   int64_t cells = 0;
   for (int u = 0; u < nm; ++u) {
     md[u] = map_begin_update(b->uniq[u], map_pts[u]);
@@ -195,6 +196,7 @@ int prepare(em_batch* b, em_map* const* maps, const em_cloud* clouds, int32_t co
     key.ray |= md[u].ray_step > 0.f;
     key.drift |= md[u].drift_flat > 0.f;
     key.overlap |= md[u].ovl_dz > 0.f;
+    key.ext |= md[u].excl_d > 0.f || md[u].upper != nullptr;
     key.stencils |= map_flags(b->uniq[u]) & (EM_F_NORMALS | EM_F_SMOOTH | EM_F_MEDIAN | EM_F_GAUSS | EM_F_INPAINT);
   }
   // clouds ordered by map (stable), so each map's points are contiguous

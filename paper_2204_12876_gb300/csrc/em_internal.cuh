@@ -147,11 +147,12 @@ inline int64_t pad_tile(int64_t cells) { return (cells + kTile - 1) / kTile * kT
 int sm_count();
 
 // ---- launchers (each returns cudaGetLastError() of its launches)
-cudaError_t launch_bin(const BatchDev* b, int64_t n_points, int64_t n_cells, cudaStream_t s);
-cudaError_t launch_drift(const BatchDev* b, int64_t n_cells, cudaStream_t s);
-cudaError_t launch_ray(const BatchDev* b, int64_t n_points, int group, cudaStream_t s);
+// ext: some map of the batch uses the exclusion area or the upper-bound layer
+cudaError_t launch_bin(const BatchDev* b, int64_t n_points, int64_t n_cells, bool ext, cudaStream_t s);
+cudaError_t launch_drift(const BatchDev* b, int64_t n_points, int64_t n_cells, bool ext, cudaStream_t s);
+cudaError_t launch_ray(const BatchDev* b, int64_t n_points, int group, bool ext, cudaStream_t s);
 cudaError_t launch_alloc(const BatchDev* b, int64_t n_cells, cudaStream_t s);
-cudaError_t launch_scatter(const BatchDev* b, int64_t n_points, cudaStream_t s);
+cudaError_t launch_scatter(const BatchDev* b, int64_t n_points, bool ext, cudaStream_t s);
 cudaError_t launch_fuse(const BatchDev* b, int64_t n_points, int chunk, cudaStream_t s);
 cudaError_t launch_clear(const BatchDev* b, int64_t n_cells, cudaStream_t s);
 cudaError_t launch_overlap(const BatchDev* b, int64_t n_cells, cudaStream_t s);

@@ -197,12 +197,13 @@ extern "C" int em_update_noalloc(const em_params* params, int64_t shift_x, int64
                  "cudaMemsetAsync");
   if (rc) return rc;
   const int64_t cells = pad_tile(ncell);
-  cudaError_t e = launch_bin(bd, total, cells, s);
-  if (e == cudaSuccess && params->drift_flatness > 0.f) e = launch_drift(bd, cells, s);
+  const bool ext = params->excl_d > 0.f;  // no upper-bound layer here
+  cudaError_t e = launch_bin(bd, total, cells, ext, s);
+  if (e == cudaSuccess && params->drift_flatness > 0.f) e = launch_drift(bd, total, cells, ext, s);
   if (total > 0) {
-    if (e == cudaSuccess && params->ray_step > 0.f) e = launch_ray(bd, total, 4, s);
+    if (e == cudaSuccess && params->ray_step > 0.f) e = launch_ray(bd, total, 4, ext, s);
     if (e == cudaSuccess) e = launch_alloc(bd, cells, s);
-    if (e == cudaSuccess) e = launch_scatter(bd, total, s);
+    if (e == cudaSuccess) e = launch_scatter(bd, total, ext, s);
     if (e == cudaSuccess) e = launch_fuse(bd, total, 256, s);
   }
   if (e == cudaSuccess) e = launch_clear(bd, cells, s);

@@ -20,6 +20,10 @@ struct PointGeom {
 
 // Transform by the sensor pose (Section II-A), distance, cell indices
 // ix = floor((x - x0) / r) of the robot-centric grid (as (x - x0) * (1/r)).
+// kExt: kernels built for batches that use the exclusion area or the upper-bound
+// layer; the others carry none of that code (every kernel of one update is
+// launched with the same kExt, so they all agree on which points are valid).
+template <bool kExt>
 __device__ __forceinline__ PointGeom point_geom(const MapDev& m, const CloudDev& c, float px, float py,
                                                 float pz) {
   PointGeom g;
@@ -37,7 +41,7 @@ __device__ __forceinline__ PointGeom point_geom(const MapDev& m, const CloudDev&
   g.iy = clamp_floor(__fmul_rn(__fsub_rn(g.y, m.y0), m.inv_res));
   // exclusion area (Section II-C): a point above the ramp over its horizontal
   // distance r from the sensor is ignored (counted as out of range)
-  if (g.in_range && m.excl_d > 0.f) {
+  if (kExt && g.in_range && m.excl_d > 0.f) {
     const float r = __fsqrt_rn(__fmaf_rn(g.vx, g.vx, __fmul_rn(g.vy, g.vy)));
     float lim = r <= m.excl_c ? m.excl_b : __fmaf_rn(__fsub_rn(r, m.excl_c), m.excl_tan, m.excl_b);
     lim = fminf(lim, m.excl_d);

@@ -51,7 +51,7 @@ struct RaySetup {
 // (transform, distance, own cell, the k range inside the map box and before
 // the point), then the warp marches them G lanes per ray, 32 / G rays at a
 // time, so the set-up cost is paid once per ray.
-template <int G>
+template <int G, bool kExt>
 __global__ void __launch_bounds__(kRayThreads) k_ray(const BatchDev* __restrict__ bp) {
   __shared__ RaySetup s_ray[kRayThreads];
   const BatchDev& b = *bp;
@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(kRayThreads) k_ray(const BatchDev* __restrict_
       if (m.ray_step > 0.f) {
         float px, py, pz;
         load_point(c, g - c.begin, px, py, pz);
-        const PointGeom pg = point_geom(m, c, px, py, pz);
+        const PointGeom pg = point_geom<kExt>(m, c, px, py, pz);
         // clip the sample range to the map box (conservative by 1 mm + 1 step)
         float lo = 0.f, hi = pg.d;
         const float ext_x = __fmul_rn((float)m.W, m.res), ext_y = __fmul_rn((float)m.H, m.res);
@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(kRayThreads) k_ray(const BatchDev* __restrict_
           int32_t py = cy + oy;
           py -= (py >= H) ? H : 0;
           const int32_t p = py * W + px;
-          if (!isfinite(m.var[p])) {
+          if (kExt && !isfinite(m.var[p])) {
             // an empty cell (its threshold is the upper bound): the sample lowers
             // the bound (Section II-H); float minimum through the ordered bits
             const float z = zz[u];
@@ -228,21 +228,26 @@ __global__ void __launch_bounds__(kClearThreads) k_clear(const BatchDev* __restr
   flush_counters(b, mc, idx, 1);
 }
 
-cudaError_t launch_ray(const BatchDev* b, int64_t n_points, int group, cudaStream_t s) {
+template <bool kExt>
+static void launch_ray_g(const BatchDev* b, int g, int grid, cudaStream_t s) {
+  switch (g) {
+    case 1: k_ray<1, kExt><<<grid, kRayThreads, 0, s>>>(b); break;
+    case 2: k_ray<2, kExt><<<grid, kRayThreads, 0, s>>>(b); break;
+    case 8: k_ray<8, kExt><<<grid, kRayThreads, 0, s>>>(b); break;
+    case 16: k_ray<16, kExt><<<grid, kRayThreads, 0, s>>>(b); break;
+    case 32: k_ray<32, kExt><<<grid, kRayThreads, 0, s>>>(b); break;
+    default: k_ray<4, kExt><<<grid, kRayThreads, 0, s>>>(b); break;
+  }
+}
+
+cudaError_t launch_ray(const BatchDev* b, int64_t n_points, int group, bool ext, cudaStream_t s) {
   if (n_points <= 0) return cudaSuccess;
   const int g = (group == 1 || group == 2 || group == 4 || group == 8 || group == 16 || group == 32) ? group : 4;
   const int64_t want = (n_points + kRayThreads - 1) / kRayThreads;  // one 32-ray chunk per warp
   const int64_t cap = (int64_t)sm_count() * 16;
   const int grid = (int)(want < cap ? want : cap);
-  switch (g) {
-    case 1: k_ray<1><<<grid, kRayThreads, 0, s>>>(b); break;
-    case 2: k_ray<2><<<grid, kRayThreads, 0, s>>>(b); break;
-    case 4: k_ray<4><<<grid, kRayThreads, 0, s>>>(b); break;
-    case 8: k_ray<8><<<grid, kRayThreads, 0, s>>>(b); break;
-    case 32: k_ray<32><<<grid, kRayThreads, 0, s>>>(b); break;
-    case 16: k_ray<16><<<grid, kRayThreads, 0, s>>>(b); break;
-    default: k_ray<4><<<grid, kRayThreads, 0, s>>>(b); break;
-  }
+  if (ext) launch_ray_g<true>(b, g, grid, s);
+  else launch_ray_g<false>(b, g, grid, s);
   return cudaGetLastError();
 }
 

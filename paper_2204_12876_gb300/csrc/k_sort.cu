@@ -90,6 +90,7 @@ __device__ __forceinline__ float ray_threshold(const MapDev& m, int32_t p, float
   return __fsub_rn(h, __fsqrt_rn(var_eff(m, var, m.t_last[p])));
 }
 
+template <bool kExt>
 __global__ void __launch_bounds__(kPointThreads) k_count(const BatchDev* __restrict__ bp) {
   __shared__ float4 stage[kPointThreads / 32][24];
   const BatchDev& b = *bp;
@@ -114,10 +115,6 @@ __global__ void __launch_bounds__(kPointThreads) k_count(const BatchDev* __restr
   block_range(b.n_points, beg, end);
   MapCounters mc;
   const int idx[2] = {kStValid, kStInMap};
-  // drift compensation sums of this lane (Section II-D), for map dmap
-  int dmap = -1;
-  long long dh = 0;
-  unsigned long long dl = 0, dn = 0;
   for (int64_t wbase = beg + warp * 32; wbase < end; wbase += kPointThreads) {
     float px, py, pz;
     const int ci = load_warp_points(b, wbase, end, stage[warp], px, py, pz);
@@ -125,7 +122,7 @@ __global__ void __launch_bounds__(kPointThreads) k_count(const BatchDev* __restr
     const bool live = g < end;
     const CloudDev& c = b.clouds[ci];
     const MapDev& m = b.maps[c.map];
-    const PointGeom pg = point_geom(m, c, px, py, pz);
+    const PointGeom pg = point_geom<kExt>(m, c, px, py, pz);
     const bool inm = live && pg.in_range && in_map(m, pg.ix, pg.iy);
     const int32_t key = inm ? phys_index(m, pg.ix, pg.iy) : -1;
     if (live) {
@@ -141,23 +138,71 @@ __global__ void __launch_bounds__(kPointThreads) k_count(const BatchDev* __restr
     int head, run;
     key_runs(tag, head, run);
     if (inm && lane == head) atomicAdd(&m.cnt[key], run);
-    // the point's error against a flat cell holding an estimate (previous normal
-    // n_z >= drift_flatness; a NaN normal is not flat), summed exactly
-    if (inm && m.drift_flat > 0.f && isfinite(m.var[key]) && m.nz[key] >= m.drift_flat) {
-      if (c.map != dmap) {
-        if (dmap >= 0) drift_add(b.maps[dmap], dh, dl, dn);
-        dmap = c.map;
-        dh = 0;
-        dl = dn = 0;
-      }
-      const Fix e = to_fix(__fsub_rn(pg.z, m.h[key]));
-      dh += e.h;
-      dl += e.l;
-      ++dn;
-    }
   }
   flush_counters(b, mc, idx, 2);
-  // drift sums: a warp sum when the warp's lanes hold one map (the usual case)
+  // ray thresholds of the pre-update map over the cell space (Eq. 3)
+  for_each_tile(b, [&](const MapDev& m, int, int32_t p0, int32_t count) {
+    if (m.ray_step <= 0.f || m.drift_flat > 0.f) return;  // with drift: k_drift, after the shift
+    for (int32_t i = threadIdx.x; i < count; i += kPointThreads) {
+      const int32_t p = p0 + i;
+      // an empty cell is never penetrated (-inf); with the upper-bound layer it holds
+      // the cell's bound instead, so a ray sample below the bound takes the march's
+      // candidate path and lowers it (Section II-H)
+      const float var = m.var[p];
+      float t;
+      if (kExt) {
+        t = ray_threshold(m, p, isfinite(var) ? m.h[p] : 0.f, var);
+      } else {  // no upper-bound layer in this batch: an empty cell is never penetrated
+        t = __int_as_float(0xff800000);
+        if (isfinite(var)) t = __fsub_rn(m.h[p], __fsqrt_rn(var_eff(m, var, m.t_last[p])));
+      }
+      int32_t lx, ly;
+      logical_of(m, p, lx, ly);
+      m.thr[ly * m.W + lx] = t;  // logical layout: the ray march indexes it without the ring wrap
+    }
+  });
+}
+
+// Drift-compensation sums (Section II-D): per point of a map with drift
+// compensation, its error against a flat cell holding an estimate (previous
+// normal n_z >= drift_flatness; a NaN normal is not flat), summed exactly per map.
+template <bool kExt>
+__global__ void __launch_bounds__(kPointThreads) k_drift_sum(const BatchDev* __restrict__ bp) {
+  __shared__ float4 stage[kPointThreads / 32][24];
+  const BatchDev& b = *bp;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int64_t beg, end;
+  block_range(b.n_points, beg, end);
+  int dmap = -1;
+  long long dh = 0;
+  unsigned long long dl = 0, dn = 0;
+  for (int64_t wbase = beg + warp * 32; wbase < end; wbase += kPointThreads) {
+    const int c0 = find_cloud(b.clouds, b.n_clouds, wbase);
+    const int c1 = find_cloud(b.clouds, b.n_clouds, wbase + 31 < end ? wbase + 31 : end - 1);
+    if (c0 == c1 && b.maps[b.clouds[c0].map].drift_flat <= 0.f) continue;  // a whole warp without drift
+    float px, py, pz;
+    const int ci = load_warp_points(b, wbase, end, stage[warp], px, py, pz);
+    const int64_t g = wbase + lane;
+    const CloudDev& c = b.clouds[ci];
+    const MapDev& m = b.maps[c.map];
+    const PointGeom pg = point_geom<kExt>(m, c, px, py, pz);
+    if (g < end && m.drift_flat > 0.f && pg.in_range && in_map(m, pg.ix, pg.iy)) {
+      const int32_t key = phys_index(m, pg.ix, pg.iy);
+      if (isfinite(m.var[key]) && m.nz[key] >= m.drift_flat) {
+        if (c.map != dmap) {
+          if (dmap >= 0) drift_add(b.maps[dmap], dh, dl, dn);
+          dmap = c.map;
+          dh = 0;
+          dl = dn = 0;
+        }
+        const Fix e = to_fix(__fsub_rn(pg.z, m.h[key]));
+        dh += e.h;
+        dl += e.l;
+        ++dn;
+      }
+    }
+  }
+  // a warp sum when the warp's lanes hold one map (the usual case)
   const int d0 = __shfl_sync(kFull, dmap, 0);
   if (__all_sync(kFull, dmap == d0 || dn == 0)) {
     for (int o = 16; o > 0; o >>= 1) {
@@ -169,21 +214,6 @@ __global__ void __launch_bounds__(kPointThreads) k_count(const BatchDev* __restr
   } else if (dmap >= 0 && dn) {
     drift_add(b.maps[dmap], dh, dl, dn);
   }
-  // ray thresholds of the pre-update map over the cell space (Eq. 3)
-  for_each_tile(b, [&](const MapDev& m, int, int32_t p0, int32_t count) {
-    if (m.ray_step <= 0.f || m.drift_flat > 0.f) return;  // with drift: k_drift, after the shift
-    for (int32_t i = threadIdx.x; i < count; i += kPointThreads) {
-      const int32_t p = p0 + i;
-      // an empty cell is never penetrated (-inf); with the upper-bound layer it holds
-      // the cell's bound instead, so a ray sample below the bound takes the march's
-      // candidate path and lowers it (Section II-H)
-      const float var = m.var[p];
-      const float t = ray_threshold(m, p, isfinite(var) ? m.h[p] : 0.f, var);
-      int32_t lx, ly;
-      logical_of(m, p, lx, ly);
-      m.thr[ly * m.W + lx] = t;  // logical layout: the ray march indexes it without the ring wrap
-    }
-  });
 }
 
 // Height drift compensation (Section II-D): every estimate moves by the mean
@@ -305,20 +335,25 @@ __global__ void __launch_bounds__(kCellThreads) k_alloc(const BatchDev* __restri
   }
 }
 
-__global__ void __launch_bounds__(kPointThreads) k_scatter(const BatchDev* __restrict__ bp) {
+// Warps take the point space in waves (warp w: points (w + k W) 32 .. + 31, W
+// the warps of the grid), so at any moment the grid writes the records of one
+// stretch of points -- one or two maps -- and their sectors fill up in L2
+// before they are written back.
+template <bool kExt>
+__global__ void __launch_bounds__(kPointThreads, 6) k_scatter(const BatchDev* __restrict__ bp) {
   __shared__ float4 stage[kPointThreads / 32][24];
   const BatchDev& b = *bp;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int64_t beg, end;
-  block_range(b.n_points, beg, end);
-  for (int64_t wbase = beg + warp * 32; wbase < end; wbase += kPointThreads) {
+  const int64_t end = b.n_points;
+  for (int64_t wbase = ((int64_t)blockIdx.x * (kPointThreads / 32) + warp) * 32; wbase < end;
+       wbase += (int64_t)gridDim.x * kPointThreads) {
     float px, py, pz;
     const int ci = load_warp_points(b, wbase, end, stage[warp], px, py, pz);
     const int64_t g = wbase + lane;
     const bool live = g < end;
     const CloudDev& c = b.clouds[ci];
     const MapDev& m = b.maps[c.map];
-    const PointGeom pg = point_geom(m, c, px, py, pz);
+    const PointGeom pg = point_geom<kExt>(m, c, px, py, pz);
     const bool inm = live && pg.in_range && in_map(m, pg.ix, pg.iy);
     const int32_t key = inm ? phys_index(m, pg.ix, pg.iy) : -1;
     const unsigned long long tag = inm ? ((unsigned long long)(uint32_t)c.map << 32) | (uint32_t)key : ~0ull;
@@ -374,15 +409,18 @@ static int tile_grid(int64_t n_cells) {
   return g < 1 ? 1 : (int)g;
 }
 
-cudaError_t launch_bin(const BatchDev* b, int64_t n_points, int64_t n_cells, cudaStream_t s) {
+cudaError_t launch_bin(const BatchDev* b, int64_t n_points, int64_t n_cells, bool ext, cudaStream_t s) {
   const int64_t tiles = n_cells / kTile;
   int grid = point_grid(n_points);
   if (grid < tiles && tiles < (int64_t)sm_count() * 8) grid = (int)tiles;  // enough blocks for the cell pass
-  k_count<<<grid, kPointThreads, 0, s>>>(b);
+  if (ext) k_count<true><<<grid, kPointThreads, 0, s>>>(b);
+  else k_count<false><<<grid, kPointThreads, 0, s>>>(b);
   return cudaGetLastError();
 }
 
-cudaError_t launch_drift(const BatchDev* b, int64_t n_cells, cudaStream_t s) {
+cudaError_t launch_drift(const BatchDev* b, int64_t n_points, int64_t n_cells, bool ext, cudaStream_t s) {
+  if (n_points > 0 && ext) k_drift_sum<true><<<point_grid(n_points), kPointThreads, 0, s>>>(b);
+  if (n_points > 0 && !ext) k_drift_sum<false><<<point_grid(n_points), kPointThreads, 0, s>>>(b);
   k_drift<<<tile_grid(n_cells), kPointThreads, 0, s>>>(b);
   return cudaGetLastError();
 }
@@ -392,9 +430,10 @@ cudaError_t launch_alloc(const BatchDev* b, int64_t n_cells, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_scatter(const BatchDev* b, int64_t n_points, cudaStream_t s) {
+cudaError_t launch_scatter(const BatchDev* b, int64_t n_points, bool ext, cudaStream_t s) {
   if (n_points <= 0) return cudaSuccess;
-  k_scatter<<<point_grid(n_points), kPointThreads, 0, s>>>(b);
+  if (ext) k_scatter<true><<<point_grid(n_points), kPointThreads, 0, s>>>(b);
+  else k_scatter<false><<<point_grid(n_points), kPointThreads, 0, s>>>(b);
   return cudaGetLastError();
 }
 
