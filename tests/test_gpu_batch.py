@@ -11,9 +11,10 @@ from tests import parity
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-BASE = dict(resolution=0.04, noise_a0=0.005, noise_a2=0.002, mahalanobis_k=2.5, outlier_variance=1e-4,
-            ray_step=0.04)
-SHAPES = [(37, 51, 0), (100, 100, 1), (200, 64, 0), (120, 120, 1 | 2 | 4)]
+BASE = dict(resolution=0.04, noise_a0=0.005, noise_a2=0.002, mahalanobis_k=2.5, outlier_variance=1e-4)
+# (width, height, flags, ray step): one batch mixes ray steps of one, two and
+# two and a half cells
+SHAPES = [(37, 51, 0, 0.04), (100, 100, 1, 0.1), (200, 64, 0, 0.04), (120, 120, 1 | 2 | 4, 0.08)]
 
 
 @pytest.fixture(scope="module")
@@ -30,8 +31,8 @@ def dev(a):
 
 def make_maps(em, seed):
     maps, pairs = [], []
-    for j, (w, h, flags) in enumerate(SHAPES):
-        m = em.Map(em.Params(width=w, height=h, flags=flags, **BASE))
+    for j, (w, h, flags, step) in enumerate(SHAPES):
+        m = em.Map(em.Params(width=w, height=h, flags=flags, ray_step=step, **BASE))
         prior = synth.random_prior(seed=seed + j, width=w, height=h, t_now=5)
         parity.prior_to_gpu(m, prior)
         m.shift(j, -j)

@@ -260,6 +260,19 @@ def test_visibility_depth_frame(em):
     assert st["cells_cleared"] >= cmp.notes["cleared"] - cmp.notes["mark_marginal_cells"]
 
 
+@pytest.mark.parametrize("step", [0.02, 0.08, 0.1])
+def test_visibility_ray_step(em, step):
+    """The same frame marched at half a cell, two cells and 2.5 cells per step:
+    samples skip cells, and a ray's consecutive samples may share a cell."""
+    fr = next(synth.depth_stream(seed=2, frames=1))
+    prior = synth.random_prior(seed=3, width=200, height=200, t_now=5, obstacle_frac=0.05)
+    P = dict(DEPTH_P, ray_step=step)
+    cmp, tr, gm, _ = run_case(em, P, fr["clouds"][:2], prior=prior)
+    assert cmp.notes["cleared"] > 20
+    check_counts(gm, tr, cmp.notes["marginal_points"])
+    assert gm.stats()["ray_samples"] > 0
+
+
 def test_upper_bound_layer_depth_frames(em):
     """Section II-H: two depth frames over a prior with empty cells; rays through
     empty cells lower their upper bound, cells that take an estimate lose it.
