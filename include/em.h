@@ -355,6 +355,27 @@ int em_server_submit(em_server* srv, int32_t map_id, const em_cloud* clouds, int
  * completes. */
 int em_server_submit_after(em_server* srv, int32_t map_id, const em_cloud* clouds, int32_t n_clouds,
                            void* ready, uint64_t* ticket);
+/* One request of em_server_submit_many. */
+typedef struct em_request {
+  int32_t map_id;
+  int32_t n_clouds;          /* 1..8 */
+  const em_cloud* clouds;    /* device points, valid until the ticket finishes */
+  uint32_t read_mask;        /* EM_LAYER_* bits to read back right after the update; 0 = none */
+  int32_t read_to_host;      /* read_dst is page-locked host memory (else device memory) */
+  float* read_dst;           /* popcount(read_mask) * width * height floats, em_get_layers layout */
+} em_request;
+
+/* Queue n requests under one lock, so that those that fit reach the same batch;
+ * each first waits for `ready` (a cudaEvent_t recorded after the points were
+ * written, or NULL).  A request with read_mask != 0 gets its map's layers
+ * written to read_dst on the batch's stream right after its update (the map
+ * state the update produced); its ticket finishes once they have landed.  A
+ * host read_dst must be page-locked (cudaHostAlloc, cudaHostRegister): the GPU
+ * writes it directly.  All or nothing: EM_ERR_INVALID_ARG for a malformed
+ * request (pageable or unknown read_dst memory included) and EM_ERR_REJECTED
+ * for one that can never fit leave nothing queued; else tickets[i] is request
+ * i's ticket. */
+int em_server_submit_many(em_server* srv, const em_request* reqs, int32_t n, void* ready, uint64_t* tickets);
 /* Wait for a ticket (timeout_us < 0: forever); EM_ERR_TIMEOUT when it has not
  * finished in time (the request stays queued).  Fills *out and forgets the
  * ticket once finished. */

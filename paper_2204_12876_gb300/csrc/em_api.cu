@@ -363,6 +363,12 @@ int map_copy_state(em_map* dst, const em_map* src, cudaStream_t s) {
 
 int map_record_error(const char* what, cudaError_t e) { return cuda_status(e, what); }
 
+int map_read_layers(em_map* m, uint32_t mask, float* dst, cudaStream_t s) {
+  EM_TRY(launch_layers_out(make_mapdev(m), mask, dst, s), "k_layers_out");
+  m->last_stream = s;
+  return EM_OK;
+}
+
 }  // namespace em
 
 extern "C" {

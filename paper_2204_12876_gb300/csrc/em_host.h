@@ -23,6 +23,10 @@ void map_undo_update(em_map* m, int64_t points);
 // Copy layers, ring offsets, shift and update index of src into dst (same size).
 int map_copy_state(em_map* dst, const em_map* src, cudaStream_t s);
 
+// Write the layers in mask (em_get_layers layout) to dst, a pointer the device
+// can write (device memory or mapped page-locked host memory), on stream s.
+int map_read_layers(em_map* m, uint32_t mask, float* dst, cudaStream_t s);
+
 // Record a CUDA error for em_last_cuda_error() and map it to a status code.
 int map_record_error(const char* what, cudaError_t e);
 

@@ -38,6 +38,8 @@ struct Request {
   int64_t points = 0;
   int64_t bytes = 0;
   cudaEvent_t ready = nullptr;  // the caller's "points written" event, or null
+  uint32_t read_mask = 0;       // layers to write to read_dst after the update
+  float* read_dst = nullptr;    // device-writable address (device or mapped host memory)
   ReqState state = kPending;
   em_result res{};
 };
@@ -147,9 +149,12 @@ bool worker_pass(em_server* s, std::unique_lock<std::mutex>& lk) {
       em_map* m = s->maps[r.map_id];
       std::vector<em_cloud> cl = r.clouds;
       cudaEvent_t ready = r.ready;
+      const uint32_t read_mask = r.read_mask;
+      float* read_dst = r.read_dst;
       lk.unlock();
       if (ready) cudaStreamWaitEvent(s->streams[0], ready, 0);
       int rc = em_update_multi(m, cl.data(), (int32_t)cl.size(), (em_stream_t)s->streams[0]);
+      if (rc == EM_OK && read_mask) rc = map_read_layers(m, read_mask, read_dst, s->streams[0]);
       if (rc == EM_OK) cudaEventRecord(f.ev, s->streams[0]);
       lk.lock();
       s->st.batches += 1;
@@ -186,10 +191,12 @@ bool worker_pass(em_server* s, std::unique_lock<std::mutex>& lk) {
       std::vector<em_map*> pm;
       std::vector<em_cloud> pc;
       std::vector<cudaEvent_t> ready;
+      std::vector<std::pair<em_map*, Request*>> reads;
       const int64_t t0 = now_ns();
       for (uint64_t tk : take) {
         Request& r = s->reqs[tk];
         if (r.ready) ready.push_back(r.ready);
+        if (r.read_mask) reads.emplace_back(s->maps[r.map_id], &r);
         r.state = kRunning;
         r.res.t_start_ns = t0;
         r.res.batch_size = (int32_t)take.size();
@@ -208,6 +215,10 @@ bool worker_pass(em_server* s, std::unique_lock<std::mutex>& lk) {
       lk.unlock();
       for (cudaEvent_t e : ready) cudaStreamWaitEvent(s->streams[si], e, 0);
       int rc = em_update_batch(s->batches[si], pm.data(), pc.data(), (int32_t)pc.size(), (em_stream_t)s->streams[si]);
+      // read-backs after the whole batch (the requests stay in reqs while running,
+      // and unordered_map references survive other insertions)
+      for (size_t i = 0; i < reads.size() && rc == EM_OK; ++i)
+        rc = map_read_layers(reads[i].first, reads[i].second->read_mask, reads[i].second->read_dst, s->streams[si]);
       if (rc == EM_OK) cudaEventRecord(f.ev, s->streams[si]);
       lk.lock();
       if (rc != EM_OK) {
@@ -332,38 +343,77 @@ int em_server_submit(em_server* s, int32_t map_id, const em_cloud* clouds, int32
 
 int em_server_submit_after(em_server* s, int32_t map_id, const em_cloud* clouds, int32_t n_clouds, void* ready,
                            uint64_t* ticket) {
-  if (!s || !clouds || n_clouds < 1 || n_clouds > 8 || !ticket) return EM_ERR_INVALID_ARG;
-  int64_t pts = 0;
-  for (int i = 0; i < n_clouds; ++i) {
-    const em_cloud& c = clouds[i];
-    if (c.n < 0 || (c.stride != 3 && c.stride != 4) || (c.n > 0 && !c.points)) return EM_ERR_INVALID_ARG;
-    pts += c.n;
+  if (!ticket) return EM_ERR_INVALID_ARG;
+  em_request r{};
+  r.map_id = map_id;
+  r.n_clouds = n_clouds;
+  r.clouds = clouds;
+  return em_server_submit_many(s, &r, 1, ready, ticket);
+}
+
+int em_server_submit_many(em_server* s, const em_request* reqs, int32_t n, void* ready, uint64_t* tickets) {
+  if (!s || !reqs || n < 1 || !tickets) return EM_ERR_INVALID_ARG;
+  std::vector<int64_t> pts(n, 0);
+  std::vector<float*> dst(n, nullptr);
+  for (int32_t q = 0; q < n; ++q) {
+    const em_request& r = reqs[q];
+    if (!r.clouds || r.n_clouds < 1 || r.n_clouds > 8) return EM_ERR_INVALID_ARG;
+    for (int i = 0; i < r.n_clouds; ++i) {
+      const em_cloud& c = r.clouds[i];
+      if (c.n < 0 || (c.stride != 3 && c.stride != 4) || (c.n > 0 && !c.points)) return EM_ERR_INVALID_ARG;
+      pts[q] += c.n;
+    }
+    if (r.read_mask) {
+      if ((r.read_mask >> 11) || !r.read_dst) return EM_ERR_INVALID_ARG;
+      // the GPU writes the read-back itself: device memory, or page-locked host
+      // memory mapped into the device's address space
+      cudaPointerAttributes a{};
+      if (cudaPointerGetAttributes(&a, r.read_dst) != cudaSuccess) {
+        cudaGetLastError();
+        return EM_ERR_INVALID_ARG;
+      }
+      const bool host = a.type == cudaMemoryTypeHost;
+      const bool devmem = a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+      if ((r.read_to_host != 0) != host || !(host || devmem) || !a.devicePointer) return EM_ERR_INVALID_ARG;
+      if (devmem && a.device != s->cfg.device) return EM_ERR_INVALID_ARG;
+      dst[q] = static_cast<float*>(a.devicePointer);
+    }
   }
   std::lock_guard<std::mutex> lk(s->mu);
-  if (map_id < 0 || map_id >= (int32_t)s->maps.size()) return EM_ERR_INVALID_ARG;
-  s->st.submitted += 1;
-  const int64_t bytes = pts * kRecordBytes;
   const int64_t maps_bytes = [&] {
     int64_t t = 0;
     for (int64_t b : s->map_bytes) t += b;
     return t;
   }();
-  if (pts > s->cfg.max_batch_points || s->fixed_bytes + maps_bytes + bytes > s->cfg.budget_bytes) {
-    s->st.rejected += 1;
-    return EM_ERR_REJECTED;
+  for (int32_t q = 0; q < n; ++q) {
+    if (reqs[q].map_id < 0 || reqs[q].map_id >= (int32_t)s->maps.size()) return EM_ERR_INVALID_ARG;
   }
-  const uint64_t tk = s->next_ticket++;
-  Request& r = s->reqs[tk];
-  r.map_id = map_id;
-  r.clouds.assign(clouds, clouds + n_clouds);
-  r.points = pts;
-  r.bytes = bytes;
-  r.ready = (cudaEvent_t)ready;
-  r.res.map_id = map_id;
-  r.res.points = pts;
-  r.res.t_submit_ns = now_ns();
-  s->pending.push_back(tk);
-  *ticket = tk;
+  for (int32_t q = 0; q < n; ++q) {
+    if (pts[q] > s->cfg.max_batch_points || s->fixed_bytes + maps_bytes + pts[q] * kRecordBytes > s->cfg.budget_bytes) {
+      s->st.submitted += 1;
+      s->st.rejected += 1;
+      return EM_ERR_REJECTED;
+    }
+  }
+  const int64_t t_submit = now_ns();
+  for (int32_t q = 0; q < n; ++q) {
+    const em_request& in = reqs[q];
+    s->st.submitted += 1;
+    const uint64_t tk = s->next_ticket++;
+    Request& r = s->reqs[tk];
+    r.map_id = in.map_id;
+    r.clouds.assign(in.clouds, in.clouds + in.n_clouds);
+    r.points = pts[q];
+    r.bytes = pts[q] * kRecordBytes;
+    r.ready = (cudaEvent_t)ready;
+    r.read_mask = in.read_mask;
+    r.read_dst = dst[q];
+    r.res.map_id = in.map_id;
+    r.res.points = pts[q];
+    r.res.t_submit_ns = t_submit;
+    s->pending.push_back(tk);
+    tickets[q] = tk;
+  }
   s->cv_work.notify_one();
   return EM_OK;
 }

@@ -411,6 +411,11 @@ class _Result(ctypes.Structure):
                 ("t_done_ns", ctypes.c_int64)]
 
 
+class _Request(ctypes.Structure):
+    _fields_ = [("map_id", ctypes.c_int32), ("n_clouds", ctypes.c_int32), ("clouds", ctypes.POINTER(_Cloud)),
+                ("read_mask", ctypes.c_uint32), ("read_to_host", ctypes.c_int32), ("read_dst", ctypes.c_void_p)]
+
+
 class _ServerStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "completed", "rejected", "cancelled", "batches",
                                              "batched_requests", "max_batch_size", "bytes_in_use", "peak_bytes",
@@ -426,6 +431,8 @@ def _bind_server():
         "em_server_submit": ([vp, i32, ctypes.POINTER(_Cloud), i32, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
         "em_server_submit_after": ([vp, i32, ctypes.POINTER(_Cloud), i32, vp, ctypes.POINTER(ctypes.c_uint64)],
                                    ctypes.c_int),
+        "em_server_submit_many": ([vp, ctypes.POINTER(_Request), i32, vp, ctypes.POINTER(ctypes.c_uint64)],
+                                  ctypes.c_int),
         "em_server_wait": ([vp, ctypes.c_uint64, i64, ctypes.POINTER(_Result)], ctypes.c_int),
         "em_server_cancel": ([vp, ctypes.c_uint64], ctypes.c_int),
         "em_server_drain": ([vp, i64], ctypes.c_int),
@@ -501,6 +508,36 @@ class Server:
                                               ctypes.byref(tk)), "em_server_submit_after")
         self._keep[tk.value] = (clouds, ready)
         return tk.value
+
+    def submit_many(self, requests, ready=None) -> list:
+        """requests: [(map_id, [(points CUDA tensor, pose), ...], read), ...] with read None or
+        (layer_mask, out): out a contiguous float32 tensor (CUDA, or pinned CPU memory) that
+        receives the map's layers right after this update.  One call queues them all (they
+        reach the same batch when they fit); ready as in submit.  Returns the tickets."""
+        n = len(requests)
+        reqs = (_Request * n)()
+        keep = []
+        for q, (map_id, clouds, read) in enumerate(requests):
+            arr = (_Cloud * len(clouds))(*[_cloud_struct(p, pose, False) for p, pose in clouds])
+            keep.append((arr, clouds, read))
+            reqs[q].map_id = int(map_id)
+            reqs[q].n_clouds = len(clouds)
+            reqs[q].clouds = arr
+            if read is not None:
+                mask, out = read
+                if out.dtype.__str__() != "torch.float32" or not out.is_contiguous():
+                    raise ValueError("read-back buffer must be a contiguous float32 tensor")
+                if not out.is_cuda and not out.is_pinned():
+                    raise ValueError("a host read-back buffer must be pinned memory")
+                reqs[q].read_mask = int(mask)
+                reqs[q].read_to_host = 0 if out.is_cuda else 1
+                reqs[q].read_dst = out.data_ptr()
+        tks = (ctypes.c_uint64 * n)()
+        _check(lib.em_server_submit_many(self._h, reqs, n, ready.cuda_event if ready is not None else None, tks),
+               "em_server_submit_many")
+        for q in range(n):
+            self._keep[tks[q]] = (keep[q], ready)
+        return list(tks)
 
     def wait(self, ticket: int, timeout_us: int = -1) -> dict:
         r = _Result()

@@ -53,7 +53,7 @@ def test_struct_layout_matches_header(tmp_path, lib_path):
     src = tmp_path / "layout.c"
     structs = {"em_params": em._Params, "em_cloud": em._Cloud, "em_info": em._Info, "em_stats": em._Stats,
                "em_tuning": em._Tuning, "em_server_cfg": em._ServerCfg, "em_result": em._Result,
-               "em_server_stats": em._ServerStats}
+               "em_server_stats": em._ServerStats, "em_request": em._Request}
     consts = {"EM_OK": em.EM_OK, "EM_ERR_INVALID_ARG": em.EM_ERR_INVALID_ARG, "EM_ERR_OOM": em.EM_ERR_OOM,
               "EM_ERR_CUDA": em.EM_ERR_CUDA, "EM_ERR_TIMEOUT": em.EM_ERR_TIMEOUT,
               "EM_ERR_REJECTED": em.EM_ERR_REJECTED, "EM_ERR_BUSY": em.EM_ERR_BUSY,
