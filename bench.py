@@ -250,14 +250,14 @@ def run_ours(args, rank: int, world: int):
     round_pts = sum(len(request_cloud(pools, robots, i, 0)[0]) for i in range(N_ROBOTS))
 
     def new_server(mode):
-        srv = em.Server(budget_bytes=BUDGET, max_slots=4096, n_streams=args.streams, max_batch_maps=N_ROBOTS,
+        srv = em.Server(budget_bytes=BUDGET, max_slots=4096, n_streams=args.streams, max_batch_maps=args.batch_maps,
                         max_batch_points=N_ROBOTS * 262144, max_map_cells=500 * 500, mode=mode, graph=True,
                         device=dev)
         ids = [srv.add_map(em.Params(**r["params"])) for r in robots]
         return srv, ids
 
     def submit_round(srv, ids, k):
-        return [srv.submit(ids[i], [request_cloud(dpools, robots, i, k)]) for i in range(N_ROBOTS)]
+        return srv.submit_many([(ids[i], [request_cloud(dpools, robots, i, k)], None) for i in range(N_ROBOTS)])
 
     def saturate(srv, ids, K, k0):
         """K rounds submitted at once; returns (seconds, points, batches).  The
@@ -271,8 +271,7 @@ def run_ours(args, rank: int, world: int):
         tickets = []
         for k in range(K):
             tickets += submit_round(srv, ids, k0 + k)
-        for t in tickets:
-            srv.wait(t)
+        srv.wait_many(tickets)
         e1.record()
         barrier()
         sec = e0.elapsed_time(e1) / 1e3
@@ -282,8 +281,7 @@ def run_ours(args, rank: int, world: int):
     # on one round (scratch copies of the maps: the served maps do not advance)
     served, sids = new_server(em.SERVE_BATCHED)
     for k in range(args.warmup):
-        for t in submit_round(served, sids, k):
-            served.wait(t)
+        served.wait_many(submit_round(served, sids, k))
     served.drain()
     tuner = em.Batch(max_maps=N_ROBOTS, max_clouds=N_ROBOTS, max_points=N_ROBOTS * 262144, max_cells=500 * 500,
                      graph=False, device=dev)
@@ -299,8 +297,7 @@ def run_ours(args, rank: int, world: int):
     # ---- plain per-request path at saturation (fresh maps)
     plain, pids = new_server(em.SERVE_PLAIN)
     for k in range(args.warmup):
-        for t in submit_round(plain, pids, k):
-            plain.wait(t)
+        plain.wait_many(submit_round(plain, pids, k))
     psec, ppts, _ = saturate(plain, pids, K, args.warmup)
     plain_value = job_rate(ppts, world, psec)
 
@@ -412,8 +409,7 @@ def run_ours(args, rank: int, world: int):
     pending = e2e_launch(0)
     for k in range(1, e2e_rounds + 1):
         nxt = e2e_launch(k) if k < e2e_rounds else []
-        for t in pending:  # round k - 1: every map's elevation is now in host_out[(k - 1) % 2]
-            served.wait(t)
+        served.wait_many(pending)  # round k - 1: every map's elevation is now in host_out[(k - 1) % 2]
         pending = nxt
     barrier()
     e2e_s = max_over_ranks(time.perf_counter() - t0)
@@ -434,7 +430,8 @@ def run_ours(args, rank: int, world: int):
         "dtype": "f32",
         "data": "synthetic: seeded depth-camera and LiDAR clouds (pools of 8 and 2 clouds cycled), seeded terrain",
         "config": {"workload": WORKLOAD, "robots": N_ROBOTS, "points_per_step": round_pts,
-                   "step": "one round = one request per robot", "streams": args.streams, "tuning": tuning,
+                   "step": "one round = one request per robot", "streams": args.streams,
+                   "batch_maps": args.batch_maps, "tuning": tuning,
                    "l2": "inputs + map state per step > L2 (about 65 MB of clouds + 200 MB of maps), no flush",
                    "parallelism": f"replicas{world}"},
         "updates_per_s": K * N_ROBOTS * world / sec,
@@ -665,7 +662,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--streams", type=int, default=2, help="batches in flight in the served path")
+    ap.add_argument("--streams", type=int, default=3, help="batches in flight in the served path")
+    ap.add_argument("--batch-maps", type=int, default=16, help="maps per batch in the served path")
     ap.add_argument("--load-seconds", type=float, default=4.0, help="duration of the Poisson-load phase")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

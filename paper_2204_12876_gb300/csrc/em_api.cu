@@ -9,6 +9,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <cmath>
 #include <new>
 
@@ -366,6 +367,21 @@ int map_record_error(const char* what, cudaError_t e) { return cuda_status(e, wh
 int map_read_layers(em_map* m, uint32_t mask, float* dst, cudaStream_t s) {
   EM_TRY(launch_layers_out(make_mapdev(m), mask, dst, s), "k_layers_out");
   m->last_stream = s;
+  return EM_OK;
+}
+
+int maps_read_layers(em_map* const* maps, const uint32_t* masks, float* const* dst, int n, cudaStream_t s) {
+  ReadJobs jobs;
+  for (int i0 = 0; i0 < n; i0 += kMaxReadJobs) {
+    jobs.n = std::min(kMaxReadJobs, n - i0);
+    for (int i = 0; i < jobs.n; ++i) {
+      jobs.job[i].m = make_mapdev(maps[i0 + i]);
+      jobs.job[i].mask = masks[i0 + i];
+      jobs.job[i].dst = dst[i0 + i];
+      maps[i0 + i]->last_stream = s;
+    }
+    EM_TRY(launch_layers_out_multi(jobs, s), "k_layers_out_multi");
+  }
   return EM_OK;
 }
 

@@ -270,11 +270,15 @@ int run_graph(em_batch* b, const Prepared& p, cudaStream_t s) {
     cudaError_t le = launch_sequence(p.bd, b->max_points, (int64_t)b->max_maps * pad_tile(b->max_cells), p.key,
                                      b->capture_stream);
     cudaError_t ce = cudaStreamEndCapture(b->capture_stream, &g);
-    if (le != cudaSuccess) {
+    if (le != cudaSuccess || ce != cudaSuccess) {
+      // Another thread can break a capture (a device-wide synchronize while it
+      // runs invalidates it).  The sequence then runs without a graph this
+      // time, and the next update of this kind tries the capture again.
       if (g) cudaGraphDestroy(g);
-      return map_record_error("capture launches", le);
+      cudaGetLastError();
+      EB_TRY(launch_sequence(p.bd, p.points, p.cells, p.key, s), "launch (capture failed)");
+      return EM_OK;
     }
-    EB_TRY(ce, "end capture");
     cudaGraphExec_t ex = nullptr;
     cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
     cudaGraphDestroy(g);

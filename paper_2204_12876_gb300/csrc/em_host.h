@@ -26,6 +26,8 @@ int map_copy_state(em_map* dst, const em_map* src, cudaStream_t s);
 // Write the layers in mask (em_get_layers layout) to dst, a pointer the device
 // can write (device memory or mapped page-locked host memory), on stream s.
 int map_read_layers(em_map* m, uint32_t mask, float* dst, cudaStream_t s);
+// The same for n maps, kMaxReadJobs per launch.
+int maps_read_layers(em_map* const* maps, const uint32_t* masks, float* const* dst, int n, cudaStream_t s);
 
 // Record a CUDA error for em_last_cuda_error() and map it to a status code.
 int map_record_error(const char* what, cudaError_t e);

@@ -161,6 +161,19 @@ cudaError_t launch_smooth(const BatchDev* b, int64_t n_cells, cudaStream_t s);
 cudaError_t launch_inpaint(const BatchDev* b, int64_t n_cells, cudaStream_t s);
 cudaError_t launch_shift_clear(const MapDev& m, int32_t dx, int32_t dy, cudaStream_t s);
 cudaError_t launch_layers_out(const MapDev& m, uint32_t mask, float* dst, cudaStream_t s);
+// Layer reads of up to kMaxReadJobs maps in one launch (the jobs are the kernel parameters).
+constexpr int kMaxReadJobs = 32;
+struct ReadJob {
+  MapDev m;
+  uint32_t mask;
+  float* dst;
+};
+struct ReadJobs {
+  int n;
+  ReadJob job[kMaxReadJobs];
+};
+cudaError_t launch_layers_out_multi(const ReadJobs& jobs, cudaStream_t s);
+static_assert(sizeof(ReadJobs) <= 32000, "the read jobs must fit a kernel's parameter block");
 cudaError_t launch_layers_in(const MapDev& m, uint32_t mask, const float* src, cudaStream_t s);
 cudaError_t launch_fill_map(const MapDev& m, cudaStream_t s);
 

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 #include <string.h>
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -40,13 +41,17 @@ struct Request {
   cudaEvent_t ready = nullptr;  // the caller's "points written" event, or null
   uint32_t read_mask = 0;       // layers to write to read_dst after the update
   float* read_dst = nullptr;    // device-writable address (device or mapped host memory)
+  float* read_host = nullptr;   // the caller's host address when read_dst is host memory
+  int64_t read_floats = 0;
   ReqState state = kPending;
   em_result res{};
 };
 
 struct Flight {
   bool busy = false;
-  cudaEvent_t ev = nullptr;
+  bool holds_maps = false;      // its maps are released once ev_maps has passed
+  cudaEvent_t ev = nullptr;     // everything done (read-backs landed): tickets complete
+  cudaEvent_t ev_maps = nullptr;  // updates and layer reads done: the maps may take new updates
   std::vector<uint64_t> tickets;
   std::vector<int32_t> maps;
   int64_t bytes = 0;
@@ -65,6 +70,8 @@ struct em_server {
   std::vector<char> blocked;  // batch-builder scratch, one flag per map
   std::vector<cudaStream_t> streams;
   std::vector<em_batch*> batches;
+  std::vector<float*> stage;  // per batch stream: layer reads bound for host memory land here first
+  int64_t stage_cap = 0;      // floats per stage buffer
   std::vector<Flight> flights;            // batched: one per stream; plain: grows as needed
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
@@ -108,7 +115,9 @@ void complete(em_server* s, Flight& f, int status) {
     s->slots_in_use -= 1;
     s->st.completed += 1;
   }
-  for (int32_t m : f.maps) s->map_busy[m] = 0;
+  if (f.holds_maps)
+    for (int32_t m : f.maps) s->map_busy[m] = 0;
+  f.holds_maps = false;
   f.tickets.clear();
   f.maps.clear();
   f.busy = false;
@@ -120,6 +129,11 @@ bool worker_pass(em_server* s, std::unique_lock<std::mutex>& lk) {
   // completions (cudaEventQuery does not block)
   for (Flight& f : s->flights) {
     if (!f.busy) continue;
+    if (f.holds_maps && f.ev_maps && cudaEventQuery(f.ev_maps) == cudaSuccess) {
+      // the maps are read: later updates may run while the read-backs travel
+      for (int32_t m : f.maps) s->map_busy[m] = 0;
+      f.holds_maps = false;
+    }
     cudaError_t q = cudaEventQuery(f.ev);
     if (q == cudaErrorNotReady) continue;
     complete(s, f, q == cudaSuccess ? EM_OK : map_record_error("request", q));
@@ -191,12 +205,29 @@ bool worker_pass(em_server* s, std::unique_lock<std::mutex>& lk) {
       std::vector<em_map*> pm;
       std::vector<em_cloud> pc;
       std::vector<cudaEvent_t> ready;
-      std::vector<std::pair<em_map*, Request*>> reads;
+      // layer reads: host-bound ones through this stream's stage buffer while it
+      // has room (then copied by DMA after the maps are released), others direct
+      std::vector<em_map*> rmaps;
+      std::vector<uint32_t> rmasks;
+      std::vector<float*> rdst;
+      struct Staged { float* host; int64_t off, floats; };
+      std::vector<Staged> staged;
+      int64_t stage_used = 0;
       const int64_t t0 = now_ns();
       for (uint64_t tk : take) {
         Request& r = s->reqs[tk];
         if (r.ready) ready.push_back(r.ready);
-        if (r.read_mask) reads.emplace_back(s->maps[r.map_id], &r);
+        if (r.read_mask) {
+          rmaps.push_back(s->maps[r.map_id]);
+          rmasks.push_back(r.read_mask);
+          if (r.read_host && stage_used + r.read_floats <= s->stage_cap) {
+            rdst.push_back(s->stage[si] + stage_used);
+            staged.push_back({r.read_host, stage_used, r.read_floats});
+            stage_used += r.read_floats;
+          } else {
+            rdst.push_back(r.read_dst);
+          }
+        }
         r.state = kRunning;
         r.res.t_start_ns = t0;
         r.res.batch_size = (int32_t)take.size();
@@ -207,6 +238,7 @@ bool worker_pass(em_server* s, std::unique_lock<std::mutex>& lk) {
         s->map_busy[r.map_id] = 1;
       }
       f.busy = true;
+      f.holds_maps = true;
       f.tickets = take;
       f.maps = bmaps;
       s->st.batches += 1;
@@ -215,10 +247,14 @@ bool worker_pass(em_server* s, std::unique_lock<std::mutex>& lk) {
       lk.unlock();
       for (cudaEvent_t e : ready) cudaStreamWaitEvent(s->streams[si], e, 0);
       int rc = em_update_batch(s->batches[si], pm.data(), pc.data(), (int32_t)pc.size(), (em_stream_t)s->streams[si]);
-      // read-backs after the whole batch (the requests stay in reqs while running,
-      // and unordered_map references survive other insertions)
-      for (size_t i = 0; i < reads.size() && rc == EM_OK; ++i)
-        rc = map_read_layers(reads[i].first, reads[i].second->read_mask, reads[i].second->read_dst, s->streams[si]);
+      if (rc == EM_OK && !rmaps.empty())
+        rc = maps_read_layers(rmaps.data(), rmasks.data(), rdst.data(), (int)rmaps.size(), s->streams[si]);
+      if (rc == EM_OK) cudaEventRecord(f.ev_maps, s->streams[si]);
+      for (size_t i = 0; i < staged.size() && rc == EM_OK; ++i) {
+        cudaError_t ce = cudaMemcpyAsync(staged[i].host, s->stage[si] + staged[i].off, staged[i].floats * sizeof(float),
+                                         cudaMemcpyDeviceToHost, s->streams[si]);
+        if (ce != cudaSuccess) rc = map_record_error("read-back copy", ce);
+      }
       if (rc == EM_OK) cudaEventRecord(f.ev, s->streams[si]);
       lk.lock();
       if (rc != EM_OK) {
@@ -287,13 +323,25 @@ int em_server_create(const em_server_cfg* cfg, em_server** out) {
       }
       Flight f;
       if (rc == EM_OK && cudaEventCreateWithFlags(&f.ev, cudaEventDisableTiming) != cudaSuccess) rc = EM_ERR_CUDA;
+      if (rc == EM_OK && cudaEventCreateWithFlags(&f.ev_maps, cudaEventDisableTiming) != cudaSuccess) rc = EM_ERR_CUDA;
       s->flights.push_back(f);
+      // one layer of every map of a full batch, at most 64 MiB (reads that do not
+      // fit are written to their destination directly)
+      s->stage_cap = std::min<int64_t>((int64_t)cfg->max_batch_maps * cfg->max_map_cells, int64_t(1) << 24);
+      float* st = nullptr;
+      if (rc == EM_OK && cudaMalloc((void**)&st, (size_t)s->stage_cap * sizeof(float)) != cudaSuccess) rc = EM_ERR_OOM;
+      s->stage.push_back(st);
+      if (rc == EM_OK) s->fixed_bytes += s->stage_cap * (int64_t)sizeof(float);
     }
   }
   if (rc == EM_OK && s->fixed_bytes > cfg->budget_bytes) rc = EM_ERR_REJECTED;
   if (rc != EM_OK) {
     for (em_batch* b : s->batches) em_batch_destroy(b);
-    for (Flight& f : s->flights) if (f.ev) cudaEventDestroy(f.ev);
+    for (Flight& f : s->flights) {
+      if (f.ev) cudaEventDestroy(f.ev);
+      if (f.ev_maps) cudaEventDestroy(f.ev_maps);
+    }
+    for (float* st : s->stage) cudaFree(st);
     for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
     delete s;
     return rc;
@@ -408,6 +456,9 @@ int em_server_submit_many(em_server* s, const em_request* reqs, int32_t n, void*
     r.ready = (cudaEvent_t)ready;
     r.read_mask = in.read_mask;
     r.read_dst = dst[q];
+    r.read_host = in.read_mask && in.read_to_host ? in.read_dst : nullptr;
+    if (in.read_mask)
+      r.read_floats = (int64_t)__builtin_popcount(in.read_mask) * map_cells(s->maps[in.map_id]);
     r.res.map_id = in.map_id;
     r.res.points = pts[q];
     r.res.t_submit_ns = t_submit;
@@ -431,6 +482,28 @@ int em_server_wait(em_server* s, uint64_t ticket, int64_t timeout_us, em_result*
   }
   if (out) *out = s->reqs[ticket].res;
   s->reqs.erase(ticket);
+  return EM_OK;
+}
+
+int em_server_wait_many(em_server* s, const uint64_t* tickets, int32_t n, int64_t timeout_us, em_result* out) {
+  if (!s || n < 0 || (n > 0 && !tickets)) return EM_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lk(s->mu);
+  for (int32_t i = 0; i < n; ++i)
+    if (s->reqs.find(tickets[i]) == s->reqs.end()) return EM_ERR_INVALID_ARG;
+  auto done = [&] {
+    for (int32_t i = 0; i < n; ++i)
+      if (s->reqs[tickets[i]].state != kDone) return false;
+    return true;
+  };
+  if (timeout_us < 0) {
+    s->cv_done.wait(lk, done);
+  } else if (!s->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), done)) {
+    return EM_ERR_TIMEOUT;
+  }
+  for (int32_t i = 0; i < n; ++i) {
+    if (out) out[i] = s->reqs[tickets[i]].res;
+    s->reqs.erase(tickets[i]);
+  }
   return EM_OK;
 }
 
@@ -509,8 +582,11 @@ int em_server_destroy(em_server* s) {
   cudaSetDevice(s->cfg.device);
   for (cudaStream_t st : s->streams) cudaStreamSynchronize(st);
   for (em_batch* b : s->batches) em_batch_destroy(b);
-  for (Flight& f : s->flights)
+  for (Flight& f : s->flights) {
     if (f.ev) cudaEventDestroy(f.ev);
+    if (f.ev_maps) cudaEventDestroy(f.ev_maps);
+  }
+  for (float* st : s->stage) cudaFree(st);
   for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
   for (em_map* m : s->maps) em_destroy(m);
   delete s;

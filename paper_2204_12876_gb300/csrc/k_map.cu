@@ -11,6 +11,8 @@
 // [0, H) does not exist (the ring never wraps a stencil).
 #include <math.h>
 
+#include <algorithm>
+
 #include "em.h"
 #include "em_point.cuh"
 
@@ -234,9 +236,12 @@ enum : uint32_t {
   L_SMOOTH = 1u << 6, L_INPAINT = 1u << 7, L_VALID = 1u << 8, L_VAR_NOW = 1u << 9, L_UPPER = 1u << 10
 };
 
-__global__ void __launch_bounds__(kMapThreads) k_layers_out(MapDev m, uint32_t mask, float* __restrict__ dst) {
+// The layers of one map in mask (ascending bit order, logical row-major), cells
+// c = first, first + stride, ... of the map.
+__device__ __forceinline__ void layers_out(const MapDev& m, uint32_t mask, float* __restrict__ dst, int32_t first,
+                                           int32_t stride) {
   const int32_t ncell = m.W * m.H;
-  for (int32_t c = blockIdx.x * kMapThreads + threadIdx.x; c < ncell; c += gridDim.x * kMapThreads) {
+  for (int32_t c = first; c < ncell; c += stride) {
     const int32_t lx = c % m.W, ly = c / m.W;
     const int32_t p = phys_index(m, lx, ly);
     const bool v = isfinite(m.var[p]);
@@ -261,6 +266,17 @@ __global__ void __launch_bounds__(kMapThreads) k_layers_out(MapDev m, uint32_t m
       ++k;
     }
   }
+}
+
+__global__ void __launch_bounds__(kMapThreads) k_layers_out(MapDev m, uint32_t mask, float* __restrict__ dst) {
+  layers_out(m, mask, dst, blockIdx.x * kMapThreads + threadIdx.x, gridDim.x * kMapThreads);
+}
+
+// Many maps at once: blockIdx.y picks the job (the jobs travel as the kernel's
+// parameter block, so there is nothing to upload).
+__global__ void __launch_bounds__(kMapThreads) k_layers_out_multi(ReadJobs jobs) {
+  const ReadJob& j = jobs.job[blockIdx.y];
+  layers_out(j.m, j.mask, j.dst, blockIdx.x * kMapThreads + threadIdx.x, gridDim.x * kMapThreads);
 }
 
 __global__ void __launch_bounds__(kMapThreads) k_layers_in(MapDev m, uint32_t mask, const float* __restrict__ src) {
@@ -329,6 +345,15 @@ cudaError_t launch_fill_map(const MapDev& m, cudaStream_t s) {
 
 cudaError_t launch_layers_out(const MapDev& m, uint32_t mask, float* dst, cudaStream_t s) {
   k_layers_out<<<cell_grid((int64_t)m.W * m.H), kMapThreads, 0, s>>>(m, mask, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_layers_out_multi(const ReadJobs& jobs, cudaStream_t s) {
+  if (jobs.n <= 0) return cudaSuccess;
+  int64_t most = 1;
+  for (int i = 0; i < jobs.n; ++i) most = std::max(most, (int64_t)jobs.job[i].m.W * jobs.job[i].m.H);
+  const int gx = std::max(1, std::min(cell_grid(most), 2 * sm_count() * 8 / jobs.n));
+  k_layers_out_multi<<<dim3(gx, jobs.n), kMapThreads, 0, s>>>(jobs);
   return cudaGetLastError();
 }
 

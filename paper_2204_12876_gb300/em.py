@@ -434,6 +434,8 @@ def _bind_server():
         "em_server_submit_many": ([vp, ctypes.POINTER(_Request), i32, vp, ctypes.POINTER(ctypes.c_uint64)],
                                   ctypes.c_int),
         "em_server_wait": ([vp, ctypes.c_uint64, i64, ctypes.POINTER(_Result)], ctypes.c_int),
+        "em_server_wait_many": ([vp, ctypes.POINTER(ctypes.c_uint64), i32, i64, ctypes.POINTER(_Result)],
+                                ctypes.c_int),
         "em_server_cancel": ([vp, ctypes.c_uint64], ctypes.c_int),
         "em_server_drain": ([vp, i64], ctypes.c_int),
         "em_server_get_stats": ([vp, ctypes.POINTER(_ServerStats)], ctypes.c_int),
@@ -527,8 +529,6 @@ class Server:
                 mask, out = read
                 if out.dtype.__str__() != "torch.float32" or not out.is_contiguous():
                     raise ValueError("read-back buffer must be a contiguous float32 tensor")
-                if not out.is_cuda and not out.is_pinned():
-                    raise ValueError("a host read-back buffer must be pinned memory")
                 reqs[q].read_mask = int(mask)
                 reqs[q].read_to_host = 0 if out.is_cuda else 1
                 reqs[q].read_dst = out.data_ptr()
@@ -538,6 +538,18 @@ class Server:
         for q in range(n):
             self._keep[tks[q]] = (keep[q], ready)
         return list(tks)
+
+    def wait_many(self, tickets, timeout_us: int = -1, results: bool = False):
+        """Wait for all tickets in one call.  Returns their statuses (or result dicts)."""
+        n = len(tickets)
+        tks = (ctypes.c_uint64 * n)(*tickets)
+        res = (_Result * n)()
+        _check(lib.em_server_wait_many(self._h, tks, n, int(timeout_us), res), "em_server_wait_many")
+        for t in tickets:
+            self._keep.pop(t, None)
+        if results:
+            return [{f: getattr(r, f) for f, _ in _Result._fields_} for r in res]
+        return [r.status for r in res]
 
     def wait(self, ticket: int, timeout_us: int = -1) -> dict:
         r = _Result()

@@ -178,8 +178,9 @@ def test_submit_many_reads_back_each_update(em):
                         torch.full((n,), -7.0, dtype=torch.float32).pin_memory())
         tickets = srv.submit_many([(ids[j], [(dev(pts), pose)], (mask, outs[q]))
                                    for q, (j, pts, pose) in enumerate(reqs)])
-        for t in tickets:
-            assert srv.wait(t)["status"] == 0
+        res = srv.wait_many(tickets, results=True)
+        assert [r["status"] for r in res] == [0] * len(reqs)
+        assert [r["map_id"] for r in res] == [ids[j] for j, _, _ in reqs]
         for q in range(len(reqs)):
             got = outs[q].cpu().numpy() if outs[q].is_cuda else outs[q].numpy()
             assert np.array_equal(got, expect[q], equal_nan=True), (mode, q)
@@ -197,8 +198,9 @@ def test_submit_many_all_or_nothing(em):
         srv.submit_many([(a, [(p, pose)], None), (a + 5, [(p, pose)], None)])
     assert e.value.code == em.EM_ERR_INVALID_ARG
     assert srv.stats()["submitted"] == 0
-    with pytest.raises(ValueError):  # pageable host memory cannot take a GPU-written read-back
+    with pytest.raises(em.EMError) as e:  # pageable host memory cannot take a GPU-written read-back
         srv.submit_many([(a, [(p, pose)], (em.LAYER_ELEVATION, torch.empty(3600)))])
+    assert e.value.code == em.EM_ERR_INVALID_ARG
     # the same through the C ABI directly: the library checks the memory kind itself
     host = np.empty(3600, np.float32)
     req = (em._Request * 1)()
@@ -210,4 +212,24 @@ def test_submit_many_all_or_nothing(em):
     assert srv.stats()["submitted"] == 0
     t = srv.submit_many([(a, [(p, pose)], None)])
     assert srv.wait(t[0])["status"] == 0
+    srv.close()
+
+
+def test_requests_survive_device_synchronize_during_capture(em):
+    """A fresh server captures a CUDA graph for its first batch.  A device-wide
+    synchronize from another thread while that capture runs breaks it; the
+    batch must then run without the graph, so every request still succeeds."""
+    srv = em.Server(budget_bytes=1 << 30, n_streams=2, max_batch_maps=4, max_batch_points=100_000)
+    ids = [srv.add_map(em.Params(width=s, height=s, **BASE)) for s in SIDES[:4]]
+    clouds = [dev(synth.scattered_cloud(400 + j, 20000, 0.5 * SIDES[j] * 0.04)[0]) for j in range(4)]
+    pose = np.eye(3, 4).reshape(12)
+    tickets = srv.submit_many([(ids[j], [(clouds[j], pose)], None) for j in range(4)])
+    errors = 0
+    for _ in range(200):  # races the worker's capture
+        try:
+            torch.cuda.synchronize()
+        except RuntimeError:
+            errors += 1
+    assert all(srv.wait(t)["status"] == 0 for t in tickets)
+    torch.cuda.synchronize()
     srv.close()
