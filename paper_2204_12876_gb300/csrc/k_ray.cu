@@ -200,35 +200,45 @@ __global__ void __launch_bounds__(kRayThreads) k_ray(const BatchDev* __restrict_
 
 constexpr int kClearThreads = 256;
 
+// One warp per tile: a tile of kTile cells is kTile / 32 = 32 mark words, one
+// per lane (marks are rare, so most warps read one word each and leave).
+static_assert(kTile == 32 * 32, "k_clear: one mark word per lane of a tile");
 __global__ void __launch_bounds__(kClearThreads) k_clear(const BatchDev* __restrict__ bp) {
   const BatchDev& b = *bp;
-  MapCounters mc;
-  const int idx[1] = {kStCleared};
-  // a tile of kTile cells is kTile / 32 mark words; one word per thread
-  for_each_tile(b, [&](const MapDev& m, int mi, int32_t p0, int32_t count) {
-    const int32_t min_age = m.min_age > 1 ? m.min_age : 1;
-    const int32_t nword = (count + 31) >> 5;
-    unsigned long long cleared = 0;
-    for (int32_t wi = threadIdx.x; wi < nword; wi += kClearThreads) {
-      const int32_t w = (p0 >> 5) + wi;
+  const int lane = threadIdx.x & 31;
+  const int64_t n_tiles = b.n_cells / kTile;
+  const int64_t n_warps = (int64_t)gridDim.x * (kClearThreads / 32);
+  for (int64_t t = (int64_t)blockIdx.x * (kClearThreads / 32) + (threadIdx.x >> 5); t < n_tiles; t += n_warps) {
+    const int64_t g0 = t * kTile;
+    const int mi = find_map_cell(b.maps, b.n_maps, g0);
+    const MapDev& m = b.maps[mi];
+    const int64_t p0 = g0 - m.cell_begin;
+    const int32_t ncell = m.W * m.H;
+    if (p0 >= ncell) continue;  // padding at the end of a map (warp-uniform)
+    const int32_t end = (int32_t)(ncell - p0 < kTile ? ncell : p0 + kTile);
+    const int32_t w = (int32_t)(p0 >> 5) + lane;
+    uint32_t cleared = 0;
+    if (w * 32 < end) {
       uint32_t bits = m.mark[w];
-      if (!bits) continue;
-      m.mark[w] = 0u;
-      while (bits) {
-        const int bit = __ffs(bits) - 1;
-        bits &= bits - 1;
-        const int32_t p = w * 32 + bit;
-        if (p >= p0 + count) break;
-        if (!isfinite(m.var[p])) continue;
-        if (m.t_now - m.t_last[p] < min_age) continue;
-        m.h[p] = __int_as_float(0x7fc00000);
-        m.var[p] = __int_as_float(0x7f800000);
-        ++cleared;
+      if (bits) {
+        m.mark[w] = 0u;
+        const int32_t min_age = m.min_age > 1 ? m.min_age : 1;
+        while (bits) {
+          const int bit = __ffs(bits) - 1;
+          bits &= bits - 1;
+          const int32_t p = w * 32 + bit;
+          if (p >= end) break;
+          if (!isfinite(m.var[p])) continue;
+          if (m.t_now - m.t_last[p] < min_age) continue;
+          m.h[p] = __int_as_float(0x7fc00000);
+          m.var[p] = __int_as_float(0x7f800000);
+          ++cleared;
+        }
       }
     }
-    add_counter(b, mc, mi, idx, 1, &cleared);
-  });
-  flush_counters(b, mc, idx, 1);
+    const unsigned tot = __reduce_add_sync(0xffffffffu, cleared);
+    if (lane == 0 && tot) atomicAdd(&m.ctl->stats[kStCleared], (unsigned long long)tot);
+  }
 }
 
 template <bool kExt>
@@ -285,9 +295,9 @@ cudaError_t launch_overlap(const BatchDev* b, int64_t n_cells, cudaStream_t s) {
 }
 
 cudaError_t launch_clear(const BatchDev* b, int64_t n_cells, cudaStream_t s) {
-  const int64_t tiles = n_cells / kTile;
+  const int64_t blocks = (n_cells / kTile + kClearThreads / 32 - 1) / (kClearThreads / 32);  // a warp per tile
   const int64_t cap = (int64_t)sm_count() * 8;
-  const int grid = (int)(tiles < 1 ? 1 : tiles < cap ? tiles : cap);
+  const int grid = (int)(blocks < 1 ? 1 : blocks < cap ? blocks : cap);
   k_clear<<<grid, kClearThreads, 0, s>>>(b);
   return cudaGetLastError();
 }
