@@ -41,7 +41,9 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kFuseThreads = 256;
 constexpr int kFuseWarps = kFuseThreads / 32;
 #ifndef EM_FUSE_BLOCKS_PER_SM
-#define EM_FUSE_BLOCKS_PER_SM 3
+// 4 resident blocks (64 registers, a few spilled) measured 5-6 % faster than 3
+// (80 registers, no spills) on both the served round and the 64-map batch
+#define EM_FUSE_BLOCKS_PER_SM 4
 #endif
 constexpr int kFuseBlocksPerSM = EM_FUSE_BLOCKS_PER_SM;  // resident blocks per SM (sets the register budget)
 
