@@ -148,54 +148,112 @@ __global__ void __launch_bounds__(kMapThreads) k_smooth(const BatchDev* __restri
 // is a hole: all its cells take the minimum height of the valid cells
 // 8-adjacent to the component (each cell of the component computes the same
 // value independently, so no labels are needed).
-__global__ void __launch_bounds__(kMapThreads) k_inpaint(const BatchDev* __restrict__ bp) {
+// In-painting works on logical tiles of kIpT x kIpT cells.  A hole has at most
+// 8 cells, so every cell of it lies within 7 cells of any other: the empty
+// cells of the tile and a rim of kIpRim cells, one bit each, are all a tile
+// needs to find its holes (shared memory, one 64-bit word per row).
+constexpr int kIpT = 32, kIpRim = 8, kIpSpan = kIpT + 2 * kIpRim;  // 48 bits of a row word
+static_assert(kIpT * kIpT == 4 * kMapThreads, "k_inpaint: four cells per thread");
+
+// Is cell (i, j) of the tile window empty and inside the map?  Bits outside the
+// map are clear, so the search never leaves it; a hole may not touch the map
+// edge, which is tested on the cells themselves.
+__device__ __forceinline__ bool ip_empty(const uint64_t* rows, int i, int j) { return (rows[j] >> i) & 1ull; }
+
+__global__ void __launch_bounds__(kMapThreads, 4) k_inpaint(const BatchDev* __restrict__ bp) {
+  __shared__ uint64_t s_rows[kIpSpan];
   const BatchDev& b = *bp;
-  for_each_tile(b, [&](const MapDev& m, int, int32_t p0, int32_t count) {
-  if (!m.inpaint) return;
-  for (int32_t i = threadIdx.x; i < count; i += kMapThreads) {
-    const int32_t p = p0 + i;
-    int32_t lx, ly;
-    logical_of(m, p, lx, ly);
-    if (valid_at(m, p)) {
-      m.inpaint[p] = m.h[p];
-      continue;
-    }
-    int32_t qx[8], qy[8];
-    int n = 1, head = 0;
-    qx[0] = lx;
-    qy[0] = ly;
-    bool hole = true;
-    while (head < n && hole) {
-      const int32_t x = qx[head], y = qy[head];
-      ++head;
-      if (x == 0 || y == 0 || x == m.W - 1 || y == m.H - 1) { hole = false; break; }
-      const int ddx[4] = {1, -1, 0, 0}, ddy[4] = {0, 0, 1, -1};
-      for (int k = 0; k < 4 && hole; ++k) {
-        const int32_t jx = x + ddx[k], jy = y + ddy[k];
-        if (valid_at(m, phys_index(m, jx, jy))) continue;
-        bool seen = false;
-        for (int t = 0; t < n; ++t) seen |= (qx[t] == jx && qy[t] == jy);
-        if (seen) continue;
-        if (n == 8) { hole = false; break; }  // a 9th cell: too large
-        qx[n] = jx;
-        qy[n] = jy;
-        ++n;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int mi = 0; mi < b.n_maps; ++mi) {
+    const MapDev& m = b.maps[mi];
+    if (!m.inpaint) continue;
+    const int32_t ntx = (m.W + kIpT - 1) / kIpT, nty = (m.H + kIpT - 1) / kIpT;
+    for (int32_t tile = blockIdx.x; tile < ntx * nty; tile += gridDim.x) {
+      const int32_t x0 = (tile % ntx) * kIpT - kIpRim, y0 = (tile / ntx) * kIpT - kIpRim;  // window origin
+      // empty bits of the window: each warp takes 6 rows of 32 + 16 columns, with
+      // all 12 loads in flight before the votes
+      constexpr int kRowsPerWarp = kIpSpan / (kMapThreads / 32);
+      static_assert(kRowsPerWarp * (kMapThreads / 32) == kIpSpan, "k_inpaint: rows per warp");
+      bool empty[kRowsPerWarp][2];
+#pragma unroll
+      for (int k = 0; k < kRowsPerWarp; ++k)
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+          const int32_t y = y0 + warp * kRowsPerWarp + k, x = x0 + half * 32 + lane;
+          const bool in = y >= 0 && y < m.H && x >= 0 && x < m.W && half * 32 + lane < kIpSpan;
+          empty[k][half] = in && !isfinite(__ldg(m.var + (in ? phys_index(m, x, y) : 0)));
+        }
+#pragma unroll
+      for (int k = 0; k < kRowsPerWarp; ++k) {
+        const uint64_t word = (uint64_t)__ballot_sync(0xffffffffu, empty[k][0]) |
+                              (uint64_t)__ballot_sync(0xffffffffu, empty[k][1]) << 32;
+        if (lane == 0) s_rows[warp * kRowsPerWarp + k] = word;
       }
-    }
-    float out = qnan();
-    if (hole) {
-      float mn = pinf();
-      for (int t = 0; t < n; ++t)
-        for (int dy = -1; dy <= 1; ++dy)
-          for (int dx = -1; dx <= 1; ++dx) {
-            const int32_t q = phys_index(m, qx[t] + dx, qy[t] + dy);  // in range: holes avoid the border
-            if (valid_at(m, q)) mn = fminf(mn, m.h[q]);
+      __syncthreads();
+      for (int k = 0; k < 4; ++k) {
+        const int ci = threadIdx.x % kIpT, cj = threadIdx.x / kIpT + k * (kMapThreads / kIpT);
+        const int32_t lx = x0 + kIpRim + ci, ly = y0 + kIpRim + cj;
+        if (lx >= m.W || ly >= m.H) continue;
+        const int32_t p = phys_index(m, lx, ly);
+        const int i = kIpRim + ci, j = kIpRim + cj;  // the cell in the window
+        if (!ip_empty(s_rows, i, j)) {
+          m.inpaint[p] = m.h[p];
+          continue;
+        }
+        float out = qnan();
+        // a run of 9 or more empty cells along the row is part of a component too
+        // large to be a hole (the window holds 8 cells on either side)
+        const uint64_t row = s_rows[j];
+        const int up = __ffsll((long long)~(row >> i)) - 1;           // empty cells from i upwards
+        const int down = __clzll((long long)~(row << (63 - i)));      // empty cells from i downwards
+        if (up + down - 1 <= 8) {
+          // breadth-first search of the component, at most 8 cells, each stored as
+          // one byte (dx + 8) | (dy + 8) << 4 of a 64-bit word
+          uint64_t cells = 0x88ull;  // the start cell: dx = dy = 0
+          int n = 1, head = 0;
+          bool hole = true;
+          while (head < n && hole) {
+            const uint32_t c = (uint32_t)(cells >> (8 * head)) & 0xffu;
+            ++head;
+            const int dx = (int)(c & 15u) - 8, dy = (int)(c >> 4) - 8;
+            const int32_t x = lx + dx, y = ly + dy;
+            if (x == 0 || y == 0 || x == m.W - 1 || y == m.H - 1) { hole = false; break; }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int ex = dx + (q == 0) - (q == 1), ey = dy + (q == 2) - (q == 3);
+              if (!ip_empty(s_rows, i + ex, j + ey)) continue;
+              // 8 cells from the start needs a path of 9: too large (and not codable)
+              if (ex < -7 || ex > 7 || ey < -7 || ey > 7) { hole = false; break; }
+              const uint64_t code = (uint64_t)((ex + 8) | ((ey + 8) << 4));
+              const uint64_t v = cells ^ (code * 0x0101010101010101ull);  // a zero byte: already found
+              if ((v - 0x0101010101010101ull) & ~v & 0x8080808080808080ull) continue;
+              if (n == 8) { hole = false; break; }  // a 9th cell: too large
+              cells |= code << (8 * n);
+              ++n;
+            }
           }
-      out = mn;
+          if (hole) {
+            // lowest estimate among the 8-neighbours (all inside the map: holes
+            // avoid the edge, so a cell there that is not empty holds an estimate)
+            float mn = pinf();
+            for (int t = 0; t < n; ++t) {
+              const uint32_t c = (uint32_t)(cells >> (8 * t)) & 0xffu;
+              const int32_t x = lx + (int)(c & 15u) - 8, y = ly + (int)(c >> 4) - 8;
+              const int wi = i + (int)(c & 15u) - 8, wj = j + (int)(c >> 4) - 8;
+#pragma unroll
+              for (int ddy = -1; ddy <= 1; ++ddy)
+#pragma unroll
+                for (int ddx = -1; ddx <= 1; ++ddx)
+                  if (!ip_empty(s_rows, wi + ddx, wj + ddy)) mn = fminf(mn, m.h[phys_index(m, x + ddx, y + ddy)]);
+            }
+            out = mn;
+          }
+        }
+        m.inpaint[p] = out;
+      }
+      __syncthreads();
     }
-    m.inpaint[p] = out;
   }
-  });
 }
 
 __device__ __forceinline__ void empty_cell(const MapDev& m, int32_t p) {

@@ -200,44 +200,50 @@ __global__ void __launch_bounds__(kRayThreads) k_ray(const BatchDev* __restrict_
 
 constexpr int kClearThreads = 256;
 
-// One warp per tile: a tile of kTile cells is kTile / 32 = 32 mark words, one
-// per lane (marks are rare, so most warps read one word each and leave).
-static_assert(kTile == 32 * 32, "k_clear: one mark word per lane of a tile");
+// One block per tile of kTile cells, four consecutive cells per thread, so the
+// loads of all marked cells of a tile are in flight together (the marks of a
+// LiDAR frame are dense along the rays: one thread walking a word's bits would
+// chain its loads).
+static_assert(kTile == 4 * kClearThreads, "k_clear: four cells per thread");
 __global__ void __launch_bounds__(kClearThreads) k_clear(const BatchDev* __restrict__ bp) {
   const BatchDev& b = *bp;
-  const int lane = threadIdx.x & 31;
   const int64_t n_tiles = b.n_cells / kTile;
-  const int64_t n_warps = (int64_t)gridDim.x * (kClearThreads / 32);
-  for (int64_t t = (int64_t)blockIdx.x * (kClearThreads / 32) + (threadIdx.x >> 5); t < n_tiles; t += n_warps) {
+  for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
     const int64_t g0 = t * kTile;
     const int mi = find_map_cell(b.maps, b.n_maps, g0);
     const MapDev& m = b.maps[mi];
     const int64_t p0 = g0 - m.cell_begin;
     const int32_t ncell = m.W * m.H;
-    if (p0 >= ncell) continue;  // padding at the end of a map (warp-uniform)
-    const int32_t end = (int32_t)(ncell - p0 < kTile ? ncell : p0 + kTile);
-    const int32_t w = (int32_t)(p0 >> 5) + lane;
-    uint32_t cleared = 0;
-    if (w * 32 < end) {
-      uint32_t bits = m.mark[w];
-      if (bits) {
-        m.mark[w] = 0u;
-        const int32_t min_age = m.min_age > 1 ? m.min_age : 1;
-        while (bits) {
-          const int bit = __ffs(bits) - 1;
-          bits &= bits - 1;
-          const int32_t p = w * 32 + bit;
-          if (p >= end) break;
-          if (!isfinite(m.var[p])) continue;
-          if (m.t_now - m.t_last[p] < min_age) continue;
-          m.h[p] = __int_as_float(0x7fc00000);
-          m.var[p] = __int_as_float(0x7f800000);
-          ++cleared;
-        }
+    if (p0 >= ncell) continue;  // padding at the end of a map (block-uniform)
+    const int32_t c0 = (int32_t)p0 + 4 * threadIdx.x;  // this thread's cells c0 .. c0 + 3 (one word's quarter byte)
+    const int32_t w = c0 >> 5;
+    const uint32_t word = c0 < ncell ? m.mark[w] : 0u;
+    const uint32_t bits = (word >> (c0 & 31)) & 15u;
+    unsigned cleared = 0;
+    if (bits) {
+      const int32_t min_age = m.min_age > 1 ? m.min_age : 1;
+      float var[4];
+      int32_t tl[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {  // all loads first
+        const bool mk = ((bits >> k) & 1u) && c0 + k < ncell;
+        var[k] = mk ? m.var[c0 + k] : __int_as_float(0x7f800000);
+        tl[k] = mk ? m.t_last[c0 + k] : 0;
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (!isfinite(var[k]) || m.t_now - tl[k] < min_age) continue;
+        m.h[c0 + k] = __int_as_float(0x7fc00000);
+        m.var[c0 + k] = __int_as_float(0x7f800000);
+        ++cleared;
       }
     }
+    // the word is reset by the thread holding its first cells, after its 8 readers
+    // (one warp) have read it
+    __syncwarp();
+    if ((c0 & 31) == 0 && word) m.mark[w] = 0u;
     const unsigned tot = __reduce_add_sync(0xffffffffu, cleared);
-    if (lane == 0 && tot) atomicAdd(&m.ctl->stats[kStCleared], (unsigned long long)tot);
+    if ((threadIdx.x & 31) == 0 && tot) atomicAdd(&m.ctl->stats[kStCleared], (unsigned long long)tot);
   }
 }
 
@@ -295,9 +301,9 @@ cudaError_t launch_overlap(const BatchDev* b, int64_t n_cells, cudaStream_t s) {
 }
 
 cudaError_t launch_clear(const BatchDev* b, int64_t n_cells, cudaStream_t s) {
-  const int64_t blocks = (n_cells / kTile + kClearThreads / 32 - 1) / (kClearThreads / 32);  // a warp per tile
+  const int64_t tiles = n_cells / kTile;  // a block per tile
   const int64_t cap = (int64_t)sm_count() * 8;
-  const int grid = (int)(blocks < 1 ? 1 : blocks < cap ? blocks : cap);
+  const int grid = (int)(tiles < 1 ? 1 : tiles < cap ? tiles : cap);
   k_clear<<<grid, kClearThreads, 0, s>>>(b);
   return cudaGetLastError();
 }

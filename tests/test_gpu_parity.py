@@ -394,6 +394,53 @@ def test_lidar_frame_with_filters(em, smoothing):
     assert np.isfinite(s["nz"]).sum() > 10000 and np.isfinite(s["inpaint"]).sum() >= np.isfinite(s["h"]).sum()
 
 
+def test_inpainting_hole_shapes(em):
+    """Section II-I in-painting on carved empty patterns, over a shifted (ring)
+    map: lines, L shapes and blocks of exactly 8 cells (holes) and 9 cells (too
+    large), holes across the 32-cell tile edges of the kernel, single cells,
+    components touching the map edge, and a random field of empty cells."""
+    W, H = 100, 90
+    P = dict(width=W, height=H, resolution=0.04, noise_a0=0.005, flags=4)
+    prior = synth.random_prior(seed=31, width=W, height=H, t_now=5, invalid_frac=0.0, with_normals=False)
+    empty = np.zeros((H, W), bool)
+    empty[28:36, 31] = True                  # vertical 8, across the tile edge at y = 32
+    empty[10:19, 50] = True                  # vertical 9
+    empty[40, 28:36] = True                  # horizontal 8, across the tile edge at x = 32
+    empty[60, 60:69] = True                  # horizontal 9
+    empty[70, 10:15] = True; empty[71:74, 14] = True      # L of 8
+    empty[80, 20:25] = True; empty[81:85, 24] = True      # L of 9
+    empty[5:7, 80:84] = True                 # 2 x 4 block of 8
+    empty[20:23, 80:83] = True               # 3 x 3 block of 9
+    empty[50, 5] = empty[52, 7] = empty[64, 64] = True    # single cells (one at a tile corner)
+    empty[45, 0] = True                      # single cell on the map edge
+    empty[H - 1, 40:43] = True               # three cells on the map edge
+    rng = np.random.default_rng(32)
+    field = rng.random((H, W)) < 0.3
+    field[:, :86] = False
+    field[:8, :] = False
+    empty |= field                           # a random field of components of every size
+    prior["var"][empty] = np.inf
+    prior["h"][empty] = np.nan
+    om = oracle.OracleMap(parity.oracle_params(P))
+    gm = gpu_map(em, P)
+    om.shift(17, -11)
+    gm.shift(17, -11)
+    parity.prior_to_oracle(om, prior)
+    parity.prior_to_gpu(gm, prior)
+    pose = synth.pose_matrix(np.eye(3), np.array([0.0, 0.0, 0.5]))
+    clouds = [(np.zeros((0, 3), np.float32), pose)]
+    tr = om.update(clouds, trace=True, unit=oracle.FP32_UNIT, abs_band=parity.ABS_BAND)
+    gm.update_multi([(dev(p), q) for p, q in clouds])
+    o, g = om.state()["inpaint"], gm.state()["inpaint"]
+    assert np.array_equal(np.isnan(o), np.isnan(g))
+    assert np.allclose(o[~np.isnan(o)], g[~np.isnan(g)], rtol=0, atol=1e-6)
+    # the shapes: 8 cells are holes, 9 cells or the map edge are not
+    for (y, x), hole in [((30, 31), True), ((12, 50), False), ((40, 33), True), ((60, 64), False),
+                         ((72, 14), True), ((83, 24), False), ((6, 81), True), ((21, 81), False),
+                         ((50, 5), True), ((64, 64), True), ((45, 0), False), ((H - 1, 41), False)]:
+        assert np.isnan(o[y, x]) != hole, (y, x)
+
+
 def test_maximum_map_size(em):
     """The largest map (2^26 cells) takes an update; its centre agrees with a
     small map on the same points (cells offset by an integer)."""
