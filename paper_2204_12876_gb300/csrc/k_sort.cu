@@ -178,8 +178,8 @@ __global__ void __launch_bounds__(kPointThreads) k_drift_sum(const BatchDev* __r
   unsigned long long dl = 0, dn = 0;
   for (int64_t wbase = beg + warp * 32; wbase < end; wbase += kPointThreads) {
     const int c0 = find_cloud(b.clouds, b.n_clouds, wbase);
-    const int c1 = find_cloud(b.clouds, b.n_clouds, wbase + 31 < end ? wbase + 31 : end - 1);
-    if (c0 == c1 && b.maps[b.clouds[c0].map].drift_flat <= 0.f) continue;  // a whole warp without drift
+    const CloudDev& cl0 = b.clouds[c0];
+    if (wbase + 32 <= cl0.begin + cl0.n && b.maps[cl0.map].drift_flat <= 0.f) continue;  // a whole warp without drift
     float px, py, pz;
     const int ci = load_warp_points(b, wbase, end, stage[warp], px, py, pz);
     const int64_t g = wbase + lane;
@@ -188,14 +188,16 @@ __global__ void __launch_bounds__(kPointThreads) k_drift_sum(const BatchDev* __r
     const PointGeom pg = point_geom<kExt>(m, c, px, py, pz);
     if (g < end && m.drift_flat > 0.f && pg.in_range && in_map(m, pg.ix, pg.iy)) {
       const int32_t key = phys_index(m, pg.ix, pg.iy);
-      if (isfinite(m.var[key]) && m.nz[key] >= m.drift_flat) {
+      // the three loads are independent: all in flight at once
+      const float var = m.var[key], nz = m.nz[key], hc = m.h[key];
+      if (isfinite(var) && nz >= m.drift_flat) {
         if (c.map != dmap) {
           if (dmap >= 0) drift_add(b.maps[dmap], dh, dl, dn);
           dmap = c.map;
           dh = 0;
           dl = dn = 0;
         }
-        const Fix e = to_fix(__fsub_rn(pg.z, m.h[key]));
+        const Fix e = to_fix(__fsub_rn(pg.z, hc));
         dh += e.h;
         dl += e.l;
         ++dn;
