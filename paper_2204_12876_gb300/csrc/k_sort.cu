@@ -204,7 +204,41 @@ __global__ void __launch_bounds__(kPointThreads) k_drift_sum(const BatchDev* __r
       }
     }
   }
-  // a warp sum when the warp's lanes hold one map (the usual case)
+  // One atomic triple per block when the block's sums all belong to one map (the
+  // usual case): every block adding to the same three words of that map would
+  // otherwise queue at one L2 slice.  Else per warp or per lane.
+  __shared__ int s_map;
+  __shared__ long long s_h[kPointThreads / 32];
+  __shared__ unsigned long long s_l[kPointThreads / 32], s_n[kPointThreads / 32];
+  if (threadIdx.x == 0) s_map = -1;
+  __syncthreads();
+  if (dn) atomicMax(&s_map, dmap);
+  __syncthreads();
+  const int bm = s_map;
+  if (__syncthreads_and(dn == 0 || dmap == bm)) {
+    for (int o = 16; o > 0; o >>= 1) {
+      dh += __shfl_xor_sync(kFull, dh, o);
+      dl += __shfl_xor_sync(kFull, dl, o);
+      dn += __shfl_xor_sync(kFull, dn, o);
+    }
+    if (lane == 0) {
+      s_h[warp] = dh;
+      s_l[warp] = dl;
+      s_n[warp] = dn;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && bm >= 0) {
+      long long th = 0;
+      unsigned long long tl = 0, tn = 0;
+      for (int w = 0; w < kPointThreads / 32; ++w) {
+        th += s_h[w];
+        tl += s_l[w];
+        tn += s_n[w];
+      }
+      if (tn) drift_add(b.maps[bm], th, tl, tn);
+    }
+    return;
+  }
   const int d0 = __shfl_sync(kFull, dmap, 0);
   if (__all_sync(kFull, dmap == d0 || dn == 0)) {
     for (int o = 16; o > 0; o >>= 1) {
