@@ -160,8 +160,64 @@ static_assert(kIpT * kIpT == 4 * kMapThreads, "k_inpaint: four cells per thread"
 // edge, which is tested on the cells themselves.
 __device__ __forceinline__ bool ip_empty(const uint64_t* rows, int i, int j) { return (rows[j] >> i) & 1ull; }
 
+// Empty cells in a run of 9 or more along a row or a column are part of a
+// component too large to be a hole (the window holds 8 cells on either side).
+__device__ __forceinline__ int run_through(uint64_t word, int bit) {
+  const int up = __ffsll((long long)~(word >> bit)) - 1;       // set bits from bit upwards
+  const int down = __clzll((long long)~(word << (63 - bit)));  // set bits from bit downwards
+  return up + down - 1;
+}
+
+// The component of window cell (i, j) (logical (lx, ly)): a hole gets the
+// lowest estimate among its 8-neighbours, anything else NaN.  A breadth-first
+// search of at most 8 cells, each stored as one byte (dx + 8) | (dy + 8) << 4
+// of a 64-bit word.
+__device__ float inpaint_cell(const MapDev& m, const uint64_t* rows, int i, int j, int32_t lx, int32_t ly) {
+  uint64_t cells = 0x88ull;  // the start cell: dx = dy = 0
+  int n = 1, head = 0;
+  bool hole = true;
+  while (head < n && hole) {
+    const uint32_t c = (uint32_t)(cells >> (8 * head)) & 0xffu;
+    ++head;
+    const int dx = (int)(c & 15u) - 8, dy = (int)(c >> 4) - 8;
+    const int32_t x = lx + dx, y = ly + dy;
+    if (x == 0 || y == 0 || x == m.W - 1 || y == m.H - 1) { hole = false; break; }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int ex = dx + (q == 0) - (q == 1), ey = dy + (q == 2) - (q == 3);
+      if (!ip_empty(rows, i + ex, j + ey)) continue;
+      // 8 cells from the start needs a path of 9: too large (and not codable)
+      if (ex < -7 || ex > 7 || ey < -7 || ey > 7) { hole = false; break; }
+      const uint64_t code = (uint64_t)((ex + 8) | ((ey + 8) << 4));
+      const uint64_t v = cells ^ (code * 0x0101010101010101ull);  // a zero byte: already found
+      if ((v - 0x0101010101010101ull) & ~v & 0x8080808080808080ull) continue;
+      if (n == 8) { hole = false; break; }  // a 9th cell: too large
+      cells |= code << (8 * n);
+      ++n;
+    }
+  }
+  if (!hole) return qnan();
+  // lowest estimate among the 8-neighbours (all inside the map: holes avoid the
+  // edge, so a cell there that is not empty holds an estimate)
+  float mn = pinf();
+  for (int t = 0; t < n; ++t) {
+    const uint32_t c = (uint32_t)(cells >> (8 * t)) & 0xffu;
+    const int32_t x = lx + (int)(c & 15u) - 8, y = ly + (int)(c >> 4) - 8;
+    const int wi = i + (int)(c & 15u) - 8, wj = j + (int)(c >> 4) - 8;
+#pragma unroll
+    for (int ddy = -1; ddy <= 1; ++ddy)
+#pragma unroll
+      for (int ddx = -1; ddx <= 1; ++ddx)
+        if (!ip_empty(rows, wi + ddx, wj + ddy)) mn = fminf(mn, m.h[phys_index(m, x + ddx, y + ddy)]);
+  }
+  return mn;
+}
+
 __global__ void __launch_bounds__(kMapThreads, 4) k_inpaint(const BatchDev* __restrict__ bp) {
   __shared__ uint64_t s_rows[kIpSpan];
+  __shared__ uint64_t s_cols[kIpSpan];      // the same bits by column
+  __shared__ uint16_t s_queue[kIpT * kIpT];  // tile cells that need the search
+  __shared__ int s_queued;
   const BatchDev& b = *bp;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int mi = 0; mi < b.n_maps; ++mi) {
@@ -170,6 +226,7 @@ __global__ void __launch_bounds__(kMapThreads, 4) k_inpaint(const BatchDev* __re
     const int32_t ntx = (m.W + kIpT - 1) / kIpT, nty = (m.H + kIpT - 1) / kIpT;
     for (int32_t tile = blockIdx.x; tile < ntx * nty; tile += gridDim.x) {
       const int32_t x0 = (tile % ntx) * kIpT - kIpRim, y0 = (tile / ntx) * kIpT - kIpRim;  // window origin
+      if (threadIdx.x == 0) s_queued = 0;
       // empty bits of the window: each warp takes 6 rows of 32 + 16 columns, with
       // all 12 loads in flight before the votes
       constexpr int kRowsPerWarp = kIpSpan / (kMapThreads / 32);
@@ -190,66 +247,37 @@ __global__ void __launch_bounds__(kMapThreads, 4) k_inpaint(const BatchDev* __re
         if (lane == 0) s_rows[warp * kRowsPerWarp + k] = word;
       }
       __syncthreads();
+      if (threadIdx.x < kIpSpan) {  // transpose
+        uint64_t col = 0;
+        for (int r = 0; r < kIpSpan; ++r) col |= ((s_rows[r] >> threadIdx.x) & 1ull) << r;
+        s_cols[threadIdx.x] = col;
+      }
+      __syncthreads();
+      // every cell: estimates copied, cells of long empty runs NaN, the rest queued
       for (int k = 0; k < 4; ++k) {
         const int ci = threadIdx.x % kIpT, cj = threadIdx.x / kIpT + k * (kMapThreads / kIpT);
         const int32_t lx = x0 + kIpRim + ci, ly = y0 + kIpRim + cj;
-        if (lx >= m.W || ly >= m.H) continue;
-        const int32_t p = phys_index(m, lx, ly);
+        const bool in = lx < m.W && ly < m.H;
         const int i = kIpRim + ci, j = kIpRim + cj;  // the cell in the window
-        if (!ip_empty(s_rows, i, j)) {
-          m.inpaint[p] = m.h[p];
-          continue;
+        bool search = false;
+        if (in) {
+          const int32_t p = phys_index(m, lx, ly);
+          if (!ip_empty(s_rows, i, j)) m.inpaint[p] = m.h[p];
+          else if (run_through(s_rows[j], i) > 8 || run_through(s_cols[i], j) > 8) m.inpaint[p] = qnan();
+          else search = true;
         }
-        float out = qnan();
-        // a run of 9 or more empty cells along the row is part of a component too
-        // large to be a hole (the window holds 8 cells on either side)
-        const uint64_t row = s_rows[j];
-        const int up = __ffsll((long long)~(row >> i)) - 1;           // empty cells from i upwards
-        const int down = __clzll((long long)~(row << (63 - i)));      // empty cells from i downwards
-        if (up + down - 1 <= 8) {
-          // breadth-first search of the component, at most 8 cells, each stored as
-          // one byte (dx + 8) | (dy + 8) << 4 of a 64-bit word
-          uint64_t cells = 0x88ull;  // the start cell: dx = dy = 0
-          int n = 1, head = 0;
-          bool hole = true;
-          while (head < n && hole) {
-            const uint32_t c = (uint32_t)(cells >> (8 * head)) & 0xffu;
-            ++head;
-            const int dx = (int)(c & 15u) - 8, dy = (int)(c >> 4) - 8;
-            const int32_t x = lx + dx, y = ly + dy;
-            if (x == 0 || y == 0 || x == m.W - 1 || y == m.H - 1) { hole = false; break; }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const int ex = dx + (q == 0) - (q == 1), ey = dy + (q == 2) - (q == 3);
-              if (!ip_empty(s_rows, i + ex, j + ey)) continue;
-              // 8 cells from the start needs a path of 9: too large (and not codable)
-              if (ex < -7 || ex > 7 || ey < -7 || ey > 7) { hole = false; break; }
-              const uint64_t code = (uint64_t)((ex + 8) | ((ey + 8) << 4));
-              const uint64_t v = cells ^ (code * 0x0101010101010101ull);  // a zero byte: already found
-              if ((v - 0x0101010101010101ull) & ~v & 0x8080808080808080ull) continue;
-              if (n == 8) { hole = false; break; }  // a 9th cell: too large
-              cells |= code << (8 * n);
-              ++n;
-            }
-          }
-          if (hole) {
-            // lowest estimate among the 8-neighbours (all inside the map: holes
-            // avoid the edge, so a cell there that is not empty holds an estimate)
-            float mn = pinf();
-            for (int t = 0; t < n; ++t) {
-              const uint32_t c = (uint32_t)(cells >> (8 * t)) & 0xffu;
-              const int32_t x = lx + (int)(c & 15u) - 8, y = ly + (int)(c >> 4) - 8;
-              const int wi = i + (int)(c & 15u) - 8, wj = j + (int)(c >> 4) - 8;
-#pragma unroll
-              for (int ddy = -1; ddy <= 1; ++ddy)
-#pragma unroll
-                for (int ddx = -1; ddx <= 1; ++ddx)
-                  if (!ip_empty(s_rows, wi + ddx, wj + ddy)) mn = fminf(mn, m.h[phys_index(m, x + ddx, y + ddy)]);
-            }
-            out = mn;
-          }
-        }
-        m.inpaint[p] = out;
+        const unsigned want = __ballot_sync(0xffffffffu, search);
+        int base = 0;
+        if (lane == 0 && want) base = atomicAdd(&s_queued, __popc(want));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (search) s_queue[base + __popc(want & ((1u << lane) - 1u))] = (uint16_t)(cj * kIpT + ci);
+      }
+      __syncthreads();
+      // the searches, one per thread (the queue keeps the lanes of a warp busy)
+      for (int q = threadIdx.x; q < s_queued; q += kMapThreads) {
+        const int ci = s_queue[q] % kIpT, cj = s_queue[q] / kIpT;
+        const int32_t lx = x0 + kIpRim + ci, ly = y0 + kIpRim + cj;
+        m.inpaint[phys_index(m, lx, ly)] = inpaint_cell(m, s_rows, kIpRim + ci, kIpRim + cj, lx, ly);
       }
       __syncthreads();
     }
