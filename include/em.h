@@ -113,7 +113,9 @@ typedef struct em_params {
 } em_params;
 
 /* One point cloud: n points of `stride` floats (3 = xyz, 4 = xyz + pad) in the
- * sensor frame, and the sensor-to-map pose as a row-major 3x4 [R | t]. */
+ * sensor frame, and the sensor-to-map pose as a row-major 3x4 [R | t].  Every
+ * buffer the library reads or writes as floats (points, layers, read-backs)
+ * must start on a 4-byte boundary; calls refuse others with EM_ERR_INVALID_ARG. */
 typedef struct em_cloud {
   const float* points;
   int64_t n;

@@ -524,7 +524,8 @@ static int check_clouds(const em_cloud* clouds, int32_t n_clouds) {
   if (n_clouds < 1 || n_clouds > kMaxClouds || !clouds) return EM_ERR_INVALID_ARG;
   for (int i = 0; i < n_clouds; ++i) {
     const em_cloud& c = clouds[i];
-    if (c.n < 0 || (c.stride != 3 && c.stride != 4) || (c.n > 0 && !c.points) || !pose_ok(c.pose))
+    if (c.n < 0 || (c.stride != 3 && c.stride != 4) || (c.n > 0 && !c.points) || !word_aligned(c.points) ||
+        !pose_ok(c.pose))
       return EM_ERR_INVALID_ARG;
   }
   return EM_OK;
@@ -621,7 +622,7 @@ static int ensure_layer_stage(em_map* m, size_t floats) {
 }
 
 int em_get_layers(em_map* m, uint32_t mask, float* dst, int dst_is_host, em_stream_t stream) {
-  if (!m || !dst || !mask || (mask >> 11)) return EM_ERR_INVALID_ARG;
+  if (!m || !dst || !mask || (mask >> 11) || !word_aligned(dst)) return EM_ERR_INVALID_ARG;
   int rc = set_device(m->device);
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)stream;
@@ -642,7 +643,7 @@ int em_get_layers(em_map* m, uint32_t mask, float* dst, int dst_is_host, em_stre
 int em_set_layers(em_map* m, uint32_t mask, const float* src, int src_is_host, em_stream_t stream) {
   const uint32_t allowed = EM_LAYER_ELEVATION | EM_LAYER_VARIANCE | EM_LAYER_TIME | EM_LAYER_NORMAL_X |
                            EM_LAYER_NORMAL_Y | EM_LAYER_NORMAL_Z | EM_LAYER_UPPER;
-  if (!m || !src || !mask || (mask & ~allowed)) return EM_ERR_INVALID_ARG;
+  if (!m || !src || !mask || (mask & ~allowed) || !word_aligned(src)) return EM_ERR_INVALID_ARG;
   int rc = set_device(m->device);
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)stream;

@@ -154,7 +154,8 @@ int prepare(em_batch* b, em_map* const* maps, const em_cloud* clouds, int32_t co
   b->map_of.assign(count, -1);
   for (int i = 0; i < count; ++i) {
     const em_cloud& c = clouds[i];
-    if (!maps[i] || c.n < 0 || (c.stride != 3 && c.stride != 4) || (c.n > 0 && !c.points)) return EM_ERR_INVALID_ARG;
+    if (!maps[i] || c.n < 0 || (c.stride != 3 && c.stride != 4) || (c.n > 0 && !c.points) || !word_aligned(c.points))
+      return EM_ERR_INVALID_ARG;
     for (int k = 0; k < 12; ++k)
       if (!std::isfinite(c.pose[k])) return EM_ERR_INVALID_ARG;
     if (map_device(maps[i]) != b->device) return EM_ERR_INVALID_ARG;

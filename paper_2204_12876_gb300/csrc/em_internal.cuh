@@ -142,6 +142,9 @@ struct BatchDev {
 constexpr int kMinBig = 32;
 inline int64_t big_list_cap(int64_t n) { return n / (kMinBig + 1) + 1; }
 inline int64_t pad_tile(int64_t cells) { return (cells + kTile - 1) / kTile * kTile; }
+// The kernels read points and layers as 4-byte words: a buffer that does not
+// start on a 4-byte boundary is refused on the host (it would fault on the device).
+inline bool word_aligned(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 3u) == 0; }
 
 // number of SMs of the current device (cached)
 int sm_count();

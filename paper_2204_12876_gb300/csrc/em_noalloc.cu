@@ -102,13 +102,17 @@ extern "C" int em_update_noalloc(const em_params* params, int64_t shift_x, int64
                                  const float* nz, const em_cloud* clouds, int32_t n_clouds, em_stream_t stream) {
   if (!na_params_ok(params) || !h || !var || !t_last || !clouds || n_clouds < 1 || t_now < 1)
     return EM_ERR_INVALID_ARG;
+  if (!word_aligned(h) || !word_aligned(var) || !word_aligned(t_last) || !word_aligned(nx) || !word_aligned(ny) ||
+      !word_aligned(nz))
+    return EM_ERR_INVALID_ARG;
   if ((params->cleanup_normal_thresh > 0.f || params->drift_flatness > 0.f) && (!nx || !ny || !nz))
     return EM_ERR_INVALID_ARG;
   if ((int64_t)params->width * params->height > kMaxCells || n_clouds > kMaxCloudsNA) return EM_ERR_CAPACITY;
   int64_t total = 0;
   for (int i = 0; i < n_clouds; ++i) {
     const em_cloud& c = clouds[i];
-    if (c.n < 0 || (c.stride != 3 && c.stride != 4) || (c.n > 0 && !c.points)) return EM_ERR_INVALID_ARG;
+    if (c.n < 0 || (c.stride != 3 && c.stride != 4) || (c.n > 0 && !c.points) || !word_aligned(c.points))
+      return EM_ERR_INVALID_ARG;
     for (int k = 0; k < 12; ++k)
       if (!std::isfinite(c.pose[k])) return EM_ERR_INVALID_ARG;
     total += c.n;

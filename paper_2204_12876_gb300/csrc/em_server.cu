@@ -408,11 +408,12 @@ int em_server_submit_many(em_server* s, const em_request* reqs, int32_t n, void*
     if (!r.clouds || r.n_clouds < 1 || r.n_clouds > 8) return EM_ERR_INVALID_ARG;
     for (int i = 0; i < r.n_clouds; ++i) {
       const em_cloud& c = r.clouds[i];
-      if (c.n < 0 || (c.stride != 3 && c.stride != 4) || (c.n > 0 && !c.points)) return EM_ERR_INVALID_ARG;
+      if (c.n < 0 || (c.stride != 3 && c.stride != 4) || (c.n > 0 && !c.points) || !word_aligned(c.points))
+        return EM_ERR_INVALID_ARG;
       pts[q] += c.n;
     }
     if (r.read_mask) {
-      if ((r.read_mask >> 11) || !r.read_dst) return EM_ERR_INVALID_ARG;
+      if ((r.read_mask >> 11) || !r.read_dst || !word_aligned(r.read_dst)) return EM_ERR_INVALID_ARG;
       // the GPU writes the read-back itself: device memory, or page-locked host
       // memory mapped into the device's address space
       cudaPointerAttributes a{};

@@ -245,6 +245,14 @@ def test_invalid_arguments(em):
         g.update(pts, bad)
     with pytest.raises(em.EMError):
         g.get_layers(1 << 12)
+    # buffers that do not start on a 4-byte boundary are refused before any launch
+    pose = em._pose(np.eye(3, 4).reshape(12))
+    big = dev(np.zeros((11, 3), np.float32))
+    assert em.lib.em_update(g._h, big.data_ptr() + 2, 10, 3, pose, None) == em.EM_ERR_INVALID_ARG
+    out = torch.empty(101, dtype=torch.float32, device="cuda")
+    assert em.lib.em_get_layers(g._h, em.LAYER_ELEVATION, out.data_ptr() + 1, 0, None) == em.EM_ERR_INVALID_ARG
+    assert em.lib.em_set_layers(g._h, em.LAYER_ELEVATION, out.data_ptr() + 3, 0, None) == em.EM_ERR_INVALID_ARG
+    assert g.stats()["updates"] == 0
 
 
 def test_visibility_depth_frame(em):
