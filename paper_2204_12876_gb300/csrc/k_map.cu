@@ -25,50 +25,72 @@ __device__ __forceinline__ float pinf() { return __int_as_float(0x7f800000); }
 
 __device__ __forceinline__ bool valid_at(const MapDev& m, int32_t p) { return isfinite(m.var[p]); }
 
+// Normals work on logical tiles of kNmT x kNmT cells with the heights of the
+// tile and a 1-cell rim staged in shared memory (+inf where empty or outside).
+constexpr int kNmT = 32, kNmSpan = kNmT + 2;
+static_assert(kNmT * kNmT == 4 * kMapThreads, "k_normals: four cells per thread");
+
 __global__ void __launch_bounds__(kMapThreads) k_normals(const BatchDev* __restrict__ bp) {
+  __shared__ float s_h[kNmSpan][kNmSpan + 1];
   const BatchDev& b = *bp;
-  for_each_tile(b, [&](const MapDev& m, int, int32_t p0, int32_t count) {
-  if (!m.nx || !(m.flags & EM_F_NORMALS)) return;  // a batch may mix maps with and without normals
-  for (int32_t i = threadIdx.x; i < count; i += kMapThreads) {
-    const int32_t p = p0 + i;
-    int32_t lx, ly;
-    logical_of(m, p, lx, ly);
-    float rx = qnan(), ry = qnan(), rz = qnan();
-    if (valid_at(m, p)) {
-      const float hc = m.h[p];
-      int n = 0, si = 0, sj = 0, sii = 0, sjj = 0, sij = 0;
-      float sh = 0.f, sih = 0.f, sjh = 0.f;
-      for (int dy = -1; dy <= 1; ++dy) {
-        const int32_t jy = ly + dy;
-        if (jy < 0 || jy >= m.H) continue;
-        for (int dx = -1; dx <= 1; ++dx) {
-          const int32_t jx = lx + dx;
-          if (jx < 0 || jx >= m.W) continue;
-          const int32_t q = phys_index(m, jx, jy);
-          if (!valid_at(m, q)) continue;
-          const float dh = m.h[q] - hc;
-          ++n; si += dx; sj += dy; sii += dx * dx; sjj += dy * dy; sij += dx * dy;
-          sh += dh; sih += dx * dh; sjh += dy * dh;
+  for (int mi = 0; mi < b.n_maps; ++mi) {
+    const MapDev& m = b.maps[mi];
+    if (!m.nx || !(m.flags & EM_F_NORMALS)) continue;  // a batch may mix maps with and without normals
+    const int32_t ntx = (m.W + kNmT - 1) / kNmT, nty = (m.H + kNmT - 1) / kNmT;
+    for (int32_t tile = blockIdx.x; tile < ntx * nty; tile += gridDim.x) {
+      const int32_t x0 = (tile % ntx) * kNmT - 1, y0 = (tile / ntx) * kNmT - 1;  // window origin
+      for (int e = threadIdx.x; e < kNmSpan * kNmSpan; e += kMapThreads) {
+        const int wi = e % kNmSpan, wj = e / kNmSpan;
+        const int32_t x = x0 + wi, y = y0 + wj;
+        float h = pinf();
+        if (x >= 0 && x < m.W && y >= 0 && y < m.H) {
+          const int32_t q = phys_index(m, x, y);
+          if (valid_at(m, q)) h = m.h[q];
         }
+        s_h[wj][wi] = h;
       }
-      // centred normal equations scaled by n (exact integers on the left)
-      const int cxx = n * sii - si * si, cyy = n * sjj - sj * sj, cxy = n * sij - si * sj;
-      const int det = cxx * cyy - cxy * cxy;  // 0 iff the valid cells are collinear
-      if (n >= 3 && det != 0) {
-        const float cxh = n * sih - si * sh, cyh = n * sjh - sj * sh;
-        const float a = ((float)cyy * cxh - (float)cxy * cyh) / ((float)det * m.res);
-        const float bb = ((float)cxx * cyh - (float)cxy * cxh) / ((float)det * m.res);
-        const float inv = rsqrtf(a * a + bb * bb + 1.f);
-        rx = -a * inv;
-        ry = -bb * inv;
-        rz = inv;
+      __syncthreads();
+      for (int k = 0; k < 4; ++k) {
+        const int ci = threadIdx.x % kNmT, cj = threadIdx.x / kNmT + k * (kMapThreads / kNmT);
+        const int32_t lx = x0 + 1 + ci, ly = y0 + 1 + cj;
+        if (lx >= m.W || ly >= m.H) continue;
+        float rx = qnan(), ry = qnan(), rz = qnan();
+        const float hc = s_h[cj + 1][ci + 1];
+        if (hc != pinf()) {  // a valid centre
+          int n = 0, si = 0, sj = 0, sii = 0, sjj = 0, sij = 0;
+          float sh = 0.f, sih = 0.f, sjh = 0.f;
+#pragma unroll
+          for (int dy = -1; dy <= 1; ++dy) {
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) {
+              const float hq = s_h[cj + 1 + dy][ci + 1 + dx];
+              if (hq == pinf()) continue;
+              const float dh = hq - hc;
+              ++n; si += dx; sj += dy; sii += dx * dx; sjj += dy * dy; sij += dx * dy;
+              sh += dh; sih += dx * dh; sjh += dy * dh;
+            }
+          }
+          // centred normal equations scaled by n (exact integers on the left)
+          const int cxx = n * sii - si * si, cyy = n * sjj - sj * sj, cxy = n * sij - si * sj;
+          const int det = cxx * cyy - cxy * cxy;  // 0 iff the valid cells are collinear
+          if (n >= 3 && det != 0) {
+            const float cxh = n * sih - si * sh, cyh = n * sjh - sj * sh;
+            const float a = ((float)cyy * cxh - (float)cxy * cyh) / ((float)det * m.res);
+            const float bb = ((float)cxx * cyh - (float)cxy * cxh) / ((float)det * m.res);
+            const float inv = rsqrtf(a * a + bb * bb + 1.f);
+            rx = -a * inv;
+            ry = -bb * inv;
+            rz = inv;
+          }
+        }
+        const int32_t p = phys_index(m, lx, ly);
+        m.nx[p] = rx;
+        m.ny[p] = ry;
+        m.nz[p] = rz;
       }
+      __syncthreads();
     }
-    m.nx[p] = rx;
-    m.ny[p] = ry;
-    m.nz[p] = rz;
   }
-  });
 }
 
 // 5x5 smoothing of valid cells over the valid cells of the window (Section
@@ -76,71 +98,87 @@ __global__ void __launch_bounds__(kMapThreads) k_normals(const BatchDev* __restr
 // rank floor((n - 1) / 2) of the n valid heights, found by counting ranks in
 // registers) or a Gaussian with sigma = 1 cell renormalised over the valid
 // cells (EM_F_GAUSS).  Sums run in a fixed window order.
+// Smoothing works on logical tiles of kSmT x kSmT cells: the heights of the
+// tile and a 2-cell rim (+inf where empty or outside the map) are staged in
+// shared memory once, so the 25 reads of a cell's window hit shared memory.
+constexpr int kSmT = 32, kSmRim = 2, kSmSpan = kSmT + 2 * kSmRim;
+static_assert(kSmT * kSmT == 4 * kMapThreads, "k_smooth: four cells per thread");
+
 __global__ void __launch_bounds__(kMapThreads) k_smooth(const BatchDev* __restrict__ bp) {
+  __shared__ float s_h[kSmSpan][kSmSpan + 1];
   const BatchDev& b = *bp;
-  for_each_tile(b, [&](const MapDev& m, int, int32_t p0, int32_t count) {
-  if (!m.smooth) return;
-  const int mode = (m.flags & EM_F_MEDIAN) ? 1 : (m.flags & EM_F_GAUSS) ? 2 : 0;
-  for (int32_t i = threadIdx.x; i < count; i += kMapThreads) {
-    const int32_t p = p0 + i;
-    int32_t lx, ly;
-    logical_of(m, p, lx, ly);
-    float out = qnan();
-    if (valid_at(m, p)) {
-      float v[25];  // the window's heights, +inf where not valid
-      int n = 0;
+  for (int mi = 0; mi < b.n_maps; ++mi) {
+    const MapDev& m = b.maps[mi];
+    if (!m.smooth) continue;
+    const int mode = (m.flags & EM_F_MEDIAN) ? 1 : (m.flags & EM_F_GAUSS) ? 2 : 0;
+    const int32_t ntx = (m.W + kSmT - 1) / kSmT, nty = (m.H + kSmT - 1) / kSmT;
+    for (int32_t tile = blockIdx.x; tile < ntx * nty; tile += gridDim.x) {
+      const int32_t x0 = (tile % ntx) * kSmT - kSmRim, y0 = (tile / ntx) * kSmT - kSmRim;  // window origin
+      for (int e = threadIdx.x; e < kSmSpan * kSmSpan; e += kMapThreads) {
+        const int wi = e % kSmSpan, wj = e / kSmSpan;
+        const int32_t x = x0 + wi, y = y0 + wj;
+        float h = pinf();
+        if (x >= 0 && x < m.W && y >= 0 && y < m.H) {
+          const int32_t q = phys_index(m, x, y);
+          if (valid_at(m, q)) h = m.h[q];
+        }
+        s_h[wj][wi] = h;
+      }
+      __syncthreads();
+      for (int k = 0; k < 4; ++k) {
+        const int ci = threadIdx.x % kSmT, cj = threadIdx.x / kSmT + k * (kMapThreads / kSmT);
+        const int32_t lx = x0 + kSmRim + ci, ly = y0 + kSmRim + cj;
+        if (lx >= m.W || ly >= m.H) continue;
+        float out = qnan();
+        if (s_h[cj + kSmRim][ci + kSmRim] != pinf()) {  // a valid centre
+          float v[25];  // the window's heights, +inf where not valid
+          int n = 0;
 #pragma unroll
-      for (int dy = -2; dy <= 2; ++dy) {
+          for (int dy = 0; dy < 5; ++dy)
 #pragma unroll
-        for (int dx = -2; dx <= 2; ++dx) {
-          const int32_t jx = lx + dx, jy = ly + dy;
-          float h = pinf();
-          if (jx >= 0 && jx < m.W && jy >= 0 && jy < m.H) {
-            const int32_t q = phys_index(m, jx, jy);
-            if (valid_at(m, q)) {
-              h = m.h[q];
-              ++n;
+            for (int dx = 0; dx < 5; ++dx) {
+              const float h = s_h[cj + dy][ci + dx];
+              n += h != pinf();
+              v[dy * 5 + dx] = h;
             }
+          if (mode == 0) {
+            float s = 0.f;
+#pragma unroll
+            for (int q = 0; q < 25; ++q)
+              if (v[q] != pinf()) s += v[q];
+            out = s / (float)n;
+          } else if (mode == 1) {
+            // rank of v[q] = #{j : v[j] < v[q]} + #{j < q : v[j] == v[q]}; the invalid
+            // (+inf) entries rank last, so rank (n - 1) / 2 is the lower median
+            const int want = (n - 1) / 2;
+#pragma unroll
+            for (int q = 0; q < 25; ++q) {
+              int rank = 0;
+#pragma unroll
+              for (int j = 0; j < 25; ++j) rank += (v[j] < v[q]) || (j < q && v[j] == v[q]);
+              if (rank == want) out = v[q];
+            }
+          } else {
+            float s = 0.f, ws = 0.f;
+#pragma unroll
+            for (int dy = -2; dy <= 2; ++dy) {
+#pragma unroll
+              for (int dx = -2; dx <= 2; ++dx) {
+                const float h = v[(dy + 2) * 5 + dx + 2];
+                if (h == pinf()) continue;
+                const float w = expf(-0.5f * (float)(dx * dx + dy * dy));
+                s = __fmaf_rn(w, h, s);
+                ws += w;
+              }
+            }
+            out = __fdiv_rn(s, ws);
           }
-          v[(dy + 2) * 5 + dx + 2] = h;
         }
+        m.smooth[phys_index(m, lx, ly)] = out;
       }
-      if (mode == 0) {
-        float s = 0.f;
-#pragma unroll
-        for (int k = 0; k < 25; ++k)
-          if (v[k] != pinf()) s += v[k];
-        out = s / (float)n;
-      } else if (mode == 1) {
-        // rank of v[k] = #{j : v[j] < v[k]} + #{j < k : v[j] == v[k]}; the invalid
-        // (+inf) entries rank last, so rank (n - 1) / 2 is the lower median
-        const int want = (n - 1) / 2;
-#pragma unroll
-        for (int k = 0; k < 25; ++k) {
-          int rank = 0;
-#pragma unroll
-          for (int j = 0; j < 25; ++j) rank += (v[j] < v[k]) || (j < k && v[j] == v[k]);
-          if (rank == want) out = v[k];
-        }
-      } else {
-        float s = 0.f, ws = 0.f;
-#pragma unroll
-        for (int dy = -2; dy <= 2; ++dy) {
-#pragma unroll
-          for (int dx = -2; dx <= 2; ++dx) {
-            const float h = v[(dy + 2) * 5 + dx + 2];
-            if (h == pinf()) continue;
-            const float w = expf(-0.5f * (float)(dx * dx + dy * dy));
-            s = __fmaf_rn(w, h, s);
-            ws += w;
-          }
-        }
-        out = __fdiv_rn(s, ws);
-      }
+      __syncthreads();
     }
-    m.smooth[p] = out;
   }
-  });
 }
 
 // Every empty cell explores its 4-connected component of empty cells until
