@@ -592,6 +592,33 @@ def test_inpainting(oracle_mod):
     assert np.array_equal(ip[fin], h[fin])
 
 
+def test_inpainting_component_shapes(oracle_mod):
+    """Holes are 4-connected: lines and L shapes of 8 cells are filled, of 9
+    are not, and cells touching only at a corner are separate holes."""
+    rng = np.random.default_rng(3)
+    h = rng.uniform(0.0, 1.0, (24, 24))
+    h[2:10, 2] = np.nan                                # vertical line of 8: filled
+    h[2:11, 6] = np.nan                                # vertical line of 9: too large
+    h[14, 2:7] = np.nan
+    h[15:18, 6] = np.nan                               # L of 8: filled
+    h[14, 10:15] = np.nan
+    h[15:19, 14] = np.nan                              # L of 9: too large
+    h[20, 18] = np.nan
+    h[21, 19] = np.nan                                 # diagonal neighbours: two holes of one cell
+    s = _field(oracle_mod, h, oracle_mod.INPAINT)
+    ip = s["inpaint"]
+    assert np.allclose(ip[2:10, 2], np.nanmin(h[1:11, 1:4]))
+    assert np.all(np.isnan(ip[2:11, 6]))
+    L8 = np.isnan(h) & (np.arange(24)[:, None] >= 14) & (np.arange(24)[:, None] <= 17) & (np.arange(24)[None, :] <= 7)
+    ring = np.zeros_like(L8)
+    for y, x in zip(*np.nonzero(L8)):
+        ring[y - 1:y + 2, x - 1:x + 2] = True
+    assert np.allclose(ip[L8], np.nanmin(np.where(ring & np.isfinite(h), h, np.nan)))
+    assert np.all(np.isnan(ip[14, 10:15])) and np.all(np.isnan(ip[15:19, 14]))
+    assert ip[20, 18] == pytest.approx(np.nanmin(h[19:22, 17:20]))
+    assert ip[21, 19] == pytest.approx(np.nanmin(h[20:23, 18:21]))
+
+
 # --------------------------------------------------------------------- shift
 
 def test_shift(oracle_mod):
