@@ -62,3 +62,22 @@ def test_job_rate_and_single_rank():
     assert bench.rank_max(1, "cpu")(3.25) == 3.25
     # 2 ranks x 1e6 points, slowest rank 0.5 s -> 4e6 points/s for the job
     assert bench.job_rate(1e6, 2, 0.5) == 4e6
+
+
+def test_reference_line_keeps_the_contract():
+    """The reference arm's line (the oracle on the host) carries every key of the
+    bench contract, with the served metric and workload of our arm."""
+    import json
+    import bench
+
+    class A:
+        steps, warmup = 1, 0
+    line = bench.run_reference(A(), 0, 1)
+    json.dumps(line)  # one JSON line
+    for k in ("metric", "impl", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == "points/s"
+    assert line["config"]["workload"] == bench.WORKLOAD and line["value"] > 0
+    assert set(line["cpu_baseline"]) >= {"value", "unit", "cores", "kind", "sample"}
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
