@@ -382,9 +382,10 @@ int em_server_submit_many(em_server* srv, const em_request* reqs, int32_t n, voi
  * finished in time (the request stays queued).  Fills *out and forgets the
  * ticket once finished. */
 int em_server_wait(em_server* srv, uint64_t ticket, int64_t timeout_us, em_result* out);
-/* Wait for n tickets (timeout_us < 0: forever, else for all of them together).
- * On EM_OK every ticket is finished and forgotten and out[i] (if out is not
- * NULL) is ticket i's result; on EM_ERR_TIMEOUT none is forgotten. */
+/* Wait for n distinct tickets (timeout_us < 0: forever, else for all of them
+ * together).  On EM_OK every ticket is finished and forgotten and out[i] (if
+ * out is not NULL) is ticket i's result; on EM_ERR_TIMEOUT none is forgotten.
+ * EM_ERR_INVALID_ARG for an unknown or repeated ticket. */
 int em_server_wait_many(em_server* srv, const uint64_t* tickets, int32_t n, int64_t timeout_us, em_result* out);
 /* Withdraw a request that has not been launched; EM_ERR_BUSY if it already runs. */
 int em_server_cancel(em_server* srv, uint64_t ticket);

@@ -473,27 +473,40 @@ int em_server_submit_many(em_server* s, const em_request* reqs, int32_t n, void*
 int em_server_wait(em_server* s, uint64_t ticket, int64_t timeout_us, em_result* out) {
   if (!s) return EM_ERR_INVALID_ARG;
   std::unique_lock<std::mutex> lk(s->mu);
-  auto it = s->reqs.find(ticket);
-  if (it == s->reqs.end()) return EM_ERR_INVALID_ARG;
-  auto done = [&] { return s->reqs[ticket].state == kDone; };
+  if (s->reqs.find(ticket) == s->reqs.end()) return EM_ERR_INVALID_ARG;
+  // find, never operator[]: another thread may have waited for (and forgotten)
+  // the same ticket meanwhile, and a lookup must not bring it back
+  auto done = [&] {
+    auto it = s->reqs.find(ticket);
+    return it == s->reqs.end() || it->second.state == kDone;
+  };
   if (timeout_us < 0) {
     s->cv_done.wait(lk, done);
   } else if (!s->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), done)) {
     return EM_ERR_TIMEOUT;
   }
-  if (out) *out = s->reqs[ticket].res;
-  s->reqs.erase(ticket);
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return EM_ERR_INVALID_ARG;
+  if (out) *out = it->second.res;
+  s->reqs.erase(it);
   return EM_OK;
 }
 
 int em_server_wait_many(em_server* s, const uint64_t* tickets, int32_t n, int64_t timeout_us, em_result* out) {
   if (!s || n < 0 || (n > 0 && !tickets)) return EM_ERR_INVALID_ARG;
+  {  // each ticket once
+    std::vector<uint64_t> t(tickets, tickets + n);
+    std::sort(t.begin(), t.end());
+    if (std::adjacent_find(t.begin(), t.end()) != t.end()) return EM_ERR_INVALID_ARG;
+  }
   std::unique_lock<std::mutex> lk(s->mu);
   for (int32_t i = 0; i < n; ++i)
     if (s->reqs.find(tickets[i]) == s->reqs.end()) return EM_ERR_INVALID_ARG;
-  auto done = [&] {
-    for (int32_t i = 0; i < n; ++i)
-      if (s->reqs[tickets[i]].state != kDone) return false;
+  auto done = [&] {  // (find, never operator[]: see em_server_wait)
+    for (int32_t i = 0; i < n; ++i) {
+      auto it = s->reqs.find(tickets[i]);
+      if (it != s->reqs.end() && it->second.state != kDone) return false;
+    }
     return true;
   };
   if (timeout_us < 0) {
@@ -501,11 +514,17 @@ int em_server_wait_many(em_server* s, const uint64_t* tickets, int32_t n, int64_
   } else if (!s->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), done)) {
     return EM_ERR_TIMEOUT;
   }
+  int rc = EM_OK;
   for (int32_t i = 0; i < n; ++i) {
-    if (out) out[i] = s->reqs[tickets[i]].res;
-    s->reqs.erase(tickets[i]);
+    auto it = s->reqs.find(tickets[i]);
+    if (it == s->reqs.end()) {  // forgotten by a concurrent wait
+      rc = EM_ERR_INVALID_ARG;
+      continue;
+    }
+    if (out) out[i] = it->second.res;
+    s->reqs.erase(it);
   }
-  return EM_OK;
+  return rc;
 }
 
 int em_server_cancel(em_server* s, uint64_t ticket) {
