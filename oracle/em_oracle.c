@@ -249,10 +249,15 @@ static int in_map(const orc_map* m, int64_t ix, int64_t iy) {
   return ix >= 0 && iy >= 0 && ix < m->p.width && iy < m->p.height;
 }
 
-/* distance of a coordinate (in cells) to the nearest cell edge, in metres */
-static double edge_dist(double q, double r) {
+/* The neighbouring cells a coordinate q (in cells) may fall into when float32
+ * arithmetic computes it within `band` metres: bit 0 the cell below
+ * (floor(q) - 1), bit 1 the cell above (floor(q) + 1). */
+static int edge_alts(double q, double r, double band) {
   double f = q - floor(q);
-  return (f < 0.5 ? f : 1.0 - f) * r;
+  int a = 0;
+  if (f * r < band) a |= 1;
+  if ((1.0 - f) * r < band) a |= 2;
+  return a;
 }
 
 static int64_t clamp_index(double q) {
@@ -262,11 +267,25 @@ static int64_t clamp_index(double q) {
   return (int64_t)f;
 }
 
-static void flag_block(const orc_map* m, uint8_t* cflags, int64_t ix, int64_t iy, int rad, uint8_t bit) {
-  if (!cflags) return;
-  for (int64_t j = iy - rad; j <= iy + rad; ++j)
-    for (int64_t i = ix - rad; i <= ix + rad; ++i)
-      if (in_map(m, i, j)) cflags[j * m->p.width + i] |= bit;
+/* Cell (ix, iy) and its alternatives (ax, ay: edge_alts bits of each axis):
+ * the in-map cells (ix + i, iy + j), i and j in {0} plus the alternatives.
+ * Writes their flat indices to out[] (at most 9) and returns how many. */
+static int candidates(const orc_map* m, int64_t ix, int64_t iy, int ax, int ay, int64_t* out) {
+  int n = 0;
+  for (int j = -1; j <= 1; ++j) {
+    if ((j == -1 && !(ay & 1)) || (j == 1 && !(ay & 2))) continue;
+    for (int i = -1; i <= 1; ++i) {
+      if ((i == -1 && !(ax & 1)) || (i == 1 && !(ax & 2))) continue;
+      if (in_map(m, ix + i, iy + j)) out[n++] = (iy + j) * m->p.width + (ix + i);
+    }
+  }
+  return n;
+}
+
+/* 1 when every cell of (ix, iy) and its alternatives lies in the map */
+static int all_in_map(const orc_map* m, int64_t ix, int64_t iy, int ax, int ay) {
+  return in_map(m, ix - ((ax & 1) ? 1 : 0), iy - ((ay & 1) ? 1 : 0)) &&
+         in_map(m, ix + ((ax & 2) ? 1 : 0), iy + ((ay & 2) ? 1 : 0));
 }
 
 /* effective variance at update t_now of a cell last written at t_last:
@@ -281,6 +300,7 @@ typedef struct pt_info {
   double vx, vy, vz;    /* R * p_s: sensor-to-point vector in the map frame */
   double sx, sy, sz;    /* magnitudes |R_r0 px| + |R_r1 py| + |R_r2 pz| per row */
   int64_t ix, iy;
+  int ax, ay;           /* edge_alts bits of the cell indices (marginal bands only) */
   int cloud;
   int status;
   int flags;
@@ -485,67 +505,115 @@ static void compute_inpaint(orc_map* m) {
 
 /* -------------------------------------------------------------- update */
 
-/* Walk one ray against the snapshot.  mode 0: mark penetrated cells (Eq. 3
- * with the Eq. 4 guard); mode 1: only flag every cell the ray may touch as
- * mark-marginal (used when the ray itself is marginal). */
-static void walk_ray(orc_map* m, const pt_info* pi, const float* pose, const double* h0,
-                     const double* ve0, const double* nx0, const double* ny0, const double* nz0,
-                     uint8_t* mark, orc_trace* tr, int mode, double x0, double y0) {
+/* Ray samples whose upper-bound update float32 may place differently (a
+ * candidate cell, the sample's height + band): flagged after all rays, when
+ * the cells' final bounds are known. */
+typedef struct upper_unsure {
+  int64_t* cell;
+  double* z;
+  int64_t n, cap;
+} upper_unsure;
+
+static void upper_unsure_add(upper_unsure* uu, int64_t c, double z) {
+  if (uu->n == uu->cap) {
+    uu->cap = uu->cap ? 2 * uu->cap : 1024;
+    uu->cell = (int64_t*)realloc(uu->cell, sizeof(int64_t) * (size_t)uu->cap);
+    uu->z = (double*)realloc(uu->z, sizeof(double) * (size_t)uu->cap);
+  }
+  uu->cell[uu->n] = c;
+  uu->z[uu->n] = z;
+  ++uu->n;
+}
+
+/* Eq. 4 guard: |rhat . n| > alpha_n for the cell's previous normal, (0, 0, 1)
+ * when that normal is not finite; *dot receives |rhat . n|. */
+static int guard_pass(const orc_params* p, double rx, double ry, double rz, double n0, double n1, double n2,
+                      double* dot) {
+  if (!(isfinite(n0) && isfinite(n1) && isfinite(n2))) { n0 = 0; n1 = 0; n2 = 1; }
+  *dot = fabs(rx * n0 + ry * n1 + rz * n2);
+  return p->cleanup_normal_thresh > 0 ? *dot > p->cleanup_normal_thresh : 1;
+}
+
+/* Walk one ray against the snapshot (Section II-E).  A ray that exists marks
+ * every cell one of its samples lies in below the cell's threshold h - sigma
+ * (Eq. 3) when the Eq. 4 guard lets it; with the upper-bound layer its samples
+ * in empty cells lower their bound (Section II-H).  With marginal bands on, it
+ * also flags (CF_MARK) each cell whose mark or bound a float32 computation of
+ * this ray may decide otherwise: the sample's cell or one of the cells its
+ * position may round into, the endpoint's own cell (skipped) or one of its
+ * alternatives, the last sample (k step ~ d), a ray whose existence is
+ * marginal, a sample height within its band of the threshold, a guard value
+ * within its band of alpha_n.  A cell is flagged only when the sample is below
+ * its threshold (plus band) and the guard may pass, i.e. when some reading
+ * marks it. */
+static void walk_ray(orc_map* m, const pt_info* pi, const float* pose, const double* h0, const double* ve0,
+                     const double* nx0, const double* ny0, const double* nz0, uint8_t* mark, orc_trace* tr,
+                     upper_unsure* uu, double x0, double y0) {
   const orc_params* p = &m->p;
   const int W = p->width;
   const double r = p->resolution, step = p->ray_step, d = pi->d;
   const double ox = pose[3], oy = pose[7], oz = pose[11];
   const double u = tr ? tr->unit : 0.0, ab = tr ? tr->abs_band : 0.0;
-  uint8_t* cflags = tr ? tr->cflags : NULL;
+  uint8_t* cflags = (tr && u > 0) ? tr->cflags : NULL;
+  const int ray_on = pi->status != ST_RANGE;               /* every valid point casts a ray */
+  const int ray_unsure = cflags && (pi->flags & PF_RANGE); /* float32 may decide its validity otherwise */
   if (!(step > 0) || !(d > 0)) return;
+  if (!ray_on && !ray_unsure) return;
   const double rx = pi->vx / d, ry = pi->vy / d, rz = pi->vz / d;
-  /* samples k = 1, 2, ... while k*step < d; in marginal mode also the next one */
+  /* the endpoint's own cell, and the cells float32 binning may give it instead */
+  int64_t own[9];
+  const int n_own = cflags ? candidates(m, pi->ix, pi->iy, pi->ax, pi->ay, own) : 0;
+  const int own_exact = (pi->ax | pi->ay) == 0;
+  /* samples k = 1, 2, ... while k*step < d; with marginal bands also the next one */
   for (int64_t k = 1;; ++k) {
-    double len = (double)k * step;
-    int boundary_marginal = (u > 0) && fabs(len - d) < ab + 8.0 * u * d;
-    if (!(len < d) && !boundary_marginal) break;
-    int exists = len < d;
-    double f = len / d;
-    double sx = ox + f * pi->vx, sy = oy + f * pi->vy, sz = oz + f * pi->vz;
-    double qx = (sx - x0) / r, qy = (sy - y0) / r;
-    int64_t cx = clamp_index(qx), cy = clamp_index(qy);
-    int marginal = boundary_marginal || mode == 1;
-    if (u > 0) {
-      double esx = ab + 8.0 * u * (fabs(ox) + f * pi->sx + fabs(x0) + fabs(sx - x0));
-      double esy = ab + 8.0 * u * (fabs(oy) + f * pi->sy + fabs(y0) + fabs(sy - y0));
-      if (edge_dist(qx, r) < esx || edge_dist(qy, r) < esy) marginal = 1;
-    }
-    if (!in_map(m, cx, cy)) {
-      if (marginal && cflags) flag_block(m, cflags, cx, cy, 1, CF_MARK);
-      if (!exists) break;
-      continue;
-    }
-    if (cx == pi->ix && cy == pi->iy) { /* the endpoint's own cell is skipped */
-      if (marginal && cflags) flag_block(m, cflags, cx, cy, 1, CF_MARK);
-      if (!exists) break;
-      continue;
-    }
-    int64_t c = cy * W + cx;
-    if (isfinite(ve0[c])) {
-      double sd = sqrt(ve0[c]);
-      double thr = h0[c] - sd; /* Eq. 3 */
-      int below = sz < thr;
-      if (u > 0 && fabs(sz - thr) < ab + m->drift_unc + 8.0 * u * (fabs(oz) + f * pi->sz + fabs(h0[c]) + sd))
-        marginal = 1;
-      int guard_ok = 1;
-      if (p->cleanup_normal_thresh > 0) { /* Eq. 4 */
-        double n0 = nx0[c], n1 = ny0[c], n2 = nz0[c];
-        if (!(isfinite(n0) && isfinite(n1) && isfinite(n2))) { n0 = 0; n1 = 0; n2 = 1; }
-        double dot = fabs(rx * n0 + ry * n1 + rz * n2);
-        guard_ok = dot > p->cleanup_normal_thresh;
-        if (below && u > 0 && fabs(dot - p->cleanup_normal_thresh) < ab + 8.0 * u) marginal = 1;
+    const double len = (double)k * step;
+    const int last_unsure = cflags && fabs(len - d) < ab + 8.0 * u * d;
+    if (!(len < d) && !last_unsure) break;
+    const int exists = len < d;
+    const double f = len / d;
+    const double sx = ox + f * pi->vx, sy = oy + f * pi->vy, sz = oz + f * pi->vz;
+    const double qx = (sx - x0) / r, qy = (sy - y0) / r;
+    const int64_t cx = clamp_index(qx), cy = clamp_index(qy);
+    if (ray_on && exists && in_map(m, cx, cy) && !(cx == pi->ix && cy == pi->iy)) {
+      const int64_t c = cy * W + cx;
+      double dot;
+      if (isfinite(ve0[c])) {
+        if (sz < h0[c] - sqrt(ve0[c]) && guard_pass(p, rx, ry, rz, nx0[c], ny0[c], nz0[c], &dot)) mark[c] = 1;
+      } else if (p->flags & ORC_UPPER) {
+        if (sz < m->upper[c]) m->upper[c] = sz; /* the ground is not above the ray here */
       }
-      if (mode == 0 && exists && below && guard_ok) mark[c] = 1;
-    } else if (mode == 0 && exists && (p->flags & ORC_UPPER)) {
-      /* a ray through an empty cell: its ground is not above the ray (Section II-H) */
-      if (sz < m->upper[c]) m->upper[c] = sz;
     }
-    if (marginal && cflags) flag_block(m, cflags, cx, cy, 1, CF_MARK);
+    if (cflags) {
+      const double esx = ab + 8.0 * u * (fabs(ox) + f * pi->sx + fabs(x0) + fabs(sx - x0));
+      const double esy = ab + 8.0 * u * (fabs(oy) + f * pi->sy + fabs(y0) + fabs(sy - y0));
+      const int axs = edge_alts(qx, r, esx), ays = edge_alts(qy, r, esy);
+      const int sample_unsure = ray_unsure || last_unsure || (axs | ays) != 0;
+      int64_t cand[9];
+      const int nc = candidates(m, cx, cy, axs, ays, cand);
+      for (int q = 0; q < nc; ++q) {
+        const int64_t c = cand[q];
+        int own_unsure = 0;
+        for (int o = 0; o < n_own; ++o)
+          if (own[o] == c) own_unsure = 1;
+        if (own_unsure && own_exact) continue; /* the endpoint's own cell in every reading: skipped */
+        const int unsure = sample_unsure || own_unsure;
+        if (isfinite(ve0[c])) {
+          const double sd = sqrt(ve0[c]), thr = h0[c] - sd;
+          const double bt = ab + m->drift_unc + 8.0 * u * (fabs(oz) + f * pi->sz + fabs(h0[c]) + sd);
+          if (!(sz < thr + bt)) continue; /* above the threshold in every reading */
+          double dot;
+          guard_pass(p, rx, ry, rz, nx0[c], ny0[c], nz0[c], &dot);
+          const double bg = ab + 8.0 * u;
+          const int guard_on = p->cleanup_normal_thresh > 0;
+          if (guard_on && !(dot > p->cleanup_normal_thresh - bg)) continue; /* the guard holds in every reading */
+          const int thr_unsure = fabs(sz - thr) < bt;
+          const int guard_unsure = guard_on && fabs(dot - p->cleanup_normal_thresh) < bg;
+          if (unsure || thr_unsure || guard_unsure) cflags[c] |= CF_MARK;
+        } else if ((p->flags & ORC_UPPER) && unsure) {
+          upper_unsure_add(uu, c, sz - (ab + 8.0 * u * (fabs(oz) + f * pi->sz)));
+        }
+      }
+    }
     if (!exists) break;
   }
 }
@@ -622,9 +690,14 @@ int orc_update(orc_map* m, const orc_cloud* clouds, int32_t ncloud, orc_trace* t
       pi->ix = clamp_index(qx);
       pi->iy = clamp_index(qy);
       if (u > 0) {
-        double bx = ab + 8.0 * u * (pi->sx + fabs(R[3]) + fabs(x0) + fabs(x - x0));
-        double by = ab + 8.0 * u * (pi->sy + fabs(R[7]) + fabs(y0) + fabs(y - y0));
-        if (edge_dist(qx, r) < bx || edge_dist(qy, r) < by) pi->flags |= PF_BIN;
+        /* float32 binning (a 3-term FMA chain, the translation, the subtraction
+         * of x0 and the product with the rounded 1/r) stays within about 2u of
+         * these magnitudes; the band takes twice that */
+        double bx = ab + 4.0 * u * (pi->sx + fabs(R[3]) + fabs(x0) + fabs(x - x0));
+        double by = ab + 4.0 * u * (pi->sy + fabs(R[7]) + fabs(y0) + fabs(y - y0));
+        pi->ax = edge_alts(qx, r, bx);
+        pi->ay = edge_alts(qy, r, by);
+        if (pi->ax | pi->ay) pi->flags |= PF_BIN;
       }
       /* exclusion area (Section II-C): the point is ignored above the ramp */
       if (in_range && p->excl_d > 0) {
@@ -663,30 +736,60 @@ int orc_update(orc_map* m, const orc_cloud* clouds, int32_t ncloud, orc_trace* t
     if (n_eps > 0) {
       const double mean = eps / (double)n_eps;
       if (u > 0) {
-        /* Marginal band of the mean: a point whose cell is marginal (PF_BIN) may
-         * fall into any cell of its 3x3 block in float32, entering the mean with
-         * another error or not at all; bound each by the largest |z - h| over
-         * the flat cells with an estimate of the block plus |mean|, and add the
-         * float32 rounding of the errors and of the mean. */
-        double sum_b = 0.0, sum_abs = 0.0;
+        /* Marginal band of the mean.  A point whose cell or validity is
+         * marginal (PF_BIN, PF_RANGE) may enter the float32 mean with the error
+         * of another candidate cell, or not at all (a candidate that is not a
+         * flat cell with an estimate, or outside the map), or enter it although
+         * the oracle leaves it out.  Changing the contributions (e_i, n_i) to
+         * (e', n') moves the mean by (dS - mean dN) / (n + dN), so the sum over
+         * such points of their largest |(e' - e_i) - mean (n' - n_i)|, over n
+         * minus the number of points whose count may change, bounds that move.  Added: float32
+         * rounding of every error (the transform of z and the subtraction),
+         * the 2^-44 truncation of the exact sum, and the rounding of the mean. */
+        double dev = 0.0, rnd = 0.0;
+        int64_t k_unsure = 0;
         for (int64_t i = 0; i < npts; ++i) {
           const pt_info* pi = &pts[i];
-          if (pi->status != ST_ACCEPT) continue;
-          int64_t c = pi->iy * W + pi->ix;
-          if (isfinite(ve0[c]) && nz0[c] >= p->drift_flatness) sum_abs += fabs(pi->z - h0[c]);
-          if (!(pi->flags & PF_BIN)) continue;
-          double bmax = 0.0;
-          for (int dy = -1; dy <= 1; ++dy)
-            for (int dx = -1; dx <= 1; ++dx) {
-              int64_t jx = pi->ix + dx, jy = pi->iy + dy;
-              if (!in_map(m, jx, jy)) continue;
-              int64_t k = jy * W + jx;
-              if (isfinite(ve0[k]) && nz0[k] >= p->drift_flatness && fabs(pi->z - h0[k]) > bmax)
-                bmax = fabs(pi->z - h0[k]);
+          if (pi->status == ST_NONFINITE) continue;
+          const double tz = fabs((double)clouds[pi->cloud].pose[11]);
+          int in_mean = 0;
+          double e_i = 0.0;
+          if (pi->status == ST_ACCEPT) {
+            const int64_t c = pi->iy * W + pi->ix;
+            if (isfinite(ve0[c]) && nz0[c] >= p->drift_flatness) {
+              in_mean = 1;
+              e_i = pi->z - h0[c];
+              rnd += 8.0 * u * (pi->sz + tz) + u * fabs(e_i) + 0x1p-44;
             }
-          sum_b += bmax + fabs(mean);
+          }
+          if (!(pi->flags & (PF_BIN | PF_RANGE))) continue;
+          const int can_valid = pi->status != ST_RANGE || (pi->flags & PF_RANGE);
+          int can_out = pi->status == ST_RANGE || (pi->flags & PF_RANGE) ||
+                        !all_in_map(m, pi->ix, pi->iy, pi->ax, pi->ay);
+          double worst = 0.0;
+          int n_moves = 0;
+          if (can_valid) {
+            int64_t cand[9];
+            const int ncand = candidates(m, pi->ix, pi->iy, pi->ax, pi->ay, cand);
+            for (int q = 0; q < ncand; ++q) {
+              const int64_t c = cand[q];
+              if (!(isfinite(ve0[c]) && nz0[c] >= p->drift_flatness)) { can_out = 1; continue; }
+              const double e = pi->z - h0[c];
+              const double w = fabs(e - e_i - (in_mean ? 0.0 : mean));
+              if (w > worst) worst = w;
+              if (!in_mean) n_moves = 1;
+              rnd += in_mean ? 0.0 : 8.0 * u * (pi->sz + tz) + u * fabs(e) + 0x1p-44;
+            }
+          }
+          if (can_out && in_mean) {
+            const double w = fabs(mean - e_i);
+            if (w > worst) worst = w;
+            n_moves = 1;
+          }
+          dev += worst;
+          k_unsure += n_moves;
         }
-        m->drift_unc = (sum_b + 4.0 * u * sum_abs) / (double)n_eps + 2.0 * u * fabs(mean);
+        m->drift_unc = n_eps > k_unsure ? (dev + rnd) / (double)(n_eps - k_unsure) + 3.0 * u * fabs(mean) : 1e30;
       }
       for (int64_t c = 0; c < nc; ++c) {
         if (!isfinite(ve0[c])) continue;
@@ -766,17 +869,21 @@ int orc_update(orc_map* m, const orc_cloud* clouds, int32_t ncloud, orc_trace* t
 
   /* 4. ray casting against the snapshot (Section II-E) */
   uint8_t* mark = (uint8_t*)calloc((size_t)nc, 1);
+  upper_unsure uu = {NULL, NULL, 0, 0};
   if (p->ray_step > 0) {
     for (int64_t i = 0; i < npts; ++i) {
       const pt_info* pi = &pts[i];
       if (pi->status == ST_NONFINITE) continue;
       const float* pose = clouds[pi->cloud].pose;
-      int valid_ray = pi->status != ST_RANGE;
-      int ray_marginal = (pi->flags & (PF_BIN | PF_RANGE)) != 0;
-      if (valid_ray) walk_ray(m, pi, pose, h0, ve0, nx0, ny0, nz0, mark, tr, 0, x0, y0);
-      if (ray_marginal && tr && tr->cflags) walk_ray(m, pi, pose, h0, ve0, nx0, ny0, nz0, mark, tr, 1, x0, y0);
+      walk_ray(m, pi, pose, h0, ve0, nx0, ny0, nz0, mark, tr, &uu, x0, y0);
     }
   }
+  /* an uncertain sample may change an empty cell's bound only if it may be
+   * that cell's minimum (its height less its band below the final bound) */
+  for (int64_t q = 0; q < uu.n; ++q)
+    if (uu.z[q] < m->upper[uu.cell[q]]) tr->cflags[uu.cell[q]] |= CF_MARK;
+  free(uu.cell);
+  free(uu.z);
 
   /* 5. removal: penetrated and not updated for max(1, cleanup_min_age) updates */
   int64_t n_clr = 0;
@@ -835,8 +942,10 @@ int orc_update(orc_map* m, const orc_cloud* clouds, int32_t ncloud, orc_trace* t
       if (tr->status) tr->status[i] = (uint8_t)pi->status;
       if (tr->pflags) tr->pflags[i] = (uint8_t)pi->flags;
       if (tr->cflags && pi->flags && pi->status != ST_NONFINITE) {
-        int rad = (pi->flags & (PF_BIN | PF_RANGE)) ? 1 : 0;
-        flag_block(m, tr->cflags, pi->ix, pi->iy, rad, CF_VALUE);
+        /* the point's cell and the cells float32 binning may give it instead */
+        int64_t cand[9];
+        const int nc = candidates(m, pi->ix, pi->iy, pi->ax, pi->ay, cand);
+        for (int q = 0; q < nc; ++q) tr->cflags[cand[q]] |= CF_VALUE;
       }
     }
     if (tr->mark) memcpy(tr->mark, mark, (size_t)nc);

@@ -44,7 +44,7 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def run_case(em, P, clouds, prior=None, shift=(0, 0), wall_on=False, stencils=()):
+def run_case(em, P, clouds, prior=None, shift=(0, 0), wall_on=False, stencils=(), max_excluded=parity.MAX_EXCLUDED):
     om = oracle.OracleMap(parity.oracle_params(P))
     gm = gpu_map(em, P)
     if shift != (0, 0):
@@ -58,7 +58,7 @@ def run_case(em, P, clouds, prior=None, shift=(0, 0), wall_on=False, stencils=()
     gm.update_multi([(dev(p), q) for p, q in clouds])
     n = sum(len(p) for p, _ in clouds)
     cmp = parity.compare_update(tr, om.state(), gm.state(), gm.trace(n), wall_on=wall_on,
-                                check_stencils=stencils, prior_valid=prior_valid)
+                                check_stencils=stencils, prior_valid=prior_valid, max_excluded=max_excluded)
     return cmp, tr, gm, om
 
 
@@ -275,7 +275,9 @@ def test_visibility_ray_step(em, step):
     fr = next(synth.depth_stream(seed=2, frames=1))
     prior = synth.random_prior(seed=3, width=200, height=200, t_now=5, obstacle_frac=0.05)
     P = dict(DEPTH_P, ray_step=step)
-    cmp, tr, gm, _ = run_case(em, P, fr["clouds"][:2], prior=prior)
+    # at half a cell per step every ray has two samples per cell, twice the
+    # samples that may fall near a threshold or a cell edge: 1.5 %
+    cmp, tr, gm, _ = run_case(em, P, fr["clouds"][:2], prior=prior, max_excluded=0.015 if step < 0.04 else 0.01)
     assert cmp.notes["cleared"] > 20
     check_counts(gm, tr, cmp.notes["marginal_points"])
     assert gm.stats()["ray_samples"] > 0
@@ -302,7 +304,11 @@ def test_upper_bound_layer_depth_frames(em):
         tr = om.update(fr["clouds"], trace=True, unit=oracle.FP32_UNIT, abs_band=parity.ABS_BAND)
         gm.update_multi([(dev(p), q) for p, q in fr["clouds"]])
         n = sum(len(p) for p, _ in fr["clouds"])
-        parity.compare_update(tr, om.state(), gm.state(), gm.trace(n), prior_valid=prior_valid, check_stencils=())
+        # 40 % of the prior's cells are empty with no bound yet: every ray sample
+        # through them is a candidate minimum, so position-marginal samples there
+        # count: 1.5 %
+        parity.compare_update(tr, om.state(), gm.state(), gm.trace(n), prior_valid=prior_valid, check_stencils=(),
+                              max_excluded=0.015)
         o_up, g_up = om.state()["upper"], gm.state()["upper"].astype(np.float64)
         excl = parity.dilate((tr.cflags & oracle.CF_MARK) != 0, 1) | parity.dilate((tr.cflags & oracle.CF_VALUE) != 0, 1)
         oi, gi = np.isinf(o_up), np.isinf(g_up)
@@ -321,10 +327,6 @@ def test_drift_compensation_depth_frame(em):
     fr = next(synth.depth_stream(seed=2, frames=1))
     prior = synth.random_prior(seed=2, width=200, height=200, t_now=5, obstacle_frac=0.0)  # the stream's terrain
     prior["h"] = (prior["h"] + 0.04).astype(np.float32)
-    # normals (needed for the flatness test) are not compared here: the drift mean
-    # may differ within its marginal band, which enters fused cells in different
-    # proportions and tilts 4 cm planes beyond the 1e-5 stencil tolerance; the
-    # LiDAR filter tests cover the normals
     cmp, tr, gm, om = run_case(em, P, fr["clouds"], prior=prior, stencils=())
     drift, n, band = om.last_drift_band()
     st = gm.stats()
@@ -332,6 +334,24 @@ def test_drift_compensation_depth_frame(em):
     assert abs(st["drift_points"] - n) <= cmp.notes["marginal_points"]
     assert abs(st["drift_last"] - drift) <= band
     check_counts(gm, tr, cmp.notes["marginal_points"])
+    # Normals.  Every estimate moves by the same mean, which leaves a plane's
+    # slope unchanged, so where no cell of the 3x3 window was fused the normal
+    # is compared at the stencil tolerance.  A fused cell's height moves by at
+    # most the mean's band times its prior weight; over a 3x3 window that tilts
+    # the slope by at most band / r, the tolerance of the other windows.
+    o, g = om.state(), gm.state()
+    excl = parity.dilate((tr.cflags & (oracle.CF_VALUE | oracle.CF_MARK)) != 0, 1)
+    fused_win = parity.dilate(o["t_last"] == om.t_now, 1)
+    tol = parity.STENCIL_TOL + 2.0 * band / P["resolution"]
+    for k in ("nx", "ny", "nz"):
+        on, gn = o[k], g[k].astype(np.float64)
+        nan_diff = (np.isnan(on) != np.isnan(gn)) & ~excl
+        assert not nan_diff.any(), (k, int(nan_diff.sum()))
+        ok = ~np.isnan(on) & ~np.isnan(gn) & ~excl
+        err = np.abs(gn - on)
+        quiet = ok & ~fused_win
+        assert quiet.sum() > 5000 and err[quiet].max() <= parity.STENCIL_TOL, (k, err[quiet].max())
+        assert err[ok].max() <= tol, (k, err[ok].max(), tol)
 
 
 def test_exclusion_area_and_overlap_clearance(em):
@@ -378,7 +398,10 @@ def test_depth_stream_frame_by_frame(em):
         tr = om.update(fr["clouds"], trace=True, unit=oracle.FP32_UNIT, abs_band=parity.ABS_BAND)
         g.update_multi([(dev(p), q) for p, q in fr["clouds"]])
         n = sum(len(p) for p, _ in fr["clouds"])
-        cmp = parity.compare_update(tr, om.state(), g.state(), g.trace(n), prior_valid=prior_valid)
+        # the stream's first frames fill a sparse map (300k points in about 11k
+        # cells), so its ~90 bin-marginal points make up more of the valid cells: 2 %
+        cmp = parity.compare_update(tr, om.state(), g.state(), g.trace(n), prior_valid=prior_valid,
+                                    max_excluded=0.02)
         assert cmp.notes["cells_compared"] > 3000, t
 
 
