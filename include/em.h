@@ -361,10 +361,13 @@ int em_server_submit_after(em_server* srv, int32_t map_id, const em_cloud* cloud
 typedef struct em_request {
   int32_t map_id;
   int32_t n_clouds;          /* 1..8 */
-  const em_cloud* clouds;    /* device points, valid until the ticket finishes */
+  const em_cloud* clouds;    /* points valid until the ticket finishes (device memory unless clouds_on_host) */
   uint32_t read_mask;        /* EM_LAYER_* bits to read back right after the update; 0 = none */
   int32_t read_to_host;      /* read_dst is page-locked host memory (else device memory) */
   float* read_dst;           /* popcount(read_mask) * width * height floats, em_get_layers layout */
+  int32_t clouds_on_host;    /* clouds[i].points are page-locked host memory: the server copies them by
+                                DMA (one cudaMemcpyAsync per cloud, on the batch's stream, after `ready`)
+                                into a device input buffer of that stream before the update */
 } em_request;
 
 /* Queue n requests under one lock, so that those that fit reach the same batch;
@@ -373,7 +376,10 @@ typedef struct em_request {
  * written to read_dst on the batch's stream right after its update (the map
  * state the update produced); its ticket finishes once they have landed.  A
  * host read_dst must be page-locked (cudaHostAlloc, cudaHostRegister): the GPU
- * writes it directly.  All or nothing: EM_ERR_INVALID_ARG for a malformed
+ * writes it directly.  Host clouds (clouds_on_host) must be page-locked too; the
+ * first such request makes the server allocate one input buffer of
+ * max_batch_points x 16 bytes per stream, counted in its byte budget
+ * (EM_ERR_REJECTED if it does not fit).  All or nothing: EM_ERR_INVALID_ARG for a malformed
  * request (pageable or unknown read_dst memory included) and EM_ERR_REJECTED
  * for one that can never fit leave nothing queued; else tickets[i] is request
  * i's ticket. */
@@ -399,9 +405,8 @@ int em_server_destroy(em_server* srv); /* NULL-safe: drains, stops the worker, f
 /* ---- Update without allocation.
  * The paper has no counterpart: this entry point exists for callers that
  * cannot allocate device memory when they update a map -- a real-time loop
- * that forbids allocation after start-up, a framework whose own allocator
- * already holds the device memory, or code running while a stream is being
- * captured.  It runs the update of em_update (binning, counting sort by cell,
+ * that forbids allocation after start-up, or a framework whose own allocator
+ * already holds the device memory.  It runs the update of em_update (binning, counting sort by cell,
  * wall rule, Mahalanobis gate, Eq. 1/2 fusion, ray march and removal; not the
  * per-cell filters) on layers the caller owns, in logical row-major order
  * without a ring offset:
@@ -422,8 +427,12 @@ int em_server_destroy(em_server* srv); /* NULL-safe: drains, stops the worker, f
  * what must start at zero); calls whose GPU work overlaps race on it.  Calls
  * no cudaMalloc / cudaFree.  Returns EM_ERR_CAPACITY when width*height >
  * EM_NOALLOC_MAX_CELLS, the points of all clouds > EM_NOALLOC_MAX_POINTS or
- * n_clouds > EM_NOALLOC_MAX_CLOUDS; EM_ERR_INVALID_ARG for bad arguments.
- * Asynchronous on `stream`; device-side errors are not reported. */
+ * n_clouds > EM_NOALLOC_MAX_CLOUDS; EM_ERR_INVALID_ARG for bad arguments
+ * (the library cannot check the layers' sizes: each must hold width*height
+ * elements).  The call's descriptor travels as a kernel parameter; it uses no
+ * host buffer and copies nothing between host and device.  Asynchronous on
+ * `stream`; a failed CUDA call returns EM_ERR_CUDA and is logged for
+ * em_last_cuda_error(); device-side errors are not reported. */
 #define EM_NOALLOC_MAX_CELLS 65536
 #define EM_NOALLOC_MAX_POINTS 327680
 #define EM_NOALLOC_MAX_CLOUDS 8

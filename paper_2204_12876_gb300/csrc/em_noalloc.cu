@@ -2,12 +2,13 @@
 //
 // Some callers cannot call cudaMalloc at update time: a real-time control loop
 // that forbids allocation after start-up (an allocation can block on the
-// driver for milliseconds), a host framework whose own caching allocator has
-// already claimed the device memory, or code that prepares work while a CUDA
-// stream is being captured.  For them this entry point runs the same kernels
-// as em_update (binning, counting sort by cell, gate + fusion, ray march,
-// removal) on map layers the caller owns, and keeps every piece of scratch
-// memory in one file-scope __device__ array of fixed size.
+// driver for milliseconds), or a host framework whose own caching allocator
+// has already claimed the device memory.  For them this entry point runs the
+// same kernels as em_update (binning, counting sort by cell, gate + fusion, ray
+// march, removal) on map layers the caller owns, and keeps every piece of
+// scratch memory in one file-scope __device__ array of fixed size.  The call's
+// descriptor goes to the device as a kernel parameter (no host buffer, no
+// copy), and its only other preparation is a memset of the scratch.
 //
 // Limits: at most kMaxCells cells per map and kMaxPoints points per update
 // (about 6.1 MiB of scratch, held by every GPU that loads the library until the
@@ -15,13 +16,14 @@
 // contents; the call clears what must start at zero.  Calls whose GPU work
 // overlaps (e.g. on two streams) race on the array.
 #include <cuda_runtime.h>
-#include <stdio.h>
 #include <string.h>
 
 #include <cmath>
+#include <cstddef>
 #include <mutex>
 
 #include "em.h"
+#include "em_host.h"
 #include "em_internal.cuh"
 
 using namespace em;
@@ -34,9 +36,18 @@ constexpr int kMaxCloudsNA = EM_NOALLOC_MAX_CLOUDS;
 
 constexpr size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// Everything one call's kernels read from the descriptor, passed by value to
+// k_put_desc (well below the 32 KB of a kernel's parameters).
+struct Desc {
+  BatchDev b;
+  MapDev m;
+  CloudDev c[kMaxCloudsNA];
+};
+static_assert(sizeof(Desc) <= 4096, "the descriptor travels as a kernel parameter");
+
 // scratch layout; the part that must start at zero (ctl, marks, counts) is contiguous
 constexpr size_t kOffDesc = 0;
-constexpr size_t kOffCtl = kOffDesc + up256(sizeof(BatchDev) + sizeof(MapDev) + kMaxCloudsNA * sizeof(CloudDev));
+constexpr size_t kOffCtl = kOffDesc + up256(sizeof(Desc));
 constexpr size_t kOffBCtl = kOffCtl + up256(sizeof(MapCtl));
 constexpr size_t kOffMark = kOffBCtl + up256(sizeof(BatchCtl));
 constexpr size_t kOffCnt = kOffMark + up256(((size_t)kMaxCells + 31) / 32 * sizeof(uint32_t));
@@ -50,20 +61,25 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 unsigned char* g_addr[kMaxDevices] = {};
 
-thread_local char g_msg[192] = "";
-
 }  // namespace
 
 // The scratch itself.  In host code this name is only a stand-in for the
 // device array: its device address comes from cudaGetSymbolAddress.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
+// The descriptor, from the kernel's parameters into the front of the scratch
+// (the kernels that follow on the stream read it there).
+static_assert(kOffDesc == 0 && sizeof(Desc) % 4 == 0, "word copy of the descriptor");
+__global__ void k_put_desc(const Desc d) {
+  const uint32_t* src = reinterpret_cast<const uint32_t*>(&d);
+  uint32_t* dst = reinterpret_cast<uint32_t*>(g_noalloc_scratch + kOffDesc);
+  for (int i = threadIdx.x; i < (int)(sizeof(Desc) / 4); i += blockDim.x) dst[i] = src[i];
+}
+
 namespace {
 
 int na_status(cudaError_t e, const char* what) {
-  if (e == cudaSuccess) return EM_OK;
-  snprintf(g_msg, sizeof(g_msg), "%s: %s", what, cudaGetErrorString(e));
-  return EM_ERR_CUDA;
+  return e == cudaSuccess ? EM_OK : map_record_error(what, e);
 }
 
 // Device address of the scratch on the current device, looked up once per
@@ -120,19 +136,20 @@ extern "C" int em_update_noalloc(const em_params* params, int64_t shift_x, int64
   if (total > kMaxPoints) return EM_ERR_CAPACITY;
 
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return EM_ERR_CUDA;
+  int rc = na_status(cudaGetDevice(&dev), "cudaGetDevice");
+  if (rc) return rc;
   unsigned char* base = nullptr;
-  int rc = scratch_address(dev, &base);
+  rc = scratch_address(dev, &base);
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   const int32_t W = params->width, H = params->height, ncell = W * H;
 
-  // descriptor, built on the host stack and copied into the scratch
-  unsigned char desc[sizeof(BatchDev) + sizeof(MapDev) + kMaxCloudsNA * sizeof(CloudDev)];
-  BatchDev* b = reinterpret_cast<BatchDev*>(desc);
-  MapDev* m = reinterpret_cast<MapDev*>(desc + sizeof(BatchDev));
-  CloudDev* cd = reinterpret_cast<CloudDev*>(desc + sizeof(BatchDev) + sizeof(MapDev));
-  memset(desc, 0, sizeof(desc));
+  // descriptor, built here and handed to k_put_desc by value
+  Desc desc;
+  memset(&desc, 0, sizeof(desc));
+  BatchDev* b = &desc.b;
+  MapDev* m = &desc.m;
+  CloudDev* cd = desc.c;
   m->h = h;
   m->var = var;
   m->t_last = t_last;
@@ -181,8 +198,8 @@ extern "C" int em_update_noalloc(const em_params* params, int64_t shift_x, int64
   b->n_maps = 1;
   b->n_clouds = n_clouds;
   b->n_points = total;
-  b->maps = reinterpret_cast<const MapDev*>(base + kOffDesc + sizeof(BatchDev));
-  b->clouds = reinterpret_cast<const CloudDev*>(base + kOffDesc + sizeof(BatchDev) + sizeof(MapDev));
+  b->maps = reinterpret_cast<const MapDev*>(base + kOffDesc + offsetof(Desc, m));
+  b->clouds = reinterpret_cast<const CloudDev*>(base + kOffDesc + offsetof(Desc, c));
   b->rec = reinterpret_cast<float4*>(base + kOffRec);
   b->n_cells = pad_tile(ncell);
   b->ctl = reinterpret_cast<BatchCtl*>(base + kOffBCtl);
@@ -191,10 +208,9 @@ extern "C" int em_update_noalloc(const em_params* params, int64_t shift_x, int64
   b->big_thresh = 256;
   b->chunk = 256;
 
-  const BatchDev* bd = reinterpret_cast<const BatchDev*>(base + kOffDesc);
-  const size_t desc_bytes = sizeof(BatchDev) + sizeof(MapDev) + (size_t)n_clouds * sizeof(CloudDev);
-  // pageable source: returns once the bytes are staged, so the stack buffer may go
-  rc = na_status(cudaMemcpyAsync(base + kOffDesc, desc, desc_bytes, cudaMemcpyHostToDevice, s), "descriptor");
+  const BatchDev* bd = reinterpret_cast<const BatchDev*>(base + kOffDesc + offsetof(Desc, b));
+  k_put_desc<<<1, 128, 0, s>>>(desc);
+  rc = na_status(cudaGetLastError(), "k_put_desc");
   if (rc) return rc;
   // counters, marks and per-cell counts start at zero
   rc = na_status(cudaMemsetAsync(base + kOffCtl, 0, kOffCnt - kOffCtl + (size_t)ncell * sizeof(int32_t), s),

@@ -167,12 +167,12 @@ def _pose(pose) -> ctypes.Array:
     return (ctypes.c_float * 12)(*[float(v) for v in p])
 
 
-def _cloud_struct(pts, pose, host: bool) -> _Cloud:
+def _cloud_struct(pts, pose, host: bool, any_device: bool = False) -> _Cloud:
     if host:
         n, stride = pts.shape
         ptr = pts.ctypes.data
     else:
-        if pts.dtype.__str__() != "torch.float32" or not pts.is_cuda or not pts.is_contiguous():
+        if pts.dtype.__str__() != "torch.float32" or not (pts.is_cuda or any_device) or not pts.is_contiguous():
             raise ValueError("points must be a contiguous float32 CUDA tensor of shape (n, 3) or (n, 4)")
         n, stride = pts.shape
         ptr = pts.data_ptr()
@@ -310,9 +310,38 @@ class Map:
 NOALLOC_MAX_CELLS, NOALLOC_MAX_POINTS, NOALLOC_MAX_CLOUDS = 65536, 327680, 8
 
 
+def _check_layers(layers, cells: int, device):
+    """Caller layers the kernels read or write whole, as (name, tensor, dtype):
+    each must be a contiguous tensor of its dtype with exactly `cells`
+    elements, on the CUDA device of the points (the library cannot check
+    sizes; a wrong one would be written out of bounds)."""
+    for name, t, dtype in layers:
+        if not hasattr(t, "is_cuda") or str(t.dtype) != dtype:
+            raise ValueError(f"{name} must be a {dtype} tensor, got {getattr(t, 'dtype', type(t))}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if t.numel() != cells:
+            raise ValueError(f"{name} must hold width * height = {cells} elements, got {t.numel()}")
+    for name, t, _ in layers:
+        if not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if device is not None and t.device != device:
+            raise ValueError(f"{name} is on {t.device}, the points on {device}")
+
+
 def update_noalloc(params: Params, h, var, t_last, clouds, t_now: int, shift=(0, 0), normals=None, stream=None):
     """em_update_noalloc: one update of caller-owned layers (CUDA tensors: h, var
-    float32 (H, W), t_last int32 (H, W)) that allocates no device memory."""
+    float32 (H, W), t_last int32 (H, W), optional normals (nx, ny, nz) float32
+    (H, W)) that allocates no device memory.  Every layer is checked (dtype,
+    size, contiguity, device) before the call: ValueError otherwise."""
+    cells = int(params.width) * int(params.height)
+    device = clouds[0][0].device if clouds and hasattr(clouds[0][0], "device") else None
+    layers = [("h", h, "torch.float32"), ("var", var, "torch.float32"), ("t_last", t_last, "torch.int32")]
+    if normals is not None:
+        if len(normals) != 3:
+            raise ValueError("normals must be (nx, ny, nz)")
+        layers += [(k, t, "torch.float32") for k, t in zip(("nx", "ny", "nz"), normals)]
+    _check_layers(layers, cells, device)
     cp = params._c()
     arr = (_Cloud * len(clouds))(*[_cloud_struct(p, q, False) for p, q in clouds])
     nx, ny, nz = (None, None, None) if normals is None else (n.data_ptr() for n in normals)
@@ -413,7 +442,8 @@ class _Result(ctypes.Structure):
 
 class _Request(ctypes.Structure):
     _fields_ = [("map_id", ctypes.c_int32), ("n_clouds", ctypes.c_int32), ("clouds", ctypes.POINTER(_Cloud)),
-                ("read_mask", ctypes.c_uint32), ("read_to_host", ctypes.c_int32), ("read_dst", ctypes.c_void_p)]
+                ("read_mask", ctypes.c_uint32), ("read_to_host", ctypes.c_int32), ("read_dst", ctypes.c_void_p),
+                ("clouds_on_host", ctypes.c_int32)]
 
 
 class _ServerStats(ctypes.Structure):
@@ -512,19 +542,27 @@ class Server:
         return tk.value
 
     def submit_many(self, requests, ready=None) -> list:
-        """requests: [(map_id, [(points CUDA tensor, pose), ...], read), ...] with read None or
-        (layer_mask, out): out a contiguous float32 tensor (CUDA, or pinned CPU memory) that
-        receives the map's layers right after this update.  One call queues them all (they
-        reach the same batch when they fit); ready as in submit.  Returns the tickets."""
+        """requests: [(map_id, [(points, pose), ...], read), ...]: points contiguous float32
+        (n, 3|4) tensors, all on the CUDA device or all in pinned CPU memory (then the server
+        copies them to the device itself); read None or (layer_mask, out): out a contiguous
+        float32 tensor (CUDA, or pinned CPU memory) that receives the map's layers right after
+        this update.  One call queues them all (they reach the same batch when they fit);
+        ready as in submit.  Returns the tickets."""
         n = len(requests)
         reqs = (_Request * n)()
         keep = []
         for q, (map_id, clouds, read) in enumerate(requests):
-            arr = (_Cloud * len(clouds))(*[_cloud_struct(p, pose, False) for p, pose in clouds])
+            on_host = not clouds[0][0].is_cuda
+            for p, _ in clouds:
+                if p.is_cuda == on_host or str(p.dtype) != "torch.float32" or not p.is_contiguous() or \
+                        p.dim() != 2 or p.shape[1] not in (3, 4) or (on_host and not p.is_pinned()):
+                    raise ValueError("points: contiguous float32 (n, 3|4) tensors, all CUDA or all pinned CPU")
+            arr = (_Cloud * len(clouds))(*[_cloud_struct(p, pose, False, any_device=True) for p, pose in clouds])
             keep.append((arr, clouds, read))
             reqs[q].map_id = int(map_id)
             reqs[q].n_clouds = len(clouds)
             reqs[q].clouds = arr
+            reqs[q].clouds_on_host = 1 if on_host else 0
             if read is not None:
                 mask, out = read
                 if out.dtype.__str__() != "torch.float32" or not out.is_contiguous():

@@ -94,3 +94,30 @@ def test_product_path_has_no_oracle_dependency():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in text.replace("the oracle", ""), f
+
+
+def test_noalloc_binding_checks_layers_before_the_call(lib_path):
+    """em.update_noalloc refuses layers the library could not check (wrong
+    dtype, element count, contiguity, not on a CUDA device) with ValueError
+    before anything reaches the library."""
+    torch = pytest.importorskip("torch")
+    from paper_2204_12876_gb300 import em
+    p = em.Params(width=10, height=8)
+    pose = [1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0]
+    pts = torch.zeros((5, 3))
+    ok_f = torch.zeros((8, 10))
+    ok_i = torch.zeros((8, 10), dtype=torch.int32)
+    bad = [
+        (ok_f.double(), ok_f, ok_i, "float32"),            # dtype
+        (ok_f, torch.zeros((8, 9)), ok_i, "80 elements"),   # element count
+        (ok_f, ok_f, ok_f, "int32"),                       # t_last dtype
+        (ok_f, torch.zeros((10, 8)).t(), ok_i, "contiguous"),
+    ]
+    for h, v, t, what in bad:
+        with pytest.raises(ValueError, match=what):
+            em.update_noalloc(p, h, v, t, [(pts, pose)], t_now=1)
+    with pytest.raises(ValueError, match="nx"):                  # a normal layer of the wrong size
+        em.update_noalloc(p, ok_f, ok_f, ok_i, [(pts, pose)], t_now=1,
+                          normals=(torch.zeros(3), ok_f, ok_f))
+    with pytest.raises(ValueError, match="CUDA"):                # host tensors
+        em.update_noalloc(p, ok_f, ok_f, ok_i, [(pts, pose)], t_now=1)

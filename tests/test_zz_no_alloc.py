@@ -1,9 +1,11 @@
 """em_update_noalloc -- the update for callers that cannot allocate device
-memory at update time (a real-time loop that forbids allocation after start-up,
-a framework whose allocator already holds the device memory, code preparing
-work during stream capture).  Its scratch is a fixed static device array of the
-library; these tests check, through the C ABI, that it produces what em_update
-produces on two calls in a row, and that it refuses sizes beyond its limits.
+memory at update time: a real-time loop that forbids allocation after
+start-up, or a framework whose allocator already holds the device memory.  Its
+scratch is a fixed static device array of the library, shared by every call.
+These tests check, through the C ABI, that it produces what em_update produces
+on consecutive calls -- two maps of different sizes alternating through the
+same scratch, several clouds, a shifted map centre and the Eq. 4 normal guard
+-- and that it refuses sizes beyond its limits.
 
 This file sorts last so that a run stopping at the first failure has run every
 other test before it.
@@ -28,6 +30,17 @@ def em():
     return mod
 
 
+def _compare(ref, h, var, t_last, t):
+    s = ref.state()
+    gh, gv, gt = h.cpu().numpy(), var.cpu().numpy(), t_last.cpu().numpy()
+    rv, nv = np.isfinite(s["var"]), np.isfinite(gv)
+    assert np.array_equal(rv, nv), t
+    assert np.all(np.abs(gh[rv].astype(np.float64) - s["h"][rv]) <= 1e-5), t
+    assert np.all(np.abs(gv[rv].astype(np.float64) / s["var"][rv] - 1.0) <= 1e-4), t
+    assert np.array_equal(gt[rv], s["t_last"][rv]), t
+    return int(rv.sum())
+
+
 def test_noalloc_matches_em_update_on_two_calls(em):
     ref = em.Map(em.Params(**P))
     H, W = P["height"], P["width"]
@@ -40,15 +53,51 @@ def test_noalloc_matches_em_update_on_two_calls(em):
         ref.update(d, pose)
         em.update_noalloc(em.Params(**P), h, var, t_last, [(d, pose)], t_now=t)
         torch.cuda.synchronize()
-        s = ref.state()
-        gh, gv, gt = h.cpu().numpy(), var.cpu().numpy(), t_last.cpu().numpy()
-        rv, nv = np.isfinite(s["var"]), np.isfinite(gv)
-        assert np.array_equal(rv, nv), t
-        assert rv.sum() > 5000
-        assert np.all(np.abs(gh[rv].astype(np.float64) - s["h"][rv]) <= 1e-5), t
-        assert np.all(np.abs(gv[rv].astype(np.float64) / s["var"][rv] - 1.0) <= 1e-4), t
-        assert np.array_equal(gt[rv], s["t_last"][rv]), t
+        assert _compare(ref, h, var, t_last, t) > 5000
     ref.close()
+
+
+def test_noalloc_alternating_maps_share_the_scratch(em):
+    """A 256 x 256 map (the largest the scratch holds) and a 100 x 100 map take
+    turns, each update with two clouds, a shifted map centre and the normal
+    guard reading the caller's normals; every result equals em_update's."""
+    rng = np.random.default_rng(44)
+    cases = []
+    for side, shift, seed in ((256, (9, -14), 45), (100, (-3, 5), 46)):
+        Pm = dict(P, width=side, height=side, cleanup_normal_thresh=0.2)
+        prior = synth.random_prior(seed=seed, width=side, height=side, t_now=4)
+        ref = em.Map(em.Params(**Pm))
+        ref.shift(*shift)
+        ref.set_state(h=prior["h"], var=prior["var"], t_last=prior["t_last"].astype(np.float32), nx=prior["nx"],
+                      ny=prior["ny"], nz=prior["nz"], t_now=prior["t_now"])
+        lay = {k: torch.from_numpy(np.ascontiguousarray(prior[k])).cuda() for k in ("h", "var", "nx", "ny", "nz")}
+        lay["t_last"] = torch.from_numpy(np.ascontiguousarray(prior["t_last"].astype(np.int32))).cuda()
+        lay["var"][~torch.isfinite(lay["var"])] = float("inf")
+        lay["h"][~torch.isfinite(lay["var"])] = float("nan")
+        cases.append((Pm, shift, ref, lay))
+    half = 0.038 * 256 / 2
+    cleared = 0
+    for t in range(5, 9):
+        for Pm, shift, ref, lay in cases:
+            r = Pm["resolution"]
+            c = np.array([shift[0] * r, shift[1] * r])
+            clouds = []
+            for k in range(2):
+                pts, pose = synth.single_update(seed=int(rng.integers(1 << 30)), n=15000,
+                                                half=half * Pm["width"] / 256)
+                pose = pose.copy()
+                pose[3] += c[0]
+                pose[7] += c[1]
+                clouds.append((torch.from_numpy(pts).cuda(), pose))
+            ref.update_multi(clouds)
+            em.update_noalloc(em.Params(**Pm), lay["h"], lay["var"], lay["t_last"], clouds, t_now=t, shift=shift,
+                              normals=(lay["nx"], lay["ny"], lay["nz"]))
+            torch.cuda.synchronize()
+            assert _compare(ref, lay["h"], lay["var"], lay["t_last"], (Pm["width"], t)) > 2000
+    for _, _, ref, _ in cases:
+        cleared += ref.stats()["cells_cleared"]
+        ref.close()
+    assert cleared > 0  # the ray march removed cells, so the guard's normals were read
 
 
 def test_noalloc_rejects_sizes_beyond_its_limits(em):
