@@ -43,6 +43,7 @@ struct Request {
   float* read_dst = nullptr;    // device-writable address (device or mapped host memory)
   float* read_host = nullptr;   // the caller's host address when read_dst is host memory
   int64_t read_floats = 0;
+  bool on_host = false;         // the clouds' points are page-locked host memory (copied in by the batch)
   ReqState state = kPending;
   em_result res{};
 };
@@ -72,6 +73,8 @@ struct em_server {
   std::vector<em_batch*> batches;
   std::vector<float*> stage;  // per batch stream: layer reads bound for host memory land here first
   int64_t stage_cap = 0;      // floats per stage buffer
+  std::vector<float*> in_stage;  // per stream: host clouds are copied here (allocated on first use)
+  int64_t in_cap = 0;            // floats per input buffer
   std::vector<Flight> flights;            // batched: one per stream; plain: grows as needed
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
@@ -123,6 +126,33 @@ void complete(em_server* s, Flight& f, int status) {
   f.busy = false;
 }
 
+// Host clouds of the requests in `take`: their device copies in the stream's
+// input buffer (16-byte aligned, one after the other); the copies themselves
+// are returned in `copies` to be issued on the stream after its waits.
+struct HostCopy {
+  float* dst;
+  const float* src;
+  size_t bytes;
+};
+
+em_cloud stage_cloud(em_server* s, size_t si, const em_cloud& c, int64_t& off, std::vector<HostCopy>& copies) {
+  em_cloud d = c;
+  float* dst = s->in_stage[si] + off;
+  const size_t floats = (size_t)(c.n * c.stride);
+  if (floats) copies.push_back({dst, c.points, floats * sizeof(float)});
+  d.points = dst;
+  off += (int64_t)((floats + 3) & ~size_t(3));
+  return d;
+}
+
+int issue_copies(const std::vector<HostCopy>& copies, cudaStream_t st) {
+  for (const HostCopy& c : copies) {
+    cudaError_t e = cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return map_record_error("host cloud copy", e);
+  }
+  return EM_OK;
+}
+
 // One worker pass: complete finished flights, admit, launch.  Returns true when
 // anything is in flight or waiting (the worker keeps polling).
 bool worker_pass(em_server* s, std::unique_lock<std::mutex>& lk) {
@@ -162,12 +192,18 @@ bool worker_pass(em_server* s, std::unique_lock<std::mutex>& lk) {
       f.maps.clear();
       em_map* m = s->maps[r.map_id];
       std::vector<em_cloud> cl = r.clouds;
+      std::vector<HostCopy> copies;
+      if (r.on_host) {
+        int64_t off = 0;
+        for (em_cloud& c : cl) c = stage_cloud(s, 0, c, off, copies);
+      }
       cudaEvent_t ready = r.ready;
       const uint32_t read_mask = r.read_mask;
       float* read_dst = r.read_dst;
       lk.unlock();
       if (ready) cudaStreamWaitEvent(s->streams[0], ready, 0);
-      int rc = em_update_multi(m, cl.data(), (int32_t)cl.size(), (em_stream_t)s->streams[0]);
+      int rc = issue_copies(copies, s->streams[0]);
+      if (rc == EM_OK) rc = em_update_multi(m, cl.data(), (int32_t)cl.size(), (em_stream_t)s->streams[0]);
       if (rc == EM_OK && read_mask) rc = map_read_layers(m, read_mask, read_dst, s->streams[0]);
       if (rc == EM_OK) cudaEventRecord(f.ev, s->streams[0]);
       lk.lock();
@@ -213,6 +249,8 @@ bool worker_pass(em_server* s, std::unique_lock<std::mutex>& lk) {
       struct Staged { float* host; int64_t off, floats; };
       std::vector<Staged> staged;
       int64_t stage_used = 0;
+      std::vector<HostCopy> copies;
+      int64_t in_used = 0;
       const int64_t t0 = now_ns();
       for (uint64_t tk : take) {
         Request& r = s->reqs[tk];
@@ -233,7 +271,7 @@ bool worker_pass(em_server* s, std::unique_lock<std::mutex>& lk) {
         r.res.batch_size = (int32_t)take.size();
         for (const em_cloud& c : r.clouds) {
           pm.push_back(s->maps[r.map_id]);
-          pc.push_back(c);
+          pc.push_back(r.on_host ? stage_cloud(s, si, c, in_used, copies) : c);
         }
         s->map_busy[r.map_id] = 1;
       }
@@ -246,7 +284,9 @@ bool worker_pass(em_server* s, std::unique_lock<std::mutex>& lk) {
       if ((int64_t)take.size() > s->st.max_batch_size) s->st.max_batch_size = (int64_t)take.size();
       lk.unlock();
       for (cudaEvent_t e : ready) cudaStreamWaitEvent(s->streams[si], e, 0);
-      int rc = em_update_batch(s->batches[si], pm.data(), pc.data(), (int32_t)pc.size(), (em_stream_t)s->streams[si]);
+      int rc = issue_copies(copies, s->streams[si]);
+      if (rc == EM_OK)
+        rc = em_update_batch(s->batches[si], pm.data(), pc.data(), (int32_t)pc.size(), (em_stream_t)s->streams[si]);
       if (rc == EM_OK && !rmaps.empty())
         rc = maps_read_layers(rmaps.data(), rmasks.data(), rdst.data(), (int)rmaps.size(), s->streams[si]);
       if (rc == EM_OK) cudaEventRecord(f.ev_maps, s->streams[si]);
@@ -403,6 +443,7 @@ int em_server_submit_many(em_server* s, const em_request* reqs, int32_t n, void*
   if (!s || !reqs || n < 1 || !tickets) return EM_ERR_INVALID_ARG;
   std::vector<int64_t> pts(n, 0);
   std::vector<float*> dst(n, nullptr);
+  bool any_host = false;
   for (int32_t q = 0; q < n; ++q) {
     const em_request& r = reqs[q];
     if (!r.clouds || r.n_clouds < 1 || r.n_clouds > 8) return EM_ERR_INVALID_ARG;
@@ -410,8 +451,17 @@ int em_server_submit_many(em_server* s, const em_request* reqs, int32_t n, void*
       const em_cloud& c = r.clouds[i];
       if (c.n < 0 || (c.stride != 3 && c.stride != 4) || (c.n > 0 && !c.points) || !word_aligned(c.points))
         return EM_ERR_INVALID_ARG;
+      if (r.clouds_on_host && c.n > 0) {  // page-locked host memory: the copy is asynchronous DMA
+        cudaPointerAttributes a{};
+        if (cudaPointerGetAttributes(&a, c.points) != cudaSuccess) {
+          cudaGetLastError();
+          return EM_ERR_INVALID_ARG;
+        }
+        if (a.type != cudaMemoryTypeHost) return EM_ERR_INVALID_ARG;
+      }
       pts[q] += c.n;
     }
+    any_host |= r.clouds_on_host != 0;
     if (r.read_mask) {
       if ((r.read_mask >> 11) || !r.read_dst || !word_aligned(r.read_dst)) return EM_ERR_INVALID_ARG;
       // the GPU writes the read-back itself: device memory, or page-locked host
@@ -437,6 +487,27 @@ int em_server_submit_many(em_server* s, const em_request* reqs, int32_t n, void*
   for (int32_t q = 0; q < n; ++q) {
     if (reqs[q].map_id < 0 || reqs[q].map_id >= (int32_t)s->maps.size()) return EM_ERR_INVALID_ARG;
   }
+  if (any_host && s->in_stage.empty()) {
+    // one input buffer per stream: a full batch of stride-4 points, each cloud padded to 16 bytes
+    const int64_t cap = s->cfg.max_batch_points * 4 + 4 * (int64_t)s->cfg.max_batch_maps * 8;
+    const int64_t bytes = cap * (int64_t)sizeof(float) * (int64_t)s->streams.size();
+    if (s->bytes_in_use + bytes > s->cfg.budget_bytes) return EM_ERR_REJECTED;
+    cudaSetDevice(s->cfg.device);
+    for (size_t i = 0; i < s->streams.size(); ++i) {
+      float* b = nullptr;
+      if (cudaMalloc((void**)&b, (size_t)cap * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        for (float* x : s->in_stage) cudaFree(x);
+        s->in_stage.clear();
+        return EM_ERR_OOM;
+      }
+      s->in_stage.push_back(b);
+    }
+    s->in_cap = cap;
+    s->fixed_bytes += bytes;
+    s->bytes_in_use += bytes;
+    if (s->bytes_in_use > s->st.peak_bytes) s->st.peak_bytes = s->bytes_in_use;
+  }
   for (int32_t q = 0; q < n; ++q) {
     if (pts[q] > s->cfg.max_batch_points || s->fixed_bytes + maps_bytes + pts[q] * kRecordBytes > s->cfg.budget_bytes) {
       s->st.submitted += 1;
@@ -458,6 +529,7 @@ int em_server_submit_many(em_server* s, const em_request* reqs, int32_t n, void*
     r.read_mask = in.read_mask;
     r.read_dst = dst[q];
     r.read_host = in.read_mask && in.read_to_host ? in.read_dst : nullptr;
+    r.on_host = in.clouds_on_host != 0;
     if (in.read_mask)
       r.read_floats = (int64_t)__builtin_popcount(in.read_mask) * map_cells(s->maps[in.map_id]);
     r.res.map_id = in.map_id;
@@ -607,6 +679,7 @@ int em_server_destroy(em_server* s) {
     if (f.ev_maps) cudaEventDestroy(f.ev_maps);
   }
   for (float* st : s->stage) cudaFree(st);
+  for (float* st : s->in_stage) cudaFree(st);
   for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
   for (em_map* m : s->maps) em_destroy(m);
   delete s;

@@ -233,3 +233,30 @@ def test_requests_survive_device_synchronize_during_capture(em):
     assert all(srv.wait(t)["status"] == 0 for t in tickets)
     torch.cuda.synchronize()
     srv.close()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_host_clouds_equal_device_clouds(em, mode):
+    """Requests whose clouds sit in page-locked host memory (the server copies
+    them to the device itself, on the batch's stream) leave every map exactly
+    as the same requests with device clouds do; pageable host clouds are
+    refused before anything is queued."""
+    reqs = workload(n_req=24, seed=9)
+    host = [(j, p.cpu().pin_memory(), q) for j, p, q in reqs]
+    states = []
+    for which in ("device", "host"):
+        srv = em.Server(budget_bytes=1 << 30, n_streams=2, max_batch_maps=4, max_batch_points=100_000, mode=mode)
+        ids = [srv.add_map(em.Params(width=s, height=s, **BASE)) for s in SIDES]
+        src = reqs if which == "device" else host
+        tickets = srv.submit_many([(ids[j], [(p, q)], None) for j, p, q in src])
+        assert all(s == 0 for s in srv.wait_many(tickets))
+        states.append([srv.map(ids[j]).state() for j in range(len(SIDES))])
+        if which == "host":
+            assert srv.stats()["bytes_in_use"] > 0
+            pageable = torch.zeros((100, 3))
+            with pytest.raises(ValueError):
+                srv.submit_many([(ids[0], [(pageable, reqs[0][2])], None)])
+        srv.close()
+    for j in range(len(SIDES)):
+        for k in ("h", "var", "t_last"):
+            assert np.array_equal(states[0][j][k], states[1][j][k], equal_nan=True), (j, k)
