@@ -226,11 +226,11 @@ int em_get_trace(em_map* map, int32_t* ix, int32_t* iy, uint8_t* status, int64_t
  * for the previous update's events (so timing adds a host wait per update).
  * Slots of em_profile_read, in this order: */
 enum {
-  EM_PROF_COUNT = 0,   /* k_count: transform + bin + per-cell counts */
+  EM_PROF_COUNT = 0,   /* k_count: transform + bin + per-tile counts; ray thresholds */
   EM_PROF_RAY,         /* k_ray: visibility ray march */
-  EM_PROF_ALLOC,       /* k_alloc: segment allocation */
-  EM_PROF_SCATTER,     /* k_scatter: records into segments */
-  EM_PROF_FUSE,        /* k_fuse: per-cell gate + fusion */
+  EM_PROF_ALLOC,       /* k_alloc: record ranges of the tiles */
+  EM_PROF_SCATTER,     /* k_scatter: records into their tile's range */
+  EM_PROF_FUSE,        /* k_fuse: per-cell gate + fusion, one tile per block */
   EM_PROF_CLEAR,       /* k_clear: removal of penetrated cells */
   EM_PROF_NORMALS,
   EM_PROF_SMOOTH,
@@ -260,8 +260,9 @@ enum { EM_BATCH_GRAPH = 1u << 0 };
  * changes a result: every shape gives the same maps bit for bit. */
 typedef struct em_tuning {
   int32_t ray_group;    /* lanes per ray in the ray march: 1, 2, 4, 8, 16 or 32 */
-  int32_t fuse_chunk;   /* records per warp chunk in the fusion: 64, 128, 256, 512 or 1024 */
-  int32_t big_thresh;   /* cells with more records are fused by a whole block: 32 .. 1023 */
+  int32_t fuse_chunk;   /* threads per fusion block (one tile of 1024 cells per block): 64 .. 1024, a
+                           power of two; 512 and more run 512-thread blocks, the rest 256-thread ones */
+  int32_t big_thresh;   /* tiles with more than 16 x big_thresh records are fused first: 32 .. 1023 */
 } em_tuning;
 
 /* Capacities: at most max_maps distinct maps, max_clouds clouds and
@@ -365,9 +366,10 @@ typedef struct em_request {
   uint32_t read_mask;        /* EM_LAYER_* bits to read back right after the update; 0 = none */
   int32_t read_to_host;      /* read_dst is page-locked host memory (else device memory) */
   float* read_dst;           /* popcount(read_mask) * width * height floats, em_get_layers layout */
-  int32_t clouds_on_host;    /* clouds[i].points are page-locked host memory: the server copies them by
-                                DMA (one cudaMemcpyAsync per cloud, on the batch's stream, after `ready`)
-                                into a device input buffer of that stream before the update */
+  int32_t clouds_on_host;    /* clouds[i].points are page-locked host memory: once the request is admitted
+                                the server copies them by DMA (one cudaMemcpyAsync per cloud, on a copy
+                                stream of its own, after `ready`) into its device input arena; the
+                                request's batch waits for that copy, so it overlaps running batches */
 } em_request;
 
 /* Queue n requests under one lock, so that those that fit reach the same batch;
@@ -377,9 +379,10 @@ typedef struct em_request {
  * state the update produced); its ticket finishes once they have landed.  A
  * host read_dst must be page-locked (cudaHostAlloc, cudaHostRegister): the GPU
  * writes it directly.  Host clouds (clouds_on_host) must be page-locked too; the
- * first such request makes the server allocate one input buffer of
- * max_batch_points x 16 bytes per stream, counted in its byte budget
- * (EM_ERR_REJECTED if it does not fit).  All or nothing: EM_ERR_INVALID_ARG for a malformed
+ * first such request makes the server allocate its input arena, (n_streams +
+ * 2) x max_batch_points x 16 bytes, counted in its byte budget
+ * (EM_ERR_REJECTED if it does not fit); a host request is admitted only when
+ * its clouds fit the arena's free room.  All or nothing: EM_ERR_INVALID_ARG for a malformed
  * request (pageable or unknown read_dst memory included) and EM_ERR_REJECTED
  * for one that can never fit leave nothing queued; else tickets[i] is request
  * i's ticket. */

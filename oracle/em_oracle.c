@@ -543,12 +543,16 @@ static int guard_pass(const orc_params* p, double rx, double ry, double rz, doub
  * position may round into, the endpoint's own cell (skipped) or one of its
  * alternatives, the last sample (k step ~ d), a ray whose existence is
  * marginal, a sample height within its band of the threshold, a guard value
- * within its band of alpha_n.  A cell is flagged only when the sample is below
- * its threshold (plus band) and the guard may pass, i.e. when some reading
- * marks it. */
+ * within its band of alpha_n.  Such a sample, when some reading has it mark a
+ * cell (below the threshold plus band, the guard passing within its band),
+ * sets maybe[c]; a sample that marks c in every reading sets sure[c].  A cell
+ * is flagged after all rays when maybe is set and sure is not: a mark that one
+ * sample makes for certain no other sample can undo.  An uncertain sample in
+ * an empty cell is collected in *uu: it is flagged later if it may be that
+ * cell's minimum. */
 static void walk_ray(orc_map* m, const pt_info* pi, const float* pose, const double* h0, const double* ve0,
                      const double* nx0, const double* ny0, const double* nz0, uint8_t* mark, orc_trace* tr,
-                     upper_unsure* uu, double x0, double y0) {
+                     upper_unsure* uu, uint8_t* sure, uint8_t* maybe, double x0, double y0) {
   const orc_params* p = &m->p;
   const int W = p->width;
   const double r = p->resolution, step = p->ray_step, d = pi->d;
@@ -608,7 +612,8 @@ static void walk_ray(orc_map* m, const pt_info* pi, const float* pose, const dou
           if (guard_on && !(dot > p->cleanup_normal_thresh - bg)) continue; /* the guard holds in every reading */
           const int thr_unsure = fabs(sz - thr) < bt;
           const int guard_unsure = guard_on && fabs(dot - p->cleanup_normal_thresh) < bg;
-          if (unsure || thr_unsure || guard_unsure) cflags[c] |= CF_MARK;
+          if (unsure || thr_unsure || guard_unsure) maybe[c] = 1; /* some reading marks c, another not */
+          else sure[c] = 1;                                       /* every reading marks c */
         } else if ((p->flags & ORC_UPPER) && unsure) {
           upper_unsure_add(uu, c, sz - (ab + 8.0 * u * (fabs(oz) + f * pi->sz)));
         }
@@ -869,15 +874,22 @@ int orc_update(orc_map* m, const orc_cloud* clouds, int32_t ncloud, orc_trace* t
 
   /* 4. ray casting against the snapshot (Section II-E) */
   uint8_t* mark = (uint8_t*)calloc((size_t)nc, 1);
+  uint8_t* sure = (uint8_t*)calloc((size_t)nc, 1);
+  uint8_t* maybe = (uint8_t*)calloc((size_t)nc, 1);
   upper_unsure uu = {NULL, NULL, 0, 0};
   if (p->ray_step > 0) {
     for (int64_t i = 0; i < npts; ++i) {
       const pt_info* pi = &pts[i];
       if (pi->status == ST_NONFINITE) continue;
       const float* pose = clouds[pi->cloud].pose;
-      walk_ray(m, pi, pose, h0, ve0, nx0, ny0, nz0, mark, tr, &uu, x0, y0);
+      walk_ray(m, pi, pose, h0, ve0, nx0, ny0, nz0, mark, tr, &uu, sure, maybe, x0, y0);
     }
   }
+  if (tr && tr->cflags)
+    for (int64_t c = 0; c < nc; ++c)
+      if (maybe[c] && !sure[c]) tr->cflags[c] |= CF_MARK;
+  free(sure);
+  free(maybe);
   /* an uncertain sample may change an empty cell's bound only if it may be
    * that cell's minimum (its height less its band below the final bound) */
   for (int64_t q = 0; q < uu.n; ++q)

@@ -70,8 +70,10 @@ struct em_map {
   // per-cell scratch
   uint32_t* mark = nullptr;
   float* thr = nullptr;
-  int32_t* cnt = nullptr;
-  int2* cell_seg = nullptr;
+  int32_t* tile_cnt = nullptr;   // per tile of 1024 cells: record counts, ranges, claims
+  int32_t* tile_base = nullptr;
+  int32_t* tile_cur = nullptr;
+  int32_t* heavy = nullptr;
   MapCtl* ctl = nullptr;
   BatchCtl* bctl = nullptr;
   // geometry
@@ -80,12 +82,13 @@ struct em_map {
   int32_t t_now = 0;
   // per-update workspace
   int64_t cap = 0;
-  float4* rec = nullptr;
+  float* rz = nullptr;
+  float* rv = nullptr;
+  uint16_t* rc = nullptr;
   int32_t* idx_sorted = nullptr;
   int32_t* tr_ix = nullptr;
   int32_t* tr_iy = nullptr;
   uint8_t* tr_status = nullptr;
-  int2* big_list = nullptr;
   int64_t last_n = 0;
   // descriptors
   unsigned char* desc_host = nullptr;
@@ -103,9 +106,9 @@ struct em_map {
   cudaStream_t last_stream = nullptr;
   int64_t layer_bytes = 0;
   int64_t work_bytes = 0;
-  int fuse_chunk = 256;
+  int fuse_threads = 256;
   int ray_group = 4;
-  int big_thresh = 256;
+  int heavy_thresh = 256 * 16;
   int64_t points_in = 0;
   // per-kernel profiling
   bool prof = false;
@@ -129,7 +132,7 @@ MapDev make_mapdev(const em_map* m) {
   memset(&d, 0, sizeof(d));
   d.h = m->h; d.var = m->var; d.t_last = m->t_last;
   d.nx = m->nx; d.ny = m->ny; d.nz = m->nz; d.smooth = m->smooth; d.inpaint = m->inpaint; d.upper = m->upper;
-  d.mark = m->mark; d.thr = m->thr; d.cnt = m->cnt; d.cell_seg = m->cell_seg;
+  d.mark = m->mark; d.thr = m->thr;
   d.ctl = m->ctl;
   d.cell_begin = 0;
   d.W = m->p.width; d.H = m->p.height; d.ox = m->ox; d.oy = m->oy;
@@ -176,11 +179,10 @@ bool params_ok(const em_params* p) {
 }
 
 void free_workspace(em_map* m) {
-  cudaFree(m->rec); cudaFree(m->idx_sorted);
+  cudaFree(m->rz); cudaFree(m->rv); cudaFree(m->rc); cudaFree(m->idx_sorted);
   cudaFree(m->tr_ix); cudaFree(m->tr_iy); cudaFree(m->tr_status);
-  cudaFree(m->big_list);
-  m->rec = nullptr; m->idx_sorted = nullptr; m->tr_ix = m->tr_iy = nullptr; m->tr_status = nullptr;
-  m->big_list = nullptr;
+  m->rz = m->rv = nullptr; m->rc = nullptr; m->idx_sorted = nullptr; m->tr_ix = m->tr_iy = nullptr;
+  m->tr_status = nullptr;
   m->cap = 0;
   m->work_bytes = 0;
 }
@@ -195,8 +197,9 @@ int grow_workspace(em_map* m, int64_t n) {
   free_workspace(m);
   const bool trace = (m->p.flags & EM_F_TRACE) != 0;
   int64_t tot = 0;
-  EM_TRY(dev_alloc(&m->rec, (size_t)want, &tot), "alloc workspace");
-  EM_TRY(dev_alloc(&m->big_list, (size_t)big_list_cap(want), &tot), "alloc workspace");
+  EM_TRY(dev_alloc(&m->rz, (size_t)want, &tot), "alloc workspace");
+  EM_TRY(dev_alloc(&m->rv, (size_t)want, &tot), "alloc workspace");
+  EM_TRY(dev_alloc(&m->rc, (size_t)want, &tot), "alloc workspace");
   if (trace) {
     EM_TRY(dev_alloc(&m->idx_sorted, (size_t)want, &tot), "alloc trace");
     EM_TRY(dev_alloc(&m->tr_ix, (size_t)want, &tot), "alloc trace");
@@ -214,7 +217,8 @@ void release(em_map* m) {
     if (m->prof_ev[i]) cudaEventDestroy(m->prof_ev[i]);
   cudaFree(m->h); cudaFree(m->var); cudaFree(m->t_last);
   cudaFree(m->nx); cudaFree(m->ny); cudaFree(m->nz); cudaFree(m->smooth); cudaFree(m->inpaint); cudaFree(m->upper);
-  cudaFree(m->mark); cudaFree(m->thr); cudaFree(m->cnt); cudaFree(m->cell_seg);
+  cudaFree(m->mark); cudaFree(m->thr);
+  cudaFree(m->tile_cnt); cudaFree(m->tile_base); cudaFree(m->tile_cur); cudaFree(m->heavy);
   cudaFree(m->ctl); cudaFree(m->bctl);
   free_workspace(m);
   cudaFree(m->desc_dev);
@@ -272,17 +276,21 @@ int upload_desc(em_map* m, const em_cloud* clouds, int32_t n_clouds, int64_t tot
   b->n_points = total;
   b->maps = reinterpret_cast<const MapDev*>(db + sizeof(BatchDev));
   b->clouds = reinterpret_cast<const CloudDev*>(db + sizeof(BatchDev) + sizeof(MapDev));
-  b->rec = m->rec;
+  b->rz = m->rz;
+  b->rv = m->rv;
+  b->rc = m->rc;
   b->idx_sorted = m->idx_sorted;
   b->tr_ix = m->tr_ix;
   b->tr_iy = m->tr_iy;
   b->tr_status = m->tr_status;
   b->n_cells = pad_tile((int64_t)m->p.width * m->p.height);
   b->ctl = m->bctl;
-  b->big_list = m->big_list;
-  b->big_cap = (int32_t)big_list_cap(m->cap);
-  b->big_thresh = m->big_thresh;
-  b->chunk = m->fuse_chunk;
+  b->tile_cnt = m->tile_cnt;
+  b->tile_base = m->tile_base;
+  b->tile_cur = m->tile_cur;
+  b->heavy = m->heavy;
+  b->heavy_thresh = m->heavy_thresh;
+  b->fuse_threads = m->fuse_threads;
   const size_t bytes = sizeof(BatchDev) + sizeof(MapDev) + (size_t)n_clouds * sizeof(CloudDev);
   EM_TRY(cudaMemcpyAsync(db, hb, bytes, cudaMemcpyHostToDevice, s), "upload descriptor");
   *out = reinterpret_cast<const BatchDev*>(db);
@@ -428,7 +436,10 @@ int em_create(const em_params* params, int device, em_map** out) {
   if (params->flags & (EM_F_SMOOTH | EM_F_MEDIAN | EM_F_GAUSS)) { EM_ALLOC(m->smooth, nc) }
   if (params->flags & EM_F_INPAINT) { EM_ALLOC(m->inpaint, nc) }
   if (params->flags & EM_F_UPPER) { EM_ALLOC(m->upper, nc) }
-  EM_ALLOC(m->mark, (nc + 31) / 32) EM_ALLOC(m->thr, nc) EM_ALLOC(m->cnt, nc) EM_ALLOC(m->cell_seg, nc)
+  const size_t ntile = (size_t)(pad_tile((int64_t)nc) / kTile);
+  EM_ALLOC(m->mark, (nc + 31) / 32) EM_ALLOC(m->thr, nc)
+  EM_ALLOC(m->tile_cnt, ntile + 1) EM_ALLOC(m->tile_base, ntile + 1) EM_ALLOC(m->tile_cur, ntile + 1)
+  EM_ALLOC(m->heavy, ntile)
   EM_ALLOC(m->ctl, 1) EM_ALLOC(m->bctl, 1)
   EM_ALLOC(m->desc_dev, kDescBytes * kSlots)
 #undef EM_ALLOC
@@ -436,6 +447,7 @@ int em_create(const em_params* params, int device, em_map** out) {
   for (int i = 0; i < kSlots && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&m->desc_ev[i], cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->stage_ev, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMemset(m->ctl, 0, sizeof(MapCtl));
+  if (e == cudaSuccess) e = cudaMemset(m->tile_cnt, 0, (ntile + 1) * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMemset(m->bctl, 0, sizeof(BatchCtl));
   if (e == cudaSuccess) e = cuda_status(launch_fill_map(make_mapdev(m), nullptr), "fill") ? cudaErrorUnknown : cudaSuccess;
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -446,17 +458,17 @@ int em_create(const em_params* params, int device, em_map** out) {
   }
   m->layer_bytes = tot;
   // tuning knobs (defaults chosen by measurement; the environment overrides them)
-  if (const char* g = getenv("EM_FUSE_CHUNK")) {
+  if (const char* g = getenv("EM_FUSE_THREADS")) {
     int v = atoi(g);
-    if (v >= 64 && v <= 1024 && (v & (v - 1)) == 0) m->fuse_chunk = v;
+    if (v == 256 || v == 512) m->fuse_threads = v;
   }
   if (const char* g = getenv("EM_RAY_GROUP")) {
     int v = atoi(g);
     if (v == 1 || v == 2 || v == 4 || v == 8 || v == 16 || v == 32) m->ray_group = v;
   }
-  if (const char* g = getenv("EM_BIG_THRESH")) {
+  if (const char* g = getenv("EM_HEAVY_THRESH")) {
     int v = atoi(g);
-    if (v >= kMinBig && v <= kMaxBigThresh) m->big_thresh = v;
+    if (v >= kMinHeavy && v <= kMaxHeavy) m->heavy_thresh = v * 16;
   }
   *out = m;
   return EM_OK;
@@ -502,7 +514,7 @@ static int update_impl(em_map* m, const em_cloud* clouds, int32_t n_clouds, cuda
     if (m->p.ray_step > 0.f) EM_TRY(timed(m, EM_PROF_RAY, s, [&] { return launch_ray(bd, total, m->ray_group, ext, s); }), "k_ray");
     EM_TRY(timed(m, EM_PROF_ALLOC, s, [&] { return launch_alloc(bd, ncell, s); }), "k_alloc");
     EM_TRY(timed(m, EM_PROF_SCATTER, s, [&] { return launch_scatter(bd, total, ext, s); }), "k_scatter");
-    EM_TRY(timed(m, EM_PROF_FUSE, s, [&] { return launch_fuse(bd, total, m->fuse_chunk, s); }), "k_fuse");
+    EM_TRY(timed(m, EM_PROF_FUSE, s, [&] { return launch_fuse(bd, ncell, m->fuse_threads, s); }), "k_fuse");
   }
   EM_TRY(timed(m, EM_PROF_CLEAR, s, [&] { return launch_clear(bd, ncell, s); }), "k_clear");
   if (m->p.overlap_dz > 0.f && n_clouds > 0)

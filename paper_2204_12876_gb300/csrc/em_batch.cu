@@ -33,7 +33,7 @@ constexpr int kSlots = 3;
 bool tuning_ok(const em_tuning& t) {
   const int r = t.ray_group, f = t.fuse_chunk;
   return (r == 1 || r == 2 || r == 4 || r == 8 || r == 16 || r == 32) && f >= 64 && f <= 1024 && (f & (f - 1)) == 0 &&
-         t.big_thresh >= kMinBig && t.big_thresh <= kMaxBigThresh;
+         t.big_thresh >= kMinHeavy && t.big_thresh <= kMaxHeavy;
 }
 
 // what a captured graph depends on besides the slot
@@ -57,9 +57,15 @@ struct em_batch {
   int32_t max_maps = 0, max_clouds = 0, max_cells = 0;
   int64_t max_points = 0;
   uint32_t flags = 0;
-  float4* rec = nullptr;
+  float* rz = nullptr;  // records (k_sort.cu layout), max_points of each
+  float* rv = nullptr;
+  uint16_t* rc = nullptr;
   BatchCtl* bctl = nullptr;
-  int2* big_list = nullptr;
+  int64_t max_tiles = 0;  // tiles of the padded cell space of a full batch
+  int32_t* tile_cnt = nullptr;
+  int32_t* tile_base = nullptr;
+  int32_t* tile_cur = nullptr;
+  int32_t* heavy = nullptr;
   size_t desc_bytes = 0;
   unsigned char* desc_host = nullptr;
   unsigned char* desc_dev = nullptr;
@@ -122,7 +128,7 @@ cudaError_t launch_sequence(const BatchDev* bd, int64_t grid_points, int64_t gri
     if (e == cudaSuccess) e = timed(prof, EM_PROF_ALLOC, s, [&] { return launch_alloc(bd, grid_cells, s); });
     if (e == cudaSuccess) e = timed(prof, EM_PROF_SCATTER, s, [&] { return launch_scatter(bd, grid_points, k.ext, s); });
     if (e == cudaSuccess)
-      e = timed(prof, EM_PROF_FUSE, s, [&] { return launch_fuse(bd, grid_points, k.t.fuse_chunk, s); });
+      e = timed(prof, EM_PROF_FUSE, s, [&] { return launch_fuse(bd, grid_cells, k.t.fuse_chunk, s); });
   }
   if (e == cudaSuccess) e = timed(prof, EM_PROF_CLEAR, s, [&] { return launch_clear(bd, grid_cells, s); });
   if (e == cudaSuccess && k.overlap)
@@ -230,13 +236,17 @@ int prepare(em_batch* b, em_map* const* maps, const em_cloud* clouds, int32_t co
   bd->n_points = total;
   bd->maps = reinterpret_cast<const MapDev*>(db + sizeof(BatchDev));
   bd->clouds = reinterpret_cast<const CloudDev*>(db + sizeof(BatchDev) + (size_t)b->max_maps * sizeof(MapDev));
-  bd->rec = b->rec;
+  bd->rz = b->rz;
+  bd->rv = b->rv;
+  bd->rc = b->rc;
   bd->n_cells = cells;
   bd->ctl = b->bctl;
-  bd->big_list = b->big_list;
-  bd->big_cap = (int32_t)big_list_cap(b->max_points);
-  bd->big_thresh = tune.big_thresh;
-  bd->chunk = tune.fuse_chunk;
+  bd->tile_cnt = b->tile_cnt;
+  bd->tile_base = b->tile_base;
+  bd->tile_cur = b->tile_cur;
+  bd->heavy = b->heavy;
+  bd->heavy_thresh = tune.big_thresh * 16;
+  bd->fuse_threads = tune.fuse_chunk;
   // upload header + maps, and the clouds at their fixed offset
   cudaError_t e = cudaMemcpyAsync(db, hb, sizeof(BatchDev) + (size_t)nm * sizeof(MapDev), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
@@ -305,9 +315,14 @@ void release(em_batch* b) {
     if (b->ev[i]) cudaEventDestroy(b->ev[i]);
   }
   if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
-  cudaFree(b->rec);
+  cudaFree(b->rz);
+  cudaFree(b->rv);
+  cudaFree(b->rc);
   cudaFree(b->bctl);
-  cudaFree(b->big_list);
+  cudaFree(b->tile_cnt);
+  cudaFree(b->tile_base);
+  cudaFree(b->tile_cur);
+  cudaFree(b->heavy);
   cudaFree(b->desc_dev);
   cudaFreeHost(b->desc_host);
   delete b;
@@ -338,10 +353,19 @@ int em_batch_create(int device, int32_t max_maps, int32_t max_clouds, int64_t ma
   b->flags = flags;
   b->desc_bytes = (sizeof(BatchDev) + (size_t)max_maps * sizeof(MapDev) + (size_t)max_clouds * sizeof(CloudDev) + 255) &
                   ~size_t(255);
-  cudaError_t e = cudaMalloc((void**)&b->rec, (size_t)(max_points > 0 ? max_points : 1) * sizeof(float4));
+  const size_t np = (size_t)(max_points > 0 ? max_points : 1);
+  b->max_tiles = (int64_t)max_maps * (pad_tile(max_cells) / kTile);
+  const size_t nt = (size_t)b->max_tiles + 1;
+  cudaError_t e = cudaMalloc((void**)&b->rz, np * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->rv, np * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->rc, np * sizeof(uint16_t));
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->bctl, sizeof(BatchCtl));
   if (e == cudaSuccess) e = cudaMemset(b->bctl, 0, sizeof(BatchCtl));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&b->big_list, (size_t)big_list_cap(max_points) * sizeof(int2));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->tile_cnt, nt * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMemset(b->tile_cnt, 0, nt * sizeof(int32_t));  // k_alloc keeps it zero after
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->tile_base, nt * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->tile_cur, nt * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->heavy, nt * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->desc_dev, b->desc_bytes * kSlots);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&b->desc_host, b->desc_bytes * kSlots);
   for (int i = 0; i < kSlots && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&b->ev[i], cudaEventDisableTiming);
@@ -484,14 +508,14 @@ int em_batch_autotune(em_batch* b, em_map* const* maps, const em_cloud* clouds, 
   float best_ms = 0.f;
   rc = time_one(best, &best_ms);
   const int ray_c[] = {1, 2, 4, 8, 16};
-  const int chunk_c[] = {64, 128, 256, 512, 1024};
+  const int chunk_c[] = {256, 512, 256, 512, 256};  // fusion block sizes (repeats are skipped)
   const int big_c[] = {64, 128, 256, 512, 1023};
   const bool any_ray = [&] {
     for (em_map* m : uniq)
       if (map_params(m).ray_step > 0.f) return true;
     return false;
   }();
-  // coordinate descent: ray group, then fusion chunk, then the large-cell threshold
+  // coordinate descent: ray group, then fusion block size, then the heavy-tile threshold
   for (int pass = 0; pass < 3 && rc == EM_OK; ++pass) {
     if (pass == 0 && !any_ray) continue;
     const int* cand = pass == 0 ? ray_c : pass == 1 ? chunk_c : big_c;

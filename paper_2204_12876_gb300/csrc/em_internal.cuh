@@ -14,15 +14,15 @@
 //
 // Pipeline of one update (Section II-A of the paper: transform, height update
 // and ray casting in the same iteration, then per-cell passes):
-//   k_count    transform + noise variance + cell binning, per-cell counts;
-//              per-cell ray thresholds of the pre-update map   (Section II-C)
+//   k_count    transform + noise variance + cell binning, per-tile record
+//              counts; per cell: ray thresholds of the pre-update map
+//                                                              (Section II-C)
 //   k_ray      visibility ray march against the pre-update map (Section II-E)
-//   k_alloc    one segment of the record array per touched cell (segments of a
-//              tile in cell order); large cells listed for block fusion
-//   k_scatter  records into their cell's segment (counting sort by cell)
-//   k_fuse     per cell: wall rule, Mahalanobis gate, Eq. 1/2 in information
-//              form with exact integer accumulation; warps stream cell-aligned
-//              chunks of records (segmented reductions)   (Section II-C)
+//   k_alloc    one range of the record arrays per tile of 1024 cells
+//   k_scatter  records into their tile's range (counting sort by tile)
+//   k_fuse     per tile, one block: the tile's state in shared memory; per
+//              cell: wall rule, Mahalanobis gate, Eq. 1/2 in information form
+//              with exact integer accumulation (Section II-C)
 //   k_clear    remove penetrated cells not written recently   (Section II-E)
 //   k_normals / k_smooth / k_inpaint                          (Section II-A, II-I)
 #pragma once
@@ -33,6 +33,7 @@
 namespace em {
 
 constexpr int kTile = 1024;  // cells per tile of the cell space
+
 
 // per-map counters (device), in em_stats order
 enum StatIdx {
@@ -54,23 +55,20 @@ struct MapCtl {
   unsigned long long drift_n[2];  // points in the sum
 };
 
-// per-batch device control block (reset by k_count)
+// per-batch device control block (reset by k_count and k_alloc)
 struct BatchCtl {
-  int32_t rec_total;         // records given to segments this update (all maps)
-  int32_t n_big;             // entries in the large-cell list
-  int32_t big_next;          // work-stealing cursor over the large cells
-  int32_t overflow;          // the list was full (never with the sizes the host allocates)
+  int32_t rec_total;         // records of this update (all maps)
+  int32_t n_heavy;           // entries in the heavy-tile list
+  int32_t fuse_next;         // work counter of the fusion: heavy tiles first, then every tile
+  int32_t pad;
 };
 
-// One record per in-map point, grouped by cell (16 bytes, one store):
-//   x = z (map frame), y = sigma_p^2, z = physical cell index (int bits),
-//   w = map index (bits 0..23) | kRecWall | kRecBig (uint bits).
-// The flags are properties of the cell this update (its record count), so all
-// records of a cell carry the same (w, z) words.
-constexpr uint32_t kRecBig = 1u << 31;   // more than big_thresh records: fused by a whole block
-constexpr uint32_t kRecWall = 1u << 30;  // more than wall_num_thresh records (wall rule armed)
-constexpr uint32_t kRecMapMask = (1u << 24) - 1u;
-constexpr int kMaxBigThresh = 1023;      // run counts are packed in 10-bit fields
+// Records: one per in-map point, grouped by tile of kTile cells of the batch
+// cell space (a tile lies in one map: map cell ranges are padded to whole
+// tiles).  Structure of arrays: z (map frame), sigma_p^2, and the cell's index
+// within its tile.  Tile t's records fill [tile_base[t], tile_base[t + 1]).
+constexpr int kMinHeavy = 32;        // tuning bounds of the heavy-tile threshold (x 16 records)
+constexpr int kMaxHeavy = 1023;
 
 // device-side error word value for a failed internal consistency check (EM_ERR_CUDA)
 constexpr int32_t kErrInternal = -3;
@@ -91,8 +89,6 @@ struct MapDev {
   float* upper;     // upper bound of the ground height (Section II-H), +inf where none; may be null
   uint32_t* mark;   // visibility marks, one bit per physical cell, zero between updates
   float* thr;       // per LOGICAL cell [iy][ix]: h - sqrt(var_eff) of the pre-update map, -inf if empty
-  int32_t* cnt;     // per physical cell point count, zero between updates
-  int2* cell_seg;   // per physical cell: (first record, record count) of this update
   MapCtl* ctl;
   int64_t cell_begin;  // this map's first cell in the batch cell space (multiple of kTile)
   int32_t W, H, ox, oy;
@@ -126,21 +122,26 @@ struct BatchDev {
   int64_t n_cells;     // padded size of the cell space
   const MapDev* maps;
   const CloudDev* clouds;
-  float4* rec;         // records grouped by cell (layout above), [0, ctl->rec_total)
+  // records grouped by tile (layout above); capacity: the points of the batch
+  float* rz;
+  float* rv;
+  uint16_t* rc;
   int32_t* idx_sorted; // original point index per record (trace only, else null)
   int32_t* tr_ix;      // trace (null unless EM_F_TRACE)
   int32_t* tr_iy;
   uint8_t* tr_status;
   BatchCtl* ctl;
-  int2* big_list;      // (map, physical cell) of cells with more than big_thresh records
-  int32_t big_cap;
-  int32_t big_thresh;  // in [kMinBig, kMaxBigThresh]
-  int32_t chunk;       // records per warp chunk in the fusion (a power of two, 64..1024)
+  // per tile of the cell space (n_cells / kTile tiles): the records counted by
+  // k_count (zero between updates), their first record (k_alloc; one more
+  // entry holds the total), and k_scatter's claims (zeroed by k_alloc)
+  int32_t* tile_cnt;
+  int32_t* tile_base;
+  int32_t* tile_cur;
+  int32_t* heavy;      // tiles with more than heavy_thresh records (fused first)
+  int32_t heavy_thresh;
+  int32_t fuse_threads;  // threads per fusion block: 256 or 512
 };
 
-// Large-cell list capacity for n points (big_thresh >= kMinBig).
-constexpr int kMinBig = 32;
-inline int64_t big_list_cap(int64_t n) { return n / (kMinBig + 1) + 1; }
 inline int64_t pad_tile(int64_t cells) { return (cells + kTile - 1) / kTile * kTile; }
 // The kernels read points and layers as 4-byte words: a buffer that does not
 // start on a 4-byte boundary is refused on the host (it would fault on the device).
@@ -156,7 +157,7 @@ cudaError_t launch_drift(const BatchDev* b, int64_t n_points, int64_t n_cells, b
 cudaError_t launch_ray(const BatchDev* b, int64_t n_points, int group, bool ext, cudaStream_t s);
 cudaError_t launch_alloc(const BatchDev* b, int64_t n_cells, cudaStream_t s);
 cudaError_t launch_scatter(const BatchDev* b, int64_t n_points, bool ext, cudaStream_t s);
-cudaError_t launch_fuse(const BatchDev* b, int64_t n_points, int chunk, cudaStream_t s);
+cudaError_t launch_fuse(const BatchDev* b, int64_t n_cells, int threads, cudaStream_t s);
 cudaError_t launch_clear(const BatchDev* b, int64_t n_cells, cudaStream_t s);
 cudaError_t launch_overlap(const BatchDev* b, int64_t n_cells, cudaStream_t s);
 cudaError_t launch_normals(const BatchDev* b, int64_t n_cells, cudaStream_t s);

@@ -45,17 +45,21 @@ struct Desc {
 };
 static_assert(sizeof(Desc) <= 4096, "the descriptor travels as a kernel parameter");
 
-// scratch layout; the part that must start at zero (ctl, marks, counts) is contiguous
+// scratch layout; the part that must start at zero (ctl, marks, tile counts) is contiguous
+constexpr size_t kMaxTiles = ((size_t)kMaxCells + kTile - 1) / kTile;
 constexpr size_t kOffDesc = 0;
 constexpr size_t kOffCtl = kOffDesc + up256(sizeof(Desc));
 constexpr size_t kOffBCtl = kOffCtl + up256(sizeof(MapCtl));
 constexpr size_t kOffMark = kOffBCtl + up256(sizeof(BatchCtl));
-constexpr size_t kOffCnt = kOffMark + up256(((size_t)kMaxCells + 31) / 32 * sizeof(uint32_t));
-constexpr size_t kOffThr = kOffCnt + up256((size_t)kMaxCells * sizeof(int32_t));
-constexpr size_t kOffSeg = kOffThr + up256((size_t)kMaxCells * sizeof(float));
-constexpr size_t kOffBig = kOffSeg + up256((size_t)kMaxCells * sizeof(int2));
-constexpr size_t kOffRec = kOffBig + up256((size_t)(kMaxPoints / (kMinBig + 1) + 1) * sizeof(int2));
-constexpr size_t kScratchBytes = kOffRec + up256((size_t)kMaxPoints * sizeof(float4));
+constexpr size_t kOffTCnt = kOffMark + up256(((size_t)kMaxCells + 31) / 32 * sizeof(uint32_t));
+constexpr size_t kOffTBase = kOffTCnt + up256((kMaxTiles + 1) * sizeof(int32_t));
+constexpr size_t kOffTCur = kOffTBase + up256((kMaxTiles + 1) * sizeof(int32_t));
+constexpr size_t kOffHeavy = kOffTCur + up256((kMaxTiles + 1) * sizeof(int32_t));
+constexpr size_t kOffThr = kOffHeavy + up256(kMaxTiles * sizeof(int32_t));
+constexpr size_t kOffRz = kOffThr + up256((size_t)kMaxCells * sizeof(float));
+constexpr size_t kOffRv = kOffRz + up256((size_t)kMaxPoints * sizeof(float));
+constexpr size_t kOffRc = kOffRv + up256((size_t)kMaxPoints * sizeof(float));
+constexpr size_t kScratchBytes = kOffRc + up256((size_t)kMaxPoints * sizeof(uint16_t));
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
@@ -158,8 +162,6 @@ extern "C" int em_update_noalloc(const em_params* params, int64_t shift_x, int64
   m->nz = const_cast<float*>(nz);
   m->mark = reinterpret_cast<uint32_t*>(base + kOffMark);
   m->thr = reinterpret_cast<float*>(base + kOffThr);
-  m->cnt = reinterpret_cast<int32_t*>(base + kOffCnt);
-  m->cell_seg = reinterpret_cast<int2*>(base + kOffSeg);
   m->ctl = reinterpret_cast<MapCtl*>(base + kOffCtl);
   m->cell_begin = 0;
   m->z_ref = clouds[0].pose[11];
@@ -200,21 +202,24 @@ extern "C" int em_update_noalloc(const em_params* params, int64_t shift_x, int64
   b->n_points = total;
   b->maps = reinterpret_cast<const MapDev*>(base + kOffDesc + offsetof(Desc, m));
   b->clouds = reinterpret_cast<const CloudDev*>(base + kOffDesc + offsetof(Desc, c));
-  b->rec = reinterpret_cast<float4*>(base + kOffRec);
+  b->rz = reinterpret_cast<float*>(base + kOffRz);
+  b->rv = reinterpret_cast<float*>(base + kOffRv);
+  b->rc = reinterpret_cast<uint16_t*>(base + kOffRc);
+  b->tile_cnt = reinterpret_cast<int32_t*>(base + kOffTCnt);
+  b->tile_base = reinterpret_cast<int32_t*>(base + kOffTBase);
+  b->tile_cur = reinterpret_cast<int32_t*>(base + kOffTCur);
+  b->heavy = reinterpret_cast<int32_t*>(base + kOffHeavy);
   b->n_cells = pad_tile(ncell);
   b->ctl = reinterpret_cast<BatchCtl*>(base + kOffBCtl);
-  b->big_list = reinterpret_cast<int2*>(base + kOffBig);
-  b->big_cap = (int32_t)(kMaxPoints / (kMinBig + 1) + 1);
-  b->big_thresh = 256;
-  b->chunk = 256;
+  b->heavy_thresh = 4096;
+  b->fuse_threads = 256;
 
   const BatchDev* bd = reinterpret_cast<const BatchDev*>(base + kOffDesc + offsetof(Desc, b));
   k_put_desc<<<1, 128, 0, s>>>(desc);
   rc = na_status(cudaGetLastError(), "k_put_desc");
   if (rc) return rc;
-  // counters, marks and per-cell counts start at zero
-  rc = na_status(cudaMemsetAsync(base + kOffCtl, 0, kOffCnt - kOffCtl + (size_t)ncell * sizeof(int32_t), s),
-                 "cudaMemsetAsync");
+  // counters, marks and per-tile counts start at zero
+  rc = na_status(cudaMemsetAsync(base + kOffCtl, 0, kOffTBase - kOffCtl, s), "cudaMemsetAsync");
   if (rc) return rc;
   const int64_t cells = pad_tile(ncell);
   const bool ext = params->excl_d > 0.f;  // no upper-bound layer here
@@ -224,7 +229,7 @@ extern "C" int em_update_noalloc(const em_params* params, int64_t shift_x, int64
     if (e == cudaSuccess && params->ray_step > 0.f) e = launch_ray(bd, total, 4, ext, s);
     if (e == cudaSuccess) e = launch_alloc(bd, cells, s);
     if (e == cudaSuccess) e = launch_scatter(bd, total, ext, s);
-    if (e == cudaSuccess) e = launch_fuse(bd, total, 256, s);
+    if (e == cudaSuccess) e = launch_fuse(bd, cells, 256, s);
   }
   if (e == cudaSuccess) e = launch_clear(bd, cells, s);
   if (e == cudaSuccess && params->overlap_dz > 0.f) e = launch_overlap(bd, cells, s);

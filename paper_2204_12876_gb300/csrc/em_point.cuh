@@ -172,4 +172,44 @@ __device__ __forceinline__ void load_point(const CloudDev& c, int64_t i, float& 
   pz = __ldg(p + 2);
 }
 
+// Load the warp's 32 points [wbase, wbase + 32).  When the whole chunk sits in
+// one cloud with 16-byte aligned rows the warp reads it with float4 loads:
+// stride 4 -> one float4 per lane; stride 3 -> 24 float4 staged in shared memory.
+__device__ __forceinline__ int load_warp_points(const BatchDev& b, int64_t wbase, int64_t end, float4* stage,
+                                                float& px, float& py, float& pz) {
+  const int lane = threadIdx.x & 31;
+  const int64_t g = wbase + lane;
+  const int c0 = find_cloud(b.clouds, b.n_clouds, wbase);
+  const CloudDev& cl0 = b.clouds[c0];
+  const bool whole = (wbase + 32 <= end) && (wbase + 32 <= cl0.begin + cl0.n);
+  int ci = c0;
+  if (whole) {
+    const int64_t i0 = wbase - cl0.begin;
+    const float* base = cl0.pts + i0 * cl0.stride;
+    if (cl0.stride == 4 && ((reinterpret_cast<uintptr_t>(base) & 15) == 0)) {
+      float4 q = __ldg(reinterpret_cast<const float4*>(base) + lane);
+      px = q.x; py = q.y; pz = q.z;
+      return ci;
+    }
+    if (cl0.stride == 3 && ((reinterpret_cast<uintptr_t>(base) & 15) == 0)) {
+      if (lane < 24) stage[lane] = __ldg(reinterpret_cast<const float4*>(base) + lane);
+      __syncwarp();
+      const float* sf = reinterpret_cast<const float*>(stage);
+      px = sf[lane * 3];
+      py = sf[lane * 3 + 1];
+      pz = sf[lane * 3 + 2];
+      __syncwarp();
+      return ci;
+    }
+  } else if (g < end) {
+    ci = find_cloud(b.clouds, b.n_clouds, g);
+  }
+  if (g < end) {
+    load_point(b.clouds[ci], g - b.clouds[ci].begin, px, py, pz);
+  } else {
+    px = py = pz = __int_as_float(0x7fc00000);
+  }
+  return ci;
+}
+
 }  // namespace em

@@ -43,7 +43,11 @@ struct Request {
   float* read_dst = nullptr;    // device-writable address (device or mapped host memory)
   float* read_host = nullptr;   // the caller's host address when read_dst is host memory
   int64_t read_floats = 0;
-  bool on_host = false;         // the clouds' points are page-locked host memory (copied in by the batch)
+  bool on_host = false;         // the clouds' points are page-locked host memory, copied to the arena
+  int64_t in_off = -1;          // first float of its copy in the input arena (set at admission)
+  int64_t in_len = 0;           // floats it holds there
+  bool in_copy = false;         // admitted, copy not issued yet
+  cudaEvent_t in_ev = nullptr;  // recorded on the copy stream after its copies
   ReqState state = kPending;
   em_result res{};
 };
@@ -73,8 +77,15 @@ struct em_server {
   std::vector<em_batch*> batches;
   std::vector<float*> stage;  // per batch stream: layer reads bound for host memory land here first
   int64_t stage_cap = 0;      // floats per stage buffer
-  std::vector<float*> in_stage;  // per stream: host clouds are copied here (allocated on first use)
-  int64_t in_cap = 0;            // floats per input buffer
+  // host clouds: copied at admission, on a stream of their own, into a ring
+  // arena of device memory (allocated on the first host request), so the copy
+  // of a waiting request overlaps the batches already running
+  float* in_arena = nullptr;
+  int64_t in_cap = 0;                       // floats
+  struct InAlloc { uint64_t ticket; int64_t off, end; bool done; };
+  std::deque<InAlloc> in_allocs;            // allocation order
+  cudaStream_t copy_stream = nullptr;
+  std::vector<cudaEvent_t> ev_pool;
   std::vector<Flight> flights;            // batched: one per stream; plain: grows as needed
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
@@ -91,13 +102,67 @@ struct em_server {
 
 namespace {
 
+// Floats a request's host clouds take in the arena (each cloud 16-byte aligned).
+int64_t host_floats(const Request& r) {
+  int64_t f = 0;
+  for (const em_cloud& c : r.clouds) f += (c.n * c.stride + 3) & ~int64_t(3);
+  return f;
+}
+
+// Ring allocation of `len` floats in the input arena (allocations are freed
+// roughly in order; the oldest live one bounds the ring); -1 when full.
+int64_t arena_alloc(em_server* s, uint64_t ticket, int64_t len) {
+  int64_t off = -1;
+  if (s->in_allocs.empty()) {
+    off = len <= s->in_cap ? 0 : -1;
+  } else {
+    const int64_t tail = s->in_allocs.front().off, head = s->in_allocs.back().end;
+    if (head >= tail) {  // used region [tail, head)
+      if (head + len <= s->in_cap) off = head;
+      else if (len <= tail) off = 0;
+    } else if (head + len <= tail) {  // wrapped: used [tail, cap) and [0, head)
+      off = head;
+    }
+  }
+  if (off >= 0) s->in_allocs.push_back({ticket, off, off + len, false});
+  return off;
+}
+
+void arena_free(em_server* s, uint64_t ticket) {
+  for (auto& a : s->in_allocs)
+    if (a.ticket == ticket) a.done = true;
+  while (!s->in_allocs.empty() && s->in_allocs.front().done) s->in_allocs.pop_front();
+}
+
+// Release what an admitted or finished request holds besides its slot and bytes.
+void release_host(em_server* s, uint64_t ticket, Request& r) {
+  if (r.in_off >= 0) arena_free(s, ticket);
+  r.in_off = -1;
+  if (r.in_ev) s->ev_pool.push_back(r.in_ev);
+  r.in_ev = nullptr;
+}
+
 // Move pending requests into the admitted set while slots and memory allow
-// (strict arrival order).  Caller holds the lock.
+// (strict arrival order); a request with host clouds also needs room in the
+// input arena and an event for its copy.  Caller holds the lock.
 void admit(em_server* s) {
   while (!s->pending.empty()) {
     Request& r = s->reqs[s->pending.front()];
     if (s->slots_in_use >= s->cfg.max_slots) break;
     if (s->bytes_in_use + r.bytes > s->cfg.budget_bytes) break;
+    if (r.on_host) {
+      if (s->ev_pool.empty()) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) break;
+        s->ev_pool.push_back(e);
+      }
+      r.in_len = host_floats(r);
+      r.in_off = arena_alloc(s, s->pending.front(), r.in_len);
+      if (r.in_off < 0) break;
+      r.in_ev = s->ev_pool.back();
+      s->ev_pool.pop_back();
+      r.in_copy = true;
+    }
     s->bytes_in_use += r.bytes;
     if (s->bytes_in_use > s->st.peak_bytes) s->st.peak_bytes = s->bytes_in_use;
     s->slots_in_use += 1;
@@ -111,6 +176,7 @@ void complete(em_server* s, Flight& f, int status) {
   const int64_t t = now_ns();
   for (uint64_t tk : f.tickets) {
     Request& r = s->reqs[tk];
+    release_host(s, tk, r);
     r.state = kDone;
     r.res.status = status;
     r.res.t_done_ns = t;
@@ -126,31 +192,48 @@ void complete(em_server* s, Flight& f, int status) {
   f.busy = false;
 }
 
-// Host clouds of the requests in `take`: their device copies in the stream's
-// input buffer (16-byte aligned, one after the other); the copies themselves
-// are returned in `copies` to be issued on the stream after its waits.
-struct HostCopy {
-  float* dst;
-  const float* src;
-  size_t bytes;
-};
-
-em_cloud stage_cloud(em_server* s, size_t si, const em_cloud& c, int64_t& off, std::vector<HostCopy>& copies) {
-  em_cloud d = c;
-  float* dst = s->in_stage[si] + off;
-  const size_t floats = (size_t)(c.n * c.stride);
-  if (floats) copies.push_back({dst, c.points, floats * sizeof(float)});
-  d.points = dst;
-  off += (int64_t)((floats + 3) & ~size_t(3));
-  return d;
+// The device clouds of an admitted host request: its clouds' copies in the arena.
+void arena_clouds(em_server* s, const Request& r, std::vector<em_cloud>& out) {
+  int64_t off = r.in_off;
+  for (const em_cloud& c : r.clouds) {
+    em_cloud d = c;
+    d.points = s->in_arena + off;
+    off += (c.n * c.stride + 3) & ~int64_t(3);
+    out.push_back(d);
+  }
 }
 
-int issue_copies(const std::vector<HostCopy>& copies, cudaStream_t st) {
-  for (const HostCopy& c : copies) {
-    cudaError_t e = cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return map_record_error("host cloud copy", e);
+// Issue the arena copies of newly admitted host requests on the copy stream
+// (each after the request's ready event) and record their events.  Called
+// with the lock held; drops it while the copies are issued.
+void issue_host_copies(em_server* s, std::unique_lock<std::mutex>& lk) {
+  struct Job { const float* src; float* dst; size_t bytes; };
+  struct Rq { std::vector<Job> jobs; cudaEvent_t ready, ev; };
+  std::vector<Rq> todo;
+  for (uint64_t tk : s->admitted) {
+    Request& r = s->reqs[tk];
+    if (!r.in_copy) continue;
+    r.in_copy = false;
+    Rq q{{}, r.ready, r.in_ev};
+    int64_t off = r.in_off;
+    for (const em_cloud& c : r.clouds) {
+      const size_t floats = (size_t)(c.n * c.stride);
+      if (floats) q.jobs.push_back({c.points, s->in_arena + off, floats * sizeof(float)});
+      off += (int64_t)((floats + 3) & ~size_t(3));
+    }
+    todo.push_back(q);
   }
-  return EM_OK;
+  if (todo.empty()) return;
+  lk.unlock();
+  for (const Rq& q : todo) {
+    if (q.ready) cudaStreamWaitEvent(s->copy_stream, q.ready, 0);
+    for (const Job& j : q.jobs) {
+      cudaError_t e = cudaMemcpyAsync(j.dst, j.src, j.bytes, cudaMemcpyHostToDevice, s->copy_stream);
+      if (e != cudaSuccess) map_record_error("host cloud copy", e);  // the batch's event reports it
+    }
+    cudaEventRecord(q.ev, s->copy_stream);
+  }
+  lk.lock();
 }
 
 // One worker pass: complete finished flights, admit, launch.  Returns true when
@@ -170,6 +253,7 @@ bool worker_pass(em_server* s, std::unique_lock<std::mutex>& lk) {
     s->cv_done.notify_all();
   }
   admit(s);
+  issue_host_copies(s, lk);
   if (s->cfg.mode == EM_SERVE_PLAIN) {
     // one update per request, arrival order, one stream
     while (!s->admitted.empty()) {
@@ -191,19 +275,15 @@ bool worker_pass(em_server* s, std::unique_lock<std::mutex>& lk) {
       f.tickets.assign(1, tk);
       f.maps.clear();
       em_map* m = s->maps[r.map_id];
-      std::vector<em_cloud> cl = r.clouds;
-      std::vector<HostCopy> copies;
-      if (r.on_host) {
-        int64_t off = 0;
-        for (em_cloud& c : cl) c = stage_cloud(s, 0, c, off, copies);
-      }
-      cudaEvent_t ready = r.ready;
+      std::vector<em_cloud> cl;
+      if (r.on_host) arena_clouds(s, r, cl);
+      else cl = r.clouds;
+      cudaEvent_t ready = r.on_host ? r.in_ev : r.ready;  // host clouds: their copy (after ready)
       const uint32_t read_mask = r.read_mask;
       float* read_dst = r.read_dst;
       lk.unlock();
       if (ready) cudaStreamWaitEvent(s->streams[0], ready, 0);
-      int rc = issue_copies(copies, s->streams[0]);
-      if (rc == EM_OK) rc = em_update_multi(m, cl.data(), (int32_t)cl.size(), (em_stream_t)s->streams[0]);
+      int rc = em_update_multi(m, cl.data(), (int32_t)cl.size(), (em_stream_t)s->streams[0]);
       if (rc == EM_OK && read_mask) rc = map_read_layers(m, read_mask, read_dst, s->streams[0]);
       if (rc == EM_OK) cudaEventRecord(f.ev, s->streams[0]);
       lk.lock();
@@ -249,12 +329,11 @@ bool worker_pass(em_server* s, std::unique_lock<std::mutex>& lk) {
       struct Staged { float* host; int64_t off, floats; };
       std::vector<Staged> staged;
       int64_t stage_used = 0;
-      std::vector<HostCopy> copies;
-      int64_t in_used = 0;
       const int64_t t0 = now_ns();
       for (uint64_t tk : take) {
         Request& r = s->reqs[tk];
-        if (r.ready) ready.push_back(r.ready);
+        if (r.on_host) ready.push_back(r.in_ev);  // its copy, which waited for ready
+        else if (r.ready) ready.push_back(r.ready);
         if (r.read_mask) {
           rmaps.push_back(s->maps[r.map_id]);
           rmasks.push_back(r.read_mask);
@@ -269,10 +348,10 @@ bool worker_pass(em_server* s, std::unique_lock<std::mutex>& lk) {
         r.state = kRunning;
         r.res.t_start_ns = t0;
         r.res.batch_size = (int32_t)take.size();
-        for (const em_cloud& c : r.clouds) {
-          pm.push_back(s->maps[r.map_id]);
-          pc.push_back(r.on_host ? stage_cloud(s, si, c, in_used, copies) : c);
-        }
+        const size_t c0 = pc.size();
+        if (r.on_host) arena_clouds(s, r, pc);
+        else pc.insert(pc.end(), r.clouds.begin(), r.clouds.end());
+        for (size_t i = c0; i < pc.size(); ++i) pm.push_back(s->maps[r.map_id]);
         s->map_busy[r.map_id] = 1;
       }
       f.busy = true;
@@ -284,9 +363,7 @@ bool worker_pass(em_server* s, std::unique_lock<std::mutex>& lk) {
       if ((int64_t)take.size() > s->st.max_batch_size) s->st.max_batch_size = (int64_t)take.size();
       lk.unlock();
       for (cudaEvent_t e : ready) cudaStreamWaitEvent(s->streams[si], e, 0);
-      int rc = issue_copies(copies, s->streams[si]);
-      if (rc == EM_OK)
-        rc = em_update_batch(s->batches[si], pm.data(), pc.data(), (int32_t)pc.size(), (em_stream_t)s->streams[si]);
+      int rc = em_update_batch(s->batches[si], pm.data(), pc.data(), (int32_t)pc.size(), (em_stream_t)s->streams[si]);
       if (rc == EM_OK && !rmaps.empty())
         rc = maps_read_layers(rmaps.data(), rmasks.data(), rdst.data(), (int)rmaps.size(), s->streams[si]);
       if (rc == EM_OK) cudaEventRecord(f.ev_maps, s->streams[si]);
@@ -487,21 +564,23 @@ int em_server_submit_many(em_server* s, const em_request* reqs, int32_t n, void*
   for (int32_t q = 0; q < n; ++q) {
     if (reqs[q].map_id < 0 || reqs[q].map_id >= (int32_t)s->maps.size()) return EM_ERR_INVALID_ARG;
   }
-  if (any_host && s->in_stage.empty()) {
-    // one input buffer per stream: a full batch of stride-4 points, each cloud padded to 16 bytes
-    const int64_t cap = s->cfg.max_batch_points * 4 + 4 * (int64_t)s->cfg.max_batch_maps * 8;
-    const int64_t bytes = cap * (int64_t)sizeof(float) * (int64_t)s->streams.size();
+  if (any_host && !s->in_arena) {
+    // the input arena: full batches of stride-4 points for every stream and two more
+    // (the admitted requests waiting for a stream), each cloud padded to 16 bytes
+    const int64_t per = s->cfg.max_batch_points * 4 + 4 * (int64_t)s->cfg.max_batch_maps * 8;
+    const int64_t cap = per * ((int64_t)s->streams.size() + 2);
+    const int64_t bytes = cap * (int64_t)sizeof(float);
     if (s->bytes_in_use + bytes > s->cfg.budget_bytes) return EM_ERR_REJECTED;
     cudaSetDevice(s->cfg.device);
-    for (size_t i = 0; i < s->streams.size(); ++i) {
-      float* b = nullptr;
-      if (cudaMalloc((void**)&b, (size_t)cap * sizeof(float)) != cudaSuccess) {
-        cudaGetLastError();
-        for (float* x : s->in_stage) cudaFree(x);
-        s->in_stage.clear();
-        return EM_ERR_OOM;
-      }
-      s->in_stage.push_back(b);
+    if (cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      s->copy_stream = nullptr;
+      return EM_ERR_CUDA;
+    }
+    if (cudaMalloc((void**)&s->in_arena, (size_t)bytes) != cudaSuccess) {
+      cudaGetLastError();
+      s->in_arena = nullptr;
+      return EM_ERR_OOM;
     }
     s->in_cap = cap;
     s->fixed_bytes += bytes;
@@ -615,6 +694,7 @@ int em_server_cancel(em_server* s, uint64_t ticket) {
     drop(s->admitted);
     s->bytes_in_use -= r.bytes;
     s->slots_in_use -= 1;
+    release_host(s, ticket, r);  // a copy in flight lands before any later copy reuses the room
   } else {
     drop(s->pending);
   }
@@ -679,7 +759,12 @@ int em_server_destroy(em_server* s) {
     if (f.ev_maps) cudaEventDestroy(f.ev_maps);
   }
   for (float* st : s->stage) cudaFree(st);
-  for (float* st : s->in_stage) cudaFree(st);
+  if (s->copy_stream) cudaStreamSynchronize(s->copy_stream);
+  cudaFree(s->in_arena);
+  if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
+  for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
+  for (auto& kv : s->reqs)
+    if (kv.second.in_ev) cudaEventDestroy(kv.second.in_ev);
   for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
   for (em_map* m : s->maps) em_destroy(m);
   delete s;

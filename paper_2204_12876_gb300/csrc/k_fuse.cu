@@ -1,7 +1,7 @@
 // k_fuse.cu -- per-cell fusion (Section II-C of the paper).
 //
 // Every cell that received points in this update is fused once from its
-// segment of records (z, sigma_p^2):
+// records (z, sigma_p^2):
 //   1. wall rule: in a valid cell with more than wall_num_thresh points, points
 //      below the current height are dropped (before the outlier test);
 //   2. Mahalanobis gate against the pre-update estimate: reject iff
@@ -16,59 +16,24 @@
 //      after point gives the same result in exact arithmetic.
 //
 // The two sums are accumulated exactly: every float32 term is converted to a
-// signed 128-bit fixed-point integer with 44 fractional bits and the integers
-// are added.  Integer addition is associative, so the result is the same for
-// every order of the points and every split of a segment between lanes, bit
-// for bit (no float atomics).
+// fixed-point integer with 44 fractional bits (kept as h 2^27 + l) and the
+// integers are added.  Integer addition is associative, so the result is the
+// same for every order of the points and every split of the work, bit for bit
+// (no float atomics).
 //
-// Work split, one launch:
-//   chunks  the record array is cut into chunks of `chunk` records; a warp owns
-//           the cells whose segment STARTS in its chunk and streams their
-//           records 32 at a time (one record per lane, coalesced 16-byte
-//           loads).  Lanes of the same cell form a run; a segmented inclusive
-//           scan over the runs gives each run's sums at its last lane, which
-//           writes the cell.  A run that reaches lane 31 carries its partial
-//           sums into the next 32 records.  Load balance follows the records,
-//           not the cells, so uneven cells and maps cost no divergence.
-//   large   cells with more than big_thresh records (flagged in their records
-//           and listed by k_alloc) are skipped by the chunks and fused by a
-//           whole block each, taken from a counter (atomicAdd; no block waits).
+// Work split: one block per tile of kTile cells (the records of a tile are one
+// range, k_sort.cu).  The block stages the tile's pre-update state (h and the
+// effective variance) in shared memory, streams the tile's records with every
+// thread on one record (the next window's loads in flight), reduces each run
+// of equal cells in consecutive lanes with a segmented scan, and adds the
+// run's sums to the cell's accumulators in shared memory (64-bit integer
+// atomics).  Then every touched cell of the tile is written once.  Blocks take
+// tiles from a counter, the heavy tiles (many records) first.
 #include "em_point.cuh"
 
 namespace em {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kFuseThreads = 256;
-constexpr int kFuseWarps = kFuseThreads / 32;
-#ifndef EM_FUSE_BLOCKS_PER_SM
-// 4 resident blocks (64 registers, a few spilled) measured 5-6 % faster than 3
-// (80 registers, no spills) on both the served round and the 64-map batch
-#define EM_FUSE_BLOCKS_PER_SM 4
-#endif
-constexpr int kFuseBlocksPerSM = EM_FUSE_BLOCKS_PER_SM;  // resident blocks per SM (sets the register budget)
-
-__device__ __forceinline__ __int128 shfl_xor_i128(__int128 v, int o) {
-  const unsigned long long lo = (unsigned long long)v;
-  const unsigned long long hi = (unsigned long long)((unsigned __int128)v >> 64);
-  const unsigned long long lo2 = __shfl_xor_sync(kFull, lo, o);
-  const unsigned long long hi2 = __shfl_xor_sync(kFull, hi, o);
-  return (__int128)(((unsigned __int128)hi2 << 64) | lo2);
-}
-
-// Partial sums of a run of records: the two fixed-point sums as (h, l) pairs
-// (value h 2^27 + l) and the counts packed as accepted | rejected << 10 |
-// dropped-by-wall << 20 (a run holds at most kMaxBigThresh records).  Within
-// 32 records the l parts stay below 2^32; across passes they are carried in
-// 64 bits.
-struct Part {
-  long long wh, th;
-  unsigned long long wl, tl;
-  uint32_t n;
-};
-constexpr uint32_t kCntAcc = 1u, kCntRej = 1u << 10, kCntWall = 1u << 20;
-__device__ __forceinline__ int cnt_acc(uint32_t n) { return (int)(n & 1023u); }
-__device__ __forceinline__ int cnt_rej(uint32_t n) { return (int)((n >> 10) & 1023u); }
-__device__ __forceinline__ int cnt_wall(uint32_t n) { return (int)(n >> 20); }
 
 // The cell's snapshot and the decisions that do not depend on single points.
 struct CellCtx {
@@ -148,304 +113,199 @@ __device__ __forceinline__ bool write_cell(const MapDev& m, int32_t cell, const 
   return true;
 }
 
-// Statistics of one warp for its current map, in lane registers: each lane
-// counts its own records and the cells it wrote; a flush (warp sums, four
-// atomics by lane 0) happens when the warp moves to another map and at the end.
-struct WarpCount {
-  int map = -1;
-  uint32_t acc = 0, rej = 0, wal = 0, cells = 0;
+// Per-cell accumulators of one tile in shared memory, and its staged state.
+struct TileSmem {
+  long long wh[kTile], th[kTile];            // fixed-point sums: high parts
+  unsigned long long wl[kTile], tl[kTile];   // ... and low parts (value h 2^27 + l)
+  unsigned long long n[kTile];               // accepted | rejected << 32
+  float h[kTile], ve[kTile];                 // pre-update height, effective variance (+inf: empty)
+  uint32_t cnt[kTile];                       // records per cell (the wall rule)
+  int work;
+  unsigned long long stat[4];                // accepted, rejected, wall, cells of the tile
 };
 
-__device__ __forceinline__ void add_stats(const BatchDev& b, int mi, uint32_t acc, uint32_t rej, uint32_t wal,
-                                          uint32_t cells) {
-  unsigned long long* st = b.maps[mi].ctl->stats;
-  if (acc) atomicAdd(st + kStAccepted, (unsigned long long)acc);
-  if (rej) atomicAdd(st + kStRejected, (unsigned long long)rej);
-  if (wal) atomicAdd(st + kStWall, (unsigned long long)wal);
-  if (cells) atomicAdd(st + kStCellsUpdated, (unsigned long long)cells);
-}
-
-// all 32 lanes
-__device__ __forceinline__ void warp_flush(const BatchDev& b, WarpCount& wc) {
-  const uint32_t a = __reduce_add_sync(kFull, wc.acc), r = __reduce_add_sync(kFull, wc.rej);
-  const uint32_t w = __reduce_add_sync(kFull, wc.wal), c = __reduce_add_sync(kFull, wc.cells);
-  if ((threadIdx.x & 31) == 0 && wc.map >= 0) add_stats(b, wc.map, a, r, w, c);
-  wc.acc = wc.rej = wc.wal = wc.cells = 0;
-}
-
-__device__ __forceinline__ unsigned long long rec_tag(const float4& q) {
-  return ((unsigned long long)__float_as_uint(q.w) << 32) | (unsigned long long)__float_as_uint(q.z);
-}
-
-// Write a carried run that ended at the previous pass (one lane).  Its records
-// were counted in their passes; the cell is counted here.
-__device__ __forceinline__ void finish_tag(const BatchDev& b, WarpCount& wc, unsigned long long tag, const Part& a) {
-  const uint32_t w = (uint32_t)(tag >> 32);
-  const int mi = (int)(w & kRecMapMask);
-  const int32_t cell = (int32_t)(uint32_t)tag;
-  const MapDev& m = b.maps[mi];
-  const CellCtx c = load_cell(m, cell, (w & kRecWall) != 0);
-  if (write_cell(m, cell, c, fix128(a.wh, a.wl), fix128(a.th, a.tl), cnt_acc(a.n), cnt_rej(a.n))) {
-    if (mi == wc.map) ++wc.cells; else add_stats(b, mi, 0, 0, 0, 1);
-  }
-}
-
-// Record r of the batch (zeros beyond n_rec).
-__device__ __forceinline__ float4 load_rec(const BatchDev& b, int64_t r, int32_t n_rec) {
-  return r < n_rec ? __ldg(b.rec + r) : make_float4(0.f, 0.f, 0.f, 0.f);
-}
-
-// A record's map and cell words are in range (every record in [0, rec_total)
-// was written by k_scatter this update; anything else is recorded and skipped).
-__device__ __forceinline__ bool rec_sane(const BatchDev& b, const float4& q) {
-  const int mi = (int)(__float_as_uint(q.w) & kRecMapMask);
-  return mi < b.n_maps && (uint32_t)__float_as_int(q.z) < (uint32_t)(b.maps[mi].W * b.maps[mi].H);
-}
-
-// Cell state for a record, loaded one pass ahead (a cell is written only by the
-// warp that owns it, when its run ends, so the prefetched value is current).
-__device__ __forceinline__ Snap prefetch_snap(const BatchDev& b, const float4& q, bool inr) {
-  if (!inr || !rec_sane(b, q)) return Snap{0.f, 0.f, 0};
-  return load_snap(b.maps[__float_as_uint(q.w) & kRecMapMask], __float_as_int(q.z));
-}
-
-// The cells whose segment starts in [ch * chunk, (ch + 1) * chunk), one warp.
-// Software pipeline: the records of pass i + 2 and the cell state of pass i + 1
-// are in flight while pass i is fused.
-__device__ __forceinline__ void fuse_chunk(const BatchDev& b, WarpCount& wc, int64_t ch, int32_t n_rec) {
-  const int lane = threadIdx.x & 31;
-  const unsigned upto = lane == 31 ? kFull : ((1u << (lane + 1)) - 1u);  // lanes <= this lane
-  const int64_t win_end = (ch + 1) * (int64_t)b.chunk;
-  int64_t pos = ch * (int64_t)b.chunk;
-  // carried run: 0 none, 1 ours (partial sums in cp), 2 not ours (started before the chunk)
-  int cmode = 0;
-  unsigned long long ctag = 0;
-  Part cp{0, 0, 0ull, 0ull, 0u};
-  if (pos > 0) {
-    ctag = rec_tag(__ldg(b.rec + pos - 1));
-    cmode = 2;
-  }
-  float4 q = load_rec(b, pos + lane, n_rec);
-  float4 qn = load_rec(b, pos + 32 + lane, n_rec);
-  Snap sn = prefetch_snap(b, q, pos + lane < n_rec);
-  for (;;) {
-    const int64_t r = pos + lane;
-    const bool inr = r < n_rec;
-    const float4 qnn = load_rec(b, pos + 64 + lane, n_rec);
-    const Snap snn = prefetch_snap(b, qn, pos + 32 + lane < n_rec);
-    const unsigned long long tag = inr ? rec_tag(q) : ~0ull;
-    unsigned long long prev = __shfl_up_sync(kFull, tag, 1);
-    if (lane == 0) prev = cmode ? ctag : ~tag;  // nothing carried: lane 0 starts a run
-    const bool head = inr && tag != prev;
-    // the carried run of ours ends where this pass starts another run (or nothing)
-    if (cmode == 1 && __shfl_sync(kFull, !inr || head, 0)) {
-      if (lane == 0) finish_tag(b, wc, ctag, cp);
-      cmode = 0;
-    }
-    const unsigned stops = __ballot_sync(kFull, !inr || (head && r >= win_end));
-    const int first_stop = stops ? __ffs(stops) - 1 : 32;
-    if (first_stop == 0) break;
-    const bool live = lane < first_stop;
-    const unsigned heads = __ballot_sync(kFull, head && live);
-    const unsigned hm = heads & upto;
-    const bool cont = live && hm == 0;  // continues the carried run
-    const int hd = hm ? 31 - __clz(hm) : 0;
-    const uint32_t w = __float_as_uint(q.w);
-    const bool big = (w & kRecBig) != 0;
-    const int mi = (int)(w & kRecMapMask);
-    const int32_t cell = __float_as_int(q.z);
-    const bool sane = live && rec_sane(b, q);
-    if (live && !sane) atomicCAS(&b.maps[0].ctl->err, 0, kErrInternal);
-    const bool ours = sane && !big && !(cont && cmode == 2);
-    // statistics: one map per pass (the usual case) goes to the lane registers
-    const int pm = ours ? mi : -1;
-    bool mixed = false;
-    if (!__all_sync(kFull, pm < 0 || pm == wc.map)) {
-      const unsigned om = __ballot_sync(kFull, pm >= 0);
-      const int first = __shfl_sync(kFull, pm, __ffs(om) - 1);
-      if (__all_sync(kFull, pm < 0 || pm == first)) {
-        warp_flush(b, wc);
-        wc.map = first;
-      } else {
-        mixed = true;  // a pass across a map boundary: count with atomics
-      }
-    }
-    Fix fw{0, 0u}, ft{0, 0u};
-    uint32_t n = 0u;
-    CellCtx c;
-    if (ours) {
-      c = make_cell(b.maps[mi], sn, (w & kRecWall) != 0);
-      const uint8_t st = fuse_one(c, q.x, q.y, fw, ft);
-      n = st == kPtFused ? kCntAcc : st == kPtRejected ? kCntRej : kCntWall;
-      if (!mixed) {
-        wc.acc += st == kPtFused;
-        wc.rej += st == kPtRejected;
-        wc.wal += st == kPtWall;
-      } else {
-        add_stats(b, mi, st == kPtFused, st == kPtRejected, st == kPtWall, 0);
-      }
-      if (b.tr_status) b.tr_status[b.idx_sorted[r]] = st;
-    }
-    // segmented inclusive scan: lane l sums lanes hd(l) .. l of its run; only as
-    // many steps as the longest run of this pass needs
-    const int runlen = live ? lane - hd + 1 : 0;
-    const int maxrun = (int)__reduce_max_sync(kFull, (unsigned)runlen);
-    long long wh = fw.h, th = ft.h;
-    uint32_t wl = fw.l, tl = ft.l;
-    for (int o = 1; o < maxrun; o <<= 1) {
-      const long long awh = __shfl_up_sync(kFull, wh, o), ath = __shfl_up_sync(kFull, th, o);
-      const uint32_t awl = __shfl_up_sync(kFull, wl, o), atl = __shfl_up_sync(kFull, tl, o);
-      const uint32_t an = __shfl_up_sync(kFull, n, o);
-      if (lane - o >= hd) {
-        wh += awh;
-        th += ath;
-        wl += awl;
-        tl += atl;
-        n += an;
-      }
-    }
-    Part v{wh, th, (unsigned long long)wl, (unsigned long long)tl, n};
-    if (cont && cmode == 1) {  // the carried partial sums belong to this run
-      v.wh += cp.wh;
-      v.th += cp.th;
-      v.wl += cp.wl;
-      v.tl += cp.tl;
-      v.n += cp.n;
-    }
-    const bool next_head = lane < 31 && ((heads >> (lane + 1)) & 1u);
-    const bool end = live && (next_head || (lane == first_stop - 1 && first_stop < 32));
-    if (end && ours &&
-        write_cell(b.maps[mi], cell, c, fix128(v.wh, v.wl), fix128(v.th, v.tl), cnt_acc(v.n), cnt_rej(v.n))) {
-      if (!mixed) ++wc.cells; else add_stats(b, mi, 0, 0, 0, 1);
-    }
-    if (first_stop < 32) break;
-    // lane 31's run goes on in the next 32 records
-    const unsigned long long t31 = __shfl_sync(kFull, tag, 31);
-    if (__shfl_sync(kFull, ours, 31)) {
-      cp.wh = __shfl_sync(kFull, v.wh, 31);
-      cp.th = __shfl_sync(kFull, v.th, 31);
-      cp.wl = __shfl_sync(kFull, v.wl, 31);
-      cp.tl = __shfl_sync(kFull, v.tl, 31);
-      cp.n = __shfl_sync(kFull, v.n, 31);
-      cmode = 1;
-      ctag = t31;
-    } else if (__shfl_sync(kFull, big && sane, 31)) {
-      // skip the rest of a large cell: its segment end from the cell's (base, count)
-      const uint32_t w31 = (uint32_t)(t31 >> 32);
-      const int2 sg = b.maps[w31 & kRecMapMask].cell_seg[(int32_t)(uint32_t)t31];
-      const int64_t next = (int64_t)sg.x + sg.y;
-      if (next > pos + 32) {  // restart the pipeline there
-        pos = next;
-        cmode = 0;
-        q = load_rec(b, pos + lane, n_rec);
-        qn = load_rec(b, pos + 32 + lane, n_rec);
-        sn = prefetch_snap(b, q, pos + lane < n_rec);
-        continue;
-      }
-      cmode = 0;
-    } else {
-      cmode = 2;  // a run that started before the chunk
-      ctag = t31;
-    }
-    pos += 32;
-    q = qn;
-    qn = qnn;
-    sn = snn;
-  }
-}
-
-// A large cell with a whole block: lane partial sums, warp and block reductions.
-__device__ __forceinline__ void fuse_big(const BatchDev& b, int2 e, __int128* s_q, uint32_t* s_n) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const MapDev& m = b.maps[e.x];
-  const int2 sg = m.cell_seg[e.y];
-  const CellCtx c = load_cell(m, e.y, m.wall > 0 && sg.y > m.wall);
-  long long wh = 0, th = 0;
-  unsigned long long wl = 0, tl = 0;
-  uint32_t acc = 0, rej = 0, wal = 0;
-  for (int i = threadIdx.x; i < sg.y; i += kFuseThreads) {
-    const float4 q = __ldg(b.rec + sg.x + i);
-    Fix fw, ft;
-    const uint8_t st = fuse_one(c, q.x, q.y, fw, ft);
-    wh += fw.h;
-    wl += fw.l;
-    th += ft.h;
-    tl += ft.l;
-    acc += st == kPtFused;
-    rej += st == kPtRejected;
-    wal += st == kPtWall;
-    if (b.tr_status) b.tr_status[b.idx_sorted[sg.x + i]] = st;
-  }
-  __int128 qw = fix128(wh, wl), qt = fix128(th, tl);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    qw += shfl_xor_i128(qw, o);
-    qt += shfl_xor_i128(qt, o);
-  }
-  acc = __reduce_add_sync(kFull, acc);
-  rej = __reduce_add_sync(kFull, rej);
-  wal = __reduce_add_sync(kFull, wal);
-  if (lane == 0) {
-    s_q[warp] = qw;
-    s_q[kFuseWarps + warp] = qt;
-    s_n[warp] = acc;
-    s_n[kFuseWarps + warp] = rej;
-    s_n[2 * kFuseWarps + warp] = wal;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __int128 tw = 0, tt = 0;
-    uint32_t ta = 0, tr = 0, tl2 = 0;
-    for (int k = 0; k < kFuseWarps; ++k) {
-      tw += s_q[k];
-      tt += s_q[kFuseWarps + k];
-      ta += s_n[k];
-      tr += s_n[kFuseWarps + k];
-      tl2 += s_n[2 * kFuseWarps + k];
-    }
-    const bool upd = write_cell(m, e.y, c, tw, tt, (int)ta, (int)tr);
-    add_stats(b, e.x, ta, tr, tl2, upd ? 1u : 0u);
-  }
-  __syncthreads();
-}
-
-__global__ void __launch_bounds__(kFuseThreads, kFuseBlocksPerSM) k_fuse(const BatchDev* __restrict__ bp) {
-  __shared__ int s_slot;
-  __shared__ __int128 s_q[2 * kFuseWarps];
-  __shared__ uint32_t s_n[3 * kFuseWarps];
+template <int NT>
+__global__ void __launch_bounds__(NT) k_fuse(const BatchDev* __restrict__ bp) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TileSmem& S = *reinterpret_cast<TileSmem*>(smem_raw);
   const BatchDev& b = *bp;
-
-  // ---- large cells first (the longest jobs): one block each, taken from a counter
-  const int n_big = min(b.ctl->n_big, b.big_cap);
-  if (n_big > 0) {
-    for (;;) {
-      if (threadIdx.x == 0) s_slot = atomicAdd(&b.ctl->big_next, 1);
-      __syncthreads();
-      const int jb = s_slot;
-      __syncthreads();
-      if (jb >= n_big) break;
-      fuse_big(b, b.big_list[jb], s_q, s_n);
+  const int lane = threadIdx.x & 31;
+  const int64_t n_tiles = b.n_cells / kTile;
+  const int n_heavy = b.ctl->n_heavy;
+  // every block takes work items from the counter until they run out; a block
+  // takes at most all of them (a bound that holds whatever the counter reads)
+  for (int64_t items = 0;; ++items) {
+    if (threadIdx.x == 0) S.work = atomicAdd(&b.ctl->fuse_next, 1);
+    __syncthreads();
+    const int w = S.work;
+    if (items > n_tiles + n_heavy || w < 0 || n_heavy < 0 || n_heavy > n_tiles) {
+      if (threadIdx.x == 0) atomicCAS(&b.maps[0].ctl->err, 0, kErrInternal);
+      break;
     }
+    int64_t t;
+    if (w < n_heavy) {
+      t = b.heavy[w];
+    } else {
+      t = w - n_heavy;
+      if (t >= n_tiles) break;  // block-uniform
+    }
+    const int32_t r0 = b.tile_base[t], r1 = b.tile_base[t + 1];
+    if (r1 == r0 || (w >= n_heavy && r1 - r0 > b.heavy_thresh)) {  // nothing to fuse, or a heavy tile done first
+      __syncthreads();
+      continue;
+    }
+    const int mi = find_map_cell(b.maps, b.n_maps, t * kTile);
+    const MapDev& m = b.maps[mi];
+    const int32_t p0 = (int32_t)(t * kTile - m.cell_begin);
+    const int32_t ncell = min(kTile, m.W * m.H - p0);
+    const bool wall_on = m.wall > 0;
+    // ---- the tile's pre-update state; accumulators to zero
+    for (int c = threadIdx.x; c < kTile; c += NT) {
+      float h = 0.f, ve = __int_as_float(0x7f800000);
+      if (c < ncell) {
+        const float var = __ldg(m.var + p0 + c);
+        h = __ldg(m.h + p0 + c);
+        const int32_t tl = __ldg(m.t_last + p0 + c);
+        if (isfinite(var)) ve = var_eff(m, var, tl);
+      }
+      S.h[c] = h;
+      S.ve[c] = ve;
+      S.wh[c] = 0;
+      S.th[c] = 0;
+      S.wl[c] = 0;
+      S.tl[c] = 0;
+      S.n[c] = 0;
+      S.cnt[c] = 0;
+    }
+    if (threadIdx.x < 4) S.stat[threadIdx.x] = 0;
+    __syncthreads();
+    if (wall_on) {  // records per cell first: the wall rule looks at the cell's count
+      for (int32_t r = r0 + threadIdx.x; r < r1; r += NT) atomicAdd(&S.cnt[__ldg(b.rc + r)], 1u);
+      __syncthreads();
+    }
+    const float k2 = __fmul_rn(m.k, m.k);
+    uint32_t acc = 0, rej = 0, wal = 0;
+    // ---- records, NT at a time; the next window's loads in flight
+    int32_t r = r0 + threadIdx.x;
+    float z = 0.f, vp = 1.f;
+    uint32_t c = 0;
+    if (r < r1) { z = __ldg(b.rz + r); vp = __ldg(b.rv + r); c = __ldg(b.rc + r); }
+    for (int32_t base = r0; base < r1; base += NT) {
+      const bool live = r < r1;
+      const int32_t rn = r + NT;
+      float zn = 0.f, vpn = 1.f;
+      uint32_t cn = 0;
+      if (rn < r1) { zn = __ldg(b.rz + rn); vpn = __ldg(b.rv + rn); cn = __ldg(b.rc + rn); }
+      Fix fw{0, 0u}, ft{0, 0u};
+      uint8_t st = kPtFused;
+      if (live) {
+        const float h = S.h[c], ve = S.ve[c];
+        const bool valid = isfinite(ve);
+        if (wall_on && valid && (int32_t)S.cnt[c] > m.wall && z < h) {
+          st = kPtWall;
+        } else if (valid && m.k > 0.f && __fmul_rn(__fsub_rn(z, h), __fsub_rn(z, h)) > __fmul_rn(k2, __fadd_rn(ve, vp))) {
+          // |z - h| / sqrt(sigma_m^2 + sigma_p^2) > k  <=>  (z - h)^2 > k^2 (sigma_m^2 + sigma_p^2)  (k > 0)
+          st = kPtRejected;
+        } else {
+          const float wgt = __frcp_rn(vp);
+          fw = to_fix(wgt);
+          ft = to_fix(__fmul_rn(wgt, __fsub_rn(z, valid ? h : m.z_ref)));
+        }
+        acc += st == kPtFused;
+        rej += st == kPtRejected;
+        wal += st == kPtWall;
+        if (b.tr_status) b.tr_status[b.idx_sorted[r]] = st;
+      }
+      unsigned long long nn = !live ? 0ull : st == kPtFused ? 1ull : st == kPtRejected ? (1ull << 32) : 0ull;
+      // runs of equal cells in consecutive lanes: a segmented inclusive scan, as
+      // many steps as the longest run needs; the run's last lane adds its sums
+      const unsigned long long tag = live ? (unsigned long long)c : ~0ull;
+      int head, len;
+      key_runs(tag, head, len);
+      // the run's last lane (every lane takes part in the shuffle)
+      const unsigned long long next = __shfl_down_sync(kFull, tag, 1);
+      const bool tail = lane == 31 || next != tag;
+      const int maxrun = (int)__reduce_max_sync(kFull, live ? (unsigned)(lane - head + 1) : 1u);
+      long long wh = fw.h, th = ft.h;
+      unsigned long long wl = fw.l, tl = ft.l;
+      for (int o = 1; o < maxrun; o <<= 1) {
+        const long long awh = __shfl_up_sync(kFull, wh, o), ath = __shfl_up_sync(kFull, th, o);
+        const unsigned long long awl = __shfl_up_sync(kFull, wl, o), atl = __shfl_up_sync(kFull, tl, o);
+        const unsigned long long an = __shfl_up_sync(kFull, nn, o);
+        if (lane - o >= head) {
+          wh += awh;
+          th += ath;
+          wl += awl;
+          tl += atl;
+          nn += an;
+        }
+      }
+      if (live && tail) {
+        if (nn) atomicAdd(&S.n[c], nn);
+        if (wh | (long long)wl) {
+          atomicAdd(reinterpret_cast<unsigned long long*>(&S.wh[c]), (unsigned long long)wh);
+          atomicAdd(&S.wl[c], wl);
+          atomicAdd(reinterpret_cast<unsigned long long*>(&S.th[c]), (unsigned long long)th);
+          atomicAdd(&S.tl[c], tl);
+        }
+      }
+      r = rn;
+      z = zn;
+      vp = vpn;
+      c = cn;
+    }
+    __syncthreads();
+    // ---- every touched cell of the tile, once
+    uint32_t cells = 0;
+    for (int cc = threadIdx.x; cc < ncell; cc += NT) {
+      const unsigned long long nn = S.n[cc];
+      if (!nn) continue;
+      CellCtx cx;
+      cx.h = S.h[cc];
+      cx.ve = S.ve[cc];
+      cx.valid = isfinite(cx.ve);
+      cx.href = cx.valid ? cx.h : m.z_ref;
+      cells += write_cell(m, p0 + cc, cx, fix128(S.wh[cc], S.wl[cc]), fix128(S.th[cc], S.tl[cc]),
+                          (int)(uint32_t)nn, (int)(nn >> 32));
+    }
+    // ---- the tile's statistics: one atomic per counter
+    const uint32_t v[4] = {acc, rej, wal, cells};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint32_t x = __reduce_add_sync(kFull, v[k]);
+      if (lane == 0 && x) atomicAdd(&S.stat[k], (unsigned long long)x);
+    }
+    __syncthreads();
+    if (threadIdx.x < 4 && S.stat[threadIdx.x]) {
+      const int idx[4] = {kStAccepted, kStRejected, kStWall, kStCellsUpdated};
+      atomicAdd(&m.ctl->stats[idx[threadIdx.x]], S.stat[threadIdx.x]);
+    }
+    __syncthreads();
   }
-
-  // ---- record chunks, one warp each (grid-stride)
-  const int32_t n_rec = (int32_t)min((int64_t)b.ctl->rec_total, b.n_points);
-  const int64_t n_chunks = ((int64_t)n_rec + b.chunk - 1) / b.chunk;
-  const int64_t wstride = (int64_t)gridDim.x * kFuseWarps;
-  WarpCount wc;
-  for (int64_t ch = (int64_t)blockIdx.x * kFuseWarps + (threadIdx.x >> 5); ch < n_chunks; ch += wstride)
-    fuse_chunk(b, wc, ch, n_rec);
-  warp_flush(b, wc);
 }
 
-cudaError_t launch_fuse(const BatchDev* b, int64_t n_points, int chunk, cudaStream_t s) {
-  const int c = (chunk >= 64 && chunk <= 1024 && (chunk & (chunk - 1)) == 0) ? chunk : 256;
-  const int64_t warps = n_points / c + 1;
-  const int64_t want = (warps + kFuseWarps - 1) / kFuseWarps;
-  const int64_t cap = (int64_t)sm_count() * kFuseBlocksPerSM;  // one resident wave
-  const int grid = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
-  k_fuse<<<grid, kFuseThreads, 0, s>>>(b);
+template <int NT>
+static cudaError_t launch_fuse_t(const BatchDev* b, int64_t n_cells, cudaStream_t s) {
+  static bool attr[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !attr[dev]) {  // more than the 48 KB of static shared memory
+    cudaError_t e = cudaFuncSetAttribute(k_fuse<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(TileSmem));
+    if (e != cudaSuccess) return e;
+    attr[dev] = true;
+  }
+  int per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fuse<NT>, NT, sizeof(TileSmem));
+  const int64_t tiles = n_cells / kTile;
+  const int64_t cap = (int64_t)sm_count() * (per_sm > 0 ? per_sm : 1);  // one resident wave
+  const int grid = (int)(tiles < cap ? (tiles < 1 ? 1 : tiles) : cap);
+  k_fuse<NT><<<grid, NT, sizeof(TileSmem), s>>>(b);
   return cudaGetLastError();
+}
+
+cudaError_t launch_fuse(const BatchDev* b, int64_t n_cells, int threads, cudaStream_t s) {
+  return threads >= 512 ? launch_fuse_t<512>(b, n_cells, s) : launch_fuse_t<256>(b, n_cells, s);
 }
 
 }  // namespace em

@@ -348,8 +348,6 @@ __global__ void __launch_bounds__(kMapThreads) k_fill(MapDev m) {
   const int32_t ncell = m.W * m.H;
   for (int32_t p = blockIdx.x * kMapThreads + threadIdx.x; p < ncell; p += gridDim.x * kMapThreads) {
     empty_cell(m, p);
-    m.cnt[p] = 0;
-    m.cell_seg[p] = make_int2(0, 0);
     if ((p & 31) == 0) m.mark[p >> 5] = 0u;
   }
 }

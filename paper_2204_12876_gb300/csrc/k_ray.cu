@@ -90,10 +90,12 @@ __global__ void __launch_bounds__(kRayThreads) k_ray(const BatchDev* __restrict_
           const int32_t k_lo = kl < 1.f ? 1 : kl > (float)kMaxRayK ? kMaxRayK : (int32_t)kl;
           int32_t k_hi = kh > (float)kMaxRayK ? kMaxRayK : (int32_t)kh;
           // last k with k * step < d, decided exactly as sample by sample
-          float kf = floorf(__fdividef(pg.d, step));  // an estimate, made exact just below
-          int32_t k_last = kf > 1.0e9f ? 1000000000 : (int32_t)kf;
-          while (k_last > 0 && !(__fmul_rn((float)k_last, step) < pg.d)) --k_last;
-          while (k_last < 1000000000 && __fmul_rn((float)(k_last + 1), step) < pg.d) ++k_last;
+          // (the estimate is within a few units of the answer; past kMaxRayK the
+          // range is capped anyway, so the searches stop there)
+          float kf = fminf(floorf(__fdividef(pg.d, step)), (float)kMaxRayK);  // an estimate, made exact just below
+          int32_t k_last = (int32_t)kf;
+          for (int it = 0; it < 64 && k_last > 0 && !(__fmul_rn((float)k_last, step) < pg.d); ++it) --k_last;
+          for (int it = 0; it < 64 && k_last < kMaxRayK && __fmul_rn((float)(k_last + 1), step) < pg.d; ++it) ++k_last;
           if (k_last < k_hi) k_hi = k_last;
           const float cstep = __fdiv_rn(step, pg.d);  // f_k = k * step / d
           r.ax = __fmul_rn(__fsub_rn(c.t[0], m.x0), m.inv_res);

@@ -1,23 +1,19 @@
-// k_sort.cu -- grouping of points by cell: a counting sort keyed by the
-// physical cell index (one radix digit spanning the whole key).
+// k_sort.cu -- grouping of points by tile of the cell space: a counting sort
+// keyed by the tile of kTile = 1024 physical cells the point falls into.
 //
-//   k_count    per point: transform + bin, warp-aggregated per-cell counts;
+//   k_count    per point: transform + bin, per-tile counts (one atomic per tile
+//              and warp: the lanes whose points share a tile add together);
 //              then per cell: the ray-march threshold h - sqrt(var_eff) of the
 //              pre-update map, stored in logical order (one 4-byte gather per
 //              ray sample later, with no ring-buffer wrap)
-//   k_alloc    per tile of cells: a block scan of the counts gives every cell
-//              a segment [base, base + count) of the record array (the tile's
-//              segments are consecutive, in cell order; a tile takes its range
-//              from one cursor shared by all maps of the batch, so the records
-//              of the batch fill [0, rec_total) without holes); cells with more
-//              than big_thresh records are listed for whole-block fusion
-//   k_scatter  per point: transform + bin again, claim a slot in the cell's
-//              segment, write the 16-byte record (z, sigma_p^2, cell, map|flags)
+//   k_alloc    one block: every tile's range [base, base + count) of the record
+//              arrays by a running scan in tile order; heavy tiles listed
+//   k_scatter  per point: transform + bin again, claim a slot in the tile's
+//              range, write the record (z, sigma_p^2, cell within the tile)
 //
-// The order of records inside a segment depends on atomic arrival order, and
-// the order of the tiles' ranges on the cursor.  The fusion kernel sums the
-// records of a cell exactly in integer fixed point, so neither order changes
-// a result.
+// The order of records inside a tile's range depends on atomic arrival order.
+// The fusion kernel sums the records of a cell exactly in integer fixed point,
+// so the order does not change a result.
 #include "em_point.cuh"
 
 namespace em {
@@ -32,46 +28,6 @@ __device__ __forceinline__ void block_range(int64_t n, int64_t& beg, int64_t& en
   per = (per + 31) & ~int64_t(31);
   beg = (int64_t)blockIdx.x * per;
   end = beg + per < n ? beg + per : n;
-}
-
-// Load the warp's 32 points [wbase, wbase + 32).  When the whole chunk sits in
-// one cloud with 16-byte aligned rows the warp reads it with float4 loads:
-// stride 4 -> one float4 per lane; stride 3 -> 24 float4 staged in shared memory.
-__device__ __forceinline__ int load_warp_points(const BatchDev& b, int64_t wbase, int64_t end, float4* stage,
-                                                float& px, float& py, float& pz) {
-  const int lane = threadIdx.x & 31;
-  const int64_t g = wbase + lane;
-  const int c0 = find_cloud(b.clouds, b.n_clouds, wbase);
-  const CloudDev& cl0 = b.clouds[c0];
-  const bool whole = (wbase + 32 <= end) && (wbase + 32 <= cl0.begin + cl0.n);
-  int ci = c0;
-  if (whole) {
-    const int64_t i0 = wbase - cl0.begin;
-    const float* base = cl0.pts + i0 * cl0.stride;
-    if (cl0.stride == 4 && ((reinterpret_cast<uintptr_t>(base) & 15) == 0)) {
-      float4 q = __ldg(reinterpret_cast<const float4*>(base) + lane);
-      px = q.x; py = q.y; pz = q.z;
-      return ci;
-    }
-    if (cl0.stride == 3 && ((reinterpret_cast<uintptr_t>(base) & 15) == 0)) {
-      if (lane < 24) stage[lane] = __ldg(reinterpret_cast<const float4*>(base) + lane);
-      __syncwarp();
-      const float* sf = reinterpret_cast<const float*>(stage);
-      px = sf[lane * 3];
-      py = sf[lane * 3 + 1];
-      pz = sf[lane * 3 + 2];
-      __syncwarp();
-      return ci;
-    }
-  } else if (g < end) {
-    ci = find_cloud(b.clouds, b.n_clouds, g);
-  }
-  if (g < end) {
-    load_point(b.clouds[ci], g - b.clouds[ci].begin, px, py, pz);
-  } else {
-    px = py = pz = __int_as_float(0x7fc00000);
-  }
-  return ci;
 }
 
 // Add a lane's or warp's drift-compensation sums to the map's slot of this update.
@@ -98,8 +54,8 @@ __global__ void __launch_bounds__(kPointThreads) k_count(const BatchDev* __restr
   // per-update counters start at zero (the previous update is complete)
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     b.ctl->rec_total = 0;
-    b.ctl->n_big = 0;
-    b.ctl->big_next = 0;
+    b.ctl->n_heavy = 0;
+    b.ctl->fuse_next = 0;
     for (int mi = 0; mi < b.n_maps; ++mi) {
       const MapDev& m = b.maps[mi];
       atomicAdd(&m.ctl->stats[kStUpdates], 1ull);
@@ -134,10 +90,10 @@ __global__ void __launch_bounds__(kPointThreads) k_count(const BatchDev* __restr
         b.tr_status[g] = !pg.finite ? kPtNonFinite : !pg.in_range ? kPtRange : !inm ? kPtOutside : kPtFused;
       }
     }
-    const unsigned long long tag = inm ? ((unsigned long long)(uint32_t)c.map << 32) | (uint32_t)key : ~0ull;
-    int head, run;
-    key_runs(tag, head, run);
-    if (inm && lane == head) atomicAdd(&m.cnt[key], run);
+    // one count per tile and warp: the lanes whose points share a tile add together
+    const uint32_t tile = inm ? (uint32_t)((m.cell_begin + key) / kTile) : 0xffffffffu;
+    const unsigned grp = __match_any_sync(kFull, tile);
+    if (inm && lane == __ffs(grp) - 1) atomicAdd(&b.tile_cnt[tile], __popc(grp));
   }
   flush_counters(b, mc, idx, 2);
   // ray thresholds of the pre-update map over the cell space (Eq. 3)
@@ -310,76 +266,50 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* warp_tot, int& t
   return res;
 }
 
-// One tile of kTile cells per block iteration, 4 consecutive cells per thread.
-constexpr int kAllocPer = kTile / kCellThreads;
+// One block: the record ranges of all tiles, in tile order, by a running block
+// scan of their counts; the counts and the claim cursors go back to zero for
+// the next update, and the tiles with more than heavy_thresh records are listed
+// (the fusion takes them first).
+constexpr int kAllocThreads = 1024;
 
-__global__ void __launch_bounds__(kCellThreads) k_alloc(const BatchDev* __restrict__ bp) {
+__global__ void __launch_bounds__(kAllocThreads) k_alloc(const BatchDev* __restrict__ bp) {
   __shared__ int warp_tot[33];
-  __shared__ int s_base[2];
+  __shared__ int s_heavy;
   const BatchDev& b = *bp;
   const int64_t n_tiles = b.n_cells / kTile;
-  for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-    const int64_t g0 = t * kTile;
-    const int mi = find_map_cell(b.maps, b.n_maps, g0);
-    const MapDev& m = b.maps[mi];
-    const int32_t ncell = m.W * m.H;
-    const int64_t p0 = g0 - m.cell_begin;
-    if (p0 >= ncell) continue;  // padding (block-uniform)
-    int c[kAllocPer];
-    int sum = 0, nb = 0;
-    const int32_t first = (int32_t)p0 + threadIdx.x * kAllocPer;
-    if (first + kAllocPer <= ncell) {
-      const int4 v = *reinterpret_cast<const int4*>(m.cnt + first);
-      c[0] = v.x; c[1] = v.y; c[2] = v.z; c[3] = v.w;
-    } else {
-#pragma unroll
-      for (int k = 0; k < kAllocPer; ++k) c[k] = (first + k < ncell) ? m.cnt[first + k] : 0;
+  int base = 0;
+  if (threadIdx.x == 0) s_heavy = 0;
+  for (int64_t t0 = 0; t0 < n_tiles; t0 += kAllocThreads) {
+    const int64_t t = t0 + threadIdx.x;
+    const int c = t < n_tiles ? b.tile_cnt[t] : 0;
+    int tot;
+    const int off = block_exclusive_scan(c, warp_tot, tot);
+    if (t < n_tiles) {
+      b.tile_base[t] = base + off;
+      b.tile_cnt[t] = 0;
+      b.tile_cur[t] = 0;
+      if (c > b.heavy_thresh) b.heavy[atomicAdd(&s_heavy, 1)] = (int32_t)t;
     }
-#pragma unroll
-    for (int k = 0; k < kAllocPer; ++k) {
-      sum += c[k];
-      nb += c[k] > b.big_thresh;
-    }
-    int tot_c, tot_b;
-    const int off_c = block_exclusive_scan(sum, warp_tot, tot_c);
-    const int off_b = block_exclusive_scan(nb, warp_tot, tot_b);
-    if (threadIdx.x == 0) {
-      s_base[0] = tot_c ? atomicAdd(&b.ctl->rec_total, tot_c) : 0;
-      s_base[1] = tot_b ? atomicAdd(&b.ctl->n_big, tot_b) : 0;
-    }
-    __syncthreads();
-    int32_t rec = s_base[0] + off_c;
-    int32_t bs = s_base[1] + off_b;
-    int2 seg[kAllocPer];
-#pragma unroll
-    for (int k = 0; k < kAllocPer; ++k) {
-      seg[k] = make_int2(rec, c[k]);
-      rec += c[k];
-      if (c[k] > b.big_thresh) {
-        if (bs < b.big_cap) b.big_list[bs] = make_int2(mi, first + k); else atomicExch(&b.ctl->overflow, 1);
-        ++bs;
-      }
-    }
-    if (first + kAllocPer <= ncell) {  // two 16-byte stores of the (base, count) pairs
-      int4* dst = reinterpret_cast<int4*>(m.cell_seg + first);
-      dst[0] = make_int4(seg[0].x, seg[0].y, seg[1].x, seg[1].y);
-      dst[1] = make_int4(seg[2].x, seg[2].y, seg[3].x, seg[3].y);
-    } else {
-      for (int k = 0; k < kAllocPer && first + k < ncell; ++k) m.cell_seg[first + k] = seg[k];
-    }
-    __syncthreads();
+    base += tot;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    b.tile_base[n_tiles] = base;
+    b.ctl->rec_total = base;
+    b.ctl->n_heavy = s_heavy;
   }
 }
 
 // Warps take the point space in waves (warp w: points (w + k W) 32 .. + 31, W
-// the warps of the grid), so at any moment the grid writes the records of one
-// stretch of points -- one or two maps -- and their sectors fill up in L2
-// before they are written back.
+// the warps of the grid).  Each point claims a slot in its tile's range (one
+// claim per tile and warp) and writes its record there; a tile's range fills
+// in order, so its open sectors stay in L2 until they are full.
 template <bool kExt>
 __global__ void __launch_bounds__(kPointThreads, 6) k_scatter(const BatchDev* __restrict__ bp) {
   __shared__ float4 stage[kPointThreads / 32][24];
   const BatchDev& b = *bp;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned below = (1u << lane) - 1u;
   const int64_t end = b.n_points;
   for (int64_t wbase = ((int64_t)blockIdx.x * (kPointThreads / 32) + warp) * 32; wbase < end;
        wbase += (int64_t)gridDim.x * kPointThreads) {
@@ -391,26 +321,25 @@ __global__ void __launch_bounds__(kPointThreads, 6) k_scatter(const BatchDev* __
     const MapDev& m = b.maps[c.map];
     const PointGeom pg = point_geom<kExt>(m, c, px, py, pz);
     const bool inm = live && pg.in_range && in_map(m, pg.ix, pg.iy);
-    const int32_t key = inm ? phys_index(m, pg.ix, pg.iy) : -1;
-    const unsigned long long tag = inm ? ((unsigned long long)(uint32_t)c.map << 32) | (uint32_t)key : ~0ull;
-    int head, run;
-    key_runs(tag, head, run);
-    // the segment is read before the slot claim so both loads are in flight together
-    const int2 seg = inm ? __ldg(m.cell_seg + key) : make_int2(0, 0);
+    const int64_t cell = inm ? m.cell_begin + phys_index(m, pg.ix, pg.iy) : -1;
+    const uint32_t tile = inm ? (uint32_t)(cell / kTile) : 0xffffffffu;
+    const unsigned grp = __match_any_sync(kFull, tile);
+    const int leader = __ffs(grp) - 1;
+    // the range is read before the claim so both loads are in flight together
+    const int32_t lo = inm ? __ldg(b.tile_base + tile) : 0, hi = inm ? __ldg(b.tile_base + tile + 1) : 0;
     int old = 0;
-    if (inm && lane == head) old = atomicSub(&m.cnt[key], run);
-    old = __shfl_sync(kFull, old, head);
+    if (inm && lane == leader) old = atomicAdd(&b.tile_cur[tile], __popc(grp));
+    old = __shfl_sync(kFull, old, leader);
     if (inm) {
-      const int rank = lane - head;
-      const int64_t pos = (int64_t)seg.x + old - 1 - rank;
-      // the count pass found the same cell for this point, so pos lies in the
-      // cell's segment; anything else is recorded instead of written
-      if (pos < seg.x || pos >= (int64_t)seg.x + seg.y || pos >= b.n_points || old - rank <= 0) {
+      const int64_t pos = (int64_t)lo + old + __popc(grp & below);
+      // the count pass found the same tile for this point, so pos lies in the
+      // tile's range; anything else is recorded instead of written
+      if (pos >= hi || pos >= b.n_points) {
         atomicCAS(&m.ctl->err, 0, kErrInternal);
       } else {
-        const uint32_t w = (uint32_t)c.map | (seg.y > b.big_thresh ? kRecBig : 0u) |
-                           (m.wall > 0 && seg.y > m.wall ? kRecWall : 0u);
-        b.rec[pos] = make_float4(pg.z, point_variance(m, pg.d), __int_as_float(key), __uint_as_float(w));
+        b.rz[pos] = pg.z;
+        b.rv[pos] = point_variance(m, pg.d);
+        b.rc[pos] = (uint16_t)(cell % kTile);
         if (b.idx_sorted) b.idx_sorted[pos] = (int32_t)g;
       }
     }
@@ -462,7 +391,8 @@ cudaError_t launch_drift(const BatchDev* b, int64_t n_points, int64_t n_cells, b
 }
 
 cudaError_t launch_alloc(const BatchDev* b, int64_t n_cells, cudaStream_t s) {
-  k_alloc<<<tile_grid(n_cells), kCellThreads, 0, s>>>(b);
+  (void)n_cells;
+  k_alloc<<<1, kAllocThreads, 0, s>>>(b);
   return cudaGetLastError();
 }
 

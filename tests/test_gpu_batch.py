@@ -150,3 +150,46 @@ def test_launch_shapes_give_identical_maps(em, graph):
         for a, b in zip(results[0][1], stats):
             for k in ("points_accepted", "points_rejected", "cells_updated", "cells_cleared", "ray_samples"):
                 assert a[k] == b[k], k
+
+
+def test_batched_config_sizes_vs_oracle(em):
+    """One graph-launched batch over 8 maps drawn from the 64-map configuration
+    (sides 100 to 500 cells, 10k to 400k points in random order, the ray march
+    on, one map with normals, smoothing and in-painting), each over a seeded
+    prior: every map agrees with the FP64 oracle fed the same prior and cloud
+    (cell state, removed cells and filters; Section II-C, II-E)."""
+    import oracle
+    base = dict(BASE, var_min=1e-8, ray_step=0.04)
+    rng = np.random.default_rng(61)
+    specs = [(500, 400000, 0), (100, 10000, 0), (317, 150000, 1 | 2 | 4), (230, 400000, 0), (480, 60000, 0),
+             (150, 250000, 0), (400, 320000, 0), (260, 90000, 0)]
+    maps, pairs, oms, priors, clouds = [], [], [], [], []
+    for j, (side, n, flags) in enumerate(specs):
+        P = dict(base, width=side, height=side, flags=flags)
+        prior = synth.random_prior(seed=600 + j, width=side, height=side, t_now=5)
+        half = 0.5 * side * 0.04 * 1.05
+        pts, pose = synth.scattered_cloud(6000 + j, n, half, yaw=float(rng.uniform(0, 6.28)))
+        m = em.Map(em.Params(**P))
+        parity.prior_to_gpu(m, prior)
+        om = oracle.OracleMap(parity.oracle_params(P))
+        parity.prior_to_oracle(om, prior)
+        maps.append(m)
+        oms.append(om)
+        priors.append(prior)
+        clouds.append((pts, pose))
+        pairs.append((m, dev(pts), pose))
+    batch = em.Batch(max_maps=8, max_clouds=8, max_points=sum(len(p) for p, _ in clouds), max_cells=500 * 500,
+                     graph=True)
+    batch.update(pairs)
+    torch.cuda.synchronize()
+    for j, (m, om) in enumerate(zip(maps, oms)):
+        prior_valid = np.isfinite(om.state()["var"])
+        tr = om.update(clouds[j], trace=True, unit=oracle.FP32_UNIT, abs_band=parity.ABS_BAND)
+        stencils = ("nx", "ny", "nz", "smooth", "inpaint") if specs[j][2] else ()
+        cmp = parity.compare_update(tr, om.state(), m.state(), None, prior_valid=prior_valid, check_stencils=stencils)
+        assert cmp.notes["cells_compared"] > 0.9 * cmp.notes["cells_valid"], j
+        st = m.stats()
+        assert abs(st["points_rejected"] - tr.counts["rejected"]) <= 0.001 * tr.counts["in_map"] + 10, j
+    for m in maps:
+        m.close()
+    batch.close()

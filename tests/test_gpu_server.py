@@ -260,3 +260,42 @@ def test_host_clouds_equal_device_clouds(em, mode):
     for j in range(len(SIDES)):
         for k in ("h", "var", "t_last"):
             assert np.array_equal(states[0][j][k], states[1][j][k], equal_nan=True), (j, k)
+
+
+def test_served_mix_vs_oracle(em):
+    """A mix of depth-camera and LiDAR requests (one per map, maps of 200 to 500
+    cells over seeded priors) served in batches on three streams: every map
+    agrees with the FP64 oracle fed the same prior and cloud (Section II-C,
+    II-E), within the parity tolerances."""
+    import oracle
+    from tests import parity
+    depth_p = dict(resolution=0.04, noise_a0=0.005, noise_a2=0.002, var_min=1e-8, min_range=0.05, max_range=10.0,
+                   mahalanobis_k=2.5, outlier_variance=1e-4, ray_step=0.04)
+    lidar_p = dict(resolution=0.04, noise_a0=0.01, noise_a2=0.001, var_min=1e-8, min_range=0.3, max_range=40.0,
+                   mahalanobis_k=2.5, outlier_variance=1e-4, ray_step=0.04)
+    depth = [c for fr in synth.depth_stream(seed=8, frames=2) for c in fr["clouds"]][:6]
+    lidar = [fr["clouds"][0] for fr in synth.lidar_stream(seed=9, frames=2)]
+    reqs = [(dict(depth_p, width=200 + 40 * i, height=200 + 40 * i), c) for i, c in enumerate(depth)]
+    reqs += [(dict(lidar_p, width=500, height=500), c) for c in lidar]
+    srv = em.Server(budget_bytes=4 << 30, n_streams=3, max_batch_maps=3, max_batch_points=2_000_000)
+    ids, oms = [], []
+    for j, (P, _) in enumerate(reqs):
+        prior = synth.random_prior(seed=700 + j, width=P["width"], height=P["height"], t_now=5)
+        mid = srv.add_map(em.Params(**P))
+        parity.prior_to_gpu(srv.map(mid), prior)
+        om = oracle.OracleMap(parity.oracle_params(P))
+        parity.prior_to_oracle(om, prior)
+        ids.append(mid)
+        oms.append(om)
+    torch.cuda.synchronize()
+    tickets = srv.submit_many([(ids[j], [(dev(p), q)], None) for j, (_, (p, q)) in enumerate(reqs)])
+    assert all(s == 0 for s in srv.wait_many(tickets))
+    assert srv.stats()["batches"] < len(reqs)  # requests shared batches
+    for j, (_, cloud) in enumerate(reqs):
+        om = oms[j]
+        prior_valid = np.isfinite(om.state()["var"])
+        tr = om.update(cloud, trace=True, unit=oracle.FP32_UNIT, abs_band=parity.ABS_BAND)
+        cmp = parity.compare_update(tr, om.state(), srv.map(ids[j]).state(), None, prior_valid=prior_valid,
+                                    check_stencils=())
+        assert cmp.notes["cells_compared"] > 0.9 * cmp.notes["cells_valid"], j
+    srv.close()
