@@ -73,7 +73,14 @@ struct em_map {
   int32_t* tile_cnt = nullptr;   // per tile of 1024 cells: record counts, ranges, claims
   int32_t* tile_base = nullptr;
   int32_t* tile_cur = nullptr;
-  int32_t* heavy = nullptr;
+  int32_t* tile_map = nullptr;
+  FuseItem* heavy = nullptr;                // the fusion's work lists (one entry per tile)
+  FuseItem* light = nullptr;
+  unsigned long long* split_acc = nullptr;  // accumulator slots of split tiles (zero between updates)
+  int32_t* split_done = nullptr;
+  int32_t split_slots = 0;
+  FuseItem* pieces = nullptr;               // piece list (with the record workspace)
+  int32_t max_pieces = 0;
   MapCtl* ctl = nullptr;
   BatchCtl* bctl = nullptr;
   // geometry
@@ -104,6 +111,8 @@ struct em_map {
   float* layer_stage = nullptr;
   size_t layer_stage_cap = 0;
   cudaStream_t last_stream = nullptr;
+  cudaStream_t side = nullptr;  // the ray march, beside the sort and fusion (maps with a ray step)
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   int64_t layer_bytes = 0;
   int64_t work_bytes = 0;
   int fuse_threads = 256;
@@ -180,9 +189,11 @@ bool params_ok(const em_params* p) {
 
 void free_workspace(em_map* m) {
   cudaFree(m->rz); cudaFree(m->rv); cudaFree(m->rc); cudaFree(m->idx_sorted);
-  cudaFree(m->tr_ix); cudaFree(m->tr_iy); cudaFree(m->tr_status);
+  cudaFree(m->tr_ix); cudaFree(m->tr_iy); cudaFree(m->tr_status); cudaFree(m->pieces);
   m->rz = m->rv = nullptr; m->rc = nullptr; m->idx_sorted = nullptr; m->tr_ix = m->tr_iy = nullptr;
   m->tr_status = nullptr;
+  m->pieces = nullptr;
+  m->max_pieces = 0;
   m->cap = 0;
   m->work_bytes = 0;
 }
@@ -200,6 +211,10 @@ int grow_workspace(em_map* m, int64_t n) {
   EM_TRY(dev_alloc(&m->rz, (size_t)want, &tot), "alloc workspace");
   EM_TRY(dev_alloc(&m->rv, (size_t)want, &tot), "alloc workspace");
   EM_TRY(dev_alloc(&m->rc, (size_t)want, &tot), "alloc workspace");
+  // pieces: a split tile has more than 16 kMinHeavy records per piece but its last
+  const int64_t np = want / (kMinHeavy * 16) + kMaxSplit + 1;
+  EM_TRY(dev_alloc(&m->pieces, (size_t)np, &tot), "alloc workspace");
+  m->max_pieces = (int32_t)np;
   if (trace) {
     EM_TRY(dev_alloc(&m->idx_sorted, (size_t)want, &tot), "alloc trace");
     EM_TRY(dev_alloc(&m->tr_ix, (size_t)want, &tot), "alloc trace");
@@ -218,8 +233,13 @@ void release(em_map* m) {
   cudaFree(m->h); cudaFree(m->var); cudaFree(m->t_last);
   cudaFree(m->nx); cudaFree(m->ny); cudaFree(m->nz); cudaFree(m->smooth); cudaFree(m->inpaint); cudaFree(m->upper);
   cudaFree(m->mark); cudaFree(m->thr);
-  cudaFree(m->tile_cnt); cudaFree(m->tile_base); cudaFree(m->tile_cur); cudaFree(m->heavy);
+  cudaFree(m->tile_cnt); cudaFree(m->tile_base); cudaFree(m->tile_cur); cudaFree(m->tile_map);
+  cudaFree(m->heavy); cudaFree(m->light);
+  cudaFree(m->split_acc); cudaFree(m->split_done);
   cudaFree(m->ctl); cudaFree(m->bctl);
+  if (m->side) cudaStreamDestroy(m->side);
+  if (m->fork_ev) cudaEventDestroy(m->fork_ev);
+  if (m->join_ev) cudaEventDestroy(m->join_ev);
   free_workspace(m);
   cudaFree(m->desc_dev);
   cudaFreeHost(m->desc_host);
@@ -288,7 +308,14 @@ int upload_desc(em_map* m, const em_cloud* clouds, int32_t n_clouds, int64_t tot
   b->tile_cnt = m->tile_cnt;
   b->tile_base = m->tile_base;
   b->tile_cur = m->tile_cur;
+  b->tile_map = m->tile_map;
   b->heavy = m->heavy;
+  b->light = m->light;
+  b->pieces = m->pieces;
+  b->max_pieces = m->max_pieces;
+  b->split_acc = m->split_acc;
+  b->split_done = m->split_done;
+  b->split_slots = m->split_slots;
   b->heavy_thresh = m->heavy_thresh;
   b->fuse_threads = m->fuse_threads;
   const size_t bytes = sizeof(BatchDev) + sizeof(MapDev) + (size_t)n_clouds * sizeof(CloudDev);
@@ -439,16 +466,26 @@ int em_create(const em_params* params, int device, em_map** out) {
   const size_t ntile = (size_t)(pad_tile((int64_t)nc) / kTile);
   EM_ALLOC(m->mark, (nc + 31) / 32) EM_ALLOC(m->thr, nc)
   EM_ALLOC(m->tile_cnt, ntile + 1) EM_ALLOC(m->tile_base, ntile + 1) EM_ALLOC(m->tile_cur, ntile + 1)
-  EM_ALLOC(m->heavy, ntile)
+  EM_ALLOC(m->tile_map, ntile) EM_ALLOC(m->heavy, ntile) EM_ALLOC(m->light, ntile)
+  m->split_slots = (int32_t)(ntile < (size_t)kMaxSplit ? ntile : (size_t)kMaxSplit);
+  EM_ALLOC(m->split_acc, (size_t)m->split_slots * kSplitWords * kTile) EM_ALLOC(m->split_done, m->split_slots)
   EM_ALLOC(m->ctl, 1) EM_ALLOC(m->bctl, 1)
   EM_ALLOC(m->desc_dev, kDescBytes * kSlots)
 #undef EM_ALLOC
   if (e == cudaSuccess) e = cudaMallocHost((void**)&m->desc_host, kDescBytes * kSlots);
   for (int i = 0; i < kSlots && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&m->desc_ev[i], cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->stage_ev, cudaEventDisableTiming);
+  if (e == cudaSuccess && params->ray_step > 0.f) {
+    e = cudaStreamCreateWithFlags(&m->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->fork_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->join_ev, cudaEventDisableTiming);
+  }
   if (e == cudaSuccess) e = cudaMemset(m->ctl, 0, sizeof(MapCtl));
   if (e == cudaSuccess) e = cudaMemset(m->tile_cnt, 0, (ntile + 1) * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMemset(m->bctl, 0, sizeof(BatchCtl));
+  if (e == cudaSuccess)
+    e = cudaMemset(m->split_acc, 0, (size_t)m->split_slots * kSplitWords * kTile * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(m->split_done, 0, (size_t)m->split_slots * sizeof(int32_t));
   if (e == cudaSuccess) e = cuda_status(launch_fill_map(make_mapdev(m), nullptr), "fill") ? cudaErrorUnknown : cudaSuccess;
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
@@ -511,10 +548,24 @@ static int update_impl(em_map* m, const em_cloud* clouds, int32_t n_clouds, cuda
   if (m->p.drift_flatness > 0.f)
     EM_TRY(timed(m, EM_PROF_DRIFT, s, [&] { return launch_drift(bd, total, ncell, ext, s); }), "k_drift");
   if (total > 0) {
-    if (m->p.ray_step > 0.f) EM_TRY(timed(m, EM_PROF_RAY, s, [&] { return launch_ray(bd, total, m->ray_group, ext, s); }), "k_ray");
-    EM_TRY(timed(m, EM_PROF_ALLOC, s, [&] { return launch_alloc(bd, ncell, s); }), "k_alloc");
-    EM_TRY(timed(m, EM_PROF_SCATTER, s, [&] { return launch_scatter(bd, total, ext, s); }), "k_scatter");
-    EM_TRY(timed(m, EM_PROF_FUSE, s, [&] { return launch_fuse(bd, ncell, m->fuse_threads, s); }), "k_fuse");
+    // the ray march reads only the ray thresholds and the points and writes only
+    // the marks (read by k_clear): it runs on the side stream beside the sort and
+    // the fusion, unless the map has the upper-bound layer (both write it)
+    auto ray = [&](cudaStream_t rs) {
+      return timed(m, EM_PROF_RAY, rs, [&] { return launch_ray(bd, total, m->ray_group, ext, rs); });
+    };
+    auto rest = [&] {
+      cudaError_t r = timed(m, EM_PROF_ALLOC, s, [&] { return launch_alloc(bd, ncell, s); });
+      if (r == cudaSuccess) r = timed(m, EM_PROF_SCATTER, s, [&] { return launch_scatter(bd, total, ext, s); });
+      if (r == cudaSuccess) r = timed(m, EM_PROF_FUSE, s, [&] { return launch_fuse(bd, ncell, m->fuse_threads, s); });
+      return r;
+    };
+    if (m->p.ray_step > 0.f && !(m->p.flags & EM_F_UPPER)) {
+      EM_TRY(launch_beside(s, m->side, m->fork_ev, m->join_ev, ray, rest), "k_ray / k_alloc / k_scatter / k_fuse");
+    } else {
+      if (m->p.ray_step > 0.f) EM_TRY(ray(s), "k_ray");
+      EM_TRY(rest(), "k_alloc / k_scatter / k_fuse");
+    }
   }
   EM_TRY(timed(m, EM_PROF_CLEAR, s, [&] { return launch_clear(bd, ncell, s); }), "k_clear");
   if (m->p.overlap_dz > 0.f && n_clouds > 0)

@@ -42,11 +42,13 @@ struct GraphKey {
   bool ray;
   bool drift;
   bool overlap;
-  bool ext;  // some map uses the exclusion area or the upper-bound layer
+  bool ext;    // some map uses the exclusion area or the upper-bound layer
+  bool upper;  // some map has the upper-bound layer (the ray march then runs before the fusion)
   uint32_t stencils;
   bool operator==(const GraphKey& o) const {
     return t.ray_group == o.t.ray_group && t.fuse_chunk == o.t.fuse_chunk && t.big_thresh == o.t.big_thresh &&
-           ray == o.ray && drift == o.drift && overlap == o.overlap && ext == o.ext && stencils == o.stencils;
+           ray == o.ray && drift == o.drift && overlap == o.overlap && ext == o.ext && upper == o.upper &&
+           stencils == o.stencils;
   }
 };
 
@@ -65,7 +67,14 @@ struct em_batch {
   int32_t* tile_cnt = nullptr;
   int32_t* tile_base = nullptr;
   int32_t* tile_cur = nullptr;
-  int32_t* heavy = nullptr;
+  int32_t* tile_map = nullptr;
+  FuseItem* heavy = nullptr;  // the fusion's work lists (one entry per tile)
+  FuseItem* light = nullptr;
+  unsigned long long* split_acc = nullptr;  // accumulator slots of split tiles (zero between updates)
+  int32_t* split_done = nullptr;
+  int32_t split_slots = 0;
+  FuseItem* pieces = nullptr;
+  int32_t max_pieces = 0;
   size_t desc_bytes = 0;
   unsigned char* desc_host = nullptr;
   unsigned char* desc_dev = nullptr;
@@ -73,6 +82,8 @@ struct em_batch {
   int slot = 0;
   em_tuning tune{4, 256, 256};
   cudaStream_t capture_stream = nullptr;
+  cudaStream_t side = nullptr;  // the ray march, beside the sort and fusion
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   cudaGraphExec_t graph[kSlots] = {};
   GraphKey graph_key[kSlots] = {};
   // host scratch for grouping
@@ -116,19 +127,34 @@ int prof_collect(em_batch* b) {
   return EM_OK;
 }
 
-// The kernel sequence of one update over the descriptor at `bd`.
-cudaError_t launch_sequence(const BatchDev* bd, int64_t grid_points, int64_t grid_cells, const GraphKey& k,
-                            cudaStream_t s, em_batch* prof = nullptr) {
+// The kernel sequence of one update over the descriptor at `bd`.  The ray
+// march reads only the ray thresholds (k_count / k_drift) and the points, and
+// writes only the visibility marks (read by k_clear), so it runs on the side
+// stream beside the sort and the fusion -- unless a map has the upper-bound
+// layer, which both the march and the fusion write.
+cudaError_t launch_sequence(em_batch* b, const BatchDev* bd, int64_t grid_points, int64_t grid_cells,
+                            const GraphKey& k, cudaStream_t s, em_batch* prof = nullptr) {
   cudaError_t e = cudaSuccess;
   e = timed(prof, EM_PROF_COUNT, s, [&] { return launch_bin(bd, grid_points, grid_cells, k.ext, s); });
   if (e == cudaSuccess && k.drift) e = timed(prof, EM_PROF_DRIFT, s, [&] { return launch_drift(bd, grid_points, grid_cells, k.ext, s); });
   if (grid_points > 0) {
-    if (e == cudaSuccess && k.ray)
-      e = timed(prof, EM_PROF_RAY, s, [&] { return launch_ray(bd, grid_points, k.t.ray_group, k.ext, s); });
-    if (e == cudaSuccess) e = timed(prof, EM_PROF_ALLOC, s, [&] { return launch_alloc(bd, grid_cells, s); });
-    if (e == cudaSuccess) e = timed(prof, EM_PROF_SCATTER, s, [&] { return launch_scatter(bd, grid_points, k.ext, s); });
-    if (e == cudaSuccess)
-      e = timed(prof, EM_PROF_FUSE, s, [&] { return launch_fuse(bd, grid_cells, k.t.fuse_chunk, s); });
+    auto ray = [&](cudaStream_t rs) {
+      return timed(prof, EM_PROF_RAY, rs, [&] { return launch_ray(bd, grid_points, k.t.ray_group, k.ext, rs); });
+    };
+    auto rest = [&] {
+      cudaError_t r = timed(prof, EM_PROF_ALLOC, s, [&] { return launch_alloc(bd, grid_cells, s); });
+      if (r == cudaSuccess) r = timed(prof, EM_PROF_SCATTER, s, [&] { return launch_scatter(bd, grid_points, k.ext, s); });
+      if (r == cudaSuccess) r = timed(prof, EM_PROF_FUSE, s, [&] { return launch_fuse(bd, grid_cells, k.t.fuse_chunk, s); });
+      return r;
+    };
+    if (e == cudaSuccess) {
+      if (k.ray && !k.upper) {
+        e = launch_beside(s, b->side, b->fork_ev, b->join_ev, ray, rest);
+      } else {
+        if (k.ray) e = ray(s);
+        if (e == cudaSuccess) e = rest();
+      }
+    }
   }
   if (e == cudaSuccess) e = timed(prof, EM_PROF_CLEAR, s, [&] { return launch_clear(bd, grid_cells, s); });
   if (e == cudaSuccess && k.overlap)
@@ -194,7 +220,7 @@ int prepare(em_batch* b, em_map* const* maps, const em_cloud* clouds, int32_t co
   MapDev* md = reinterpret_cast<MapDev*>(hb + sizeof(BatchDev));
   CloudDev* cd = reinterpret_cast<CloudDev*>(hb + sizeof(BatchDev) + (size_t)b->max_maps * sizeof(MapDev));
   memset(bd, 0, sizeof(BatchDev));
-  GraphKey key{tune, false, false, false, false, 0u};
+  GraphKey key{tune, false, false, false, false, false, 0u};
   int64_t cells = 0;
   for (int u = 0; u < nm; ++u) {
     md[u] = map_begin_update(b->uniq[u], map_pts[u]);
@@ -204,6 +230,7 @@ int prepare(em_batch* b, em_map* const* maps, const em_cloud* clouds, int32_t co
     key.drift |= md[u].drift_flat > 0.f;
     key.overlap |= md[u].ovl_dz > 0.f;
     key.ext |= md[u].excl_d > 0.f || md[u].upper != nullptr;
+    key.upper |= md[u].upper != nullptr;
     key.stencils |= map_flags(b->uniq[u]) & (EM_F_NORMALS | EM_F_SMOOTH | EM_F_MEDIAN | EM_F_GAUSS | EM_F_INPAINT);
   }
   // clouds ordered by map (stable), so each map's points are contiguous
@@ -244,7 +271,14 @@ int prepare(em_batch* b, em_map* const* maps, const em_cloud* clouds, int32_t co
   bd->tile_cnt = b->tile_cnt;
   bd->tile_base = b->tile_base;
   bd->tile_cur = b->tile_cur;
+  bd->tile_map = b->tile_map;
   bd->heavy = b->heavy;
+  bd->light = b->light;
+  bd->pieces = b->pieces;
+  bd->max_pieces = b->max_pieces;
+  bd->split_acc = b->split_acc;
+  bd->split_done = b->split_done;
+  bd->split_slots = b->split_slots;
   bd->heavy_thresh = tune.big_thresh * 16;
   bd->fuse_threads = tune.fuse_chunk;
   // upload header + maps, and the clouds at their fixed offset
@@ -278,7 +312,7 @@ int run_graph(em_batch* b, const Prepared& p, cudaStream_t s) {
     }
     cudaGraph_t g = nullptr;
     EB_TRY(cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-    cudaError_t le = launch_sequence(p.bd, b->max_points, (int64_t)b->max_maps * pad_tile(b->max_cells), p.key,
+    cudaError_t le = launch_sequence(b, p.bd, b->max_points, (int64_t)b->max_maps * pad_tile(b->max_cells), p.key,
                                      b->capture_stream);
     cudaError_t ce = cudaStreamEndCapture(b->capture_stream, &g);
     if (le != cudaSuccess || ce != cudaSuccess) {
@@ -287,7 +321,7 @@ int run_graph(em_batch* b, const Prepared& p, cudaStream_t s) {
       // time, and the next update of this kind tries the capture again.
       if (g) cudaGraphDestroy(g);
       cudaGetLastError();
-      EB_TRY(launch_sequence(p.bd, p.points, p.cells, p.key, s), "launch (capture failed)");
+      EB_TRY(launch_sequence(b, p.bd, p.points, p.cells, p.key, s), "launch (capture failed)");
       return EM_OK;
     }
     cudaGraphExec_t ex = nullptr;
@@ -315,6 +349,9 @@ void release(em_batch* b) {
     if (b->ev[i]) cudaEventDestroy(b->ev[i]);
   }
   if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+  if (b->side) cudaStreamDestroy(b->side);
+  if (b->fork_ev) cudaEventDestroy(b->fork_ev);
+  if (b->join_ev) cudaEventDestroy(b->join_ev);
   cudaFree(b->rz);
   cudaFree(b->rv);
   cudaFree(b->rc);
@@ -322,7 +359,12 @@ void release(em_batch* b) {
   cudaFree(b->tile_cnt);
   cudaFree(b->tile_base);
   cudaFree(b->tile_cur);
+  cudaFree(b->tile_map);
   cudaFree(b->heavy);
+  cudaFree(b->light);
+  cudaFree(b->split_acc);
+  cudaFree(b->split_done);
+  cudaFree(b->pieces);
   cudaFree(b->desc_dev);
   cudaFreeHost(b->desc_host);
   delete b;
@@ -365,11 +407,26 @@ int em_batch_create(int device, int32_t max_maps, int32_t max_clouds, int64_t ma
   if (e == cudaSuccess) e = cudaMemset(b->tile_cnt, 0, nt * sizeof(int32_t));  // k_alloc keeps it zero after
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->tile_base, nt * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->tile_cur, nt * sizeof(int32_t));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&b->heavy, nt * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->tile_map, nt * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->heavy, nt * sizeof(FuseItem));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->light, nt * sizeof(FuseItem));
+  // split tiles: at most kMaxSplit slots of kSplitWords x kTile words; pieces of
+  // more than 16 kMinHeavy records but the last of each tile
+  b->split_slots = (int32_t)(b->max_tiles < kMaxSplit ? b->max_tiles : kMaxSplit);
+  b->max_pieces = (int32_t)(np / (kMinHeavy * 16) + kMaxSplit + 1);
+  const size_t acc_bytes = (size_t)b->split_slots * kSplitWords * kTile * sizeof(unsigned long long);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->split_acc, acc_bytes);
+  if (e == cudaSuccess) e = cudaMemset(b->split_acc, 0, acc_bytes);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->split_done, (size_t)b->split_slots * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMemset(b->split_done, 0, (size_t)b->split_slots * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->pieces, (size_t)b->max_pieces * sizeof(FuseItem));
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->desc_dev, b->desc_bytes * kSlots);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&b->desc_host, b->desc_bytes * kSlots);
   for (int i = 0; i < kSlots && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&b->ev[i], cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join_ev, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     release(b);
     return map_record_error("em_batch_create", e);
@@ -401,7 +458,7 @@ int em_update_batch(em_batch* b, em_map* const* maps, const em_cloud* clouds, in
   if ((b->flags & EM_BATCH_GRAPH) && !b->prof) {
     rc = run_graph(b, p, s);
   } else {
-    cudaError_t e = launch_sequence(p.bd, p.points, p.cells, p.key, s, b);
+    cudaError_t e = launch_sequence(b, p.bd, p.points, p.cells, p.key, s, b);
     rc = e == cudaSuccess ? EM_OK : map_record_error("batch launches", e);
   }
   finish(b, p, s);
@@ -491,7 +548,7 @@ int em_batch_autotune(em_batch* b, em_map* const* maps, const em_cloud* clouds, 
       int c = prepare(b, cmaps.data(), clouds, count, t, s, &p);
       if (c) return c;
       cudaEventRecord(e0, s);
-      cudaError_t le = launch_sequence(p.bd, p.points, p.cells, p.key, s);
+      cudaError_t le = launch_sequence(b, p.bd, p.points, p.cells, p.key, s);
       cudaEventRecord(e1, s);
       finish(b, p, s);
       if (le != cudaSuccess) return map_record_error("autotune launches", le);

@@ -18,17 +18,20 @@
 //              counts; per cell: ray thresholds of the pre-update map
 //                                                              (Section II-C)
 //   k_ray      visibility ray march against the pre-update map (Section II-E)
-//   k_alloc    one range of the record arrays per tile of 1024 cells
+//   k_alloc    one range of the record arrays per tile of 1024 cells; the
+//              fusion's work lists (dense tiles cut into pieces)
 //   k_scatter  records into their tile's range (counting sort by tile)
-//   k_fuse     per tile, one block: the tile's state in shared memory; per
-//              cell: wall rule, Mahalanobis gate, Eq. 1/2 in information form
-//              with exact integer accumulation (Section II-C)
+//   k_fuse     per work item, one block: the tile's state in shared memory;
+//              per cell: wall rule, Mahalanobis gate, Eq. 1/2 in information
+//              form with exact integer accumulation (Section II-C)
 //   k_clear    remove penetrated cells not written recently   (Section II-E)
 //   k_normals / k_smooth / k_inpaint                          (Section II-A, II-I)
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <vector>
 
 namespace em {
 
@@ -58,10 +61,30 @@ struct MapCtl {
 // per-batch device control block (reset by k_count and k_alloc)
 struct BatchCtl {
   int32_t rec_total;         // records of this update (all maps)
-  int32_t n_heavy;           // entries in the heavy-tile list
-  int32_t fuse_next;         // work counter of the fusion: heavy tiles first, then every tile
-  int32_t pad;
+  int32_t fuse_next;         // work counter of the fusion: pieces, heavy tiles, then light tiles
+  int32_t n_split;           // tiles split into pieces (one accumulator slot each)
+  int32_t n_pieces;          // entries of the three work lists of the fusion
+  int32_t n_heavy;
+  int32_t n_light;
+  int32_t pad[2];
 };
+
+// A tile with more than heavy_thresh records is split, while accumulator
+// slots last, into pieces of at most heavy_thresh records, fused by different
+// blocks: each adds its exact sums to the tile's slot (kSplitWords 64-bit words
+// per cell) and the last piece to finish writes the cells.
+constexpr int kMaxSplit = 512;       // accumulator slots at most
+constexpr int kSplitWords = 5;       // per cell: weight sum (high, low), term sum (high, low), counts
+
+// One work item of the fusion, written by k_alloc: a non-empty tile (whole) or
+// a piece of a split tile.  The tile's records are [r0, r1); the item fuses
+// [q0, q1) of them (the whole range unless it is a piece).
+struct FuseItem {
+  int32_t tile, map;                 // tile of the batch cell space, and the map it lies in
+  int32_t r0, r1, q0, q1;
+  int32_t slot, np;                  // accumulator slot and pieces of a split tile; -1 and 1 otherwise
+};
+static_assert(sizeof(FuseItem) == 32, "work items are read as two 16-byte words");
 
 // Records: one per in-map point, grouped by tile of kTile cells of the batch
 // cell space (a tile lies in one map: map cell ranges are padded to whole
@@ -133,11 +156,24 @@ struct BatchDev {
   BatchCtl* ctl;
   // per tile of the cell space (n_cells / kTile tiles): the records counted by
   // k_count (zero between updates), their first record (k_alloc; one more
-  // entry holds the total), and k_scatter's claims (zeroed by k_alloc)
+  // entry holds the total), k_scatter's claims (zeroed by k_alloc), and the
+  // map of every non-empty tile (k_count)
   int32_t* tile_cnt;
   int32_t* tile_base;
   int32_t* tile_cur;
-  int32_t* heavy;      // tiles with more than heavy_thresh records (fused first)
+  int32_t* tile_map;
+  // the fusion's work lists (k_alloc): pieces of split tiles (max_pieces
+  // entries), tiles with more than heavy_thresh records fused whole when the
+  // slots ran out, and the other non-empty tiles (one entry per tile each)
+  FuseItem* pieces;
+  FuseItem* heavy;
+  FuseItem* light;
+  // split tiles: per slot kSplitWords x kTile accumulator words and a count of
+  // finished pieces, both zero between updates
+  unsigned long long* split_acc;
+  int32_t* split_done;
+  int32_t split_slots; // 0: no tile is split
+  int32_t max_pieces;
   int32_t heavy_thresh;
   int32_t fuse_threads;  // threads per fusion block: 256 or 512
 };
@@ -149,6 +185,50 @@ inline bool word_aligned(const void* p) { return (reinterpret_cast<uintptr_t>(p)
 
 // number of SMs of the current device (cached)
 int sm_count();
+
+// Launch ray(stream) beside rest() (which launches on s) and join both before
+// the next launch on s.  Outside a graph capture the ray work goes to the side
+// stream between two events; while s is being captured it stays on s and the
+// capture's dependency set is edited instead (the ray node hangs off the
+// preceding node, rest() starts from that node too, and the next node depends
+// on both ends), so a capture never spans a second stream.
+template <class Ray, class Rest>
+cudaError_t launch_beside(cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join, Ray ray,
+                          Rest rest) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(s, &cs);
+  if (e != cudaSuccess) return e;
+  if (cs == cudaStreamCaptureStatusActive) {
+    const cudaGraphNode_t* dp = nullptr;
+    size_t nd = 0;
+    e = cudaStreamGetCaptureInfo(s, &cs, nullptr, nullptr, &dp, nullptr, &nd);
+    if (e != cudaSuccess) return e;
+    std::vector<cudaGraphNode_t> before(dp, dp + nd);
+    e = ray(s);
+    if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(s, &cs, nullptr, nullptr, &dp, nullptr, &nd);
+    if (e != cudaSuccess) return e;
+    std::vector<cudaGraphNode_t> after_ray(dp, dp + nd);
+    e = cudaStreamUpdateCaptureDependencies(s, before.data(), nullptr, before.size(), cudaStreamSetCaptureDependencies);
+    if (e == cudaSuccess) e = rest();
+    if (e == cudaSuccess)
+      e = cudaStreamUpdateCaptureDependencies(s, after_ray.data(), nullptr, after_ray.size(),
+                                              cudaStreamAddCaptureDependencies);
+    return e;
+  }
+  if (cs != cudaStreamCaptureStatusNone || !side) {  // an invalidated capture (or no side stream): in order
+    e = ray(s);
+    return e == cudaSuccess ? rest() : e;
+  }
+  e = cudaEventRecord(fork, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(side, fork, 0);
+  if (e != cudaSuccess) return e;
+  e = ray(side);
+  // the join is made whatever happened since the fork
+  cudaError_t je = cudaEventRecord(join, side);
+  if (e == cudaSuccess) e = rest();
+  if (je == cudaSuccess) je = cudaStreamWaitEvent(s, join, 0);
+  return e == cudaSuccess ? je : e;
+}
 
 // ---- launchers (each returns cudaGetLastError() of its launches)
 // ext: some map of the batch uses the exclusion area or the upper-bound layer

@@ -54,8 +54,10 @@ constexpr size_t kOffMark = kOffBCtl + up256(sizeof(BatchCtl));
 constexpr size_t kOffTCnt = kOffMark + up256(((size_t)kMaxCells + 31) / 32 * sizeof(uint32_t));
 constexpr size_t kOffTBase = kOffTCnt + up256((kMaxTiles + 1) * sizeof(int32_t));
 constexpr size_t kOffTCur = kOffTBase + up256((kMaxTiles + 1) * sizeof(int32_t));
-constexpr size_t kOffHeavy = kOffTCur + up256((kMaxTiles + 1) * sizeof(int32_t));
-constexpr size_t kOffThr = kOffHeavy + up256(kMaxTiles * sizeof(int32_t));
+constexpr size_t kOffTMap = kOffTCur + up256((kMaxTiles + 1) * sizeof(int32_t));
+constexpr size_t kOffHeavy = kOffTMap + up256(kMaxTiles * sizeof(int32_t));
+constexpr size_t kOffLight = kOffHeavy + up256(kMaxTiles * sizeof(FuseItem));
+constexpr size_t kOffThr = kOffLight + up256(kMaxTiles * sizeof(FuseItem));
 constexpr size_t kOffRz = kOffThr + up256((size_t)kMaxCells * sizeof(float));
 constexpr size_t kOffRv = kOffRz + up256((size_t)kMaxPoints * sizeof(float));
 constexpr size_t kOffRc = kOffRv + up256((size_t)kMaxPoints * sizeof(float));
@@ -208,10 +210,13 @@ extern "C" int em_update_noalloc(const em_params* params, int64_t shift_x, int64
   b->tile_cnt = reinterpret_cast<int32_t*>(base + kOffTCnt);
   b->tile_base = reinterpret_cast<int32_t*>(base + kOffTBase);
   b->tile_cur = reinterpret_cast<int32_t*>(base + kOffTCur);
-  b->heavy = reinterpret_cast<int32_t*>(base + kOffHeavy);
+  b->tile_map = reinterpret_cast<int32_t*>(base + kOffTMap);
+  b->heavy = reinterpret_cast<FuseItem*>(base + kOffHeavy);
+  b->light = reinterpret_cast<FuseItem*>(base + kOffLight);
   b->n_cells = pad_tile(ncell);
   b->ctl = reinterpret_cast<BatchCtl*>(base + kOffBCtl);
   b->heavy_thresh = 4096;
+  b->split_slots = 0;  // no tile is split: heavy tiles are fused whole
   b->fuse_threads = 256;
 
   const BatchDev* bd = reinterpret_cast<const BatchDev*>(base + kOffDesc + offsetof(Desc, b));

@@ -27,62 +27,28 @@
 // thread on one record (the next window's loads in flight), reduces each run
 // of equal cells in consecutive lanes with a segmented scan, and adds the
 // run's sums to the cell's accumulators in shared memory (64-bit integer
-// atomics).  Then every touched cell of the tile is written once.  Blocks take
-// tiles from a counter, the heavy tiles (many records) first.
+// atomics).  Then every touched cell of the tile is written once and its
+// accumulators go back to zero.
+//
+// A tile with many records (a dense depth image puts tens of thousands in one
+// tile) is cut into pieces that different blocks fuse at the same time: each
+// piece adds its runs' sums to the tile's accumulator slot in global memory
+// (64-bit integer atomics, exact like the rest) and counts itself done;
+// the block that finishes the tile's last piece reads the slot, writes the
+// cells and zeroes the slot for the next update.  No block waits for another.
+// Blocks take work from a counter: pieces first, then tiles listed heavy
+// (fused whole when the slots ran out), then every other tile.
 #include "em_point.cuh"
 
 namespace em {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-// The cell's snapshot and the decisions that do not depend on single points.
+// The cell's pre-update state as the cell update reads it.
 struct CellCtx {
-  float h, ve, href, k2;
-  bool valid, wall_on, gate_on;
+  float h, ve, href;
+  bool valid;
 };
-
-// The pre-update state of a cell, loaded ahead of its use.
-struct Snap {
-  float h, var;
-  int32_t t_last;
-};
-
-__device__ __forceinline__ Snap load_snap(const MapDev& m, int32_t cell) {
-  return Snap{m.h[cell], m.var[cell], m.t_last[cell]};
-}
-
-__device__ __forceinline__ CellCtx make_cell(const MapDev& m, const Snap& sn, bool wall_armed) {
-  CellCtx c;
-  c.h = sn.h;
-  c.valid = isfinite(sn.var);
-  c.ve = c.valid ? var_eff(m, sn.var, sn.t_last) : sn.var;
-  c.href = c.valid ? c.h : m.z_ref;
-  c.wall_on = wall_armed && c.valid;
-  c.gate_on = c.valid && m.k > 0.f;
-  c.k2 = __fmul_rn(m.k, m.k);
-  return c;
-}
-
-__device__ __forceinline__ CellCtx load_cell(const MapDev& m, int32_t cell, bool wall_armed) {
-  return make_cell(m, load_snap(m, cell), wall_armed);
-}
-
-// One record: wall rule, gate, and its two fixed-point terms when accepted
-// (zero terms otherwise).
-__device__ __forceinline__ uint8_t fuse_one(const CellCtx& c, float z, float vp, Fix& fw, Fix& ft) {
-  fw = Fix{0, 0u};
-  ft = Fix{0, 0u};
-  if (c.wall_on && z < c.h) return kPtWall;
-  if (c.gate_on) {
-    // |z - h| / sqrt(sigma_m^2 + sigma_p^2) > k  <=>  (z - h)^2 > k^2 (sigma_m^2 + sigma_p^2)  (k > 0)
-    const float dz = __fsub_rn(z, c.h);
-    if (__fmul_rn(dz, dz) > __fmul_rn(c.k2, __fadd_rn(c.ve, vp))) return kPtRejected;
-  }
-  const float w = __frcp_rn(vp);
-  fw = to_fix(w);
-  ft = to_fix(__fmul_rn(w, __fsub_rn(z, c.href)));
-  return kPtFused;
-}
 
 // New state of the cell from its complete sums (one thread); true when the
 // cell took a point (accepted or rejected).
@@ -120,9 +86,41 @@ struct TileSmem {
   unsigned long long n[kTile];               // accepted | rejected << 32
   float h[kTile], ve[kTile];                 // pre-update height, effective variance (+inf: empty)
   uint32_t cnt[kTile];                       // records per cell (the wall rule)
-  int work;
-  unsigned long long stat[4];                // accepted, rejected, wall, cells of the tile
+  FuseItem item;                             // this block's work (tile -1: none left)
+  int last;                                  // this block finished its tile's last piece
+  unsigned long long stat[4];                // accepted, rejected, wall, cells of the item
 };
+
+// A cell's new state from its complete sums (one thread; zero counts: untouched).
+__device__ __forceinline__ uint32_t write_from_sums(const MapDev& m, int32_t cell, float h, float ve, __int128 qw,
+                                                    __int128 qt, unsigned long long nn) {
+  CellCtx cx;
+  cx.h = h;
+  cx.ve = ve;
+  cx.valid = isfinite(ve);
+  cx.href = cx.valid ? h : m.z_ref;
+  return write_cell(m, cell, cx, qw, qt, (int)(uint32_t)nn, (int)(nn >> 32)) ? 1u : 0u;
+}
+
+// Work item w of the three lists (pieces, heavy tiles, light tiles), checked
+// against the sizes of the batch; tile -1 when w is past the end.  A failed
+// check records an internal error and also ends the block's work.
+__device__ __forceinline__ FuseItem fetch_item(const BatchDev& b, int w, int n_pieces, int n_heavy, int n_light,
+                                               int64_t n_tiles, int32_t rec_total) {
+  FuseItem it{-1, 0, 0, 0, 0, 0, -1, 1};
+  if (w >= 0 && w < n_pieces) it = b.pieces[w];
+  else if (w >= n_pieces && w - n_pieces < n_heavy) it = b.heavy[w - n_pieces];
+  else if (w >= n_pieces + n_heavy && w - n_pieces - n_heavy < n_light) it = b.light[w - n_pieces - n_heavy];
+  else if (w >= 0) return it;
+  const bool ok = it.tile >= 0 && it.tile < n_tiles && it.map >= 0 && it.map < b.n_maps && 0 <= it.r0 &&
+                  it.r0 <= it.q0 && it.q0 <= it.q1 && it.q1 <= it.r1 && it.r1 <= rec_total && it.np >= 1 &&
+                  it.slot >= -1 && it.slot < b.split_slots && w >= 0;
+  if (!ok) {
+    atomicCAS(&b.maps[0].ctl->err, 0, kErrInternal);
+    it.tile = -1;
+  }
+  return it;
+}
 
 template <int NT>
 __global__ void __launch_bounds__(NT) k_fuse(const BatchDev* __restrict__ bp) {
@@ -131,35 +129,45 @@ __global__ void __launch_bounds__(NT) k_fuse(const BatchDev* __restrict__ bp) {
   const BatchDev& b = *bp;
   const int lane = threadIdx.x & 31;
   const int64_t n_tiles = b.n_cells / kTile;
-  const int n_heavy = b.ctl->n_heavy;
+  const int n_pieces = b.ctl->n_pieces, n_heavy = b.ctl->n_heavy, n_light = b.ctl->n_light;
+  const int32_t rec_total = b.ctl->rec_total;
+  const int64_t n_items = (int64_t)n_pieces + n_heavy + n_light;
+  // the accumulators start at zero and the write-out leaves them at zero
+  for (int c = threadIdx.x; c < kTile; c += NT) {
+    S.wh[c] = 0;
+    S.th[c] = 0;
+    S.wl[c] = 0;
+    S.tl[c] = 0;
+    S.n[c] = 0;
+  }
+  if (threadIdx.x == 0)
+    S.item = fetch_item(b, atomicAdd(&b.ctl->fuse_next, 1), n_pieces, n_heavy, n_light, n_tiles, rec_total);
+  __syncthreads();
   // every block takes work items from the counter until they run out; a block
   // takes at most all of them (a bound that holds whatever the counter reads)
   for (int64_t items = 0;; ++items) {
-    if (threadIdx.x == 0) S.work = atomicAdd(&b.ctl->fuse_next, 1);
-    __syncthreads();
-    const int w = S.work;
-    if (items > n_tiles + n_heavy || w < 0 || n_heavy < 0 || n_heavy > n_tiles) {
+    const FuseItem it = S.item;
+    if (it.tile < 0) break;  // block-uniform
+    if (items >= n_items) {
       if (threadIdx.x == 0) atomicCAS(&b.maps[0].ctl->err, 0, kErrInternal);
       break;
     }
-    int64_t t;
-    if (w < n_heavy) {
-      t = b.heavy[w];
-    } else {
-      t = w - n_heavy;
-      if (t >= n_tiles) break;  // block-uniform
-    }
-    const int32_t r0 = b.tile_base[t], r1 = b.tile_base[t + 1];
-    if (r1 == r0 || (w >= n_heavy && r1 - r0 > b.heavy_thresh)) {  // nothing to fuse, or a heavy tile done first
-      __syncthreads();
-      continue;
-    }
-    const int mi = find_map_cell(b.maps, b.n_maps, t * kTile);
-    const MapDev& m = b.maps[mi];
+    // the next item's index now, its entry after this one (the atomic's latency hides behind the work)
+    int w_next = 0;
+    if (threadIdx.x == 0) w_next = atomicAdd(&b.ctl->fuse_next, 1);
+    const int64_t t = it.tile;
+    const bool split = it.slot >= 0;
+    const int32_t r0 = it.r0, r1 = it.r1, q0 = it.q0, q1 = it.q1;
+    const MapDev& m = b.maps[it.map];
     const int32_t p0 = (int32_t)(t * kTile - m.cell_begin);
     const int32_t ncell = min(kTile, m.W * m.H - p0);
     const bool wall_on = m.wall > 0;
-    // ---- the tile's pre-update state; accumulators to zero
+    // the first window of records, in flight while the tile's state is staged
+    int32_t r = q0 + threadIdx.x;
+    float z = 0.f, vp = 1.f;
+    uint32_t c = 0;
+    if (r < q1) { z = __ldg(b.rz + r); vp = __ldg(b.rv + r); c = __ldg(b.rc + r); }
+    // ---- the tile's pre-update state; record counts to zero
     for (int c = threadIdx.x; c < kTile; c += NT) {
       float h = 0.f, ve = __int_as_float(0x7f800000);
       if (c < ncell) {
@@ -170,32 +178,31 @@ __global__ void __launch_bounds__(NT) k_fuse(const BatchDev* __restrict__ bp) {
       }
       S.h[c] = h;
       S.ve[c] = ve;
-      S.wh[c] = 0;
-      S.th[c] = 0;
-      S.wl[c] = 0;
-      S.tl[c] = 0;
-      S.n[c] = 0;
       S.cnt[c] = 0;
     }
     if (threadIdx.x < 4) S.stat[threadIdx.x] = 0;
     __syncthreads();
-    if (wall_on) {  // records per cell first: the wall rule looks at the cell's count
-      for (int32_t r = r0 + threadIdx.x; r < r1; r += NT) atomicAdd(&S.cnt[__ldg(b.rc + r)], 1u);
+    // records per cell of the whole tile first: the wall rule looks at the
+    // cell's count (one atomic per cell and warp)
+    if (wall_on) {
+      for (int32_t cb = r0; cb < r1; cb += NT) {
+        const int32_t rr = cb + threadIdx.x;
+        const uint32_t key = rr < r1 ? (uint32_t)__ldg(b.rc + rr) : 0xffffffffu;
+        const unsigned grp = __match_any_sync(kFull, key);
+        if (rr < r1 && lane == __ffs(grp) - 1) atomicAdd(&S.cnt[key], (uint32_t)__popc(grp));
+      }
       __syncthreads();
     }
+    unsigned long long* const A = split ? b.split_acc + (size_t)it.slot * kSplitWords * kTile : nullptr;
     const float k2 = __fmul_rn(m.k, m.k);
-    uint32_t acc = 0, rej = 0, wal = 0;
+    uint32_t acc = 0, rej = 0, wal = 0, cells = 0;
     // ---- records, NT at a time; the next window's loads in flight
-    int32_t r = r0 + threadIdx.x;
-    float z = 0.f, vp = 1.f;
-    uint32_t c = 0;
-    if (r < r1) { z = __ldg(b.rz + r); vp = __ldg(b.rv + r); c = __ldg(b.rc + r); }
-    for (int32_t base = r0; base < r1; base += NT) {
-      const bool live = r < r1;
+    for (int32_t base = q0; base < q1; base += NT) {
+      const bool live = r < q1;
       const int32_t rn = r + NT;
       float zn = 0.f, vpn = 1.f;
       uint32_t cn = 0;
-      if (rn < r1) { zn = __ldg(b.rz + rn); vpn = __ldg(b.rv + rn); cn = __ldg(b.rc + rn); }
+      if (rn < q1) { zn = __ldg(b.rz + rn); vpn = __ldg(b.rv + rn); cn = __ldg(b.rc + rn); }
       Fix fw{0, 0u}, ft{0, 0u};
       uint8_t st = kPtFused;
       if (live) {
@@ -216,9 +223,11 @@ __global__ void __launch_bounds__(NT) k_fuse(const BatchDev* __restrict__ bp) {
         wal += st == kPtWall;
         if (b.tr_status) b.tr_status[b.idx_sorted[r]] = st;
       }
-      unsigned long long nn = !live ? 0ull : st == kPtFused ? 1ull : st == kPtRejected ? (1ull << 32) : 0ull;
       // runs of equal cells in consecutive lanes: a segmented inclusive scan, as
-      // many steps as the longest run needs; the run's last lane adds its sums
+      // many steps as the longest run needs; the run's last lane adds its sums.
+      // Within a run of at most 32 lanes the 27-bit low parts and the counts
+      // (accepted | rejected << 16) fit 32 bits.
+      uint32_t nn = !live ? 0u : st == kPtFused ? 1u : st == kPtRejected ? (1u << 16) : 0u;
       const unsigned long long tag = live ? (unsigned long long)c : ~0ull;
       int head, len;
       key_runs(tag, head, len);
@@ -227,11 +236,11 @@ __global__ void __launch_bounds__(NT) k_fuse(const BatchDev* __restrict__ bp) {
       const bool tail = lane == 31 || next != tag;
       const int maxrun = (int)__reduce_max_sync(kFull, live ? (unsigned)(lane - head + 1) : 1u);
       long long wh = fw.h, th = ft.h;
-      unsigned long long wl = fw.l, tl = ft.l;
+      uint32_t wl = fw.l, tl = ft.l;
       for (int o = 1; o < maxrun; o <<= 1) {
         const long long awh = __shfl_up_sync(kFull, wh, o), ath = __shfl_up_sync(kFull, th, o);
-        const unsigned long long awl = __shfl_up_sync(kFull, wl, o), atl = __shfl_up_sync(kFull, tl, o);
-        const unsigned long long an = __shfl_up_sync(kFull, nn, o);
+        const uint32_t awl = __shfl_up_sync(kFull, wl, o), atl = __shfl_up_sync(kFull, tl, o);
+        const uint32_t an = __shfl_up_sync(kFull, nn, o);
         if (lane - o >= head) {
           wh += awh;
           th += ath;
@@ -241,12 +250,24 @@ __global__ void __launch_bounds__(NT) k_fuse(const BatchDev* __restrict__ bp) {
         }
       }
       if (live && tail) {
-        if (nn) atomicAdd(&S.n[c], nn);
-        if (wh | (long long)wl) {
-          atomicAdd(reinterpret_cast<unsigned long long*>(&S.wh[c]), (unsigned long long)wh);
-          atomicAdd(&S.wl[c], wl);
-          atomicAdd(reinterpret_cast<unsigned long long*>(&S.th[c]), (unsigned long long)th);
-          atomicAdd(&S.tl[c], tl);
+        const unsigned long long n64 = (unsigned long long)(nn & 0xffffu) | ((unsigned long long)(nn >> 16) << 32);
+        const bool sums = (wh | th | (long long)(wl | tl)) != 0;
+        if (split) {  // a piece: straight into the tile's slot
+          if (nn) atomicAdd(&A[4 * kTile + c], n64);
+          if (sums) {
+            atomicAdd(&A[c], (unsigned long long)wh);
+            atomicAdd(&A[kTile + c], (unsigned long long)wl);
+            atomicAdd(&A[2 * kTile + c], (unsigned long long)th);
+            atomicAdd(&A[3 * kTile + c], (unsigned long long)tl);
+          }
+        } else {
+          if (nn) atomicAdd(&S.n[c], n64);
+          if (sums) {
+            atomicAdd(reinterpret_cast<unsigned long long*>(&S.wh[c]), (unsigned long long)wh);
+            atomicAdd(&S.wl[c], (unsigned long long)wl);
+            atomicAdd(reinterpret_cast<unsigned long long*>(&S.th[c]), (unsigned long long)th);
+            atomicAdd(&S.tl[c], (unsigned long long)tl);
+          }
         }
       }
       r = rn;
@@ -255,20 +276,44 @@ __global__ void __launch_bounds__(NT) k_fuse(const BatchDev* __restrict__ bp) {
       c = cn;
     }
     __syncthreads();
-    // ---- every touched cell of the tile, once
-    uint32_t cells = 0;
-    for (int cc = threadIdx.x; cc < ncell; cc += NT) {
-      const unsigned long long nn = S.n[cc];
-      if (!nn) continue;
-      CellCtx cx;
-      cx.h = S.h[cc];
-      cx.ve = S.ve[cc];
-      cx.valid = isfinite(cx.ve);
-      cx.href = cx.valid ? cx.h : m.z_ref;
-      cells += write_cell(m, p0 + cc, cx, fix128(S.wh[cc], S.wl[cc]), fix128(S.th[cc], S.tl[cc]),
-                          (int)(uint32_t)nn, (int)(nn >> 32));
+    if (!split) {
+      // ---- every cell of the tile with accumulated sums, once; the accumulators back to zero
+      for (int cc = threadIdx.x; cc < ncell; cc += NT) {
+        const unsigned long long nn = S.n[cc];
+        if (!nn) continue;
+        const __int128 qw = fix128(S.wh[cc], S.wl[cc]), qt = fix128(S.th[cc], S.tl[cc]);
+        S.wh[cc] = 0;
+        S.th[cc] = 0;
+        S.wl[cc] = 0;
+        S.tl[cc] = 0;
+        S.n[cc] = 0;
+        cells += write_from_sums(m, p0 + cc, S.h[cc], S.ve[cc], qw, qt, nn);
+      }
+    } else {
+      // ---- the last piece of the tile to finish writes the cells
+      __threadfence();  // this block's sums before its count of done pieces
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const int done = atomicAdd(&b.split_done[it.slot], 1);
+        if (done >= it.np) atomicCAS(&b.maps[0].ctl->err, 0, kErrInternal);
+        S.last = done == it.np - 1;
+        __threadfence();  // the other pieces' sums before this block reads them
+      }
+      __syncthreads();
+      if (S.last) {
+        for (int cc = threadIdx.x; cc < ncell; cc += NT) {
+          const unsigned long long nn = __ldcg(&A[4 * kTile + cc]);
+          if (!nn) continue;
+          const long long wh = (long long)__ldcg(&A[cc]), th = (long long)__ldcg(&A[2 * kTile + cc]);
+          const unsigned long long wl = __ldcg(&A[kTile + cc]), tl = __ldcg(&A[3 * kTile + cc]);
+#pragma unroll
+          for (int k = 0; k < kSplitWords; ++k) A[k * kTile + cc] = 0ull;  // zero for the next update
+          cells += write_from_sums(m, p0 + cc, S.h[cc], S.ve[cc], fix128(wh, wl), fix128(th, tl), nn);
+        }
+        if (threadIdx.x == 0) b.split_done[it.slot] = 0;
+      }
     }
-    // ---- the tile's statistics: one atomic per counter
+    // ---- the item's statistics: one atomic per counter
     const uint32_t v[4] = {acc, rej, wal, cells};
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -277,28 +322,37 @@ __global__ void __launch_bounds__(NT) k_fuse(const BatchDev* __restrict__ bp) {
     }
     __syncthreads();
     if (threadIdx.x < 4 && S.stat[threadIdx.x]) {
-      const int idx[4] = {kStAccepted, kStRejected, kStWall, kStCellsUpdated};
-      atomicAdd(&m.ctl->stats[idx[threadIdx.x]], S.stat[threadIdx.x]);
+      const int idx = threadIdx.x == 0 ? kStAccepted : threadIdx.x == 1 ? kStRejected : threadIdx.x == 2 ? kStWall
+                                                                                                     : kStCellsUpdated;
+      atomicAdd(&m.ctl->stats[idx], S.stat[threadIdx.x]);
     }
+    __syncthreads();
+    if (threadIdx.x == 0) S.item = fetch_item(b, w_next, n_pieces, n_heavy, n_light, n_tiles, rec_total);
     __syncthreads();
   }
 }
 
 template <int NT>
 static cudaError_t launch_fuse_t(const BatchDev* b, int64_t n_cells, cudaStream_t s) {
-  static bool attr[64] = {};
+  // per device, once: the shared-memory limit above the static 48 KB, and the
+  // resident blocks per SM (the host queries cost tens of microseconds)
+  static int per_sm[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
-  if (dev >= 0 && dev < 64 && !attr[dev]) {  // more than the 48 KB of static shared memory
-    cudaError_t e = cudaFuncSetAttribute(k_fuse<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sizeof(TileSmem));
-    if (e != cudaSuccess) return e;
-    attr[dev] = true;
+  int resident = 1;
+  if (dev >= 0 && dev < 64) {
+    if (!per_sm[dev]) {
+      cudaError_t e = cudaFuncSetAttribute(k_fuse<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)sizeof(TileSmem));
+      if (e != cudaSuccess) return e;
+      int n = 1;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fuse<NT>, NT, sizeof(TileSmem));
+      per_sm[dev] = n > 0 ? n : 1;
+    }
+    resident = per_sm[dev];
   }
-  int per_sm = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fuse<NT>, NT, sizeof(TileSmem));
   const int64_t tiles = n_cells / kTile;
-  const int64_t cap = (int64_t)sm_count() * (per_sm > 0 ? per_sm : 1);  // one resident wave
+  const int64_t cap = (int64_t)sm_count() * resident;  // one resident wave
   const int grid = (int)(tiles < cap ? (tiles < 1 ? 1 : tiles) : cap);
   k_fuse<NT><<<grid, NT, sizeof(TileSmem), s>>>(b);
   return cudaGetLastError();

@@ -7,7 +7,7 @@
 //              pre-update map, stored in logical order (one 4-byte gather per
 //              ray sample later, with no ring-buffer wrap)
 //   k_alloc    one block: every tile's range [base, base + count) of the record
-//              arrays by a running scan in tile order; heavy tiles listed
+//              arrays by a running scan in tile order; the fusion's work lists
 //   k_scatter  per point: transform + bin again, claim a slot in the tile's
 //              range, write the record (z, sigma_p^2, cell within the tile)
 //
@@ -54,7 +54,10 @@ __global__ void __launch_bounds__(kPointThreads) k_count(const BatchDev* __restr
   // per-update counters start at zero (the previous update is complete)
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     b.ctl->rec_total = 0;
+    b.ctl->n_split = 0;
+    b.ctl->n_pieces = 0;
     b.ctl->n_heavy = 0;
+    b.ctl->n_light = 0;
     b.ctl->fuse_next = 0;
     for (int mi = 0; mi < b.n_maps; ++mi) {
       const MapDev& m = b.maps[mi];
@@ -90,10 +93,14 @@ __global__ void __launch_bounds__(kPointThreads) k_count(const BatchDev* __restr
         b.tr_status[g] = !pg.finite ? kPtNonFinite : !pg.in_range ? kPtRange : !inm ? kPtOutside : kPtFused;
       }
     }
-    // one count per tile and warp: the lanes whose points share a tile add together
+    // one count per tile and warp: the lanes whose points share a tile add
+    // together; the tile's map for the fusion's work list (every writer agrees)
     const uint32_t tile = inm ? (uint32_t)((m.cell_begin + key) / kTile) : 0xffffffffu;
     const unsigned grp = __match_any_sync(kFull, tile);
-    if (inm && lane == __ffs(grp) - 1) atomicAdd(&b.tile_cnt[tile], __popc(grp));
+    if (inm && lane == __ffs(grp) - 1) {
+      atomicAdd(&b.tile_cnt[tile], __popc(grp));
+      b.tile_map[tile] = c.map;
+    }
   }
   flush_counters(b, mc, idx, 2);
   // ray thresholds of the pre-update map over the cell space (Eq. 3)
@@ -240,63 +247,117 @@ __global__ void __launch_bounds__(kPointThreads) k_drift(const BatchDev* __restr
   });
 }
 
-__device__ __forceinline__ int block_exclusive_scan(int v, int* warp_tot, int& total) {
+__device__ __forceinline__ unsigned long long block_exclusive_scan(unsigned long long v, unsigned long long* warp_tot,
+                                                                   unsigned long long& total) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int incl = v;
+  unsigned long long incl = v;
   for (int o = 1; o < 32; o <<= 1) {
-    int t = __shfl_up_sync(kFull, incl, o);
+    const unsigned long long t = __shfl_up_sync(kFull, incl, o);
     if (lane >= o) incl += t;
   }
   if (lane == 31) warp_tot[warp] = incl;
   __syncthreads();
   if (warp == 0) {
-    int w = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0;
-    int wi = w;
+    const unsigned long long w = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0ull;
+    unsigned long long wi = w;
     for (int o = 1; o < 32; o <<= 1) {
-      int t = __shfl_up_sync(kFull, wi, o);
+      const unsigned long long t = __shfl_up_sync(kFull, wi, o);
       if (lane >= o) wi += t;
     }
     if (lane < (int)(blockDim.x >> 5)) warp_tot[lane] = wi - w;
     if (lane == 31) warp_tot[32] = wi;
   }
   __syncthreads();
-  int res = warp_tot[warp] + incl - v;
+  const unsigned long long res = warp_tot[warp] + incl - v;
   total = warp_tot[32];
   __syncthreads();
   return res;
 }
 
 // One block: the record ranges of all tiles, in tile order, by a running block
-// scan of their counts; the counts and the claim cursors go back to zero for
-// the next update, and the tiles with more than heavy_thresh records are listed
-// (the fusion takes them first).
+// scan of their counts (the counts and the claim cursors go back to zero for
+// the next update), and the fusion's work lists:
+//   pieces  tiles with more than heavy_thresh records get an accumulator slot
+//           while slots last and are cut into ceil(count / heavy_thresh)
+//           near-equal pieces;
+//   heavy   the rest of those tiles, fused whole (before the light tiles);
+//   light   every other non-empty tile, in tile order.
+// The same scan counts the light tiles (count in the low word, one in the high
+// word: a chunk's records stay below 2^31, so the words do not mix).
 constexpr int kAllocThreads = 1024;
+static_assert(kMaxSplit <= kAllocThreads, "one thread per split tile in the piece scan");
 
 __global__ void __launch_bounds__(kAllocThreads) k_alloc(const BatchDev* __restrict__ bp) {
-  __shared__ int warp_tot[33];
-  __shared__ int s_heavy;
+  __shared__ unsigned long long warp_tot[33];
+  __shared__ int s_heavy, s_split;
+  __shared__ int32_t s_tile[kMaxSplit], s_cnt[kMaxSplit], s_r0[kMaxSplit], s_map[kMaxSplit];
   const BatchDev& b = *bp;
   const int64_t n_tiles = b.n_cells / kTile;
-  int base = 0;
-  if (threadIdx.x == 0) s_heavy = 0;
+  const int slots = min(b.split_slots, kMaxSplit);
+  const int thresh = b.heavy_thresh;
+  int base = 0, n_light = 0;
+  if (threadIdx.x == 0) {
+    s_heavy = 0;
+    s_split = 0;
+  }
+  __syncthreads();
   for (int64_t t0 = 0; t0 < n_tiles; t0 += kAllocThreads) {
     const int64_t t = t0 + threadIdx.x;
     const int c = t < n_tiles ? b.tile_cnt[t] : 0;
-    int tot;
-    const int off = block_exclusive_scan(c, warp_tot, tot);
+    const int mp = c > 0 ? b.tile_map[t] : 0;
+    const bool light = c > 0 && c <= thresh;
+    unsigned long long tot;
+    const unsigned long long off =
+        block_exclusive_scan((unsigned long long)(uint32_t)c | ((unsigned long long)light << 32), warp_tot, tot);
     if (t < n_tiles) {
-      b.tile_base[t] = base + off;
+      const int32_t r0 = base + (int32_t)(uint32_t)off;
+      b.tile_base[t] = r0;
       b.tile_cnt[t] = 0;
       b.tile_cur[t] = 0;
-      if (c > b.heavy_thresh) b.heavy[atomicAdd(&s_heavy, 1)] = (int32_t)t;
+      const FuseItem whole{(int32_t)t, mp, r0, r0 + c, r0, r0 + c, -1, 1};
+      if (light) {
+        b.light[n_light + (int)(off >> 32)] = whole;
+      } else if (c > thresh) {
+        const int sl = slots > 0 ? atomicAdd(&s_split, 1) : slots;
+        if (sl < slots) {
+          s_tile[sl] = (int32_t)t;
+          s_cnt[sl] = c;
+          s_r0[sl] = r0;
+          s_map[sl] = mp;
+        } else {
+          b.heavy[atomicAdd(&s_heavy, 1)] = whole;
+        }
+      }
     }
-    base += tot;
+    base += (int32_t)(uint32_t)tot;
+    n_light += (int)(tot >> 32);
   }
   __syncthreads();
+  // the piece list: split tile i has np = ceil(count / heavy_thresh) pieces of
+  // ceil(count / np) records (the last ones may be shorter)
+  const int n_split = min(s_split, slots);
+  const int i = threadIdx.x;
+  const int np = i < n_split ? (s_cnt[i] + thresh - 1) / thresh : 0;
+  unsigned long long n_pieces;
+  const int first = (int)block_exclusive_scan((unsigned long long)np, warp_tot, n_pieces);
+  const bool fits = n_pieces <= (unsigned long long)b.max_pieces;  // holds by the workspace's size
+  if (fits && np > 0) {
+    const int32_t c = s_cnt[i], r0 = s_r0[i];
+    const int32_t len = (c + np - 1) / np;
+    for (int k = 0; k < np; ++k) {
+      const int32_t q0 = r0 + (int32_t)min((int64_t)c, (int64_t)k * len);
+      const int32_t q1 = r0 + (int32_t)min((int64_t)c, (int64_t)(k + 1) * len);
+      b.pieces[first + k] = FuseItem{s_tile[i], s_map[i], r0, r0 + c, q0, q1, i, np};
+    }
+  }
   if (threadIdx.x == 0) {
     b.tile_base[n_tiles] = base;
     b.ctl->rec_total = base;
+    b.ctl->n_split = fits ? n_split : 0;
+    b.ctl->n_pieces = fits ? (int32_t)n_pieces : 0;
     b.ctl->n_heavy = s_heavy;
+    b.ctl->n_light = n_light;
+    if (!fits) atomicCAS(&b.maps[0].ctl->err, 0, kErrInternal);
   }
 }
 

@@ -193,3 +193,40 @@ def test_batched_config_sizes_vs_oracle(em):
     for m in maps:
         m.close()
     batch.close()
+
+
+def test_split_tiles_and_slot_overflow_give_identical_maps(em):
+    """Tiles with many records are cut into pieces that several blocks fuse at
+    once.  No tile cut, some tiles cut, and more tiles worth cutting than there
+    are accumulator slots (the rest fused whole) all give the same map bit for
+    bit, with the wall rule on (its per-cell counts span the whole tile, not
+    one piece) and a few cells holding thousands of records."""
+    side = 1000
+    P = dict(BASE, width=side, height=side, wall_num_thresh=2)
+    prior = synth.random_prior(seed=71, width=side, height=side, t_now=5, with_normals=False)
+    half = 0.5 * side * 0.04
+    clouds = [synth.scattered_cloud(72, 1_500_000, half, nan_frac=0.01),
+              dense_cloud(73, [(0.3, -0.2), (0.34, -0.2), (-7.0, 5.0)], 3000, half)]
+    dclouds = [(dev(p), q) for p, q in clouds]
+    # tiles hold about 1,536 records: 16 x 1023 cuts none, 16 x 100 cuts a few
+    # tens, 16 x 32 would cut all 977 (more than the 512 slots)
+    shapes = [dict(ray_group=4, fuse_chunk=256, big_thresh=1023), dict(ray_group=4, fuse_chunk=256, big_thresh=100),
+              dict(ray_group=4, fuse_chunk=512, big_thresh=32), dict(ray_group=4, fuse_chunk=256, big_thresh=32)]
+    results = []
+    for tune in shapes:
+        m = em.Map(em.Params(**P))
+        parity.prior_to_gpu(m, prior)
+        batch = em.Batch(max_maps=1, max_clouds=2, max_points=1_600_000, max_cells=side * side, graph=False)
+        batch.set_tuning(**tune)
+        for _ in range(2):
+            batch.update([(m, p, q) for p, q in dclouds])
+        torch.cuda.synchronize()
+        results.append((m.state(), m.stats()))
+        batch.close()
+        m.close()
+    st0, stats0 = results[0]
+    assert stats0["points_wall"] > 0 and stats0["points_rejected"] > 0
+    for st, stats in results[1:]:
+        assert_same([st0], [st])
+        for k in ("points_accepted", "points_rejected", "points_wall", "cells_updated"):
+            assert stats0[k] == stats[k], k
