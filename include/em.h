@@ -259,7 +259,8 @@ enum { EM_BATCH_GRAPH = 1u << 0 };
 /* Launch shapes picked by the autotuner (or set by hand).  None of them
  * changes a result: every shape gives the same maps bit for bit. */
 typedef struct em_tuning {
-  int32_t ray_group;    /* lanes per ray in the ray march: 1, 2, 4, 8, 16 or 32 */
+  int32_t ray_group;    /* ray march: samples per chunk tested against the coarse threshold grid,
+                           and lanes per marched chunk: 1, 2, 4, 8, 16 or 32 */
   int32_t fuse_chunk;   /* threads per fusion block (one tile of 1024 cells per block): 64 .. 1024, a
                            power of two; 512 and more run 512-thread blocks, the rest 256-thread ones */
   int32_t big_thresh;   /* tiles with more than 16 x big_thresh records are fused first: 32 .. 1023 */

@@ -70,6 +70,7 @@ struct em_map {
   // per-cell scratch
   uint32_t* mark = nullptr;
   float* thr = nullptr;
+  float* cthr = nullptr;  // coarse grid of the ray thresholds (maps with the ray march)
   int32_t* tile_cnt = nullptr;   // per tile of 1024 cells: record counts, ranges, claims
   int32_t* tile_base = nullptr;
   int32_t* tile_cur = nullptr;
@@ -116,7 +117,7 @@ struct em_map {
   int64_t layer_bytes = 0;
   int64_t work_bytes = 0;
   int fuse_threads = 256;
-  int ray_group = 4;
+  int ray_group = 8;
   int heavy_thresh = 256 * 16;
   int64_t points_in = 0;
   // per-kernel profiling
@@ -141,7 +142,11 @@ MapDev make_mapdev(const em_map* m) {
   memset(&d, 0, sizeof(d));
   d.h = m->h; d.var = m->var; d.t_last = m->t_last;
   d.nx = m->nx; d.ny = m->ny; d.nz = m->nz; d.smooth = m->smooth; d.inpaint = m->inpaint; d.upper = m->upper;
-  d.mark = m->mark; d.thr = m->thr;
+  d.mark = m->mark; d.thr = m->thr; d.cthr = m->cthr;
+  if (m->cthr) {
+    d.CW = coarse_dim(m->p.width);
+    d.CH = coarse_dim(m->p.height);
+  }
   d.ctl = m->ctl;
   d.cell_begin = 0;
   d.W = m->p.width; d.H = m->p.height; d.ox = m->ox; d.oy = m->oy;
@@ -232,7 +237,7 @@ void release(em_map* m) {
     if (m->prof_ev[i]) cudaEventDestroy(m->prof_ev[i]);
   cudaFree(m->h); cudaFree(m->var); cudaFree(m->t_last);
   cudaFree(m->nx); cudaFree(m->ny); cudaFree(m->nz); cudaFree(m->smooth); cudaFree(m->inpaint); cudaFree(m->upper);
-  cudaFree(m->mark); cudaFree(m->thr);
+  cudaFree(m->mark); cudaFree(m->thr); cudaFree(m->cthr);
   cudaFree(m->tile_cnt); cudaFree(m->tile_base); cudaFree(m->tile_cur); cudaFree(m->tile_map);
   cudaFree(m->heavy); cudaFree(m->light);
   cudaFree(m->split_acc); cudaFree(m->split_done);
@@ -304,6 +309,7 @@ int upload_desc(em_map* m, const em_cloud* clouds, int32_t n_clouds, int64_t tot
   b->tr_iy = m->tr_iy;
   b->tr_status = m->tr_status;
   b->n_cells = pad_tile((int64_t)m->p.width * m->p.height);
+  b->n_coarse = (int64_t)md->CW * md->CH;
   b->ctl = m->bctl;
   b->tile_cnt = m->tile_cnt;
   b->tile_base = m->tile_base;
@@ -465,6 +471,7 @@ int em_create(const em_params* params, int device, em_map** out) {
   if (params->flags & EM_F_UPPER) { EM_ALLOC(m->upper, nc) }
   const size_t ntile = (size_t)(pad_tile((int64_t)nc) / kTile);
   EM_ALLOC(m->mark, (nc + 31) / 32) EM_ALLOC(m->thr, nc)
+  if (params->ray_step > 0.f) { EM_ALLOC(m->cthr, (size_t)coarse_dim(params->width) * coarse_dim(params->height)) }
   EM_ALLOC(m->tile_cnt, ntile + 1) EM_ALLOC(m->tile_base, ntile + 1) EM_ALLOC(m->tile_cur, ntile + 1)
   EM_ALLOC(m->tile_map, ntile) EM_ALLOC(m->heavy, ntile) EM_ALLOC(m->light, ntile)
   m->split_slots = (int32_t)(ntile < (size_t)kMaxSplit ? ntile : (size_t)kMaxSplit);
@@ -552,7 +559,7 @@ static int update_impl(em_map* m, const em_cloud* clouds, int32_t n_clouds, cuda
     // the marks (read by k_clear): it runs on the side stream beside the sort and
     // the fusion, unless the map has the upper-bound layer (both write it)
     auto ray = [&](cudaStream_t rs) {
-      return timed(m, EM_PROF_RAY, rs, [&] { return launch_ray(bd, total, m->ray_group, ext, rs); });
+      return timed(m, EM_PROF_RAY, rs, [&] { return launch_ray(bd, total, ncell, m->ray_group, ext, rs); });
     };
     auto rest = [&] {
       cudaError_t r = timed(m, EM_PROF_ALLOC, s, [&] { return launch_alloc(bd, ncell, s); });

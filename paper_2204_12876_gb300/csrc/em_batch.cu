@@ -80,7 +80,7 @@ struct em_batch {
   unsigned char* desc_dev = nullptr;
   cudaEvent_t ev[kSlots] = {};
   int slot = 0;
-  em_tuning tune{4, 256, 256};
+  em_tuning tune{8, 256, 256};
   cudaStream_t capture_stream = nullptr;
   cudaStream_t side = nullptr;  // the ray march, beside the sort and fusion
   cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
@@ -139,7 +139,7 @@ cudaError_t launch_sequence(em_batch* b, const BatchDev* bd, int64_t grid_points
   if (e == cudaSuccess && k.drift) e = timed(prof, EM_PROF_DRIFT, s, [&] { return launch_drift(bd, grid_points, grid_cells, k.ext, s); });
   if (grid_points > 0) {
     auto ray = [&](cudaStream_t rs) {
-      return timed(prof, EM_PROF_RAY, rs, [&] { return launch_ray(bd, grid_points, k.t.ray_group, k.ext, rs); });
+      return timed(prof, EM_PROF_RAY, rs, [&] { return launch_ray(bd, grid_points, grid_cells, k.t.ray_group, k.ext, rs); });
     };
     auto rest = [&] {
       cudaError_t r = timed(prof, EM_PROF_ALLOC, s, [&] { return launch_alloc(bd, grid_cells, s); });
@@ -221,11 +221,13 @@ int prepare(em_batch* b, em_map* const* maps, const em_cloud* clouds, int32_t co
   CloudDev* cd = reinterpret_cast<CloudDev*>(hb + sizeof(BatchDev) + (size_t)b->max_maps * sizeof(MapDev));
   memset(bd, 0, sizeof(BatchDev));
   GraphKey key{tune, false, false, false, false, false, 0u};
-  int64_t cells = 0;
+  int64_t cells = 0, coarse = 0;
   for (int u = 0; u < nm; ++u) {
     md[u] = map_begin_update(b->uniq[u], map_pts[u]);
     md[u].cell_begin = cells;
     cells += pad_tile(map_cells(b->uniq[u]));
+    md[u].cbegin = coarse;
+    coarse += (int64_t)md[u].CW * md[u].CH;
     key.ray |= md[u].ray_step > 0.f;
     key.drift |= md[u].drift_flat > 0.f;
     key.overlap |= md[u].ovl_dz > 0.f;
@@ -267,6 +269,7 @@ int prepare(em_batch* b, em_map* const* maps, const em_cloud* clouds, int32_t co
   bd->rv = b->rv;
   bd->rc = b->rc;
   bd->n_cells = cells;
+  bd->n_coarse = coarse;
   bd->ctl = b->bctl;
   bd->tile_cnt = b->tile_cnt;
   bd->tile_base = b->tile_base;

@@ -36,6 +36,12 @@
 namespace em {
 
 constexpr int kTile = 1024;  // cells per tile of the cell space
+// The ray march's coarse grid: per block of kCoarse x kCoarse logical cells the
+// largest ray threshold of the block (a chunk of samples whose lowest z is not
+// below it cannot mark any cell).
+constexpr int kCoarseShift = 3;
+constexpr int kCoarse = 1 << kCoarseShift;
+inline int32_t coarse_dim(int32_t cells) { return (cells + kCoarse - 1) >> kCoarseShift; }
 
 
 // per-map counters (device), in em_stats order
@@ -112,7 +118,10 @@ struct MapDev {
   float* upper;     // upper bound of the ground height (Section II-H), +inf where none; may be null
   uint32_t* mark;   // visibility marks, one bit per physical cell, zero between updates
   float* thr;       // per LOGICAL cell [iy][ix]: h - sqrt(var_eff) of the pre-update map, -inf if empty
+  float* cthr;      // per coarse block [by][bx] (CW x CH of them): the largest thr of its cells
   MapCtl* ctl;
+  int64_t cbegin;   // this map's first block in the batch's coarse space (maps with the ray march)
+  int32_t CW, CH;   // coarse blocks per row and column; 0 x 0 without the ray march
   int64_t cell_begin;  // this map's first cell in the batch cell space (multiple of kTile)
   int32_t W, H, ox, oy;
   float x0, y0, res, inv_res;  // inv_res = 1 / res rounded to float
@@ -143,6 +152,7 @@ struct BatchDev {
   int32_t n_maps, n_clouds;
   int64_t n_points;
   int64_t n_cells;     // padded size of the cell space
+  int64_t n_coarse;    // blocks of the coarse grids of all maps
   const MapDev* maps;
   const CloudDev* clouds;
   // records grouped by tile (layout above); capacity: the points of the batch
@@ -234,7 +244,8 @@ cudaError_t launch_beside(cudaStream_t s, cudaStream_t side, cudaEvent_t fork, c
 // ext: some map of the batch uses the exclusion area or the upper-bound layer
 cudaError_t launch_bin(const BatchDev* b, int64_t n_points, int64_t n_cells, bool ext, cudaStream_t s);
 cudaError_t launch_drift(const BatchDev* b, int64_t n_points, int64_t n_cells, bool ext, cudaStream_t s);
-cudaError_t launch_ray(const BatchDev* b, int64_t n_points, int group, bool ext, cudaStream_t s);
+// the coarse threshold grids, then the march (group: samples per chunk and lanes per marched chunk)
+cudaError_t launch_ray(const BatchDev* b, int64_t n_points, int64_t n_cells, int group, bool ext, cudaStream_t s);
 cudaError_t launch_alloc(const BatchDev* b, int64_t n_cells, cudaStream_t s);
 cudaError_t launch_scatter(const BatchDev* b, int64_t n_points, bool ext, cudaStream_t s);
 cudaError_t launch_fuse(const BatchDev* b, int64_t n_cells, int threads, cudaStream_t s);

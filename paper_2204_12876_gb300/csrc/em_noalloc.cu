@@ -58,7 +58,10 @@ constexpr size_t kOffTMap = kOffTCur + up256((kMaxTiles + 1) * sizeof(int32_t));
 constexpr size_t kOffHeavy = kOffTMap + up256(kMaxTiles * sizeof(int32_t));
 constexpr size_t kOffLight = kOffHeavy + up256(kMaxTiles * sizeof(FuseItem));
 constexpr size_t kOffThr = kOffLight + up256(kMaxTiles * sizeof(FuseItem));
-constexpr size_t kOffRz = kOffThr + up256((size_t)kMaxCells * sizeof(float));
+// coarse blocks of a map of at most kMaxCells cells: (W/8 + 1)(H/8 + 1) <= kMaxCells/64 + (W + H)/8 + 1
+constexpr size_t kMaxCoarse = (size_t)kMaxCells / 64 + ((size_t)kMaxCells + 1) / 8 + 2;
+constexpr size_t kOffCThr = kOffThr + up256((size_t)kMaxCells * sizeof(float));
+constexpr size_t kOffRz = kOffCThr + up256(kMaxCoarse * sizeof(float));
 constexpr size_t kOffRv = kOffRz + up256((size_t)kMaxPoints * sizeof(float));
 constexpr size_t kOffRc = kOffRv + up256((size_t)kMaxPoints * sizeof(float));
 constexpr size_t kScratchBytes = kOffRc + up256((size_t)kMaxPoints * sizeof(uint16_t));
@@ -164,6 +167,11 @@ extern "C" int em_update_noalloc(const em_params* params, int64_t shift_x, int64
   m->nz = const_cast<float*>(nz);
   m->mark = reinterpret_cast<uint32_t*>(base + kOffMark);
   m->thr = reinterpret_cast<float*>(base + kOffThr);
+  if (params->ray_step > 0.f) {
+    m->cthr = reinterpret_cast<float*>(base + kOffCThr);
+    m->CW = coarse_dim(W);
+    m->CH = coarse_dim(H);
+  }
   m->ctl = reinterpret_cast<MapCtl*>(base + kOffCtl);
   m->cell_begin = 0;
   m->z_ref = clouds[0].pose[11];
@@ -214,6 +222,7 @@ extern "C" int em_update_noalloc(const em_params* params, int64_t shift_x, int64
   b->heavy = reinterpret_cast<FuseItem*>(base + kOffHeavy);
   b->light = reinterpret_cast<FuseItem*>(base + kOffLight);
   b->n_cells = pad_tile(ncell);
+  b->n_coarse = (int64_t)m->CW * m->CH;
   b->ctl = reinterpret_cast<BatchCtl*>(base + kOffBCtl);
   b->heavy_thresh = 4096;
   b->split_slots = 0;  // no tile is split: heavy tiles are fused whole
@@ -231,7 +240,7 @@ extern "C" int em_update_noalloc(const em_params* params, int64_t shift_x, int64
   cudaError_t e = launch_bin(bd, total, cells, ext, s);
   if (e == cudaSuccess && params->drift_flatness > 0.f) e = launch_drift(bd, total, cells, ext, s);
   if (total > 0) {
-    if (e == cudaSuccess && params->ray_step > 0.f) e = launch_ray(bd, total, 4, ext, s);
+    if (e == cudaSuccess && params->ray_step > 0.f) e = launch_ray(bd, total, cells, 8, ext, s);
     if (e == cudaSuccess) e = launch_alloc(bd, cells, s);
     if (e == cudaSuccess) e = launch_scatter(bd, total, ext, s);
     if (e == cudaSuccess) e = launch_fuse(bd, cells, 256, s);

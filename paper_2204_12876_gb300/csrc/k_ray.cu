@@ -1,18 +1,26 @@
 // k_ray.cu -- visibility cleanup by ray casting (Section II-E of the paper).
 //
-// k_ray: one ray per valid point, marched by a group of G lanes.  The ray from
-// the sensor origin o (the pose translation) to the point is sampled at
-// s_k = o + (k step / d) (R p_s) for k = 1, 2, ... while k step < d (computed
-// as a + k b in cell units: one FMA per coordinate); lane j of the group takes
-// k = k_lo + j, k_lo + j + G, ..., so the group keeps G independent gathers in
-// flight, and each lane loads the thresholds of 4 samples before testing them.  A sample inside the map, outside the point's
-// own cell, below the cell's threshold h - sqrt(sigma_m^2) of the pre-update
-// map (Eq. 3; the threshold layer is -inf for empty cells) and -- when
-// alpha_n > 0 -- with |rhat . n| > alpha_n for the cell's previous normal
-// (Eq. 4; a NaN normal counts as (0, 0, 1)) marks the cell in a bitmask
-// (atomicOr: idempotent, so the marks do not depend on thread order).  Only
-// the k whose samples can lie inside the map's box are visited.  The kernel
-// runs before the fusion, so it sees the pre-update map.
+// k_ray: one ray per valid point.  The ray from the sensor origin o (the pose
+// translation) to the point is sampled at s_k = o + (k step / d) (R p_s) for
+// k = 1, 2, ... while k step < d (computed as a + k b in cell units: one FMA
+// per coordinate).  A sample inside the map, outside the point's own cell,
+// below the cell's threshold h - sqrt(sigma_m^2) of the pre-update map (Eq. 3;
+// the threshold layer is -inf for empty cells) and -- when alpha_n > 0 -- with
+// |rhat . n| > alpha_n for the cell's previous normal (Eq. 4; a NaN normal
+// counts as (0, 0, 1)) marks the cell in a bitmask (atomicOr: idempotent, so
+// the marks do not depend on thread order).  Only the k whose samples can lie
+// inside the map's box are visited.  The kernel sees the pre-update map.
+//
+// Most samples of a scan pass far above the surface.  k_coarse keeps, per
+// block of kCoarse x kCoarse cells, the largest threshold of the block.  The
+// march cuts each ray into chunks of at most G samples spanning at most
+// kCoarse cells per axis; a chunk's samples lie in the cells between those of
+// its first and last sample (both coordinates and z are monotone in k, and the
+// same rounded arithmetic gives every sample), so when the lower of its end
+// heights is not below the largest threshold of the (at most 2 x 2) blocks it
+// touches, none of its samples can mark a cell and it is skipped -- an exact
+// test, not a heuristic.  Each lane tests its own ray's chunks; the warp
+// queues the others and marches them G lanes per chunk, one sample per lane.
 //
 // k_clear: after the fusion, every marked cell that holds an estimate and was
 // last written at least max(1, cleanup_min_age) updates ago is removed; the
@@ -38,37 +46,87 @@ __device__ __forceinline__ bool slab(float o, float v, float d, float a0, float 
   return true;
 }
 
-// Per-ray set-up shared by the lanes that march it.  Sample k lies at
-// q = a + k b in cell units (x, y) and at z = az + k bz, i.e. the track
-// o + (k step / d) (R p_s) measured from the map corner in cells.
-// Samples per ray are capped at 2^24 - 1, so the float sample index is exact.
+// Per-ray set-up, made by one lane and read by the lanes that test and march
+// the ray's chunks.  Sample k lies at q = a + k b in cell units (x, y) and at
+// z = az + k bz, i.e. the track o + (k step / d) (R p_s) measured from the map
+// corner in cells.  Samples per ray are capped at 2^24 - 1, so the float
+// sample index is exact.
 constexpr int32_t kMaxRayK = (1 << 24) - 1;
 
 struct RaySetup {
   float ax, bx, ay, by, az, bz;
   float vx, vy, vz, d;  // for the Eq. 4 guard
   int32_t ix, iy, k_lo, n, map;
+  int32_t cn;           // samples per chunk
 };
 
-// Each warp takes 32 consecutive points: first every lane sets up one ray
-// (transform, distance, own cell, the k range inside the map box and before
-// the point), then the warp marches them G lanes per ray, 32 / G rays at a
-// time, so the set-up cost is paid once per ray.
+// floor(t) of a cell coordinate by one add rounded down: t + 1.5 2^23 lands
+// where the float spacing is 1, so its bits hold floor(t) + 0x4B400000 (|t| <
+// 2^22; anything farther out gives an index outside [0, 2^22) and fails the
+// map's box test)
+__device__ __forceinline__ int32_t cell_floor(float t) {
+  return __float_as_int(__fadd_rd(t, 12582912.0f)) - 0x4B400000;
+}
+
+// Largest ray threshold per coarse block of every map with the ray march.
+constexpr int kCoarseThreads = 256;
+__global__ void __launch_bounds__(kCoarseThreads) k_coarse(const BatchDev* __restrict__ bp) {
+  const BatchDev& b = *bp;
+  for (int64_t g = (int64_t)blockIdx.x * kCoarseThreads + threadIdx.x; g < b.n_coarse;
+       g += (int64_t)gridDim.x * kCoarseThreads) {
+    int lo = 0, hi = b.n_maps - 1;  // the last map whose coarse range starts at or before g
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (b.maps[mid].cbegin <= g) lo = mid; else hi = mid - 1;
+    }
+    const MapDev& m = b.maps[lo];
+    const int32_t q = (int32_t)(g - m.cbegin);
+    const int32_t by = q / m.CW, bx = q - by * m.CW;
+    const int32_t x0 = bx << kCoarseShift, y0 = by << kCoarseShift;
+    const int32_t nx = min(kCoarse, m.W - x0), ny = min(kCoarse, m.H - y0);
+    float mx = __int_as_float(0xff800000);
+    for (int32_t y = 0; y < ny; ++y) {
+      const float* row = m.thr + (int64_t)(y0 + y) * m.W + x0;
+      for (int32_t x = 0; x < nx; ++x) mx = fmaxf(mx, __ldg(row + x));  // a NaN never marks: skipped
+    }
+    m.cthr[q] = mx;
+  }
+}
+
+// Each warp takes 32 consecutive points: every lane sets up one ray (transform,
+// distance, own cell, the k range inside the map box and before the point, its
+// chunk length) and tests its ray's chunks one after another; the warp queues
+// the chunks that may mark a cell and marches them 4 x 32 / G at a time, G
+// lanes per chunk and one sample per lane and round (4 gathers in flight).
 template <int G, bool kExt>
-__global__ void __launch_bounds__(kRayThreads) k_ray(const BatchDev* __restrict__ bp) {
+__global__ void __launch_bounds__(kRayThreads, 4) k_ray(const BatchDev* __restrict__ bp) {
+  constexpr int kWarps = kRayThreads / 32;
+  constexpr int kU = G >= 4 ? 4 : G;         // samples per lane and march round
+  constexpr int kFQ = kU * 32 / G;           // chunks per march round (at most 32)
+  constexpr int kCU = 4;                     // chunks per lane and test round (their loads in flight together)
+  constexpr int kQ = 256;                    // queued chunks per warp (a ring)
+  static_assert(kQ >= kFQ - 1 + 32 * kCU && kFQ <= 32, "queue capacity");
   __shared__ RaySetup s_ray[kRayThreads];
+  __shared__ int2 s_q[kWarps][kQ];           // {ray | samples << 8, first sample}
   const BatchDev& b = *bp;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   RaySetup* wr = s_ray + warp * 32;
-  const int64_t n_warps = (int64_t)gridDim.x * (kRayThreads / 32);
-  int smap = -1;  // map of this lane's sample count
+  int2* q = s_q[warp];
+  // each warp takes a contiguous run of 32-point batches, so its batches mostly
+  // share a cloud and a map (one sample count per map change below)
+  const int64_t n_warps = (int64_t)gridDim.x * kWarps;
+  const int64_t n_batches = (b.n_points + 31) / 32;
+  const int64_t per_warp = (n_batches + n_warps - 1) / n_warps;
+  const int64_t wid = (int64_t)blockIdx.x * kWarps + warp;
+  const int64_t w_end = min((wid + 1) * per_warp, n_batches) * 32;
+  int smap = -1;  // the map of the warp's running sample count (warp-uniform)
   unsigned long long samples = 0;
-  for (int64_t wbase = ((int64_t)blockIdx.x * (kRayThreads / 32) + warp) * 32; wbase < b.n_points;
-       wbase += n_warps * 32) {
+  for (int64_t wbase = wid * per_warp * 32; wbase < w_end; wbase += 32) {
     // ---- set-up: one ray per lane
     RaySetup r;
     r.n = 0;
     r.map = 0;
+    r.cn = 1;
     const int64_t g = wbase + lane;
     if (g < b.n_points) {
       const int ci = find_cloud(b.clouds, b.n_clouds, g);
@@ -110,94 +168,141 @@ __global__ void __launch_bounds__(kRayThreads) k_ray(const BatchDev* __restrict_
           r.iy = pg.iy;
           r.k_lo = k_lo;
           r.n = k_hi >= k_lo ? k_hi - k_lo + 1 : 0;
+          // chunks span at most kCoarse - 1/2 cells per axis, so they touch at most 2 x 2 blocks
+          const float span = fmaxf(fmaxf(fabsf(r.bx), fabsf(r.by)), 1e-6f);
+          r.cn = (int32_t)fminf((float)G, 1.f + floorf(__fdividef((float)kCoarse - 0.5f, span)));
         }
+      }
+    }
+    {  // samples of the march, per map: a warp sum when the batch's rays share a map
+      const int m0 = __shfl_sync(0xffffffffu, r.map, 0);
+      unsigned long long t = (unsigned long long)r.n;
+      if (__all_sync(0xffffffffu, r.map == m0 || r.n == 0)) {
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (m0 != smap) {
+          if (lane == 0 && smap >= 0 && samples) atomicAdd(&b.maps[smap].ctl->stats[kStRaySamples], samples);
+          samples = 0;
+          smap = m0;
+        }
+        samples += t;
+      } else if (r.n > 0) {  // a batch across a map boundary: per lane
+        atomicAdd(&b.maps[r.map].ctl->stats[kStRaySamples], t);
       }
     }
     wr[lane] = r;
-    __syncwarp();
-    // ---- march: G lanes per ray, 4 samples per lane and step (4 gathers in flight)
-    const int gl = lane % G;
-    for (int r0 = 0; r0 < 32; r0 += 32 / G) {
-      const RaySetup& R = wr[r0 + lane / G];
-      if (R.n <= 0) continue;
-      if (R.map != smap) {  // count this lane's samples per map
-        if (smap >= 0 && samples) atomicAdd(&b.maps[smap].ctl->stats[kStRaySamples], samples);
-        samples = 0;
-        smap = R.map;
-      }
-      if (gl == 0) samples += (unsigned long long)R.n;
-      const MapDev& m = b.maps[R.map];
-      const int32_t W = m.W, H = m.H, ox = m.ox, oy = m.oy;
-      const float* __restrict__ thr = m.thr;
-      const bool guard = m.alpha_n > 0.f;
-      const int32_t k_end = R.k_lo + R.n, rix = R.ix, riy = R.iy;
-      const float ax = R.ax, bx = R.bx, ay = R.ay, by = R.by, az = R.az, bz = R.bz;
-      float kf = (float)(R.k_lo + gl);  // sample index as a float, stepped exactly (k < 2^24)
-      for (int32_t k = R.k_lo + gl; k < k_end; k += 4 * G) {
-        int32_t pl[4];
-        float zz[4], th[4];
-        bool any = false;
+    // ---- this lane's ray: its chunks against the coarse grid, in order
+    const MapDev& m = b.maps[r.map];
+    const float* __restrict__ ct = m.cthr;
+    const int32_t W = m.W, H = m.H, CW = m.CW;
+    const int32_t nch = r.n > 0 ? (r.n + r.cn - 1) / r.cn : 0;
+    int qh = 0, qn = 0;  // queue head and length (warp-uniform)
+    for (int32_t c0 = 0; __any_sync(0xffffffffu, c0 < nch); c0 += kCU) {
+      // all loads of the round first (predicated, no branches between them), then the tests
+      bool keep[kCU], test[kCU];
+      int32_t k0[kCU], cnt[kCU];
+      float mx[kCU], zmin[kCU];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          // floor(t) of t = fma(k, b, a) by one add rounded down: t + 1.5 2^23 lands where the
-          // float spacing is 1, so its bits hold floor(t) + 0x4B400000 (|t| < 2^22; anything
-          // farther out gives an index outside [0, 2^22) and fails the box test below)
-          const int32_t cx = __float_as_int(__fadd_rd(__fmaf_rn(kf, bx, ax), 12582912.0f)) - 0x4B400000;
-          const int32_t cy = __float_as_int(__fadd_rd(__fmaf_rn(kf, by, ay), 12582912.0f)) - 0x4B400000;
-          const bool ok = k + u * G < k_end && (uint32_t)cx < (uint32_t)W && (uint32_t)cy < (uint32_t)H &&
-                          !(cx == rix && cy == riy);
-          pl[u] = cy * W + cx;  // logical index
-          zz[u] = __fmaf_rn(kf, bz, az);
-          th[u] = ok ? __ldg(thr + pl[u]) : __int_as_float(0xff800000);
-          kf = __fadd_rn(kf, (float)G);
+      for (int u = 0; u < kCU; ++u) {
+        const int32_t c = c0 + u;
+        k0[u] = r.k_lo + c * r.cn;
+        cnt[u] = min(r.cn, r.n - c * r.cn);
+        const float k0f = (float)k0[u], k1f = (float)(k0[u] + cnt[u] - 1);
+        const int32_t xa0 = cell_floor(__fmaf_rn(k0f, r.bx, r.ax)), xa1 = cell_floor(__fmaf_rn(k1f, r.bx, r.ax));
+        const int32_t ya0 = cell_floor(__fmaf_rn(k0f, r.by, r.ay)), ya1 = cell_floor(__fmaf_rn(k1f, r.by, r.ay));
+        const int32_t xl = min(xa0, xa1), xh = max(xa0, xa1), yl = min(ya0, ya1), yh = max(ya0, ya1);
+        // some sample of the chunk may be inside the map
+        const bool inside = c < nch && xh >= 0 && xl < W && yh >= 0 && yl < H;
+        const int32_t bxl = max(xl, 0) >> kCoarseShift, bxh = min(xh, W - 1) >> kCoarseShift;
+        const int32_t byl = max(yl, 0) >> kCoarseShift, byh = min(yh, H - 1) >> kCoarseShift;
+        // more than 2 x 2 blocks (not for the chunk lengths above): march it untested
+        const bool wide = bxh - bxl > 1 || byh - byl > 1;
+        test[u] = inside && !wide;
+        keep[u] = inside && wide;
+        const float ninf = __int_as_float(0xff800000);
+        const float v0 = test[u] ? __ldg(ct + byl * CW + bxl) : ninf;
+        const float v1 = test[u] ? __ldg(ct + byl * CW + bxh) : ninf;
+        const float v2 = test[u] ? __ldg(ct + byh * CW + bxl) : ninf;
+        const float v3 = test[u] ? __ldg(ct + byh * CW + bxh) : ninf;
+        mx[u] = fmaxf(fmaxf(v0, v1), fmaxf(v2, v3));
+        zmin[u] = fminf(__fmaf_rn(k0f, r.bz, r.az), __fmaf_rn(k1f, r.bz, r.az));
+      }
+#pragma unroll
+      for (int u = 0; u < kCU; ++u) keep[u] = keep[u] || (test[u] && zmin[u] < mx[u]);
+      // ---- queue the chunks that may mark a cell
+#pragma unroll
+      for (int u = 0; u < kCU; ++u) {
+        const unsigned km = __ballot_sync(0xffffffffu, keep[u]);
+        if (keep[u])
+          q[(qh + qn + __popc(km & ((1u << lane) - 1u))) & (kQ - 1)] = make_int2(lane | (cnt[u] << 8), k0[u]);
+        qn += __popc(km);
+      }
+      __syncwarp();
+      // ---- march the queued chunks, kFQ at a time (all of them after the last test)
+      const bool last = !__any_sync(0xffffffffu, c0 + kCU < nch);
+      while (qn >= kFQ || (last && qn > 0)) {
+        const int sj = lane % G;
+        // every sample's threshold first (kU gathers in flight), then the marks
+        int32_t pl[kU];
+        float zz[kU], th[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+          const int qi = u * (32 / G) + lane / G;
+          const int2 e = q[(qh + qi) & (kQ - 1)];
+          const bool live = qi < qn && sj < (e.x >> 8);
+          const RaySetup& R = wr[e.x & 31];
+          const MapDev& mm = b.maps[live ? R.map : 0];
+          const int32_t Wm = mm.W, Hm = mm.H;
+          const float* __restrict__ tm = mm.thr;
+          const float kf = (float)(e.y + sj);
+          const int32_t cx = cell_floor(__fmaf_rn(kf, R.bx, R.ax));
+          const int32_t cy = cell_floor(__fmaf_rn(kf, R.by, R.ay));
+          const bool ok = live && (uint32_t)cx < (uint32_t)Wm && (uint32_t)cy < (uint32_t)Hm && !(cx == R.ix && cy == R.iy);
+          zz[u] = __fmaf_rn(kf, R.bz, R.az);
+          pl[u] = cy * Wm + cx;  // logical index
+          th[u] = ok ? __ldg(tm + pl[u]) : __int_as_float(0xff800000);  // -inf: never below
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) any |= zz[u] < th[u];
-        if (!any) continue;  // the common case: no sample of these four is below its cell
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          if (!(zz[u] < th[u])) continue;  // also skips the samples that are not taken (th = -inf)
+        for (int u = 0; u < kU; ++u) {
+          if (!(zz[u] < th[u])) continue;  // the common case, and every sample not taken
+          const RaySetup& R = wr[q[(qh + u * (32 / G) + lane / G) & (kQ - 1)].x & 31];
+          const MapDev& mm = b.maps[R.map];
+          const int32_t Wm = mm.W, Hm = mm.H;
           // physical cell of the sample (ring-buffer layout of the map layers)
-          const int32_t cy = pl[u] / W, cx = pl[u] - cy * W;
-          int32_t px = cx + ox;
-          px -= (px >= W) ? W : 0;
-          int32_t py = cy + oy;
-          py -= (py >= H) ? H : 0;
-          const int32_t p = py * W + px;
-          if (kExt && !isfinite(m.var[p])) {
+          const int32_t cy = pl[u] / Wm, cx = pl[u] - cy * Wm;
+          int32_t px = cx + mm.ox;
+          px -= (px >= Wm) ? Wm : 0;
+          int32_t py = cy + mm.oy;
+          py -= (py >= Hm) ? Hm : 0;
+          const int32_t p = py * Wm + px;
+          if (kExt && !isfinite(mm.var[p])) {
             // an empty cell (its threshold is the upper bound): the sample lowers
             // the bound (Section II-H); float minimum through the ordered bits
-            const float z = zz[u];
-            if (__float_as_int(z) >= 0) atomicMin(reinterpret_cast<int*>(m.upper + p), __float_as_int(z));
-            else atomicMax(reinterpret_cast<unsigned int*>(m.upper + p), __float_as_uint(z));
+            if (__float_as_int(zz[u]) >= 0) atomicMin(reinterpret_cast<int*>(mm.upper + p), __float_as_int(zz[u]));
+            else atomicMax(reinterpret_cast<unsigned int*>(mm.upper + p), __float_as_uint(zz[u]));
             continue;
           }
-          if (guard) {
-            float n0 = m.nx[p], n1 = m.ny[p], n2 = m.nz[p];
+          if (mm.alpha_n > 0.f) {
+            float n0 = mm.nx[p], n1 = mm.ny[p], n2 = mm.nz[p];
             if (!(isfinite(n0) && isfinite(n1) && isfinite(n2))) { n0 = 0.f; n1 = 0.f; n2 = 1.f; }
             const float rx = __fdiv_rn(R.vx, R.d), ry = __fdiv_rn(R.vy, R.d), rz = __fdiv_rn(R.vz, R.d);
             const float dot = fabsf(__fmaf_rn(rx, n0, __fmaf_rn(ry, n1, __fmul_rn(rz, n2))));
-            if (!(dot > m.alpha_n)) continue;
+            if (!(dot > mm.alpha_n)) continue;
           }
           // many rays graze the same surface cells: skip the atomic when the bit is
-          // already set (marks are only ever set during this kernel)
+          // already set.  Bits are only ever set during this kernel, so a stale read
+          // can only cost a redundant atomic, never a lost mark.
           const uint32_t bit = 1u << (p & 31);
-          if (!(*(volatile uint32_t*)(m.mark + (p >> 5)) & bit)) atomicOr(&m.mark[p >> 5], bit);
+          if (!(mm.mark[p >> 5] & bit)) atomicOr(&mm.mark[p >> 5], bit);
         }
+        const int took = min(qn, kFQ);
+        qh = (qh + took) & (kQ - 1);
+        qn -= took;
+        __syncwarp();
       }
     }
     __syncwarp();
   }
-  // samples per map: a warp sum when the warp's lanes end on one map, else per
-  // lane (no block barrier: warps of a block finish at different times)
-  const int m0 = __shfl_sync(0xffffffffu, smap, 0);
-  if (__all_sync(0xffffffffu, smap == m0 || samples == 0)) {
-    unsigned long long t = samples;
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (lane == 0 && m0 >= 0 && t) atomicAdd(&b.maps[m0].ctl->stats[kStRaySamples], t);
-  } else if (smap >= 0 && samples) {
-    atomicAdd(&b.maps[smap].ctl->stats[kStRaySamples], samples);
-  }
+  if (lane == 0 && smap >= 0 && samples) atomicAdd(&b.maps[smap].ctl->stats[kStRaySamples], samples);
 }
 
 constexpr int kClearThreads = 256;
@@ -254,16 +359,21 @@ static void launch_ray_g(const BatchDev* b, int g, int grid, cudaStream_t s) {
   switch (g) {
     case 1: k_ray<1, kExt><<<grid, kRayThreads, 0, s>>>(b); break;
     case 2: k_ray<2, kExt><<<grid, kRayThreads, 0, s>>>(b); break;
-    case 8: k_ray<8, kExt><<<grid, kRayThreads, 0, s>>>(b); break;
+    case 4: k_ray<4, kExt><<<grid, kRayThreads, 0, s>>>(b); break;
     case 16: k_ray<16, kExt><<<grid, kRayThreads, 0, s>>>(b); break;
     case 32: k_ray<32, kExt><<<grid, kRayThreads, 0, s>>>(b); break;
-    default: k_ray<4, kExt><<<grid, kRayThreads, 0, s>>>(b); break;
+    default: k_ray<8, kExt><<<grid, kRayThreads, 0, s>>>(b); break;
   }
 }
 
-cudaError_t launch_ray(const BatchDev* b, int64_t n_points, int group, bool ext, cudaStream_t s) {
+cudaError_t launch_ray(const BatchDev* b, int64_t n_points, int64_t n_cells, int group, bool ext, cudaStream_t s) {
   if (n_points <= 0) return cudaSuccess;
-  const int g = (group == 1 || group == 2 || group == 4 || group == 8 || group == 16 || group == 32) ? group : 4;
+  // the coarse grids first (grid-stride: any batch up to the capacities)
+  const int64_t blocks = n_cells / (kCoarse * kCoarse) + 1;
+  const int64_t ccap = (int64_t)sm_count() * 8;
+  const int64_t cgrid = (blocks + kCoarseThreads - 1) / kCoarseThreads;
+  k_coarse<<<(int)(cgrid < ccap ? cgrid : ccap), kCoarseThreads, 0, s>>>(b);
+  const int g = (group == 1 || group == 2 || group == 4 || group == 8 || group == 16 || group == 32) ? group : 8;
   const int64_t want = (n_points + kRayThreads - 1) / kRayThreads;  // one 32-ray chunk per warp
   const int64_t cap = (int64_t)sm_count() * 16;
   const int grid = (int)(want < cap ? want : cap);
