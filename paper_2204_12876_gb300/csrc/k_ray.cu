@@ -15,11 +15,11 @@
 // block of kCoarse x kCoarse cells, the largest threshold of the block.  The
 // march cuts each ray into chunks of at most G samples spanning at most
 // kCoarse cells per axis; a chunk's samples lie in the cells between those of
-// its first and last sample (both coordinates and z are monotone in k, and the
-// same rounded arithmetic gives every sample), so when the lower of its end
-// heights is not below the largest threshold of the (at most 2 x 2) blocks it
-// touches, none of its samples can mark a cell and it is skipped -- an exact
-// test, not a heuristic.  Each lane tests its own ray's chunks; the warp
+// its first sample and the next chunk's first sample (both coordinates and z
+// are monotone in k, and the same rounded arithmetic gives every sample), so
+// when the lower of those two heights is not below the largest threshold of
+// the (at most 2 x 2) blocks they span, none of its samples can mark a cell
+// and it is skipped -- an exact test, not a heuristic.  Each lane tests its own ray's chunks; the warp
 // queues the others and marches them G lanes per chunk, one sample per lane.
 //
 // k_clear: after the fusion, every marked cell that holds an estimate and was
@@ -101,8 +101,9 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse(const BatchDev* __res
 template <int G, bool kExt>
 __global__ void __launch_bounds__(kRayThreads, 4) k_ray(const BatchDev* __restrict__ bp) {
   constexpr int kWarps = kRayThreads / 32;
-  constexpr int kU = G >= 4 ? 4 : G;         // samples per lane and march round
-  constexpr int kFQ = kU * 32 / G;           // chunks per march round (at most 32)
+  constexpr int kU = G >= 4 ? 4 : G;         // samples per lane and march round, all of one chunk
+  constexpr int kLPC = G / kU;               // lanes per chunk in the march
+  constexpr int kFQ = 32 / kLPC;             // chunks per march round (at most 32)
   constexpr int kCU = 4;                     // chunks per lane and test round (their loads in flight together)
   constexpr int kQ = 256;                    // queued chunks per warp (a ring)
   static_assert(kQ >= kFQ - 1 + 32 * kCU && kFQ <= 32, "queue capacity");
@@ -168,9 +169,11 @@ __global__ void __launch_bounds__(kRayThreads, 4) k_ray(const BatchDev* __restri
           r.iy = pg.iy;
           r.k_lo = k_lo;
           r.n = k_hi >= k_lo ? k_hi - k_lo + 1 : 0;
-          // chunks span at most kCoarse - 1/2 cells per axis, so they touch at most 2 x 2 blocks
+          // a chunk and the next chunk's first sample span about kCoarse cells per axis at
+          // most, so they touch at most 2 x 2 blocks (a rounding case that touches more is
+          // marched untested)
           const float span = fmaxf(fmaxf(fabsf(r.bx), fabsf(r.by)), 1e-6f);
-          r.cn = (int32_t)fminf((float)G, 1.f + floorf(__fdividef((float)kCoarse - 0.5f, span)));
+          r.cn = (int32_t)fminf((float)G, fmaxf(1.f, floorf(__fdividef((float)kCoarse, span))));
         }
       }
     }
@@ -197,37 +200,45 @@ __global__ void __launch_bounds__(kRayThreads, 4) k_ray(const BatchDev* __restri
     const int32_t nch = r.n > 0 ? (r.n + r.cn - 1) / r.cn : 0;
     int qh = 0, qn = 0;  // queue head and length (warp-uniform)
     for (int32_t c0 = 0; __any_sync(0xffffffffu, c0 < nch); c0 += kCU) {
-      // all loads of the round first (predicated, no branches between them), then the tests
-      bool keep[kCU], test[kCU];
+      // The round's chunks c0 .. c0 + kCU - 1 and their end samples: chunk u is
+      // tested over its own samples and the next chunk's first one (a superset,
+      // so the test stays exact), so neighbouring chunks share an end and its
+      // block.  All loads of the round come first (predicated, no branches
+      // between them), then the tests.
+      const int32_t klast = r.k_lo + r.n - 1;
+      const bool act = c0 < nch;
+      int32_t xc[kCU + 1], yc[kCU + 1], bxs[kCU + 1], bys[kCU + 1];
+      float zc[kCU + 1], ve[kCU + 1];
+#pragma unroll
+      for (int u = 0; u <= kCU; ++u) {
+        const float kf = (float)min(r.k_lo + (c0 + u) * r.cn, klast);
+        xc[u] = cell_floor(__fmaf_rn(kf, r.bx, r.ax));
+        yc[u] = cell_floor(__fmaf_rn(kf, r.by, r.ay));
+        zc[u] = __fmaf_rn(kf, r.bz, r.az);
+        bxs[u] = min(max(xc[u], 0), W - 1) >> kCoarseShift;
+        bys[u] = min(max(yc[u], 0), H - 1) >> kCoarseShift;
+        ve[u] = act ? __ldg(ct + bys[u] * CW + bxs[u]) : __int_as_float(0xff800000);
+      }
+      bool keep[kCU];
       int32_t k0[kCU], cnt[kCU];
-      float mx[kCU], zmin[kCU];
 #pragma unroll
       for (int u = 0; u < kCU; ++u) {
         const int32_t c = c0 + u;
         k0[u] = r.k_lo + c * r.cn;
         cnt[u] = min(r.cn, r.n - c * r.cn);
-        const float k0f = (float)k0[u], k1f = (float)(k0[u] + cnt[u] - 1);
-        const int32_t xa0 = cell_floor(__fmaf_rn(k0f, r.bx, r.ax)), xa1 = cell_floor(__fmaf_rn(k1f, r.bx, r.ax));
-        const int32_t ya0 = cell_floor(__fmaf_rn(k0f, r.by, r.ay)), ya1 = cell_floor(__fmaf_rn(k1f, r.by, r.ay));
-        const int32_t xl = min(xa0, xa1), xh = max(xa0, xa1), yl = min(ya0, ya1), yh = max(ya0, ya1);
+        const int32_t xl = min(xc[u], xc[u + 1]), xh = max(xc[u], xc[u + 1]);
+        const int32_t yl = min(yc[u], yc[u + 1]), yh = max(yc[u], yc[u + 1]);
         // some sample of the chunk may be inside the map
         const bool inside = c < nch && xh >= 0 && xl < W && yh >= 0 && yl < H;
-        const int32_t bxl = max(xl, 0) >> kCoarseShift, bxh = min(xh, W - 1) >> kCoarseShift;
-        const int32_t byl = max(yl, 0) >> kCoarseShift, byh = min(yh, H - 1) >> kCoarseShift;
         // more than 2 x 2 blocks (not for the chunk lengths above): march it untested
-        const bool wide = bxh - bxl > 1 || byh - byl > 1;
-        test[u] = inside && !wide;
-        keep[u] = inside && wide;
-        const float ninf = __int_as_float(0xff800000);
-        const float v0 = test[u] ? __ldg(ct + byl * CW + bxl) : ninf;
-        const float v1 = test[u] ? __ldg(ct + byl * CW + bxh) : ninf;
-        const float v2 = test[u] ? __ldg(ct + byh * CW + bxl) : ninf;
-        const float v3 = test[u] ? __ldg(ct + byh * CW + bxh) : ninf;
-        mx[u] = fmaxf(fmaxf(v0, v1), fmaxf(v2, v3));
-        zmin[u] = fminf(__fmaf_rn(k0f, r.bz, r.az), __fmaf_rn(k1f, r.bz, r.az));
+        const bool wide = abs(bxs[u + 1] - bxs[u]) > 1 || abs(bys[u + 1] - bys[u]) > 1;
+        // the two other corners of the 2 x 2 box, when the chunk crosses a block row and column
+        const bool cross = inside && !wide && bxs[u] != bxs[u + 1] && bys[u] != bys[u + 1];
+        const float o1 = cross ? __ldg(ct + bys[u] * CW + bxs[u + 1]) : __int_as_float(0xff800000);
+        const float o2 = cross ? __ldg(ct + bys[u + 1] * CW + bxs[u]) : __int_as_float(0xff800000);
+        const float mx = fmaxf(fmaxf(ve[u], ve[u + 1]), fmaxf(o1, o2));
+        keep[u] = inside && (wide || fminf(zc[u], zc[u + 1]) < mx);
       }
-#pragma unroll
-      for (int u = 0; u < kCU; ++u) keep[u] = keep[u] || (test[u] && zmin[u] < mx[u]);
       // ---- queue the chunks that may mark a cell
 #pragma unroll
       for (int u = 0; u < kCU; ++u) {
@@ -240,33 +251,35 @@ __global__ void __launch_bounds__(kRayThreads, 4) k_ray(const BatchDev* __restri
       // ---- march the queued chunks, kFQ at a time (all of them after the last test)
       const bool last = !__any_sync(0xffffffffu, c0 + kCU < nch);
       while (qn >= kFQ || (last && qn > 0)) {
-        const int sj = lane % G;
-        // every sample's threshold first (kU gathers in flight), then the marks
+        // lane: chunk qi, samples sj, sj + kLPC, ...; every threshold first (kU gathers
+        // in flight), then the marks
+        const int qi = lane / kLPC, sj = lane % kLPC;
+        const int2 e = q[(qh + qi) & (kQ - 1)];
+        const int32_t ne = e.x >> 8;
+        const RaySetup& R = wr[e.x & 31];
+        const bool live = qi < qn;
+        const MapDev& mm = b.maps[live ? R.map : 0];
+        const int32_t Wm = mm.W, Hm = mm.H;
+        const float* __restrict__ tm = mm.thr;
+        const float ax = R.ax, bx = R.bx, ay = R.ay, by = R.by, az = R.az, bz = R.bz;
+        const int32_t rix = R.ix, riy = R.iy;
         int32_t pl[kU];
         float zz[kU], th[kU];
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
-          const int qi = u * (32 / G) + lane / G;
-          const int2 e = q[(qh + qi) & (kQ - 1)];
-          const bool live = qi < qn && sj < (e.x >> 8);
-          const RaySetup& R = wr[e.x & 31];
-          const MapDev& mm = b.maps[live ? R.map : 0];
-          const int32_t Wm = mm.W, Hm = mm.H;
-          const float* __restrict__ tm = mm.thr;
-          const float kf = (float)(e.y + sj);
-          const int32_t cx = cell_floor(__fmaf_rn(kf, R.bx, R.ax));
-          const int32_t cy = cell_floor(__fmaf_rn(kf, R.by, R.ay));
-          const bool ok = live && (uint32_t)cx < (uint32_t)Wm && (uint32_t)cy < (uint32_t)Hm && !(cx == R.ix && cy == R.iy);
-          zz[u] = __fmaf_rn(kf, R.bz, R.az);
+          const int32_t j = sj + u * kLPC;
+          const float kf = (float)(e.y + j);
+          const int32_t cx = cell_floor(__fmaf_rn(kf, bx, ax));
+          const int32_t cy = cell_floor(__fmaf_rn(kf, by, ay));
+          const bool ok = live && j < ne && (uint32_t)cx < (uint32_t)Wm && (uint32_t)cy < (uint32_t)Hm &&
+                          !(cx == rix && cy == riy);
+          zz[u] = __fmaf_rn(kf, bz, az);
           pl[u] = cy * Wm + cx;  // logical index
           th[u] = ok ? __ldg(tm + pl[u]) : __int_as_float(0xff800000);  // -inf: never below
         }
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
           if (!(zz[u] < th[u])) continue;  // the common case, and every sample not taken
-          const RaySetup& R = wr[q[(qh + u * (32 / G) + lane / G) & (kQ - 1)].x & 31];
-          const MapDev& mm = b.maps[R.map];
-          const int32_t Wm = mm.W, Hm = mm.H;
           // physical cell of the sample (ring-buffer layout of the map layers)
           const int32_t cy = pl[u] / Wm, cx = pl[u] - cy * Wm;
           int32_t px = cx + mm.ox;
