@@ -527,6 +527,26 @@ def run_batched(args, em, torch, dev, barrier, max_over_ranks, world):
     total_ms = sum(v[0] for v in prof.values() if v[1])
     kernels = {em.KERNEL_NAMES[k]: {"ms_per_launch": round(v[0] / v[1], 5), "share": round(v[0] / total_ms, 4)}
                for k, v in prof.items() if v[1]}
+    # the same batch in one persistent launch per update (EM_BATCH_PERSISTENT), same tuning, fresh maps
+    xmaps = fleet()
+    xbatch = em.Batch(max_maps=64, max_clouds=64, max_points=pts_step, max_cells=max_cells, graph=True, device=dev,
+                      persistent=True)
+    xbatch.set_tuning(**tuning)
+    xpairs = [(m, p, q) for m, (p, q) in zip(xmaps, clouds)]
+    for _ in range(args.warmup):
+        xbatch.update(xpairs)
+    barrier()
+    e0.record()
+    for _ in range(K):
+        xbatch.update(xpairs)
+    e1.record()
+    barrier()
+    xsec = max_over_ranks(e0.elapsed_time(e1) / 1e3)
+    xbatch.profile(True)
+    xbatch.update(xpairs)
+    xprof = xbatch.profile_read()
+    xbatch.profile(False)
+    xbatch.close()
     # plain comparison: 64 sequential em_update on a second set of maps
     pmaps = fleet()
     for _ in range(args.warmup):
@@ -540,12 +560,17 @@ def run_batched(args, em, torch, dev, barrier, max_over_ranks, world):
     e1.record()
     barrier()
     psec = max_over_ranks(e0.elapsed_time(e1) / 1e3)
-    for m in maps + pmaps:
+    for m in maps + pmaps + xmaps:
         m.close()
     batch.close()
     return {"workload": "64 maps, side U{100..500} cells @ 0.04 m, 10k..400k points each, random point order; "
                         "fusion, outlier gate and visibility ray march (step 0.04 m)",
-            "form": "one kernel sequence over every map, replayed from a captured CUDA graph",
+            "form": "one kernel sequence over every map, replayed from a captured CUDA graph (the default form)",
+            "persistent": {"form": "EM_BATCH_PERSISTENT: the update's passes in one cooperative launch with grid "
+                                   "barriers (stencils as kernels of their own), replayed from a captured CUDA graph",
+                           "value": pts_step * K * world / xsec, "unit": "points/s", "ms_per_step": xsec / K * 1e3,
+                           "kernels": {em.KERNEL_NAMES[k]: {"ms_per_launch": round(v[0] / v[1], 5)}
+                                       for k, v in xprof.items() if v[1]}},
             "points_per_step": pts_step, "value": pts_step * K * world / sec, "unit": "points/s",
             "ms_per_step": sec / K * 1e3, "updates_per_s": 64 * K * world / sec, "tuning": tuning,
             "ray_samples_per_step": samples,

@@ -237,6 +237,7 @@ enum {
   EM_PROF_INPAINT,
   EM_PROF_DRIFT,       /* k_drift: drift compensation of the estimates (and the ray thresholds) */
   EM_PROF_OVERLAP,     /* k_overlap: overlap clearance near the robot */
+  EM_PROF_PERSIST,     /* k_persist: the passes of a batched update in one launch (EM_BATCH_PERSISTENT) */
   EM_PROF_SLOTS
 };
 int em_profile(em_map* map, int enable);
@@ -254,7 +255,23 @@ int em_profile_read(em_map* map, double* ms, int64_t* launches);
  * are sized from the capacities; actual sizes are read from the descriptor). */
 typedef struct em_batch em_batch;
 
-enum { EM_BATCH_GRAPH = 1u << 0 };
+/* EM_BATCH_PERSISTENT: one cooperative launch of all blocks that fit on the
+ * device at once runs the passes of the update (transform, binning, grouping,
+ * gate, fusion, ray march, removal) over every map, with grid-wide barriers
+ * between them, instead of one kernel per pass (the normals, smoothing and
+ * in-painting stencils stay kernels of their own).  Every barrier wait is
+ * bounded (EM_PERSIST_WAIT_MS): a wait that runs out gives EM_ERR_TIMEOUT at
+ * the maps' next em_sync.  Batches with a drift-compensated map, and devices
+ * that cannot run the launch, use the kernel sequence.  Same results either
+ * way, bit for bit. */
+enum { EM_BATCH_GRAPH = 1u << 0, EM_BATCH_PERSISTENT = 1u << 1 };
+enum { EM_PERSIST_WAIT_MS = 1000 };
+
+/* The bounded device-side wait of the persistent launch, on a word that
+ * nothing sets, for wait_us microseconds: EM_ERR_TIMEOUT when the wait ran
+ * out as it must (and the device is still usable), EM_OK if it did not, or
+ * another error.  A check of the wait itself; synchronous. */
+int em_wait_selftest(int device, int32_t wait_us);
 
 /* Launch shapes picked by the autotuner (or set by hand).  None of them
  * changes a result: every shape gives the same maps bit for bit. */

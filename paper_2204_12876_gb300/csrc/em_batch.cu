@@ -135,30 +135,47 @@ int prof_collect(em_batch* b) {
 cudaError_t launch_sequence(em_batch* b, const BatchDev* bd, int64_t grid_points, int64_t grid_cells,
                             const GraphKey& k, cudaStream_t s, em_batch* prof = nullptr) {
   cudaError_t e = cudaSuccess;
-  e = timed(prof, EM_PROF_COUNT, s, [&] { return launch_bin(bd, grid_points, grid_cells, k.ext, s); });
-  if (e == cudaSuccess && k.drift) e = timed(prof, EM_PROF_DRIFT, s, [&] { return launch_drift(bd, grid_points, grid_cells, k.ext, s); });
-  if (grid_points > 0) {
-    auto ray = [&](cudaStream_t rs) {
-      return timed(prof, EM_PROF_RAY, rs, [&] { return launch_ray(bd, grid_points, grid_cells, k.t.ray_group, k.ext, rs); });
-    };
-    auto rest = [&] {
-      cudaError_t r = timed(prof, EM_PROF_ALLOC, s, [&] { return launch_alloc(bd, grid_cells, s); });
-      if (r == cudaSuccess) r = timed(prof, EM_PROF_SCATTER, s, [&] { return launch_scatter(bd, grid_points, k.ext, s); });
-      if (r == cudaSuccess) r = timed(prof, EM_PROF_FUSE, s, [&] { return launch_fuse(bd, grid_cells, k.t.fuse_chunk, s); });
-      return r;
-    };
-    if (e == cudaSuccess) {
-      if (k.ray && !k.upper) {
-        e = launch_beside(s, b->side, b->fork_ev, b->join_ev, ray, rest);
-      } else {
-        if (k.ray) e = ray(s);
-        if (e == cudaSuccess) e = rest();
-      }
+  // EM_BATCH_PERSISTENT: the update's passes in one launch (k_persist.cu), when
+  // the device can run it and no map needs the drift compensation
+  bool persisted = false;
+  if ((b->flags & EM_BATCH_PERSISTENT) && !k.drift) {
+    e = timed(prof, EM_PROF_PERSIST, s, [&] { return launch_persist(bd, k.t.ray_group, k.ext, EM_PERSIST_WAIT_MS, s); });
+    persisted = e != cudaErrorNotSupported;
+    if (!persisted) {
+      cudaGetLastError();
+      e = cudaSuccess;
     }
   }
-  if (e == cudaSuccess) e = timed(prof, EM_PROF_CLEAR, s, [&] { return launch_clear(bd, grid_cells, s); });
-  if (e == cudaSuccess && k.overlap)
-    e = timed(prof, EM_PROF_OVERLAP, s, [&] { return launch_overlap(bd, grid_cells, s); });
+  if (!persisted) {
+    e = timed(prof, EM_PROF_COUNT, s, [&] { return launch_bin(bd, grid_points, grid_cells, k.ext, s); });
+    if (e == cudaSuccess && k.drift)
+      e = timed(prof, EM_PROF_DRIFT, s, [&] { return launch_drift(bd, grid_points, grid_cells, k.ext, s); });
+    if (grid_points > 0) {
+      auto ray = [&](cudaStream_t rs) {
+        return timed(prof, EM_PROF_RAY, rs,
+                     [&] { return launch_ray(bd, grid_points, grid_cells, k.t.ray_group, k.ext, rs); });
+      };
+      auto rest = [&] {
+        cudaError_t r = timed(prof, EM_PROF_ALLOC, s, [&] { return launch_alloc(bd, grid_cells, s); });
+        if (r == cudaSuccess)
+          r = timed(prof, EM_PROF_SCATTER, s, [&] { return launch_scatter(bd, grid_points, k.ext, s); });
+        if (r == cudaSuccess)
+          r = timed(prof, EM_PROF_FUSE, s, [&] { return launch_fuse(bd, grid_cells, k.t.fuse_chunk, s); });
+        return r;
+      };
+      if (e == cudaSuccess) {
+        if (k.ray && !k.upper) {
+          e = launch_beside(s, b->side, b->fork_ev, b->join_ev, ray, rest);
+        } else {
+          if (k.ray) e = ray(s);
+          if (e == cudaSuccess) e = rest();
+        }
+      }
+    }
+    if (e == cudaSuccess) e = timed(prof, EM_PROF_CLEAR, s, [&] { return launch_clear(bd, grid_cells, s); });
+    if (e == cudaSuccess && k.overlap)
+      e = timed(prof, EM_PROF_OVERLAP, s, [&] { return launch_overlap(bd, grid_cells, s); });
+  }
   if (e == cudaSuccess && (k.stencils & EM_F_NORMALS))
     e = timed(prof, EM_PROF_NORMALS, s, [&] { return launch_normals(bd, grid_cells, s); });
   if (e == cudaSuccess && (k.stencils & (EM_F_SMOOTH | EM_F_MEDIAN | EM_F_GAUSS)))
@@ -283,6 +300,7 @@ int prepare(em_batch* b, em_map* const* maps, const em_cloud* clouds, int32_t co
   bd->split_done = b->split_done;
   bd->split_slots = b->split_slots;
   bd->heavy_thresh = tune.big_thresh * 16;
+  bd->passes = (key.ray ? kPassRay : 0u) | (key.overlap ? kPassOverlap : 0u);
   bd->fuse_threads = tune.fuse_chunk;
   // upload header + maps, and the clouds at their fixed offset
   cudaError_t e = cudaMemcpyAsync(db, hb, sizeof(BatchDev) + (size_t)nm * sizeof(MapDev), cudaMemcpyHostToDevice, s);
@@ -307,6 +325,51 @@ void finish(em_batch* b, const Prepared& p, cudaStream_t s) {
   cudaEventRecord(b->ev[p.slot], s);
 }
 
+// A captured sequence is one chain of kernel nodes.  Let the ray march
+// (k_coarse -> k_ray) hang off the node before it and join again at k_clear, so
+// it runs beside k_alloc -> k_scatter -> k_fuse (the ray march reads only the
+// ray thresholds and the points and writes only the marks, which k_clear reads).
+// Anything but the expected chain is left as it is.  False when an edit failed
+// half way (the graph must not be used).
+bool overlap_ray_march(cudaGraph_t g) {
+  cudaGraphNode_t root = nullptr;
+  size_t n = 0;
+  if (cudaGraphGetRootNodes(g, nullptr, &n) != cudaSuccess || n != 1) return true;
+  if (cudaGraphGetRootNodes(g, &root, &n) != cudaSuccess) return true;
+  std::vector<cudaGraphNode_t> chain;
+  for (cudaGraphNode_t cur = root; cur && chain.size() < 64;) {
+    chain.push_back(cur);
+    size_t nd = 0;
+    if (cudaGraphNodeGetDependentNodes(cur, nullptr, nullptr, &nd) != cudaSuccess || nd > 1) return true;
+    cudaGraphNode_t next = nullptr;
+    if (nd == 1 && cudaGraphNodeGetDependentNodes(cur, &next, nullptr, &nd) != cudaSuccess) return true;
+    cur = nd == 1 ? next : nullptr;
+  }
+  auto fn = [](cudaGraphNode_t node) -> const void* {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(node, &t) != cudaSuccess || t != cudaGraphNodeTypeKernel) return nullptr;
+    cudaKernelNodeParams kp = {};
+    if (cudaGraphKernelNodeGetParams(node, &kp) != cudaSuccess) return nullptr;
+    return kp.func;
+  };
+  for (size_t i = 1; i + 5 < chain.size(); ++i) {
+    if (fn(chain[i]) != coarse_kernel()) continue;
+    // chain: prev -> coarse -> ray -> alloc -> scatter -> fuse -> clear
+    if (fn(chain[i + 2]) != alloc_kernel() || !is_fuse_kernel(fn(chain[i + 4])) || fn(chain[i + 5]) != clear_kernel())
+      return true;
+    cudaGraphNode_t prev = chain[i - 1], ray = chain[i + 1], alloc = chain[i + 2], clear = chain[i + 5];
+    if (cudaGraphRemoveDependencies(g, &ray, &alloc, nullptr, 1) != cudaSuccess) {
+      cudaGetLastError();
+      return true;  // nothing changed
+    }
+    const bool ok = cudaGraphAddDependencies(g, &prev, &alloc, nullptr, 1) == cudaSuccess &&
+                    cudaGraphAddDependencies(g, &ray, &clear, nullptr, 1) == cudaSuccess;
+    if (!ok) cudaGetLastError();
+    return ok;
+  }
+  return true;
+}
+
 int run_graph(em_batch* b, const Prepared& p, cudaStream_t s) {
   if (!b->graph[p.slot] || !(b->graph_key[p.slot] == p.key)) {
     if (b->graph[p.slot]) {
@@ -325,6 +388,11 @@ int run_graph(em_batch* b, const Prepared& p, cudaStream_t s) {
       if (g) cudaGraphDestroy(g);
       cudaGetLastError();
       EB_TRY(launch_sequence(b, p.bd, p.points, p.cells, p.key, s), "launch (capture failed)");
+      return EM_OK;
+    }
+    if (p.key.ray && !p.key.upper && !overlap_ray_march(g)) {  // a half-edited graph is not used
+      cudaGraphDestroy(g);
+      EB_TRY(launch_sequence(b, p.bd, p.points, p.cells, p.key, s), "launch (graph edit failed)");
       return EM_OK;
     }
     cudaGraphExec_t ex = nullptr;
@@ -377,12 +445,37 @@ void release(em_batch* b) {
 
 extern "C" {
 
+int em_wait_selftest(int device, int32_t wait_us) {
+  if (wait_us < 1 || wait_us > 10 * 1000 * 1000) return EM_ERR_INVALID_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return EM_ERR_INVALID_ARG;
+  int rc = set_dev(device);
+  if (rc) return rc;
+  unsigned long long* word = nullptr;  // nothing ever sets it
+  int* flag = nullptr;
+  cudaStream_t s = nullptr;
+  cudaError_t e = cudaMalloc((void**)&word, sizeof(*word));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&flag, sizeof(*flag));
+  if (e == cudaSuccess) e = cudaMemset(word, 0, sizeof(*word));
+  if (e == cudaSuccess) e = cudaMemset(flag, 0, sizeof(*flag));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = launch_wait_selftest(word, flag, wait_us, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  int timed_out = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&timed_out, flag, sizeof(timed_out), cudaMemcpyDeviceToHost);
+  if (s) cudaStreamDestroy(s);
+  cudaFree(word);
+  cudaFree(flag);
+  if (e != cudaSuccess) return map_record_error("em_wait_selftest", e);
+  return timed_out ? EM_ERR_TIMEOUT : EM_OK;
+}
+
 int em_batch_create(int device, int32_t max_maps, int32_t max_clouds, int64_t max_points, int32_t max_cells,
                     uint32_t flags, em_batch** out) {
   if (!out) return EM_ERR_INVALID_ARG;
   *out = nullptr;
   if (max_maps < 1 || max_maps > 65535 || max_clouds < 1 || max_points < 0 || max_points > (int64_t(1) << 31) - 1 ||
-      max_cells < 1 || max_cells > (1 << 26) || (flags & ~EM_BATCH_GRAPH))
+      max_cells < 1 || max_cells > (1 << 26) || (flags & ~(uint32_t)(EM_BATCH_GRAPH | EM_BATCH_PERSISTENT)))
     return EM_ERR_INVALID_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return EM_ERR_INVALID_ARG;

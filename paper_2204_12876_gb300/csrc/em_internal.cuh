@@ -31,8 +31,6 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include <vector>
-
 namespace em {
 
 constexpr int kTile = 1024;  // cells per tile of the cell space
@@ -72,7 +70,13 @@ struct BatchCtl {
   int32_t n_pieces;          // entries of the three work lists of the fusion
   int32_t n_heavy;
   int32_t n_light;
-  int32_t pad[2];
+  int32_t ray_next;          // work counter of the ray march: runs of kRayRun 32-point batches
+  int32_t pad;
+  // grid barrier of the persistent kernel (k_persist.cu): block tickets, blocks
+  // done, and the abort flag of a barrier wait that ran out; zero between launches
+  unsigned long long bar_ticket;
+  int32_t bar_done;
+  int32_t bar_abort;
 };
 
 // A tile with more than heavy_thresh records is split, while accumulator
@@ -101,6 +105,8 @@ constexpr int kMaxHeavy = 1023;
 
 // device-side error word value for a failed internal consistency check (EM_ERR_CUDA)
 constexpr int32_t kErrInternal = -3;
+// ... and for a bounded device-side wait that ran out (EM_ERR_TIMEOUT)
+constexpr int32_t kErrTimeout = -4;
 
 // point status codes (trace)
 enum PointStatus : uint8_t { kPtNonFinite = 0, kPtRange = 1, kPtOutside = 2, kPtFused = 3, kPtRejected = 4, kPtWall = 5 };
@@ -186,7 +192,9 @@ struct BatchDev {
   int32_t max_pieces;
   int32_t heavy_thresh;
   int32_t fuse_threads;  // threads per fusion block: 256 or 512
+  uint32_t passes;       // kPass* bits: optional passes some map of the batch needs
 };
+enum : uint32_t { kPassRay = 1u, kPassOverlap = 2u };
 
 inline int64_t pad_tile(int64_t cells) { return (cells + kTile - 1) / kTile * kTile; }
 // The kernels read points and layers as 4-byte words: a buffer that does not
@@ -197,35 +205,17 @@ inline bool word_aligned(const void* p) { return (reinterpret_cast<uintptr_t>(p)
 int sm_count();
 
 // Launch ray(stream) beside rest() (which launches on s) and join both before
-// the next launch on s.  Outside a graph capture the ray work goes to the side
-// stream between two events; while s is being captured it stays on s and the
-// capture's dependency set is edited instead (the ray node hangs off the
-// preceding node, rest() starts from that node too, and the next node depends
-// on both ends), so a capture never spans a second stream.
+// the next launch on s: the ray work goes to the side stream between two
+// events.  While s is being captured into a graph the two run in order on s
+// (a capture never spans a second stream, and nothing edits a capture while
+// it runs; em_batch.cu rearranges its own finished graphs instead).
 template <class Ray, class Rest>
 cudaError_t launch_beside(cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join, Ray ray,
                           Rest rest) {
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   cudaError_t e = cudaStreamIsCapturing(s, &cs);
   if (e != cudaSuccess) return e;
-  if (cs == cudaStreamCaptureStatusActive) {
-    const cudaGraphNode_t* dp = nullptr;
-    size_t nd = 0;
-    e = cudaStreamGetCaptureInfo(s, &cs, nullptr, nullptr, &dp, nullptr, &nd);
-    if (e != cudaSuccess) return e;
-    std::vector<cudaGraphNode_t> before(dp, dp + nd);
-    e = ray(s);
-    if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(s, &cs, nullptr, nullptr, &dp, nullptr, &nd);
-    if (e != cudaSuccess) return e;
-    std::vector<cudaGraphNode_t> after_ray(dp, dp + nd);
-    e = cudaStreamUpdateCaptureDependencies(s, before.data(), nullptr, before.size(), cudaStreamSetCaptureDependencies);
-    if (e == cudaSuccess) e = rest();
-    if (e == cudaSuccess)
-      e = cudaStreamUpdateCaptureDependencies(s, after_ray.data(), nullptr, after_ray.size(),
-                                              cudaStreamAddCaptureDependencies);
-    return e;
-  }
-  if (cs != cudaStreamCaptureStatusNone || !side) {  // an invalidated capture (or no side stream): in order
+  if (cs != cudaStreamCaptureStatusNone || !side) {
     e = ray(s);
     return e == cudaSuccess ? rest() : e;
   }
@@ -240,6 +230,12 @@ cudaError_t launch_beside(cudaStream_t s, cudaStream_t side, cudaEvent_t fork, c
   return e == cudaSuccess ? je : e;
 }
 
+// The kernels a captured sequence is rearranged by (em_batch.cu).
+const void* coarse_kernel();
+const void* alloc_kernel();
+const void* clear_kernel();
+bool is_fuse_kernel(const void* f);
+
 // ---- launchers (each returns cudaGetLastError() of its launches)
 // ext: some map of the batch uses the exclusion area or the upper-bound layer
 cudaError_t launch_bin(const BatchDev* b, int64_t n_points, int64_t n_cells, bool ext, cudaStream_t s);
@@ -250,6 +246,14 @@ cudaError_t launch_alloc(const BatchDev* b, int64_t n_cells, cudaStream_t s);
 cudaError_t launch_scatter(const BatchDev* b, int64_t n_points, bool ext, cudaStream_t s);
 cudaError_t launch_fuse(const BatchDev* b, int64_t n_cells, int threads, cudaStream_t s);
 cudaError_t launch_clear(const BatchDev* b, int64_t n_cells, cudaStream_t s);
+// The whole update but the drift compensation and the stencils (count, coarse
+// grids, tile ranges, scatter, ray march, fusion, removal, overlap clearance)
+// in one cooperative launch with grid barriers; barrier waits are bounded by
+// wait_ms.  cudaErrorNotSupported when the device cannot run it.
+cudaError_t launch_persist(const BatchDev* b, int group, bool ext, int wait_ms, cudaStream_t s);
+// The bounded wait of the persistent kernel on a word that nothing sets: one
+// block, budget wait_us; *timed_out (device memory) becomes 1 when it runs out.
+cudaError_t launch_wait_selftest(const unsigned long long* word, int* timed_out, int wait_us, cudaStream_t s);
 cudaError_t launch_overlap(const BatchDev* b, int64_t n_cells, cudaStream_t s);
 cudaError_t launch_normals(const BatchDev* b, int64_t n_cells, cudaStream_t s);
 cudaError_t launch_smooth(const BatchDev* b, int64_t n_cells, cudaStream_t s);
@@ -323,12 +327,19 @@ __device__ __forceinline__ int find_map_cell(const MapDev* maps, int n_maps, int
   return lo;
 }
 
+// The blocks that share a pass: a kernel's own grid, or the blocks of the
+// persistent kernel (k_persist.cu) that the pass runs on.
+struct Grid {
+  int bid, nb;
+};
+__device__ __forceinline__ Grid own_grid() { return Grid{(int)blockIdx.x, (int)gridDim.x}; }
+
 // Iterate over the tiles of the cell space: for each tile the map it lies in
 // (block-uniform) and the tile's first physical cell.  body(m, map, p0, count).
 template <class F>
-__device__ __forceinline__ void for_each_tile(const struct BatchDev& b, F body) {
+__device__ __forceinline__ void for_each_tile(const struct BatchDev& b, Grid gr, F body) {
   const int64_t n_tiles = b.n_cells / kTile;
-  for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+  for (int64_t t = gr.bid; t < n_tiles; t += gr.nb) {
     const int64_t g0 = t * kTile;
     const int mi = find_map_cell(b.maps, b.n_maps, g0);
     const MapDev& m = b.maps[mi];
@@ -338,6 +349,10 @@ __device__ __forceinline__ void for_each_tile(const struct BatchDev& b, F body) 
     const int32_t cnt = (int32_t)(ncell - p0 < kTile ? ncell - p0 : kTile);
     body(m, mi, (int32_t)p0, cnt);
   }
+}
+template <class F>
+__device__ __forceinline__ void for_each_tile(const struct BatchDev& b, F body) {
+  for_each_tile(b, own_grid(), body);
 }
 
 }  // namespace em

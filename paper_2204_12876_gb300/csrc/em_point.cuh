@@ -9,6 +9,8 @@
 
 namespace em {
 
+constexpr unsigned kFull = 0xffffffffu;  // all lanes of a warp
+
 struct PointGeom {
   float vx, vy, vz;  // R * p_s: sensor-to-point vector in the map frame
   float x, y, z;     // p_m = R * p_s + t
@@ -117,22 +119,28 @@ struct MapCounters {
   unsigned long long v[4] = {0, 0, 0, 0};
 };
 
-__device__ __forceinline__ void flush_counters(const BatchDev& b, MapCounters& mc, const int* idx, int n) {
-  __shared__ int s_map;
-  __shared__ unsigned long long s_sum[4];
-  if (threadIdx.x == 0) s_map = mc.map;
-  if (threadIdx.x < 4) s_sum[threadIdx.x] = 0;
+// shared memory of flush_counters (the caller's)
+struct FlushSmem {
+  int map;
+  unsigned long long sum[4];
+};
+
+__device__ __forceinline__ void flush_counters(const BatchDev& b, MapCounters& mc, const int* idx, int n,
+                                               FlushSmem& fs) {
+  if (threadIdx.x == 0) fs.map = mc.map;
+  if (threadIdx.x < 4) fs.sum[threadIdx.x] = 0;
   __syncthreads();
-  const bool uniform = __syncthreads_and(mc.map == s_map || mc.map < 0);
+  const bool uniform = __syncthreads_and(mc.map == fs.map || mc.map < 0);
   if (uniform) {
     for (int k = 0; k < n; ++k) {
       unsigned long long v = mc.v[k];
       for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if ((threadIdx.x & 31) == 0 && v) atomicAdd(&s_sum[k], v);
+      if ((threadIdx.x & 31) == 0 && v) atomicAdd(&fs.sum[k], v);
     }
     __syncthreads();
-    if ((int)threadIdx.x < n && s_map >= 0 && s_sum[threadIdx.x])
-      atomicAdd(&b.maps[s_map].ctl->stats[idx[threadIdx.x]], s_sum[threadIdx.x]);
+    if ((int)threadIdx.x < n && fs.map >= 0 && fs.sum[threadIdx.x])
+      atomicAdd(&b.maps[fs.map].ctl->stats[idx[threadIdx.x]], fs.sum[threadIdx.x]);
+    __syncthreads();  // the shared sums are free again
   } else if (mc.map >= 0) {
     for (int k = 0; k < n; ++k)
       if (mc.v[k]) atomicAdd(&b.maps[mc.map].ctl->stats[idx[k]], mc.v[k]);

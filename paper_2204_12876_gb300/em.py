@@ -24,10 +24,10 @@ LAYER_ELEVATION, LAYER_VARIANCE, LAYER_TIME = 1, 2, 4
 LAYER_NORMAL_X, LAYER_NORMAL_Y, LAYER_NORMAL_Z = 8, 16, 32
 LAYER_SMOOTH, LAYER_INPAINT, LAYER_VALID, LAYER_VARIANCE_NOW, LAYER_UPPER = 64, 128, 256, 512, 1024
 PROF_SLOTS = ("count", "ray", "alloc", "scatter", "fuse", "clear", "normals", "smooth", "inpaint", "drift",
-              "overlap")
+              "overlap", "persist")
 KERNEL_NAMES = {"count": "k_count", "ray": "k_ray", "alloc": "k_alloc", "scatter": "k_scatter", "fuse": "k_fuse",
                 "clear": "k_clear", "normals": "k_normals", "smooth": "k_smooth", "inpaint": "k_inpaint",
-                "drift": "k_drift", "overlap": "k_overlap"}
+                "drift": "k_drift", "overlap": "k_overlap", "persist": "k_persist"}
 LAYER_NAMES = {LAYER_ELEVATION: "h", LAYER_VARIANCE: "var", LAYER_TIME: "t_last", LAYER_NORMAL_X: "nx",
                LAYER_NORMAL_Y: "ny", LAYER_NORMAL_Z: "nz", LAYER_SMOOTH: "smooth", LAYER_INPAINT: "inpaint",
                LAYER_VALID: "valid", LAYER_VARIANCE_NOW: "var_now", LAYER_UPPER: "upper"}
@@ -351,6 +351,7 @@ def update_noalloc(params: Params, h, var, t_last, clouds, t_now: int, shift=(0,
 
 
 BATCH_GRAPH = 1
+BATCH_PERSISTENT = 2
 
 
 class _Tuning(ctypes.Structure):
@@ -367,6 +368,7 @@ def _bind_batch():
         "em_batch_get_tuning": ([vp, ctypes.POINTER(_Tuning)], ctypes.c_int),
         "em_batch_autotune": ([vp, ctypes.POINTER(vp), ctypes.POINTER(_Cloud), i32, vp, i32,
                                ctypes.POINTER(_Tuning)], ctypes.c_int),
+        "em_wait_selftest": ([ctypes.c_int, i32], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -377,14 +379,21 @@ def _bind_batch():
 _bind_batch()
 
 
+def wait_selftest(device: int = 0, wait_us: int = 20000) -> int:
+    """em_wait_selftest: the persistent launch's bounded wait on a word that nothing
+    sets; returns the status code (EM_ERR_TIMEOUT when the wait ran out, as it must)."""
+    return int(lib.em_wait_selftest(int(device), int(wait_us)))
+
+
 class Batch:
     """em_batch: many maps updated by one kernel sequence (optionally one CUDA graph launch)."""
 
     def __init__(self, max_maps: int, max_clouds: int, max_points: int, max_cells: int, graph: bool = True,
-                 device: int = 0):
+                 device: int = 0, persistent: bool = False):
         h = ctypes.c_void_p()
+        flags = (BATCH_GRAPH if graph else 0) | (BATCH_PERSISTENT if persistent else 0)
         _check(lib.em_batch_create(int(device), int(max_maps), int(max_clouds), int(max_points), int(max_cells),
-                                   BATCH_GRAPH if graph else 0, ctypes.byref(h)), "em_batch_create")
+                                   flags, ctypes.byref(h)), "em_batch_create")
         self._h = h
         self.device = device
 

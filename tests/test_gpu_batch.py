@@ -152,7 +152,8 @@ def test_launch_shapes_give_identical_maps(em, graph):
                 assert a[k] == b[k], k
 
 
-def test_batched_config_sizes_vs_oracle(em):
+@pytest.mark.parametrize("persistent", [False, True])
+def test_batched_config_sizes_vs_oracle(em, persistent):
     """One graph-launched batch over 8 maps drawn from the 64-map configuration
     (sides 100 to 500 cells, 10k to 400k points in random order, the ray march
     on, one map with normals, smoothing and in-painting), each over a seeded
@@ -179,7 +180,7 @@ def test_batched_config_sizes_vs_oracle(em):
         clouds.append((pts, pose))
         pairs.append((m, dev(pts), pose))
     batch = em.Batch(max_maps=8, max_clouds=8, max_points=sum(len(p) for p, _ in clouds), max_cells=500 * 500,
-                     graph=True)
+                     graph=True, persistent=persistent)
     batch.update(pairs)
     torch.cuda.synchronize()
     for j, (m, om) in enumerate(zip(maps, oms)):
@@ -230,3 +231,74 @@ def test_split_tiles_and_slot_overflow_give_identical_maps(em):
         assert_same([st0], [st])
         for k in ("points_accepted", "points_rejected", "points_wall", "cells_updated"):
             assert stats0[k] == stats[k], k
+
+
+def _persistent_case(em, seed, extra_flags=0, overlap=False):
+    maps, pairs = make_maps(em, seed=seed)
+    half = 0.5 * 100 * 0.04
+    pts, pose = dense_cloud(seed + 1, [(-0.52, 0.36), (0.8, -1.2), (0.0, 0.0)], 3000, half)
+    pairs.append((maps[1], dev(pts), pose))
+    if extra_flags or overlap:  # one more map: the upper-bound layer and / or the overlap clearance
+        P = dict(BASE, width=90, height=70, ray_step=0.04, flags=extra_flags,
+                 overlap_radius=0.6 if overlap else 0.0, overlap_dz=0.3 if overlap else 0.0)
+        m = em.Map(em.Params(**P))
+        parity.prior_to_gpu(m, synth.random_prior(seed=seed + 7, width=90, height=70, t_now=5))
+        maps.append(m)
+        c, q = synth.scattered_cloud(seed + 8, 20000, 0.5 * 90 * 0.04, nan_frac=0.02)
+        pairs.append((m, dev(c), q))
+    return maps, pairs
+
+
+@pytest.mark.parametrize("graph", [False, True])
+@pytest.mark.parametrize("extra", ["plain", "upper_overlap"])
+def test_persistent_launch_equals_sequence(em, graph, extra):
+    """The batched update in one persistent launch (grid barriers between the
+    passes) gives the maps and statistics of the kernel sequence bit for bit:
+    uneven maps, two clouds for one map, cells with thousands of records, ray
+    steps of one to two and a half cells, and the upper-bound layer and the
+    overlap clearance."""
+    flags = 32 if extra == "upper_overlap" else 0
+    results = []
+    for persistent in (False, True):
+        maps, pairs = _persistent_case(em, 500, extra_flags=flags, overlap=extra == "upper_overlap")
+        batch = em.Batch(max_maps=8, max_clouds=16, max_points=400000, max_cells=200 * 200, graph=graph,
+                         persistent=persistent)
+        for _ in range(3):  # the graph replays from the second round
+            batch.update(pairs)
+        torch.cuda.synchronize()
+        for m in maps:
+            m.sync()
+        results.append((states(maps), [m.stats() for m in maps], [m.state().get("upper") for m in maps]))
+        batch.close()
+        for m in maps:
+            m.close()
+    (sa, ta, ua), (sb, tb, ub) = results
+    assert_same(sa, sb)
+    for a, b in zip(ta, tb):
+        for k in ("updates", "points_valid", "points_in_map", "points_accepted", "points_rejected", "points_wall",
+                  "cells_updated", "cells_cleared", "ray_samples"):
+            assert a[k] == b[k], k
+    for a, b in zip(ua, ub):
+        if a is not None or b is not None:
+            assert np.array_equal(a, b, equal_nan=True)
+
+
+def test_wait_selftest_times_out_and_device_stays_usable(em):
+    """The persistent launch's bounded wait, on a word that nothing sets, runs
+    out with EM_ERR_TIMEOUT after its budget; the context stays usable (a
+    persistent batch update afterwards gives the sequence's result)."""
+    import time
+    t0 = time.perf_counter()
+    assert em.wait_selftest(0, 20000) == em.EM_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 5.0
+    out = []
+    for persistent in (False, True):
+        maps, pairs = make_maps(em, seed=900)
+        batch = em.Batch(max_maps=8, max_clouds=16, max_points=200000, max_cells=200 * 200, graph=False,
+                         persistent=persistent)
+        batch.update(pairs)
+        for m in maps:
+            m.sync()
+        out.append(states(maps))
+        batch.close()
+    assert_same(out[0], out[1])
