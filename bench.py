@@ -167,12 +167,13 @@ def file_hash(*paths) -> str:
 
 
 CSRC = "paper_2204_12876_gb300/csrc/"
-KERNEL_SOURCES = {"ray": [CSRC + "k_ray.cu", CSRC + "em_point.cuh", CSRC + "em_internal.cuh"],
-                  "count": [CSRC + "k_sort.cu", CSRC + "em_point.cuh", CSRC + "em_internal.cuh"],
-                  "scatter": [CSRC + "k_sort.cu", CSRC + "em_point.cuh", CSRC + "em_internal.cuh"],
-                  "alloc": [CSRC + "k_sort.cu", CSRC + "em_internal.cuh"],
-                  "fuse": [CSRC + "k_fuse.cu", CSRC + "em_point.cuh", CSRC + "em_internal.cuh"],
-                  "clear": [CSRC + "k_ray.cu", CSRC + "em_internal.cuh"]}
+KERNEL_SOURCES = {"ray": [CSRC + "k_ray.cu", CSRC + "ray_pass.cuh", CSRC + "em_point.cuh", CSRC + "em_internal.cuh"],
+                  "count": [CSRC + "k_sort.cu", CSRC + "sort_pass.cuh", CSRC + "em_point.cuh", CSRC + "em_internal.cuh"],
+                  "scatter": [CSRC + "k_sort.cu", CSRC + "sort_pass.cuh", CSRC + "em_point.cuh",
+                              CSRC + "em_internal.cuh"],
+                  "alloc": [CSRC + "k_sort.cu", CSRC + "sort_pass.cuh", CSRC + "em_point.cuh", CSRC + "em_internal.cuh"],
+                  "fuse": [CSRC + "k_fuse.cu", CSRC + "fuse_pass.cuh", CSRC + "em_point.cuh", CSRC + "em_internal.cuh"],
+                  "clear": [CSRC + "k_ray.cu", CSRC + "ray_pass.cuh", CSRC + "em_point.cuh", CSRC + "em_internal.cuh"]}
 
 
 def ncu_traffic(kernel: str, workload: str):
@@ -577,8 +578,50 @@ def run_batched(args, em, torch, dev, barrier, max_over_ranks, world):
             "plain_sequential": {"value": pts_step * K * world / psec, "ms_per_step": psec / K * 1e3},
             "update_roofline": {"bound": "hbm", "algorithmic_bytes": alg, "achieved": alg / (sec / K) / 1e9,
                                 "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
-                                "frac": alg / (sec / K) / 1e9 / hbm},
+                                "frac": alg / (sec / K) / 1e9 / hbm,
+                                "traffic": ncu_step_traffic([k for k in prof if prof[k][1]], "batched_64maps")},
             "kernels": kernels}
+
+
+def run_round(args, em, torch, which):
+    """Profiler workload: one served round (the 32 robots' requests, one batch) or
+    the 64-map batch, as direct launches (no graph): --warmup rounds, then
+    --steps rounds with per-kernel event timing."""
+    import synth
+    if which == "served_round":
+        robots = make_fleet(5)
+        pools = make_pools(5)
+        dp = {k: [(torch.from_numpy(p).cuda(), q) for p, q in v] for k, v in pools.items()}
+        maps = [em.Map(em.Params(**r["params"])) for r in robots]
+        batch = em.Batch(max_maps=N_ROBOTS, max_clouds=N_ROBOTS, max_points=N_ROBOTS * 262144, max_cells=500 * 500,
+                         graph=False)
+
+        def pairs(k):
+            return [(maps[i], *request_cloud(dp, robots, i, k)) for i in range(N_ROBOTS)]
+    else:
+        work = synth.batch_clouds(seed=4, maps=64)
+        maps = [em.Map(em.Params(width=w["side"], height=w["side"], **BATCH_P)) for w in work]
+        cl = [(torch.from_numpy(w["clouds"][0][0]).cuda(), w["clouds"][0][1]) for w in work]
+        batch = em.Batch(max_maps=64, max_clouds=64, max_points=sum(len(w["clouds"][0][0]) for w in work),
+                         max_cells=max(w["side"] ** 2 for w in work), graph=False)
+
+        def pairs(k):
+            return [(m, p, q) for m, (p, q) in zip(maps, cl)]
+    for k in range(args.warmup):
+        batch.update(pairs(k))
+    torch.cuda.synchronize()
+    batch.profile(True)
+    for k in range(args.steps):
+        batch.update(pairs(args.warmup + k))
+    prof = batch.profile_read()
+    batch.profile(False)
+    torch.cuda.synchronize()
+    out = {"workload": which, "rounds": args.steps,
+           "kernels_ms": {em.KERNEL_NAMES[k]: round(v[0] / v[1], 5) for k, v in prof.items() if v[1]}}
+    batch.close()
+    for m in maps:
+        m.close()
+    return out
 
 
 def run_lidar_filters(args, em, torch, dev):
@@ -765,8 +808,10 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=24.0, help="seconds for the three oracle legs together")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--served-only", action="store_true", help="skip the batched and depth-stream sub-results")
-    ap.add_argument("--workload", default="all", choices=["all", "batched", "depth", "lidar"],
-                    help="batched / depth: run only that sub-result (for profiler runs)")
+    ap.add_argument("--workload", default="all",
+                    choices=["all", "batched", "depth", "lidar", "served_round", "batch_round"],
+                    help="run only that sub-result, or one round of the served mix / the 64-map batch as a "
+                         "batch of direct launches (warm-up rounds, then --steps rounds: for profiler runs)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -792,6 +837,8 @@ def main():
 
         if args.workload == "batched":
             res = run_batched(args, em, torch, 0, barrier, lambda x: x, 1)
+        elif args.workload in ("served_round", "batch_round"):
+            res = run_round(args, em, torch, args.workload)
         elif args.workload == "lidar":
             res = run_lidar_filters(args, em, torch, 0)
         else:
