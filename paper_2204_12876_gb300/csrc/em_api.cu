@@ -116,7 +116,7 @@ struct em_map {
   cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   int64_t layer_bytes = 0;
   int64_t work_bytes = 0;
-  int fuse_threads = 256;
+  int fuse_threads = 512;
   int ray_group = 8;
   int heavy_thresh = 256 * 16;
   int64_t points_in = 0;

@@ -80,7 +80,7 @@ struct em_batch {
   unsigned char* desc_dev = nullptr;
   cudaEvent_t ev[kSlots] = {};
   int slot = 0;
-  em_tuning tune{8, 256, 256};
+  em_tuning tune{8, 512, 256};
   cudaStream_t capture_stream = nullptr;
   cudaStream_t side = nullptr;  // the ray march, beside the sort and fusion
   cudaEvent_t fork_ev = nullptr, join_ev = nullptr;

@@ -71,7 +71,7 @@ __device__ __forceinline__ void coarse_pass(const BatchDev& b, Grid gr) {
 
 // Shared memory of the march: the warps' rays and chunk queues.
 constexpr int kRayQ = 256;  // queued chunks per warp (a ring)
-constexpr int kRayRun = 8;   // 32-point batches per take from the work counter
+constexpr int kRayRun = 8;   // 32-point batches per take from the work counter, at most
 struct RaySmem {
   RaySetup ray[kRayThreads];
   int2 q[kRayThreads / 32][kRayQ];  // {ray | samples << 8, first sample}
@@ -94,11 +94,13 @@ __device__ __forceinline__ void ray_pass(const BatchDev& b, Grid gr, RaySmem& S)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   RaySetup* wr = S.ray + warp * 32;
   int2* q = S.q[warp];
-  // warps take runs of kRayRun consecutive 32-point batches from the work
-  // counter (rays of uneven maps differ in length: the counter balances
-  // them); a run mostly lies in one cloud and map (one sample count per map
-  // change below)
+  // warps take runs of consecutive 32-point batches from the work counter
+  // (rays of uneven maps differ in length: the counter balances them); a run
+  // mostly lies in one cloud and map (one sample count per map change below).
+  // Runs are as long as leaves every warp of the grid two of them, at most
+  // kRayRun batches.
   const int64_t n_batches = (b.n_points + 31) / 32;
+  const int64_t run_len = max((int64_t)1, min((int64_t)kRayRun, n_batches / (2 * (int64_t)gr.nb * kWarps)));
   int smap = -1;  // the map of the warp's running sample count (warp-uniform)
   unsigned long long samples = 0;
   int64_t wbase = 0, w_end = 0;
@@ -107,10 +109,10 @@ __device__ __forceinline__ void ray_pass(const BatchDev& b, Grid gr, RaySmem& S)
       int run = 0;
       if (lane == 0) run = atomicAdd(&b.ctl->ray_next, 1);
       run = __shfl_sync(0xffffffffu, run, 0);
-      const int64_t b0 = (int64_t)run * kRayRun;
+      const int64_t b0 = (int64_t)run * run_len;
       if (run < 0 || b0 >= n_batches) break;
       wbase = b0 * 32;
-      w_end = min(b0 + kRayRun, n_batches) * 32;
+      w_end = min(b0 + run_len, n_batches) * 32;
     }
     // ---- set-up: one ray per lane
     RaySetup r;
