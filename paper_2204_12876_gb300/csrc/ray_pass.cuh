@@ -69,13 +69,24 @@ __device__ __forceinline__ void coarse_pass(const BatchDev& b, Grid gr) {
   }
 }
 
-// Shared memory of the march: the warps' rays and chunk queues.
+// Shared memory of the march: the warps' rays, one array per field (lanes
+// reading the fields of different rays hit different banks), and the chunk
+// queues.
 constexpr int kRayQ = 256;  // queued chunks per warp (a ring)
 constexpr int kRayRun = 8;   // 32-point batches per take from the work counter, at most
 struct RaySmem {
-  RaySetup ray[kRayThreads];
+  float ax[kRayThreads], bx[kRayThreads], ay[kRayThreads], by[kRayThreads], az[kRayThreads], bz[kRayThreads];
+  float vx[kRayThreads], vy[kRayThreads], vz[kRayThreads], d[kRayThreads];
+  int32_t ix[kRayThreads], iy[kRayThreads], k_lo[kRayThreads], n[kRayThreads], map[kRayThreads],
+      cn[kRayThreads];
   int2 q[kRayThreads / 32][kRayQ];  // {ray | samples << 8, first sample}
 };
+
+__device__ __forceinline__ void put_ray(RaySmem& S, int t, const RaySetup& r) {
+  S.ax[t] = r.ax; S.bx[t] = r.bx; S.ay[t] = r.ay; S.by[t] = r.by; S.az[t] = r.az; S.bz[t] = r.bz;
+  S.vx[t] = r.vx; S.vy[t] = r.vy; S.vz[t] = r.vz; S.d[t] = r.d;
+  S.ix[t] = r.ix; S.iy[t] = r.iy; S.k_lo[t] = r.k_lo; S.n[t] = r.n; S.map[t] = r.map; S.cn[t] = r.cn;
+}
 
 // Each warp takes 32 consecutive points: every lane sets up one ray (transform,
 // distance, own cell, the k range inside the map box and before the point, its
@@ -92,7 +103,7 @@ __device__ __forceinline__ void ray_pass(const BatchDev& b, Grid gr, RaySmem& S)
   constexpr int kQ = kRayQ;
   static_assert(kQ >= kFQ - 1 + 32 * kCU && kFQ <= 32, "queue capacity");
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  RaySetup* wr = S.ray + warp * 32;
+  const int wb = warp * 32;  // the warp's rays in S
   int2* q = S.q[warp];
   // warps take runs of consecutive 32-point batches from the work counter
   // (rays of uneven maps differ in length: the counter balances them); a run
@@ -183,29 +194,65 @@ __device__ __forceinline__ void ray_pass(const BatchDev& b, Grid gr, RaySmem& S)
         atomicAdd(&b.maps[r.map].ctl->stats[kStRaySamples], t);
       }
     }
-    wr[lane] = r;
-    // ---- this lane's ray: its chunks against the coarse grid, in order
-    const MapDev& m = b.maps[r.map];
-    const float* __restrict__ ct = m.cthr;
-    const int32_t W = m.W, H = m.H, CW = m.CW;
+    put_ray(S, wb + lane, r);
+    __syncwarp();
+    // ---- the chunks of the warp's rays against the coarse grid, kCU consecutive
+    // chunks of one ray per lane and round.  A ray has nq such quads.  When
+    // the rays' lengths differ (points in random order), lanes that each test
+    // only their own ray would idle while the longest ray is tested: the quads
+    // are then dealt out in order across the lanes (quad j of the warp goes to
+    // lane j mod 32 in round j / 32), which the warp does when that saves at
+    // least a quarter of the rounds.
     const int32_t nch = r.n > 0 ? (r.n + r.cn - 1) / r.cn : 0;
+    const int32_t nq = (nch + kCU - 1) / kCU;
+    int32_t qinc = nq;  // inclusive scan of the quads over the lanes
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t t = __shfl_up_sync(0xffffffffu, qinc, o);
+      if (lane >= o) qinc += t;
+    }
+    const int32_t qtot = __shfl_sync(0xffffffffu, qinc, 31);
+    const int32_t qmax = (int32_t)__reduce_max_sync(0xffffffffu, (unsigned)nq);
+    const bool flat = 4 * ((qtot + 31) >> 5) <= 3 * qmax;  // warp-uniform
+    const int32_t rounds = flat ? (qtot + 31) >> 5 : qmax;
     int qh = 0, qn = 0;  // queue head and length (warp-uniform)
-    for (int32_t c0 = 0; __any_sync(0xffffffffu, c0 < nch); c0 += kCU) {
+    for (int32_t it = 0; it < rounds; ++it) {
+      // this lane's quad: ray `src`, chunks c0 .. c0 + kCU - 1
+      int src = lane;
+      int32_t c0 = it * kCU;
+      bool act = it < nq;
+      if (flat) {
+        const int32_t j = it * 32 + lane;
+        int o = 0;  // lanes whose quads all come before quad j: the owner of quad j
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1) {
+          const int32_t v = __shfl_sync(0xffffffffu, qinc, o + s - 1);
+          if (v <= j) o += s;
+        }
+        act = j < qtot;
+        src = o < 32 ? o : 31;
+        c0 = (j - __shfl_sync(0xffffffffu, qinc - nq, src)) * kCU;
+      }
+      const int sr = wb + src;
+      const int32_t k_lo = S.k_lo[sr], n = S.n[sr], cn = S.cn[sr];
+      const float ax = S.ax[sr], bx = S.bx[sr], ay = S.ay[sr], by = S.by[sr], az = S.az[sr], bz = S.bz[sr];
+      const MapDev& m = b.maps[S.map[sr]];
+      const float* __restrict__ ct = m.cthr;
+      const int32_t W = m.W, H = m.H, CW = m.CW;
       // The round's chunks c0 .. c0 + kCU - 1 and their end samples: chunk u is
       // tested over its own samples and the next chunk's first one (a superset,
       // so the test stays exact), so neighbouring chunks share an end and its
       // block.  All loads of the round come first (predicated, no branches
       // between them), then the tests.
-      const int32_t klast = r.k_lo + r.n - 1;
-      const bool act = c0 < nch;
+      const int32_t klast = k_lo + n - 1;
       int32_t xc[kCU + 1], yc[kCU + 1], bxs[kCU + 1], bys[kCU + 1];
       float zc[kCU + 1], ve[kCU + 1];
 #pragma unroll
       for (int u = 0; u <= kCU; ++u) {
-        const float kf = (float)min(r.k_lo + (c0 + u) * r.cn, klast);
-        xc[u] = cell_floor(__fmaf_rn(kf, r.bx, r.ax));
-        yc[u] = cell_floor(__fmaf_rn(kf, r.by, r.ay));
-        zc[u] = __fmaf_rn(kf, r.bz, r.az);
+        const float kf = (float)min(k_lo + (c0 + u) * cn, klast);
+        xc[u] = cell_floor(__fmaf_rn(kf, bx, ax));
+        yc[u] = cell_floor(__fmaf_rn(kf, by, ay));
+        zc[u] = __fmaf_rn(kf, bz, az);
         bxs[u] = min(max(xc[u], 0), W - 1) >> kCoarseShift;
         bys[u] = min(max(yc[u], 0), H - 1) >> kCoarseShift;
         ve[u] = act ? __ldg(ct + bys[u] * CW + bxs[u]) : __int_as_float(0xff800000);
@@ -215,12 +262,12 @@ __device__ __forceinline__ void ray_pass(const BatchDev& b, Grid gr, RaySmem& S)
 #pragma unroll
       for (int u = 0; u < kCU; ++u) {
         const int32_t c = c0 + u;
-        k0[u] = r.k_lo + c * r.cn;
-        cnt[u] = min(r.cn, r.n - c * r.cn);
+        k0[u] = k_lo + c * cn;
+        cnt[u] = min(cn, n - c * cn);
         const int32_t xl = min(xc[u], xc[u + 1]), xh = max(xc[u], xc[u + 1]);
         const int32_t yl = min(yc[u], yc[u + 1]), yh = max(yc[u], yc[u + 1]);
         // some sample of the chunk may be inside the map
-        const bool inside = c < nch && xh >= 0 && xl < W && yh >= 0 && yl < H;
+        const bool inside = act && c * cn < n && xh >= 0 && xl < W && yh >= 0 && yl < H;
         // more than 2 x 2 blocks (not for the chunk lengths above): march it untested
         const bool wide = abs(bxs[u + 1] - bxs[u]) > 1 || abs(bys[u + 1] - bys[u]) > 1;
         // the two other corners of the 2 x 2 box, when the chunk crosses a block row and column
@@ -235,25 +282,26 @@ __device__ __forceinline__ void ray_pass(const BatchDev& b, Grid gr, RaySmem& S)
       for (int u = 0; u < kCU; ++u) {
         const unsigned km = __ballot_sync(0xffffffffu, keep[u]);
         if (keep[u])
-          q[(qh + qn + __popc(km & ((1u << lane) - 1u))) & (kQ - 1)] = make_int2(lane | (cnt[u] << 8), k0[u]);
+          q[(qh + qn + __popc(km & ((1u << lane) - 1u))) & (kQ - 1)] = make_int2(src | (cnt[u] << 8), k0[u]);
         qn += __popc(km);
       }
       __syncwarp();
       // ---- march the queued chunks, kFQ at a time (all of them after the last test)
-      const bool last = !__any_sync(0xffffffffu, c0 + kCU < nch);
+      const bool last = it + 1 >= rounds;
       while (qn >= kFQ || (last && qn > 0)) {
         // lane: chunk qi, samples sj, sj + kLPC, ...; every threshold first (kU gathers
         // in flight), then the marks
         const int qi = lane / kLPC, sj = lane % kLPC;
         const int2 e = q[(qh + qi) & (kQ - 1)];
         const int32_t ne = e.x >> 8;
-        const RaySetup& R = wr[e.x & 31];
-        const bool live = qi < qn && (unsigned)R.map < (unsigned)b.n_maps;
-        const MapDev& mm = b.maps[live ? R.map : 0];
+        const int sr = wb + (e.x & 31);
+        const int32_t rmap = S.map[sr];
+        const bool live = qi < qn && (unsigned)rmap < (unsigned)b.n_maps;
+        const MapDev& mm = b.maps[live ? rmap : 0];
         const int32_t Wm = mm.W, Hm = mm.H;
         const float* __restrict__ tm = mm.thr;
-        const float ax = R.ax, bx = R.bx, ay = R.ay, by = R.by, az = R.az, bz = R.bz;
-        const int32_t rix = R.ix, riy = R.iy;
+        const float ax = S.ax[sr], bx = S.bx[sr], ay = S.ay[sr], by = S.by[sr], az = S.az[sr], bz = S.bz[sr];
+        const int32_t rix = S.ix[sr], riy = S.iy[sr];
         int32_t pl[kU];
         float zz[kU], th[kU];
 #pragma unroll
@@ -288,7 +336,8 @@ __device__ __forceinline__ void ray_pass(const BatchDev& b, Grid gr, RaySmem& S)
           if (mm.alpha_n > 0.f) {
             float n0 = mm.nx[p], n1 = mm.ny[p], n2 = mm.nz[p];
             if (!(isfinite(n0) && isfinite(n1) && isfinite(n2))) { n0 = 0.f; n1 = 0.f; n2 = 1.f; }
-            const float rx = __fdiv_rn(R.vx, R.d), ry = __fdiv_rn(R.vy, R.d), rz = __fdiv_rn(R.vz, R.d);
+            const float rd = S.d[sr];
+            const float rx = __fdiv_rn(S.vx[sr], rd), ry = __fdiv_rn(S.vy[sr], rd), rz = __fdiv_rn(S.vz[sr], rd);
             const float dot = fabsf(__fmaf_rn(rx, n0, __fmaf_rn(ry, n1, __fmul_rn(rz, n2))));
             if (!(dot > mm.alpha_n)) continue;
           }
