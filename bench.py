@@ -716,10 +716,13 @@ def cpu_baseline(robots, pools, budget_s: float = 12.0) -> dict:
     own robots' maps (independent maps run in parallel; ctypes releases the GIL
     during an oracle update); (3) the LiDAR configuration with every per-cell
     filter on one thread over the first 50 updates of its stream (3 scans
-    cycled).  Each leg runs for a third of the budget at most."""
+    cycled); (4) the 64-map batch on every host core, each thread fusing whole
+    maps of it (one update each, fresh maps, in map order).  Each leg runs for a
+    quarter of the budget at most."""
     import oracle
+    import synth
     host_cores = os.cpu_count() or 1
-    leg = budget_s / 3.0
+    leg = budget_s / 4.0
 
     def serve(threads):
         per = [{"pts": 0, "n": 0} for _ in range(threads)]
@@ -759,6 +762,33 @@ def cpu_baseline(robots, pools, budget_s: float = 12.0) -> dict:
         om.update(scans[frames % 3])
         lt += time.perf_counter() - t0
         frames += 1
+    # (4) the 64-map batch: threads take maps in order until the leg's time is up
+    work = synth.batch_clouds(seed=4, maps=64)
+    lock = threading.Lock()
+    nxt = [0]
+    done = {"maps": 0, "pts": 0}
+    t_end = time.perf_counter() + leg
+
+    def bwork():
+        while time.perf_counter() < t_end:
+            with lock:
+                j = nxt[0]
+                nxt[0] += 1
+            if j >= len(work):
+                return
+            w = work[j]
+            om_b = oracle.OracleMap(oracle.Params(**f32params(dict(BATCH_P, width=w["side"], height=w["side"]))))
+            om_b.update(w["clouds"][0])
+            with lock:
+                done["maps"] += 1
+                done["pts"] += len(w["clouds"][0][0])
+    t0 = time.perf_counter()
+    ths = [threading.Thread(target=bwork) for _ in range(host_cores)]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    db = time.perf_counter() - t0
     return {"value": v1, "unit": "points/s", "cores": 1, "host_cores": host_cores, "kind": "oracle",
             "sample": f"{n1} requests of the served mix (robots in turn, {p1} points) in {d1:.1f} s, one thread",
             "all_cores": {"value": vN, "unit": "points/s", "threads": host_cores,
@@ -766,7 +796,11 @@ def cpu_baseline(robots, pools, budget_s: float = 12.0) -> dict:
                                     "each serving its own robots' maps"},
             "lidar_filters": {"ms_per_update": lt / max(1, frames) * 1e3, "updates": frames,
                               "sample": f"first {frames} of 50 updates of the LiDAR configuration (500x500, "
-                                        "normals, box smoothing, in-painting; 3 scans cycled), one thread"}}
+                                        "normals, box smoothing, in-painting; 3 scans cycled), one thread"},
+            "batched_all_cores": {"value": done["pts"] / db, "unit": "points/s", "threads": host_cores,
+                                  "sample": f"{done['maps']} of the 64 maps of the batched configuration "
+                                            f"({done['pts']} points, one update each) in {db:.1f} s, "
+                                            f"{host_cores} threads"}}
 
 
 def run_reference(args, rank: int, world: int):
@@ -813,7 +847,7 @@ def main():
     ap.add_argument("--streams", type=int, default=3, help="batches in flight in the served path")
     ap.add_argument("--batch-maps", type=int, default=16, help="maps per batch in the served path")
     ap.add_argument("--load-seconds", type=float, default=4.0, help="duration of the Poisson-load phase")
-    ap.add_argument("--cpu-budget", type=float, default=24.0, help="seconds for the three oracle legs together")
+    ap.add_argument("--cpu-budget", type=float, default=32.0, help="seconds for the four oracle legs together")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--served-only", action="store_true", help="skip the batched and depth-stream sub-results")
     ap.add_argument("--workload", default="all",

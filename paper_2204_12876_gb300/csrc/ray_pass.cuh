@@ -298,11 +298,11 @@ __device__ __forceinline__ void ray_pass(const BatchDev& b, Grid gr, RaySmem& S)
         const int32_t rmap = S.map[sr];
         const bool live = qi < qn && (unsigned)rmap < (unsigned)b.n_maps;
         const MapDev& mm = b.maps[live ? rmap : 0];
-        const int32_t Wm = mm.W, Hm = mm.H;
+        const int32_t Wm = mm.W, Hm = mm.H, ox = mm.ox, oy = mm.oy;
         const float* __restrict__ tm = mm.thr;
+        uint32_t* __restrict__ mk = mm.mark;
         const float ax = S.ax[sr], bx = S.bx[sr], ay = S.ay[sr], by = S.by[sr], az = S.az[sr], bz = S.bz[sr];
         const int32_t rix = S.ix[sr], riy = S.iy[sr];
-        int32_t pl[kU];
         float zz[kU], th[kU];
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
@@ -313,17 +313,20 @@ __device__ __forceinline__ void ray_pass(const BatchDev& b, Grid gr, RaySmem& S)
           const bool ok = live && j < ne && (uint32_t)cx < (uint32_t)Wm && (uint32_t)cy < (uint32_t)Hm &&
                           !(cx == rix && cy == riy);
           zz[u] = __fmaf_rn(kf, bz, az);
-          pl[u] = cy * Wm + cx;  // logical index
-          th[u] = ok ? __ldg(tm + pl[u]) : __int_as_float(0xff800000);  // -inf: never below
+          th[u] = ok ? __ldg(tm + cy * Wm + cx) : __int_as_float(0xff800000);  // logical index; -inf: never below
         }
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
           if (!(zz[u] < th[u])) continue;  // the common case, and every sample not taken
-          // physical cell of the sample (ring-buffer layout of the map layers)
-          const int32_t cy = pl[u] / Wm, cx = pl[u] - cy * Wm;
-          int32_t px = cx + mm.ox;
+          // the sample's cell again (the same rounded arithmetic as above: no
+          // register holds it through the gathers), then its physical index in
+          // the ring-buffer layout of the map layers
+          const float kf = (float)(e.y + sj + u * kLPC);
+          const int32_t cx = cell_floor(__fmaf_rn(kf, bx, ax));
+          const int32_t cy = cell_floor(__fmaf_rn(kf, by, ay));
+          int32_t px = cx + ox;
           px -= (px >= Wm) ? Wm : 0;
-          int32_t py = cy + mm.oy;
+          int32_t py = cy + oy;
           py -= (py >= Hm) ? Hm : 0;
           const int32_t p = py * Wm + px;
           if (kExt && !isfinite(mm.var[p])) {
@@ -345,7 +348,7 @@ __device__ __forceinline__ void ray_pass(const BatchDev& b, Grid gr, RaySmem& S)
           // already set.  Bits are only ever set during this kernel, so a stale read
           // can only cost a redundant atomic, never a lost mark.
           const uint32_t bit = 1u << (p & 31);
-          if (!(mm.mark[p >> 5] & bit)) atomicOr(&mm.mark[p >> 5], bit);
+          if (!(mk[p >> 5] & bit)) atomicOr(&mk[p >> 5], bit);
         }
         const int took = min(qn, kFQ);
         qh = (qh + took) & (kQ - 1);
