@@ -317,6 +317,14 @@ __device__ __forceinline__ int find_cloud(const CloudDev* cl, int n_clouds, int6
   return lo;
 }
 
+// The same, tried first on cloud `hint` (the cloud of the caller's previous
+// point: passes walk the point space in order, so it usually holds g); an
+// empty cloud never holds g, so the answer is the search's.
+__device__ __forceinline__ int find_cloud(const CloudDev* cl, int n_clouds, int64_t g, int hint) {
+  if ((unsigned)hint < (unsigned)n_clouds && cl[hint].begin <= g && g < cl[hint].begin + cl[hint].n) return hint;
+  return find_cloud(cl, n_clouds, g);
+}
+
 // index of the map whose cell range holds batch cell g (maps sorted by cell_begin)
 __device__ __forceinline__ int find_map_cell(const MapDev* maps, int n_maps, int64_t g) {
   int lo = 0, hi = n_maps - 1;

@@ -183,11 +183,14 @@ __device__ __forceinline__ void load_point(const CloudDev& c, int64_t i, float& 
 // Load the warp's 32 points [wbase, wbase + 32).  When the whole chunk sits in
 // one cloud with 16-byte aligned rows the warp reads it with float4 loads:
 // stride 4 -> one float4 per lane; stride 3 -> 24 float4 staged in shared memory.
+// `hint` is the cloud of the warp's previous chunk (-1: none); it becomes the
+// cloud of this chunk's first point.
 __device__ __forceinline__ int load_warp_points(const BatchDev& b, int64_t wbase, int64_t end, float4* stage,
-                                                float& px, float& py, float& pz) {
+                                                float& px, float& py, float& pz, int& hint) {
   const int lane = threadIdx.x & 31;
   const int64_t g = wbase + lane;
-  const int c0 = find_cloud(b.clouds, b.n_clouds, wbase);
+  const int c0 = find_cloud(b.clouds, b.n_clouds, wbase, hint);
+  hint = c0;
   const CloudDev& cl0 = b.clouds[c0];
   const bool whole = (wbase + 32 <= end) && (wbase + 32 <= cl0.begin + cl0.n);
   int ci = c0;
@@ -210,7 +213,7 @@ __device__ __forceinline__ int load_warp_points(const BatchDev& b, int64_t wbase
       return ci;
     }
   } else if (g < end) {
-    ci = find_cloud(b.clouds, b.n_clouds, g);
+    ci = find_cloud(b.clouds, b.n_clouds, g, c0);
   }
   if (g < end) {
     load_point(b.clouds[ci], g - b.clouds[ci].begin, px, py, pz);

@@ -42,8 +42,11 @@
 
 namespace em {
 
+// Three resident blocks of 512 threads per SM (40 registers; the kernel waits
+// on memory, and 75 % of the warp slots hide more of it than the 50 % that 60
+// registers allow), four of 256 (shared memory allows no more).
 template <int NT>
-__global__ void __launch_bounds__(NT) k_fuse(const BatchDev* __restrict__ bp) {
+__global__ void __launch_bounds__(NT, NT >= 512 ? 3 : 4) k_fuse(const BatchDev* __restrict__ bp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   fuse_pass<NT>(*bp, *reinterpret_cast<TileSmem*>(smem_raw));
 }

@@ -37,12 +37,14 @@ __global__ void __launch_bounds__(kPointThreads) k_drift_sum(const BatchDev* __r
   int dmap = -1;
   long long dh = 0;
   unsigned long long dl = 0, dn = 0;
+  int hint = -1;
   for (int64_t wbase = beg + warp * 32; wbase < end; wbase += kPointThreads) {
-    const int c0 = find_cloud(b.clouds, b.n_clouds, wbase);
+    const int c0 = find_cloud(b.clouds, b.n_clouds, wbase, hint);
+    hint = c0;
     const CloudDev& cl0 = b.clouds[c0];
     if (wbase + 32 <= cl0.begin + cl0.n && b.maps[cl0.map].drift_flat <= 0.f) continue;  // a whole warp without drift
     float px, py, pz;
-    const int ci = load_warp_points(b, wbase, end, stage[warp], px, py, pz);
+    const int ci = load_warp_points(b, wbase, end, stage[warp], px, py, pz, hint);
     const int64_t g = wbase + lane;
     const CloudDev& c = b.clouds[ci];
     const MapDev& m = b.maps[c.map];

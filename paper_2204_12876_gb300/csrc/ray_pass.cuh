@@ -113,6 +113,7 @@ __device__ __forceinline__ void ray_pass(const BatchDev& b, Grid gr, RaySmem& S)
   const int64_t n_batches = (b.n_points + 31) / 32;
   const int64_t run_len = max((int64_t)1, min((int64_t)kRayRun, n_batches / (2 * (int64_t)gr.nb * kWarps)));
   int smap = -1;  // the map of the warp's running sample count (warp-uniform)
+  int hint = -1;  // this lane's cloud in the previous batch
   unsigned long long samples = 0;
   int64_t wbase = 0, w_end = 0;
   for (;;) {
@@ -132,7 +133,8 @@ __device__ __forceinline__ void ray_pass(const BatchDev& b, Grid gr, RaySmem& S)
     r.cn = 1;
     const int64_t g = wbase + lane;
     if (g < b.n_points) {
-      const int ci = find_cloud(b.clouds, b.n_clouds, g);
+      const int ci = find_cloud(b.clouds, b.n_clouds, g, hint);
+      hint = ci;
       const CloudDev& c = b.clouds[ci];
       const MapDev& m = b.maps[c.map];
       r.map = c.map;

@@ -73,9 +73,10 @@ __device__ __forceinline__ void count_pass(const BatchDev& b, Grid gr, PointSmem
   block_range(b.n_points, gr, beg, end);
   MapCounters mc;
   const int idx[2] = {kStValid, kStInMap};
+  int hint = -1;
   for (int64_t wbase = beg + warp * 32; wbase < end; wbase += kPointThreads) {
     float px, py, pz;
-    const int ci = load_warp_points(b, wbase, end, S.stage[warp], px, py, pz);
+    const int ci = load_warp_points(b, wbase, end, S.stage[warp], px, py, pz, hint);
     const int64_t g = wbase + lane;
     const bool live = g < end;
     const CloudDev& c = b.clouds[ci];
@@ -261,7 +262,8 @@ __device__ __forceinline__ void scatter_pass(const BatchDev& b, Grid gr, PointSm
   for (int64_t wbase = ((int64_t)gr.bid * (kPointThreads / 32) + warp) * 32; wbase < end;
        wbase += (int64_t)gr.nb * kPointThreads) {
     float px, py, pz;
-    const int ci = load_warp_points(b, wbase, end, S.stage[warp], px, py, pz);
+    int hint = -1;  // consecutive waves lie far apart in the point space: no cloud to guess
+    const int ci = load_warp_points(b, wbase, end, S.stage[warp], px, py, pz, hint);
     const int64_t g = wbase + lane;
     const bool live = g < end;
     const CloudDev& c = b.clouds[ci];
