@@ -42,16 +42,18 @@
 
 namespace em {
 
-// Three resident blocks of 512 threads per SM (40 registers; the kernel waits
-// on memory, and 75 % of the warp slots hide more of it than the 50 % that 60
-// registers allow), four of 256 (shared memory allows no more).
-template <int NT>
-__global__ void __launch_bounds__(NT, NT >= 512 ? 3 : 4) k_fuse(const BatchDev* __restrict__ bp) {
+// MINB resident blocks per SM.  Updates with many tiles take three blocks of
+// 512 threads (40 registers: the kernel waits on memory, and 75 % of the warp
+// slots hide more of it than the 50 % that 60 registers allow); updates with
+// fewer tiles than three blocks per SM could use take two (60 registers, the
+// faster block); blocks of 256 threads: four (shared memory allows no more).
+template <int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_fuse(const BatchDev* __restrict__ bp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   fuse_pass<NT>(*bp, *reinterpret_cast<TileSmem*>(smem_raw));
 }
 
-template <int NT>
+template <int NT, int MINB>
 static cudaError_t launch_fuse_t(const BatchDev* b, int64_t n_cells, cudaStream_t s) {
   // per device, once: the shared-memory limit above the static 48 KB, and the
   // resident blocks per SM (the host queries cost tens of microseconds)
@@ -61,11 +63,11 @@ static cudaError_t launch_fuse_t(const BatchDev* b, int64_t n_cells, cudaStream_
   int resident = 1;
   if (dev >= 0 && dev < 64) {
     if (!per_sm[dev]) {
-      cudaError_t e = cudaFuncSetAttribute(k_fuse<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      cudaError_t e = cudaFuncSetAttribute(k_fuse<NT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)sizeof(TileSmem));
       if (e != cudaSuccess) return e;
       int n = 1;
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fuse<NT>, NT, sizeof(TileSmem));
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fuse<NT, MINB>, NT, sizeof(TileSmem));
       per_sm[dev] = n > 0 ? n : 1;
     }
     resident = per_sm[dev];
@@ -73,16 +75,19 @@ static cudaError_t launch_fuse_t(const BatchDev* b, int64_t n_cells, cudaStream_
   const int64_t tiles = n_cells / kTile;
   const int64_t cap = (int64_t)sm_count() * resident;  // one resident wave
   const int grid = (int)(tiles < cap ? (tiles < 1 ? 1 : tiles) : cap);
-  k_fuse<NT><<<grid, NT, sizeof(TileSmem), s>>>(b);
+  k_fuse<NT, MINB><<<grid, NT, sizeof(TileSmem), s>>>(b);
   return cudaGetLastError();
 }
 
 bool is_fuse_kernel(const void* f) {
-  return f == reinterpret_cast<const void*>(&k_fuse<256>) || f == reinterpret_cast<const void*>(&k_fuse<512>);
+  return f == reinterpret_cast<const void*>(&k_fuse<256, 4>) || f == reinterpret_cast<const void*>(&k_fuse<512, 2>) ||
+         f == reinterpret_cast<const void*>(&k_fuse<512, 3>);
 }
 
 cudaError_t launch_fuse(const BatchDev* b, int64_t n_cells, int threads, cudaStream_t s) {
-  return threads >= 512 ? launch_fuse_t<512>(b, n_cells, s) : launch_fuse_t<256>(b, n_cells, s);
+  if (threads < 512) return launch_fuse_t<256, 4>(b, n_cells, s);
+  return n_cells / kTile >= 3 * (int64_t)sm_count() ? launch_fuse_t<512, 3>(b, n_cells, s)
+                                                    : launch_fuse_t<512, 2>(b, n_cells, s);
 }
 
 }  // namespace em
