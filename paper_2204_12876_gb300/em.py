@@ -162,9 +162,16 @@ def _stream_handle(stream) -> int | None:
     return stream.cuda_stream
 
 
+def _torch():
+    import torch  # imported on first use (the module loads without it)
+    return torch
+
+
+_F12 = ctypes.c_float * 12
+
+
 def _pose(pose) -> ctypes.Array:
-    p = np.ascontiguousarray(pose, dtype=np.float32).reshape(12)
-    return (ctypes.c_float * 12)(*[float(v) for v in p])
+    return _F12.from_buffer_copy(np.ascontiguousarray(pose, dtype=np.float32).reshape(12))
 
 
 def _cloud_struct(pts, pose, host: bool, any_device: bool = False) -> _Cloud:
@@ -172,16 +179,11 @@ def _cloud_struct(pts, pose, host: bool, any_device: bool = False) -> _Cloud:
         n, stride = pts.shape
         ptr = pts.ctypes.data
     else:
-        if pts.dtype.__str__() != "torch.float32" or not (pts.is_cuda or any_device) or not pts.is_contiguous():
+        if pts.dtype is not _torch().float32 or not (pts.is_cuda or any_device) or not pts.is_contiguous():
             raise ValueError("points must be a contiguous float32 CUDA tensor of shape (n, 3) or (n, 4)")
         n, stride = pts.shape
         ptr = pts.data_ptr()
-    c = _Cloud()
-    c.points = ptr
-    c.n = n
-    c.stride = stride
-    c.pose = _pose(pose)
-    return c
+    return _Cloud(ptr, n, stride, _pose(pose))
 
 
 class Map:
@@ -560,25 +562,29 @@ class Server:
         n = len(requests)
         reqs = (_Request * n)()
         keep = []
+        f32 = _torch().float32
         for q, (map_id, clouds, read) in enumerate(requests):
             on_host = not clouds[0][0].is_cuda
-            for p, _ in clouds:
-                if p.is_cuda == on_host or str(p.dtype) != "torch.float32" or not p.is_contiguous() or \
+            cs = []
+            for p, pose in clouds:
+                if p.is_cuda == on_host or p.dtype is not f32 or not p.is_contiguous() or \
                         p.dim() != 2 or p.shape[1] not in (3, 4) or (on_host and not p.is_pinned()):
                     raise ValueError("points: contiguous float32 (n, 3|4) tensors, all CUDA or all pinned CPU")
-            arr = (_Cloud * len(clouds))(*[_cloud_struct(p, pose, False, any_device=True) for p, pose in clouds])
+                cs.append(_Cloud(p.data_ptr(), p.shape[0], p.shape[1], _pose(pose)))
+            arr = (_Cloud * len(cs))(*cs)
             keep.append((arr, clouds, read))
-            reqs[q].map_id = int(map_id)
-            reqs[q].n_clouds = len(clouds)
-            reqs[q].clouds = arr
-            reqs[q].clouds_on_host = 1 if on_host else 0
+            r = reqs[q]
+            r.map_id = int(map_id)
+            r.n_clouds = len(cs)
+            r.clouds = arr
+            r.clouds_on_host = 1 if on_host else 0
             if read is not None:
                 mask, out = read
-                if out.dtype.__str__() != "torch.float32" or not out.is_contiguous():
+                if out.dtype is not f32 or not out.is_contiguous():
                     raise ValueError("read-back buffer must be a contiguous float32 tensor")
-                reqs[q].read_mask = int(mask)
-                reqs[q].read_to_host = 0 if out.is_cuda else 1
-                reqs[q].read_dst = out.data_ptr()
+                r.read_mask = int(mask)
+                r.read_to_host = 0 if out.is_cuda else 1
+                r.read_dst = out.data_ptr()
         tks = (ctypes.c_uint64 * n)()
         _check(lib.em_server_submit_many(self._h, reqs, n, ready.cuda_event if ready is not None else None, tks),
                "em_server_submit_many")
