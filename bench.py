@@ -75,6 +75,7 @@ BATCH_P = dict(resolution=0.04, noise_a0=0.005, noise_a2=0.002, var_min=1e-8, ma
 N_ROBOTS = 32
 RATE_HZ = 2000.0
 SWEEP_HZ = (2000.0, 10000.0, 40000.0)
+E2E_DEPTH = 3  # rounds in flight in the end-to-end leg (each with its own read-back buffer)
 CLOCK_SOAK_S = 1.0  # seconds of untimed load inside the clock sampler before the timed rounds
 BUDGET = 40 << 30
 L2_FLUSH_BYTES = 256 << 20
@@ -414,8 +415,8 @@ def run_ours(args, rank: int, world: int):
     # host memory (a client's ring of input buffers; the pools repeat every 8 rounds);
     # one submit_many per round hands them to the server, which copies each cloud to
     # the device by DMA on the batch's stream and writes each map's elevation into a
-    # page-locked host buffer right after its update.  Rounds are double-buffered:
-    # round k + 1 is queued before round k is waited for.
+    # page-locked host buffer right after its update.  E2E_DEPTH rounds are in
+    # flight: round k + E2E_DEPTH - 1 is queued before round k is waited for.
     P = 8
     packs = []
     for r in range(P):
@@ -424,13 +425,13 @@ def run_ours(args, rank: int, world: int):
     cells = [r["params"]["width"] * r["params"]["height"] for r in robots]
     offs = np.concatenate([[0], np.cumsum(cells)]).astype(np.int64)
     out_bytes = int(offs[-1]) * 4
-    host_out = [torch.empty(int(offs[-1]), dtype=torch.float32).pin_memory() for _ in range(2)]
+    host_out = [torch.empty(int(offs[-1]), dtype=torch.float32).pin_memory() for _ in range(E2E_DEPTH)]
 
     def e2e_launch(k):
         reqs = []
         for i in range(N_ROBOTS):
             reqs.append((sids[i], [packs[k % P][i]],
-                         (em.LAYER_ELEVATION, host_out[k % 2][int(offs[i]):int(offs[i + 1])])))
+                         (em.LAYER_ELEVATION, host_out[k % E2E_DEPTH][int(offs[i]):int(offs[i + 1])])))
         return served.submit_many(reqs)
 
     e2e_rounds = max(4, K)
@@ -438,11 +439,12 @@ def run_ours(args, rank: int, world: int):
     served.drain()
     barrier()
     t0 = time.perf_counter()
-    pending = e2e_launch(0)
-    for k in range(1, e2e_rounds + 1):
-        nxt = e2e_launch(k) if k < e2e_rounds else []
-        served.wait_many(pending)  # round k - 1: every map's elevation is now in host_out[(k - 1) % 2]
-        pending = nxt
+    inflight = [e2e_launch(k) for k in range(min(E2E_DEPTH - 1, e2e_rounds))]
+    for k in range(E2E_DEPTH - 1, e2e_rounds + E2E_DEPTH - 1):
+        if k < e2e_rounds:
+            inflight.append(e2e_launch(k))
+        # round k - E2E_DEPTH + 1: every map's elevation is now in its host_out buffer
+        served.wait_many(inflight.pop(0))
     barrier()
     e2e_s = max_over_ranks(time.perf_counter() - t0)
     e2e = {"value": e2e_rounds * round_pts * world / e2e_s, "unit": "points/s",
