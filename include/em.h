@@ -280,8 +280,9 @@ typedef struct em_tuning {
                            and lanes per marched chunk: 1, 2, 4, 8, 16 or 32 */
   int32_t fuse_chunk;   /* threads per fusion block (one tile of 1024 cells per block): 64 .. 1024, a
                            power of two; 512 and more run 512-thread blocks (three resident per SM
-                           when the update has at least three tiles per SM, else two), the rest
-                           256-thread ones */
+                           when the cell space has at least three tiles per SM -- for a graph-
+                           replayed batch the capacity's, else the update's -- otherwise two),
+                           the rest 256-thread ones */
   int32_t big_thresh;   /* tiles with more than 16 x big_thresh records are fused first: 32 .. 1023 */
 } em_tuning;
 
