@@ -121,3 +121,25 @@ def test_noalloc_binding_checks_layers_before_the_call(lib_path):
                           normals=(torch.zeros(3), ok_f, ok_f))
     with pytest.raises(ValueError, match="CUDA"):                # host tensors
         em.update_noalloc(p, ok_f, ok_f, ok_i, [(pts, pose)], t_now=1)
+
+
+def test_cloud_marshalling_without_gpu(lib_path):
+    """The binding's cloud descriptor (em_cloud): pointer, count, stride and the
+    row-major 3x4 pose as the library reads them; points that are not
+    contiguous float32 and poses that are not 12 numbers are refused."""
+    torch = pytest.importorskip("torch")
+    np = pytest.importorskip("numpy")
+    from paper_2204_12876_gb300 import em
+    pts = torch.arange(12, dtype=torch.float32).reshape(4, 3)
+    pose = np.arange(12, dtype=np.float64).reshape(3, 4) / 8.0  # converted to float32, row-major
+    c = em._cloud_struct(pts, pose, False, any_device=True)
+    assert c.points == pts.data_ptr() and c.n == 4 and c.stride == 3
+    assert list(c.pose) == [v / 8.0 for v in range(12)]
+    c4 = em._cloud_struct(torch.zeros((7, 4)), pose.reshape(12), False, any_device=True)
+    assert c4.n == 7 and c4.stride == 4
+    with pytest.raises(ValueError):
+        em._cloud_struct(pts.double(), pose, False, any_device=True)
+    with pytest.raises(ValueError):
+        em._cloud_struct(torch.zeros((3, 4)).t(), pose, False, any_device=True)  # not contiguous
+    with pytest.raises(ValueError):
+        em._pose(np.zeros(11))
